@@ -1,0 +1,147 @@
+"""Seeded synthetic frames for the blob-detection filter bank.
+
+This module only draws inputs: it holds none of the filter-bank arithmetic, and
+both the CUDA path and the FP64 oracle take their inputs from it.  The frames
+stand in for the aerial surveillance imagery of Kennedy (arXiv:1912.07133,
+Sec. 5, Fig. 9), which is not available: Gaussian-profile blobs (the blob model
+of Sec. 5: a bright or dark bivariate Gaussian) on uniform or 1/f backgrounds.
+
+A blob of semi-axes (r_a, r_b) has profile A exp(-2 (u^2/r_a^2 + v^2/r_b^2)),
+i.e. a Gaussian of standard deviation r/2 along each axis, so a blob of radius
+r is matched by the filter scale lambda = r (sigma = lambda / 2, Sec. 5).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+#: scale lists (blob radius lambda in pixels) of the reference workloads
+SCALES_TINY = (4.0,)
+SCALES_IIR_FIR = (2.0, 4.0, 8.0, 16.0, 32.0, 48.0)
+SCALES_EIGHT = tuple(2.0 * 32.0 ** (s / 7.0) for s in range(8))
+BATCH_SIZES = ((1024, 768), (1920, 1080), (2048, 2048), (4096, 3072), (6144, 4096))
+
+
+def _render_blobs(img: np.ndarray, rng: np.random.Generator, n: int, rmin: float,
+                  rmax: float, amin: float, amax: float, elliptical: bool,
+                  bipolar: bool) -> None:
+    H, W = img.shape
+    for _ in range(n):
+        cx = rng.uniform(0, W)
+        cy = rng.uniform(0, H)
+        ra = rng.uniform(rmin, rmax)
+        rb = ra * rng.uniform(0.5, 1.0) if elliptical else ra
+        th = rng.uniform(0, math.pi) if elliptical else 0.0
+        amp = rng.uniform(amin, amax)
+        if bipolar and rng.uniform() < 0.5:
+            amp = -amp
+        ext = int(math.ceil(3.0 * ra)) + 1
+        x0, x1 = max(0, int(cx) - ext), min(W, int(cx) + ext + 1)
+        y0, y1 = max(0, int(cy) - ext), min(H, int(cy) + ext + 1)
+        if x0 >= x1 or y0 >= y1:
+            continue
+        yy, xx = np.mgrid[y0:y1, x0:x1]
+        dx = xx + 0.0 - cx
+        dy = yy + 0.0 - cy
+        u = dx * math.cos(th) + dy * math.sin(th)
+        v = -dx * math.sin(th) + dy * math.cos(th)
+        img[y0:y1, x0:x1] += amp * np.exp(-2.0 * (u * u / (ra * ra) + v * v / (rb * rb)))
+
+
+def one_over_f(rng: np.random.Generator, H: int, W: int, std: float) -> np.ndarray:
+    """Background with power spectrum ~ |f|^-2 (amplitude ~ 1/|f|), DC removed."""
+    white = rng.standard_normal((H, W))
+    F = np.fft.rfft2(white)
+    fy = np.fft.fftfreq(H)[:, None]
+    fx = np.fft.rfftfreq(W)[None, :]
+    f = np.sqrt(fx * fx + fy * fy)
+    f[0, 0] = 1.0
+    F /= f
+    F[0, 0] = 0.0
+    bg = np.fft.irfft2(F, s=(H, W))
+    bg *= std / bg.std()
+    return bg
+
+
+def tiny_frame(seed: int = 0, H: int = 512, W: int = 512, nblobs: int = 20) -> np.ndarray:
+    """One FP32 frame: U[0, 0.1] background plus 20 bright round blobs, radii
+    2-8 px, amplitudes 0.5-1 (the 512 x 512 single-scale workload)."""
+    rng = np.random.default_rng(seed)
+    img = rng.uniform(0.0, 0.1, (H, W))
+    _render_blobs(img, rng, nblobs, 2.0, 8.0, 0.5, 1.0, False, False)
+    return img.astype(np.float32)
+
+
+def iir_fir_frame(seed: int = 1, H: int = 4096, W: int = 4096, nblobs: int = 500) -> np.ndarray:
+    """One FP32 frame: 1/f background (std 0.1) plus bright and dark elliptical
+    blobs, radii 2-48 px, random orientation (the 4096 x 4096 six-scale
+    workload)."""
+    rng = np.random.default_rng(seed)
+    img = one_over_f(rng, H, W, 0.1)
+    _render_blobs(img, rng, nblobs, 2.0, 48.0, 0.5, 1.0, True, True)
+    return img.astype(np.float32)
+
+
+def batch_frames(seed: int = 2, nframes: int = 64, sizes=BATCH_SIZES,
+                 density: float = 20.0 / (512 * 512)):
+    """Uneven batch: frame sizes drawn uniformly from ``sizes`` (W, H); each
+    frame uses the tiny-frame generator at 20 blobs per 512^2."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nframes):
+        W, H = sizes[rng.integers(len(sizes))]
+        out.append(tiny_frame(int(rng.integers(1 << 31)), H, W, int(round(density * H * W))))
+    return out
+
+
+def counts_frame(seed: int = 3, H: int = 8192, W: int = 8192, nblobs: int = 2000,
+                 gain: float = 2500.0) -> np.ndarray:
+    """12-bit uint16 frame: Poisson(gain * (0.5 + 1/f background + blobs)),
+    clipped to 4095; radii 2-64 px."""
+    rng = np.random.default_rng(seed)
+    img = 0.5 + one_over_f(rng, H, W, 0.1)
+    _render_blobs(img, rng, nblobs, 2.0, 64.0, 0.3, 0.6, True, True)
+    lam = np.clip(gain * img, 0.0, None)
+    return np.clip(rng.poisson(lam), 0, 4095).astype(np.uint16)
+
+
+def clustered_frame(seed: int = 4, H: int = 6144, W: int = 6144, tile: int = 64,
+                    active_fraction: float = 0.05, blobs_per_tile: float = 2.0) -> np.ndarray:
+    """Sparse blob clusters covering about ``active_fraction`` of the 64 x 64
+    tiles, on a 1/f background; radii 2-64 px; FP16 storage."""
+    rng = np.random.default_rng(seed)
+    img = one_over_f(rng, H, W, 0.1)
+    th, tw = H // tile, W // tile
+    n_active = max(1, int(round(active_fraction * th * tw)))
+    # clusters: random seeds grown by neighbours so active tiles are grouped
+    active = np.zeros((th, tw), bool)
+    while active.sum() < n_active:
+        cy, cx = rng.integers(th), rng.integers(tw)
+        size = int(rng.integers(1, 7))
+        for _ in range(size):
+            active[np.clip(cy, 0, th - 1), np.clip(cx, 0, tw - 1)] = True
+            cy += int(rng.integers(-1, 2))
+            cx += int(rng.integers(-1, 2))
+    for ty, tx in zip(*np.nonzero(active)):
+        sub = np.zeros((tile, tile))
+        k = rng.poisson(blobs_per_tile)
+        _render_blobs(sub, rng, k, 2.0, min(64.0, tile / 2), 0.5, 1.0, True, True)
+        img[ty * tile:(ty + 1) * tile, tx * tile:(tx + 1) * tile] += sub
+    return img.astype(np.float16)
+
+
+@dataclass
+class Workload:
+    name: str
+    scales: tuple
+    note: str
+
+
+WORKLOADS = {
+    "tiny": Workload("tiny 512x512 FP32, 1 scale (lambda 4), Filter D 3rd order", SCALES_TINY,
+                     "tiny_frame(seed=0)"),
+    "iir_fir_4096": Workload("4096x4096 FP32, 6 scales (lambda 2..48), Filter D 4th order "
+                             "and colored SG FIR", SCALES_IIR_FIR, "iir_fir_frame(seed=1)"),
+}
