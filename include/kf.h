@@ -1,0 +1,184 @@
+/*
+ * kf.h -- C ABI of the GB300 (sm_103a) multi-scale shape-filter bank.
+ *
+ * Kennedy, "Digital filters with vanishing moments for shape analysis"
+ * (arXiv:1912.07133).  A low-pass blur (repeated-pole IIR "Filter D",
+ * Sec. 4.3 / Table IV; discrete Butterworth IIR "Filter E", Sec. 4.4;
+ * colored Savitzky-Golay FIR "Filter C", Sec. 4.2) is cascaded with the
+ * derivative filters of Table I and a scale-space extremum detector (Sec. 5,
+ * eqs 26-27).  Every stage runs in the library's CUDA kernels.
+ *
+ * Conventions
+ *   - Status codes: 0 (KF_OK) or a negative KF_E* value.  No C++ exception
+ *     crosses this boundary.  kf_last_error() describes the last failure of a
+ *     context (thread-unsafe per context; use one context per thread).
+ *   - Pointers named "device" must be CUDA device pointers on the context's
+ *     device; "host" pointers are ordinary host memory.  The caller owns every
+ *     pointer it passes; the library never frees them.  The context owns its
+ *     workspace (intermediate planes, carries, candidate list).
+ *   - Images are row-major: element (x, y) of a frame is data[y * pitch + x],
+ *     0 <= x < width, 0 <= y < height, pitch >= width (in elements).
+ *   - Scales are blob radii lambda in pixels; the filters use
+ *     sigma = lambda / 2 (Sec. 5).
+ */
+#ifndef KF_H
+#define KF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define KF_OK 0
+#define KF_EINVAL -1     /* invalid argument (sizes, enums, sigma, pointers)   */
+#define KF_ECOND -2      /* a filter design failed (singular / ill-conditioned) */
+#define KF_ENOMEM -3     /* device allocation failed                            */
+#define KF_ECUDA -4      /* a CUDA runtime call or kernel launch failed         */
+#define KF_ETIMEOUT -5   /* a bounded device-side wait gave up                  */
+#define KF_EOVERFLOW -6  /* output capacity too small; *count holds the need    */
+#define KF_ENODEV -7     /* no usable CUDA device                               */
+
+/* ---- enumerations -------------------------------------------------------- */
+#define KF_IIR_REPEATED_POLE 0 /* Filter D, Sec. 4.3 / Table IV                  */
+#define KF_IIR_BUTTERWORTH 1   /* Filter E, Sec. 4.4                             */
+#define KF_FIR_COLORED_SG 2    /* Filter C, Sec. 4.2                             */
+
+#define KF_DTYPE_F32 0
+#define KF_DTYPE_F16 1
+#define KF_DTYPE_BF16 2
+#define KF_DTYPE_U16 3
+
+#define KF_RESP_LAPLACIAN 0 /* R_L = -sigma^2 (D20 + D02)                        */
+#define KF_RESP_HESSIAN 1   /* R_H = sigma^4 (D20 D02 - D11^2), eq (26)          */
+
+#define KF_BOUNDARY_HOLD 0 /* frame edges held to +-infinity (Appendix, A32)     */
+
+#define KF_NEIGH_ALL_SCALES 0 /* extremum over 3 x 3 x (all scales)            */
+#define KF_NEIGH_ADJACENT 1   /* extremum over 3 x 3 x (scale -1, 0, +1)       */
+
+#define KF_MAX_SCALES 16
+#define KF_MAX_ORDER 8
+#define KF_MAX_FIR_K 160
+
+/* ---- data structures ------------------------------------------------------ */
+
+/* Coefficients of one designed blur (host-side copy of the FP64 design).
+ * IIR (types 0, 1): three-term DE of eqs (A6)-(A10): y = y+ + y- + b0 x with
+ *   y+(n) = sum_{m=1..K} bplus[m] x(n-m) - sum_{m=1..K} aplus[m] y+(n-m),
+ *   y- the mirror image (b- = b+, a- = a+), aplus[0] = 1, bplus[0] = 0.
+ * FIR (type 2): taps h[0..K], h(-m) = h(m), eq (A5).
+ * dc_gain and moment2 are the realised sum h(m) and sum m^2 h(m) (design
+ * self-check; 1 and 0 by construction, eq 7). */
+typedef struct {
+  int32_t type, order, K, reserved;
+  double scale;  /* lambda (px) */
+  double sigma;  /* lambda / 2 */
+  double param;  /* D: pole p = exp(-1/sigma); E: cut-off omega_c; C: omega_c */
+  double b0;
+  double bplus[KF_MAX_ORDER + 1];
+  double aplus[KF_MAX_ORDER + 1];
+  double h[KF_MAX_FIR_K + 1];
+  double dc_gain;
+  double moment2;
+} kf_coeffs;
+
+/* One input frame (device memory). */
+typedef struct {
+  const void *data;    /* device pointer, dtype elements                       */
+  int32_t width;       /* 1 .. 8192                                            */
+  int32_t height;      /* >= 1                                                 */
+  int64_t pitch;       /* elements between rows, >= width                      */
+  int32_t dtype;       /* KF_DTYPE_*                                           */
+  float value_scale;   /* input multiplier (e.g. 1/4095 for 12-bit counts); 0 = 1 */
+} kf_frame;
+
+/* Options of one filter-bank call. */
+typedef struct {
+  int32_t response;      /* KF_RESP_*                                          */
+  int32_t boundary;      /* KF_BOUNDARY_HOLD (only hold is implemented)        */
+  int32_t neighbourhood; /* KF_NEIGH_*                                         */
+  int32_t storage;       /* intermediate planes: KF_DTYPE_F32 / F16 / BF16     */
+  double threshold;      /* Threshold #1: |R| > threshold to be a candidate    */
+  int32_t fir_kmax;      /* cap on the colored-SG half-length (0 -> 96)        */
+  int32_t reserved0;
+  float *responses;      /* optional device output, f32: for frame f, scale s,
+                            R at (x, y) is responses[off_f + (s*H + y)*W + x],
+                            off_f = sum over earlier frames of nscales*H*W.
+                            NULL: not written.                                 */
+  int64_t reserved[4];
+} kf_bank_opts;
+
+/* One detection (Threshold #1 extremum). */
+typedef struct {
+  int32_t frame, x, y, scale;
+  int32_t polarity;  /* +1 bright (maximum of R), -1 dark (minimum of R_L) */
+  float response;    /* R at (x, y, scale) */
+} kf_blob;
+
+typedef struct kf_ctx kf_ctx;
+
+/* ---- entry points --------------------------------------------------------- */
+
+/* Fill *opts with defaults: Laplacian response, hold boundary, all-scales
+ * neighbourhood, f32 storage, threshold 0.05, fir_kmax 96, no responses.
+ * Returns KF_OK or KF_EINVAL (NULL). */
+int kf_bank_opts_default(kf_bank_opts *opts);
+
+/* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *ctx receives the
+ * handle (host).  Errors: KF_EINVAL (ctx NULL), KF_ENODEV, KF_ECUDA. */
+int kf_create(kf_ctx **ctx, int device, void *cuda_stream);
+
+/* Free the context and its workspace (synchronises its stream).  NULL is a
+ * no-op. */
+void kf_destroy(kf_ctx *ctx);
+
+/* Message for the last failure on this context ("" if none); valid until the
+ * next call on the context.  ctx NULL gives the message of the last
+ * context-less call (kf_design). */
+const char *kf_last_error(const kf_ctx *ctx);
+
+/* Design one blur in FP64 on the current CUDA device (Sec. 4; the same
+ * design kernel kf_filter_bank runs) and copy it to *out (host, caller-owned).
+ *   type  KF_IIR_REPEATED_POLE: order = K^lpf = L_D + Lpi with L_D = 1
+ *         (3 = Table IV, 4 = the fourth-order blur); p = exp(-1/sigma)
+ *         (Sec. 4.3).
+ *         KF_IIR_BUTTERWORTH: order = L_B / 2 = L_D + 1 (2 for D = 3);
+ *         omega_c = sqrt(2 ln 2) / sigma, bilinear transform (Sec. 4.4).
+ *         KF_FIR_COLORED_SG: order = L_D (1 or 2); K = ceil(5 sigma)
+ *         (ceil(7 sigma) for L_D = 2) capped at 96, omega_c = 3 / sigma
+ *         (Sec. 4.2).
+ *   scale lambda in pixels, sigma = lambda / 2 (Sec. 5).
+ * Errors: KF_EINVAL (bad type/order, sigma <= 0, colored SG with
+ * 3/sigma >= pi), KF_ECOND (design solve failed), KF_ENODEV, KF_ECUDA. */
+int kf_design(int type, int order, double scale, kf_coeffs *out);
+
+/* Run the bank on `nframes` frames (host array of descriptors pointing to
+ * device images) for `nscales` scales (host array of lambdas, ascending not
+ * required, <= KF_MAX_SCALES) with one blur type/order: designs (FP64
+ * kernel), separable blur of the derivative-filtered frame (Table I taps),
+ * response and the scale-space extremum detector (Sec. 5).  Candidates with
+ * |R| > opts->threshold are kept in the context for kf_detect_blobs; a new
+ * call replaces them.  Asynchronous on the context stream: the frames must
+ * stay valid until the stream reaches this work.
+ * Errors: KF_EINVAL (arguments, unsupported option), KF_ECOND, KF_ENOMEM,
+ * KF_ECUDA. */
+int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes,
+                   const double *scales, int nscales, int type, int order,
+                   const kf_bank_opts *opts);
+
+/* Copy the candidates of the last kf_filter_bank call with |R| > threshold
+ * into out[0..capacity) (host, caller-owned), sorted by (frame, scale, y, x);
+ * *count (host) receives the number of such blobs.  threshold must be >= the
+ * bank's opts->threshold.  Synchronises the context stream.
+ * Errors: KF_EINVAL, KF_EOVERFLOW (capacity < *count; the first `capacity`
+ * blobs are written), KF_ECUDA. */
+int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out,
+                    int64_t capacity, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KF_H */

@@ -1,0 +1,416 @@
+// kf_api.cu -- host implementation of the C ABI declared in include/kf.h:
+// argument checks, workspace, design cache, kernel launches, candidate
+// read-back.  Every arithmetic step of the filter bank runs in the kernels of
+// kf_design.cu, kf_iir.cu and kf_fir.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kf.h"
+#include "kf_common.cuh"
+#include "kf_internal.h"
+
+struct kf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // workspace (grown on demand)
+  float *P = nullptr;
+  size_t P_floats = 0;
+  float *edge = nullptr;
+  size_t edge_floats = 0;
+  float *carry = nullptr;
+  size_t carry_floats = 0;
+  kf::Coef *coef = nullptr;
+  double *lambdas = nullptr;
+  double *dwork = nullptr;
+  int dwork_nmax = 0;
+  kf::DevStatus *status = nullptr;
+  kf::Blob *blobs = nullptr;
+  long blob_cap = 0;
+  // design cache: (type, order, kmax, scales) -> coef
+  bool design_valid = false;
+  int d_type = -1, d_order = -1, d_kmax = -1, d_S = 0;
+  double d_lam[KF_MAX_SCALES];
+  std::vector<kf::Coef> h_coef;
+  // last bank call
+  bool have_result = false;
+  double last_threshold = 0.0;
+  int last_S = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(kf_ctx *ctx, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(kf_ctx *ctx, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else g_err = buf;
+  return code;
+}
+
+int cuda_fail(kf_ctx *ctx, cudaError_t e, const char *what) {
+  return fail(ctx, e == cudaErrorMemoryAllocation ? KF_ENOMEM : KF_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+template <class T>
+int grow(kf_ctx *ctx, T **p, size_t *have, size_t need, const char *what) {
+  if (*have >= need && *p) return KF_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc((void **)p, need * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(ctx, e, what);
+  }
+  *have = need;
+  return KF_OK;
+}
+
+int nmax_for(int type, int order, int kmax) {
+  if (type != KF_FIR_COLORED_SG) return 1;
+  return kmax + 1 + order + 1;
+}
+
+// Run the FP64 design kernel for (type, order, scales) unless the context
+// already holds exactly this design; returns the per-scale records on host.
+int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S, int kmax) {
+  if (ctx->design_valid && ctx->d_type == type && ctx->d_order == order && ctx->d_kmax == kmax &&
+      ctx->d_S == S && std::equal(scales, scales + S, ctx->d_lam))
+    return KF_OK;
+  ctx->design_valid = false;
+  cudaError_t e;
+  if (!ctx->coef) {
+    if ((e = cudaMalloc(&ctx->coef, sizeof(kf::Coef) * KF_MAX_SCALES)) != cudaSuccess)
+      return cuda_fail(ctx, e, "cudaMalloc(coef)");
+    if ((e = cudaMalloc(&ctx->lambdas, sizeof(double) * KF_MAX_SCALES)) != cudaSuccess)
+      return cuda_fail(ctx, e, "cudaMalloc(lambdas)");
+  }
+  const int nmax = nmax_for(type, order, kmax);
+  if (nmax > ctx->dwork_nmax) {
+    if (ctx->dwork) cudaFree(ctx->dwork);
+    ctx->dwork = nullptr;
+    size_t n = (size_t)KF_MAX_SCALES * ((size_t)nmax * nmax + 2 * nmax);
+    if ((e = cudaMalloc(&ctx->dwork, n * sizeof(double))) != cudaSuccess)
+      return cuda_fail(ctx, e, "cudaMalloc(design work)");
+    ctx->dwork_nmax = nmax;
+  }
+  if ((e = cudaMemcpyAsync(ctx->lambdas, scales, sizeof(double) * S, cudaMemcpyHostToDevice,
+                           ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "copy scales");
+  if (kf::launch_design(type, order, ctx->lambdas, S, kmax, ctx->coef, ctx->dwork, ctx->dwork_nmax,
+                        ctx->stream))
+    return cuda_fail(ctx, cudaGetLastError(), "design kernel launch");
+  ctx->h_coef.resize(S);
+  if ((e = cudaMemcpyAsync(ctx->h_coef.data(), ctx->coef, sizeof(kf::Coef) * S,
+                           cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "copy design");
+  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "design");
+  for (int s = 0; s < S; ++s) {
+    const kf::Coef &c = ctx->h_coef[s];
+    if (c.status == 1)
+      return fail(ctx, KF_EINVAL, "design: invalid parameters for scale %g (type %d, order %d)",
+                  scales[s], type, order);
+    if (c.status != 0)
+      return fail(ctx, KF_ECOND, "design failed for scale %g (code %d)", scales[s], c.status);
+    if (!(std::fabs(c.dc_gain - 1.0) < 1e-6))
+      return fail(ctx, KF_ECOND, "design for scale %g has dc gain %.9g", scales[s], c.dc_gain);
+  }
+  ctx->design_valid = true;
+  ctx->d_type = type;
+  ctx->d_order = order;
+  ctx->d_kmax = kmax;
+  ctx->d_S = S;
+  std::copy(scales, scales + S, ctx->d_lam);
+  return KF_OK;
+}
+
+int check_type_order(kf_ctx *ctx, int type, int order) {
+  if (type == KF_IIR_REPEATED_POLE && (order < 2 || order > 6))
+    return fail(ctx, KF_EINVAL, "repeated-pole order must be 2..6 (got %d)", order);
+  if (type == KF_IIR_BUTTERWORTH && (order < 1 || order > 6))
+    return fail(ctx, KF_EINVAL, "Butterworth order (L_B/2) must be 1..6 (got %d)", order);
+  if (type == KF_FIR_COLORED_SG && order != 1 && order != 2)
+    return fail(ctx, KF_EINVAL, "colored SG order (L_D) must be 1 or 2 (got %d)", order);
+  if (type < 0 || type > 2) return fail(ctx, KF_EINVAL, "unknown filter type %d", type);
+  return KF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kf_bank_opts_default(kf_bank_opts *o) {
+  if (!o) return KF_EINVAL;
+  std::memset(o, 0, sizeof *o);
+  o->response = KF_RESP_LAPLACIAN;
+  o->boundary = KF_BOUNDARY_HOLD;
+  o->neighbourhood = KF_NEIGH_ALL_SCALES;
+  o->storage = KF_DTYPE_F32;
+  o->threshold = 0.05;
+  o->fir_kmax = 96;
+  o->responses = nullptr;
+  return KF_OK;
+}
+
+int kf_create(kf_ctx **out, int device, void *stream) {
+  if (!out) return fail(nullptr, KF_EINVAL, "kf_create: ctx is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) return fail(nullptr, KF_ENODEV, "no CUDA device");
+  if (device < 0 || device >= n) return fail(nullptr, KF_EINVAL, "device %d out of range", device);
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+  kf_ctx *ctx = new kf_ctx();
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  if ((e = cudaMalloc(&ctx->status, sizeof(kf::DevStatus))) != cudaSuccess) {
+    delete ctx;
+    return cuda_fail(nullptr, e, "cudaMalloc(status)");
+  }
+  ctx->blob_cap = 1 << 20;
+  if ((e = cudaMalloc(&ctx->blobs, sizeof(kf::Blob) * ctx->blob_cap)) != cudaSuccess) {
+    cudaFree(ctx->status);
+    delete ctx;
+    return cuda_fail(nullptr, e, "cudaMalloc(blobs)");
+  }
+  *out = ctx;
+  return KF_OK;
+}
+
+void kf_destroy(kf_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->P);
+  cudaFree(ctx->edge);
+  cudaFree(ctx->carry);
+  cudaFree(ctx->coef);
+  cudaFree(ctx->lambdas);
+  cudaFree(ctx->dwork);
+  cudaFree(ctx->status);
+  cudaFree(ctx->blobs);
+  delete ctx;
+}
+
+const char *kf_last_error(const kf_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+int kf_design(int type, int order, double scale, kf_coeffs *out) {
+  if (!out) return fail(nullptr, KF_EINVAL, "kf_design: out is NULL");
+  if (!(scale > 0.0) || !std::isfinite(scale))
+    return fail(nullptr, KF_EINVAL, "kf_design: scale must be > 0");
+  kf_ctx tmp;
+  int rc = check_type_order(&tmp, type, order);
+  if (rc) return fail(nullptr, rc, "%s", tmp.err.c_str());
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return fail(nullptr, KF_ENODEV, "no CUDA device");
+  cudaGetDevice(&tmp.device);
+  rc = ensure_design(&tmp, type, order, &scale, 1, 96);
+  cudaFree(tmp.coef);
+  cudaFree(tmp.lambdas);
+  cudaFree(tmp.dwork);
+  if (rc) return fail(nullptr, rc, "%s", tmp.err.c_str());
+  const kf::Coef &c = tmp.h_coef[0];
+  std::memset(out, 0, sizeof *out);
+  out->type = type;
+  out->order = order;
+  out->scale = scale;
+  out->sigma = c.sigma;
+  out->param = c.param;
+  out->b0 = c.db0;
+  out->dc_gain = c.dc_gain;
+  out->moment2 = c.moment2;
+  if (type == KF_FIR_COLORED_SG) {
+    out->K = c.K;
+    for (int k = 0; k <= c.K; ++k) out->h[k] = c.dh[k];
+  } else {
+    const int K = (type == KF_IIR_REPEATED_POLE) ? order : order;
+    out->K = K;
+    for (int m = 0; m <= K; ++m) {
+      out->bplus[m] = c.dbplus[m];
+      out->aplus[m] = c.daplus[m];
+    }
+  }
+  return KF_OK;
+}
+
+int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *scales, int nscales,
+                   int type, int order, const kf_bank_opts *opts_in) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_filter_bank: ctx is NULL");
+  ctx->have_result = false;
+  kf_bank_opts opts;
+  if (opts_in) opts = *opts_in;
+  else kf_bank_opts_default(&opts);
+  if (!frames || nframes < 1) return fail(ctx, KF_EINVAL, "need at least one frame");
+  if (!scales || nscales < 1 || nscales > KF_MAX_SCALES)
+    return fail(ctx, KF_EINVAL, "nscales must be 1..%d", KF_MAX_SCALES);
+  for (int s = 0; s < nscales; ++s)
+    if (!(scales[s] > 0.0) || !std::isfinite(scales[s]))
+      return fail(ctx, KF_EINVAL, "scale %d must be > 0", s);
+  int rc = check_type_order(ctx, type, order);
+  if (rc) return rc;
+  if (opts.response != KF_RESP_LAPLACIAN)
+    return fail(ctx, KF_EINVAL, "only the Laplacian response is implemented");
+  if (opts.boundary != KF_BOUNDARY_HOLD) return fail(ctx, KF_EINVAL, "only the hold boundary is implemented");
+  if (opts.neighbourhood != KF_NEIGH_ALL_SCALES && opts.neighbourhood != KF_NEIGH_ADJACENT)
+    return fail(ctx, KF_EINVAL, "unknown neighbourhood %d", opts.neighbourhood);
+  if (opts.storage != KF_DTYPE_F32) return fail(ctx, KF_EINVAL, "only f32 storage is implemented");
+  if (!(opts.threshold >= 0.0)) return fail(ctx, KF_EINVAL, "threshold must be >= 0");
+  const int kmax_opt = opts.fir_kmax > 0 ? opts.fir_kmax : 96;
+  if (kmax_opt > KF_MAX_FIR_K) return fail(ctx, KF_EINVAL, "fir_kmax must be <= %d", KF_MAX_FIR_K);
+  long maxH = 0, maxPW = 0;
+  size_t maxplane = 0;
+  for (int f = 0; f < nframes; ++f) {
+    const kf_frame &fr = frames[f];
+    if (!fr.data) return fail(ctx, KF_EINVAL, "frame %d: data is NULL", f);
+    if (fr.width < 1 || fr.height < 1 || fr.pitch < fr.width)
+      return fail(ctx, KF_EINVAL, "frame %d: bad geometry %dx%d pitch %lld", f, fr.width, fr.height,
+                  (long long)fr.pitch);
+    if (fr.width > 8192) return fail(ctx, KF_EINVAL, "frame %d: width > 8192", f);
+    if (fr.dtype != KF_DTYPE_F32) return fail(ctx, KF_EINVAL, "frame %d: only f32 input is implemented", f);
+    if (fr.value_scale != 0.0f && fr.value_scale != 1.0f)
+      return fail(ctx, KF_EINVAL, "frame %d: value_scale is only supported for u16 input", f);
+    const long PW = ((long)fr.width + 31) / 32 * 32;
+    maxH = std::max(maxH, (long)fr.height);
+    maxPW = std::max(maxPW, PW);
+    maxplane = std::max(maxplane, (size_t)fr.height * PW);
+  }
+  cudaError_t e;
+  if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  rc = ensure_design(ctx, type, order, scales, nscales, kmax_opt);
+  if (rc) return rc;
+  int nstate = 0, kmax = 0;
+  for (int s = 0; s < nscales; ++s) {
+    nstate = std::max(nstate, ctx->h_coef[s].K);
+    kmax = std::max(kmax, ctx->h_coef[s].K);
+  }
+  const int nf = (type == KF_IIR_BUTTERWORTH) ? 2 * nstate : nstate;
+  if ((rc = grow(ctx, &ctx->P, &ctx->P_floats, (size_t)nscales * maxplane, "planes"))) return rc;
+  if ((rc = grow(ctx, &ctx->edge, &ctx->edge_floats, (size_t)nscales * 2 * maxPW, "edge rows"))) return rc;
+  if (type != KF_FIR_COLORED_SG) {
+    size_t need = 0;
+    for (int f = 0; f < nframes; ++f) {
+      const long PW = ((long)frames[f].width + 31) / 32 * 32;
+      need = std::max(need, kf::iir_carry_floats(frames[f].height, PW, nscales, nf));
+    }
+    if ((rc = grow(ctx, &ctx->carry, &ctx->carry_floats, need, "carries"))) return rc;
+  }
+  if ((e = cudaMemsetAsync(ctx->status, 0, sizeof(kf::DevStatus), ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "reset status");
+  kf::BankArgs a;
+  a.coef = ctx->coef;
+  a.S = nscales;
+  a.type = type;
+  a.nstate = nstate;
+  a.kmax = kmax;
+  a.threshold = (float)opts.threshold;
+  a.neigh = opts.neighbourhood;
+  a.P = ctx->P;
+  a.edge = ctx->edge;
+  a.carry = ctx->carry;
+  a.blobs = ctx->blobs;
+  a.cap = ctx->blob_cap;
+  a.status = ctx->status;
+  a.responses = opts.responses;
+  long resp_off = 0;
+  for (int f = 0; f < nframes; ++f) {
+    const kf_frame &fr = frames[f];
+    kf::FrameGeom g;
+    g.X = static_cast<const float *>(fr.data);
+    g.xpitch = fr.pitch;
+    g.H = fr.height;
+    g.W = fr.width;
+    g.PW = ((long)fr.width + 31) / 32 * 32;
+    g.frame = f;
+    g.resp_off = resp_off;
+    resp_off += (long)nscales * fr.height * fr.width;
+    int lr = (type == KF_FIR_COLORED_SG) ? kf::launch_fir_frame(g, a, ctx->stream)
+                                         : kf::launch_iir_frame(g, a, ctx->stream);
+    if (lr == -2) return fail(ctx, KF_EINVAL, "no kernel instance for order %d", order);
+    if (lr) return cuda_fail(ctx, cudaGetLastError(), "filter-bank kernel launch");
+  }
+  ctx->have_result = true;
+  ctx->last_threshold = opts.threshold;
+  ctx->last_S = nscales;
+  return KF_OK;
+}
+
+int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacity, int64_t *count) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_detect_blobs: ctx is NULL");
+  if (!count || capacity < 0 || (capacity > 0 && !out))
+    return fail(ctx, KF_EINVAL, "kf_detect_blobs: bad output arguments");
+  if (!ctx->have_result) return fail(ctx, KF_EINVAL, "kf_detect_blobs: no filter-bank result");
+  if (!(threshold >= ctx->last_threshold))
+    return fail(ctx, KF_EINVAL, "threshold %g is below the bank threshold %g", threshold,
+                ctx->last_threshold);
+  cudaError_t e;
+  if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  kf::DevStatus st;
+  if ((e = cudaMemcpyAsync(&st, ctx->status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "read status");
+  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "filter bank");
+  if (st.error) return fail(ctx, KF_ETIMEOUT, "device wait gave up (code %d)", st.error);
+  if (st.count > (unsigned long long)ctx->blob_cap) {
+    *count = (int64_t)st.count;
+    // grow for the next call; this call's list is incomplete
+    cudaFree(ctx->blobs);
+    ctx->blobs = nullptr;
+    long ncap = (long)st.count + (long)st.count / 4 + 1024;
+    if ((e = cudaMalloc(&ctx->blobs, sizeof(kf::Blob) * ncap)) != cudaSuccess) {
+      ctx->blob_cap = 0;
+      return cuda_fail(ctx, e, "cudaMalloc(blobs)");
+    }
+    ctx->blob_cap = ncap;
+    ctx->have_result = false;
+    return fail(ctx, KF_EOVERFLOW,
+                "candidate list overflowed (%llu found); capacity raised, run the bank again",
+                (unsigned long long)st.count);
+  }
+  std::vector<kf::Blob> h((size_t)st.count);
+  if (st.count) {
+    if ((e = cudaMemcpyAsync(h.data(), ctx->blobs, sizeof(kf::Blob) * st.count, cudaMemcpyDeviceToHost,
+                             ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "copy blobs");
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "copy blobs");
+  }
+  std::vector<kf::Blob> keep;
+  keep.reserve(h.size());
+  for (const kf::Blob &b : h)
+    if (std::fabs((double)b.response) > threshold) keep.push_back(b);
+  std::sort(keep.begin(), keep.end(), [](const kf::Blob &a, const kf::Blob &b) {
+    if (a.frame != b.frame) return a.frame < b.frame;
+    if (a.scale != b.scale) return a.scale < b.scale;
+    if (a.y != b.y) return a.y < b.y;
+    return a.x < b.x;
+  });
+  *count = (int64_t)keep.size();
+  const int64_t n = std::min<int64_t>(capacity, (int64_t)keep.size());
+  for (int64_t i = 0; i < n; ++i) {
+    out[i].frame = keep[i].frame;
+    out[i].x = keep[i].x;
+    out[i].y = keep[i].y;
+    out[i].scale = keep[i].scale;
+    out[i].polarity = keep[i].polarity;
+    out[i].response = keep[i].response;
+  }
+  if ((int64_t)keep.size() > capacity)
+    return fail(ctx, KF_EOVERFLOW, "capacity %lld < %lld blobs", (long long)capacity,
+                (long long)keep.size());
+  return KF_OK;
+}
+
+}  // extern "C"

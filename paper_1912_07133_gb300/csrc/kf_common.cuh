@@ -1,0 +1,68 @@
+// kf_common.cuh -- device-side records and helpers shared by the product
+// kernels of the shape-filter bank (Kennedy, arXiv:1912.07133).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kf {
+
+constexpr int MAXK = 8;          // largest recursive order / number of modes
+constexpr int MAXS = 16;         // scales per bank call
+constexpr int CH = 32;           // row-kernel pixels per thread (chunk)
+constexpr int LC = 64;           // column segment length (rows)
+constexpr int TW = 30;           // column-kernel tile interior width (32 with halo)
+constexpr int SCAN_LEVELS = 10;  // Kogge-Stone levels of the row scan (<= 1024 threads)
+constexpr int MAX_FIR_K = 160;   // largest colored-SG half-length
+
+enum { T_D = 0, T_E = 1, T_C = 2 };
+
+// Per-scale realisation of one designed blur.  Written by the FP64 design
+// kernel; read by the filter kernels.  All recursive realisations are sums of
+// one-sided parts (Appendix, eq A6): y = y+ + y- + b0 x, where y+ runs over
+// the input left-to-right (top-to-bottom) and y- right-to-left, both on the
+// INPUT (eq A10a-b), so the two directions are independent.
+struct Coef {
+  int type;      // T_D / T_E / T_C
+  int K;         // D: chain length = K^lpf; E: number of modes; C: FIR half-length
+  int status;    // 0 ok, else design failure code
+  int pad0;
+  float sigma2;  // sigma^2: R_L = -sigma^2 (D20 + D02)
+  float b0;      // centre coefficient of the DE
+  // Filter D: the K-fold pole p = exp(-1/sigma) realised as a delayed chain of
+  // first-order sections t_1(n) = p t_1(n-1) + x(n), t_j(n) = p t_j(n-1) +
+  // t_{j-1}(n-1); the one-sided output is sum_j w_j t_j(n-1).
+  float p;
+  float w[MAXK];
+  float hold[MAXK];              // steady state per unit constant input: 1/q^j
+  float phiL[MAXK];              // first column of Phi^LC (Toeplitz)
+  float phiS[SCAN_LEVELS][MAXK]; // first column of Phi^(CH 2^k)
+  // Filter E: complex (or real) one-pole modes t(n) = z t(n-1) + x(n);
+  // one-sided output Re(sum_i g_i t_i(n-1)).
+  float zr[MAXK], zi[MAXK];
+  float gr[MAXK], gi[MAXK];
+  float hr[MAXK], hi[MAXK];      // steady state per unit input: 1/(1-z)
+  float zLr[MAXK], zLi[MAXK];    // z^LC
+  float zSr[SCAN_LEVELS][MAXK], zSi[SCAN_LEVELS][MAXK];  // z^(CH 2^k)
+  // Filter C taps h[0..K]
+  float h[MAX_FIR_K + 1];
+  // FP64 design, copied to the host by kf_design
+  double lambda, sigma, param, db0;
+  double dbplus[MAXK + 1], daplus[MAXK + 1];
+  double dh[MAX_FIR_K + 1];
+  double dc_gain, moment2;
+};
+
+// Candidate record written by the detector kernels (matches kf_blob).
+struct Blob {
+  int32_t frame, x, y, scale, polarity;
+  float response;
+};
+
+// Bounded device-side status word shared by the kernels of one call.
+struct DevStatus {
+  unsigned long long count;  // candidates found (may exceed capacity)
+  int error;                 // first error code seen by a kernel
+  int pad;
+};
+
+}  // namespace kf

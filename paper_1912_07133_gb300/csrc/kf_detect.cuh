@@ -1,0 +1,126 @@
+// kf_detect.cuh -- scale-space extremum detector on a tile of responses held
+// in shared memory (Kennedy, arXiv:1912.07133, Sec. 5, Threshold #1).
+//
+// The tile buffer holds R for all S scales on NR rows x 32 columns; row 0 and
+// row NR-1, lane 0 and lane 31 are halo.  A candidate at (s, y, x) must beat
+// every in-frame neighbour of its 3 x 3 x (scales) neighbourhood: strictly a
+// neighbour earlier in (scale, y, x) order, non-strictly a later one, so that
+// exactly one pixel of a plateau survives.  Bright: R > T; dark (Laplacian
+// response only): R < -T, mirrored.
+#pragma once
+#include <math_constants.h>
+
+#include "kf_common.cuh"
+
+namespace kf {
+
+struct DetectArgs {
+  int S, NR;           // scales, buffer rows
+  int x0;              // frame column of lane 0
+  int r0;              // frame row of buffer row 0
+  int H, W;
+  float thr;
+  int neigh;           // 0 all scales, 1 adjacent scales
+  int dark;            // 1: also report minima (Laplacian response)
+  int frame;
+  Blob *out;
+  long cap;
+  DevStatus *status;
+  float *resp;         // optional: R planes of this frame (S x H x W)
+};
+
+static __device__ __forceinline__ void emit_blob(const DetectArgs &a, int s, int y, int x, int pol, float v) {
+  unsigned long long idx = atomicAdd(&a.status->count, 1ull);
+  if (idx < (unsigned long long)a.cap) {
+    Blob b;
+    b.frame = a.frame;
+    b.x = x;
+    b.y = y;
+    b.scale = s;
+    b.polarity = pol;
+    b.response = v;
+    a.out[idx] = b;
+  }
+}
+
+// buf: [S][NR][32] responses; red: scratch of NR*32*(2 floats + 2 bytes).
+// Must be called by all threads of the block (contains __syncthreads).
+static __device__ void detect_tile(const float *buf, float *red, const DetectArgs &a) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int NP = a.NR * 32;
+  float *mx = red, *mn = red + NP;
+  unsigned char *amx = reinterpret_cast<unsigned char *>(red + 2 * NP);
+  unsigned char *amn = amx + NP;
+  // per-pixel extremes over scales (first argmax / argmin), out-of-frame -> +-inf
+  for (int p = tid; p < NP; p += nt) {
+    const int i = p >> 5, lane = p & 31;
+    const int y = a.r0 + i, x = a.x0 + lane;
+    float vmax = -CUDART_INF_F, vmin = CUDART_INF_F;
+    int smax = a.S, smin = a.S;
+    if (y >= 0 && y < a.H && x >= 0 && x < a.W) {
+      for (int s = 0; s < a.S; ++s) {
+        const float v = buf[(s * a.NR + i) * 32 + lane];
+        if (v > vmax) vmax = v, smax = s;
+        if (v < vmin) vmin = v, smin = s;
+      }
+    }
+    mx[p] = vmax;
+    mn[p] = vmin;
+    amx[p] = (unsigned char)smax;
+    amn[p] = (unsigned char)smin;
+  }
+  __syncthreads();
+  const int NI = (a.NR - 2) * 30;  // interior pixels
+  for (int q = tid; q < NI; q += nt) {
+    const int i = 1 + q / 30, lane = 1 + q % 30;
+    const int y = a.r0 + i, x = a.x0 + lane;
+    if (y < 0 || y >= a.H || x < 0 || x >= a.W) continue;
+    const int p = i * 32 + lane;
+    if (a.resp) {
+      const long plane = (long)a.H * a.W;
+      for (int s = 0; s < a.S; ++s)
+        a.resp[s * plane + (long)y * a.W + x] = buf[(s * a.NR + i) * 32 + lane];
+    }
+    if (a.neigh == 0) {
+      // bright: the own pixel's first argmax over scales competes spatially
+      for (int pol = 1; pol >= -1; pol -= 2) {
+        if (pol == -1 && !a.dark) break;
+        const float v = (pol == 1) ? mx[p] : mn[p];
+        const int s = (pol == 1) ? amx[p] : amn[p];
+        if (!(pol * v > a.thr)) continue;
+        bool ok = true;
+        for (int di = -1; di <= 1 && ok; ++di)
+          for (int dl = -1; dl <= 1 && ok; ++dl) {
+            if (di == 0 && dl == 0) continue;
+            const int pn = p + di * 32 + dl;
+            const float vn = (pol == 1) ? mx[pn] : mn[pn];
+            const int sn = (pol == 1) ? amx[pn] : amn[pn];
+            const bool after = di > 0 || (di == 0 && dl > 0);
+            const float a1 = pol * v, b1 = pol * vn;
+            ok = (a1 > b1) || (a1 == b1 && (sn > s || (sn == s && after)));
+          }
+        if (ok) emit_blob(a, s, y, x, pol, v);
+      }
+    } else {
+      for (int s = 0; s < a.S; ++s) {
+        const float v = buf[(s * a.NR + i) * 32 + lane];
+        const int pol = (v > a.thr) ? 1 : ((a.dark && v < -a.thr) ? -1 : 0);
+        if (!pol) continue;
+        bool ok = true;
+        for (int t = max(0, s - 1); t <= min(a.S - 1, s + 1) && ok; ++t)
+          for (int di = -1; di <= 1 && ok; ++di)
+            for (int dl = -1; dl <= 1 && ok; ++dl) {
+              if (t == s && di == 0 && dl == 0) continue;
+              const int yn = y + di, xn = x + dl;
+              if (yn < 0 || yn >= a.H || xn < 0 || xn >= a.W) continue;
+              const float vn = buf[(t * a.NR + i + di) * 32 + lane + dl];
+              const bool earlier = t < s || (t == s && (di < 0 || (di == 0 && dl < 0)));
+              ok = earlier ? (pol * v > pol * vn) : (pol * v >= pol * vn);
+            }
+        if (ok) emit_blob(a, s, y, x, pol, v);
+      }
+    }
+  }
+}
+
+}  // namespace kf

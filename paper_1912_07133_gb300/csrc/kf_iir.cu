@@ -1,0 +1,495 @@
+// kf_iir.cu -- recursive (IIR) blur banks: Filter D (repeated pole, Sec. 4.3)
+// and Filter E (discrete Butterworth, Sec. 4.4) of Kennedy, arXiv:1912.07133,
+// with the derivative stage of Table I and the Sec. 5 detector.
+//
+// The derivative filters are applied first: the hpf pair [1,-2,1] along x and
+// along y (Table I, d = 2) turns the frame into the 5-point Laplacian L = U + V
+// (U = d2/dx2, V = d2/dy2, edge-held frame); the blur commutes with them, so
+// D20 + D02 = blur_y(blur_x(L)).  Because the frame is held outside its
+// edges, U vanishes beyond the left/right edges and V beyond the top/bottom
+// ones: the x-recursion starts from the steady state of V at the row ends and
+// the y-recursion from the steady state of blur_x(U) at the first/last row.
+//
+// Each one-sided recursion (eq A10a-b) runs on the input in FP32 as a chain of
+// first-order sections (Filter D) or complex one-pole modes (Filter E) whose
+// states keep unit-dc-gain accuracy; the three-term sum (eq A6) adds them.
+//
+// Passes per frame:
+//   k_row      one CTA per row: chunk of CH pixels per thread, zero-state end
+//              states, Kogge-Stone scan of the carries across the CTA, then
+//              both directions with exact starting states; all scales.
+//   k_row<EDGE> the same on U alone for rows 0 and H-1 (column boundary).
+//   k_colseg   zero-state end states of every LC-row column segment.
+//   k_colfold  carries: sequential fold of the segment states per column.
+//   k_coldet   LC+2 rows x 32 columns x all scales per CTA: both column
+//              directions from the carries, response, extremum detector.
+#include "kf_common.cuh"
+#include "kf_detect.cuh"
+#include "kf_internal.h"
+
+namespace kf {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// one-sided recursions
+// ---------------------------------------------------------------------------
+template <int KK>
+struct Chain {
+  static constexpr int NF = KK;
+  struct View {
+    float p, b0, w[KK];
+    __device__ void load(const Coef &c) {
+      p = c.p;
+      b0 = c.b0;
+#pragma unroll
+      for (int j = 0; j < KK; ++j) w[j] = c.w[j];
+    }
+  };
+  float t[KK];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int j = 0; j < KK; ++j) t[j] = 0.f;
+  }
+  __device__ __forceinline__ void hold(const Coef &c, float x) {
+#pragma unroll
+    for (int j = 0; j < KK; ++j) t[j] = c.hold[j] * x;
+  }
+  __device__ __forceinline__ float out(const View &v) const {
+    float y = 0.f;
+#pragma unroll
+    for (int j = 0; j < KK; ++j) y = fmaf(v.w[j], t[j], y);
+    return y;
+  }
+  __device__ __forceinline__ void push(const View &v, float x) {
+#pragma unroll
+    for (int j = KK - 1; j > 0; --j) t[j] = fmaf(v.p, t[j], t[j - 1]);
+    t[0] = fmaf(v.p, t[0], x);
+  }
+  // this <- Phi^n prev + this, Phi^n lower-triangular Toeplitz, first column phi
+  __device__ __forceinline__ void combine(const float *phi, const Chain &prev) {
+#pragma unroll
+    for (int j = 0; j < KK; ++j) {
+      float acc = t[j];
+#pragma unroll
+      for (int i = 0; i <= j; ++i) acc = fmaf(phi[i], prev.t[j - i], acc);
+      t[j] = acc;
+    }
+  }
+  __device__ __forceinline__ void combine_level(const Coef &c, int lv, const Chain &prev) {
+    float phi[KK];
+#pragma unroll
+    for (int i = 0; i < KK; ++i) phi[i] = c.phiS[lv][i];
+    combine(phi, prev);
+  }
+  __device__ __forceinline__ void combine_L(const Coef &c, const Chain &prev) {
+    float phi[KK];
+#pragma unroll
+    for (int i = 0; i < KK; ++i) phi[i] = c.phiL[i];
+    combine(phi, prev);
+  }
+  __device__ __forceinline__ void store(float *dst, long stride) const {
+#pragma unroll
+    for (int j = 0; j < KK; ++j) dst[j * stride] = t[j];
+  }
+  __device__ __forceinline__ void load(const float *src, long stride) {
+#pragma unroll
+    for (int j = 0; j < KK; ++j) t[j] = src[j * stride];
+  }
+  __device__ __forceinline__ Chain shfl_up(int d) const {
+    Chain r;
+#pragma unroll
+    for (int j = 0; j < KK; ++j) r.t[j] = __shfl_up_sync(0xffffffffu, t[j], d);
+    return r;
+  }
+  __device__ __forceinline__ Chain shfl_down(int d) const {
+    Chain r;
+#pragma unroll
+    for (int j = 0; j < KK; ++j) r.t[j] = __shfl_down_sync(0xffffffffu, t[j], d);
+    return r;
+  }
+};
+
+template <int NM>
+struct Modes {
+  static constexpr int NF = 2 * NM;
+  struct View {
+    float zr[NM], zi[NM], gr[NM], gi[NM], b0;
+    __device__ void load(const Coef &c) {
+      b0 = c.b0;
+#pragma unroll
+      for (int i = 0; i < NM; ++i) zr[i] = c.zr[i], zi[i] = c.zi[i], gr[i] = c.gr[i], gi[i] = c.gi[i];
+    }
+  };
+  float tr[NM], ti[NM];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) tr[i] = ti[i] = 0.f;
+  }
+  __device__ __forceinline__ void hold(const Coef &c, float x) {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) tr[i] = c.hr[i] * x, ti[i] = c.hi[i] * x;
+  }
+  __device__ __forceinline__ float out(const View &v) const {
+    float y = 0.f;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) y = fmaf(v.gr[i], tr[i], fmaf(-v.gi[i], ti[i], y));
+    return y;
+  }
+  __device__ __forceinline__ void push(const View &v, float x) {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+      const float nr = fmaf(v.zr[i], tr[i], fmaf(-v.zi[i], ti[i], x));
+      const float ni = fmaf(v.zr[i], ti[i], v.zi[i] * tr[i]);
+      tr[i] = nr;
+      ti[i] = ni;
+    }
+  }
+  __device__ __forceinline__ void combine_z(const float *zr, const float *zi, const Modes &prev) {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+      tr[i] = fmaf(zr[i], prev.tr[i], fmaf(-zi[i], prev.ti[i], tr[i]));
+      ti[i] = fmaf(zr[i], prev.ti[i], fmaf(zi[i], prev.tr[i], ti[i]));
+    }
+  }
+  __device__ __forceinline__ void combine_level(const Coef &c, int lv, const Modes &prev) {
+    float zr[NM], zi[NM];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) zr[i] = c.zSr[lv][i], zi[i] = c.zSi[lv][i];
+    combine_z(zr, zi, prev);
+  }
+  __device__ __forceinline__ void combine_L(const Coef &c, const Modes &prev) {
+    float zr[NM], zi[NM];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) zr[i] = c.zLr[i], zi[i] = c.zLi[i];
+    combine_z(zr, zi, prev);
+  }
+  __device__ __forceinline__ void store(float *dst, long stride) const {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) dst[(2 * i) * stride] = tr[i], dst[(2 * i + 1) * stride] = ti[i];
+  }
+  __device__ __forceinline__ void load(const float *src, long stride) {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) tr[i] = src[(2 * i) * stride], ti[i] = src[(2 * i + 1) * stride];
+  }
+  __device__ __forceinline__ Modes shfl_up(int d) const {
+    Modes r;
+#pragma unroll
+    for (int i = 0; i < NM; ++i)
+      r.tr[i] = __shfl_up_sync(0xffffffffu, tr[i], d), r.ti[i] = __shfl_up_sync(0xffffffffu, ti[i], d);
+    return r;
+  }
+  __device__ __forceinline__ Modes shfl_down(int d) const {
+    Modes r;
+#pragma unroll
+    for (int i = 0; i < NM; ++i)
+      r.tr[i] = __shfl_down_sync(0xffffffffu, tr[i], d), r.ti[i] = __shfl_down_sync(0xffffffffu, ti[i], d);
+    return r;
+  }
+};
+
+// Block-wide carry scan of a chain of chunks of CH samples.  `u` is this
+// thread's zero-state end state; `k` its position in scan order (0 = first
+// chunk of the direction); `init` the state before chunk 0.  Returns the state
+// before this thread's chunk.  REV: scan order is the reverse thread order.
+template <class Rec, bool REV>
+__device__ Rec carry_scan(Rec u, const Coef &c, int k, int NT, float *sm, const Rec &init) {
+  if (k == 0) {
+    Rec t = u;
+    t.combine_level(c, 0, init);  // Phi^CH init + u
+    u = t;
+  }
+  const int lane = k & 31;
+  int lv = 0;
+  for (int d = 1; d < 32 && d < NT; d <<= 1, ++lv) {
+    Rec o = REV ? u.shfl_down(d) : u.shfl_up(d);
+    if (lane >= d) u.combine_level(c, lv, o);
+  }
+  const int tid = threadIdx.x;
+  for (int d = 32; d < NT; d <<= 1, ++lv) {
+    u.store(sm + tid, NT);
+    __syncthreads();
+    Rec o;
+    o.zero();
+    if (k >= d) o.load(sm + (REV ? tid + d : tid - d), NT);
+    __syncthreads();
+    if (k >= d) u.combine_level(c, lv, o);
+  }
+  u.store(sm + tid, NT);
+  __syncthreads();
+  Rec r = init;
+  if (k > 0) r.load(sm + (REV ? tid + 1 : tid - 1), NT);
+  __syncthreads();
+  return r;
+}
+
+__host__ __device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
+
+// ---------------------------------------------------------------------------
+// row pass
+// ---------------------------------------------------------------------------
+template <class Rec, bool EDGE>
+__global__ void __launch_bounds__(256) k_row(const float *__restrict__ X, long xpitch, int H, int W,
+                                             const Coef *__restrict__ coef, int S,
+                                             float *__restrict__ P, long PW, float *__restrict__ edge) {
+  extern __shared__ float sm[];
+  const int NT = blockDim.x, tid = threadIdx.x;
+  const int RP = pad32(NT * CH) + 1;
+  float *s_m = sm, *s_0 = sm + RP, *s_p = sm + 2 * RP, *s_scan = sm + 3 * RP;
+  const int y = EDGE ? (blockIdx.x == 0 ? 0 : H - 1) : blockIdx.x;
+  const float *rm = X + (long)max(y - 1, 0) * xpitch;
+  const float *r0 = X + (long)y * xpitch;
+  const float *rp = X + (long)min(y + 1, H - 1) * xpitch;
+  for (int e = tid; e < W; e += NT) {
+    const int a = pad32(e);
+    s_m[a] = __ldg(rm + e);
+    s_0[a] = __ldg(r0 + e);
+    s_p[a] = __ldg(rp + e);
+  }
+  __syncthreads();
+  const float v_lo = s_p[0] - 2.f * s_0[0] + s_m[0];
+  const int eW = pad32(W - 1);
+  const float v_hi = s_p[eW] - 2.f * s_0[eW] + s_m[eW];
+  float L[CH];
+  const int x0 = tid * CH;
+#pragma unroll
+  for (int i = 0; i < CH; ++i) {
+    const int e = x0 + i;
+    if (e < W) {
+      const float c0 = s_0[pad32(e)];
+      const float u = s_0[pad32(min(e + 1, W - 1))] - 2.f * c0 + s_0[pad32(max(e - 1, 0))];
+      const float v = s_p[pad32(e)] - 2.f * c0 + s_m[pad32(e)];
+      L[i] = EDGE ? u : u + v;
+    } else {
+      L[i] = EDGE ? 0.f : v_hi;  // beyond the right edge only the held V part
+    }
+  }
+  const float in_lo = EDGE ? 0.f : v_lo, in_hi = EDGE ? 0.f : v_hi;
+  __syncthreads();
+  float *s_out = sm;
+  for (int s = 0; s < S; ++s) {
+    const Coef &c = coef[s];
+    typename Rec::View v;
+    v.load(c);
+    Rec ef, eb;
+    ef.zero();
+    eb.zero();
+#pragma unroll
+    for (int i = 0; i < CH; ++i) ef.push(v, L[i]);
+#pragma unroll
+    for (int i = CH - 1; i >= 0; --i) eb.push(v, L[i]);
+    Rec hlo, hhi;
+    hlo.hold(c, in_lo);
+    hhi.hold(c, in_hi);
+    const Rec cf = carry_scan<Rec, false>(ef, c, tid, NT, s_scan, hlo);
+    const Rec cb = carry_scan<Rec, true>(eb, c, NT - 1 - tid, NT, s_scan, hhi);
+    float yv[CH];
+    Rec r = cf;
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      yv[i] = r.out(v);
+      r.push(v, L[i]);
+    }
+    r = cb;
+#pragma unroll
+    for (int i = CH - 1; i >= 0; --i) {
+      yv[i] += fmaf(v.b0, L[i], r.out(v));
+      r.push(v, L[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < CH; ++i) s_out[pad32(x0 + i)] = yv[i];
+    __syncthreads();
+    float *dst = EDGE ? edge + ((long)s * 2 + blockIdx.x) * PW : P + (long)s * H * PW + (long)y * PW;
+    for (int e = tid; e < W; e += NT) dst[e] = s_out[pad32(e)];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// column passes
+// ---------------------------------------------------------------------------
+// input of the column recursion at row r (phantom rows use the held one-sided
+// rows of U at the frame's first/last row)
+__device__ __forceinline__ float col_in(const float *Pc, long PW, int r, int H, float top, float bot) {
+  return r < 0 ? top : (r >= H ? bot : __ldg(Pc + (long)r * PW));
+}
+
+template <class Rec>
+__global__ void __launch_bounds__(128) k_colseg(const float *__restrict__ P, long PW, int H, int W,
+                                                const float *__restrict__ edge,
+                                                const Coef *__restrict__ coef, float *__restrict__ E,
+                                                int nseg) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= W) return;
+  const int c = blockIdx.y, s = blockIdx.z;
+  typename Rec::View v;
+  v.load(coef[s]);
+  const float *Pc = P + (long)s * H * PW + x;
+  const float top = edge[((long)s * 2 + 0) * PW + x], bot = edge[((long)s * 2 + 1) * PW + x];
+  Rec r;
+  r.zero();
+  // causal segment: rows [c LC - 1, (c+1) LC - 1)
+  const int rf = c * LC - 1;
+#pragma unroll 8
+  for (int i = 0; i < LC; ++i) r.push(v, col_in(Pc, PW, rf + i, H, top, bot));
+  const long fs = (long)Rec::NF * PW;
+  float *Ef = E + (((long)s * nseg + c) * 2 + 0) * fs + x;
+  r.store(Ef, PW);
+  // anticausal segment: rows (c+1) LC down to c LC + 1
+  r.zero();
+  const int rb = (c + 1) * LC;
+#pragma unroll 8
+  for (int i = 0; i < LC; ++i) r.push(v, col_in(Pc, PW, rb - i, H, top, bot));
+  r.store(Ef + fs, PW);
+}
+
+template <class Rec>
+__global__ void __launch_bounds__(128) k_colfold(int W, long PW, const float *__restrict__ edge,
+                                                 const Coef *__restrict__ coef, float *__restrict__ E,
+                                                 int nseg) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= W) return;
+  const int s = blockIdx.y;
+  const Coef &c = coef[s];
+  const long fs = (long)Rec::NF * PW;
+  Rec st, e;
+  st.hold(c, edge[((long)s * 2 + 0) * PW + x]);
+  for (int k = 0; k < nseg; ++k) {
+    float *slot = E + (((long)s * nseg + k) * 2 + 0) * fs + x;
+    e.load(slot, PW);
+    st.store(slot, PW);
+    Rec n = e;
+    n.combine_L(c, st);  // Phi^LC st + e
+    st = n;
+  }
+  st.hold(c, edge[((long)s * 2 + 1) * PW + x]);
+  for (int k = nseg - 1; k >= 0; --k) {
+    float *slot = E + (((long)s * nseg + k) * 2 + 1) * fs + x;
+    e.load(slot, PW);
+    st.store(slot, PW);
+    Rec n = e;
+    n.combine_L(c, st);
+    st = n;
+  }
+}
+
+template <class Rec>
+__global__ void __launch_bounds__(512) k_coldet(const float *__restrict__ P, long PW, int H, int W,
+                                                const float *__restrict__ edge,
+                                                const Coef *__restrict__ coef, int S,
+                                                const float *__restrict__ E, int nseg,
+                                                DetectArgs da) {
+  extern __shared__ float sm[];
+  constexpr int NR = LC + 2;
+  float *buf = sm;                       // [S][NR][32]
+  float *red = sm + (long)S * NR * 32;   // detector scratch
+  const int lane = threadIdx.x & 31, s = threadIdx.x >> 5;
+  const int c = blockIdx.y;
+  const int x = blockIdx.x * TW - 1 + lane;
+  const int xv = min(max(x, 0), W - 1);
+  const int r0 = c * LC - 1;
+  {
+    const Coef &cf = coef[s];
+    typename Rec::View v;
+    v.load(cf);
+    const float *Pc = P + (long)s * H * PW + xv;
+    const float top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
+    const long fs = (long)Rec::NF * PW;
+    const float *Ef = E + (((long)s * nseg + c) * 2) * fs + xv;
+    float *b = buf + (long)s * NR * 32 + lane;
+    Rec r;
+    r.load(Ef, PW);
+#pragma unroll 2
+    for (int i = 0; i < NR; ++i) {
+      const float in = col_in(Pc, PW, r0 + i, H, top, bot);
+      b[i * 32] = r.out(v);
+      r.push(v, in);
+    }
+    r.load(Ef + fs, PW);
+    const float ms2 = -cf.sigma2;
+#pragma unroll 2
+    for (int i = NR - 1; i >= 0; --i) {
+      const float in = col_in(Pc, PW, r0 + i, H, top, bot);
+      const float q = b[i * 32] + fmaf(v.b0, in, r.out(v));
+      b[i * 32] = ms2 * q;  // R_L = -sigma^2 (D20 + D02)
+      r.push(v, in);
+    }
+  }
+  __syncthreads();
+  DetectArgs a = da;
+  a.S = S;
+  a.NR = NR;
+  a.x0 = blockIdx.x * TW - 1;
+  a.r0 = r0;
+  detect_tile(buf, red, a);
+}
+
+template <class Rec>
+int run_iir(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
+  const int NT = ((g.W + CH - 1) / CH + 31) / 32 * 32;
+  if (NT > 1024) return -1;
+  const size_t row_smem = (size_t)(3 * (pad32(NT * CH) + 1) + NT * Rec::NF) * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_row<Rec, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_row<Rec, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_coldet<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr = true;
+  }
+  if (row_smem > 200 * 1024) return -1;
+  k_row<Rec, false><<<g.H, NT, row_smem, st>>>(g.X, g.xpitch, g.H, g.W, a.coef, a.S, a.P, g.PW, a.edge);
+  k_row<Rec, true><<<2, NT, row_smem, st>>>(g.X, g.xpitch, g.H, g.W, a.coef, a.S, a.P, g.PW, a.edge);
+  const int nseg = (g.H + LC - 1) / LC;
+  dim3 gs((g.W + 127) / 128, nseg, a.S);
+  k_colseg<Rec><<<gs, 128, 0, st>>>(a.P, g.PW, g.H, g.W, a.edge, a.coef, a.carry, nseg);
+  dim3 gf((g.W + 127) / 128, a.S);
+  k_colfold<Rec><<<gf, 128, 0, st>>>(g.W, g.PW, a.edge, a.coef, a.carry, nseg);
+  DetectArgs da;
+  da.H = g.H;
+  da.W = g.W;
+  da.thr = a.threshold;
+  da.neigh = a.neigh;
+  da.dark = 1;
+  da.frame = g.frame;
+  da.out = a.blobs;
+  da.cap = a.cap;
+  da.status = a.status;
+  da.resp = a.responses ? a.responses + g.resp_off : nullptr;
+  constexpr int NR = LC + 2;
+  const size_t det_smem = ((size_t)a.S * NR * 32 + (size_t)NR * 32 * 2) * sizeof(float) + (size_t)NR * 32 * 2;
+  dim3 gd((g.W + TW - 1) / TW, nseg);
+  k_coldet<Rec><<<gd, 32 * a.S, det_smem, st>>>(a.P, g.PW, g.H, g.W, a.edge, a.coef, a.S, a.carry,
+                                                 nseg, da);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+size_t iir_carry_floats(int H, long PW, int S, int nf) {
+  const int nseg = (H + LC - 1) / LC;
+  return (size_t)S * nseg * 2 * nf * PW;
+}
+
+int launch_iir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
+  if (a.type == T_D) {
+    switch (a.nstate) {
+      case 2: return run_iir<Chain<2>>(g, a, st);
+      case 3: return run_iir<Chain<3>>(g, a, st);
+      case 4: return run_iir<Chain<4>>(g, a, st);
+      case 5: return run_iir<Chain<5>>(g, a, st);
+      case 6: return run_iir<Chain<6>>(g, a, st);
+      default: return -2;
+    }
+  }
+  if (a.type == T_E) {
+    switch (a.nstate) {
+      case 1: return run_iir<Modes<1>>(g, a, st);
+      case 2: return run_iir<Modes<2>>(g, a, st);
+      case 3: return run_iir<Modes<3>>(g, a, st);
+      default: return -2;
+    }
+  }
+  return -2;
+}
+
+}  // namespace kf

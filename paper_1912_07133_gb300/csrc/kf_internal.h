@@ -1,0 +1,47 @@
+// kf_internal.h -- host-side declarations shared by the library's translation
+// units (launchers of the CUDA kernels).  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kf_common.cuh"
+
+namespace kf {
+
+// FP64 design of S scales into d_out (device array of S Coef).  d_work holds
+// S * (Nmax^2 + 2 Nmax) doubles for the colored-SG KKT solve.
+int launch_design(int type, int order, const double *d_lambdas, int S, int fir_kmax, Coef *d_out,
+                  double *d_work, int Nmax, cudaStream_t st);
+
+// Geometry of one frame in the bank.
+struct FrameGeom {
+  const float *X;   // input frame (f32)
+  long xpitch;      // elements between input rows
+  int H, W;
+  long PW;          // pitch of the intermediate planes (elements)
+  int frame;        // frame index (for blob records)
+  long resp_off;    // offset of this frame in the responses output
+};
+
+struct BankArgs {
+  const Coef *coef;      // device, S entries
+  int S;
+  int type, nstate;      // filter type; D: chain length, E: number of modes
+  int kmax;              // FIR: largest half-length over the scales
+  float threshold;
+  int neigh;
+  float *P;              // S planes of H x PW (f32)
+  float *edge;           // S x 2 x PW: one-sided rows for the column boundary
+  float *carry;          // S x nseg x 2 x NF x PW (IIR column carries)
+  Blob *blobs;
+  long cap;
+  DevStatus *status;
+  float *responses;      // optional
+};
+
+int launch_iir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st);
+int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st);
+
+// workspace needs (bytes) of one frame
+size_t iir_carry_floats(int H, long PW, int S, int nf);
+
+}  // namespace kf

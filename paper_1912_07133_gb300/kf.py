@@ -1,0 +1,237 @@
+"""Thin Python binding of the C ABI in ``include/kf.h`` (ctypes).
+
+Argument marshalling only: every step of the filter bank runs in the CUDA
+kernels of ``_lib/libkf.so``.  Device buffers come from PyTorch tensors
+(``data_ptr``) and work is issued on PyTorch's current CUDA stream.  Loading
+fails loudly if the library is missing (build it with
+``python -c "import __graft_entry__ as g; g.build()"``) or no GPU is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libkf.so")
+
+KF_OK = 0
+KF_EINVAL = -1
+KF_ECOND = -2
+KF_ENOMEM = -3
+KF_ECUDA = -4
+KF_ETIMEOUT = -5
+KF_EOVERFLOW = -6
+KF_ENODEV = -7
+
+KF_IIR_REPEATED_POLE = 0
+KF_IIR_BUTTERWORTH = 1
+KF_FIR_COLORED_SG = 2
+
+KF_DTYPE_F32 = 0
+KF_DTYPE_F16 = 1
+KF_DTYPE_BF16 = 2
+KF_DTYPE_U16 = 3
+
+KF_RESP_LAPLACIAN = 0
+KF_RESP_HESSIAN = 1
+KF_BOUNDARY_HOLD = 0
+KF_NEIGH_ALL_SCALES = 0
+KF_NEIGH_ADJACENT = 1
+KF_MAX_SCALES = 16
+KF_MAX_ORDER = 8
+KF_MAX_FIR_K = 160
+
+ENTRY_POINTS = ("kf_bank_opts_default", "kf_create", "kf_destroy", "kf_last_error", "kf_design",
+                "kf_filter_bank", "kf_detect_blobs")
+
+
+class kf_coeffs(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("order", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("scale", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("param", ctypes.c_double), ("b0", ctypes.c_double),
+                ("bplus", ctypes.c_double * (KF_MAX_ORDER + 1)),
+                ("aplus", ctypes.c_double * (KF_MAX_ORDER + 1)),
+                ("h", ctypes.c_double * (KF_MAX_FIR_K + 1)),
+                ("dc_gain", ctypes.c_double), ("moment2", ctypes.c_double)]
+
+
+class kf_frame(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("pitch", ctypes.c_int64), ("dtype", ctypes.c_int32), ("value_scale", ctypes.c_float)]
+
+
+class kf_bank_opts(ctypes.Structure):
+    _fields_ = [("response", ctypes.c_int32), ("boundary", ctypes.c_int32),
+                ("neighbourhood", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("threshold", ctypes.c_double), ("fir_kmax", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("responses", ctypes.c_void_p),
+                ("reserved", ctypes.c_int64 * 4)]
+
+
+class kf_blob(ctypes.Structure):
+    _fields_ = [("frame", ctypes.c_int32), ("x", ctypes.c_int32), ("y", ctypes.c_int32),
+                ("scale", ctypes.c_int32), ("polarity", ctypes.c_int32), ("response", ctypes.c_float)]
+
+
+BLOB_DTYPE = np.dtype([("frame", "<i4"), ("x", "<i4"), ("y", "<i4"), ("scale", "<i4"),
+                       ("polarity", "<i4"), ("response", "<f4")])
+
+_lib = None
+
+
+class KfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"kf error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Load the library and declare its signatures (no GPU needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    L.kf_bank_opts_default.restype = i32
+    L.kf_bank_opts_default.argtypes = [ctypes.POINTER(kf_bank_opts)]
+    L.kf_create.restype = i32
+    L.kf_create.argtypes = [ctypes.POINTER(vp), i32, vp]
+    L.kf_destroy.restype = None
+    L.kf_destroy.argtypes = [vp]
+    L.kf_last_error.restype = ctypes.c_char_p
+    L.kf_last_error.argtypes = [vp]
+    L.kf_design.restype = i32
+    L.kf_design.argtypes = [i32, i32, dbl, ctypes.POINTER(kf_coeffs)]
+    L.kf_filter_bank.restype = i32
+    L.kf_filter_bank.argtypes = [vp, ctypes.POINTER(kf_frame), i32, ctypes.POINTER(dbl), i32, i32, i32,
+                                 ctypes.POINTER(kf_bank_opts)]
+    L.kf_detect_blobs.restype = i32
+    L.kf_detect_blobs.argtypes = [vp, dbl, ctypes.POINTER(kf_blob), i64, ctypes.POINTER(i64)]
+    _lib = L
+    return L
+
+
+def _check(rc: int, ctx=None):
+    if rc != KF_OK:
+        raise KfError(rc, load().kf_last_error(ctx).decode())
+
+
+# ---- entry points under their C names ---------------------------------------
+def kf_bank_opts_default() -> kf_bank_opts:
+    o = kf_bank_opts()
+    _check(load().kf_bank_opts_default(ctypes.byref(o)))
+    return o
+
+
+def kf_create(device: int = 0, stream=None) -> int:
+    """Context on `device` using `stream` (default: torch's current stream)."""
+    import torch
+
+    if not torch.cuda.is_available():
+        raise KfError(KF_ENODEV, "no CUDA device (the filter bank has no CPU path)")
+    if stream is None:
+        stream = torch.cuda.current_stream(device).cuda_stream
+    ctx = ctypes.c_void_p()
+    _check(load().kf_create(ctypes.byref(ctx), device, ctypes.c_void_p(stream)))
+    return ctx.value
+
+
+def kf_destroy(ctx: int) -> None:
+    load().kf_destroy(ctx)
+
+
+def kf_last_error(ctx=None) -> str:
+    return load().kf_last_error(ctx).decode()
+
+
+def kf_design(ftype: int, order: int, scale: float) -> dict:
+    c = kf_coeffs()
+    _check(load().kf_design(ftype, order, float(scale), ctypes.byref(c)))
+    K = c.K
+    d = dict(type=c.type, order=c.order, K=K, scale=c.scale, sigma=c.sigma, param=c.param, b0=c.b0,
+             dc_gain=c.dc_gain, moment2=c.moment2)
+    if ftype == KF_FIR_COLORED_SG:
+        d["h"] = np.array(c.h[: K + 1])
+    else:
+        d["bplus"] = np.array(c.bplus[: K + 1])
+        d["aplus"] = np.array(c.aplus[: K + 1])
+    return d
+
+
+def _frame_desc(t) -> kf_frame:
+    import torch
+
+    if not t.is_cuda or t.dim() != 2:
+        raise ValueError("frames must be 2-D CUDA tensors")
+    if t.stride(1) != 1:
+        raise ValueError("frames must have unit column stride")
+    dt = {torch.float32: KF_DTYPE_F32, torch.float16: KF_DTYPE_F16, torch.bfloat16: KF_DTYPE_BF16,
+          torch.uint16: KF_DTYPE_U16}.get(t.dtype)
+    if dt is None:
+        raise ValueError(f"unsupported frame dtype {t.dtype}")
+    return kf_frame(t.data_ptr(), t.shape[1], t.shape[0], t.stride(0), dt, 0.0)
+
+
+def kf_filter_bank(ctx: int, frames, scales, ftype: int, order: int, opts: kf_bank_opts = None) -> None:
+    """Enqueue the bank on the context stream; `frames` are CUDA tensors."""
+    descs = (kf_frame * len(frames))(*[_frame_desc(f) for f in frames])
+    sc = (ctypes.c_double * len(scales))(*[float(s) for s in scales])
+    if opts is None:
+        opts = kf_bank_opts_default()
+    _check(load().kf_filter_bank(ctx, descs, len(frames), sc, len(scales), ftype, order,
+                                 ctypes.byref(opts)), ctx)
+
+
+def kf_detect_blobs(ctx: int, threshold: float, capacity: int = 1 << 20) -> np.ndarray:
+    """Blob list of the last bank call, sorted by (frame, scale, y, x)."""
+    out = np.zeros(capacity, dtype=BLOB_DTYPE)
+    n = ctypes.c_int64(0)
+    rc = load().kf_detect_blobs(ctx, float(threshold),
+                                out.ctypes.data_as(ctypes.POINTER(kf_blob)), capacity, ctypes.byref(n))
+    if rc == KF_EOVERFLOW and n.value > capacity:
+        return kf_detect_blobs(ctx, threshold, int(n.value))
+    _check(rc, ctx)
+    return out[: n.value].copy()
+
+
+class Bank:
+    """Convenience wrapper: one context, repeated bank calls."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.ctx = kf_create(device, stream)
+
+    def run(self, frames, scales, ftype=KF_IIR_REPEATED_POLE, order=4, threshold=0.05,
+            neighbourhood=KF_NEIGH_ALL_SCALES, responses=None, fir_kmax=96):
+        o = kf_bank_opts_default()
+        o.threshold = float(threshold)
+        o.neighbourhood = neighbourhood
+        o.fir_kmax = fir_kmax
+        if responses is not None:
+            import torch
+
+            if not responses.is_cuda or responses.dtype != torch.float32 or not responses.is_contiguous():
+                raise ValueError("responses must be a contiguous float32 CUDA tensor")
+            need = sum(len(scales) * f.shape[0] * f.shape[1] for f in frames)
+            if responses.numel() < need:
+                raise ValueError(f"responses needs {need} elements")
+            o.responses = responses.data_ptr()
+        self.threshold = float(threshold)
+        kf_filter_bank(self.ctx, frames, scales, ftype, order, o)
+
+    def blobs(self, threshold=None, capacity=1 << 20) -> np.ndarray:
+        return kf_detect_blobs(self.ctx, self.threshold if threshold is None else threshold, capacity)
+
+    def close(self):
+        if self.ctx:
+            kf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,69 @@
+"""The C-ABI library loads on the CPU and exports every entry point that
+include/kf.h declares; the Python binding carries the same names.  No compute
+call is made (no GPU here)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "kf.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kf_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1912_07133_gb300 import build as B
+    B.build()
+    from paper_1912_07133_gb300 import kf
+    return kf.load()
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("kf_create", "kf_destroy", "kf_last_error", "kf_design", "kf_filter_bank",
+                 "kf_detect_blobs", "kf_bank_opts_default"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    from paper_1912_07133_gb300 import build as B
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (kf_\w+)", out))
+    assert set(declared_symbols()) <= exported
+
+
+def test_binding_names_match_header():
+    from paper_1912_07133_gb300 import kf
+    assert sorted(kf.ENTRY_POINTS) == declared_symbols()
+    for name in kf.ENTRY_POINTS:
+        assert callable(getattr(kf, name))
+
+
+def test_struct_layouts_match_header(lib):
+    """ctypes mirrors of the ABI structs have the C sizes (no GPU needed)."""
+    import ctypes
+    from paper_1912_07133_gb300 import kf
+    assert ctypes.sizeof(kf.kf_frame) == 32
+    assert ctypes.sizeof(kf.kf_blob) == 24
+    assert ctypes.sizeof(kf.kf_bank_opts) == 4 * 4 + 8 + 8 + 8 + 32
+    o = kf.kf_bank_opts_default()
+    assert o.threshold == 0.05 and o.fir_kmax == 96 and o.storage == kf.KF_DTYPE_F32
+
+
+def test_no_device_is_a_loud_error(lib):
+    """Without a GPU the binding refuses instead of computing anything."""
+    import torch
+    from paper_1912_07133_gb300 import kf
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(kf.KfError):
+        kf.kf_create(0)
