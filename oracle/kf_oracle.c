@@ -538,9 +538,15 @@ typedef struct {
 } design_t;
 
 static int make_design(int type, int order, double sigma, int fir_kmax,
-                       design_t *d) {
+                       const double *taps, int tapK, design_t *d) {
   d->type = type;
   d->h = NULL;
+  if (type == KO_FIR_COLORED_SG && taps) { /* taps designed by the caller */
+    d->K = tapK;
+    d->h = malloc(sizeof(double) * (tapK + 1));
+    memcpy(d->h, taps, sizeof(double) * (tapK + 1));
+    return 0;
+  }
   if (type == KO_IIR_REPEATED_POLE) {
     /* order = K^lpf = L_D + Lpi with L_D = 1 (D = 3) */
     d->K = ko_design_repeated_pole(1, order - 1, sigma, &d->b0, d->bplus,
@@ -567,7 +573,8 @@ static void filt1d(const design_t *d, const double *x, long n, long sx,
 
 int ko_bank(const double *img, int H, int W, int nscales, const double *lambdas,
             int type, int order, int resp, int boundary, int fir_kmax,
-            double *R, double *D) {
+            const double *taps, const int *tapK, int tap_stride, double *R,
+            double *D) {
   const long Hp = H + 2, Wp = W + 2;
   /* frame extended by one pixel on each side by the boundary rule */
   double *P = malloc(sizeof(double) * Hp * Wp);
@@ -586,7 +593,11 @@ int ko_bank(const double *img, int H, int W, int nscales, const double *lambdas,
   for (int s = 0; s < nscales && !status; ++s) {
     double sigma = lambdas[s] / 2.0; /* lambda = 2 sigma (Sec. 5) */
     design_t d;
-    if (make_design(type, order, sigma, fir_kmax, &d)) { status = -1; break; }
+    if (make_design(type, order, sigma, fir_kmax,
+                    taps ? taps + (long)s * tap_stride : NULL, taps ? tapK[s] : 0, &d)) {
+      status = -1;
+      break;
+    }
     /* rows (x) then columns (y) */
 #pragma omp parallel for schedule(static)
     for (long y = 0; y < Hp; ++y) filt1d(&d, P + y * Wp, Wp, 1, T + y * Wp, 1, boundary);

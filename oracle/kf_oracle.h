@@ -108,10 +108,13 @@ void ko_fir1d(const double *x, long n, long sx, double *y, long sy, int K,
  * Table I / Sec. 5, response.  R receives nscales*H*W values.  If D is not
  * NULL it receives 5*nscales*H*W values, ordered (scale, which, y, x) with
  * which = D10, D01, D20, D02, D11.  fir_kmax caps the colored-SG length.
- * Returns 0, or -1 if a design fails. */
+ * For the colored SG, taps (nscales rows of tap_stride doubles, h[0..tapK[s]])
+ * may be given by the caller (the high-precision design of oracle.py);
+ * NULL designs them here in FP64.  Returns 0, or -1 if a design fails. */
 int ko_bank(const double *img, int H, int W, int nscales, const double *lambdas,
             int type, int order, int resp, int boundary, int fir_kmax,
-            double *R, double *D);
+            const double *taps, const int *tapK, int tap_stride, double *R,
+            double *D);
 
 /* Offsets of eq (27) and |H| of eq (26) from the five derivatives. */
 void ko_eq27(double d10, double d01, double d20, double d02, double d11,

@@ -96,7 +96,8 @@ def lib():
             L.ko_fir1d.restype = None
             L.ko_fir1d.argtypes = [P, l, l, P, l, i, P, i]
             L.ko_bank.restype = i
-            L.ko_bank.argtypes = [P, i, i, i, P, i, i, i, i, i, P, P]
+            L.ko_bank.argtypes = [P, i, i, i, P, i, i, i, i, i, P,
+                                  ctypes.POINTER(ctypes.c_int), i, P, P]
             L.ko_eq27.restype = None
             L.ko_eq27.argtypes = [d, d, d, d, d, P, P, P]
             L.ko_detect.restype = l
@@ -189,6 +190,61 @@ def design_colored_sg(L_D: int, sigma: float, kmax: int = 0) -> np.ndarray:
     return h[: K + 1].copy()
 
 
+_MP_CACHE = {}
+
+
+def design_colored_sg_mp(L_D: int, K: int, omega_c: float, dps: int = 40) -> np.ndarray:
+    """Filter C (Sec. 4.2, eqs 16, 20-22) solved in `dps`-digit arithmetic.
+
+    The KKT matrix of eq (20) is nearly singular when omega_c = 3/sigma
+    approaches pi (condition number ~1e17 at sigma = 1), where an FP64 solve
+    is not reproducible; 40 digits give the minimiser to full FP64 accuracy.
+    Same steps as ko_design_colored_sg_raw: Sbar of eq (22b), S = T Sbar T^T
+    (eq 22c), dc constraints of the pure-delay basis (eq 16c-d), eq (20)."""
+    import mpmath as mp
+
+    key = (L_D, K, float(omega_c), dps)
+    if key in _MP_CACHE:
+        return _MP_CACHE[key].copy()
+    ctx = mp.MPContext()
+    ctx.dps = dps
+    wc = ctx.mpf(omega_c)
+    NK, Ldc = K + 1, L_D + 1
+    N = NK + Ldc
+
+    def sbar(d):  # eq (22b); sin(pi d) = 0 for integer d
+        if d == 0:
+            return (ctx.pi - wc) / ctx.pi
+        return (ctx.sin(ctx.pi * d) - ctx.sin(wc * d)) / (ctx.pi * d)
+
+    sb = {d: sbar(d) for d in range(-2 * K, 2 * K + 1)}
+    A = ctx.zeros(N, N)
+    rhs = ctx.zeros(N, 1)
+    for k1 in range(NK):
+        for k2 in range(NK):
+            v = 0
+            for s1 in ((-1,) if k1 == 0 else (-1, 1)):
+                for s2 in ((-1,) if k2 == 0 else (-1, 1)):
+                    v += sb[s1 * k1 - s2 * k2]
+            A[k1, k2] = v
+    for lb in range(Ldc):
+        for k in range(NK):
+            mu = ctx.mpf(1) / 2 if k == 0 else 1
+            v = 2 * mu * (-1) ** lb * (1 if lb == 0 else ctx.mpf(k) ** (2 * lb))
+            A[NK + lb, k] = v
+            A[k, NK + lb] = v
+    rhs[NK] = 1
+    x = ctx.lu_solve(A, rhs)
+    h = np.array([float(x[k]) for k in range(NK)])
+    _MP_CACHE[key] = h
+    return h.copy()
+
+
+def sg_half_length(L_D: int, sigma: float, kmax: int = 96) -> int:
+    K = int(np.ceil((5.0 if L_D == 1 else 7.0) * sigma))
+    return min(K, kmax) if kmax > 0 else K
+
+
 def design_colored_sg_raw(L_D: int, K: int, omega_c: float) -> np.ndarray:
     h = np.zeros(K + 1)
     if lib().ko_design_colored_sg_raw(L_D, K, omega_c, _p(h)) < 0:
@@ -221,7 +277,22 @@ def bank(img, lambdas, ftype=IIR_REPEATED_POLE, order=3, resp=RESP_LAPLACIAN,
     S = len(lam)
     R = np.zeros((S, H, W))
     D = np.zeros((S, 5, H, W)) if want_d else None
+    taps = tapK = None
+    stride = 0
+    if ftype == FIR_COLORED_SG:  # high-precision design (see design_colored_sg_mp)
+        hs = []
+        for l in lam:
+            sigma = l / 2.0
+            if not (3.0 / sigma < np.pi):
+                raise ValueError("oracle bank: design failed")
+            hs.append(design_colored_sg_mp(order, sg_half_length(order, sigma, fir_kmax), 3.0 / sigma))
+        stride = max(len(h) for h in hs)
+        taps = np.zeros((S, stride))
+        for s, h in enumerate(hs):
+            taps[s, :len(h)] = h
+        tapK = (ctypes.c_int * S)(*[len(h) - 1 for h in hs])
     rc = lib().ko_bank(_p(img), H, W, S, _p(lam), ftype, order, resp, boundary, fir_kmax,
+                       _p(taps) if taps is not None else None, tapK, stride,
                        _p(R), _p(D) if want_d else None)
     if rc:
         raise ValueError("oracle bank: design failed")

@@ -104,7 +104,8 @@ int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S,
   if (nmax > ctx->dwork_nmax) {
     if (ctx->dwork) cudaFree(ctx->dwork);
     ctx->dwork = nullptr;
-    size_t n = (size_t)KF_MAX_SCALES * ((size_t)nmax * nmax + 2 * nmax);
+    // double-double KKT matrix and right-hand side per scale
+    size_t n = (size_t)KF_MAX_SCALES * 2 * ((size_t)nmax * nmax + nmax);
     if ((e = cudaMalloc(&ctx->dwork, n * sizeof(double))) != cudaSuccess)
       return cuda_fail(ctx, e, "cudaMalloc(design work)");
     ctx->dwork_nmax = nmax;

@@ -167,7 +167,7 @@ __device__ void design_D(Coef &c, int order, double lambda) {
   }
   for (int i = 0; i < K; ++i) {
     c.phiL[i] = (float)binom_pow(LC, i, p);
-    for (int lv = 0; lv < SCAN_LEVELS; ++lv) c.phiS[lv][i] = (float)binom_pow((long)CH << lv, i, p);
+    for (int m = 1; m <= WARPM; ++m) c.phiM[m - 1][i] = (float)binom_pow((long)CH * m, i, p);
   }
   c.p = pf;
   c.b0 = (float)hm[0];
@@ -268,10 +268,10 @@ __device__ void design_E(Coef &c, int order, double lambda) {
     cd zl = cpow(zm[i], LC);
     c.zLr[i] = (float)zl.r;
     c.zLi[i] = (float)zl.i;
-    for (int lv = 0; lv < SCAN_LEVELS; ++lv) {
-      cd zs = cpow(zm[i], (long)CH << lv);
-      c.zSr[lv][i] = (float)zs.r;
-      c.zSi[lv][i] = (float)zs.i;
+    for (int m = 1; m <= WARPM; ++m) {
+      cd zs = cpow(zm[i], (long)CH * m);
+      c.zMr[m - 1][i] = (float)zs.r;
+      c.zMi[m - 1][i] = (float)zs.i;
     }
   }
   c.K = nm;
@@ -307,12 +307,96 @@ __device__ void design_E(Coef &c, int order, double lambda) {
 }
 
 // ---------------------------------------------------------------------------
+// double-double arithmetic (about 32 significant digits from FP64 pairs;
+// error-free transformations of Knuth/Dekker, fma-based products)
+// ---------------------------------------------------------------------------
+struct dd {
+  double hi, lo;
+};
+__device__ __forceinline__ dd two_sum(double a, double b) {
+  const double s = __dadd_rn(a, b), bb = __dsub_rn(s, a);
+  return {s, __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb))};
+}
+__device__ __forceinline__ dd quick_two_sum(double a, double b) {
+  const double s = __dadd_rn(a, b);
+  return {s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+  s.lo = __dadd_rn(s.lo, t.hi);
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo = __dadd_rn(s.lo, t.lo);
+  return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  const double p = __dmul_rn(a.hi, b.hi);
+  double e = fma(a.hi, b.hi, -p);
+  e = fma(a.hi, b.lo, e);
+  e = fma(a.lo, b.hi, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ dd dd_mul_d(dd a, double b) { return dd_mul(a, dd{b, 0.0}); }
+__device__ dd dd_div(dd a, dd b) {
+  const double q1 = a.hi / b.hi;
+  dd r = dd_sub(a, dd_mul_d(b, q1));
+  const double q2 = r.hi / b.hi;
+  r = dd_sub(r, dd_mul_d(b, q2));
+  const double q3 = r.hi / b.hi;
+  dd q = quick_two_sum(q1, q2);
+  return dd_add(q, dd{q3, 0.0});
+}
+__device__ __forceinline__ dd dd_from(double a) { return {a, 0.0}; }
+__device__ __forceinline__ double dd_abs_hi(dd a) { return fabs(a.hi); }
+
+// pi/2 and pi as double-double constants
+__device__ __forceinline__ dd dd_pi2() { return {1.5707963267948966, 6.123233995736766e-17}; }
+__device__ __forceinline__ dd dd_pi() { return {3.141592653589793, 1.2246467991473532e-16}; }
+
+// sin of a double-double argument |x| < ~1e3: reduce by k pi/2 (Cody-Waite
+// with the double-double pi/2), Taylor series on |r| <= pi/4.
+__device__ dd dd_sin(dd x) {
+  const double kf = rint(x.hi / 1.5707963267948966);
+  const dd r = dd_sub(x, dd_mul_d(dd_pi2(), kf));
+  const int q = ((long long)kf % 4 + 4) % 4;
+  const dd r2 = dd_mul(r, r);
+  dd s, c;
+  {  // sin r = r - r^3/3! + ...
+    dd term = r, sum = r;
+    for (int n = 1; n < 20; ++n) {
+      term = dd_div(dd_mul(term, r2), dd_from(-(double)(2 * n) * (double)(2 * n + 1)));
+      sum = dd_add(sum, term);
+      if (dd_abs_hi(term) < 1e-36) break;
+    }
+    s = sum;
+  }
+  {  // cos r = 1 - r^2/2! + ...
+    dd term = dd_from(1.0), sum = dd_from(1.0);
+    for (int n = 1; n < 20; ++n) {
+      term = dd_div(dd_mul(term, r2), dd_from(-(double)(2 * n - 1) * (double)(2 * n)));
+      sum = dd_add(sum, term);
+      if (dd_abs_hi(term) < 1e-36) break;
+    }
+    c = sum;
+  }
+  switch (q) {
+    case 0: return s;
+    case 1: return c;
+    case 2: return dd_neg(s);
+    default: return dd_neg(c);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Filter C (Sec. 4.2): minimise (1/pi) int_wc^pi |H|^2 subject to the dc
 // constraints (eq 20), pure-delay basis (eq 16), S = T Sbar T^T (eq 22).
-// Parallel equilibrated Gaussian elimination on the KKT matrix in `work`.
+// Near sigma = 1 (wc = 3 close to pi) the KKT matrix has a condition number
+// of about 1e17, so the matrix is built and solved in double-double
+// (equilibrated Gaussian elimination with partial pivoting, one CTA).
+// A, b: N x N and N double-double entries of workspace (as 2 doubles each).
 // ---------------------------------------------------------------------------
-__device__ void design_C(Coef &c, int order, double lambda, int kmax, double *A, double *b,
-                         double *scl, int Nmax) {
+__device__ void design_C(Coef &c, int order, double lambda, int kmax, dd *A, dd *b, int Nmax) {
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ int s_K, s_bad, s_piv;
   __shared__ double s_red[256];
@@ -334,54 +418,65 @@ __device__ void design_C(Coef &c, int order, double lambda, int kmax, double *A,
     return;
   }
   const int K = s_K, NK = K + 1, Ldc = LD + 1, N = NK + Ldc;
-  const double wc = 3.0 / sigma;
   if (N > Nmax) {
     if (tid == 0) c.status = 1;
     return;
   }
+  // wc = 3 / sigma with sigma = lambda / 2 exact in binary: wc = 6 / lambda
+  const dd wcd = dd_div(dd_from(6.0), dd_from(lambda));
+  const dd pid = dd_pi();
+  // Sbar(delta) of eq (22b): (sin(pi d) - sin(wc d)) / (pi d); sin(pi d) = 0
+  // for integer d; the diagonal is (pi - wc) / pi.
   for (int idx = tid; idx < N * N; idx += nt) {
     const int i = idx / N, j = idx % N;
-    double v = 0.0;
+    dd v = dd_from(0.0);
     if (i < NK && j < NK) {
       for (int s1 = -1; s1 <= 1; s1 += 2) {
         if (i == 0 && s1 == 1) continue;
         for (int s2 = -1; s2 <= 1; s2 += 2) {
           if (j == 0 && s2 == 1) continue;
           const int d = s1 * i - s2 * j;
-          v += (d == 0) ? (M_PI - wc) / M_PI : -sin(wc * d) / (M_PI * d);
+          dd t;
+          if (d == 0) t = dd_div(dd_sub(pid, wcd), pid);
+          else t = dd_neg(dd_div(dd_sin(dd_mul_d(wcd, (double)d)), dd_mul_d(pid, (double)d)));
+          v = dd_add(v, t);
         }
       }
     } else if (i < NK || j < NK) {
       const int lb = (i < NK) ? j - NK : i - NK, k = (i < NK) ? i : j;
       const double mu = (k == 0) ? 0.5 : 1.0;
-      const double kp = (lb == 0) ? 1.0 : pow((double)k, 2.0 * lb);
-      v = 2.0 * mu * ((lb & 1) ? -1.0 : 1.0) * kp;
+      const double kp = (lb == 0) ? 1.0 : pow((double)k, 2.0 * lb);  // exact integers
+      v = dd_from(2.0 * mu * ((lb & 1) ? -1.0 : 1.0) * kp);
     }
     A[idx] = v;
   }
-  for (int i = tid; i < N; i += nt) b[i] = (i == NK) ? 1.0 : 0.0;
+  for (int i = tid; i < N; i += nt) b[i] = dd_from((i == NK) ? 1.0 : 0.0);
   __syncthreads();
-  // equilibrate rows then columns
+  // equilibrate rows and columns by powers of two (exact)
   for (int i = tid; i < N; i += nt) {
     double m = 0.0;
-    for (int j = 0; j < N; ++j) m = fmax(m, fabs(A[i * N + j]));
-    const double s = m > 0.0 ? 1.0 / m : 1.0;
-    for (int j = 0; j < N; ++j) A[i * N + j] *= s;
-    b[i] *= s;
+    for (int j = 0; j < N; ++j) m = fmax(m, fabs(A[i * N + j].hi));
+    const double sc = m > 0.0 ? exp2(-(double)ilogb(m)) : 1.0;
+    for (int j = 0; j < N; ++j) A[i * N + j] = dd_mul_d(A[i * N + j], sc);
+    b[i] = dd_mul_d(b[i], sc);
   }
   __syncthreads();
+  double *colscale = s_red;  // reused below only after this loop's last read
+  __shared__ double s_cs[MAX_FIR_K + 8];
   for (int j = tid; j < N; j += nt) {
     double m = 0.0;
-    for (int i = 0; i < N; ++i) m = fmax(m, fabs(A[i * N + j]));
-    scl[j] = m > 0.0 ? 1.0 / m : 1.0;
-    for (int i = 0; i < N; ++i) A[i * N + j] *= scl[j];
+    for (int i = 0; i < N; ++i) m = fmax(m, fabs(A[i * N + j].hi));
+    const double sc = m > 0.0 ? exp2(-(double)ilogb(m)) : 1.0;
+    s_cs[j] = sc;
+    for (int i = 0; i < N; ++i) A[i * N + j] = dd_mul_d(A[i * N + j], sc);
   }
+  (void)colscale;
   __syncthreads();
   for (int k = 0; k < N; ++k) {
     double best = -1.0;
     int bi = k;
     for (int i = k + tid; i < N; i += nt) {
-      const double a = fabs(A[i * N + k]);
+      const double a = fabs(A[i * N + k].hi);
       if (a > best) best = a, bi = i;
     }
     s_red[tid] = best;
@@ -403,23 +498,23 @@ __device__ void design_C(Coef &c, int order, double lambda, int kmax, double *A,
     const int piv = s_piv;
     if (piv != k) {
       for (int j = tid; j < N; j += nt) {
-        const double t = A[k * N + j];
+        const dd t = A[k * N + j];
         A[k * N + j] = A[piv * N + j];
         A[piv * N + j] = t;
       }
       if (tid == 0) {
-        const double t = b[k];
+        const dd t = b[k];
         b[k] = b[piv];
         b[piv] = t;
       }
     }
     __syncthreads();
-    const double akk = A[k * N + k];
+    const dd akk = A[k * N + k];
     for (int i = k + 1 + tid; i < N; i += nt) {
-      const double f = A[i * N + k] / akk;
-      if (f != 0.0) {
-        for (int j = k; j < N; ++j) A[i * N + j] -= f * A[k * N + j];
-        b[i] -= f * b[k];
+      const dd f = dd_div(A[i * N + k], akk);
+      if (f.hi != 0.0) {
+        for (int j = k; j < N; ++j) A[i * N + j] = dd_sub(A[i * N + j], dd_mul(f, A[k * N + j]));
+        b[i] = dd_sub(b[i], dd_mul(f, b[k]));
       }
     }
     __syncthreads();
@@ -429,16 +524,16 @@ __device__ void design_C(Coef &c, int order, double lambda, int kmax, double *A,
     return;
   }
   for (int i = N - 1; i >= 0; --i) {
-    if (tid == 0) b[i] /= A[i * N + i];
+    if (tid == 0) b[i] = dd_div(b[i], A[i * N + i]);
     __syncthreads();
-    const double xi = b[i];
-    for (int r = tid; r < i; r += nt) b[r] -= A[r * N + i] * xi;
+    const dd xi = b[i];
+    for (int r = tid; r < i; r += nt) b[r] = dd_sub(b[r], dd_mul(A[r * N + i], xi));
     __syncthreads();
   }
   for (int k = tid; k < NK; k += nt) {
-    const double hk = b[k] * scl[k];
-    c.dh[k] = hk;
-    c.h[k] = (float)hk;
+    const dd hk = dd_mul_d(b[k], s_cs[k]);
+    c.dh[k] = hk.hi + hk.lo;
+    c.h[k] = (float)(hk.hi + hk.lo);
   }
   __syncthreads();
   if (tid == 0) {
@@ -452,7 +547,7 @@ __device__ void design_C(Coef &c, int order, double lambda, int kmax, double *A,
     c.K = K;
     c.b0 = c.h[0];
     c.db0 = c.dh[0];
-    c.param = wc;
+    c.param = wcd.hi;
   }
 }
 
@@ -472,9 +567,8 @@ __global__ void __launch_bounds__(256) k_design(int type, int order, const doubl
   }
   __syncthreads();
   if (type == T_C) {
-    double *A = work + (size_t)s * ((size_t)Nmax * Nmax + 2 * Nmax);
-    design_C(c, order, lambda, fir_kmax, A, A + (size_t)Nmax * Nmax, A + (size_t)Nmax * Nmax + Nmax,
-             Nmax);
+    dd *A = reinterpret_cast<dd *>(work) + (size_t)s * ((size_t)Nmax * Nmax + Nmax);
+    design_C(c, order, lambda, fir_kmax, A, A + (size_t)Nmax * Nmax, Nmax);
   } else if (threadIdx.x == 0) {
     if (type == T_D) design_D(c, order, lambda);
     else if (type == T_E) design_E(c, order, lambda);

@@ -76,10 +76,11 @@ struct Chain {
       t[j] = acc;
     }
   }
-  __device__ __forceinline__ void combine_level(const Coef &c, int lv, const Chain &prev) {
+  // this <- Phi^(CH m) prev + this, 1 <= m <= 32
+  __device__ __forceinline__ void combine_m(const Coef &c, int m, const Chain &prev) {
     float phi[KK];
 #pragma unroll
-    for (int i = 0; i < KK; ++i) phi[i] = c.phiS[lv][i];
+    for (int i = 0; i < KK; ++i) phi[i] = c.phiM[m - 1][i];
     combine(phi, prev);
   }
   __device__ __forceinline__ void combine_L(const Coef &c, const Chain &prev) {
@@ -152,10 +153,10 @@ struct Modes {
       ti[i] = fmaf(zr[i], prev.ti[i], fmaf(zi[i], prev.tr[i], ti[i]));
     }
   }
-  __device__ __forceinline__ void combine_level(const Coef &c, int lv, const Modes &prev) {
+  __device__ __forceinline__ void combine_m(const Coef &c, int m, const Modes &prev) {
     float zr[NM], zi[NM];
 #pragma unroll
-    for (int i = 0; i < NM; ++i) zr[i] = c.zSr[lv][i], zi[i] = c.zSi[lv][i];
+    for (int i = 0; i < NM; ++i) zr[i] = c.zMr[m - 1][i], zi[i] = c.zMi[m - 1][i];
     combine_z(zr, zi, prev);
   }
   __device__ __forceinline__ void combine_L(const Coef &c, const Modes &prev) {
@@ -188,39 +189,47 @@ struct Modes {
   }
 };
 
-// Block-wide carry scan of a chain of chunks of CH samples.  `u` is this
-// thread's zero-state end state; `k` its position in scan order (0 = first
-// chunk of the direction); `init` the state before chunk 0.  Returns the state
-// before this thread's chunk.  REV: scan order is the reverse thread order.
+// Block-wide carry scan over the chunks of CH samples of one row.  `u` is
+// this thread's zero-state end state; `k` its position in scan order (0 =
+// first chunk of the direction); `init` the state before chunk 0.  Returns
+// the state before this thread's chunk:
+//   1. inclusive scan inside each warp (u_k <- A^d u_{k-d} + u_k, A = Phi^CH),
+//   2. one thread folds the warp aggregates: C_0 = init,
+//      C_{w+1} = A^32 C_w + G_w,
+//   3. carry_k = C_w (lane 0) or A^lane C_w + (scan value of lane - 1).
+// REV: scan order is the reverse thread order.  sm: 64 * NF floats.
 template <class Rec, bool REV>
 __device__ Rec carry_scan(Rec u, const Coef &c, int k, int NT, float *sm, const Rec &init) {
+  const int lane = k & 31, wid = k >> 5, NW = NT >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const Rec o = REV ? u.shfl_down(d) : u.shfl_up(d);
+    if (lane >= d) u.combine_m(c, d, o);
+  }
+  float *G = sm, *Cw = sm + 32 * Rec::NF;
+  if (lane == 31) u.store(G + wid, 32);
+  __syncthreads();
   if (k == 0) {
-    Rec t = u;
-    t.combine_level(c, 0, init);  // Phi^CH init + u
-    u = t;
+    Rec C = init;
+    for (int w = 0; w < NW; ++w) {
+      C.store(Cw + w, 32);
+      Rec g;
+      g.load(G + w, 32);
+      g.combine_m(c, 32, C);  // A^32 C_w + G_w
+      C = g;
+    }
   }
-  const int lane = k & 31;
-  int lv = 0;
-  for (int d = 1; d < 32 && d < NT; d <<= 1, ++lv) {
-    Rec o = REV ? u.shfl_down(d) : u.shfl_up(d);
-    if (lane >= d) u.combine_level(c, lv, o);
-  }
-  const int tid = threadIdx.x;
-  for (int d = 32; d < NT; d <<= 1, ++lv) {
-    u.store(sm + tid, NT);
-    __syncthreads();
-    Rec o;
-    o.zero();
-    if (k >= d) o.load(sm + (REV ? tid + d : tid - d), NT);
-    __syncthreads();
-    if (k >= d) u.combine_level(c, lv, o);
-  }
-  u.store(sm + tid, NT);
   __syncthreads();
-  Rec r = init;
-  if (k > 0) r.load(sm + (REV ? tid + 1 : tid - 1), NT);
+  Rec carry;
+  carry.load(Cw + wid, 32);
+  const Rec prev = REV ? u.shfl_down(1) : u.shfl_up(1);
+  if (lane > 0) {
+    Rec t = prev;
+    t.combine_m(c, lane, carry);
+    carry = t;
+  }
   __syncthreads();
-  return r;
+  return carry;
 }
 
 __host__ __device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
@@ -428,7 +437,7 @@ template <class Rec>
 int run_iir(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   const int NT = ((g.W + CH - 1) / CH + 31) / 32 * 32;
   if (NT > 1024) return -1;
-  const size_t row_smem = (size_t)(3 * (pad32(NT * CH) + 1) + NT * Rec::NF) * sizeof(float);
+  const size_t row_smem = (size_t)(3 * (pad32(NT * CH) + 1) + 64 * Rec::NF) * sizeof(float);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_row<Rec, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

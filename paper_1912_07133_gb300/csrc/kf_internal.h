@@ -8,7 +8,8 @@
 namespace kf {
 
 // FP64 design of S scales into d_out (device array of S Coef).  d_work holds
-// S * (Nmax^2 + 2 Nmax) doubles for the colored-SG KKT solve.
+// S * 2 (Nmax^2 + Nmax) doubles (double-double KKT matrix and right-hand side
+// of the colored-SG design).
 int launch_design(int type, int order, const double *d_lambdas, int S, int fir_kmax, Coef *d_out,
                   double *d_work, int Nmax, cudaStream_t st);
 

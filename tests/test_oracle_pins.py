@@ -370,7 +370,7 @@ def test_fir_boundaries_against_padding():
 # ----------------------------------------------------------------------------
 def one_d_ir(ftype, order, sigma):
     if ftype == O.FIR_COLORED_SG:
-        h = O.design_colored_sg(order, sigma, 96)
+        h = O.design_colored_sg_mp(order, O.sg_half_length(order, sigma, 96), 3.0 / sigma)
         K = len(h) - 1
         return h[np.abs(np.arange(-K, K + 1))]
     if ftype == O.IIR_REPEATED_POLE:
@@ -584,3 +584,60 @@ def test_filter_d_a17_route_matches_ir_route(Lpi, sigma):
     r = O.a17(b, a, aplus)
     np.testing.assert_allclose(r["bplus"], d["bplus"], rtol=1e-9, atol=1e-15)
     assert r["b0"] == pytest.approx(d["b0"], rel=1e-9)
+
+
+# ----------------------------------------------------------------------------
+# Filter C in high precision (the design used by the oracle bank)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("sigma", [2.0, 4.0, 8.0])
+def test_colored_sg_high_precision_matches_fp64_where_well_conditioned(sigma):
+    K = math.ceil(5 * sigma)
+    hmp = O.design_colored_sg_mp(1, K, 3.0 / sigma)
+    h64 = O.design_colored_sg(1, sigma)
+    np.testing.assert_allclose(hmp, h64, rtol=0, atol=1e-9 * np.abs(hmp).max())
+
+
+@pytest.mark.parametrize("sigma", [1.0, 1.25, 1.5])
+def test_colored_sg_high_precision_constraints_near_nyquist_cutoff(sigma):
+    """omega_c = 3/sigma close to pi: the constraints of eq (20) still hold."""
+    K = math.ceil(5 * sigma)
+    h = O.design_colored_sg_mp(1, K, 3.0 / sigma)
+    m = np.arange(-K, K + 1)
+    hh = h[np.abs(m)]
+    assert hh.sum() == pytest.approx(1.0, abs=1e-14)
+    assert abs((m.astype(float) ** 2 * hh).sum()) <= 1e-13
+
+
+def test_colored_sg_high_precision_white_noise_limit():
+    K = 7
+    h = O.design_colored_sg_mp(1, K, 0.0)
+    m = np.arange(0, K + 1)
+    textbook = (3 * (3 * K ** 2 + 3 * K - 1) - 15 * m ** 2) / ((2 * K - 1) * (2 * K + 1) * (2 * K + 3))
+    np.testing.assert_allclose(h, textbook, atol=1e-15)
+
+
+def test_colored_sg_high_precision_is_the_cng_minimum_at_sigma_1():
+    """eq (21) evaluated by adaptive quadrature in 40 digits (independent of the
+    Sbar closed form): perturbations that keep the constraints raise the CNG."""
+    import mpmath as mp
+    ctx = mp.MPContext()
+    ctx.dps = 40
+    sigma, K = 1.0, 5
+    wc = 3.0 / sigma
+    h = O.design_colored_sg_mp(1, K, wc)
+    c = [ctx.mpf(float(v)) for v in h]  # FP64-rounded minimiser
+
+    def cng(cc):
+        f = lambda w: (cc[0] + 2 * sum(cc[k] * ctx.cos(k * w) for k in range(1, K + 1))) ** 2
+        return ctx.quad(f, [wc, ctx.pi]) / ctx.pi
+
+    base = cng(c)
+    rng = np.random.default_rng(1)
+    m = np.arange(K + 1, dtype=float)
+    Cm = np.stack([np.r_[1.0, 2 * np.ones(K)], np.r_[0.0, 2 * m[1:] ** 2]])  # sum h, sum m^2 h
+    for _ in range(3):
+        v = rng.standard_normal(K + 1)
+        v -= Cm.T @ np.linalg.lstsq(Cm.T, v, rcond=None)[0]
+        v *= 1e-2 / np.abs(v).max()
+        for sg in (1, -1):
+            assert cng([c[k] + sg * ctx.mpf(float(v[k])) for k in range(K + 1)]) > base
