@@ -102,7 +102,8 @@ typedef struct {
   int32_t storage;       /* intermediate planes: KF_DTYPE_F32 / F16 / BF16     */
   double threshold;      /* Threshold #1: |R| > threshold to be a candidate    */
   int32_t fir_kmax;      /* cap on the colored-SG half-length (0 -> 96)        */
-  int32_t reserved0;
+  int32_t profile;       /* 1: record CUDA events around every kernel of the
+                            call on the context stream (kf_kernel_times)       */
   float *responses;      /* optional device output, f32: for frame f, scale s,
                             R at (x, y) is responses[off_f + (s*H + y)*W + x],
                             off_f = sum over earlier frames of nscales*H*W.
@@ -116,6 +117,13 @@ typedef struct {
   int32_t polarity;  /* +1 bright (maximum of R), -1 dark (minimum of R_L) */
   float response;    /* R at (x, y, scale) */
 } kf_blob;
+
+/* Per-kernel device time of the last profiled kf_filter_bank call. */
+typedef struct {
+  char name[32];     /* kernel name                                   */
+  int32_t launches;  /* launches of this kernel in the call            */
+  float ms;          /* summed CUDA-event time of those launches (ms)  */
+} kf_kernel_time;
 
 typedef struct kf_ctx kf_ctx;
 
@@ -177,6 +185,13 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes,
  * blobs are written), KF_ECUDA. */
 int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out,
                     int64_t capacity, int64_t *count);
+
+/* Kernel launches and, when the call ran with opts->profile = 1, per-kernel
+ * CUDA-event times of the last kf_filter_bank call: fills out[0..cap) (host,
+ * caller-owned) and sets *n (host) to the number of distinct kernels.
+ * Synchronises the context stream.  Without profiling, ms is 0.
+ * Errors: KF_EINVAL (NULL arguments, no bank call yet), KF_ECUDA. */
+int kf_kernel_times(kf_ctx *ctx, kf_kernel_time *out, int cap, int *n);
 
 #ifdef __cplusplus
 }

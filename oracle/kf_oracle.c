@@ -644,6 +644,14 @@ void ko_eq27(double d10, double d01, double d20, double d02, double d11,
   *dy = (d10 * d11 - d20 * d01) / *det;  /* eq (27b) */
 }
 
+int ko_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 long ko_detect(const double *R, const double *D, int S, int H, int W, double T,
                int resp, int neigh, double limit2, int frame, ko_blob *out,
                long cap) {

@@ -116,6 +116,9 @@ int ko_bank(const double *img, int H, int W, int nscales, const double *lambdas,
             const double *taps, const int *tapK, int tap_stride, double *R,
             double *D);
 
+/* Threads the oracle's parallel loops use (OpenMP; 1 without it). */
+int ko_threads(void);
+
 /* Offsets of eq (27) and |H| of eq (26) from the five derivatives. */
 void ko_eq27(double d10, double d01, double d20, double d02, double d11,
              double *dx, double *dy, double *det);

@@ -98,6 +98,8 @@ def lib():
             L.ko_bank.restype = i
             L.ko_bank.argtypes = [P, i, i, i, P, i, i, i, i, i, P,
                                   ctypes.POINTER(ctypes.c_int), i, P, P]
+            L.ko_threads.restype = i
+            L.ko_threads.argtypes = []
             L.ko_eq27.restype = None
             L.ko_eq27.argtypes = [d, d, d, d, d, P, P, P]
             L.ko_detect.restype = l
@@ -297,6 +299,11 @@ def bank(img, lambdas, ftype=IIR_REPEATED_POLE, order=3, resp=RESP_LAPLACIAN,
     if rc:
         raise ValueError("oracle bank: design failed")
     return (R, D) if want_d else R
+
+
+def threads() -> int:
+    """Host threads the oracle's parallel loops use."""
+    return int(lib().ko_threads())
 
 
 def eq27(d10, d01, d20, d02, d11):

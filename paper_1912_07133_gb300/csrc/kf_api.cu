@@ -39,6 +39,10 @@ struct kf_ctx {
   int d_type = -1, d_order = -1, d_kmax = -1, d_S = 0;
   double d_lam[KF_MAX_SCALES];
   std::vector<kf::Coef> h_coef;
+  // launch bookkeeping of the last bank call
+  kf::Prof prof{};
+  std::vector<cudaEvent_t> events;
+  bool have_prof = false;
   // last bank call
   bool have_result = false;
   double last_threshold = 0.0;
@@ -205,6 +209,7 @@ void kf_destroy(kf_ctx *ctx) {
   cudaFree(ctx->dwork);
   cudaFree(ctx->status);
   cudaFree(ctx->blobs);
+  for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -327,6 +332,20 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   a.cap = ctx->blob_cap;
   a.status = ctx->status;
   a.responses = opts.responses;
+  ctx->prof = kf::Prof{};
+  ctx->prof.ev = nullptr;
+  if (opts.profile) {
+    const int need = 2 * 256;
+    while ((int)ctx->events.size() < need) {
+      cudaEvent_t ev;
+      if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventCreate");
+      ctx->events.push_back(ev);
+    }
+    ctx->prof.ev = ctx->events.data();
+    ctx->prof.cap = 256;
+  }
+  a.prof = &ctx->prof;
+  ctx->have_prof = true;
   long resp_off = 0;
   for (int f = 0; f < nframes; ++f) {
     const kf_frame &fr = frames[f];
@@ -347,6 +366,42 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   ctx->have_result = true;
   ctx->last_threshold = opts.threshold;
   ctx->last_S = nscales;
+  return KF_OK;
+}
+
+int kf_kernel_times(kf_ctx *ctx, kf_kernel_time *out, int cap, int *n) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_kernel_times: ctx is NULL");
+  if (!n || cap < 0 || (cap > 0 && !out)) return fail(ctx, KF_EINVAL, "kf_kernel_times: bad outputs");
+  if (!ctx->have_prof) return fail(ctx, KF_EINVAL, "kf_kernel_times: no bank call yet");
+  cudaError_t e;
+  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sync");
+  const kf::Prof &p = ctx->prof;
+  std::vector<std::string> names;
+  std::vector<int> launches;
+  std::vector<float> ms;
+  for (int i = 0; i < p.n && i < 256; ++i) {
+    const std::string nm = p.names[i];
+    size_t k = std::find(names.begin(), names.end(), nm) - names.begin();
+    if (k == names.size()) {
+      names.push_back(nm);
+      launches.push_back(0);
+      ms.push_back(0.f);
+    }
+    launches[k] += 1;
+    if (p.ev && i < p.cap) {
+      float t = 0.f;
+      if ((e = cudaEventElapsedTime(&t, p.ev[2 * i], p.ev[2 * i + 1])) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaEventElapsedTime");
+      ms[k] += t;
+    }
+  }
+  *n = (int)names.size();
+  for (int i = 0; i < cap && i < (int)names.size(); ++i) {
+    std::memset(out[i].name, 0, sizeof out[i].name);
+    std::strncpy(out[i].name, names[i].c_str(), sizeof out[i].name - 1);
+    out[i].launches = launches[i];
+    out[i].ms = ms[i];
+  }
   return KF_OK;
 }
 

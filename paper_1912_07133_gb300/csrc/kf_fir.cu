@@ -168,9 +168,13 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   const int kmax = a.kmax;
   const size_t rsm = (size_t)(RSEG + 2 * kmax + 8 + kmax + 1) * sizeof(float);
   dim3 gr((g.W + RSEG - 1) / RSEG, g.H);
+  a.prof->begin("fir_row", st);
   k_rowfir<false><<<gr, RNT, rsm, st>>>(g.X, g.xpitch, g.H, g.W, a.coef, a.S, kmax, a.P, g.PW, a.edge);
+  a.prof->end(st);
   dim3 ge((g.W + RSEG - 1) / RSEG, 2);
+  a.prof->begin("fir_row_edge", st);
   k_rowfir<true><<<ge, RNT, rsm, st>>>(g.X, g.xpitch, g.H, g.W, a.coef, a.S, kmax, a.P, g.PW, a.edge);
+  a.prof->end(st);
   DetectArgs da;
   da.H = g.H;
   da.W = g.W;
@@ -186,7 +190,9 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
                       (size_t)CROWS * 32 * 2) * sizeof(float) + (size_t)CROWS * 32 * 2;
   if (csm > 220 * 1024) return -1;
   dim3 gc((g.W + TW - 1) / TW, (g.H + CROWS - 3) / (CROWS - 2));
+  a.prof->begin("fir_coldet", st);
   k_colfir<<<gc, 256, csm, st>>>(a.P, g.PW, g.H, g.W, a.edge, a.coef, a.S, kmax, da);
+  a.prof->end(st);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -446,13 +446,21 @@ int run_iir(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
     attr = true;
   }
   if (row_smem > 200 * 1024) return -1;
+  a.prof->begin("iir_row", st);
   k_row<Rec, false><<<g.H, NT, row_smem, st>>>(g.X, g.xpitch, g.H, g.W, a.coef, a.S, a.P, g.PW, a.edge);
+  a.prof->end(st);
+  a.prof->begin("iir_row_edge", st);
   k_row<Rec, true><<<2, NT, row_smem, st>>>(g.X, g.xpitch, g.H, g.W, a.coef, a.S, a.P, g.PW, a.edge);
+  a.prof->end(st);
   const int nseg = (g.H + LC - 1) / LC;
   dim3 gs((g.W + 127) / 128, nseg, a.S);
+  a.prof->begin("iir_colseg", st);
   k_colseg<Rec><<<gs, 128, 0, st>>>(a.P, g.PW, g.H, g.W, a.edge, a.coef, a.carry, nseg);
+  a.prof->end(st);
   dim3 gf((g.W + 127) / 128, a.S);
+  a.prof->begin("iir_colfold", st);
   k_colfold<Rec><<<gf, 128, 0, st>>>(g.W, g.PW, a.edge, a.coef, a.carry, nseg);
+  a.prof->end(st);
   DetectArgs da;
   da.H = g.H;
   da.W = g.W;
@@ -467,8 +475,10 @@ int run_iir(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   constexpr int NR = LC + 2;
   const size_t det_smem = ((size_t)a.S * NR * 32 + (size_t)NR * 32 * 2) * sizeof(float) + (size_t)NR * 32 * 2;
   dim3 gd((g.W + TW - 1) / TW, nseg);
+  a.prof->begin("iir_coldet", st);
   k_coldet<Rec><<<gd, 32 * a.S, det_smem, st>>>(a.P, g.PW, g.H, g.W, a.edge, a.coef, a.S, a.carry,
                                                  nseg, da);
+  a.prof->end(st);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -23,6 +23,22 @@ struct FrameGeom {
   long resp_off;    // offset of this frame in the responses output
 };
 
+// Optional per-launch event recording (profiling) and launch counting.
+struct Prof {
+  cudaEvent_t *ev;        // 2 events per launch, or nullptr
+  int cap;                // launches that fit in ev
+  int n;                  // launches so far in this call
+  const char *names[256]; // kernel name of each launch
+  void begin(const char *name, cudaStream_t st) {
+    if (n < 256) names[n] = name;
+    if (ev && n < cap) cudaEventRecord(ev[2 * n], st);
+  }
+  void end(cudaStream_t st) {
+    if (ev && n < cap) cudaEventRecord(ev[2 * n + 1], st);
+    ++n;
+  }
+};
+
 struct BankArgs {
   const Coef *coef;      // device, S entries
   int S;
@@ -37,6 +53,7 @@ struct BankArgs {
   long cap;
   DevStatus *status;
   float *responses;      // optional
+  Prof *prof;            // launch bookkeeping (never null)
 };
 
 int launch_iir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st);

@@ -44,7 +44,7 @@ KF_MAX_ORDER = 8
 KF_MAX_FIR_K = 160
 
 ENTRY_POINTS = ("kf_bank_opts_default", "kf_create", "kf_destroy", "kf_last_error", "kf_design",
-                "kf_filter_bank", "kf_detect_blobs")
+                "kf_filter_bank", "kf_detect_blobs", "kf_kernel_times")
 
 
 class kf_coeffs(ctypes.Structure):
@@ -66,13 +66,17 @@ class kf_bank_opts(ctypes.Structure):
     _fields_ = [("response", ctypes.c_int32), ("boundary", ctypes.c_int32),
                 ("neighbourhood", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("threshold", ctypes.c_double), ("fir_kmax", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("responses", ctypes.c_void_p),
+                ("profile", ctypes.c_int32), ("responses", ctypes.c_void_p),
                 ("reserved", ctypes.c_int64 * 4)]
 
 
 class kf_blob(ctypes.Structure):
     _fields_ = [("frame", ctypes.c_int32), ("x", ctypes.c_int32), ("y", ctypes.c_int32),
                 ("scale", ctypes.c_int32), ("polarity", ctypes.c_int32), ("response", ctypes.c_float)]
+
+
+class kf_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 BLOB_DTYPE = np.dtype([("frame", "<i4"), ("x", "<i4"), ("y", "<i4"), ("scale", "<i4"),
@@ -111,6 +115,8 @@ def load(path: str = LIB_PATH):
                                  ctypes.POINTER(kf_bank_opts)]
     L.kf_detect_blobs.restype = i32
     L.kf_detect_blobs.argtypes = [vp, dbl, ctypes.POINTER(kf_blob), i64, ctypes.POINTER(i64)]
+    L.kf_kernel_times.restype = i32
+    L.kf_kernel_times.argtypes = [vp, ctypes.POINTER(kf_kernel_time), i32, ctypes.POINTER(i32)]
     _lib = L
     return L
 
@@ -198,6 +204,14 @@ def kf_detect_blobs(ctx: int, threshold: float, capacity: int = 1 << 20) -> np.n
     return out[: n.value].copy()
 
 
+def kf_kernel_times(ctx: int) -> dict:
+    """{kernel name: (launches, ms)} of the last bank call."""
+    out = (kf_kernel_time * 64)()
+    n = ctypes.c_int(0)
+    _check(load().kf_kernel_times(ctx, out, 64, ctypes.byref(n)), ctx)
+    return {out[i].name.decode(): (out[i].launches, out[i].ms) for i in range(min(n.value, 64))}
+
+
 class Bank:
     """Convenience wrapper: one context, repeated bank calls."""
 
@@ -205,9 +219,10 @@ class Bank:
         self.ctx = kf_create(device, stream)
 
     def run(self, frames, scales, ftype=KF_IIR_REPEATED_POLE, order=4, threshold=0.05,
-            neighbourhood=KF_NEIGH_ALL_SCALES, responses=None, fir_kmax=96):
+            neighbourhood=KF_NEIGH_ALL_SCALES, responses=None, fir_kmax=96, profile=False):
         o = kf_bank_opts_default()
         o.threshold = float(threshold)
+        o.profile = 1 if profile else 0
         o.neighbourhood = neighbourhood
         o.fir_kmax = fir_kmax
         if responses is not None:
@@ -221,6 +236,9 @@ class Bank:
             o.responses = responses.data_ptr()
         self.threshold = float(threshold)
         kf_filter_bank(self.ctx, frames, scales, ftype, order, o)
+
+    def kernel_times(self) -> dict:
+        return kf_kernel_times(self.ctx)
 
     def blobs(self, threshold=None, capacity=1 << 20) -> np.ndarray:
         return kf_detect_blobs(self.ctx, self.threshold if threshold is None else threshold, capacity)

@@ -28,7 +28,7 @@ def lib():
 def test_header_declares_the_boundary():
     syms = declared_symbols()
     for name in ("kf_create", "kf_destroy", "kf_last_error", "kf_design", "kf_filter_bank",
-                 "kf_detect_blobs", "kf_bank_opts_default"):
+                 "kf_detect_blobs", "kf_bank_opts_default", "kf_kernel_times"):
         assert name in syms
 
 
@@ -55,6 +55,7 @@ def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(kf.kf_frame) == 32
     assert ctypes.sizeof(kf.kf_blob) == 24
     assert ctypes.sizeof(kf.kf_bank_opts) == 4 * 4 + 8 + 8 + 8 + 32
+    assert ctypes.sizeof(kf.kf_kernel_time) == 40
     o = kf.kf_bank_opts_default()
     assert o.threshold == 0.05 and o.fir_kmax == 96 and o.storage == kf.KF_DTYPE_F32
 
