@@ -27,18 +27,33 @@ struct kf_ctx {
   size_t edge_floats = 0;
   float *carry = nullptr;
   size_t carry_floats = 0;
-  kf::Coef *coef = nullptr;
   double *lambdas = nullptr;
   double *dwork = nullptr;
   int dwork_nmax = 0;
   kf::DevStatus *status = nullptr;
   kf::Blob *blobs = nullptr;
   long blob_cap = 0;
-  // design cache: (type, order, kmax, scales) -> coef
-  bool design_valid = false;
-  int d_type = -1, d_order = -1, d_kmax = -1, d_S = 0;
-  double d_lam[KF_MAX_SCALES];
-  std::vector<kf::Coef> h_coef;
+  // design cache: (type, order, kmax, scales) -> coefficients, LRU
+  struct Design {
+    int type = -1, order = -1, kmax = -1, S = 0;
+    double lam[KF_MAX_SCALES];
+    kf::Coef *d_coef = nullptr;
+    std::vector<kf::Coef> h_coef;
+    unsigned long long used = 0;
+  };
+  std::vector<Design> designs;
+  unsigned long long tick = 0;
+  Design *cur = nullptr;
+  // candidate ordering
+  kf::Blob *sorted = nullptr;
+  void *sort_work = nullptr;
+  size_t sort_work_bytes = 0;
+  unsigned *d_npass = nullptr;
+  bool sorted_valid = false;
+  double sorted_thr = 0.0;
+  long sorted_n = 0;
+  int last_nframes = 0;
+  long last_hmax = 0, last_wmax = 0;
   // launch bookkeeping of the last bank call
   kf::Prof prof{};
   std::vector<cudaEvent_t> events;
@@ -91,18 +106,36 @@ int nmax_for(int type, int order, int kmax) {
 }
 
 // Run the FP64 design kernel for (type, order, scales) unless the context
-// already holds exactly this design; returns the per-scale records on host.
+// already holds exactly this design (small LRU cache); ctx->cur points at it.
+constexpr size_t kDesignSlots = 8;
+
 int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S, int kmax) {
-  if (ctx->design_valid && ctx->d_type == type && ctx->d_order == order && ctx->d_kmax == kmax &&
-      ctx->d_S == S && std::equal(scales, scales + S, ctx->d_lam))
-    return KF_OK;
-  ctx->design_valid = false;
+  for (auto &d : ctx->designs)
+    if (d.type == type && d.order == order && d.kmax == kmax && d.S == S &&
+        std::equal(scales, scales + S, d.lam)) {
+      d.used = ++ctx->tick;
+      ctx->cur = &d;
+      return KF_OK;
+    }
+  ctx->cur = nullptr;
   cudaError_t e;
-  if (!ctx->coef) {
-    if ((e = cudaMalloc(&ctx->coef, sizeof(kf::Coef) * KF_MAX_SCALES)) != cudaSuccess)
-      return cuda_fail(ctx, e, "cudaMalloc(coef)");
+  if (!ctx->lambdas) {
     if ((e = cudaMalloc(&ctx->lambdas, sizeof(double) * KF_MAX_SCALES)) != cudaSuccess)
       return cuda_fail(ctx, e, "cudaMalloc(lambdas)");
+  }
+  kf_ctx::Design *slot = nullptr;
+  if (ctx->designs.size() < kDesignSlots) {
+    ctx->designs.reserve(kDesignSlots);
+    ctx->designs.emplace_back();
+    slot = &ctx->designs.back();
+  } else {
+    slot = &*std::min_element(ctx->designs.begin(), ctx->designs.end(),
+                              [](const kf_ctx::Design &a, const kf_ctx::Design &b) { return a.used < b.used; });
+  }
+  slot->type = -1;  // invalid until the design succeeds
+  if (!slot->d_coef) {
+    if ((e = cudaMalloc(&slot->d_coef, sizeof(kf::Coef) * KF_MAX_SCALES)) != cudaSuccess)
+      return cuda_fail(ctx, e, "cudaMalloc(coef)");
   }
   const int nmax = nmax_for(type, order, kmax);
   if (nmax > ctx->dwork_nmax) {
@@ -117,16 +150,16 @@ int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S,
   if ((e = cudaMemcpyAsync(ctx->lambdas, scales, sizeof(double) * S, cudaMemcpyHostToDevice,
                            ctx->stream)) != cudaSuccess)
     return cuda_fail(ctx, e, "copy scales");
-  if (kf::launch_design(type, order, ctx->lambdas, S, kmax, ctx->coef, ctx->dwork, ctx->dwork_nmax,
+  if (kf::launch_design(type, order, ctx->lambdas, S, kmax, slot->d_coef, ctx->dwork, ctx->dwork_nmax,
                         ctx->stream))
     return cuda_fail(ctx, cudaGetLastError(), "design kernel launch");
-  ctx->h_coef.resize(S);
-  if ((e = cudaMemcpyAsync(ctx->h_coef.data(), ctx->coef, sizeof(kf::Coef) * S,
+  slot->h_coef.resize(S);
+  if ((e = cudaMemcpyAsync(slot->h_coef.data(), slot->d_coef, sizeof(kf::Coef) * S,
                            cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
     return cuda_fail(ctx, e, "copy design");
   if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "design");
   for (int s = 0; s < S; ++s) {
-    const kf::Coef &c = ctx->h_coef[s];
+    const kf::Coef &c = slot->h_coef[s];
     if (c.status == 1)
       return fail(ctx, KF_EINVAL, "design: invalid parameters for scale %g (type %d, order %d)",
                   scales[s], type, order);
@@ -135,12 +168,13 @@ int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S,
     if (!(std::fabs(c.dc_gain - 1.0) < 1e-6))
       return fail(ctx, KF_ECOND, "design for scale %g has dc gain %.9g", scales[s], c.dc_gain);
   }
-  ctx->design_valid = true;
-  ctx->d_type = type;
-  ctx->d_order = order;
-  ctx->d_kmax = kmax;
-  ctx->d_S = S;
-  std::copy(scales, scales + S, ctx->d_lam);
+  slot->type = type;
+  slot->order = order;
+  slot->kmax = kmax;
+  slot->S = S;
+  std::copy(scales, scales + S, slot->lam);
+  slot->used = ++ctx->tick;
+  ctx->cur = slot;
   return KF_OK;
 }
 
@@ -204,7 +238,10 @@ void kf_destroy(kf_ctx *ctx) {
   cudaFree(ctx->P);
   cudaFree(ctx->edge);
   cudaFree(ctx->carry);
-  cudaFree(ctx->coef);
+  for (auto &d : ctx->designs) cudaFree(d.d_coef);
+  cudaFree(ctx->sorted);
+  cudaFree(ctx->sort_work);
+  cudaFree(ctx->d_npass);
   cudaFree(ctx->lambdas);
   cudaFree(ctx->dwork);
   cudaFree(ctx->status);
@@ -226,11 +263,12 @@ int kf_design(int type, int order, double scale, kf_coeffs *out) {
   if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return fail(nullptr, KF_ENODEV, "no CUDA device");
   cudaGetDevice(&tmp.device);
   rc = ensure_design(&tmp, type, order, &scale, 1, 96);
-  cudaFree(tmp.coef);
+  kf::Coef c{};
+  if (!rc) c = tmp.cur->h_coef[0];
+  for (auto &d : tmp.designs) cudaFree(d.d_coef);
   cudaFree(tmp.lambdas);
   cudaFree(tmp.dwork);
   if (rc) return fail(nullptr, rc, "%s", tmp.err.c_str());
-  const kf::Coef &c = tmp.h_coef[0];
   std::memset(out, 0, sizeof *out);
   out->type = type;
   out->order = order;
@@ -301,8 +339,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   if (rc) return rc;
   int nstate = 0, kmax = 0;
   for (int s = 0; s < nscales; ++s) {
-    nstate = std::max(nstate, ctx->h_coef[s].K);
-    kmax = std::max(kmax, ctx->h_coef[s].K);
+    nstate = std::max(nstate, ctx->cur->h_coef[s].K);
+    kmax = std::max(kmax, ctx->cur->h_coef[s].K);
   }
   const int nf = (type == KF_IIR_BUTTERWORTH) ? 2 * nstate : nstate;
   if ((rc = grow(ctx, &ctx->P, &ctx->P_floats, (size_t)nscales * maxplane, "planes"))) return rc;
@@ -318,7 +356,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   if ((e = cudaMemsetAsync(ctx->status, 0, sizeof(kf::DevStatus), ctx->stream)) != cudaSuccess)
     return cuda_fail(ctx, e, "reset status");
   kf::BankArgs a;
-  a.coef = ctx->coef;
+  a.coef = ctx->cur->d_coef;
   a.S = nscales;
   a.type = type;
   a.nstate = nstate;
@@ -364,8 +402,13 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     if (lr) return cuda_fail(ctx, cudaGetLastError(), "filter-bank kernel launch");
   }
   ctx->have_result = true;
+  ctx->sorted_valid = false;
   ctx->last_threshold = opts.threshold;
   ctx->last_S = nscales;
+  ctx->last_nframes = nframes;
+  ctx->last_hmax = maxH;
+  ctx->last_wmax = 0;
+  for (int f = 0; f < nframes; ++f) ctx->last_wmax = std::max(ctx->last_wmax, (long)frames[f].width);
   return KF_OK;
 }
 
@@ -436,36 +479,54 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
                 "candidate list overflowed (%llu found); capacity raised, run the bank again",
                 (unsigned long long)st.count);
   }
-  std::vector<kf::Blob> h((size_t)st.count);
-  if (st.count) {
-    if ((e = cudaMemcpyAsync(h.data(), ctx->blobs, sizeof(kf::Blob) * st.count, cudaMemcpyDeviceToHost,
+  const long n = (long)st.count;
+  if (!ctx->sorted_valid || ctx->sorted_thr != threshold) {
+    ctx->sorted_n = 0;
+    if (n > 0) {
+      const size_t wb = kf::sort_workspace_bytes(ctx->blob_cap);
+      if (!ctx->sort_work || ctx->sort_work_bytes < wb) {
+        cudaFree(ctx->sort_work);
+        cudaFree(ctx->sorted);
+        ctx->sort_work = nullptr;
+        ctx->sorted = nullptr;
+        ctx->sort_work_bytes = 0;
+        if ((e = cudaMalloc(&ctx->sort_work, wb)) != cudaSuccess) return cuda_fail(ctx, e, "sort workspace");
+        if ((e = cudaMalloc(&ctx->sorted, sizeof(kf::Blob) * ctx->blob_cap)) != cudaSuccess)
+          return cuda_fail(ctx, e, "sorted blobs");
+        ctx->sort_work_bytes = wb;
+      }
+      if (!ctx->d_npass && (e = cudaMalloc(&ctx->d_npass, sizeof(unsigned))) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMalloc(npass)");
+      const unsigned long long span = (unsigned long long)ctx->last_nframes * ctx->last_S *
+                                      (unsigned long long)ctx->last_hmax * ctx->last_wmax;
+      int keybits = 0;
+      while (keybits < 64 && (span >> keybits) != 0) ++keybits;
+      kf::Prof none{};
+      if (kf::launch_sort(ctx->blobs, n, (float)threshold, ctx->last_S, ctx->last_hmax, ctx->last_wmax,
+                          keybits, ctx->sort_work, ctx->sorted, ctx->d_npass, &none, ctx->stream))
+        return cuda_fail(ctx, cudaGetLastError(), "sort launch");
+      unsigned np = 0;
+      if ((e = cudaMemcpyAsync(&np, ctx->d_npass, sizeof np, cudaMemcpyDeviceToHost, ctx->stream)) !=
+          cudaSuccess)
+        return cuda_fail(ctx, e, "read count");
+      if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sort");
+      ctx->sorted_n = np;
+    }
+    ctx->sorted_valid = true;
+    ctx->sorted_thr = threshold;
+  }
+  *count = (int64_t)ctx->sorted_n;
+  const int64_t ncopy = std::min<int64_t>(capacity, ctx->sorted_n);
+  if (ncopy > 0) {
+    static_assert(sizeof(kf_blob) == sizeof(kf::Blob), "record layout");
+    if ((e = cudaMemcpyAsync(out, ctx->sorted, sizeof(kf::Blob) * ncopy, cudaMemcpyDeviceToHost,
                              ctx->stream)) != cudaSuccess)
       return cuda_fail(ctx, e, "copy blobs");
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "copy blobs");
   }
-  std::vector<kf::Blob> keep;
-  keep.reserve(h.size());
-  for (const kf::Blob &b : h)
-    if (std::fabs((double)b.response) > threshold) keep.push_back(b);
-  std::sort(keep.begin(), keep.end(), [](const kf::Blob &a, const kf::Blob &b) {
-    if (a.frame != b.frame) return a.frame < b.frame;
-    if (a.scale != b.scale) return a.scale < b.scale;
-    if (a.y != b.y) return a.y < b.y;
-    return a.x < b.x;
-  });
-  *count = (int64_t)keep.size();
-  const int64_t n = std::min<int64_t>(capacity, (int64_t)keep.size());
-  for (int64_t i = 0; i < n; ++i) {
-    out[i].frame = keep[i].frame;
-    out[i].x = keep[i].x;
-    out[i].y = keep[i].y;
-    out[i].scale = keep[i].scale;
-    out[i].polarity = keep[i].polarity;
-    out[i].response = keep[i].response;
-  }
-  if ((int64_t)keep.size() > capacity)
+  if (ctx->sorted_n > capacity)
     return fail(ctx, KF_EOVERFLOW, "capacity %lld < %lld blobs", (long long)capacity,
-                (long long)keep.size());
+                (long long)ctx->sorted_n);
   return KF_OK;
 }
 

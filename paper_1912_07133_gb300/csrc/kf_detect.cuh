@@ -29,17 +29,29 @@ struct DetectArgs {
   float *resp;         // optional: R planes of this frame (S x H x W)
 };
 
-static __device__ __forceinline__ void emit_blob(const DetectArgs &a, int s, int y, int x, int pol, float v) {
-  unsigned long long idx = atomicAdd(&a.status->count, 1ull);
-  if (idx < (unsigned long long)a.cap) {
-    Blob b;
-    b.frame = a.frame;
-    b.x = x;
-    b.y = y;
-    b.scale = s;
-    b.polarity = pol;
-    b.response = v;
-    a.out[idx] = b;
+constexpr int TILE_CANDS = 256;  // candidates staged per tile before one global reservation
+
+struct TileList {
+  int n;
+  Blob rec[TILE_CANDS];
+};
+
+// Stage a candidate in the tile's list; when it is full, reserve globally.
+static __device__ __forceinline__ void emit_blob(const DetectArgs &a, TileList &tl, int s, int y, int x,
+                                                 int pol, float v) {
+  Blob b;
+  b.frame = a.frame;
+  b.x = x;
+  b.y = y;
+  b.scale = s;
+  b.polarity = pol;
+  b.response = v;
+  const int slot = atomicAdd(&tl.n, 1);
+  if (slot < TILE_CANDS) {
+    tl.rec[slot] = b;
+  } else {
+    const unsigned long long idx = atomicAdd(&a.status->count, 1ull);
+    if (idx < (unsigned long long)a.cap) a.out[idx] = b;
   }
 }
 
@@ -47,6 +59,9 @@ static __device__ __forceinline__ void emit_blob(const DetectArgs &a, int s, int
 // Must be called by all threads of the block (contains __syncthreads).
 static __device__ void detect_tile(const float *buf, float *red, const DetectArgs &a) {
   const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ TileList tl;
+  __shared__ unsigned long long s_base;
+  if (tid == 0) tl.n = 0;
   const int NP = a.NR * 32;
   float *mx = red, *mn = red + NP;
   unsigned char *amx = reinterpret_cast<unsigned char *>(red + 2 * NP);
@@ -99,7 +114,7 @@ static __device__ void detect_tile(const float *buf, float *red, const DetectArg
             const float a1 = pol * v, b1 = pol * vn;
             ok = (a1 > b1) || (a1 == b1 && (sn > s || (sn == s && after)));
           }
-        if (ok) emit_blob(a, s, y, x, pol, v);
+        if (ok) emit_blob(a, tl, s, y, x, pol, v);
       }
     } else {
       for (int s = 0; s < a.S; ++s) {
@@ -117,9 +132,17 @@ static __device__ void detect_tile(const float *buf, float *red, const DetectArg
               const bool earlier = t < s || (t == s && (di < 0 || (di == 0 && dl < 0)));
               ok = earlier ? (pol * v > pol * vn) : (pol * v >= pol * vn);
             }
-        if (ok) emit_blob(a, s, y, x, pol, v);
+        if (ok) emit_blob(a, tl, s, y, x, pol, v);
       }
     }
+  }
+  __syncthreads();
+  const int nloc = min(tl.n, TILE_CANDS);
+  if (tid == 0 && nloc > 0) s_base = atomicAdd(&a.status->count, (unsigned long long)nloc);
+  __syncthreads();
+  for (int i = tid; i < nloc; i += nt) {
+    const unsigned long long idx = s_base + i;
+    if (idx < (unsigned long long)a.cap) a.out[idx] = tl.rec[i];
   }
 }
 

@@ -24,9 +24,46 @@ namespace kf {
 
 namespace {
 
-constexpr int RSEG = 1024;  // outputs per row CTA
-constexpr int RNT = 256;    // threads per row CTA (4 outputs each)
-constexpr int CROWS = 64;   // output rows per column CTA (incl. 2 halo rows)
+constexpr int NOUT = 16;             // outputs per thread (register block)
+constexpr int TB = 8;                // taps per block of the inner loop
+constexpr int RNT = 128;             // threads per row CTA
+constexpr int RSEG = RNT * NOUT;     // outputs per row CTA (2048)
+constexpr int CNT = 128;             // threads per column CTA (4 warps x 32 columns)
+constexpr int CROWS = 4 * NOUT;      // output rows per column CTA (64, incl. 2 halo rows)
+
+// taps h[0..K] padded with zeros to a multiple of TB beyond K
+__device__ __forceinline__ void stage_taps(float *sh, const Coef &c, int K, int tid, int nt) {
+  const int KP = ((K + TB - 1) / TB) * TB;
+  for (int k = tid; k <= KP; k += nt) sh[k] = (k <= K) ? c.h[k] : 0.f;
+}
+
+// Symmetric FIR on a register block of NOUT consecutive outputs.
+// at(t) returns the input at offset t from the first output (t may be
+// negative); the window loads for taps [k0, k0+TB) are statically indexed.
+template <class At>
+__device__ __forceinline__ void fir_block(const float *sh, int K, At at, float (&acc)[NOUT]) {
+  const float h0 = sh[0];
+#pragma unroll
+  for (int j = 0; j < NOUT; ++j) acc[j] = h0 * at(j);
+  for (int k0 = 1; k0 <= K; k0 += TB) {
+    float A[NOUT + TB - 1], B[NOUT + TB - 1], hk[TB];
+#pragma unroll
+    for (int u = 0; u < TB; ++u) hk[u] = sh[k0 + u];
+    // A[m] = x(m - k0 - TB + 1): left operands x(j - k) = A[j - u + TB - 1]
+    // B[m] = x(k0 + m):          right operands x(j + k) = B[j + u]
+#pragma unroll
+    for (int m = 0; m < NOUT + TB - 1; ++m) {
+      A[m] = at(m - k0 - TB + 1);
+      B[m] = at(k0 + m);
+    }
+#pragma unroll
+    for (int u = 0; u < TB; ++u)
+#pragma unroll
+      for (int j = 0; j < NOUT; ++j) acc[j] = fmaf(hk[u], A[j - u + TB - 1] + B[j + u], acc[j]);
+  }
+}
+
+__host__ __device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
 
 template <bool EDGE>
 __global__ void __launch_bounds__(RNT) k_rowfir(const float *__restrict__ X, long xpitch, int H, int W,
@@ -36,18 +73,19 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const float *__restrict__ X, lon
   const int tid = threadIdx.x;
   const int y = EDGE ? (blockIdx.y == 0 ? 0 : H - 1) : blockIdx.y;
   const int xs = blockIdx.x * RSEG;
-  // L on [xs - kmax - 1, xs + RSEG + kmax + 7): the sliding window reads one
-  // element past the taps on each side in its last step
-  const int n = RSEG + 2 * kmax + 8;
-  float *sL = sm;
-  float *sh = sm + n;
+  // L on [xs - G, xs + RSEG + G), G = kmax + TB: the 8-tap blocks read up to
+  // TB - 1 elements past the last tap
+  const int G = kmax + TB;
+  const int n = RSEG + 2 * G;
+  float *sL = sm;                       // padded: element j at pad16(j)
+  float *sh = sm + pad16(n) + 1;
   const float *rm = X + (long)max(y - 1, 0) * xpitch;
   const float *r0 = X + (long)y * xpitch;
   const float *rp = X + (long)min(y + 1, H - 1) * xpitch;
   const float vlo = __ldg(rp) - 2.f * __ldg(r0) + __ldg(rm);
   const float vhi = __ldg(rp + W - 1) - 2.f * __ldg(r0 + W - 1) + __ldg(rm + W - 1);
   for (int j = tid; j < n; j += RNT) {
-    const int e = xs - kmax - 1 + j;
+    const int e = xs - G + j;
     float v;
     if (e < 0) v = EDGE ? 0.f : vlo;
     else if (e >= W) v = EDGE ? 0.f : vhi;
@@ -56,56 +94,43 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const float *__restrict__ X, lon
       const float u = __ldg(r0 + min(e + 1, W - 1)) - 2.f * c0 + __ldg(r0 + max(e - 1, 0));
       v = EDGE ? u : u + (__ldg(rp + e) - 2.f * c0 + __ldg(rm + e));
     }
-    sL[j] = v;
+    sL[pad16(j)] = v;
   }
+  const int base = G + NOUT * tid;  // local index of this thread's first output
   for (int s = 0; s < S; ++s) {
     const Coef &c = coef[s];
     const int K = c.K;
     __syncthreads();
-    for (int k = tid; k <= K; k += RNT) sh[k] = c.h[k];
+    stage_taps(sh, c, K, tid, RNT);
     __syncthreads();
-    const int xl = 4 * tid;             // local output index
-    const float *base = sL + kmax + 1 + xl;  // L at output xl
-    float acc[4], lw[4], rw[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      acc[j] = sh[0] * base[j];
-      lw[j] = base[j - 1];
-      rw[j] = base[j + 1];
-    }
-    for (int k = 1; k <= K; ++k) {
-      const float hk = sh[k];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] = fmaf(hk, lw[j] + rw[j], acc[j]);
-      // slide: left window one step further left, right window one step right
-      lw[3] = lw[2];
-      lw[2] = lw[1];
-      lw[1] = lw[0];
-      lw[0] = base[-k - 1];
-      rw[0] = rw[1];
-      rw[1] = rw[2];
-      rw[2] = rw[3];
-      rw[3] = base[3 + k + 1];
-    }
+    float acc[NOUT];
+    fir_block(sh, K, [&](int t) { return sL[pad16(base + t)]; }, acc);
     float *dst = EDGE ? edge + ((long)s * 2 + blockIdx.y) * PW : P + (long)s * H * PW + (long)y * PW;
+    const int x0 = xs + NOUT * tid;
+    if (x0 + NOUT <= W) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int e = xs + xl + j;
-      if (e < W) dst[e] = acc[j];
+      for (int j = 0; j < NOUT; j += 4)
+        *reinterpret_cast<float4 *>(dst + x0 + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < NOUT; ++j)
+        if (x0 + j < W) dst[x0 + j] = acc[j];
     }
   }
 }
 
-__global__ void __launch_bounds__(256) k_colfir(const float *__restrict__ P, long PW, int H, int W,
+__global__ void __launch_bounds__(CNT) k_colfir(const float *__restrict__ P, long PW, int H, int W,
                                                 const float *__restrict__ edge,
                                                 const Coef *__restrict__ coef, int S, int kmax,
                                                 DetectArgs da) {
   extern __shared__ float sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int NIN = CROWS + 2 * kmax + 2;
+  const int G = kmax + TB;
+  const int NIN = CROWS + 2 * G;
   float *in = sm;                               // [NIN][32]
   float *buf = sm + (long)NIN * 32;             // [S][CROWS][32]
   float *red = buf + (long)S * CROWS * 32;
+  float *sh = red + CROWS * 32 * 2 + CROWS * 32 * 2 / 4;
   const int x = blockIdx.x * TW - 1 + lane;
   const int xv = min(max(x, 0), W - 1);
   const int r0 = blockIdx.y * (CROWS - 2) - 1;  // frame row of output row 0
@@ -115,36 +140,19 @@ __global__ void __launch_bounds__(256) k_colfir(const float *__restrict__ P, lon
     const float *Pc = P + (long)s * H * PW + xv;
     const float top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
     __syncthreads();
-    // in[j] = input row r0 - K - 1 + j, j < CROWS + 2K + 2 (the sliding window
-    // reads one row past the taps on each side in its last step)
-    for (int j = warp; j < CROWS + 2 * K + 2; j += 8) {
-      const int r = r0 - K - 1 + j;
+    stage_taps(sh, c, K, threadIdx.x, CNT);
+    // in[j] = input row r0 - G + j
+    for (int j = warp; j < NIN; j += CNT / 32) {
+      const int r = r0 - G + j;
       in[j * 32 + lane] = r < 0 ? top : (r >= H ? bot : __ldg(Pc + (long)r * PW));
     }
     __syncthreads();
-    const float *col = in + lane + (K + 1 + 8 * warp) * 32;  // output row 8*warp
-    float acc[8], lw[8], rw[8];
-    const float h0 = c.h[0];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      acc[j] = h0 * col[j * 32];
-      lw[j] = col[(j - 1) * 32];
-      rw[j] = col[(j + 1) * 32];
-    }
-    for (int k = 1; k <= K; ++k) {
-      const float hk = __ldg(&c.h[k]);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) acc[j] = fmaf(hk, lw[j] + rw[j], acc[j]);
-#pragma unroll
-      for (int j = 7; j > 0; --j) lw[j] = lw[j - 1];
-      lw[0] = col[(-k - 1) * 32];
-#pragma unroll
-      for (int j = 0; j < 7; ++j) rw[j] = rw[j + 1];
-      rw[7] = col[(7 + k + 1) * 32];
-    }
+    const float *col = in + lane + (G + NOUT * warp) * 32;  // output row NOUT*warp
+    float acc[NOUT];
+    fir_block(sh, K, [&](int t) { return col[t * 32]; }, acc);
     const float ms2 = -c.sigma2;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) buf[((long)s * CROWS + 8 * warp + j) * 32 + lane] = ms2 * acc[j];
+    for (int j = 0; j < NOUT; ++j) buf[((long)s * CROWS + NOUT * warp + j) * 32 + lane] = ms2 * acc[j];
   }
   __syncthreads();
   DetectArgs a = da;
@@ -166,7 +174,9 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
     attr = true;
   }
   const int kmax = a.kmax;
-  const size_t rsm = (size_t)(RSEG + 2 * kmax + 8 + kmax + 1) * sizeof(float);
+  const int G = kmax + TB;
+  const int KP = ((kmax + TB - 1) / TB) * TB;
+  const size_t rsm = (size_t)(pad16(RSEG + 2 * G) + 1 + KP + 1) * sizeof(float);
   dim3 gr((g.W + RSEG - 1) / RSEG, g.H);
   a.prof->begin("fir_row", st);
   k_rowfir<false><<<gr, RNT, rsm, st>>>(g.X, g.xpitch, g.H, g.W, a.coef, a.S, kmax, a.P, g.PW, a.edge);
@@ -186,12 +196,13 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   da.cap = a.cap;
   da.status = a.status;
   da.resp = a.responses ? a.responses + g.resp_off : nullptr;
-  const size_t csm = ((size_t)(CROWS + 2 * kmax + 2) * 32 + (size_t)a.S * CROWS * 32 +
-                      (size_t)CROWS * 32 * 2) * sizeof(float) + (size_t)CROWS * 32 * 2;
+  // in + buf + detector scratch (2 float planes + 2 byte planes) + taps
+  const size_t csm = ((size_t)(CROWS + 2 * G) * 32 + (size_t)a.S * CROWS * 32 + (size_t)CROWS * 32 * 2 +
+                      (size_t)CROWS * 32 * 2 / 4 + KP + 1) * sizeof(float);
   if (csm > 220 * 1024) return -1;
   dim3 gc((g.W + TW - 1) / TW, (g.H + CROWS - 3) / (CROWS - 2));
   a.prof->begin("fir_coldet", st);
-  k_colfir<<<gc, 256, csm, st>>>(a.P, g.PW, g.H, g.W, a.edge, a.coef, a.S, kmax, da);
+  k_colfir<<<gc, CNT, csm, st>>>(a.P, g.PW, g.H, g.W, a.edge, a.coef, a.S, kmax, da);
   a.prof->end(st);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -62,4 +62,9 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st);
 // workspace needs (bytes) of one frame
 size_t iir_carry_floats(int H, long PW, int S, int nf);
 
+// candidate ordering (kf_sort.cu)
+size_t sort_workspace_bytes(long n);
+int launch_sort(const Blob *blobs, long n, float thr, int nscales, long hmax, long wmax, int keybits,
+                void *work, Blob *out, unsigned *d_npass, Prof *prof, cudaStream_t st);
+
 }  // namespace kf

@@ -192,16 +192,27 @@ def kf_filter_bank(ctx: int, frames, scales, ftype: int, order: int, opts: kf_ba
                                  ctypes.byref(opts)), ctx)
 
 
-def kf_detect_blobs(ctx: int, threshold: float, capacity: int = 1 << 20) -> np.ndarray:
-    """Blob list of the last bank call, sorted by (frame, scale, y, x)."""
-    out = np.zeros(capacity, dtype=BLOB_DTYPE)
+def kf_detect_blobs(ctx: int, threshold: float, capacity: int = None) -> np.ndarray:
+    """Blob list of the last bank call, sorted by (frame, scale, y, x).
+
+    The library orders the list on the GPU and keeps it; the first call (with
+    no output space) returns the count, the second copies exactly that many."""
+    L = load()
     n = ctypes.c_int64(0)
-    rc = load().kf_detect_blobs(ctx, float(threshold),
-                                out.ctypes.data_as(ctypes.POINTER(kf_blob)), capacity, ctypes.byref(n))
+    if capacity is None:
+        rc = L.kf_detect_blobs(ctx, float(threshold), None, 0, ctypes.byref(n))
+        if rc not in (KF_OK, KF_EOVERFLOW):
+            _check(rc, ctx)
+        capacity = int(n.value)
+    out = np.empty(capacity, dtype=BLOB_DTYPE)
+    if capacity == 0:
+        return out
+    rc = L.kf_detect_blobs(ctx, float(threshold), out.ctypes.data_as(ctypes.POINTER(kf_blob)), capacity,
+                           ctypes.byref(n))
     if rc == KF_EOVERFLOW and n.value > capacity:
         return kf_detect_blobs(ctx, threshold, int(n.value))
     _check(rc, ctx)
-    return out[: n.value].copy()
+    return out[: n.value]
 
 
 def kf_kernel_times(ctx: int) -> dict:
@@ -240,7 +251,7 @@ class Bank:
     def kernel_times(self) -> dict:
         return kf_kernel_times(self.ctx)
 
-    def blobs(self, threshold=None, capacity=1 << 20) -> np.ndarray:
+    def blobs(self, threshold=None, capacity=None) -> np.ndarray:
         return kf_detect_blobs(self.ctx, self.threshold if threshold is None else threshold, capacity)
 
     def close(self):
