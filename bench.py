@@ -183,25 +183,26 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         step(False)
-    # --- device-resident timed region ---------------------------------------
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    ktimes, nblobs = {}, 0
-    barrier()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(stream)
-            n, times = step(True)
-            ev[i][1].record(stream)
-            nblobs = n
-            for k, (nl, ms) in times.items():
-                a, b = ktimes.get(k, (0, 0.0))
-                ktimes[k] = (a + nl, b + ms)
+
+    def timed(profile):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        kt, nb = {}, 0
         barrier()
-    clocks = clk.summary()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                nb, times = step(profile)
+                ev[i][1].record(stream)
+                for k, (nl, ms) in times.items():
+                    a, b = kt.get(k, (0, 0.0))
+                    kt[k] = (a + nl, b + ms)
+            barrier()
+        return sum(a.elapsed_time(b) for a, b in ev), kt, nb, clk.summary()
+
+    # --- device-resident timed region (no profiling events) ------------------
+    total_ms, _, nblobs, clocks = timed(False)
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -209,6 +210,8 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     pix_scales = len(BANKS) * H * W * len(SCALES)
     value = world * pix_scales / (ms_per_step * 1e-3) / 1e6
+    # --- the same steps again with CUDA events around every kernel ------------
+    _, ktimes, _, _ = timed(True)
 
     # --- end to end: host frame in pinned memory, copies inside the timed region
     host = torch.from_numpy(img).pin_memory()

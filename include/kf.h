@@ -39,6 +39,9 @@ extern "C" {
 #define KF_ETIMEOUT -5   /* a bounded device-side wait gave up                  */
 #define KF_EOVERFLOW -6  /* output capacity too small; *count holds the need    */
 #define KF_ENODEV -7     /* no usable CUDA device                               */
+#define KF_ERERUN -8     /* the context's candidate list overflowed during the
+                            last bank call; its capacity has been raised: run
+                            kf_filter_bank again (*count holds the need)       */
 
 /* ---- enumerations -------------------------------------------------------- */
 #define KF_IIR_REPEATED_POLE 0 /* Filter D, Sec. 4.3 / Table IV                  */
@@ -182,7 +185,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes,
  * *count (host) receives the number of such blobs.  threshold must be >= the
  * bank's opts->threshold.  Synchronises the context stream.
  * Errors: KF_EINVAL, KF_EOVERFLOW (capacity < *count; the first `capacity`
- * blobs are written), KF_ECUDA. */
+ * blobs are written), KF_ERERUN (the device-side candidate list of the last
+ * call overflowed; capacity raised, run the bank again), KF_ECUDA. */
 int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out,
                     int64_t capacity, int64_t *count);
 

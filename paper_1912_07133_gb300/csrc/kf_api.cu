@@ -475,7 +475,7 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
     }
     ctx->blob_cap = ncap;
     ctx->have_result = false;
-    return fail(ctx, KF_EOVERFLOW,
+    return fail(ctx, KF_ERERUN,
                 "candidate list overflowed (%llu found); capacity raised, run the bank again",
                 (unsigned long long)st.count);
   }

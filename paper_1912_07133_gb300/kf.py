@@ -24,6 +24,7 @@ KF_ECUDA = -4
 KF_ETIMEOUT = -5
 KF_EOVERFLOW = -6
 KF_ENODEV = -7
+KF_ERERUN = -8
 
 KF_IIR_REPEATED_POLE = 0
 KF_IIR_BUTTERWORTH = 1

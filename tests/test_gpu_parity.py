@@ -207,7 +207,7 @@ def test_candidate_overflow_raises_capacity():
 
 
 def test_device_candidate_list_overflow_grows_capacity():
-    """More candidates than the context's device list: KF_EOVERFLOW with the
+    """More candidates than the context's device list: KF_ERERUN with the
     count, capacity raised; the next run returns the complete ordered list."""
     import torch
     from paper_1912_07133_gb300 import kf
@@ -217,7 +217,7 @@ def test_device_candidate_list_overflow_grows_capacity():
     bank.run([x], [2.0, 3.0], kf.KF_IIR_REPEATED_POLE, 3, threshold=0.0)
     with pytest.raises(kf.KfError) as e:
         bank.blobs()
-    assert e.value.code == kf.KF_EOVERFLOW
+    assert e.value.code == kf.KF_ERERUN
     bank.run([x], [2.0, 3.0], kf.KF_IIR_REPEATED_POLE, 3, threshold=0.0)
     b = bank.blobs()
     assert len(b) > (1 << 20)
