@@ -197,6 +197,40 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out,
  * Errors: KF_EINVAL (NULL arguments, no bank call yet), KF_ECUDA. */
 int kf_kernel_times(kf_ctx *ctx, kf_kernel_time *out, int cap, int *n);
 
+/* Size of the static scratch that kf_responses_noalloc uses (MiB). */
+#define KF_NOALLOC_SCRATCH_MB 32
+
+/* kf_responses_noalloc: the response planes R of one frame through a
+ * recursive bank, with no device allocation by the library.  The paper has
+ * no counterpart to this entry point; it exists for callers that cannot call
+ * cudaMalloc -- programs whose device memory is owned by a host framework's
+ * pool allocator, and real-time loops that forbid allocation after start-up
+ * because cudaMalloc can synchronise the device and can fail under memory
+ * pressure.  The caller passes the frame and the output; every intermediate
+ * lives in one static device array of KF_NOALLOC_SCRATCH_MB MiB that each GPU
+ * which loads the library holds until the process exits.
+ *   frame      one f32 frame descriptor (device data), width <= 8192
+ *   scales     host array of nscales blob radii lambda (px), 1..16
+ *   type       KF_IIR_REPEATED_POLE (order 2..6) or KF_IIR_BUTTERWORTH
+ *              (order 1..6); the FIR bank is not offered here
+ *   responses  device output, nscales*H*W floats: R at (x, y) of scale s is
+ *              responses[(s*H + y)*W + x] (same values as opts->responses of
+ *              kf_filter_bank for this frame)
+ *   cuda_stream cudaStream_t for all work (NULL = legacy default stream)
+ * The frame's planes, edge rows and column carries must fit the scratch;
+ * larger frames (roughly more than 4M pixel-scales) are rejected with
+ * KF_EINVAL and a message naming the sizes (kf_last_error(NULL)).
+ * The first call on a device looks up the device address of the scratch
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the one scratch array and
+ * finds the previous call's contents there: the library clears what must
+ * start at zero, but calls that overlap on the GPU (e.g. on two streams)
+ * race -- serialise them.  The designs are checked on the host, so the call
+ * synchronises the stream once before the filter kernels are enqueued.
+ * Errors: KF_EINVAL, KF_ECOND, KF_ENODEV, KF_ECUDA. */
+int kf_responses_noalloc(const kf_frame *frame, const double *scales, int nscales, int type,
+                         int order, float *responses, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -191,6 +191,11 @@ int check_type_order(kf_ctx *ctx, int type, int order) {
 
 }  // namespace
 
+namespace kf {
+// message of a context-less failure, as read by kf_last_error(NULL)
+void set_global_error(const char *msg) { g_err = msg; }
+}  // namespace kf
+
 extern "C" {
 
 int kf_bank_opts_default(kf_bank_opts *o) {

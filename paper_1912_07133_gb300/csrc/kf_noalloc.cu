@@ -1,0 +1,161 @@
+// kf_noalloc.cu -- response planes of the recursive banks without any device
+// allocation (kf_responses_noalloc in include/kf.h).
+//
+// Who needs this: programs whose device memory belongs to a host framework's
+// pool allocator, or real-time loops that forbid cudaMalloc after start-up
+// because it can synchronise the device and can fail under memory pressure.
+// They pass the frame and the output buffer; every intermediate (designs,
+// one-sided planes, edge rows, column carries, status word) lives in the one
+// file-scope device array below, which each GPU that loads the library keeps
+// until the process exits.  The paper has no counterpart to this entry point.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "kf.h"
+#include "kf_common.cuh"
+#include "kf_internal.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)KF_NOALLOC_SCRATCH_MB << 20;
+
+// The shared scratch.  Host code must not use this name as a pointer: it is a
+// host-side stand-in for the device symbol; cudaGetSymbolAddress gives the
+// device address.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void *g_addr[kMaxDevices];  // device address of g_scratch, per device (set-up)
+thread_local char g_msg[256];
+
+}  // namespace
+
+namespace kf {
+void set_global_error(const char *msg);
+}
+
+namespace {
+
+int nofail(int code, const char *msg) {
+  std::snprintf(g_msg, sizeof g_msg, "kf_responses_noalloc: %s", msg);
+  kf::set_global_error(g_msg);
+  return code;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales, int nscales, int type,
+                                    int order, float *responses, void *cuda_stream) {
+  g_msg[0] = 0;
+  if (!frame || !scales || !responses) return nofail(KF_EINVAL, "NULL argument");
+  if (type != KF_IIR_REPEATED_POLE && type != KF_IIR_BUTTERWORTH)
+    return nofail(KF_EINVAL, "only the recursive banks (repeated pole, Butterworth) are supported");
+  if (type == KF_IIR_REPEATED_POLE && (order < 2 || order > 6))
+    return nofail(KF_EINVAL, "repeated-pole order must be 2..6");
+  if (type == KF_IIR_BUTTERWORTH && (order < 1 || order > 6))
+    return nofail(KF_EINVAL, "Butterworth order must be 1..6");
+  if (nscales < 1 || nscales > KF_MAX_SCALES) return nofail(KF_EINVAL, "nscales must be 1..16");
+  for (int s = 0; s < nscales; ++s)
+    if (!(scales[s] > 0.0) || !std::isfinite(scales[s])) return nofail(KF_EINVAL, "scales must be > 0");
+  if (!frame->data || frame->dtype != KF_DTYPE_F32 || frame->width < 1 || frame->height < 1 ||
+      frame->width > 8192 || frame->pitch < frame->width ||
+      (frame->value_scale != 0.0f && frame->value_scale != 1.0f))
+    return nofail(KF_EINVAL, "frame must be f32, 1 <= width <= 8192, pitch >= width");
+  const int W = frame->width, H = frame->height, S = nscales;
+  const long PW = ((long)W + 31) / 32 * 32;
+  // layout of the scratch: coefficients | scales | status | planes | edges | carries
+  const int nstate_max = 6;  // chain length (repeated pole) or 2 x modes (Butterworth)
+  const size_t b_coef = align256(sizeof(kf::Coef) * KF_MAX_SCALES);
+  const size_t b_lam = align256(sizeof(double) * KF_MAX_SCALES);
+  const size_t b_stat = align256(sizeof(kf::DevStatus));
+  const size_t b_P = align256(sizeof(float) * (size_t)S * H * PW);
+  const size_t b_edge = align256(sizeof(float) * (size_t)S * 2 * PW);
+  const size_t b_carry = align256(sizeof(float) * kf::iir_carry_floats(H, PW, S, nstate_max));
+  const size_t need = b_coef + b_lam + b_stat + b_P + b_edge + b_carry;
+  if (need > kScratchBytes) {
+    char m[200];
+    std::snprintf(m, sizeof m, "%d scales of %dx%d need %zu bytes of scratch; the limit is %zu", S, W, H,
+                  need, kScratchBytes);
+    return nofail(KF_EINVAL, m);
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return nofail(KF_ENODEV, "no usable CUDA device");
+  // set-up, once per device, with that device current
+  if (!g_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) return nofail(KF_ECUDA, cudaGetErrorString(e));
+    g_addr[dev] = p;
+  }
+  unsigned char *base = static_cast<unsigned char *>(g_addr[dev]);
+  auto *coef = reinterpret_cast<kf::Coef *>(base);
+  auto *lam = reinterpret_cast<double *>(base + b_coef);
+  auto *status = reinterpret_cast<kf::DevStatus *>(base + b_coef + b_lam);
+  auto *P = reinterpret_cast<float *>(base + b_coef + b_lam + b_stat);
+  auto *edge = reinterpret_cast<float *>(base + b_coef + b_lam + b_stat + b_P);
+  auto *carry = reinterpret_cast<float *>(base + b_coef + b_lam + b_stat + b_P + b_edge);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e;
+  // FP64 designs into the scratch; the host checks them (stack copy, no allocation)
+  if ((e = cudaMemcpyAsync(lam, scales, sizeof(double) * S, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return nofail(KF_ECUDA, cudaGetErrorString(e));
+  if (kf::launch_design(type, order, lam, S, 96, coef, nullptr, 1, st))
+    return nofail(KF_ECUDA, "design kernel launch failed");
+  struct Check {
+    int status, K;
+    double dc;
+  } chk[KF_MAX_SCALES];
+  for (int s = 0; s < S; ++s) {
+    if ((e = cudaMemcpyAsync(&chk[s].status, &coef[s].status, sizeof(int), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(&chk[s].K, &coef[s].K, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&chk[s].dc, &coef[s].dc_gain, sizeof(double), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess)
+      return nofail(KF_ECUDA, cudaGetErrorString(e));
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return nofail(KF_ECUDA, cudaGetErrorString(e));
+  int nstate = 0;
+  for (int s = 0; s < S; ++s) {
+    if (chk[s].status == 1) return nofail(KF_EINVAL, "invalid design parameters");
+    if (chk[s].status != 0 || !(std::fabs(chk[s].dc - 1.0) < 1e-6)) return nofail(KF_ECOND, "design failed");
+    nstate = chk[s].K > nstate ? chk[s].K : nstate;
+  }
+  // the status word must start at zero; everything else is written before it is read
+  if ((e = cudaMemsetAsync(status, 0, sizeof(kf::DevStatus), st)) != cudaSuccess)
+    return nofail(KF_ECUDA, cudaGetErrorString(e));
+  kf::Prof prof{};
+  kf::BankArgs a;
+  a.coef = coef;
+  a.S = S;
+  a.type = type;
+  a.nstate = nstate;
+  a.kmax = 0;
+  a.threshold = INFINITY;  // responses only: no candidates
+  a.neigh = KF_NEIGH_ALL_SCALES;
+  a.P = P;
+  a.edge = edge;
+  a.carry = carry;
+  a.blobs = nullptr;
+  a.cap = 0;
+  a.status = status;
+  a.responses = responses;
+  a.prof = &prof;
+  kf::FrameGeom g;
+  g.X = static_cast<const float *>(frame->data);
+  g.xpitch = frame->pitch;
+  g.H = H;
+  g.W = W;
+  g.PW = PW;
+  g.frame = 0;
+  g.resp_off = 0;
+  const int rc = kf::launch_iir_frame(g, a, st);
+  if (rc == -2) return nofail(KF_EINVAL, "no kernel instance for this order");
+  if (rc) return nofail(KF_ECUDA, cudaGetErrorString(cudaGetLastError()));
+  return KF_OK;
+}

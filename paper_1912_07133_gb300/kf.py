@@ -45,7 +45,8 @@ KF_MAX_ORDER = 8
 KF_MAX_FIR_K = 160
 
 ENTRY_POINTS = ("kf_bank_opts_default", "kf_create", "kf_destroy", "kf_last_error", "kf_design",
-                "kf_filter_bank", "kf_detect_blobs", "kf_kernel_times")
+                "kf_filter_bank", "kf_detect_blobs", "kf_kernel_times", "kf_responses_noalloc")
+KF_NOALLOC_SCRATCH_MB = 32
 
 
 class kf_coeffs(ctypes.Structure):
@@ -118,6 +119,8 @@ def load(path: str = LIB_PATH):
     L.kf_detect_blobs.argtypes = [vp, dbl, ctypes.POINTER(kf_blob), i64, ctypes.POINTER(i64)]
     L.kf_kernel_times.restype = i32
     L.kf_kernel_times.argtypes = [vp, ctypes.POINTER(kf_kernel_time), i32, ctypes.POINTER(i32)]
+    L.kf_responses_noalloc.restype = i32
+    L.kf_responses_noalloc.argtypes = [ctypes.POINTER(kf_frame), ctypes.POINTER(dbl), i32, i32, i32, vp, vp]
     _lib = L
     return L
 
@@ -222,6 +225,24 @@ def kf_kernel_times(ctx: int) -> dict:
     n = ctypes.c_int(0)
     _check(load().kf_kernel_times(ctx, out, 64, ctypes.byref(n)), ctx)
     return {out[i].name.decode(): (out[i].launches, out[i].ms) for i in range(min(n.value, 64))}
+
+
+def kf_responses_noalloc(frame, scales, ftype: int, order: int, responses, stream=None) -> None:
+    """Response planes of one frame without any device allocation by the
+    library (for callers whose device memory is owned by another allocator or
+    whose loops may not allocate); see include/kf.h for the size limit."""
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    if not responses.is_cuda or responses.dtype != torch.float32 or not responses.is_contiguous():
+        raise ValueError("responses must be a contiguous float32 CUDA tensor")
+    if responses.numel() < len(scales) * frame.shape[0] * frame.shape[1]:
+        raise ValueError("responses is too small")
+    d = _frame_desc(frame)
+    sc = (ctypes.c_double * len(scales))(*[float(s) for s in scales])
+    _check(load().kf_responses_noalloc(ctypes.byref(d), sc, len(scales), ftype, order, responses.data_ptr(),
+                                       ctypes.c_void_p(stream)))
 
 
 class Bank:
