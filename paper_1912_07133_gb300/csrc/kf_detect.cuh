@@ -27,6 +27,8 @@ struct DetectArgs {
   long cap;
   DevStatus *status;
   float *resp;         // optional: R planes of this frame (S x H x W)
+  int ld = 32;         // row stride of the response buffer (floats)
+  int coff = 0;        // column of lane 0 inside a buffer row
 };
 
 constexpr int TILE_CANDS = 256;  // candidates staged per tile before one global reservation
@@ -35,6 +37,10 @@ struct TileList {
   int n;
   Blob rec[TILE_CANDS];
 };
+
+// one staged list per CTA (file-scope shared: every kernel gets its own)
+static __shared__ TileList g_tl;
+static __shared__ unsigned long long g_tl_base;
 
 // Stage a candidate in the tile's list; when it is full, reserve globally.
 static __device__ __forceinline__ void emit_blob(const DetectArgs &a, TileList &tl, int s, int y, int x,
@@ -55,35 +61,18 @@ static __device__ __forceinline__ void emit_blob(const DetectArgs &a, TileList &
   }
 }
 
-// buf: [S][NR][32] responses; red: scratch of NR*32*(2 floats + 2 bytes).
+// Spatial part of the all-scales test.  mx/mn: per-pixel maximum/minimum of R
+// over the scales of an NR x 32 tile (+-inf outside the frame), amx/amn: the
+// first scale attaining them.  A pixel's candidate is its first argmax
+// (argmin); it must beat the 8 neighbours' extremes with the tie rule.
+// Candidates are staged in shared memory and reserved globally once per tile.
 // Must be called by all threads of the block (contains __syncthreads).
-static __device__ void detect_tile(const float *buf, float *red, const DetectArgs &a) {
+static __device__ void spatial_detect(const float *mx, const float *mn, const unsigned char *amx,
+                                      const unsigned char *amn, const DetectArgs &a) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  __shared__ TileList tl;
-  __shared__ unsigned long long s_base;
+  TileList &tl = g_tl;
+  unsigned long long &s_base = g_tl_base;
   if (tid == 0) tl.n = 0;
-  const int NP = a.NR * 32;
-  float *mx = red, *mn = red + NP;
-  unsigned char *amx = reinterpret_cast<unsigned char *>(red + 2 * NP);
-  unsigned char *amn = amx + NP;
-  // per-pixel extremes over scales (first argmax / argmin), out-of-frame -> +-inf
-  for (int p = tid; p < NP; p += nt) {
-    const int i = p >> 5, lane = p & 31;
-    const int y = a.r0 + i, x = a.x0 + lane;
-    float vmax = -CUDART_INF_F, vmin = CUDART_INF_F;
-    int smax = a.S, smin = a.S;
-    if (y >= 0 && y < a.H && x >= 0 && x < a.W) {
-      for (int s = 0; s < a.S; ++s) {
-        const float v = buf[(s * a.NR + i) * 32 + lane];
-        if (v > vmax) vmax = v, smax = s;
-        if (v < vmin) vmin = v, smin = s;
-      }
-    }
-    mx[p] = vmax;
-    mn[p] = vmin;
-    amx[p] = (unsigned char)smax;
-    amn[p] = (unsigned char)smin;
-  }
   __syncthreads();
   const int NI = (a.NR - 2) * 30;  // interior pixels
   for (int q = tid; q < NI; q += nt) {
@@ -91,49 +80,102 @@ static __device__ void detect_tile(const float *buf, float *red, const DetectArg
     const int y = a.r0 + i, x = a.x0 + lane;
     if (y < 0 || y >= a.H || x < 0 || x >= a.W) continue;
     const int p = i * 32 + lane;
-    if (a.resp) {
-      const long plane = (long)a.H * a.W;
-      for (int s = 0; s < a.S; ++s)
-        a.resp[s * plane + (long)y * a.W + x] = buf[(s * a.NR + i) * 32 + lane];
+    for (int pol = 1; pol >= -1; pol -= 2) {
+      if (pol == -1 && !a.dark) break;
+      const float v = (pol == 1) ? mx[p] : mn[p];
+      const int s = (pol == 1) ? amx[p] : amn[p];
+      if (!(pol * v > a.thr)) continue;
+      bool ok = true;
+      for (int di = -1; di <= 1 && ok; ++di)
+        for (int dl = -1; dl <= 1 && ok; ++dl) {
+          if (di == 0 && dl == 0) continue;
+          const int pn = p + di * 32 + dl;
+          const float vn = (pol == 1) ? mx[pn] : mn[pn];
+          const int sn = (pol == 1) ? amx[pn] : amn[pn];
+          const bool after = di > 0 || (di == 0 && dl > 0);
+          const float a1 = pol * v, b1 = pol * vn;
+          ok = (a1 > b1) || (a1 == b1 && (sn > s || (sn == s && after)));
+        }
+      if (ok) emit_blob(a, tl, s, y, x, pol, v);
     }
-    if (a.neigh == 0) {
-      // bright: the own pixel's first argmax over scales competes spatially
-      for (int pol = 1; pol >= -1; pol -= 2) {
-        if (pol == -1 && !a.dark) break;
-        const float v = (pol == 1) ? mx[p] : mn[p];
-        const int s = (pol == 1) ? amx[p] : amn[p];
-        if (!(pol * v > a.thr)) continue;
-        bool ok = true;
+  }
+  __syncthreads();
+  const int nloc = min(tl.n, TILE_CANDS);
+  if (tid == 0 && nloc > 0) s_base = atomicAdd(&a.status->count, (unsigned long long)nloc);
+  __syncthreads();
+  for (int i = tid; i < nloc; i += nt) {
+    const unsigned long long idx = s_base + i;
+    if (idx < (unsigned long long)a.cap) a.out[idx] = tl.rec[i];
+  }
+}
+
+// buf: [S][NR][32] responses; red: scratch of NR*32*(2 floats + 2 bytes).
+// Must be called by all threads of the block (contains __syncthreads).
+static __device__ void detect_tile(const float *buf, float *red, const DetectArgs &a) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int NP = a.NR * 32;
+  const int NI = (a.NR - 2) * 30;  // interior pixels
+  if (a.resp) {
+    const long plane = (long)a.H * a.W;
+    for (int q = tid; q < NI; q += nt) {
+      const int i = 1 + q / 30, lane = 1 + q % 30;
+      const int y = a.r0 + i, x = a.x0 + lane;
+      if (y < 0 || y >= a.H || x < 0 || x >= a.W) continue;
+      for (int s = 0; s < a.S; ++s)
+        a.resp[s * plane + (long)y * a.W + x] = buf[(s * a.NR + i) * a.ld + a.coff + lane];
+    }
+  }
+  float *mx = red, *mn = red + NP;
+  unsigned char *amx = reinterpret_cast<unsigned char *>(red + 2 * NP);
+  unsigned char *amn = amx + NP;
+  if (a.neigh == 0) {
+    // per-pixel extremes over scales (first argmax / argmin), out-of-frame -> +-inf
+    for (int p = tid; p < NP; p += nt) {
+      const int i = p >> 5, lane = p & 31;
+      const int y = a.r0 + i, x = a.x0 + lane;
+      float vmax = -CUDART_INF_F, vmin = CUDART_INF_F;
+      int smax = a.S, smin = a.S;
+      if (y >= 0 && y < a.H && x >= 0 && x < a.W) {
+        for (int s = 0; s < a.S; ++s) {
+          const float v = buf[(s * a.NR + i) * a.ld + a.coff + lane];
+          if (v > vmax) vmax = v, smax = s;
+          if (v < vmin) vmin = v, smin = s;
+        }
+      }
+      mx[p] = vmax;
+      mn[p] = vmin;
+      amx[p] = (unsigned char)smax;
+      amn[p] = (unsigned char)smin;
+    }
+    __syncthreads();
+    spatial_detect(mx, mn, amx, amn, a);
+    return;
+  }
+  // adjacent scales: every (scale, pixel) against its 3 x 3 x 3 neighbourhood
+  TileList &tl = g_tl;
+  unsigned long long &s_base = g_tl_base;
+  if (tid == 0) tl.n = 0;
+  __syncthreads();
+  for (int q = tid; q < NI; q += nt) {
+    const int i = 1 + q / 30, lane = 1 + q % 30;
+    const int y = a.r0 + i, x = a.x0 + lane;
+    if (y < 0 || y >= a.H || x < 0 || x >= a.W) continue;
+    for (int s = 0; s < a.S; ++s) {
+      const float v = buf[(s * a.NR + i) * a.ld + a.coff + lane];
+      const int pol = (v > a.thr) ? 1 : ((a.dark && v < -a.thr) ? -1 : 0);
+      if (!pol) continue;
+      bool ok = true;
+      for (int t = max(0, s - 1); t <= min(a.S - 1, s + 1) && ok; ++t)
         for (int di = -1; di <= 1 && ok; ++di)
           for (int dl = -1; dl <= 1 && ok; ++dl) {
-            if (di == 0 && dl == 0) continue;
-            const int pn = p + di * 32 + dl;
-            const float vn = (pol == 1) ? mx[pn] : mn[pn];
-            const int sn = (pol == 1) ? amx[pn] : amn[pn];
-            const bool after = di > 0 || (di == 0 && dl > 0);
-            const float a1 = pol * v, b1 = pol * vn;
-            ok = (a1 > b1) || (a1 == b1 && (sn > s || (sn == s && after)));
+            if (t == s && di == 0 && dl == 0) continue;
+            const int yn = y + di, xn = x + dl;
+            if (yn < 0 || yn >= a.H || xn < 0 || xn >= a.W) continue;
+            const float vn = buf[(t * a.NR + i + di) * a.ld + a.coff + lane + dl];
+            const bool earlier = t < s || (t == s && (di < 0 || (di == 0 && dl < 0)));
+            ok = earlier ? (pol * v > pol * vn) : (pol * v >= pol * vn);
           }
-        if (ok) emit_blob(a, tl, s, y, x, pol, v);
-      }
-    } else {
-      for (int s = 0; s < a.S; ++s) {
-        const float v = buf[(s * a.NR + i) * 32 + lane];
-        const int pol = (v > a.thr) ? 1 : ((a.dark && v < -a.thr) ? -1 : 0);
-        if (!pol) continue;
-        bool ok = true;
-        for (int t = max(0, s - 1); t <= min(a.S - 1, s + 1) && ok; ++t)
-          for (int di = -1; di <= 1 && ok; ++di)
-            for (int dl = -1; dl <= 1 && ok; ++dl) {
-              if (t == s && di == 0 && dl == 0) continue;
-              const int yn = y + di, xn = x + dl;
-              if (yn < 0 || yn >= a.H || xn < 0 || xn >= a.W) continue;
-              const float vn = buf[(t * a.NR + i + di) * 32 + lane + dl];
-              const bool earlier = t < s || (t == s && (di < 0 || (di == 0 && dl < 0)));
-              ok = earlier ? (pol * v > pol * vn) : (pol * v >= pol * vn);
-            }
-        if (ok) emit_blob(a, tl, s, y, x, pol, v);
-      }
+      if (ok) emit_blob(a, tl, s, y, x, pol, v);
     }
   }
   __syncthreads();

@@ -16,9 +16,12 @@
 //               input block (64 + 2K rows) is staged in shared memory, each
 //               warp slides an 8-row register window down its column; then
 //               the detector.
+#include <cudaTypedefs.h>
+
 #include "kf_common.cuh"
 #include "kf_detect.cuh"
 #include "kf_internal.h"
+#include "kf_tma.cuh"
 
 namespace kf {
 
@@ -30,6 +33,9 @@ constexpr int RNT = 128;             // threads per row CTA
 constexpr int RSEG = RNT * NOUT;     // outputs per row CTA (2048)
 constexpr int CNT = 128;             // threads per column CTA (4 warps x 32 columns)
 constexpr int CROWS = 4 * NOUT;      // output rows per column CTA (64, incl. 2 halo rows)
+constexpr int BOXW = 36;             // TMA box width (floats): 32 columns + alignment offset <= 3
+constexpr int BOXH = 16;             // TMA box height (rows)
+constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
 // taps h[0..K] padded with zeros to a multiple of TB beyond K
 __device__ __forceinline__ void stage_taps(float *sh, const Coef &c, int K, int tid, int nt) {
@@ -163,7 +169,128 @@ __global__ void __launch_bounds__(CNT) k_colfir(const float *__restrict__ P, lon
   detect_tile(buf, red, a);
 }
 
+// Column FIR + detector, all-scales neighbourhood.  Per scale the input block
+// (64 + 2(K+8) rows x 36 columns of the one-sided plane) arrives by TMA into
+// one of two shared-memory stages (the next scale loads while this one is
+// filtered); rows outside the frame are then set to the held values.  Each
+// thread keeps no per-scale responses: the per-pixel maximum / minimum over
+// scales (and their first scale) are updated in shared memory as scales
+// complete, and the spatial 3 x 3 test runs once at the end.
+__global__ void __launch_bounds__(CNT, 2) k_colfir_tma(const __grid_constant__ CUtensorMap map,
+                                                       const float *__restrict__ edge, long PW, int H, int W,
+                                                       const Coef *__restrict__ coef, int S, int stage_rows,
+                                                       int taps_len, DetectArgs da) {
+  extern __shared__ __align__(128) float sm[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // stage b at sm + b * stage_rows * BOXW; taps of stage b after both stages
+  auto stage = [&](int b) { return sm + b * stage_rows * BOXW; };
+  auto taps = [&](int b) { return sm + 2 * stage_rows * BOXW + b * taps_len; };
+  float *mx = sm + 2 * stage_rows * BOXW + 2 * taps_len;
+  float *mn = mx + CROWS * 32;
+  unsigned char *amx = reinterpret_cast<unsigned char *>(mn + CROWS * 32);
+  unsigned char *amn = amx + CROWS * 32;
+  const int x0 = blockIdx.x * TW - 1;       // frame column of lane 0
+  const int off = ((x0 % 4) + 4) % 4;       // TMA x must be a multiple of 4 floats
+  const int xa = x0 - off;
+  const int r0 = blockIdx.y * (CROWS - 2) - 1;  // frame row of output row 0
+  const int x = x0 + lane, xv = min(max(x, 0), W - 1);
+  const bool xin = x >= 0 && x < W;
+#pragma unroll
+  for (int j = 0; j < NOUT; ++j) {
+    const int p = (NOUT * warp + j) * 32 + lane;
+    mx[p] = -CUDART_INF_F;
+    mn[p] = CUDART_INF_F;
+    amx[p] = (unsigned char)S;
+    amn[p] = (unsigned char)S;
+  }
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  auto issue = [&](int s, int b) {  // thread 0 only
+    const int G = coef[s].K + TB;
+    const int nb = (CROWS + 2 * G + BOXH - 1) / BOXH;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&mbar[b], (uint32_t)(nb * BOXH * BOXW * sizeof(float)));
+    for (int i = 0; i < nb; ++i) tma_load_3d(stage(b) + i * BOXH * BOXW, &map, xa, r0 - G + i * BOXH, s, &mbar[b]);
+  };
+  if (tid == 0) issue(0, 0);
+  const long plane = (long)H * W;
+  for (int s = 0; s < S; ++s) {
+    const int b = s & 1;
+    if (tid == 0 && s + 1 < S) issue(s + 1, b ^ 1);
+    const Coef &c = coef[s];
+    const int K = c.K, G = K + TB, nin = CROWS + 2 * G;
+    stage_taps(taps(b), c, K, tid, CNT);
+    const bool ok = mbar_wait_bounded(&mbar[b], (uint32_t)((s >> 1) & 1), WAIT_LIMIT);
+    if (__syncthreads_or(!ok)) {
+      // a load never completed: report, let the other stage's load finish, stop
+      if (tid == 0) {
+        atomicExch(&da.status->error, 1);
+        if (s + 1 < S) mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)(((s + 1) >> 1) & 1), WAIT_LIMIT);
+      }
+      __syncthreads();
+      return;
+    }
+    if (r0 - G < 0 || r0 + CROWS + G > H) {  // rows outside the frame: held values
+      const float top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
+      for (int j = warp; j < nin; j += CNT / 32) {
+        const int r = r0 - G + j;
+        if (r < 0) stage(b)[j * BOXW + off + lane] = top;
+        else if (r >= H) stage(b)[j * BOXW + off + lane] = bot;
+      }
+    }
+    __syncthreads();
+    const float *col = stage(b) + (G + NOUT * warp) * BOXW + off + lane;
+    float acc[NOUT];
+    fir_block(taps(b), K, [&](int t) { return col[t * BOXW]; }, acc);
+    const float ms2 = -c.sigma2;
+#pragma unroll
+    for (int j = 0; j < NOUT; ++j) {
+      const int i = NOUT * warp + j, y = r0 + i;
+      if (!xin || y < 0 || y >= H) continue;
+      const int p = i * 32 + lane;
+      const float v = ms2 * acc[j];
+      if (v > mx[p]) mx[p] = v, amx[p] = (unsigned char)s;
+      if (v < mn[p]) mn[p] = v, amn[p] = (unsigned char)s;
+      if (da.resp && i >= 1 && i <= CROWS - 2 && lane >= 1 && lane <= TW)
+        da.resp[s * plane + (long)y * W + x] = v;
+    }
+    __syncthreads();
+  }
+  DetectArgs a = da;
+  a.S = S;
+  a.NR = CROWS;
+  a.x0 = x0;
+  a.r0 = r0;
+  spatial_detect(mx, mn, amx, amn, a);
+}
+
 }  // namespace
+
+// 3-D tensor map over the S one-sided planes (x, y, scale), box boxw x boxh x 1
+int encode_plane_map(CUtensorMap *m, float *P, long PW, int H, int S, int boxw, int boxh) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return -1;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)PW, (cuuint64_t)H, (cuuint64_t)S};
+  const cuuint64_t strides[2] = {(cuuint64_t)PW * sizeof(float), (cuuint64_t)H * PW * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)boxw, (cuuint32_t)boxh, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P, dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
+}
 
 int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   static bool attr = false;
@@ -171,6 +298,7 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
     cudaFuncSetAttribute(k_rowfir<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_rowfir<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_colfir, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_colfir_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr = true;
   }
   const int kmax = a.kmax;
@@ -196,11 +324,24 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   da.cap = a.cap;
   da.status = a.status;
   da.resp = a.responses ? a.responses + g.resp_off : nullptr;
+  dim3 gc((g.W + TW - 1) / TW, (g.H + CROWS - 3) / (CROWS - 2));
+  if (a.neigh == 0) {
+    CUtensorMap map;
+    if (encode_plane_map(&map, a.P, g.PW, g.H, a.S, BOXW, BOXH)) return -1;
+    const int stage_rows = (CROWS + 2 * G + BOXH - 1) / BOXH * BOXH;
+    const int taps_len = KP + 1;
+    const size_t tsm = ((size_t)2 * stage_rows * BOXW + 2 * taps_len + (size_t)CROWS * 32 * 2) * sizeof(float) +
+                       (size_t)CROWS * 32 * 2;
+    if (tsm > 220 * 1024) return -1;
+    a.prof->begin("fir_coldet", st);
+    k_colfir_tma<<<gc, CNT, tsm, st>>>(map, a.edge, g.PW, g.H, g.W, a.coef, a.S, stage_rows, taps_len, da);
+    a.prof->end(st);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  }
   // in + buf + detector scratch (2 float planes + 2 byte planes) + taps
   const size_t csm = ((size_t)(CROWS + 2 * G) * 32 + (size_t)a.S * CROWS * 32 + (size_t)CROWS * 32 * 2 +
                       (size_t)CROWS * 32 * 2 / 4 + KP + 1) * sizeof(float);
   if (csm > 220 * 1024) return -1;
-  dim3 gc((g.W + TW - 1) / TW, (g.H + CROWS - 3) / (CROWS - 2));
   a.prof->begin("fir_coldet", st);
   k_colfir<<<gc, CNT, csm, st>>>(a.P, g.PW, g.H, g.W, a.edge, a.coef, a.S, kmax, da);
   a.prof->end(st);

@@ -26,6 +26,7 @@
 #include "kf_common.cuh"
 #include "kf_detect.cuh"
 #include "kf_internal.h"
+#include "kf_tma.cuh"
 
 namespace kf {
 
@@ -382,54 +383,83 @@ __global__ void __launch_bounds__(128) k_colfold(int W, long PW, const float *__
   }
 }
 
+// Column pass + detector.  One CTA per (32-column, LC+2-row) tile, one warp
+// per scale, one thread per (column, scale).  The tile of every scale's
+// one-sided plane arrives by TMA into shared memory (box 36 x 66: the TMA x
+// coordinate must be a multiple of 4 floats, so the tile starts up to 3
+// columns early); rows outside the frame are then set to the held values.
+// Both recursions run from shared memory, the causal outputs stay in
+// registers, and R overwrites the input in place for the detector.
+constexpr int CLD = 36;
+constexpr uint32_t CWAIT_LIMIT = 1u << 24;
+
 template <class Rec>
-__global__ void __launch_bounds__(512) k_coldet(const float *__restrict__ P, long PW, int H, int W,
-                                                const float *__restrict__ edge,
+__global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUtensorMap map, long PW, int H,
+                                                int W, const float *__restrict__ edge,
                                                 const Coef *__restrict__ coef, int S,
-                                                const float *__restrict__ E, int nseg,
-                                                DetectArgs da) {
-  extern __shared__ float sm[];
+                                                const float *__restrict__ E, int nseg, DetectArgs da) {
+  extern __shared__ __align__(128) float sm[];
+  __shared__ __align__(8) uint64_t mbar;
   constexpr int NR = LC + 2;
-  float *buf = sm;                       // [S][NR][32]
-  float *red = sm + (long)S * NR * 32;   // detector scratch
-  const int lane = threadIdx.x & 31, s = threadIdx.x >> 5;
+  float *buf = sm;                            // [S][NR][CLD]
+  float *red = sm + (long)S * NR * CLD;       // detector scratch
+  const int tid = threadIdx.x, lane = tid & 31, s = tid >> 5;
   const int c = blockIdx.y;
-  const int x = blockIdx.x * TW - 1 + lane;
-  const int xv = min(max(x, 0), W - 1);
+  const int x0 = blockIdx.x * TW - 1;
+  const int off = ((x0 % 4) + 4) % 4;
+  const int xv = min(max(x0 + lane, 0), W - 1);
   const int r0 = c * LC - 1;
-  {
-    const Coef &cf = coef[s];
-    typename Rec::View v;
-    v.load(cf);
-    const float *Pc = P + (long)s * H * PW + xv;
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&mbar, (uint32_t)(S * NR * CLD * sizeof(float)));
+    for (int t = 0; t < S; ++t) tma_load_3d(buf + (long)t * NR * CLD, &map, x0 - off, r0, t, &mbar);
+  }
+  const Coef &cf = coef[s];
+  typename Rec::View v;
+  v.load(cf);
+  const long fs = (long)Rec::NF * PW;
+  const float *Ef = E + (((long)s * nseg + c) * 2) * fs + xv;
+  Rec r;
+  r.load(Ef, PW);
+  const bool ok = mbar_wait_bounded(&mbar, 0, CWAIT_LIMIT);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicExch(&da.status->error, 1);
+    return;
+  }
+  float *b = buf + (long)s * NR * CLD + off + lane;
+  if (r0 < 0 || r0 + NR > H) {  // rows outside the frame: held one-sided rows of U
     const float top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
-    const long fs = (long)Rec::NF * PW;
-    const float *Ef = E + (((long)s * nseg + c) * 2) * fs + xv;
-    float *b = buf + (long)s * NR * 32 + lane;
-    Rec r;
-    r.load(Ef, PW);
-#pragma unroll 2
+#pragma unroll
     for (int i = 0; i < NR; ++i) {
-      const float in = col_in(Pc, PW, r0 + i, H, top, bot);
-      b[i * 32] = r.out(v);
-      r.push(v, in);
+      const int y = r0 + i;
+      if (y < 0) b[i * CLD] = top;
+      else if (y >= H) b[i * CLD] = bot;
     }
-    r.load(Ef + fs, PW);
-    const float ms2 = -cf.sigma2;
-#pragma unroll 2
-    for (int i = NR - 1; i >= 0; --i) {
-      const float in = col_in(Pc, PW, r0 + i, H, top, bot);
-      const float q = b[i * 32] + fmaf(v.b0, in, r.out(v));
-      b[i * 32] = ms2 * q;  // R_L = -sigma^2 (D20 + D02)
-      r.push(v, in);
-    }
+  }
+  float yp[NR];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    const float in = b[i * CLD];
+    yp[i] = r.out(v);
+    r.push(v, in);
+  }
+  r.load(Ef + fs, PW);
+  const float ms2 = -cf.sigma2;
+#pragma unroll
+  for (int i = NR - 1; i >= 0; --i) {
+    const float in = b[i * CLD];
+    b[i * CLD] = ms2 * (yp[i] + fmaf(v.b0, in, r.out(v)));  // R_L = -sigma^2 (D20 + D02)
+    r.push(v, in);
   }
   __syncthreads();
   DetectArgs a = da;
   a.S = S;
   a.NR = NR;
-  a.x0 = blockIdx.x * TW - 1;
+  a.x0 = x0;
   a.r0 = r0;
+  a.ld = CLD;
+  a.coff = off;
   detect_tile(buf, red, a);
 }
 
@@ -473,11 +503,12 @@ int run_iir(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   da.status = a.status;
   da.resp = a.responses ? a.responses + g.resp_off : nullptr;
   constexpr int NR = LC + 2;
-  const size_t det_smem = ((size_t)a.S * NR * 32 + (size_t)NR * 32 * 2) * sizeof(float) + (size_t)NR * 32 * 2;
+  const size_t det_smem = ((size_t)a.S * NR * CLD + (size_t)NR * 32 * 2) * sizeof(float) + (size_t)NR * 32 * 2;
+  CUtensorMap map;
+  if (encode_plane_map(&map, a.P, g.PW, g.H, a.S, CLD, NR)) return -1;
   dim3 gd((g.W + TW - 1) / TW, nseg);
   a.prof->begin("iir_coldet", st);
-  k_coldet<Rec><<<gd, 32 * a.S, det_smem, st>>>(a.P, g.PW, g.H, g.W, a.edge, a.coef, a.S, a.carry,
-                                                 nseg, da);
+  k_coldet<Rec><<<gd, 32 * a.S, det_smem, st>>>(map, g.PW, g.H, g.W, a.edge, a.coef, a.S, a.carry, nseg, da);
   a.prof->end(st);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

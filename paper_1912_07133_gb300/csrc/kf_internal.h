@@ -1,6 +1,7 @@
 // kf_internal.h -- host-side declarations shared by the library's translation
 // units (launchers of the CUDA kernels).  Not part of the C ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "kf_common.cuh"
@@ -58,6 +59,10 @@ struct BankArgs {
 
 int launch_iir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st);
 int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st);
+
+// 3-D tensor map over S one-sided planes (x, y, scale) of pitch PW, box
+// boxw x boxh x 1 (kf_fir.cu)
+int encode_plane_map(CUtensorMap *m, float *P, long PW, int H, int S, int boxw, int boxh);
 
 // workspace needs (bytes) of one frame
 size_t iir_carry_floats(int H, long PW, int S, int nf);
