@@ -29,6 +29,7 @@ struct DetectArgs {
   float *resp;         // optional: R planes of this frame (S x H x W)
   int ld = 32;         // row stride of the response buffer (floats)
   int coff = 0;        // column of lane 0 inside a buffer row
+  int srows = 0;       // rows per scale in the buffer (0: NR)
 };
 
 constexpr int TILE_CANDS = 256;  // candidates staged per tile before one global reservation
@@ -115,6 +116,7 @@ static __device__ void detect_tile(const float *buf, float *red, const DetectArg
   const int tid = threadIdx.x, nt = blockDim.x;
   const int NP = a.NR * 32;
   const int NI = (a.NR - 2) * 30;  // interior pixels
+  const int SR = a.srows ? a.srows : a.NR;
   if (a.resp) {
     const long plane = (long)a.H * a.W;
     for (int q = tid; q < NI; q += nt) {
@@ -122,7 +124,7 @@ static __device__ void detect_tile(const float *buf, float *red, const DetectArg
       const int y = a.r0 + i, x = a.x0 + lane;
       if (y < 0 || y >= a.H || x < 0 || x >= a.W) continue;
       for (int s = 0; s < a.S; ++s)
-        a.resp[s * plane + (long)y * a.W + x] = buf[(s * a.NR + i) * a.ld + a.coff + lane];
+        a.resp[s * plane + (long)y * a.W + x] = buf[(s * SR + i) * a.ld + a.coff + lane];
     }
   }
   float *mx = red, *mn = red + NP;
@@ -137,7 +139,7 @@ static __device__ void detect_tile(const float *buf, float *red, const DetectArg
       int smax = a.S, smin = a.S;
       if (y >= 0 && y < a.H && x >= 0 && x < a.W) {
         for (int s = 0; s < a.S; ++s) {
-          const float v = buf[(s * a.NR + i) * a.ld + a.coff + lane];
+          const float v = buf[(s * SR + i) * a.ld + a.coff + lane];
           if (v > vmax) vmax = v, smax = s;
           if (v < vmin) vmin = v, smin = s;
         }
@@ -161,7 +163,7 @@ static __device__ void detect_tile(const float *buf, float *red, const DetectArg
     const int y = a.r0 + i, x = a.x0 + lane;
     if (y < 0 || y >= a.H || x < 0 || x >= a.W) continue;
     for (int s = 0; s < a.S; ++s) {
-      const float v = buf[(s * a.NR + i) * a.ld + a.coff + lane];
+      const float v = buf[(s * SR + i) * a.ld + a.coff + lane];
       const int pol = (v > a.thr) ? 1 : ((a.dark && v < -a.thr) ? -1 : 0);
       if (!pol) continue;
       bool ok = true;
@@ -171,7 +173,7 @@ static __device__ void detect_tile(const float *buf, float *red, const DetectArg
             if (t == s && di == 0 && dl == 0) continue;
             const int yn = y + di, xn = x + dl;
             if (yn < 0 || yn >= a.H || xn < 0 || xn >= a.W) continue;
-            const float vn = buf[(t * a.NR + i + di) * a.ld + a.coff + lane + dl];
+            const float vn = buf[(t * SR + i + di) * a.ld + a.coff + lane + dl];
             const bool earlier = t < s || (t == s && (di < 0 || (di == 0 && dl < 0)));
             ok = earlier ? (pol * v > pol * vn) : (pol * v >= pol * vn);
           }

@@ -180,8 +180,9 @@ __global__ void __launch_bounds__(CNT, 2) k_colfir_tma(const __grid_constant__ C
                                                        const float *__restrict__ edge, long PW, int H, int W,
                                                        const Coef *__restrict__ coef, int S, int stage_rows,
                                                        int taps_len, DetectArgs da) {
-  extern __shared__ __align__(128) float sm[];
+  extern __shared__ __align__(128) float sm_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
+  float *sm = align_smem(sm_raw);  // stages: multiples of BOXH rows x 144 B = 2304 B (18 x 128 B)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // stage b at sm + b * stage_rows * BOXW; taps of stage b after both stages
   auto stage = [&](int b) { return sm + b * stage_rows * BOXW; };
@@ -215,7 +216,9 @@ __global__ void __launch_bounds__(CNT, 2) k_colfir_tma(const __grid_constant__ C
     const int nb = (CROWS + 2 * G + BOXH - 1) / BOXH;
     fence_proxy_async();
     mbar_arrive_expect_tx(&mbar[b], (uint32_t)(nb * BOXH * BOXW * sizeof(float)));
-    for (int i = 0; i < nb; ++i) tma_load_3d(stage(b) + i * BOXH * BOXW, &map, xa, r0 - G + i * BOXH, s, &mbar[b]);
+    for (int i = 0; i < nb; ++i)
+      if (!tma_load_3d(stage(b) + i * BOXH * BOXW, &map, xa, r0 - G + i * BOXH, s, &mbar[b]))
+        atomicExch(&da.status->error, 2);
   };
   if (tid == 0) issue(0, 0);
   const long plane = (long)H * W;
@@ -331,7 +334,7 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
     const int stage_rows = (CROWS + 2 * G + BOXH - 1) / BOXH * BOXH;
     const int taps_len = KP + 1;
     const size_t tsm = ((size_t)2 * stage_rows * BOXW + 2 * taps_len + (size_t)CROWS * 32 * 2) * sizeof(float) +
-                       (size_t)CROWS * 32 * 2;
+                       (size_t)CROWS * 32 * 2 + TMA_SMEM_ALIGN;
     if (tsm > 220 * 1024) return -1;
     a.prof->begin("fir_coldet", st);
     k_colfir_tma<<<gc, CNT, tsm, st>>>(map, a.edge, g.PW, g.H, g.W, a.coef, a.S, stage_rows, taps_len, da);

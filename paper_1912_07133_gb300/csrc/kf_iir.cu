@@ -391,6 +391,7 @@ __global__ void __launch_bounds__(128) k_colfold(int W, long PW, const float *__
 // Both recursions run from shared memory, the causal outputs stay in
 // registers, and R overwrites the input in place for the detector.
 constexpr int CLD = 36;
+constexpr int CNRP = 72;  // rows reserved per scale: 72 x 144 B = 81 x 128 B keeps every box 128-byte aligned
 constexpr uint32_t CWAIT_LIMIT = 1u << 24;
 
 template <class Rec>
@@ -398,11 +399,12 @@ __global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUten
                                                 int W, const float *__restrict__ edge,
                                                 const Coef *__restrict__ coef, int S,
                                                 const float *__restrict__ E, int nseg, DetectArgs da) {
-  extern __shared__ __align__(128) float sm[];
+  extern __shared__ __align__(128) float sm_raw[];
   __shared__ __align__(8) uint64_t mbar;
   constexpr int NR = LC + 2;
-  float *buf = sm;                            // [S][NR][CLD]
-  float *red = sm + (long)S * NR * CLD;       // detector scratch
+  static_assert(NR <= CNRP && (CNRP * CLD * 4) % TMA_SMEM_ALIGN == 0, "scale stride alignment");
+  float *buf = align_smem(sm_raw);            // [S][CNRP][CLD], rows NR..CNRP-1 unused
+  float *red = buf + (long)S * CNRP * CLD;    // detector scratch
   const int tid = threadIdx.x, lane = tid & 31, s = tid >> 5;
   const int c = blockIdx.y;
   const int x0 = blockIdx.x * TW - 1;
@@ -412,8 +414,12 @@ __global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUten
   if (tid == 0) {
     mbar_init(&mbar, 1);
     fence_proxy_async();
+  }
+  __syncthreads();  // no thread polls the barrier before it is initialised
+  if (tid == 0) {
     mbar_arrive_expect_tx(&mbar, (uint32_t)(S * NR * CLD * sizeof(float)));
-    for (int t = 0; t < S; ++t) tma_load_3d(buf + (long)t * NR * CLD, &map, x0 - off, r0, t, &mbar);
+    for (int t = 0; t < S; ++t)
+      if (!tma_load_3d(buf + (long)t * CNRP * CLD, &map, x0 - off, r0, t, &mbar)) atomicExch(&da.status->error, 2);
   }
   const Coef &cf = coef[s];
   typename Rec::View v;
@@ -427,7 +433,7 @@ __global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUten
     if (tid == 0) atomicExch(&da.status->error, 1);
     return;
   }
-  float *b = buf + (long)s * NR * CLD + off + lane;
+  float *b = buf + (long)s * CNRP * CLD + off + lane;
   if (r0 < 0 || r0 + NR > H) {  // rows outside the frame: held one-sided rows of U
     const float top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
 #pragma unroll
@@ -460,6 +466,7 @@ __global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUten
   a.r0 = r0;
   a.ld = CLD;
   a.coff = off;
+  a.srows = CNRP;
   detect_tile(buf, red, a);
 }
 
@@ -503,7 +510,8 @@ int run_iir(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   da.status = a.status;
   da.resp = a.responses ? a.responses + g.resp_off : nullptr;
   constexpr int NR = LC + 2;
-  const size_t det_smem = ((size_t)a.S * NR * CLD + (size_t)NR * 32 * 2) * sizeof(float) + (size_t)NR * 32 * 2;
+  const size_t det_smem = ((size_t)a.S * CNRP * CLD + (size_t)NR * 32 * 2) * sizeof(float) + (size_t)NR * 32 * 2 +
+                          TMA_SMEM_ALIGN;
   CUtensorMap map;
   if (encode_plane_map(&map, a.P, g.PW, g.H, a.S, CLD, NR)) return -1;
   dim3 gd((g.W + TW - 1) / TW, nseg);

@@ -46,15 +46,27 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   return false;
 }
 
-// 3-D tiled TMA load of one box at coordinates (x, y, z) into shared memory;
-// x * 4 bytes must be a multiple of 16.
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+// TMA destinations in shared memory are kept 128-byte aligned.
+constexpr int TMA_SMEM_ALIGN = 128;
+
+__device__ __forceinline__ float *align_smem(float *p) {
+  return reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(p) + TMA_SMEM_ALIGN - 1) &
+                                   ~(uintptr_t)(TMA_SMEM_ALIGN - 1));
+}
+
+// 3-D tiled TMA load of one box at coordinates (x, y, z) into shared memory
+// (destination 128-byte aligned); x * 4 bytes must be a multiple of 16.
+// A destination or coordinate that breaks these rules is not issued: the
+// function returns false and the caller's bounded wait reports the failure.
+__device__ __forceinline__ bool tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
                                             uint64_t *bar) {
+  if ((smem_u32(dst) & (TMA_SMEM_ALIGN - 1)) != 0 || (x & 3) != 0) return false;
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
       "[%5];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
+  return true;
 }
 
 }  // namespace kf
