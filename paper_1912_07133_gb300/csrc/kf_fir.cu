@@ -69,22 +69,64 @@ __device__ __forceinline__ void fir_block(const float *sh, int K, At at, float (
   }
 }
 
-__host__ __device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
+// Row layout in shared memory: 16 elements then 4 unused floats (20 per 16),
+// so 128-bit loads of quads that start at multiples of 4 never straddle a gap
+// and a quarter-warp whose threads start 16 elements apart hits 8 distinct
+// 4-bank groups.
+__host__ __device__ __forceinline__ int pad20(int e) { return e + ((e >> 4) << 2); }
+
+// Symmetric FIR of NOUT consecutive outputs from a padded row: `row` points at
+// element 0, `base` (a multiple of 16) is the first output.  Taps are used 8
+// at a time: the left window x(base-8(i+1) .. +23) and the right window
+// x(base+8i .. +23) are six 128-bit loads each.
+__device__ __forceinline__ void fir_row_block(const float *sh, int K, const float *row, int base,
+                                              float (&acc)[NOUT]) {
+  auto quad = [&](int e) { return *reinterpret_cast<const float4 *>(row + pad20(e)); };
+  const float h0 = sh[0];
+#pragma unroll
+  for (int q = 0; q < NOUT / 4; ++q) {
+    const float4 v = quad(base + 4 * q);
+    acc[4 * q + 0] = h0 * v.x;
+    acc[4 * q + 1] = h0 * v.y;
+    acc[4 * q + 2] = h0 * v.z;
+    acc[4 * q + 3] = h0 * v.w;
+  }
+  for (int k0 = 1, i = 0; k0 <= K; k0 += TB, ++i) {
+    float A[NOUT + TB], B[NOUT + TB], hk[TB];
+#pragma unroll
+    for (int u = 0; u < TB; ++u) hk[u] = sh[k0 + u];
+#pragma unroll
+    for (int q = 0; q < (NOUT + TB) / 4; ++q) {
+      const float4 a = quad(base - TB * (i + 1) + 4 * q);  // A[m] = x(base + m - k0 - 7)
+      const float4 b = quad(base + TB * i + 4 * q);        // B[m] = x(base + m + k0 - 1)
+      A[4 * q + 0] = a.x, A[4 * q + 1] = a.y, A[4 * q + 2] = a.z, A[4 * q + 3] = a.w;
+      B[4 * q + 0] = b.x, B[4 * q + 1] = b.y, B[4 * q + 2] = b.z, B[4 * q + 3] = b.w;
+    }
+    // output j, tap k0 + u: x(j - k0 - u) = A[j - u + 7], x(j + k0 + u) = B[j + u + 1]
+#pragma unroll
+    for (int u = 0; u < TB; ++u)
+#pragma unroll
+      for (int j = 0; j < NOUT; ++j) acc[j] = fmaf(hk[u], A[j - u + TB - 1] + B[j + u + 1], acc[j]);
+  }
+}
+
+// halo of the row kernel: >= kmax + TB, a multiple of 16
+__host__ __device__ __forceinline__ int row_halo(int kmax) { return (kmax + TB + 15) / 16 * 16; }
 
 template <bool EDGE>
 __global__ void __launch_bounds__(RNT) k_rowfir(const float *__restrict__ X, long xpitch, int H, int W,
                                                 const Coef *__restrict__ coef, int S, int kmax,
                                                 float *__restrict__ P, long PW, float *__restrict__ edge) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   const int tid = threadIdx.x;
   const int y = EDGE ? (blockIdx.y == 0 ? 0 : H - 1) : blockIdx.y;
   const int xs = blockIdx.x * RSEG;
-  // L on [xs - G, xs + RSEG + G), G = kmax + TB: the 8-tap blocks read up to
-  // TB - 1 elements past the last tap
-  const int G = kmax + TB;
+  // L on [xs - G, xs + RSEG + G): the 8-tap blocks read up to TB elements past
+  // the last tap on each side
+  const int G = row_halo(kmax);
   const int n = RSEG + 2 * G;
-  float *sL = sm;                       // padded: element j at pad16(j)
-  float *sh = sm + pad16(n) + 1;
+  float *sL = sm;                       // padded: element j at pad20(j)
+  float *sh = sm + pad20(n) + 4;
   const float *rm = X + (long)max(y - 1, 0) * xpitch;
   const float *r0 = X + (long)y * xpitch;
   const float *rp = X + (long)min(y + 1, H - 1) * xpitch;
@@ -100,7 +142,7 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const float *__restrict__ X, lon
       const float u = __ldg(r0 + min(e + 1, W - 1)) - 2.f * c0 + __ldg(r0 + max(e - 1, 0));
       v = EDGE ? u : u + (__ldg(rp + e) - 2.f * c0 + __ldg(rm + e));
     }
-    sL[pad16(j)] = v;
+    sL[pad20(j)] = v;
   }
   const int base = G + NOUT * tid;  // local index of this thread's first output
   for (int s = 0; s < S; ++s) {
@@ -110,7 +152,7 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const float *__restrict__ X, lon
     stage_taps(sh, c, K, tid, RNT);
     __syncthreads();
     float acc[NOUT];
-    fir_block(sh, K, [&](int t) { return sL[pad16(base + t)]; }, acc);
+    fir_row_block(sh, K, sL, base, acc);
     float *dst = EDGE ? edge + ((long)s * 2 + blockIdx.y) * PW : P + (long)s * H * PW + (long)y * PW;
     const int x0 = xs + NOUT * tid;
     if (x0 + NOUT <= W) {
@@ -169,39 +211,41 @@ __global__ void __launch_bounds__(CNT) k_colfir(const float *__restrict__ P, lon
   detect_tile(buf, red, a);
 }
 
-// Column FIR + detector, all-scales neighbourhood.  Per scale the input block
-// (64 + 2(K+8) rows x 36 columns of the one-sided plane) arrives by TMA into
-// one of two shared-memory stages (the next scale loads while this one is
-// filtered); rows outside the frame are then set to the held values.  Each
-// thread keeps no per-scale responses: the per-pixel maximum / minimum over
-// scales (and their first scale) are updated in shared memory as scales
-// complete, and the spatial 3 x 3 test runs once at the end.
-__global__ void __launch_bounds__(CNT, 2) k_colfir_tma(const __grid_constant__ CUtensorMap map,
-                                                       const float *__restrict__ edge, long PW, int H, int W,
-                                                       const Coef *__restrict__ coef, int S, int stage_rows,
-                                                       int taps_len, DetectArgs da) {
+// Column FIR + detector, all-scales neighbourhood.  A CTA of 8 warps covers
+// 32 columns x 128 rows (row 0 and row 127 are halo); per scale the input
+// block (128 + 2(K+8) rows x 36 columns of the one-sided plane) arrives by TMA
+// into one of two shared-memory stages while the previous scale is filtered;
+// rows outside the frame are then set to the held values.  Each thread keeps
+// the running maximum / minimum over scales of its 16 pixels in registers
+// (their first scale in shared memory); the spatial 3 x 3 test runs once at
+// the end on those extremes.
+constexpr int CNT2 = 256;
+constexpr int CROWS2 = 8 * NOUT;  // 128
+
+__global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ CUtensorMap map,
+                                                        const float *__restrict__ edge, long PW, int H, int W,
+                                                        const Coef *__restrict__ coef, int S, int stage_rows,
+                                                        int taps_len, DetectArgs da) {
   extern __shared__ __align__(128) float sm_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
   float *sm = align_smem(sm_raw);  // stages: multiples of BOXH rows x 144 B = 2304 B (18 x 128 B)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // stage b at sm + b * stage_rows * BOXW; taps of stage b after both stages
   auto stage = [&](int b) { return sm + b * stage_rows * BOXW; };
   auto taps = [&](int b) { return sm + 2 * stage_rows * BOXW + b * taps_len; };
-  float *mx = sm + 2 * stage_rows * BOXW + 2 * taps_len;
-  float *mn = mx + CROWS * 32;
-  unsigned char *amx = reinterpret_cast<unsigned char *>(mn + CROWS * 32);
-  unsigned char *amn = amx + CROWS * 32;
+  unsigned char *amx = reinterpret_cast<unsigned char *>(sm + 2 * stage_rows * BOXW + 2 * taps_len);
+  unsigned char *amn = amx + CROWS2 * 32;
   const int x0 = blockIdx.x * TW - 1;       // frame column of lane 0
   const int off = ((x0 % 4) + 4) % 4;       // TMA x must be a multiple of 4 floats
   const int xa = x0 - off;
-  const int r0 = blockIdx.y * (CROWS - 2) - 1;  // frame row of output row 0
+  const int r0 = blockIdx.y * (CROWS2 - 2) - 1;  // frame row of output row 0
   const int x = x0 + lane, xv = min(max(x, 0), W - 1);
   const bool xin = x >= 0 && x < W;
+  float mxr[NOUT], mnr[NOUT];
 #pragma unroll
   for (int j = 0; j < NOUT; ++j) {
     const int p = (NOUT * warp + j) * 32 + lane;
-    mx[p] = -CUDART_INF_F;
-    mn[p] = CUDART_INF_F;
+    mxr[j] = -CUDART_INF_F;
+    mnr[j] = CUDART_INF_F;
     amx[p] = (unsigned char)S;
     amn[p] = (unsigned char)S;
   }
@@ -213,7 +257,7 @@ __global__ void __launch_bounds__(CNT, 2) k_colfir_tma(const __grid_constant__ C
   __syncthreads();
   auto issue = [&](int s, int b) {  // thread 0 only
     const int G = coef[s].K + TB;
-    const int nb = (CROWS + 2 * G + BOXH - 1) / BOXH;
+    const int nb = (CROWS2 + 2 * G + BOXH - 1) / BOXH;
     fence_proxy_async();
     mbar_arrive_expect_tx(&mbar[b], (uint32_t)(nb * BOXH * BOXW * sizeof(float)));
     for (int i = 0; i < nb; ++i)
@@ -226,8 +270,8 @@ __global__ void __launch_bounds__(CNT, 2) k_colfir_tma(const __grid_constant__ C
     const int b = s & 1;
     if (tid == 0 && s + 1 < S) issue(s + 1, b ^ 1);
     const Coef &c = coef[s];
-    const int K = c.K, G = K + TB, nin = CROWS + 2 * G;
-    stage_taps(taps(b), c, K, tid, CNT);
+    const int K = c.K, G = K + TB, nin = CROWS2 + 2 * G;
+    stage_taps(taps(b), c, K, tid, CNT2);
     const bool ok = mbar_wait_bounded(&mbar[b], (uint32_t)((s >> 1) & 1), WAIT_LIMIT);
     if (__syncthreads_or(!ok)) {
       // a load never completed: report, let the other stage's load finish, stop
@@ -238,9 +282,9 @@ __global__ void __launch_bounds__(CNT, 2) k_colfir_tma(const __grid_constant__ C
       __syncthreads();
       return;
     }
-    if (r0 - G < 0 || r0 + CROWS + G > H) {  // rows outside the frame: held values
+    if (r0 - G < 0 || r0 + CROWS2 + G > H) {  // rows outside the frame: held values
       const float top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
-      for (int j = warp; j < nin; j += CNT / 32) {
+      for (int j = warp; j < nin; j += CNT2 / 32) {
         const int r = r0 - G + j;
         if (r < 0) stage(b)[j * BOXW + off + lane] = top;
         else if (r >= H) stage(b)[j * BOXW + off + lane] = bot;
@@ -255,18 +299,26 @@ __global__ void __launch_bounds__(CNT, 2) k_colfir_tma(const __grid_constant__ C
     for (int j = 0; j < NOUT; ++j) {
       const int i = NOUT * warp + j, y = r0 + i;
       if (!xin || y < 0 || y >= H) continue;
-      const int p = i * 32 + lane;
       const float v = ms2 * acc[j];
-      if (v > mx[p]) mx[p] = v, amx[p] = (unsigned char)s;
-      if (v < mn[p]) mn[p] = v, amn[p] = (unsigned char)s;
-      if (da.resp && i >= 1 && i <= CROWS - 2 && lane >= 1 && lane <= TW)
+      if (v > mxr[j]) mxr[j] = v, amx[i * 32 + lane] = (unsigned char)s;
+      if (v < mnr[j]) mnr[j] = v, amn[i * 32 + lane] = (unsigned char)s;
+      if (da.resp && i >= 1 && i <= CROWS2 - 2 && lane >= 1 && lane <= TW)
         da.resp[s * plane + (long)y * W + x] = v;
     }
     __syncthreads();
   }
+  // the stages are free now: the extremes go to shared memory for the 3 x 3 test
+  float *mx = sm, *mn = sm + CROWS2 * 32;
+#pragma unroll
+  for (int j = 0; j < NOUT; ++j) {
+    const int p = (NOUT * warp + j) * 32 + lane;
+    mx[p] = mxr[j];
+    mn[p] = mnr[j];
+  }
+  __syncthreads();
   DetectArgs a = da;
   a.S = S;
-  a.NR = CROWS;
+  a.NR = CROWS2;
   a.x0 = x0;
   a.r0 = r0;
   spatial_detect(mx, mn, amx, amn, a);
@@ -307,7 +359,8 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   const int kmax = a.kmax;
   const int G = kmax + TB;
   const int KP = ((kmax + TB - 1) / TB) * TB;
-  const size_t rsm = (size_t)(pad16(RSEG + 2 * G) + 1 + KP + 1) * sizeof(float);
+  const int RG = row_halo(kmax);
+  const size_t rsm = (size_t)(pad20(RSEG + 2 * RG) + 4 + KP + 1) * sizeof(float);
   dim3 gr((g.W + RSEG - 1) / RSEG, g.H);
   a.prof->begin("fir_row", st);
   k_rowfir<false><<<gr, RNT, rsm, st>>>(g.X, g.xpitch, g.H, g.W, a.coef, a.S, kmax, a.P, g.PW, a.edge);
@@ -331,13 +384,15 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   if (a.neigh == 0) {
     CUtensorMap map;
     if (encode_plane_map(&map, a.P, g.PW, g.H, a.S, BOXW, BOXH)) return -1;
-    const int stage_rows = (CROWS + 2 * G + BOXH - 1) / BOXH * BOXH;
-    const int taps_len = KP + 1;
-    const size_t tsm = ((size_t)2 * stage_rows * BOXW + 2 * taps_len + (size_t)CROWS * 32 * 2) * sizeof(float) +
-                       (size_t)CROWS * 32 * 2 + TMA_SMEM_ALIGN;
-    if (tsm > 220 * 1024) return -1;
+    const int stage_rows = (CROWS2 + 2 * G + BOXH - 1) / BOXH * BOXH;
+    const int taps_len = (KP + 1 + 3) / 4 * 4;
+    // two stages (>= 2 x 128 x 32 floats for the final extremes) + taps + first-scale bytes
+    const size_t tsm = ((size_t)2 * stage_rows * BOXW + 2 * taps_len) * sizeof(float) + (size_t)CROWS2 * 32 * 2 +
+                       TMA_SMEM_ALIGN;
+    if (tsm > 220 * 1024 || 2 * stage_rows * BOXW < 2 * CROWS2 * 32) return -1;
+    dim3 gt((g.W + TW - 1) / TW, (g.H + CROWS2 - 3) / (CROWS2 - 2));
     a.prof->begin("fir_coldet", st);
-    k_colfir_tma<<<gc, CNT, tsm, st>>>(map, a.edge, g.PW, g.H, g.W, a.coef, a.S, stage_rows, taps_len, da);
+    k_colfir_tma<<<gt, CNT2, tsm, st>>>(map, a.edge, g.PW, g.H, g.W, a.coef, a.S, stage_rows, taps_len, da);
     a.prof->end(st);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
   }

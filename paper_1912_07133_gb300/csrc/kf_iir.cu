@@ -353,33 +353,39 @@ __global__ void __launch_bounds__(128) k_colseg(const float *__restrict__ P, lon
   r.store(Ef + fs, PW);
 }
 
+// Carries of the column segments, one thread per (column, scale, direction):
+// C_0 = steady state of the held row, C_{k+1} = Phi^LC C_k + e_k in the
+// direction's segment order; the segment states e_k are replaced by the C_k.
+// Segment states are read 8 at a time ahead of the sequential fold.
 template <class Rec>
 __global__ void __launch_bounds__(128) k_colfold(int W, long PW, const float *__restrict__ edge,
                                                  const Coef *__restrict__ coef, float *__restrict__ E,
                                                  int nseg) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= W) return;
-  const int s = blockIdx.y;
+  const int s = blockIdx.y, dir = blockIdx.z;  // 0: top-down, 1: bottom-up
   const Coef &c = coef[s];
   const long fs = (long)Rec::NF * PW;
-  Rec st, e;
-  st.hold(c, edge[((long)s * 2 + 0) * PW + x]);
-  for (int k = 0; k < nseg; ++k) {
-    float *slot = E + (((long)s * nseg + k) * 2 + 0) * fs + x;
-    e.load(slot, PW);
-    st.store(slot, PW);
-    Rec n = e;
-    n.combine_L(c, st);  // Phi^LC st + e
-    st = n;
-  }
-  st.hold(c, edge[((long)s * 2 + 1) * PW + x]);
-  for (int k = nseg - 1; k >= 0; --k) {
-    float *slot = E + (((long)s * nseg + k) * 2 + 1) * fs + x;
-    e.load(slot, PW);
-    st.store(slot, PW);
-    Rec n = e;
-    n.combine_L(c, st);
-    st = n;
+  float *base = E + ((long)s * nseg * 2 + dir) * fs + x;  // segment k at base + 2 k fs
+  Rec st;
+  st.hold(c, edge[((long)s * 2 + dir) * PW + x]);
+  constexpr int BATCH = 8;
+  for (int k0 = 0; k0 < nseg; k0 += BATCH) {
+    Rec e[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const int k = k0 + u;
+      if (k < nseg) e[u].load(base + 2L * (dir ? nseg - 1 - k : k) * fs, PW);
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const int k = k0 + u;
+      if (k >= nseg) break;
+      st.store(base + 2L * (dir ? nseg - 1 - k : k) * fs, PW);
+      Rec n = e[u];
+      n.combine_L(c, st);  // Phi^LC st + e
+      st = n;
+    }
   }
 }
 
@@ -494,7 +500,7 @@ int run_iir(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   a.prof->begin("iir_colseg", st);
   k_colseg<Rec><<<gs, 128, 0, st>>>(a.P, g.PW, g.H, g.W, a.edge, a.coef, a.carry, nseg);
   a.prof->end(st);
-  dim3 gf((g.W + 127) / 128, a.S);
+  dim3 gf((g.W + 127) / 128, a.S, 2);
   a.prof->begin("iir_colfold", st);
   k_colfold<Rec><<<gf, 128, 0, st>>>(g.W, g.PW, a.edge, a.coef, a.carry, nseg);
   a.prof->end(st);
