@@ -34,8 +34,8 @@ constexpr int RSEG = RNT * NOUT;     // outputs per row CTA (2048)
 constexpr int CNT = 128;             // threads per column CTA (4 warps x 32 columns)
 constexpr int CROWS = 4 * NOUT;      // output rows per column CTA (64, incl. 2 halo rows)
 constexpr int BOXW = 36;             // TMA box width (floats): 32 columns + alignment offset <= 3
-constexpr int BOXH = 16;             // TMA box height (rows)
-constexpr uint32_t WAIT_LIMIT = 1u << 24;
+constexpr int BOXH = 48;             // TMA box height (rows)
+constexpr uint32_t WAIT_LIMIT = 1u << 20;
 
 // taps h[0..K] padded with zeros to a multiple of TB beyond K
 __device__ __forceinline__ void stage_taps(float *sh, const Coef &c, int K, int tid, int nt) {
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
                                                         int taps_len, DetectArgs da) {
   extern __shared__ __align__(128) float sm_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
-  float *sm = align_smem(sm_raw);  // stages: multiples of BOXH rows x 144 B = 2304 B (18 x 128 B)
+  float *sm = align_smem(sm_raw);  // stages: multiples of 16 rows x 144 B = 2304 B (18 x 128 B)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   auto stage = [&](int b) { return sm + b * stage_rows * BOXW; };
   auto taps = [&](int b) { return sm + 2 * stage_rows * BOXW + b * taps_len; };
@@ -264,20 +264,24 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
       if (!tma_load_3d(stage(b) + i * BOXH * BOXW, &map, xa, r0 - G + i * BOXH, s, &mbar[b]))
         atomicExch(&da.status->error, 2);
   };
-  if (tid == 0) issue(0, 0);
+  // scales from the longest filter down (the order of the caller's scales is
+  // kept for ties: the first scale attaining an extreme is the one reported)
+  const int s_first = S - 1;
+  if (tid == 0) issue(s_first, 0);
   const long plane = (long)H * W;
-  for (int s = 0; s < S; ++s) {
-    const int b = s & 1;
-    if (tid == 0 && s + 1 < S) issue(s + 1, b ^ 1);
+  for (int it = 0; it < S; ++it) {
+    const int s = S - 1 - it;
+    const int b = it & 1;
+    if (tid == 0 && it + 1 < S) issue(s - 1, b ^ 1);
     const Coef &c = coef[s];
     const int K = c.K, G = K + TB, nin = CROWS2 + 2 * G;
     stage_taps(taps(b), c, K, tid, CNT2);
-    const bool ok = mbar_wait_bounded(&mbar[b], (uint32_t)((s >> 1) & 1), WAIT_LIMIT);
+    const bool ok = mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1), WAIT_LIMIT);
     if (__syncthreads_or(!ok)) {
       // a load never completed: report, let the other stage's load finish, stop
       if (tid == 0) {
         atomicExch(&da.status->error, 1);
-        if (s + 1 < S) mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)(((s + 1) >> 1) & 1), WAIT_LIMIT);
+        if (it + 1 < S) mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), WAIT_LIMIT);
       }
       __syncthreads();
       return;
@@ -300,8 +304,9 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
       const int i = NOUT * warp + j, y = r0 + i;
       if (!xin || y < 0 || y >= H) continue;
       const float v = ms2 * acc[j];
-      if (v > mxr[j]) mxr[j] = v, amx[i * 32 + lane] = (unsigned char)s;
-      if (v < mnr[j]) mnr[j] = v, amn[i * 32 + lane] = (unsigned char)s;
+      // scales arrive in decreasing order: >= keeps the smallest scale of a tie
+      if (v >= mxr[j]) mxr[j] = v, amx[i * 32 + lane] = (unsigned char)s;
+      if (v <= mnr[j]) mnr[j] = v, amn[i * 32 + lane] = (unsigned char)s;
       if (da.resp && i >= 1 && i <= CROWS2 - 2 && lane >= 1 && lane <= TW)
         da.resp[s * plane + (long)y * W + x] = v;
     }
@@ -384,7 +389,7 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   if (a.neigh == 0) {
     CUtensorMap map;
     if (encode_plane_map(&map, a.P, g.PW, g.H, a.S, BOXW, BOXH)) return -1;
-    const int stage_rows = (CROWS2 + 2 * G + BOXH - 1) / BOXH * BOXH;
+    const int stage_rows = (CROWS2 + 2 * G + BOXH - 1) / BOXH * BOXH;  // whole boxes; 144 B rows
     const int taps_len = (KP + 1 + 3) / 4 * 4;
     // two stages (>= 2 x 128 x 32 floats for the final extremes) + taps + first-scale bytes
     const size_t tsm = ((size_t)2 * stage_rows * BOXW + 2 * taps_len) * sizeof(float) + (size_t)CROWS2 * 32 * 2 +

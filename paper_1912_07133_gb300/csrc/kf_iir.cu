@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(128) k_colfold(int W, long PW, const float *__
 // registers, and R overwrites the input in place for the detector.
 constexpr int CLD = 36;
 constexpr int CNRP = 72;  // rows reserved per scale: 72 x 144 B = 81 x 128 B keeps every box 128-byte aligned
-constexpr uint32_t CWAIT_LIMIT = 1u << 24;
+constexpr uint32_t CWAIT_LIMIT = 1u << 20;
 
 template <class Rec>
 __global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUtensorMap map, long PW, int H,
