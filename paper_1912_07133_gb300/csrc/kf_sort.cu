@@ -52,27 +52,40 @@ __global__ void __launch_bounds__(SORT_NT) k_hist(const unsigned long long *__re
   hist[(long)tid * gridDim.x + blockIdx.x] = h[tid];
 }
 
-// exclusive scan of m entries, one block of 1024 threads
+// exclusive scan of m entries, one block of 1024 threads: rounds of 1024
+// consecutive (coalesced) entries, warp-shuffle scans, a carried prefix
 __global__ void __launch_bounds__(1024) k_scan(unsigned *__restrict__ a, long m) {
-  __shared__ unsigned part[1024];
-  const int tid = threadIdx.x;
-  const long per = (m + 1023) / 1024;
-  const long lo = tid * per, hi = min(m, lo + per);
-  unsigned s = 0;
-  for (long i = lo; i < hi; ++i) s += a[i];
-  part[tid] = s;
+  __shared__ unsigned wsum[32];
+  __shared__ unsigned carry;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) carry = 0;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    unsigned v = (tid >= off) ? part[tid - off] : 0u;
+  for (long r = 0; r < m; r += 1024) {
+    const long i = r + tid;
+    const unsigned v = i < m ? a[i] : 0u;
+    unsigned x = v;  // inclusive warp scan
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
     __syncthreads();
-    part[tid] += v;
+    if (w == 0) {
+      unsigned t = wsum[lane];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, t, d);
+        if (lane >= d) t += y;
+      }
+      wsum[lane] = t;  // inclusive over warps
+    }
     __syncthreads();
-  }
-  unsigned run = part[tid] - s;  // exclusive prefix of this thread's chunk
-  for (long i = lo; i < hi; ++i) {
-    const unsigned v = a[i];
-    a[i] = run;
-    run += v;
+    const unsigned before = carry + (w > 0 ? wsum[w - 1] : 0u) + x - v;
+    if (i < m) a[i] = before;
+    __syncthreads();
+    if (tid == 0) carry += wsum[31];
+    __syncthreads();
   }
 }
 
