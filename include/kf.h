@@ -42,16 +42,23 @@ extern "C" {
 #define KF_ERERUN -8     /* the context's candidate list overflowed during the
                             last bank call; its capacity has been raised: run
                             kf_filter_bank again (*count holds the need)       */
+#define KF_ERANGE -9     /* with f16 storage, a plane value exceeded 65504: the
+                            responses of that call are not finite; scale the
+                            input down (value_scale) or store bf16 / f32       */
 
 /* ---- enumerations -------------------------------------------------------- */
 #define KF_IIR_REPEATED_POLE 0 /* Filter D, Sec. 4.3 / Table IV                  */
 #define KF_IIR_BUTTERWORTH 1   /* Filter E, Sec. 4.4                             */
 #define KF_FIR_COLORED_SG 2    /* Filter C, Sec. 4.2                             */
 
+/* Element types.  Input frames: any of the four; each element is converted
+ * to f32 and multiplied by the frame's value_scale.  Intermediate planes
+ * (kf_bank_opts.storage): f32, f16 or bf16; every recursion, tap sum and
+ * response is computed in f32 whatever the storage. */
 #define KF_DTYPE_F32 0
-#define KF_DTYPE_F16 1
-#define KF_DTYPE_BF16 2
-#define KF_DTYPE_U16 3
+#define KF_DTYPE_F16 1  /* IEEE binary16                                       */
+#define KF_DTYPE_BF16 2 /* bfloat16                                            */
+#define KF_DTYPE_U16 3  /* unsigned 16-bit counts (input only)                 */
 
 #define KF_RESP_LAPLACIAN 0 /* R_L = -sigma^2 (D20 + D02)                        */
 #define KF_RESP_HESSIAN 1   /* R_H = sigma^4 (D20 D02 - D11^2), eq (26)          */
@@ -89,7 +96,7 @@ typedef struct {
 
 /* One input frame (device memory). */
 typedef struct {
-  const void *data;    /* device pointer, dtype elements                       */
+  const void *data;    /* device pointer, dtype elements, aligned to the element */
   int32_t width;       /* 1 .. 8192                                            */
   int32_t height;      /* >= 1                                                 */
   int64_t pitch;       /* elements between rows, >= width                      */
@@ -102,7 +109,12 @@ typedef struct {
   int32_t response;      /* KF_RESP_*                                          */
   int32_t boundary;      /* KF_BOUNDARY_HOLD (only hold is implemented)        */
   int32_t neighbourhood; /* KF_NEIGH_*                                         */
-  int32_t storage;       /* intermediate planes: KF_DTYPE_F32 / F16 / BF16     */
+  int32_t storage;       /* element type of the one-sided planes between the
+                            row and column passes: KF_DTYPE_F32 / F16 / BF16.
+                            16-bit planes halve their traffic; they hold
+                            sigma^2 x the row-blurred derivative, so their
+                            values have the magnitude of R at every scale.
+                            Responses and the detector stay f32.            */
   double threshold;      /* Threshold #1: |R| > threshold to be a candidate    */
   int32_t fir_kmax;      /* cap on the colored-SG half-length (0 -> 96)        */
   int32_t profile;       /* 1: record CUDA events around every kernel of the
@@ -186,7 +198,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes,
  * bank's opts->threshold.  Synchronises the context stream.
  * Errors: KF_EINVAL, KF_EOVERFLOW (capacity < *count; the first `capacity`
  * blobs are written), KF_ERERUN (the device-side candidate list of the last
- * call overflowed; capacity raised, run the bank again), KF_ECUDA. */
+ * call overflowed; capacity raised, run the bank again), KF_ERANGE (f16
+ * storage overflowed in the last call), KF_ETIMEOUT, KF_ECUDA. */
 int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out,
                     int64_t capacity, int64_t *count);
 

@@ -317,7 +317,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   if (opts.boundary != KF_BOUNDARY_HOLD) return fail(ctx, KF_EINVAL, "only the hold boundary is implemented");
   if (opts.neighbourhood != KF_NEIGH_ALL_SCALES && opts.neighbourhood != KF_NEIGH_ADJACENT)
     return fail(ctx, KF_EINVAL, "unknown neighbourhood %d", opts.neighbourhood);
-  if (opts.storage != KF_DTYPE_F32) return fail(ctx, KF_EINVAL, "only f32 storage is implemented");
+  if (opts.storage != KF_DTYPE_F32 && opts.storage != KF_DTYPE_F16 && opts.storage != KF_DTYPE_BF16)
+    return fail(ctx, KF_EINVAL, "storage must be f32, f16 or bf16");
   if (!(opts.threshold >= 0.0)) return fail(ctx, KF_EINVAL, "threshold must be >= 0");
   const int kmax_opt = opts.fir_kmax > 0 ? opts.fir_kmax : 96;
   if (kmax_opt > KF_MAX_FIR_K) return fail(ctx, KF_EINVAL, "fir_kmax must be <= %d", KF_MAX_FIR_K);
@@ -330,9 +331,12 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
       return fail(ctx, KF_EINVAL, "frame %d: bad geometry %dx%d pitch %lld", f, fr.width, fr.height,
                   (long long)fr.pitch);
     if (fr.width > 8192) return fail(ctx, KF_EINVAL, "frame %d: width > 8192", f);
-    if (fr.dtype != KF_DTYPE_F32) return fail(ctx, KF_EINVAL, "frame %d: only f32 input is implemented", f);
-    if (fr.value_scale != 0.0f && fr.value_scale != 1.0f)
-      return fail(ctx, KF_EINVAL, "frame %d: value_scale is only supported for u16 input", f);
+    if (fr.dtype != KF_DTYPE_F32 && fr.dtype != KF_DTYPE_F16 && fr.dtype != KF_DTYPE_BF16 &&
+        fr.dtype != KF_DTYPE_U16)
+      return fail(ctx, KF_EINVAL, "frame %d: unknown dtype %d", f, fr.dtype);
+    if (!std::isfinite(fr.value_scale)) return fail(ctx, KF_EINVAL, "frame %d: value_scale is not finite", f);
+    if ((reinterpret_cast<uintptr_t>(fr.data) & (uintptr_t)(kf::in_bytes(fr.dtype) - 1)) != 0)
+      return fail(ctx, KF_EINVAL, "frame %d: data is not aligned to its element size", f);
     const long PW = ((long)fr.width + 31) / 32 * 32;
     maxH = std::max(maxH, (long)fr.height);
     maxPW = std::max(maxPW, PW);
@@ -348,7 +352,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     kmax = std::max(kmax, ctx->cur->h_coef[s].K);
   }
   const int nf = (type == KF_IIR_BUTTERWORTH) ? 2 * nstate : nstate;
-  if ((rc = grow(ctx, &ctx->P, &ctx->P_floats, (size_t)nscales * maxplane, "planes"))) return rc;
+  const size_t plane_floats = ((size_t)nscales * maxplane * kf::store_bytes(opts.storage) + 3) / 4;
+  if ((rc = grow(ctx, &ctx->P, &ctx->P_floats, plane_floats, "planes"))) return rc;
   if ((rc = grow(ctx, &ctx->edge, &ctx->edge_floats, (size_t)nscales * 2 * maxPW, "edge rows"))) return rc;
   if (type != KF_FIR_COLORED_SG) {
     size_t need = 0;
@@ -369,6 +374,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   a.threshold = (float)opts.threshold;
   a.neigh = opts.neighbourhood;
   a.P = ctx->P;
+  a.storage = opts.storage;  // KF_DTYPE_F32 / F16 / BF16 equal ST_F32 / ST_F16 / ST_BF16
   a.edge = ctx->edge;
   a.carry = ctx->carry;
   a.blobs = ctx->blobs;
@@ -393,7 +399,9 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   for (int f = 0; f < nframes; ++f) {
     const kf_frame &fr = frames[f];
     kf::FrameGeom g;
-    g.X = static_cast<const float *>(fr.data);
+    g.X = fr.data;
+    g.dtype = fr.dtype;
+    g.vscale = fr.value_scale == 0.0f ? 1.0f : fr.value_scale;
     g.xpitch = fr.pitch;
     g.H = fr.height;
     g.W = fr.width;
@@ -468,6 +476,9 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
     return cuda_fail(ctx, e, "read status");
   if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "filter bank");
   if (st.error) return fail(ctx, KF_ETIMEOUT, "device wait gave up (code %d)", st.error);
+  if (st.range)
+    return fail(ctx, KF_ERANGE,
+                "a stored plane value exceeded the f16 range: scale the input (value_scale) or use bf16/f32 storage");
   if (st.count > (unsigned long long)ctx->blob_cap) {
     *count = (int64_t)st.count;
     // grow for the next call; this call's list is incomplete

@@ -1,6 +1,8 @@
 // kf_common.cuh -- device-side records and helpers shared by the product
 // kernels of the shape-filter bank (Kennedy, arXiv:1912.07133).
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -15,6 +17,64 @@ constexpr int WARPM = 32;        // powers Phi^(CH m), m = 1..32, for the row sc
 constexpr int MAX_FIR_K = 160;   // largest colored-SG half-length
 
 enum { T_D = 0, T_E = 1, T_C = 2 };
+
+// element types of input frames (same values as KF_DTYPE_*) and of the
+// one-sided planes between the row and column passes
+enum { IN_F32 = 0, IN_F16 = 1, IN_BF16 = 2, IN_U16 = 3 };
+enum { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
+
+template <int ST>
+struct Store;
+template <>
+struct Store<ST_F32> {
+  using T = float;
+  static __device__ __forceinline__ float ld(T v) { return v; }
+  static __device__ __forceinline__ T cv(float x) { return x; }
+};
+template <>
+struct Store<ST_F16> {
+  using T = __half;
+  static __device__ __forceinline__ float ld(T v) { return __half2float(v); }
+  static __device__ __forceinline__ T cv(float x) { return __float2half_rn(x); }
+};
+template <>
+struct Store<ST_BF16> {
+  using T = __nv_bfloat16;
+  static __device__ __forceinline__ float ld(T v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ T cv(float x) { return __float2bfloat16_rn(x); }
+};
+
+// largest finite f16 value: stored planes beyond it are reported, not clipped
+constexpr float F16_MAX = 65504.f;
+
+__host__ __device__ __forceinline__ int store_bytes(int st) { return st == ST_F32 ? 4 : 2; }
+__host__ __device__ __forceinline__ int in_bytes(int dt) { return dt == IN_F32 ? 4 : 2; }
+
+// element e of an input row (any input type) times the frame's value scale
+__device__ __forceinline__ float load_in(const void *row, int e, int dt, float vs) {
+  switch (dt) {
+    case IN_F16: return vs * __half2float(__ldg(static_cast<const __half *>(row) + e));
+    case IN_BF16: return vs * __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(row) + e));
+    case IN_U16: return vs * (float)__ldg(static_cast<const unsigned short *>(row) + e);
+    default: return vs * __ldg(static_cast<const float *>(row) + e);
+  }
+}
+
+// element i of a one-sided plane buffer of storage type st
+__device__ __forceinline__ float load_plane(const void *P, long i, int st) {
+  switch (st) {
+    case ST_F16: return __half2float(__ldg(static_cast<const __half *>(P) + i));
+    case ST_BF16: return __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(P) + i));
+    default: return __ldg(static_cast<const float *>(P) + i);
+  }
+}
+__device__ __forceinline__ void store_plane(void *P, long i, int st, float v) {
+  switch (st) {
+    case ST_F16: static_cast<__half *>(P)[i] = __float2half_rn(v); break;
+    case ST_BF16: static_cast<__nv_bfloat16 *>(P)[i] = __float2bfloat16_rn(v); break;
+    default: static_cast<float *>(P)[i] = v;
+  }
+}
 
 // Per-scale realisation of one designed blur.  Written by the FP64 design
 // kernel; read by the filter kernels.  All recursive realisations are sums of
@@ -62,7 +122,7 @@ struct Blob {
 struct DevStatus {
   unsigned long long count;  // candidates found (may exceed capacity)
   int error;                 // first error code seen by a kernel
-  int pad;
+  int range;                 // 1: a value exceeded the range of 16-bit (f16) plane storage
 };
 
 }  // namespace kf

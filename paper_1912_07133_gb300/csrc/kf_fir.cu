@@ -114,9 +114,10 @@ __device__ __forceinline__ void fir_row_block(const float *sh, int K, const floa
 __host__ __device__ __forceinline__ int row_halo(int kmax) { return (kmax + TB + 15) / 16 * 16; }
 
 template <bool EDGE>
-__global__ void __launch_bounds__(RNT) k_rowfir(const float *__restrict__ X, long xpitch, int H, int W,
-                                                const Coef *__restrict__ coef, int S, int kmax,
-                                                float *__restrict__ P, long PW, float *__restrict__ edge) {
+__global__ void __launch_bounds__(RNT) k_rowfir(const void *__restrict__ X, long xpitch, int dt, float vs, int H,
+                                                int W, const Coef *__restrict__ coef, int S, int kmax,
+                                                void *__restrict__ P, int st, long PW,
+                                                float *__restrict__ edge, DevStatus *__restrict__ status) {
   extern __shared__ __align__(16) float sm[];
   const int tid = threadIdx.x;
   const int y = EDGE ? (blockIdx.y == 0 ? 0 : H - 1) : blockIdx.y;
@@ -127,24 +128,27 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const float *__restrict__ X, lon
   const int n = RSEG + 2 * G;
   float *sL = sm;                       // padded: element j at pad20(j)
   float *sh = sm + pad20(n) + 4;
-  const float *rm = X + (long)max(y - 1, 0) * xpitch;
-  const float *r0 = X + (long)y * xpitch;
-  const float *rp = X + (long)min(y + 1, H - 1) * xpitch;
-  const float vlo = __ldg(rp) - 2.f * __ldg(r0) + __ldg(rm);
-  const float vhi = __ldg(rp + W - 1) - 2.f * __ldg(r0 + W - 1) + __ldg(rm + W - 1);
+  const int eb = in_bytes(dt);
+  const void *rm = static_cast<const char *>(X) + (long)max(y - 1, 0) * xpitch * eb;
+  const void *r0 = static_cast<const char *>(X) + (long)y * xpitch * eb;
+  const void *rp = static_cast<const char *>(X) + (long)min(y + 1, H - 1) * xpitch * eb;
+  auto ld = [&](const void *row, int e) { return load_in(row, e, dt, vs); };
+  const float vlo = ld(rp, 0) - 2.f * ld(r0, 0) + ld(rm, 0);
+  const float vhi = ld(rp, W - 1) - 2.f * ld(r0, W - 1) + ld(rm, W - 1);
   for (int j = tid; j < n; j += RNT) {
     const int e = xs - G + j;
     float v;
     if (e < 0) v = EDGE ? 0.f : vlo;
     else if (e >= W) v = EDGE ? 0.f : vhi;
     else {
-      const float c0 = __ldg(r0 + e);
-      const float u = __ldg(r0 + min(e + 1, W - 1)) - 2.f * c0 + __ldg(r0 + max(e - 1, 0));
-      v = EDGE ? u : u + (__ldg(rp + e) - 2.f * c0 + __ldg(rm + e));
+      const float c0 = ld(r0, e);
+      const float u = ld(r0, min(e + 1, W - 1)) - 2.f * c0 + ld(r0, max(e - 1, 0));
+      v = EDGE ? u : u + (ld(rp, e) - 2.f * c0 + ld(rm, e));
     }
     sL[pad20(j)] = v;
   }
   const int base = G + NOUT * tid;  // local index of this thread's first output
+  bool ovf = false;                 // a value beyond the f16 range
   for (int s = 0; s < S; ++s) {
     const Coef &c = coef[s];
     const int K = c.K;
@@ -153,21 +157,52 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const float *__restrict__ X, lon
     __syncthreads();
     float acc[NOUT];
     fir_row_block(sh, K, sL, base, acc);
-    float *dst = EDGE ? edge + ((long)s * 2 + blockIdx.y) * PW : P + (long)s * H * PW + (long)y * PW;
+    // planes hold sigma^2 x the one-sided blur (the column pass only negates)
+    const float s2 = c.sigma2;
+#pragma unroll
+    for (int j = 0; j < NOUT; ++j) acc[j] *= s2;
     const int x0 = xs + NOUT * tid;
-    if (x0 + NOUT <= W) {
+    const long row = (long)s * H * PW + (long)y * PW;
+    if (EDGE || st == ST_F32) {
+      float *dst = EDGE ? edge + ((long)s * 2 + blockIdx.y) * PW : static_cast<float *>(P) + row;
+      if (x0 + NOUT <= W) {
 #pragma unroll
-      for (int j = 0; j < NOUT; j += 4)
-        *reinterpret_cast<float4 *>(dst + x0 + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+        for (int j = 0; j < NOUT; j += 4)
+          *reinterpret_cast<float4 *>(dst + x0 + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j)
+          if (x0 + j < W) dst[x0 + j] = acc[j];
+      }
     } else {
+      // 16-bit planes: four values per 8-byte store
+      unsigned short *dst = static_cast<unsigned short *>(P) + row;
+      unsigned short h[NOUT];
 #pragma unroll
-      for (int j = 0; j < NOUT; ++j)
-        if (x0 + j < W) dst[x0 + j] = acc[j];
+      for (int j = 0; j < NOUT; ++j) {
+        if (st == ST_F16) {
+          ovf |= x0 + j < W && fabsf(acc[j]) > F16_MAX;
+          h[j] = __half_as_ushort(__float2half_rn(acc[j]));
+        } else {
+          h[j] = __bfloat16_as_ushort(__float2bfloat16_rn(acc[j]));
+        }
+      }
+      if (x0 + NOUT <= W) {
+#pragma unroll
+        for (int j = 0; j < NOUT; j += 4)
+          *reinterpret_cast<uint2 *>(dst + x0 + j) =
+              make_uint2(h[j] | ((unsigned)h[j + 1] << 16), h[j + 2] | ((unsigned)h[j + 3] << 16));
+      } else {
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j)
+          if (x0 + j < W) dst[x0 + j] = h[j];
+      }
     }
   }
+  if (ovf) atomicExch(&status->range, 1);
 }
 
-__global__ void __launch_bounds__(CNT) k_colfir(const float *__restrict__ P, long PW, int H, int W,
+__global__ void __launch_bounds__(CNT) k_colfir(const void *__restrict__ P, int st, long PW, int H, int W,
                                                 const float *__restrict__ edge,
                                                 const Coef *__restrict__ coef, int S, int kmax,
                                                 DetectArgs da) {
@@ -185,22 +220,21 @@ __global__ void __launch_bounds__(CNT) k_colfir(const float *__restrict__ P, lon
   for (int s = 0; s < S; ++s) {
     const Coef &c = coef[s];
     const int K = c.K;
-    const float *Pc = P + (long)s * H * PW + xv;
+    const long pc = (long)s * H * PW + xv;
     const float top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
     __syncthreads();
     stage_taps(sh, c, K, threadIdx.x, CNT);
     // in[j] = input row r0 - G + j
     for (int j = warp; j < NIN; j += CNT / 32) {
       const int r = r0 - G + j;
-      in[j * 32 + lane] = r < 0 ? top : (r >= H ? bot : __ldg(Pc + (long)r * PW));
+      in[j * 32 + lane] = r < 0 ? top : (r >= H ? bot : load_plane(P, pc + (long)r * PW, st));
     }
     __syncthreads();
     const float *col = in + lane + (G + NOUT * warp) * 32;  // output row NOUT*warp
     float acc[NOUT];
     fir_block(sh, K, [&](int t) { return col[t * 32]; }, acc);
-    const float ms2 = -c.sigma2;
 #pragma unroll
-    for (int j = 0; j < NOUT; ++j) buf[((long)s * CROWS + NOUT * warp + j) * 32 + lane] = ms2 * acc[j];
+    for (int j = 0; j < NOUT; ++j) buf[((long)s * CROWS + NOUT * warp + j) * 32 + lane] = -acc[j];
   }
   __syncthreads();
   DetectArgs a = da;
@@ -213,29 +247,49 @@ __global__ void __launch_bounds__(CNT) k_colfir(const float *__restrict__ P, lon
 
 // Column FIR + detector, all-scales neighbourhood.  A CTA of 8 warps covers
 // 32 columns x 128 rows (row 0 and row 127 are halo); per scale the input
-// block (128 + 2(K+8) rows x 36 columns of the one-sided plane) arrives by TMA
-// into one of two shared-memory stages while the previous scale is filtered;
-// rows outside the frame are then set to the held values.  Each thread keeps
-// the running maximum / minimum over scales of its 16 pixels in registers
-// (their first scale in shared memory); the spatial 3 x 3 test runs once at
-// the end on those extremes.
+// block (128 + 2(K+8) rows of the one-sided plane) arrives by TMA while an
+// earlier scale is filtered; rows outside the frame take the held values.
+// Each thread keeps the running maximum / minimum over scales of its 16
+// pixels in registers (their first scale in shared memory); the spatial
+// 3 x 3 test runs once at the end on those extremes.
+//
+// f32 planes: two stages of 36-float rows (x a multiple of 4 floats), the
+// filter reads the stage itself after the held rows are written into it.
+// 16-bit planes: two landing stages of 40-element rows (x a multiple of 8
+// elements); each is widened once into one f32 work tile of 32-float rows,
+// after which its next scale (two ahead) is issued.
 constexpr int CNT2 = 256;
 constexpr int CROWS2 = 8 * NOUT;  // 128
+constexpr int BOXW16 = 40;        // 16-bit box width (elements): 32 columns + alignment offset <= 7
 
+// floats of the stages (f32: 2 stages; 16-bit: 2 landing stages + work tile)
+template <int ST>
+__host__ __device__ constexpr int colfir_stage_floats(int stage_rows) {
+  return ST == ST_F32 ? 2 * stage_rows * BOXW : stage_rows * BOXW16 + stage_rows * 32;
+}
+
+template <int ST>
 __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ CUtensorMap map,
                                                         const float *__restrict__ edge, long PW, int H, int W,
                                                         const Coef *__restrict__ coef, int S, int stage_rows,
                                                         int taps_len, DetectArgs da) {
+  using T = typename Store<ST>::T;
+  constexpr bool F32 = ST == ST_F32;
+  constexpr int BW = F32 ? BOXW : BOXW16;  // box width (elements)
+  constexpr int XA = F32 ? 4 : 8;          // TMA x alignment (elements)
+  constexpr int LDW = F32 ? BOXW : 32;     // row stride of the f32 tile the filter reads
   extern __shared__ __align__(128) float sm_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
-  float *sm = align_smem(sm_raw);  // stages: multiples of 16 rows x 144 B = 2304 B (18 x 128 B)
+  float *sm = align_smem(sm_raw);  // boxes: 48 rows x 144 B (f32) or x 80 B (16-bit), multiples of 128 B
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  auto stage = [&](int b) { return sm + b * stage_rows * BOXW; };
-  auto taps = [&](int b) { return sm + 2 * stage_rows * BOXW + b * taps_len; };
-  unsigned char *amx = reinterpret_cast<unsigned char *>(sm + 2 * stage_rows * BOXW + 2 * taps_len);
+  auto land = [&](int b) { return reinterpret_cast<T *>(sm) + (long)b * stage_rows * BW; };
+  float *work = sm + stage_rows * BOXW16;  // 16-bit planes only
+  const int SF = colfir_stage_floats<ST>(stage_rows);
+  auto taps = [&](int b) { return sm + SF + b * taps_len; };
+  unsigned char *amx = reinterpret_cast<unsigned char *>(sm + SF + 2 * taps_len);
   unsigned char *amn = amx + CROWS2 * 32;
-  const int x0 = blockIdx.x * TW - 1;       // frame column of lane 0
-  const int off = ((x0 % 4) + 4) % 4;       // TMA x must be a multiple of 4 floats
+  const int x0 = blockIdx.x * TW - 1;  // frame column of lane 0
+  const int off = ((x0 % XA) + XA) % XA;
   const int xa = x0 - off;
   const int r0 = blockIdx.y * (CROWS2 - 2) - 1;  // frame row of output row 0
   const int x = x0 + lane, xv = min(max(x, 0), W - 1);
@@ -259,20 +313,22 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
     const int G = coef[s].K + TB;
     const int nb = (CROWS2 + 2 * G + BOXH - 1) / BOXH;
     fence_proxy_async();
-    mbar_arrive_expect_tx(&mbar[b], (uint32_t)(nb * BOXH * BOXW * sizeof(float)));
+    mbar_arrive_expect_tx(&mbar[b], (uint32_t)(nb * BOXH * BW * sizeof(T)));
     for (int i = 0; i < nb; ++i)
-      if (!tma_load_3d(stage(b) + i * BOXH * BOXW, &map, xa, r0 - G + i * BOXH, s, &mbar[b]))
+      if (!tma_load_3d(land(b) + i * BOXH * BW, &map, xa, r0 - G + i * BOXH, s, &mbar[b], (int)sizeof(T)))
         atomicExch(&da.status->error, 2);
   };
   // scales from the longest filter down (the order of the caller's scales is
   // kept for ties: the first scale attaining an extreme is the one reported)
-  const int s_first = S - 1;
-  if (tid == 0) issue(s_first, 0);
+  if (tid == 0) {
+    issue(S - 1, 0);
+    if (!F32 && S > 1) issue(S - 2, 1);
+  }
   const long plane = (long)H * W;
   for (int it = 0; it < S; ++it) {
     const int s = S - 1 - it;
     const int b = it & 1;
-    if (tid == 0 && it + 1 < S) issue(s - 1, b ^ 1);
+    if (F32 && tid == 0 && it + 1 < S) issue(s - 1, b ^ 1);
     const Coef &c = coef[s];
     const int K = c.K, G = K + TB, nin = CROWS2 + 2 * G;
     stage_taps(taps(b), c, K, tid, CNT2);
@@ -286,24 +342,40 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
       __syncthreads();
       return;
     }
-    if (r0 - G < 0 || r0 + CROWS2 + G > H) {  // rows outside the frame: held values
-      const float top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
+    const bool outside = r0 - G < 0 || r0 + CROWS2 + G > H;
+    float top = 0.f, bot = 0.f;
+    if (outside) top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
+    const float *tile;
+    if constexpr (F32) {
+      float *st = land(b);
+      if (outside) {  // rows outside the frame: held values
+        for (int j = warp; j < nin; j += CNT2 / 32) {
+          const int r = r0 - G + j;
+          if (r < 0) st[j * BOXW + off + lane] = top;
+          else if (r >= H) st[j * BOXW + off + lane] = bot;
+        }
+      }
+      tile = st + off;
+      __syncthreads();
+    } else {
+      const T *src = land(b) + off + lane;
       for (int j = warp; j < nin; j += CNT2 / 32) {
         const int r = r0 - G + j;
-        if (r < 0) stage(b)[j * BOXW + off + lane] = top;
-        else if (r >= H) stage(b)[j * BOXW + off + lane] = bot;
+        const float v = Store<ST>::ld(src[j * BW]);
+        work[j * 32 + lane] = r < 0 ? top : (r >= H ? bot : v);
       }
+      tile = work;
+      __syncthreads();  // landing stage b is free again
+      if (tid == 0 && it + 2 < S) issue(s - 2, b);
     }
-    __syncthreads();
-    const float *col = stage(b) + (G + NOUT * warp) * BOXW + off + lane;
+    const float *col = tile + (G + NOUT * warp) * LDW + lane;
     float acc[NOUT];
-    fir_block(taps(b), K, [&](int t) { return col[t * BOXW]; }, acc);
-    const float ms2 = -c.sigma2;
+    fir_block(taps(b), K, [&](int t) { return col[t * LDW]; }, acc);
 #pragma unroll
     for (int j = 0; j < NOUT; ++j) {
       const int i = NOUT * warp + j, y = r0 + i;
       if (!xin || y < 0 || y >= H) continue;
-      const float v = ms2 * acc[j];
+      const float v = -acc[j];  // R_L = -sigma^2 (D20 + D02); planes carry sigma^2
       // scales arrive in decreasing order: >= keeps the smallest scale of a tie
       if (v >= mxr[j]) mxr[j] = v, amx[i * 32 + lane] = (unsigned char)s;
       if (v <= mnr[j]) mnr[j] = v, amn[i * 32 + lane] = (unsigned char)s;
@@ -329,10 +401,33 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
   spatial_detect(mx, mn, amx, amn, a);
 }
 
+template <int ST>
+int launch_colfir_tma(const FrameGeom &g, const BankArgs &a, const DetectArgs &da, int G, int KP,
+                      cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_colfir_tma<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr = true;
+  }
+  CUtensorMap map;
+  if (encode_plane_map(&map, a.P, ST, g.PW, g.H, a.S, ST == ST_F32 ? BOXW : BOXW16, BOXH)) return -1;
+  const int stage_rows = (CROWS2 + 2 * G + BOXH - 1) / BOXH * BOXH;  // whole boxes
+  const int taps_len = (KP + 1 + 3) / 4 * 4;
+  const int SF = colfir_stage_floats<ST>(stage_rows);
+  // stages (>= 2 x 128 x 32 floats for the final extremes) + taps + first-scale bytes
+  const size_t tsm = ((size_t)SF + 2 * taps_len) * sizeof(float) + (size_t)CROWS2 * 32 * 2 + TMA_SMEM_ALIGN;
+  if (tsm > 220 * 1024 || SF < 2 * CROWS2 * 32) return -1;
+  dim3 gt((g.W + TW - 1) / TW, (g.H + CROWS2 - 3) / (CROWS2 - 2));
+  a.prof->begin("fir_coldet", st);
+  k_colfir_tma<ST><<<gt, CNT2, tsm, st>>>(map, a.edge, g.PW, g.H, g.W, a.coef, a.S, stage_rows, taps_len, da);
+  a.prof->end(st);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 }  // namespace
 
 // 3-D tensor map over the S one-sided planes (x, y, scale), box boxw x boxh x 1
-int encode_plane_map(CUtensorMap *m, float *P, long PW, int H, int S, int boxw, int boxh) {
+int encode_plane_map(CUtensorMap *m, void *P, int storage, long PW, int H, int S, int boxw, int boxh) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -343,10 +438,14 @@ int encode_plane_map(CUtensorMap *m, float *P, long PW, int H, int S, int boxw, 
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   const cuuint64_t dims[3] = {(cuuint64_t)PW, (cuuint64_t)H, (cuuint64_t)S};
-  const cuuint64_t strides[2] = {(cuuint64_t)PW * sizeof(float), (cuuint64_t)H * PW * sizeof(float)};
+  const cuuint64_t eb = (cuuint64_t)store_bytes(storage);
+  const cuuint64_t strides[2] = {(cuuint64_t)PW * eb, (cuuint64_t)H * PW * eb};
   const cuuint32_t box[3] = {(cuuint32_t)boxw, (cuuint32_t)boxh, 1};
   const cuuint32_t es[3] = {1, 1, 1};
-  const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P, dims, strides, box, es,
+  const CUtensorMapDataType ty = storage == ST_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : storage == ST_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUresult r = encode(m, ty, 3, P, dims, strides, box, es,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -1;
@@ -358,7 +457,6 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
     cudaFuncSetAttribute(k_rowfir<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_rowfir<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_colfir, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    cudaFuncSetAttribute(k_colfir_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr = true;
   }
   const int kmax = a.kmax;
@@ -368,11 +466,13 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   const size_t rsm = (size_t)(pad20(RSEG + 2 * RG) + 4 + KP + 1) * sizeof(float);
   dim3 gr((g.W + RSEG - 1) / RSEG, g.H);
   a.prof->begin("fir_row", st);
-  k_rowfir<false><<<gr, RNT, rsm, st>>>(g.X, g.xpitch, g.H, g.W, a.coef, a.S, kmax, a.P, g.PW, a.edge);
+  k_rowfir<false><<<gr, RNT, rsm, st>>>(g.X, g.xpitch, g.dtype, g.vscale, g.H, g.W, a.coef, a.S, kmax, a.P,
+                                        a.storage, g.PW, a.edge, a.status);
   a.prof->end(st);
   dim3 ge((g.W + RSEG - 1) / RSEG, 2);
   a.prof->begin("fir_row_edge", st);
-  k_rowfir<true><<<ge, RNT, rsm, st>>>(g.X, g.xpitch, g.H, g.W, a.coef, a.S, kmax, a.P, g.PW, a.edge);
+  k_rowfir<true><<<ge, RNT, rsm, st>>>(g.X, g.xpitch, g.dtype, g.vscale, g.H, g.W, a.coef, a.S, kmax, a.P,
+                                       a.storage, g.PW, a.edge, a.status);
   a.prof->end(st);
   DetectArgs da;
   da.H = g.H;
@@ -385,28 +485,21 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   da.cap = a.cap;
   da.status = a.status;
   da.resp = a.responses ? a.responses + g.resp_off : nullptr;
-  dim3 gc((g.W + TW - 1) / TW, (g.H + CROWS - 3) / (CROWS - 2));
   if (a.neigh == 0) {
-    CUtensorMap map;
-    if (encode_plane_map(&map, a.P, g.PW, g.H, a.S, BOXW, BOXH)) return -1;
-    const int stage_rows = (CROWS2 + 2 * G + BOXH - 1) / BOXH * BOXH;  // whole boxes; 144 B rows
-    const int taps_len = (KP + 1 + 3) / 4 * 4;
-    // two stages (>= 2 x 128 x 32 floats for the final extremes) + taps + first-scale bytes
-    const size_t tsm = ((size_t)2 * stage_rows * BOXW + 2 * taps_len) * sizeof(float) + (size_t)CROWS2 * 32 * 2 +
-                       TMA_SMEM_ALIGN;
-    if (tsm > 220 * 1024 || 2 * stage_rows * BOXW < 2 * CROWS2 * 32) return -1;
-    dim3 gt((g.W + TW - 1) / TW, (g.H + CROWS2 - 3) / (CROWS2 - 2));
-    a.prof->begin("fir_coldet", st);
-    k_colfir_tma<<<gt, CNT2, tsm, st>>>(map, a.edge, g.PW, g.H, g.W, a.coef, a.S, stage_rows, taps_len, da);
-    a.prof->end(st);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    switch (a.storage) {
+      case ST_F32: return launch_colfir_tma<ST_F32>(g, a, da, G, KP, st);
+      case ST_F16: return launch_colfir_tma<ST_F16>(g, a, da, G, KP, st);
+      case ST_BF16: return launch_colfir_tma<ST_BF16>(g, a, da, G, KP, st);
+      default: return -2;
+    }
   }
   // in + buf + detector scratch (2 float planes + 2 byte planes) + taps
   const size_t csm = ((size_t)(CROWS + 2 * G) * 32 + (size_t)a.S * CROWS * 32 + (size_t)CROWS * 32 * 2 +
                       (size_t)CROWS * 32 * 2 / 4 + KP + 1) * sizeof(float);
   if (csm > 220 * 1024) return -1;
+  dim3 gc((g.W + TW - 1) / TW, (g.H + CROWS - 3) / (CROWS - 2));
   a.prof->begin("fir_coldet", st);
-  k_colfir<<<gc, CNT, csm, st>>>(a.P, g.PW, g.H, g.W, a.edge, a.coef, a.S, kmax, da);
+  k_colfir<<<gc, CNT, csm, st>>>(a.P, a.storage, g.PW, g.H, g.W, a.edge, a.coef, a.S, kmax, da);
   a.prof->end(st);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

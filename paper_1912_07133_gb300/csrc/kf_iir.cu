@@ -238,23 +238,29 @@ __host__ __device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
 // ---------------------------------------------------------------------------
 // row pass
 // ---------------------------------------------------------------------------
+// row i of the input frame (any element type)
+__device__ __forceinline__ const void *in_row(const void *X, long xpitch, int i, int dt) {
+  return static_cast<const char *>(X) + (long)i * xpitch * in_bytes(dt);
+}
+
 template <class Rec, bool EDGE>
-__global__ void __launch_bounds__(256) k_row(const float *__restrict__ X, long xpitch, int H, int W,
-                                             const Coef *__restrict__ coef, int S,
-                                             float *__restrict__ P, long PW, float *__restrict__ edge) {
+__global__ void __launch_bounds__(256) k_row(const void *__restrict__ X, long xpitch, int dt, float vs, int H,
+                                             int W, const Coef *__restrict__ coef, int S, void *__restrict__ P,
+                                             int st, long PW, float *__restrict__ edge,
+                                             DevStatus *__restrict__ status) {
   extern __shared__ float sm[];
   const int NT = blockDim.x, tid = threadIdx.x;
   const int RP = pad32(NT * CH) + 1;
   float *s_m = sm, *s_0 = sm + RP, *s_p = sm + 2 * RP, *s_scan = sm + 3 * RP;
   const int y = EDGE ? (blockIdx.x == 0 ? 0 : H - 1) : blockIdx.x;
-  const float *rm = X + (long)max(y - 1, 0) * xpitch;
-  const float *r0 = X + (long)y * xpitch;
-  const float *rp = X + (long)min(y + 1, H - 1) * xpitch;
+  const void *rm = in_row(X, xpitch, max(y - 1, 0), dt);
+  const void *r0 = in_row(X, xpitch, y, dt);
+  const void *rp = in_row(X, xpitch, min(y + 1, H - 1), dt);
   for (int e = tid; e < W; e += NT) {
     const int a = pad32(e);
-    s_m[a] = __ldg(rm + e);
-    s_0[a] = __ldg(r0 + e);
-    s_p[a] = __ldg(rp + e);
+    s_m[a] = load_in(rm, e, dt, vs);
+    s_0[a] = load_in(r0, e, dt, vs);
+    s_p[a] = load_in(rp, e, dt, vs);
   }
   __syncthreads();
   const float v_lo = s_p[0] - 2.f * s_0[0] + s_m[0];
@@ -277,6 +283,7 @@ __global__ void __launch_bounds__(256) k_row(const float *__restrict__ X, long x
   const float in_lo = EDGE ? 0.f : v_lo, in_hi = EDGE ? 0.f : v_hi;
   __syncthreads();
   float *s_out = sm;
+  bool ovf = false;  // a value beyond the f16 range
   for (int s = 0; s < S; ++s) {
     const Coef &c = coef[s];
     typename Rec::View v;
@@ -306,13 +313,34 @@ __global__ void __launch_bounds__(256) k_row(const float *__restrict__ X, long x
       yv[i] += fmaf(v.b0, L[i], r.out(v));
       r.push(v, L[i]);
     }
+    // planes hold sigma^2 x the one-sided blur: the column pass then only
+    // negates (R_L = -sigma^2 (D20 + D02)), and 16-bit planes keep the
+    // magnitude of R at every scale
+    const float s2 = c.sigma2;
 #pragma unroll
-    for (int i = 0; i < CH; ++i) s_out[pad32(x0 + i)] = yv[i];
+    for (int i = 0; i < CH; ++i) s_out[pad32(x0 + i)] = s2 * yv[i];
     __syncthreads();
-    float *dst = EDGE ? edge + ((long)s * 2 + blockIdx.x) * PW : P + (long)s * H * PW + (long)y * PW;
-    for (int e = tid; e < W; e += NT) dst[e] = s_out[pad32(e)];
+    const long row = EDGE ? 0 : (long)s * H * PW + (long)y * PW;
+    if (EDGE) {
+      float *dst = edge + ((long)s * 2 + blockIdx.x) * PW;
+      for (int e = tid; e < W; e += NT) dst[e] = s_out[pad32(e)];
+    } else if (st == ST_F32) {
+      float *dst = static_cast<float *>(P) + row;
+      for (int e = tid; e < W; e += NT) dst[e] = s_out[pad32(e)];
+    } else if (st == ST_F16) {
+      __half *dst = static_cast<__half *>(P) + row;
+      for (int e = tid; e < W; e += NT) {
+        const float val = s_out[pad32(e)];
+        ovf |= fabsf(val) > F16_MAX;
+        dst[e] = __float2half_rn(val);
+      }
+    } else {
+      __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(P) + row;
+      for (int e = tid; e < W; e += NT) dst[e] = __float2bfloat16_rn(s_out[pad32(e)]);
+    }
     __syncthreads();
   }
+  if (ovf) atomicExch(&status->range, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -320,13 +348,15 @@ __global__ void __launch_bounds__(256) k_row(const float *__restrict__ X, long x
 // ---------------------------------------------------------------------------
 // input of the column recursion at row r (phantom rows use the held one-sided
 // rows of U at the frame's first/last row)
-__device__ __forceinline__ float col_in(const float *Pc, long PW, int r, int H, float top, float bot) {
-  return r < 0 ? top : (r >= H ? bot : __ldg(Pc + (long)r * PW));
+template <int ST>
+__device__ __forceinline__ float col_in(const typename Store<ST>::T *Pc, long PW, int r, int H, float top,
+                                        float bot) {
+  return r < 0 ? top : (r >= H ? bot : Store<ST>::ld(Pc[(long)r * PW]));
 }
 
-template <class Rec>
-__global__ void __launch_bounds__(128) k_colseg(const float *__restrict__ P, long PW, int H, int W,
-                                                const float *__restrict__ edge,
+template <class Rec, int ST>
+__global__ void __launch_bounds__(128) k_colseg(const typename Store<ST>::T *__restrict__ P, long PW, int H,
+                                                int W, const float *__restrict__ edge,
                                                 const Coef *__restrict__ coef, float *__restrict__ E,
                                                 int nseg) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -334,14 +364,14 @@ __global__ void __launch_bounds__(128) k_colseg(const float *__restrict__ P, lon
   const int c = blockIdx.y, s = blockIdx.z;
   typename Rec::View v;
   v.load(coef[s]);
-  const float *Pc = P + (long)s * H * PW + x;
+  const typename Store<ST>::T *Pc = P + (long)s * H * PW + x;
   const float top = edge[((long)s * 2 + 0) * PW + x], bot = edge[((long)s * 2 + 1) * PW + x];
   Rec r;
   r.zero();
   // causal segment: rows [c LC - 1, (c+1) LC - 1)
   const int rf = c * LC - 1;
 #pragma unroll 8
-  for (int i = 0; i < LC; ++i) r.push(v, col_in(Pc, PW, rf + i, H, top, bot));
+  for (int i = 0; i < LC; ++i) r.push(v, col_in<ST>(Pc, PW, rf + i, H, top, bot));
   const long fs = (long)Rec::NF * PW;
   float *Ef = E + (((long)s * nseg + c) * 2 + 0) * fs + x;
   r.store(Ef, PW);
@@ -349,7 +379,7 @@ __global__ void __launch_bounds__(128) k_colseg(const float *__restrict__ P, lon
   r.zero();
   const int rb = (c + 1) * LC;
 #pragma unroll 8
-  for (int i = 0; i < LC; ++i) r.push(v, col_in(Pc, PW, rb - i, H, top, bot));
+  for (int i = 0; i < LC; ++i) r.push(v, col_in<ST>(Pc, PW, rb - i, H, top, bot));
   r.store(Ef + fs, PW);
 }
 
@@ -391,30 +421,54 @@ __global__ void __launch_bounds__(128) k_colfold(int W, long PW, const float *__
 
 // Column pass + detector.  One CTA per (32-column, LC+2-row) tile, one warp
 // per scale, one thread per (column, scale).  The tile of every scale's
-// one-sided plane arrives by TMA into shared memory (box 36 x 66: the TMA x
-// coordinate must be a multiple of 4 floats, so the tile starts up to 3
-// columns early); rows outside the frame are then set to the held values.
-// Both recursions run from shared memory, the causal outputs stay in
-// registers, and R overwrites the input in place for the detector.
+// one-sided plane arrives by TMA into shared memory; rows outside the frame
+// take the held values.  Both recursions run from shared memory, the causal
+// outputs stay in registers, and R overwrites the input in place for the
+// detector.
+//
+// f32 planes: box 36 x 66 (the TMA x coordinate must be a multiple of 4
+// floats, so the tile starts up to 3 columns early), rows of 36 floats.
+// 16-bit planes: box 40 x 66 (x a multiple of 8 elements) lands at byte C16B
+// of the scale's region; the causal pass widens it row by row into f32 rows
+// of 32 floats from the region's start.  f32 row i ends at 128 (i + 1) and
+// 16-bit row j starts at C16B + 80 j, so with the warp synchronised every 8
+// rows no write reaches a 16-bit row that is still to be read.
 constexpr int CLD = 36;
 constexpr int CNRP = 72;  // rows reserved per scale: 72 x 144 B = 81 x 128 B keeps every box 128-byte aligned
+constexpr int CBOX16 = 40;         // 16-bit box width (elements)
+constexpr int C16B = 3712;         // byte offset of the 16-bit box in its region (29 x 128)
+constexpr int C16REG = 9472;       // bytes per scale region, 16-bit planes (74 x 128)
 constexpr uint32_t CWAIT_LIMIT = 1u << 20;
 
-template <class Rec>
+template <int ST>
+__host__ __device__ constexpr int coldet_region_floats() {
+  return ST == ST_F32 ? CNRP * CLD : C16REG / 4;
+}
+
+template <class Rec, int ST>
 __global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUtensorMap map, long PW, int H,
                                                 int W, const float *__restrict__ edge,
                                                 const Coef *__restrict__ coef, int S,
                                                 const float *__restrict__ E, int nseg, DetectArgs da) {
+  using T = typename Store<ST>::T;
+  constexpr bool F32 = ST == ST_F32;
+  constexpr int NR = LC + 2;
+  constexpr int REG = coldet_region_floats<ST>();  // floats per scale
+  constexpr int LD = F32 ? CLD : 32;               // f32 row stride
+  static_assert(NR <= CNRP && (CNRP * CLD * 4) % TMA_SMEM_ALIGN == 0, "scale stride alignment");
+  static_assert(C16B % TMA_SMEM_ALIGN == 0 && C16REG % TMA_SMEM_ALIGN == 0 &&
+                    C16B + NR * CBOX16 * 2 <= C16REG && NR * 32 * 4 <= C16REG,
+                "16-bit region layout");
+  static_assert(128 * 64 <= C16B + 80 * 56 && 128 * NR <= C16B + 80 * 64, "widening order");
   extern __shared__ __align__(128) float sm_raw[];
   __shared__ __align__(8) uint64_t mbar;
-  constexpr int NR = LC + 2;
-  static_assert(NR <= CNRP && (CNRP * CLD * 4) % TMA_SMEM_ALIGN == 0, "scale stride alignment");
-  float *buf = align_smem(sm_raw);            // [S][CNRP][CLD], rows NR..CNRP-1 unused
-  float *red = buf + (long)S * CNRP * CLD;    // detector scratch
+  float *buf = align_smem(sm_raw);  // [S][REG]
+  float *red = buf + (long)S * REG;  // detector scratch
   const int tid = threadIdx.x, lane = tid & 31, s = tid >> 5;
   const int c = blockIdx.y;
   const int x0 = blockIdx.x * TW - 1;
-  const int off = ((x0 % 4) + 4) % 4;
+  constexpr int XA = F32 ? 4 : 8;  // TMA x alignment in elements
+  const int off = ((x0 % XA) + XA) % XA;
   const int xv = min(max(x0 + lane, 0), W - 1);
   const int r0 = c * LC - 1;
   if (tid == 0) {
@@ -423,9 +477,12 @@ __global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUten
   }
   __syncthreads();  // no thread polls the barrier before it is initialised
   if (tid == 0) {
-    mbar_arrive_expect_tx(&mbar, (uint32_t)(S * NR * CLD * sizeof(float)));
-    for (int t = 0; t < S; ++t)
-      if (!tma_load_3d(buf + (long)t * CNRP * CLD, &map, x0 - off, r0, t, &mbar)) atomicExch(&da.status->error, 2);
+    constexpr int BW = F32 ? CLD : CBOX16;
+    mbar_arrive_expect_tx(&mbar, (uint32_t)(S * NR * BW * sizeof(T)));
+    for (int t = 0; t < S; ++t) {
+      void *dst = F32 ? (void *)(buf + (long)t * REG) : (void *)((char *)(buf + (long)t * REG) + C16B);
+      if (!tma_load_3d(dst, &map, x0 - off, r0, t, &mbar, (int)sizeof(T))) atomicExch(&da.status->error, 2);
+    }
   }
   const Coef &cf = coef[s];
   typename Rec::View v;
@@ -439,29 +496,31 @@ __global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUten
     if (tid == 0) atomicExch(&da.status->error, 1);
     return;
   }
-  float *b = buf + (long)s * CNRP * CLD + off + lane;
-  if (r0 < 0 || r0 + NR > H) {  // rows outside the frame: held one-sided rows of U
-    const float top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
-#pragma unroll
-    for (int i = 0; i < NR; ++i) {
-      const int y = r0 + i;
-      if (y < 0) b[i * CLD] = top;
-      else if (y >= H) b[i * CLD] = bot;
-    }
-  }
+  float *b = buf + (long)s * REG + (F32 ? off : 0) + lane;
+  const bool outside = r0 < 0 || r0 + NR > H;
+  float top = 0.f, bot = 0.f;
+  if (outside) top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
+  // causal pass; rows outside the frame take the held one-sided rows of U
+  // (written back for the anticausal pass), 16-bit input is widened in place
+  const T *b16 = reinterpret_cast<const T *>(reinterpret_cast<const char *>(buf + (long)s * REG) + C16B) + off +
+                 lane;
   float yp[NR];
 #pragma unroll
   for (int i = 0; i < NR; ++i) {
-    const float in = b[i * CLD];
+    const int y = r0 + i;
+    float in = F32 ? b[i * LD] : Store<ST>::ld(b16[i * CBOX16]);
+    if (outside) in = y < 0 ? top : (y >= H ? bot : in);
+    if (!F32 || outside) b[i * LD] = in;
     yp[i] = r.out(v);
     r.push(v, in);
+    if ((i & 7) == 7) __syncwarp();
   }
+  __syncwarp();
   r.load(Ef + fs, PW);
-  const float ms2 = -cf.sigma2;
 #pragma unroll
   for (int i = NR - 1; i >= 0; --i) {
-    const float in = b[i * CLD];
-    b[i * CLD] = ms2 * (yp[i] + fmaf(v.b0, in, r.out(v)));  // R_L = -sigma^2 (D20 + D02)
+    const float in = b[i * LD];
+    b[i * LD] = -(yp[i] + fmaf(v.b0, in, r.out(v)));  // R_L = -sigma^2 (D20 + D02); planes carry sigma^2
     r.push(v, in);
   }
   __syncthreads();
@@ -470,14 +529,14 @@ __global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUten
   a.NR = NR;
   a.x0 = x0;
   a.r0 = r0;
-  a.ld = CLD;
-  a.coff = off;
-  a.srows = CNRP;
+  a.ld = LD;
+  a.coff = F32 ? off : 0;
+  a.srows = REG / LD;
   detect_tile(buf, red, a);
 }
 
-template <class Rec>
-int run_iir(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
+template <class Rec, int ST>
+int run_iir_st(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   const int NT = ((g.W + CH - 1) / CH + 31) / 32 * 32;
   if (NT > 1024) return -1;
   const size_t row_smem = (size_t)(3 * (pad32(NT * CH) + 1) + 64 * Rec::NF) * sizeof(float);
@@ -485,20 +544,23 @@ int run_iir(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   if (!attr) {
     cudaFuncSetAttribute(k_row<Rec, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_row<Rec, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_coldet<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_coldet<Rec, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr = true;
   }
   if (row_smem > 200 * 1024) return -1;
   a.prof->begin("iir_row", st);
-  k_row<Rec, false><<<g.H, NT, row_smem, st>>>(g.X, g.xpitch, g.H, g.W, a.coef, a.S, a.P, g.PW, a.edge);
+  k_row<Rec, false><<<g.H, NT, row_smem, st>>>(g.X, g.xpitch, g.dtype, g.vscale, g.H, g.W, a.coef, a.S, a.P,
+                                                a.storage, g.PW, a.edge, a.status);
   a.prof->end(st);
   a.prof->begin("iir_row_edge", st);
-  k_row<Rec, true><<<2, NT, row_smem, st>>>(g.X, g.xpitch, g.H, g.W, a.coef, a.S, a.P, g.PW, a.edge);
+  k_row<Rec, true><<<2, NT, row_smem, st>>>(g.X, g.xpitch, g.dtype, g.vscale, g.H, g.W, a.coef, a.S, a.P,
+                                            a.storage, g.PW, a.edge, a.status);
   a.prof->end(st);
   const int nseg = (g.H + LC - 1) / LC;
   dim3 gs((g.W + 127) / 128, nseg, a.S);
   a.prof->begin("iir_colseg", st);
-  k_colseg<Rec><<<gs, 128, 0, st>>>(a.P, g.PW, g.H, g.W, a.edge, a.coef, a.carry, nseg);
+  k_colseg<Rec, ST><<<gs, 128, 0, st>>>(static_cast<const typename Store<ST>::T *>(a.P), g.PW, g.H, g.W, a.edge,
+                                        a.coef, a.carry, nseg);
   a.prof->end(st);
   dim3 gf((g.W + 127) / 128, a.S, 2);
   a.prof->begin("iir_colfold", st);
@@ -516,15 +578,25 @@ int run_iir(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   da.status = a.status;
   da.resp = a.responses ? a.responses + g.resp_off : nullptr;
   constexpr int NR = LC + 2;
-  const size_t det_smem = ((size_t)a.S * CNRP * CLD + (size_t)NR * 32 * 2) * sizeof(float) + (size_t)NR * 32 * 2 +
-                          TMA_SMEM_ALIGN;
+  const size_t det_smem = ((size_t)a.S * coldet_region_floats<ST>() + (size_t)NR * 32 * 2) * sizeof(float) +
+                          (size_t)NR * 32 * 2 + TMA_SMEM_ALIGN;
   CUtensorMap map;
-  if (encode_plane_map(&map, a.P, g.PW, g.H, a.S, CLD, NR)) return -1;
+  if (encode_plane_map(&map, a.P, ST, g.PW, g.H, a.S, ST == ST_F32 ? CLD : CBOX16, NR)) return -1;
   dim3 gd((g.W + TW - 1) / TW, nseg);
   a.prof->begin("iir_coldet", st);
-  k_coldet<Rec><<<gd, 32 * a.S, det_smem, st>>>(map, g.PW, g.H, g.W, a.edge, a.coef, a.S, a.carry, nseg, da);
+  k_coldet<Rec, ST><<<gd, 32 * a.S, det_smem, st>>>(map, g.PW, g.H, g.W, a.edge, a.coef, a.S, a.carry, nseg, da);
   a.prof->end(st);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <class Rec>
+int run_iir(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
+  switch (a.storage) {
+    case ST_F32: return run_iir_st<Rec, ST_F32>(g, a, st);
+    case ST_F16: return run_iir_st<Rec, ST_F16>(g, a, st);
+    case ST_BF16: return run_iir_st<Rec, ST_BF16>(g, a, st);
+    default: return -2;
+  }
 }
 
 }  // namespace

@@ -16,7 +16,9 @@ int launch_design(int type, int order, const double *d_lambdas, int S, int fir_k
 
 // Geometry of one frame in the bank.
 struct FrameGeom {
-  const float *X;   // input frame (f32)
+  const void *X;    // input frame (IN_* element type)
+  int dtype;        // IN_F32 / IN_F16 / IN_BF16 / IN_U16
+  float vscale;     // input multiplier
   long xpitch;      // elements between input rows
   int H, W;
   long PW;          // pitch of the intermediate planes (elements)
@@ -47,7 +49,8 @@ struct BankArgs {
   int kmax;              // FIR: largest half-length over the scales
   float threshold;
   int neigh;
-  float *P;              // S planes of H x PW (f32)
+  void *P;               // S planes of H x PW, element type `storage`
+  int storage;           // ST_F32 / ST_F16 / ST_BF16
   float *edge;           // S x 2 x PW: one-sided rows for the column boundary
   float *carry;          // S x nseg x 2 x NF x PW (IIR column carries)
   Blob *blobs;
@@ -60,9 +63,9 @@ struct BankArgs {
 int launch_iir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st);
 int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st);
 
-// 3-D tensor map over S one-sided planes (x, y, scale) of pitch PW, box
-// boxw x boxh x 1 (kf_fir.cu)
-int encode_plane_map(CUtensorMap *m, float *P, long PW, int H, int S, int boxw, int boxh);
+// 3-D tensor map over S one-sided planes (x, y, scale) of pitch PW and
+// element type `storage`, box boxw x boxh x 1 (kf_fir.cu)
+int encode_plane_map(CUtensorMap *m, void *P, int storage, long PW, int H, int S, int boxw, int boxh);
 
 // workspace needs (bytes) of one frame
 size_t iir_carry_floats(int H, long PW, int S, int nf);

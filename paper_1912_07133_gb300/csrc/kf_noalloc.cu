@@ -62,10 +62,14 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
   if (nscales < 1 || nscales > KF_MAX_SCALES) return nofail(KF_EINVAL, "nscales must be 1..16");
   for (int s = 0; s < nscales; ++s)
     if (!(scales[s] > 0.0) || !std::isfinite(scales[s])) return nofail(KF_EINVAL, "scales must be > 0");
-  if (!frame->data || frame->dtype != KF_DTYPE_F32 || frame->width < 1 || frame->height < 1 ||
-      frame->width > 8192 || frame->pitch < frame->width ||
-      (frame->value_scale != 0.0f && frame->value_scale != 1.0f))
-    return nofail(KF_EINVAL, "frame must be f32, 1 <= width <= 8192, pitch >= width");
+  if (!frame->data || frame->width < 1 || frame->height < 1 || frame->width > 8192 ||
+      frame->pitch < frame->width || !std::isfinite(frame->value_scale))
+    return nofail(KF_EINVAL, "frame needs data, 1 <= width <= 8192, pitch >= width, a finite value_scale");
+  if (frame->dtype != KF_DTYPE_F32 && frame->dtype != KF_DTYPE_F16 && frame->dtype != KF_DTYPE_BF16 &&
+      frame->dtype != KF_DTYPE_U16)
+    return nofail(KF_EINVAL, "unknown frame dtype");
+  if ((reinterpret_cast<uintptr_t>(frame->data) & (uintptr_t)(kf::in_bytes(frame->dtype) - 1)) != 0)
+    return nofail(KF_EINVAL, "frame data is not aligned to its element size");
   const int W = frame->width, H = frame->height, S = nscales;
   const long PW = ((long)W + 31) / 32 * 32;
   // layout of the scratch: coefficients | scales | status | planes | edges | carries
@@ -139,6 +143,7 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
   a.threshold = INFINITY;  // responses only: no candidates
   a.neigh = KF_NEIGH_ALL_SCALES;
   a.P = P;
+  a.storage = kf::ST_F32;
   a.edge = edge;
   a.carry = carry;
   a.blobs = nullptr;
@@ -147,7 +152,9 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
   a.responses = responses;
   a.prof = &prof;
   kf::FrameGeom g;
-  g.X = static_cast<const float *>(frame->data);
+  g.X = frame->data;
+  g.dtype = frame->dtype;
+  g.vscale = frame->value_scale == 0.0f ? 1.0f : frame->value_scale;
   g.xpitch = frame->pitch;
   g.H = H;
   g.W = W;

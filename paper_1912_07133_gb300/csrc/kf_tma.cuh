@@ -57,12 +57,13 @@ __device__ __forceinline__ float *align_smem(float *p) {
 }
 
 // 3-D tiled TMA load of one box at coordinates (x, y, z) into shared memory
-// (destination 128-byte aligned); x * 4 bytes must be a multiple of 16.
-// A destination or coordinate that breaks these rules is not issued: the
-// function returns false and the caller's bounded wait reports the failure.
+// (destination 128-byte aligned); x times the element size (4 or 2 bytes)
+// must be a multiple of 16.  A destination or coordinate that breaks these
+// rules is not issued: the function returns false and the caller's bounded
+// wait reports the failure.
 __device__ __forceinline__ bool tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
-                                            uint64_t *bar) {
-  if ((smem_u32(dst) & (TMA_SMEM_ALIGN - 1)) != 0 || (x & 3) != 0) return false;
+                                            uint64_t *bar, int elem_bytes = 4) {
+  if ((smem_u32(dst) & (TMA_SMEM_ALIGN - 1)) != 0 || ((x * elem_bytes) & 15) != 0) return false;
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
       "[%5];" ::"r"(smem_u32(dst)),

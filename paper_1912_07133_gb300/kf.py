@@ -25,6 +25,7 @@ KF_ETIMEOUT = -5
 KF_EOVERFLOW = -6
 KF_ENODEV = -7
 KF_ERERUN = -8
+KF_ERANGE = -9
 
 KF_IIR_REPEATED_POLE = 0
 KF_IIR_BUTTERWORTH = 1
@@ -172,7 +173,7 @@ def kf_design(ftype: int, order: int, scale: float) -> dict:
     return d
 
 
-def _frame_desc(t) -> kf_frame:
+def _frame_desc(t, value_scale: float = 0.0) -> kf_frame:
     import torch
 
     if not t.is_cuda or t.dim() != 2:
@@ -183,12 +184,18 @@ def _frame_desc(t) -> kf_frame:
           torch.uint16: KF_DTYPE_U16}.get(t.dtype)
     if dt is None:
         raise ValueError(f"unsupported frame dtype {t.dtype}")
-    return kf_frame(t.data_ptr(), t.shape[1], t.shape[0], t.stride(0), dt, 0.0)
+    return kf_frame(t.data_ptr(), t.shape[1], t.shape[0], t.stride(0), dt, float(value_scale))
 
 
-def kf_filter_bank(ctx: int, frames, scales, ftype: int, order: int, opts: kf_bank_opts = None) -> None:
-    """Enqueue the bank on the context stream; `frames` are CUDA tensors."""
-    descs = (kf_frame * len(frames))(*[_frame_desc(f) for f in frames])
+def kf_filter_bank(ctx: int, frames, scales, ftype: int, order: int, opts: kf_bank_opts = None,
+                   value_scales=None) -> None:
+    """Enqueue the bank on the context stream; `frames` are CUDA tensors
+    (float32, float16, bfloat16 or uint16), each multiplied by its entry of
+    `value_scales` (None: 1)."""
+    vs = value_scales if value_scales is not None else [0.0] * len(frames)
+    if len(vs) != len(frames):
+        raise ValueError("one value scale per frame")
+    descs = (kf_frame * len(frames))(*[_frame_desc(f, v) for f, v in zip(frames, vs)])
     sc = (ctypes.c_double * len(scales))(*[float(s) for s in scales])
     if opts is None:
         opts = kf_bank_opts_default()
@@ -227,7 +234,8 @@ def kf_kernel_times(ctx: int) -> dict:
     return {out[i].name.decode(): (out[i].launches, out[i].ms) for i in range(min(n.value, 64))}
 
 
-def kf_responses_noalloc(frame, scales, ftype: int, order: int, responses, stream=None) -> None:
+def kf_responses_noalloc(frame, scales, ftype: int, order: int, responses, stream=None,
+                         value_scale: float = 0.0) -> None:
     """Response planes of one frame without any device allocation by the
     library (for callers whose device memory is owned by another allocator or
     whose loops may not allocate); see include/kf.h for the size limit."""
@@ -239,7 +247,7 @@ def kf_responses_noalloc(frame, scales, ftype: int, order: int, responses, strea
         raise ValueError("responses must be a contiguous float32 CUDA tensor")
     if responses.numel() < len(scales) * frame.shape[0] * frame.shape[1]:
         raise ValueError("responses is too small")
-    d = _frame_desc(frame)
+    d = _frame_desc(frame, value_scale)
     sc = (ctypes.c_double * len(scales))(*[float(s) for s in scales])
     _check(load().kf_responses_noalloc(ctypes.byref(d), sc, len(scales), ftype, order, responses.data_ptr(),
                                        ctypes.c_void_p(stream)))
@@ -252,12 +260,14 @@ class Bank:
         self.ctx = kf_create(device, stream)
 
     def run(self, frames, scales, ftype=KF_IIR_REPEATED_POLE, order=4, threshold=0.05,
-            neighbourhood=KF_NEIGH_ALL_SCALES, responses=None, fir_kmax=96, profile=False):
+            neighbourhood=KF_NEIGH_ALL_SCALES, responses=None, fir_kmax=96, profile=False,
+            storage=KF_DTYPE_F32, value_scales=None):
         o = kf_bank_opts_default()
         o.threshold = float(threshold)
         o.profile = 1 if profile else 0
         o.neighbourhood = neighbourhood
         o.fir_kmax = fir_kmax
+        o.storage = storage
         if responses is not None:
             import torch
 
@@ -268,7 +278,7 @@ class Bank:
                 raise ValueError(f"responses needs {need} elements")
             o.responses = responses.data_ptr()
         self.threshold = float(threshold)
-        kf_filter_bank(self.ctx, frames, scales, ftype, order, o)
+        kf_filter_bank(self.ctx, frames, scales, ftype, order, o, value_scales)
 
     def kernel_times(self) -> dict:
         return kf_kernel_times(self.ctx)

@@ -9,24 +9,38 @@ OT = {0: O.IIR_REPEATED_POLE, 1: O.IIR_BUTTERWORTH, 2: O.FIR_COLORED_SG}
 TOL = 1e-5  # max |err| / per-scale response range (FP32 path)
 
 
-def gpu_bank(frames, scales, ftype, order, threshold=0.05, neigh=0, fir_kmax=96):
+def to_device(f):
+    """A host frame (numpy f32 / f16 / u16 array, or a CPU torch tensor, e.g.
+    bfloat16) as a contiguous CUDA tensor of the same element type."""
+    import torch
+
+    if isinstance(f, torch.Tensor):
+        return f.contiguous().cuda()
+    a = np.ascontiguousarray(f)
+    if a.dtype == np.uint16:  # through a same-size view: uint16 copies need no arithmetic support
+        return torch.from_numpy(a.view(np.int16)).cuda().view(torch.uint16)
+    return torch.from_numpy(a).cuda()
+
+
+def gpu_bank(frames, scales, ftype, order, threshold=0.05, neigh=0, fir_kmax=96, storage=0,
+             value_scales=None):
     import torch
 
     from paper_1912_07133_gb300 import kf
 
-    ts = [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in frames]
-    n = sum(len(scales) * f.size for f in frames)
+    ts = [to_device(f) for f in frames]
+    n = sum(len(scales) * t.numel() for t in ts)
     R = torch.empty(n, device="cuda", dtype=torch.float32)
     bank = kf.Bank(0)
     bank.run(ts, scales, ftype, order, threshold=threshold, neighbourhood=neigh, responses=R,
-             fir_kmax=fir_kmax)
+             fir_kmax=fir_kmax, storage=storage, value_scales=value_scales)
     blobs = bank.blobs()
     torch.cuda.synchronize()
     Rh = R.cpu().numpy().astype(np.float64)
     out, off = [], 0
-    for f in frames:
-        k = len(scales) * f.size
-        out.append(Rh[off:off + k].reshape(len(scales), *f.shape))
+    for t in ts:
+        k = len(scales) * t.numel()
+        out.append(Rh[off:off + k].reshape(len(scales), *t.shape))
         off += k
     bank.close()
     return out, blobs
