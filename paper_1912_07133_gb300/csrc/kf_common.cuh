@@ -50,13 +50,21 @@ constexpr float F16_MAX = 65504.f;
 __host__ __device__ __forceinline__ int store_bytes(int st) { return st == ST_F32 ? 4 : 2; }
 __host__ __device__ __forceinline__ int in_bytes(int dt) { return dt == IN_F32 ? 4 : 2; }
 
-// element e of an input row (any input type) times the frame's value scale
-__device__ __forceinline__ float load_in(const void *row, int e, int dt, float vs) {
+// one input element as f32 (before the value scale)
+__device__ __forceinline__ float in_f32(float v) { return v; }
+__device__ __forceinline__ float in_f32(__half v) { return __half2float(v); }
+__device__ __forceinline__ float in_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float in_f32(unsigned short v) { return (float)v; }
+
+// Call f(p) with the frame pointer cast to its element type; the dispatch
+// sits outside the caller's loops.
+template <class F>
+__device__ __forceinline__ void with_input_type(const void *X, int dt, F &&f) {
   switch (dt) {
-    case IN_F16: return vs * __half2float(__ldg(static_cast<const __half *>(row) + e));
-    case IN_BF16: return vs * __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(row) + e));
-    case IN_U16: return vs * (float)__ldg(static_cast<const unsigned short *>(row) + e);
-    default: return vs * __ldg(static_cast<const float *>(row) + e);
+    case IN_F16: f(static_cast<const __half *>(X)); break;
+    case IN_BF16: f(static_cast<const __nv_bfloat16 *>(X)); break;
+    case IN_U16: f(static_cast<const unsigned short *>(X)); break;
+    default: f(static_cast<const float *>(X));
   }
 }
 

@@ -128,25 +128,26 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const void *__restrict__ X, long
   const int n = RSEG + 2 * G;
   float *sL = sm;                       // padded: element j at pad20(j)
   float *sh = sm + pad20(n) + 4;
-  const int eb = in_bytes(dt);
-  const void *rm = static_cast<const char *>(X) + (long)max(y - 1, 0) * xpitch * eb;
-  const void *r0 = static_cast<const char *>(X) + (long)y * xpitch * eb;
-  const void *rp = static_cast<const char *>(X) + (long)min(y + 1, H - 1) * xpitch * eb;
-  auto ld = [&](const void *row, int e) { return load_in(row, e, dt, vs); };
-  const float vlo = ld(rp, 0) - 2.f * ld(r0, 0) + ld(rm, 0);
-  const float vhi = ld(rp, W - 1) - 2.f * ld(r0, W - 1) + ld(rm, W - 1);
-  for (int j = tid; j < n; j += RNT) {
-    const int e = xs - G + j;
-    float v;
-    if (e < 0) v = EDGE ? 0.f : vlo;
-    else if (e >= W) v = EDGE ? 0.f : vhi;
-    else {
-      const float c0 = ld(r0, e);
-      const float u = ld(r0, min(e + 1, W - 1)) - 2.f * c0 + ld(r0, max(e - 1, 0));
-      v = EDGE ? u : u + (ld(rp, e) - 2.f * c0 + ld(rm, e));
+  with_input_type(X, dt, [&](auto Xt) {
+    const auto *rm = Xt + (long)max(y - 1, 0) * xpitch;
+    const auto *r0 = Xt + (long)y * xpitch;
+    const auto *rp = Xt + (long)min(y + 1, H - 1) * xpitch;
+    auto ld = [&](const decltype(Xt) row, int e) { return vs * in_f32(__ldg(row + e)); };
+    const float vlo = ld(rp, 0) - 2.f * ld(r0, 0) + ld(rm, 0);
+    const float vhi = ld(rp, W - 1) - 2.f * ld(r0, W - 1) + ld(rm, W - 1);
+    for (int j = tid; j < n; j += RNT) {
+      const int e = xs - G + j;
+      float v;
+      if (e < 0) v = EDGE ? 0.f : vlo;
+      else if (e >= W) v = EDGE ? 0.f : vhi;
+      else {
+        const float c0 = ld(r0, e);
+        const float u = ld(r0, min(e + 1, W - 1)) - 2.f * c0 + ld(r0, max(e - 1, 0));
+        v = EDGE ? u : u + (ld(rp, e) - 2.f * c0 + ld(rm, e));
+      }
+      sL[pad20(j)] = v;
     }
-    sL[pad20(j)] = v;
-  }
+  });
   const int base = G + NOUT * tid;  // local index of this thread's first output
   bool ovf = false;                 // a value beyond the f16 range
   for (int s = 0; s < S; ++s) {

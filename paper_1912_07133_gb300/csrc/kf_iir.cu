@@ -238,11 +238,6 @@ __host__ __device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
 // ---------------------------------------------------------------------------
 // row pass
 // ---------------------------------------------------------------------------
-// row i of the input frame (any element type)
-__device__ __forceinline__ const void *in_row(const void *X, long xpitch, int i, int dt) {
-  return static_cast<const char *>(X) + (long)i * xpitch * in_bytes(dt);
-}
-
 template <class Rec, bool EDGE>
 __global__ void __launch_bounds__(256) k_row(const void *__restrict__ X, long xpitch, int dt, float vs, int H,
                                              int W, const Coef *__restrict__ coef, int S, void *__restrict__ P,
@@ -253,15 +248,17 @@ __global__ void __launch_bounds__(256) k_row(const void *__restrict__ X, long xp
   const int RP = pad32(NT * CH) + 1;
   float *s_m = sm, *s_0 = sm + RP, *s_p = sm + 2 * RP, *s_scan = sm + 3 * RP;
   const int y = EDGE ? (blockIdx.x == 0 ? 0 : H - 1) : blockIdx.x;
-  const void *rm = in_row(X, xpitch, max(y - 1, 0), dt);
-  const void *r0 = in_row(X, xpitch, y, dt);
-  const void *rp = in_row(X, xpitch, min(y + 1, H - 1), dt);
-  for (int e = tid; e < W; e += NT) {
-    const int a = pad32(e);
-    s_m[a] = load_in(rm, e, dt, vs);
-    s_0[a] = load_in(r0, e, dt, vs);
-    s_p[a] = load_in(rp, e, dt, vs);
-  }
+  with_input_type(X, dt, [&](auto Xt) {
+    const auto *rm = Xt + (long)max(y - 1, 0) * xpitch;
+    const auto *r0 = Xt + (long)y * xpitch;
+    const auto *rp = Xt + (long)min(y + 1, H - 1) * xpitch;
+    for (int e = tid; e < W; e += NT) {
+      const int a = pad32(e);
+      s_m[a] = vs * in_f32(__ldg(rm + e));
+      s_0[a] = vs * in_f32(__ldg(r0 + e));
+      s_p[a] = vs * in_f32(__ldg(rp + e));
+    }
+  });
   __syncthreads();
   const float v_lo = s_p[0] - 2.f * s_0[0] + s_m[0];
   const int eW = pad32(W - 1);
