@@ -1,14 +1,22 @@
 #!/usr/bin/env python
 """Throughput of the multi-scale blob-detection filter bank on GB300.
 
-Workload: one 4096 x 4096 FP32 synthetic frame (1/f background, 500 bright and
-dark elliptical blobs), 6 scales (blob radii 2, 4, 8, 16, 32, 48 px).  One
-step = the fourth-order repeated-pole IIR bank (Filter D) and the colored
-Savitzky-Golay FIR bank (Filter C, <= 193 taps), each followed by the
-3 x 3 x 6 scale-space extremum detector and the read-back of its blob list.
-Metric: Mpixel-scales/s = banks x pixels x scales / step time.
+Default workload (iir_fir): one 4096 x 4096 FP32 synthetic frame (1/f
+background, 500 bright and dark elliptical blobs), 6 scales (blob radii 2, 4,
+8, 16, 32, 48 px).  One step = the fourth-order repeated-pole IIR bank
+(Filter D) and the colored Savitzky-Golay FIR bank (Filter C, <= 193 taps),
+each followed by the 3 x 3 x 6 scale-space extremum detector and the
+read-back of its blob list.
+
+--workload counts: 16 uint16 frames of 8192 x 8192 (12-bit Poisson counts on a
+1/f background, 2000 blobs of radii 2-64 px; one generated frame in 16 device
+buffers), value scale 1/4095, 8 scales (radii 2-64 px), Filter D order 4 and
+Filter C with K <= 160, one-sided planes stored as --storage (default f16).
+
+Metric: Mpixel-scales/s = banks x frames x pixels x scales / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload iir_fir|counts] [--storage f32|f16|bf16]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.  Under torchrun (N > 1) every rank runs an
@@ -28,14 +36,33 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mpixel-scales/s blob detection (IIR & FIR), gated vs plain on 1 GB300; % HBM peak"
 UNIT = "Mpixel-scales/s"
-SCALES = [2.0, 4.0, 8.0, 16.0, 32.0, 48.0]
-H = W = 4096
 THRESHOLD = 0.05
 BANKS = (("iir_repeated_pole_order4", 0, 4), ("fir_colored_sg", 2, 1))
-WORKLOAD = ("4096x4096 FP32 frame, 6 scales (lambda 2-48 px): 4th-order repeated-pole IIR bank "
-            "+ colored Savitzky-Golay FIR bank (K<=96), Laplacian response, 3x3x6 extremum, "
-            "blob lists read back")
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+SB = {"f32": 4, "f16": 2, "bf16": 2}
+WORKLOADS = {
+    "iir_fir": dict(
+        H=4096, W=4096, frames=1, dtype="f32", s_in=4, value_scale=1.0, fir_kmax=96, storage="f32",
+        scales=[2.0, 4.0, 8.0, 16.0, 32.0, 48.0], ref_rows=256,
+        text=("4096x4096 FP32 frame, 6 scales (lambda 2-48 px): 4th-order repeated-pole IIR bank "
+              "+ colored Savitzky-Golay FIR bank (K<=96), Laplacian response, 3x3x6 extremum, "
+              "blob lists read back")),
+    "counts": dict(
+        H=8192, W=8192, frames=16, dtype="u16", s_in=2, value_scale=1.0 / 4095.0, fir_kmax=160,
+        storage="f16", scales=[2.0 * 32.0 ** (s / 7.0) for s in range(8)], ref_rows=32,
+        text=("16 x 8192x8192 uint16 12-bit Poisson-count frames (one generated frame in 16 device "
+              "buffers), value scale 1/4095, 8 scales (lambda 2-64 px): 4th-order repeated-pole IIR "
+              "bank + colored Savitzky-Golay FIR bank (K<=160), Laplacian response, 3x3x8 extremum, "
+              "blob lists read back")),
+}
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def make_frame(wl):
+    from paper_1912_07133_gb300 import synthetic
+    if wl["dtype"] == "u16":
+        return synthetic.counts_frame(seed=3, H=wl["H"], W=wl["W"])
+    return synthetic.iir_fir_frame(seed=1, H=wl["H"], W=wl["W"])
 
 
 def peaks():
@@ -60,13 +87,13 @@ def fir_taps(scales, kmax=96):
     return [min(math.ceil(5 * s / 2), kmax) for s in scales]
 
 
-def algorithmic(name, S, HW, taps):
-    """(bytes, flops) a kernel must move / compute per launch."""
-    fb = 4.0
+def algorithmic(name, S, HW, taps, s_in=4.0, s_b=4.0):
+    """(bytes, flops) a kernel must move / compute per launch (one frame):
+    s_in bytes per input pixel, s_b per stored plane element."""
     if name in ("iir_row", "fir_row"):
-        byts = fb * HW + fb * S * HW                 # read frame, write S planes
+        byts = s_in * HW + s_b * S * HW              # read frame, write S planes
     elif name in ("iir_colseg", "iir_coldet", "fir_coldet"):
-        byts = fb * S * HW                           # read S planes
+        byts = s_b * S * HW                          # read S planes
     else:
         byts = 0.0
     flops = 0.0
@@ -151,9 +178,16 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     kf.load()
+    wl = WORKLOADS[args.workload]
+    storage = args.storage or wl["storage"]
+    H, W, NF, SCALES = wl["H"], wl["W"], wl["frames"], wl["scales"]
     dev = torch.device("cuda", local)
-    img = synthetic.iir_fir_frame(seed=1, H=H, W=W)
-    X = torch.from_numpy(img).to(dev)
+    img = make_frame(wl)
+    X1 = torch.from_numpy(img.view(np.int16) if img.dtype == np.uint16 else img).to(dev)
+    Xs = [X1.clone() for _ in range(NF - 1)] + [X1]
+    if img.dtype == np.uint16:
+        Xs = [x.view(torch.uint16) for x in Xs]
+    vscales = [wl["value_scale"]] * NF
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
     bank = kf.Bank(local, stream.cuda_stream)
@@ -165,10 +199,14 @@ def run_ours(args):
             kf.kf_design(ft, order, s)
     design_ms = (time.perf_counter() - t0) * 1e3
 
+    def run_bank(frames, ft, order, profile=False):
+        bank.run(frames, SCALES, ft, order, threshold=THRESHOLD, profile=profile,
+                 fir_kmax=wl["fir_kmax"], storage=STORAGE[storage], value_scales=vscales)
+
     def step(profile):
         n, times = 0, {}
         for _, ft, order in BANKS:
-            bank.run([X], SCALES, ft, order, threshold=THRESHOLD, profile=profile)
+            run_bank(Xs, ft, order, profile)
             n += len(bank.blobs())
             if profile:
                 for k, (nl, ms) in bank.kernel_times().items():
@@ -208,23 +246,25 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    pix_scales = len(BANKS) * H * W * len(SCALES)
+    pix_scales = len(BANKS) * NF * H * W * len(SCALES)
     value = world * pix_scales / (ms_per_step * 1e-3) / 1e6
     # --- the same steps again with CUDA events around every kernel ------------
     _, ktimes, _, _ = timed(True)
 
     # --- end to end: host frame in pinned memory, copies inside the timed region
-    host = torch.from_numpy(img).pin_memory()
-    Xe = torch.empty_like(X)
+    host = torch.from_numpy(img.view(np.int16) if img.dtype == np.uint16 else img).pin_memory()
+    Xe = [torch.empty_like(X1) for _ in range(NF)]
+    Xev = [x.view(torch.uint16) for x in Xe] if img.dtype == np.uint16 else Xe
     e2e_ms, bo = [], 0
     for i in range(args.warmup + args.steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        Xe.copy_(host, non_blocking=True)
+        for x in Xe:
+            x.copy_(host, non_blocking=True)
         nb = 0
         for _, ft, order in BANKS:
-            bank.run([Xe], SCALES, ft, order, threshold=THRESHOLD)
+            run_bank(Xev, ft, order)
             nb += len(bank.blobs())
         b.record(stream)
         b.synchronize()
@@ -237,17 +277,18 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_step = float(t.item())
     e2e = {"value": world * pix_scales / (e2e_step * 1e-3) / 1e6, "unit": UNIT,
-           "h2d_bytes_per_step": int(img.nbytes), "d2h_bytes_per_step": int(bo),
+           "h2d_bytes_per_step": int(img.nbytes) * NF, "d2h_bytes_per_step": int(bo),
            "ms_per_step": e2e_step}
 
     # --- roofline of the dominant kernel -------------------------------------
     hbm, hbm_src = peaks()
     alu_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
-    taps = fir_taps(SCALES)
+    taps = fir_taps(SCALES, wl["fir_kmax"])
     kern = {}
+    sizes = dict(s_in=wl["s_in"], s_b=SB[storage])
     for k, (nl, ms) in ktimes.items():
         per = ms / max(nl, 1)
-        byts, flops = algorithmic(k, len(SCALES), H * W, taps)
+        byts, flops = algorithmic(k, len(SCALES), H * W, taps, **sizes)
         kern[k] = {"launches": nl, "ms_per_launch": round(per, 4),
                    "share": round(ms / max(sum(v[1] for v in ktimes.values()), 1e-9), 4)}
         if byts:
@@ -257,7 +298,7 @@ def run_ours(args):
     dom = max(ktimes, key=lambda k: ktimes[k][1])
     nl, ms = ktimes[dom]
     per = ms / nl
-    byts, flops = algorithmic(dom, len(SCALES), H * W, taps)
+    byts, flops = algorithmic(dom, len(SCALES), H * W, taps, **sizes)
     if flops:
         ach = flops / (per * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 1),
@@ -270,7 +311,8 @@ def run_ours(args):
     launches = sum(v[0] for v in ktimes.values())
     bank.close()
 
-    cpu = cpu_baseline(img) if (rank == 0 and not args.no_cpu) else None
+    cpu = cpu_baseline(img, wl, rows=None if args.workload == "iir_fir" else wl["ref_rows"]) \
+        if (rank == 0 and not args.no_cpu) else None
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -280,8 +322,9 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frame": f"{H}x{W} f32", "scales_px": SCALES,
-                   "banks": [b[0] for b in BANKS], "threshold": THRESHOLD,
+        "config": {"workload": wl["text"], "frames": NF, "frame": f"{H}x{W} {wl['dtype']}",
+                   "storage": storage, "scales_px": [round(x, 3) for x in SCALES],
+                   "banks": [b[0] for b in BANKS], "threshold": THRESHOLD, "fir_kmax": wl["fir_kmax"],
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}", "designs": "FP64 design kernel run once "
                    "per bank configuration, timed separately (design_ms)"},
@@ -292,26 +335,39 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(img, rows=None):
+def oracle_step(x, wl):
+    """Both banks and the detector through the FP64 oracle on the array x."""
+    from oracle import oracle as O
+    for _, ft, order in BANKS:
+        R = O.bank(x, wl["scales"], {0: O.IIR_REPEATED_POLE, 2: O.FIR_COLORED_SG}[ft], order,
+                   fir_kmax=wl["fir_kmax"])
+        O.detect(R, THRESHOLD)
+
+
+def oracle_designs(wl):
+    """The oracle's colored-SG designs (cached), made before any timing."""
+    from oracle import oracle as O
+    for l in wl["scales"]:
+        O.design_colored_sg_mp(1, O.sg_half_length(1, l / 2, wl["fir_kmax"]), 6.0 / l)
+
+
+def cpu_baseline(img, wl, rows=None):
     """The FP64 oracle as it stands, on the host cores, on `rows` rows of the
-    frame (all 6 scales, both banks); designs are made before timing."""
+    frame (all scales, both banks); designs are made before timing."""
     import numpy as np
 
     from oracle import oracle as O
 
     sub = img if rows is None else img[:rows]
-    x = sub.astype(np.float64)
-    for l in SCALES:  # designs (cached), excluded like the GPU designs
-        O.design_colored_sg_mp(1, O.sg_half_length(1, l / 2, 96), 6.0 / l)
+    x = sub.astype(np.float64) * wl["value_scale"]
+    oracle_designs(wl)
     t0 = time.perf_counter()
-    for _, ft, order in BANKS:
-        R = O.bank(x, SCALES, {0: O.IIR_REPEATED_POLE, 2: O.FIR_COLORED_SG}[ft], order)
-        O.detect(R, THRESHOLD)
+    oracle_step(x, wl)
     dt = time.perf_counter() - t0
-    ps = len(BANKS) * sub.shape[0] * sub.shape[1] * len(SCALES)
+    ps = len(BANKS) * sub.shape[0] * sub.shape[1] * len(wl["scales"])
     return {"value": round(ps / dt / 1e6, 3), "unit": UNIT, "cores": O.threads(), "kind": "oracle",
-            "sample": f"{sub.shape[0]}x{sub.shape[1]} rows of the frame, 6 scales, both banks "
-                      f"({dt:.2f} s)"}
+            "sample": f"{sub.shape[0]}x{sub.shape[1]} rows of one frame, {len(wl['scales'])} scales, "
+                      f"both banks ({dt:.2f} s)"}
 
 
 # ---------------------------------------------------------------------------
@@ -324,34 +380,30 @@ def run_reference(args):
     import numpy as np
 
     from oracle import oracle as O
-    from paper_1912_07133_gb300 import synthetic
 
     O.build()
-    img = synthetic.iir_fir_frame(seed=1, H=H, W=W)
-    rows = 256  # bounded sample per step: 256 x 4096 x 6 scales x 2 banks
-    x = img[:rows].astype(np.float64)
-    for l in SCALES:
-        O.design_colored_sg_mp(1, O.sg_half_length(1, l / 2, 96), 6.0 / l)
-
-    def step():
-        for _, ft, order in BANKS:
-            R = O.bank(x, SCALES, {0: O.IIR_REPEATED_POLE, 2: O.FIR_COLORED_SG}[ft], order)
-            O.detect(R, THRESHOLD)
+    wl = WORKLOADS[args.workload]
+    img = make_frame(wl)
+    rows = wl["ref_rows"]  # bounded sample per step: rows x W x all scales x 2 banks
+    W = wl["W"]
+    x = img[:rows].astype(np.float64) * wl["value_scale"]
+    oracle_designs(wl)
 
     for _ in range(args.warmup):
-        step()
+        oracle_step(x, wl)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        oracle_step(x, wl)
     dt = (time.perf_counter() - t0) / args.steps
-    ps = len(BANKS) * rows * W * len(SCALES)
+    ps = len(BANKS) * rows * W * len(wl["scales"])
     v = ps / dt / 1e6
-    sample = f"{rows}x{W} rows of the 4096x4096 frame per step, 6 scales, both banks"
+    sample = (f"{rows}x{W} rows of one {wl['H']}x{W} frame per step, {len(wl['scales'])} scales, "
+              f"both banks")
     line = {"metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": sample, "parallelism": "host cores"},
+            "config": {"workload": wl["text"], "sample": sample, "parallelism": "host cores"},
             "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "kind": "oracle", "cores": O.threads(),
                              "sample": sample},
             "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -365,6 +417,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="iir_fir")
+    ap.add_argument("--storage", choices=tuple(STORAGE), default=None,
+                    help="element type of the one-sided planes (default: the workload's)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

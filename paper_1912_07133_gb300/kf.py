@@ -278,13 +278,24 @@ class Bank:
                 raise ValueError(f"responses needs {need} elements")
             o.responses = responses.data_ptr()
         self.threshold = float(threshold)
+        self._last = (frames, scales, ftype, order, o, value_scales)
         kf_filter_bank(self.ctx, frames, scales, ftype, order, o, value_scales)
 
     def kernel_times(self) -> dict:
         return kf_kernel_times(self.ctx)
 
     def blobs(self, threshold=None, capacity=None) -> np.ndarray:
-        return kf_detect_blobs(self.ctx, self.threshold if threshold is None else threshold, capacity)
+        """Blob list of the last run.  If the context's device candidate list
+        overflowed (KF_ERERUN: the library has raised its capacity), the last
+        run is repeated once on the same frames and the list read again."""
+        thr = self.threshold if threshold is None else threshold
+        try:
+            return kf_detect_blobs(self.ctx, thr, capacity)
+        except KfError as e:
+            if e.code != KF_ERERUN or getattr(self, "_last", None) is None:
+                raise
+        kf_filter_bank(self.ctx, *self._last)
+        return kf_detect_blobs(self.ctx, thr, capacity)
 
     def close(self):
         if self.ctx:
