@@ -8,6 +8,10 @@ background, 500 bright and dark elliptical blobs), 6 scales (blob radii 2, 4,
 each followed by the 3 x 3 x 6 scale-space extremum detector and the
 read-back of its blob list.
 
+--workload batch: 64 FP32 frames of uneven sizes (about 574 Mpx), 8 scales,
+Filter D order 4 and the Butterworth bank, all frames in one call; the line
+adds the same steps launched frame by frame (per_frame_schedule).
+
 --workload counts: 16 uint16 frames of 8192 x 8192 (12-bit Poisson counts on a
 1/f background, 2000 blobs of radii 2-64 px; one generated frame in 16 device
 buffers), value scale 1/4095, 8 scales (radii 2-64 px), Filter D order 4 and
@@ -16,7 +20,8 @@ Filter C with K <= 160, one-sided planes stored as --storage (default f16).
 Metric: Mpixel-scales/s = banks x frames x pixels x scales / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload iir_fir|counts] [--storage f32|f16|bf16]
+                  [--workload iir_fir|counts|batch] [--storage f32|f16|bf16]
+                  [--no-graph]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.  Under torchrun (N > 1) every rank runs an
@@ -37,32 +42,45 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpixel-scales/s blob detection (IIR & FIR), gated vs plain on 1 GB300; % HBM peak"
 UNIT = "Mpixel-scales/s"
 THRESHOLD = 0.05
-BANKS = (("iir_repeated_pole_order4", 0, 4), ("fir_colored_sg", 2, 1))
+IIR_FIR = (("iir_repeated_pole_order4", 0, 4), ("fir_colored_sg", 2, 1))
+IIR_BW = (("iir_repeated_pole_order4", 0, 4), ("iir_butterworth_order2", 1, 2))
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 SB = {"f32": 4, "f16": 2, "bf16": 2}
+EIGHT = [2.0 * 32.0 ** (s / 7.0) for s in range(8)]
 WORKLOADS = {
     "iir_fir": dict(
-        H=4096, W=4096, frames=1, dtype="f32", s_in=4, value_scale=1.0, fir_kmax=96, storage="f32",
+        frames=1, dtype="f32", s_in=4, value_scale=1.0, fir_kmax=96, storage="f32", banks=IIR_FIR,
         scales=[2.0, 4.0, 8.0, 16.0, 32.0, 48.0], ref_rows=256,
         text=("4096x4096 FP32 frame, 6 scales (lambda 2-48 px): 4th-order repeated-pole IIR bank "
               "+ colored Savitzky-Golay FIR bank (K<=96), Laplacian response, 3x3x6 extremum, "
               "blob lists read back")),
     "counts": dict(
-        H=8192, W=8192, frames=16, dtype="u16", s_in=2, value_scale=1.0 / 4095.0, fir_kmax=160,
-        storage="f16", scales=[2.0 * 32.0 ** (s / 7.0) for s in range(8)], ref_rows=32,
+        frames=16, dtype="u16", s_in=2, value_scale=1.0 / 4095.0, fir_kmax=160, storage="f16", banks=IIR_FIR,
+        scales=EIGHT, ref_rows=32,
         text=("16 x 8192x8192 uint16 12-bit Poisson-count frames (one generated frame in 16 device "
               "buffers), value scale 1/4095, 8 scales (lambda 2-64 px): 4th-order repeated-pole IIR "
               "bank + colored Savitzky-Golay FIR bank (K<=160), Laplacian response, 3x3x8 extremum, "
               "blob lists read back")),
+    "batch": dict(
+        frames=64, dtype="f32", s_in=4, value_scale=1.0, fir_kmax=96, storage="f32", banks=IIR_BW,
+        scales=EIGHT, ref_rows=64,
+        text=("64 FP32 frames of uneven sizes drawn from {1024x768, 1920x1080, 2048x2048, 4096x3072, "
+              "6144x4096} (uniform background, 20 blobs per 512^2), 8 scales (lambda 2-64 px): 4th-order "
+              "repeated-pole IIR bank + Butterworth bank (L_B = 4), Laplacian response, 3x3x8 extremum, "
+              "blob lists read back; all frames in one call")),
 }
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
-def make_frame(wl):
+def make_frames(wl):
+    """Host frames of the workload (the counts workload: one frame, used by
+    every device buffer)."""
     from paper_1912_07133_gb300 import synthetic
     if wl["dtype"] == "u16":
-        return synthetic.counts_frame(seed=3, H=wl["H"], W=wl["W"])
-    return synthetic.iir_fir_frame(seed=1, H=wl["H"], W=wl["W"])
+        return [synthetic.counts_frame(seed=3, H=8192, W=8192)]
+    if wl["frames"] == 1:
+        return [synthetic.iir_fir_frame(seed=1, H=4096, W=4096)]
+    return synthetic.batch_frames(seed=2, nframes=wl["frames"])
 
 
 def peaks():
@@ -168,7 +186,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     import __graft_entry__
-    from paper_1912_07133_gb300 import kf, synthetic
+    from paper_1912_07133_gb300 import kf
 
     rank, world, local = dist_info()
     if world > 1:
@@ -180,13 +198,22 @@ def run_ours(args):
     kf.load()
     wl = WORKLOADS[args.workload]
     storage = args.storage or wl["storage"]
-    H, W, NF, SCALES = wl["H"], wl["W"], wl["frames"], wl["scales"]
+    NF, SCALES, BANKS = wl["frames"], wl["scales"], wl["banks"]
+    graph = not args.no_graph
     dev = torch.device("cuda", local)
-    img = make_frame(wl)
-    X1 = torch.from_numpy(img.view(np.int16) if img.dtype == np.uint16 else img).to(dev)
-    Xs = [X1.clone() for _ in range(NF - 1)] + [X1]
-    if img.dtype == np.uint16:
-        Xs = [x.view(torch.uint16) for x in Xs]
+    host = make_frames(wl)
+    u16 = host[0].dtype == np.uint16
+    as_t = (lambda a: torch.from_numpy(a.view(np.int16))) if u16 else torch.from_numpy
+    dview = (lambda t: t.view(torch.uint16)) if u16 else (lambda t: t)
+    # device frames (inputs resident in HBM for the device-timed value)
+    if len(host) == NF:
+        X = [as_t(h).to(dev) for h in host]
+        src = list(range(NF))
+    else:  # one generated frame in NF device buffers
+        X = [as_t(host[0]).to(dev) for _ in range(NF)]
+        src = [0] * NF
+    Xs = [dview(x) for x in X]
+    pixels = sum(host[i].size for i in src)
     vscales = [wl["value_scale"]] * NF
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
@@ -199,14 +226,15 @@ def run_ours(args):
             kf.kf_design(ft, order, s)
     design_ms = (time.perf_counter() - t0) * 1e3
 
-    def run_bank(frames, ft, order, profile=False):
-        bank.run(frames, SCALES, ft, order, threshold=THRESHOLD, profile=profile,
-                 fir_kmax=wl["fir_kmax"], storage=STORAGE[storage], value_scales=vscales)
+    def run_bank(frames, ft, order, profile=False, schedule=kf.KF_SCHED_BATCHED, use_graph=graph):
+        bank.run(frames, SCALES, ft, order, threshold=THRESHOLD, profile=profile, fir_kmax=wl["fir_kmax"],
+                 storage=STORAGE[storage], value_scales=vscales, schedule=schedule, graph=use_graph)
 
-    def step(profile):
+    def step(profile, schedule=kf.KF_SCHED_BATCHED, frames=None):
         n, times = 0, {}
         for _, ft, order in BANKS:
-            run_bank(Xs, ft, order, profile)
+            run_bank(Xs if frames is None else frames, ft, order, profile, schedule,
+                     graph and not profile and schedule == kf.KF_SCHED_BATCHED)
             n += len(bank.blobs())
             if profile:
                 for k, (nl, ms) in bank.kernel_times().items():
@@ -222,7 +250,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step(False)
 
-    def timed(profile):
+    def timed(profile, schedule=kf.KF_SCHED_BATCHED):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         kt, nb = {}, 0
@@ -231,7 +259,7 @@ def run_ours(args):
             for i in range(args.steps):
                 flush.zero_()
                 ev[i][0].record(stream)
-                nb, times = step(profile)
+                nb, times = step(profile, schedule)
                 ev[i][1].record(stream)
                 for k, (nl, ms) in times.items():
                     a, b = kt.get(k, (0, 0.0))
@@ -239,92 +267,109 @@ def run_ours(args):
             barrier()
         return sum(a.elapsed_time(b) for a, b in ev), kt, nb, clk.summary()
 
+    def max_over_ranks(x):
+        if world > 1:
+            t = torch.tensor([x], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
     # --- device-resident timed region (no profiling events) ------------------
     total_ms, _, nblobs, clocks = timed(False)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    pix_scales = len(BANKS) * NF * H * W * len(SCALES)
+    ms_per_step = max_over_ranks(total_ms) / args.steps
+    pix_scales = len(BANKS) * pixels * len(SCALES)
     value = world * pix_scales / (ms_per_step * 1e-3) / 1e6
     # --- the same steps again with CUDA events around every kernel ------------
     _, ktimes, _, _ = timed(True)
+    # --- the same steps launched frame by frame (batch workloads) ------------
+    per_frame = None
+    if NF > 1:
+        for _ in range(2):
+            step(False, kf.KF_SCHED_PER_FRAME)
+        pf_ms, _, _, _ = timed(False, kf.KF_SCHED_PER_FRAME)
+        pf_step = max_over_ranks(pf_ms) / args.steps
+        per_frame = {"value": round(world * pix_scales / (pf_step * 1e-3) / 1e6, 1), "ms_per_step": round(pf_step, 4),
+                     "launches": "every pass once per frame, eager (no graph)"}
 
-    # --- end to end: host frame in pinned memory, copies inside the timed region
-    host = torch.from_numpy(img.view(np.int16) if img.dtype == np.uint16 else img).pin_memory()
-    Xe = [torch.empty_like(X1) for _ in range(NF)]
-    Xev = [x.view(torch.uint16) for x in Xe] if img.dtype == np.uint16 else Xe
+    # --- end to end: host frames in pinned memory, copies inside the timed region
+    pinned = [as_t(h).pin_memory() for h in host]
+    Xe = [torch.empty_like(x) for x in X]
+    Xev = [dview(x) for x in Xe]
     e2e_ms, bo = [], 0
     for i in range(args.warmup + args.steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for x in Xe:
-            x.copy_(host, non_blocking=True)
-        nb = 0
-        for _, ft, order in BANKS:
-            run_bank(Xev, ft, order)
-            nb += len(bank.blobs())
+        for x, j in zip(Xe, src):
+            x.copy_(pinned[j], non_blocking=True)
+        nb, _ = step(False, frames=Xev)
         b.record(stream)
         b.synchronize()
         if i >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
             bo = nb * np.dtype(kf.BLOB_DTYPE).itemsize
-    e2e_step = sum(e2e_ms) / len(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(sum(e2e_ms) / len(e2e_ms))
     e2e = {"value": world * pix_scales / (e2e_step * 1e-3) / 1e6, "unit": UNIT,
-           "h2d_bytes_per_step": int(img.nbytes) * NF, "d2h_bytes_per_step": int(bo),
+           "h2d_bytes_per_step": int(sum(host[j].nbytes for j in src)), "d2h_bytes_per_step": int(bo),
            "ms_per_step": e2e_step}
 
     # --- roofline of the dominant kernel -------------------------------------
+    # algorithmic work of a kernel per step, summed over the banks that run it
+    # and all frames; achieved = that work x steps / the kernel's summed time
     hbm, hbm_src = peaks()
     alu_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
     taps = fir_taps(SCALES, wl["fir_kmax"])
-    kern = {}
     sizes = dict(s_in=wl["s_in"], s_b=SB[storage])
+
+    def work(k):
+        byts = flops = 0.0
+        for _, ft, _o in BANKS:
+            if k.startswith("fir_") == (ft == 2):
+                b_, f_ = algorithmic(k, len(SCALES), pixels, taps, **sizes)
+                byts, flops = byts + b_, flops + f_
+        return byts * args.steps, flops * args.steps
+
+    kern = {}
+    total_kms = max(sum(v[1] for v in ktimes.values()), 1e-9)
     for k, (nl, ms) in ktimes.items():
-        per = ms / max(nl, 1)
-        byts, flops = algorithmic(k, len(SCALES), H * W, taps, **sizes)
-        kern[k] = {"launches": nl, "ms_per_launch": round(per, 4),
-                   "share": round(ms / max(sum(v[1] for v in ktimes.values()), 1e-9), 4)}
+        byts, flops = work(k)
+        kern[k] = {"launches": nl, "ms_per_launch": round(ms / max(nl, 1), 4), "share": round(ms / total_kms, 4)}
         if byts:
-            kern[k]["GB_s"] = round(byts / (per * 1e-3) / 1e9, 1)
+            kern[k]["GB_s"] = round(byts / (ms * 1e-3) / 1e9, 1)
         if flops:
-            kern[k]["TFLOP_s"] = round(flops / (per * 1e-3) / 1e12, 2)
+            kern[k]["TFLOP_s"] = round(flops / (ms * 1e-3) / 1e12, 2)
     dom = max(ktimes, key=lambda k: ktimes[k][1])
-    nl, ms = ktimes[dom]
-    per = ms / nl
-    byts, flops = algorithmic(dom, len(SCALES), H * W, taps, **sizes)
+    byts, flops = work(dom)
+    ms = ktimes[dom][1]
     if flops:
-        ach = flops / (per * 1e-3) / 1e12
+        ach = flops / (ms * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 1),
                 "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4), "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
     else:
-        ach = byts / (per * 1e-3) / 1e9
+        ach = byts / (ms * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(ach / hbm, 4), "traffic": None, "peak_source": hbm_src}
+    # filter-bank kernels launched in the timed region (the profiled pass runs the same steps)
     launches = sum(v[0] for v in ktimes.values())
     bank.close()
 
-    cpu = cpu_baseline(img, wl, rows=None if args.workload == "iir_fir" else wl["ref_rows"]) \
+    cpu = cpu_baseline(host[0], wl, rows=None if args.workload == "iir_fir" else wl["ref_rows"]) \
         if (rank == 0 and not args.no_cpu) else None
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     if rank != 0:
         return
+    shapes = sorted({f"{host[j].shape[1]}x{host[j].shape[0]}" for j in src})
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl["text"], "frames": NF, "frame": f"{H}x{W} {wl['dtype']}",
+        "config": {"workload": wl["text"], "frames": NF, "frame_sizes": shapes, "input": wl["dtype"],
                    "storage": storage, "scales_px": [round(x, 3) for x in SCALES],
                    "banks": [b[0] for b in BANKS], "threshold": THRESHOLD, "fir_kmax": wl["fir_kmax"],
+                   "launch": ("batched schedule, replayed from a CUDA graph" if graph else "batched schedule, eager"),
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}", "designs": "FP64 design kernel run once "
                    "per bank configuration, timed separately (design_ms)"},
@@ -332,21 +377,25 @@ def run_ours(args):
         "clocks": clocks, "kernels": kern, "blobs_per_step": nblobs,
         "design_ms": round(design_ms, 2),
     }
+    if per_frame:
+        line["per_frame_schedule"] = per_frame
     print(json.dumps(line), flush=True)
 
 
 def oracle_step(x, wl):
     """Both banks and the detector through the FP64 oracle on the array x."""
     from oracle import oracle as O
-    for _, ft, order in BANKS:
-        R = O.bank(x, wl["scales"], {0: O.IIR_REPEATED_POLE, 2: O.FIR_COLORED_SG}[ft], order,
-                   fir_kmax=wl["fir_kmax"])
+    for _, ft, order in wl["banks"]:
+        R = O.bank(x, wl["scales"], {0: O.IIR_REPEATED_POLE, 1: O.IIR_BUTTERWORTH, 2: O.FIR_COLORED_SG}[ft],
+                   order, fir_kmax=wl["fir_kmax"])
         O.detect(R, THRESHOLD)
 
 
 def oracle_designs(wl):
     """The oracle's colored-SG designs (cached), made before any timing."""
     from oracle import oracle as O
+    if not any(ft == 2 for _, ft, _o in wl["banks"]):
+        return
     for l in wl["scales"]:
         O.design_colored_sg_mp(1, O.sg_half_length(1, l / 2, wl["fir_kmax"]), 6.0 / l)
 
@@ -364,7 +413,7 @@ def cpu_baseline(img, wl, rows=None):
     t0 = time.perf_counter()
     oracle_step(x, wl)
     dt = time.perf_counter() - t0
-    ps = len(BANKS) * sub.shape[0] * sub.shape[1] * len(wl["scales"])
+    ps = len(wl["banks"]) * sub.shape[0] * sub.shape[1] * len(wl["scales"])
     return {"value": round(ps / dt / 1e6, 3), "unit": UNIT, "cores": O.threads(), "kind": "oracle",
             "sample": f"{sub.shape[0]}x{sub.shape[1]} rows of one frame, {len(wl['scales'])} scales, "
                       f"both banks ({dt:.2f} s)"}
@@ -383,9 +432,9 @@ def run_reference(args):
 
     O.build()
     wl = WORKLOADS[args.workload]
-    img = make_frame(wl)
+    img = make_frames(wl)[0]
     rows = wl["ref_rows"]  # bounded sample per step: rows x W x all scales x 2 banks
-    W = wl["W"]
+    W = img.shape[1]
     x = img[:rows].astype(np.float64) * wl["value_scale"]
     oracle_designs(wl)
 
@@ -395,9 +444,9 @@ def run_reference(args):
     for _ in range(args.steps):
         oracle_step(x, wl)
     dt = (time.perf_counter() - t0) / args.steps
-    ps = len(BANKS) * rows * W * len(wl["scales"])
+    ps = len(wl["banks"]) * rows * W * len(wl["scales"])
     v = ps / dt / 1e6
-    sample = (f"{rows}x{W} rows of one {wl['H']}x{W} frame per step, {len(wl['scales'])} scales, "
+    sample = (f"{rows}x{W} rows of one {img.shape[0]}x{W} frame per step, {len(wl['scales'])} scales, "
               f"both banks")
     line = {"metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
@@ -418,6 +467,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="iir_fir")
+    ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
     ap.add_argument("--storage", choices=tuple(STORAGE), default=None,
                     help="element type of the one-sided planes (default: the workload's)")
     args = ap.parse_args()

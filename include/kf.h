@@ -65,6 +65,9 @@ extern "C" {
 
 #define KF_BOUNDARY_HOLD 0 /* frame edges held to +-infinity (Appendix, A32)     */
 
+#define KF_SCHED_BATCHED 0   /* one persistent launch per pass for all frames   */
+#define KF_SCHED_PER_FRAME 1 /* every pass launched once per frame              */
+
 #define KF_NEIGH_ALL_SCALES 0 /* extremum over 3 x 3 x (all scales)            */
 #define KF_NEIGH_ADJACENT 1   /* extremum over 3 x 3 x (scale -1, 0, +1)       */
 
@@ -123,7 +126,23 @@ typedef struct {
                             R at (x, y) is responses[off_f + (s*H + y)*W + x],
                             off_f = sum over earlier frames of nscales*H*W.
                             NULL: not written.                                 */
-  int64_t reserved[4];
+  int32_t schedule;      /* KF_SCHED_BATCHED: each pass is one launch over
+                            the work items of all frames of the call (the IIR
+                            row pass one launch per block-width class);
+                            KF_SCHED_PER_FRAME: every pass launched frame by
+                            frame.  Same results either way.                 */
+  int32_t graph;         /* 1: replay the call's launches from a CUDA graph.
+                            The first call of a geometry runs eagerly; the
+                            second captures the launches (status reset + all
+                            passes) and every later call of the same geometry
+                            replays them after uploading the frame table
+                            (frame pointers, pitches, value scales and
+                            response pointers may change between calls).
+                            Geometry = type, order, scales, fir_kmax,
+                            storage, threshold, neighbourhood, schedule,
+                            frame count and each frame's width and height.
+                            Ignored when profile = 1.                        */
+  int64_t reserved[3];
 } kf_bank_opts;
 
 /* One detection (Threshold #1 extremum). */
@@ -186,6 +205,9 @@ int kf_design(int type, int order, double scale, kf_coeffs *out);
  * |R| > opts->threshold are kept in the context for kf_detect_blobs; a new
  * call replaces them.  Asynchronous on the context stream: the frames must
  * stay valid until the stream reaches this work.
+ * All frames of a call stay resident in the context's workspace (their
+ * one-sided planes, edge rows and carries): a call of many large frames needs
+ * S x (sum of frame pixels) plane elements; split the batch if KF_ENOMEM.
  * Errors: KF_EINVAL (arguments, unsupported option), KF_ECOND, KF_ENOMEM,
  * KF_ECUDA. */
 int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes,
@@ -209,6 +231,36 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out,
  * Synchronises the context stream.  Without profiling, ms is 0.
  * Errors: KF_EINVAL (NULL arguments, no bank call yet), KF_ECUDA. */
 int kf_kernel_times(kf_ctx *ctx, kf_kernel_time *out, int cap, int *n);
+
+/* Passes of a bank (launch-shape tuning).  Recursive banks: row pass (with
+ * the edge rows), column segment states, carry fold, column pass + detector.
+ * FIR bank: row pass, column pass + detector. */
+#define KF_PASS_ROW 0
+#define KF_PASS_SEG 1
+#define KF_PASS_FOLD 2
+#define KF_PASS_DET 3
+#define KF_NPASS 4
+
+/* Launch shape of one pass of one filter type on this context.  Every pass is
+ * a grid of blocks that take the call's work items (rows, column tiles, ...)
+ * in turn:
+ *   grid_mult = 0  one block per work item (the default);
+ *   grid_mult = k  at most k x (blocks resident per SM for this kernel and
+ *                  block size) x (SMs) blocks, each looping over items.
+ * Results do not depend on the shape.  Errors: KF_EINVAL. */
+int kf_set_launch_shape(kf_ctx *ctx, int type, int pass, int grid_mult);
+
+/* Autotuner: run the bank on these frames (as kf_filter_bank would, opts as
+ * there) once per candidate shape (grid_mult 1, 2, 4, 0), time every pass
+ * with CUDA events on the context stream, and keep for each pass of `type`
+ * the fastest shape on this context.  chosen (host, KF_NPASS entries, may be
+ * NULL) receives the choices (passes the type lacks: -1); ms_out (host,
+ * KF_NPASS x 4, may be NULL) the per-pass times of the candidates (ms).
+ * Leaves the last candidate's result as the context's bank result.
+ * Synchronises the context stream.  Errors: those of kf_filter_bank. */
+int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes,
+                const double *scales, int nscales, int type, int order,
+                const kf_bank_opts *opts, int32_t *chosen, float *ms_out);
 
 /* Size of the static scratch that kf_responses_noalloc uses (MiB). */
 #define KF_NOALLOC_SCRATCH_MB 32

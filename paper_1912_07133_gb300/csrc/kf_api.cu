@@ -62,6 +62,28 @@ struct kf_ctx {
   bool have_result = false;
   double last_threshold = 0.0;
   int last_S = 0;
+  // frame table of a call (frames + work-item lists): device copy, uploaded
+  // from a ring of pinned slots (a slot is reused once its copy has run)
+  static constexpr int kRing = 4;
+  unsigned char *d_table = nullptr;
+  size_t table_cap = 0;
+  unsigned char *h_table[kRing] = {};
+  cudaEvent_t table_ev[kRing] = {};
+  int table_next = 0;
+  // graph-mode replays, per call geometry (LRU)
+  struct Graph {
+    std::vector<long long> key;
+    cudaGraphExec_t exec = nullptr;
+    kf::Prof prof{};
+    unsigned long long used = 0;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t cap_stream = nullptr;  // private stream for capture (the caller's may be the legacy stream)
+  // launch shape per filter type and pass (kf_set_launch_shape / kf_autotune).
+  // Default: one block per work item, which measured fastest or within noise
+  // of the persistent shapes for every pass on GB300 (4096^2 and uneven
+  // batches); the persistent shapes remain candidates of the autotuner.
+  int grid_mult[3][KF_NPASS] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
 };
 
 namespace {
@@ -85,9 +107,18 @@ int cuda_fail(kf_ctx *ctx, cudaError_t e, const char *what) {
               cudaGetErrorString(e));
 }
 
+void drop_graphs(kf_ctx *ctx) {
+  for (auto &g : ctx->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();
+}
+
+// Grow a device buffer; a reallocation invalidates the captured graphs (their
+// kernels hold the old pointer).
 template <class T>
 int grow(kf_ctx *ctx, T **p, size_t *have, size_t need, const char *what) {
   if (*have >= need && *p) return KF_OK;
+  drop_graphs(ctx);
   if (*p) cudaFree(*p);
   *p = nullptr;
   *have = 0;
@@ -118,6 +149,7 @@ int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S,
       return KF_OK;
     }
   ctx->cur = nullptr;
+  drop_graphs(ctx);  // a slot may be overwritten: graphs hold coefficient pointers
   cudaError_t e;
   if (!ctx->lambdas) {
     if ((e = cudaMalloc(&ctx->lambdas, sizeof(double) * KF_MAX_SCALES)) != cudaSuccess)
@@ -189,6 +221,62 @@ int check_type_order(kf_ctx *ctx, int type, int order) {
   return KF_OK;
 }
 
+// Upload the call's frame table through the next pinned slot of the ring
+// (waiting, in the rare case, until that slot's previous copy has run).
+int upload_table(kf_ctx *ctx, const void *bytes, size_t n) {
+  cudaError_t e;
+  if (n > ctx->table_cap) {
+    drop_graphs(ctx);  // graphs hold pointers into the old table
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->d_table);
+    ctx->d_table = nullptr;
+    ctx->table_cap = 0;
+    for (int i = 0; i < kf_ctx::kRing; ++i) {
+      if (ctx->h_table[i]) cudaFreeHost(ctx->h_table[i]);
+      ctx->h_table[i] = nullptr;
+    }
+    const size_t cap = std::max(n + n / 2, (size_t)64 << 10);
+    if ((e = cudaMalloc(&ctx->d_table, cap)) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(frame table)");
+    for (int i = 0; i < kf_ctx::kRing; ++i) {
+      if ((e = cudaHostAlloc(&ctx->h_table[i], cap, cudaHostAllocDefault)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaHostAlloc(frame table)");
+      if (!ctx->table_ev[i] && (e = cudaEventCreateWithFlags(&ctx->table_ev[i], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaEventCreate(frame table)");
+    }
+    ctx->table_cap = cap;
+  }
+  const int slot = ctx->table_next++ % kf_ctx::kRing;
+  if ((e = cudaEventSynchronize(ctx->table_ev[slot])) != cudaSuccess) return cuda_fail(ctx, e, "frame table slot");
+  std::memcpy(ctx->h_table[slot], bytes, n);
+  if ((e = cudaMemcpyAsync(ctx->d_table, ctx->h_table[slot], n, cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "upload frame table");
+  if ((e = cudaEventRecord(ctx->table_ev[slot], ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "cudaEventRecord(frame table)");
+  return KF_OK;
+}
+
+// everything a captured launch sequence depends on besides the frame table
+std::vector<long long> call_key(const kf_ctx *ctx, const kf_frame *frames, int nframes, const double *scales, int S,
+                                int type, int order, int kmax, const kf_bank_opts &o) {
+  std::vector<long long> k = {type, order, kmax, S, o.storage, o.neighbourhood, o.schedule, nframes,
+                              (long long)(intptr_t)ctx->cur};
+  for (int p = 0; p < KF_NPASS; ++p) k.push_back(ctx->grid_mult[type][p]);
+  long long t;
+  std::memcpy(&t, &o.threshold, sizeof t);
+  k.push_back(t);
+  for (int s = 0; s < S; ++s) {
+    std::memcpy(&t, &scales[s], sizeof t);
+    k.push_back(t);
+  }
+  for (int f = 0; f < nframes; ++f) {
+    k.push_back(frames[f].width);
+    k.push_back(frames[f].height);
+  }
+  return k;
+}
+
+constexpr size_t kGraphSlots = 4;
+
 }  // namespace
 
 namespace kf {
@@ -252,6 +340,13 @@ void kf_destroy(kf_ctx *ctx) {
   cudaFree(ctx->status);
   cudaFree(ctx->blobs);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+  drop_graphs(ctx);
+  cudaFree(ctx->d_table);
+  for (int i = 0; i < kf_ctx::kRing; ++i) {
+    if (ctx->h_table[i]) cudaFreeHost(ctx->h_table[i]);
+    if (ctx->table_ev[i]) cudaEventDestroy(ctx->table_ev[i]);
+  }
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
@@ -322,8 +417,9 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   if (!(opts.threshold >= 0.0)) return fail(ctx, KF_EINVAL, "threshold must be >= 0");
   const int kmax_opt = opts.fir_kmax > 0 ? opts.fir_kmax : 96;
   if (kmax_opt > KF_MAX_FIR_K) return fail(ctx, KF_EINVAL, "fir_kmax must be <= %d", KF_MAX_FIR_K);
+  if (opts.schedule != KF_SCHED_BATCHED && opts.schedule != KF_SCHED_PER_FRAME)
+    return fail(ctx, KF_EINVAL, "unknown schedule %d", opts.schedule);
   long maxH = 0, maxPW = 0;
-  size_t maxplane = 0;
   for (int f = 0; f < nframes; ++f) {
     const kf_frame &fr = frames[f];
     if (!fr.data) return fail(ctx, KF_EINVAL, "frame %d: data is NULL", f);
@@ -340,7 +436,6 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     const long PW = ((long)fr.width + 31) / 32 * 32;
     maxH = std::max(maxH, (long)fr.height);
     maxPW = std::max(maxPW, PW);
-    maxplane = std::max(maxplane, (size_t)fr.height * PW);
   }
   cudaError_t e;
   if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
@@ -351,20 +446,116 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     nstate = std::max(nstate, ctx->cur->h_coef[s].K);
     kmax = std::max(kmax, ctx->cur->h_coef[s].K);
   }
-  const int nf = (type == KF_IIR_BUTTERWORTH) ? 2 * nstate : nstate;
-  const size_t plane_floats = ((size_t)nscales * maxplane * kf::store_bytes(opts.storage) + 3) / 4;
-  if ((rc = grow(ctx, &ctx->P, &ctx->P_floats, plane_floats, "planes"))) return rc;
-  if ((rc = grow(ctx, &ctx->edge, &ctx->edge_floats, (size_t)nscales * 2 * maxPW, "edge rows"))) return rc;
-  if (type != KF_FIR_COLORED_SG) {
-    size_t need = 0;
-    for (int f = 0; f < nframes; ++f) {
-      const long PW = ((long)frames[f].width + 31) / 32 * 32;
-      need = std::max(need, kf::iir_carry_floats(frames[f].height, PW, nscales, nf));
-    }
-    if ((rc = grow(ctx, &ctx->carry, &ctx->carry_floats, need, "carries"))) return rc;
+  const bool iir = type != KF_FIR_COLORED_SG;
+  const int nfs = (type == KF_IIR_BUTTERWORTH) ? 2 * nstate : nstate;  // states per recursion
+  // ---- layout: every frame resident in one plane row space of pitch PWb ----
+  const long PWb = maxPW;
+  std::vector<kf::FrameDev> fd(nframes);
+  long prows = 0, roff = 0;
+  size_t coff = 0;
+  for (int f = 0; f < nframes; ++f) {
+    const kf_frame &fr = frames[f];
+    kf::FrameDev &d = fd[f];
+    d.X = fr.data;
+    d.resp = opts.responses ? opts.responses + roff : nullptr;
+    d.xpitch = fr.pitch;
+    d.prow = prows;
+    d.eoff = (long)f * nscales * 2 * PWb;
+    d.coff = (long)coff;
+    d.dtype = fr.dtype;
+    d.vscale = fr.value_scale == 0.0f ? 1.0f : fr.value_scale;
+    d.H = fr.height;
+    d.W = fr.width;
+    d.nseg = iir ? kf::iir_segments(fr.height) : 0;
+    d.index = f;
+    prows += (long)nscales * fr.height;
+    roff += (long)nscales * fr.height * fr.width;
+    if (iir) coff += (size_t)nscales * d.nseg * 2 * nfs * PWb;
   }
-  if ((e = cudaMemsetAsync(ctx->status, 0, sizeof(kf::DevStatus), ctx->stream)) != cudaSuccess)
-    return cuda_fail(ctx, e, "reset status");
+  const size_t plane_floats = ((size_t)prows * PWb * kf::store_bytes(opts.storage) + 3) / 4;
+  if ((rc = grow(ctx, &ctx->P, &ctx->P_floats, plane_floats, "planes"))) return rc;
+  if ((rc = grow(ctx, &ctx->edge, &ctx->edge_floats, (size_t)nframes * nscales * 2 * PWb, "edge rows"))) return rc;
+  if (iir && (rc = grow(ctx, &ctx->carry, &ctx->carry_floats, std::max(coff, (size_t)1), "carries"))) return rc;
+  // ---- work-item lists of the launches --------------------------------------
+  struct L {
+    int pass, nt, n, total;
+    size_t fl, pre;  // offsets (ints) in the pool
+  };
+  std::vector<int> pool;
+  std::vector<L> ls;
+  auto items = [&](int pass, int f) {
+    return iir ? kf::iir_items(pass, fd[f].H, fd[f].W, nscales)
+               : kf::fir_items(pass, fd[f].H, fd[f].W, nscales, opts.neighbourhood);
+  };
+  auto add = [&](int pass, const std::vector<int> &fl, int nt) {
+    L l{pass, nt, (int)fl.size(), 0, pool.size(), 0};
+    pool.insert(pool.end(), fl.begin(), fl.end());
+    l.pre = pool.size();
+    long tot = 0;
+    pool.push_back(0);
+    for (int f : fl) {
+      tot += items(pass, f);
+      pool.push_back((int)std::min(tot, (long)INT32_MAX));
+    }
+    l.total = (int)std::min(tot, (long)INT32_MAX);
+    ls.push_back(l);
+    return tot <= INT32_MAX;
+  };
+  const std::vector<int> passes = iir ? std::vector<int>{kf::PASS_ROW, kf::PASS_SEG, kf::PASS_FOLD, kf::PASS_DET}
+                                      : std::vector<int>{kf::PASS_ROW, kf::PASS_DET};
+  bool fits = true;
+  if (opts.schedule == KF_SCHED_PER_FRAME) {
+    for (int p : passes)
+      for (int f = 0; f < nframes; ++f)
+        fits &= add(p, {f}, (iir && p == kf::PASS_ROW) ? kf::iir_row_threads(fd[f].W) : 0);
+  } else {
+    for (int p : passes) {
+      if (iir && p == kf::PASS_ROW) {  // one launch per block width (width class)
+        std::vector<int> nts;
+        for (int f = 0; f < nframes; ++f) nts.push_back(kf::iir_row_threads(fd[f].W));
+        std::vector<int> classes = nts;
+        std::sort(classes.begin(), classes.end());
+        classes.erase(std::unique(classes.begin(), classes.end()), classes.end());
+        for (int nt : classes) {
+          std::vector<int> fl;
+          for (int f = 0; f < nframes; ++f)
+            if (nts[f] == nt) fl.push_back(f);
+          fits &= add(p, fl, nt);
+        }
+      } else {
+        std::vector<int> fl(nframes);
+        for (int f = 0; f < nframes; ++f) fl[f] = f;
+        fits &= add(p, fl, 0);
+      }
+    }
+  }
+  if (!fits) return fail(ctx, KF_EINVAL, "too many work items in one call: split the batch");
+  for (const L &l : ls)
+    if (iir && l.pass == kf::PASS_ROW && l.nt == 0) return fail(ctx, KF_EINVAL, "frame too wide for the row pass");
+  // ---- frame table: FrameDev[nframes] | int pool -----------------------------
+  const size_t fd_bytes = sizeof(kf::FrameDev) * nframes;
+  const size_t pool_off = (fd_bytes + 15) / 16 * 16;
+  std::vector<unsigned char> table(pool_off + pool.size() * sizeof(int));
+  std::memcpy(table.data(), fd.data(), fd_bytes);
+  std::memcpy(table.data() + pool_off, pool.data(), pool.size() * sizeof(int));
+  if ((rc = upload_table(ctx, table.data(), table.size()))) return rc;
+  kf::Plan plan;
+  plan.fr = reinterpret_cast<const kf::FrameDev *>(ctx->d_table);
+  plan.nframes = nframes;
+  plan.PWb = PWb;
+  plan.prows = prows;
+  plan.per_frame = opts.schedule == KF_SCHED_PER_FRAME;
+  for (int p = 0; p < KF_NPASS; ++p) plan.mult[p] = ctx->grid_mult[type][p];
+  const int *dpool = reinterpret_cast<const int *>(ctx->d_table + pool_off);
+  for (const L &l : ls) {
+    kf::Launch x;
+    x.it.fl = dpool + l.fl;
+    x.it.pre = dpool + l.pre;
+    x.it.n = l.n;
+    x.it.total = l.total;
+    x.nt = l.nt;
+    plan.pass[l.pass].push_back(x);
+  }
   kf::BankArgs a;
   a.coef = ctx->cur->d_coef;
   a.S = nscales;
@@ -380,39 +571,75 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   a.blobs = ctx->blobs;
   a.cap = ctx->blob_cap;
   a.status = ctx->status;
-  a.responses = opts.responses;
-  ctx->prof = kf::Prof{};
-  ctx->prof.ev = nullptr;
-  if (opts.profile) {
-    const int need = 2 * 256;
-    while ((int)ctx->events.size() < need) {
-      cudaEvent_t ev;
-      if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventCreate");
-      ctx->events.push_back(ev);
-    }
-    ctx->prof.ev = ctx->events.data();
-    ctx->prof.cap = 256;
-  }
-  a.prof = &ctx->prof;
-  ctx->have_prof = true;
-  long resp_off = 0;
-  for (int f = 0; f < nframes; ++f) {
-    const kf_frame &fr = frames[f];
-    kf::FrameGeom g;
-    g.X = fr.data;
-    g.dtype = fr.dtype;
-    g.vscale = fr.value_scale == 0.0f ? 1.0f : fr.value_scale;
-    g.xpitch = fr.pitch;
-    g.H = fr.height;
-    g.W = fr.width;
-    g.PW = ((long)fr.width + 31) / 32 * 32;
-    g.frame = f;
-    g.resp_off = resp_off;
-    resp_off += (long)nscales * fr.height * fr.width;
-    int lr = (type == KF_FIR_COLORED_SG) ? kf::launch_fir_frame(g, a, ctx->stream)
-                                         : kf::launch_iir_frame(g, a, ctx->stream);
+  // status reset + all passes, on stream st
+  auto issue = [&](cudaStream_t st, kf::Prof *prof) -> int {
+    cudaError_t ee;
+    if ((ee = cudaMemsetAsync(ctx->status, 0, sizeof(kf::DevStatus), st)) != cudaSuccess)
+      return cuda_fail(ctx, ee, "reset status");
+    a.prof = prof;
+    const int lr = iir ? kf::launch_iir(plan, a, st) : kf::launch_fir(plan, a, st);
     if (lr == -2) return fail(ctx, KF_EINVAL, "no kernel instance for order %d", order);
     if (lr) return cuda_fail(ctx, cudaGetLastError(), "filter-bank kernel launch");
+    return KF_OK;
+  };
+  ctx->prof = kf::Prof{};
+  ctx->prof.ev = nullptr;
+  ctx->have_prof = true;
+  if (opts.graph && !opts.profile) {
+    const std::vector<long long> key = call_key(ctx, frames, nframes, scales, nscales, type, order, kmax_opt, opts);
+    kf_ctx::Graph *g = nullptr;
+    for (auto &x : ctx->graphs)
+      if (x.key == key) g = &x;
+    if (!g) {  // first call of this geometry: run eagerly, remember it
+      if (ctx->graphs.size() >= kGraphSlots) {
+        auto lru = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                    [](const kf_ctx::Graph &p, const kf_ctx::Graph &q) { return p.used < q.used; });
+        if (lru->exec) cudaGraphExecDestroy(lru->exec);
+        ctx->graphs.erase(lru);
+      }
+      ctx->graphs.emplace_back();
+      ctx->graphs.back().key = key;
+      ctx->graphs.back().used = ++ctx->tick;
+      if ((rc = issue(ctx->stream, &ctx->prof))) return rc;
+    } else {
+      g->used = ++ctx->tick;
+      if (!g->exec) {  // second call: capture on the private stream, instantiate
+        if (!ctx->cap_stream && (e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+          return cuda_fail(ctx, e, "cudaStreamCreate(capture)");
+        kf::Prof cp{};
+        cp.ev = nullptr;
+        if ((e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+          return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+        const int irc = issue(ctx->cap_stream, &cp);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (irc || e != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          return irc ? irc : cuda_fail(ctx, e, "cudaStreamEndCapture");
+        }
+        e = cudaGraphInstantiate(&g->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+          g->exec = nullptr;
+          return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        }
+        g->prof = cp;
+      }
+      if ((e = cudaGraphLaunch(g->exec, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+      ctx->prof = g->prof;
+    }
+  } else {
+    if (opts.profile) {
+      const int need = 2 * 256;
+      while ((int)ctx->events.size() < need) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventCreate");
+        ctx->events.push_back(ev);
+      }
+      ctx->prof.ev = ctx->events.data();
+      ctx->prof.cap = 256;
+    }
+    if ((rc = issue(ctx->stream, &ctx->prof))) return rc;
   }
   ctx->have_result = true;
   ctx->sorted_valid = false;
@@ -422,6 +649,80 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   ctx->last_hmax = maxH;
   ctx->last_wmax = 0;
   for (int f = 0; f < nframes; ++f) ctx->last_wmax = std::max(ctx->last_wmax, (long)frames[f].width);
+  return KF_OK;
+}
+
+int kf_set_launch_shape(kf_ctx *ctx, int type, int pass, int grid_mult) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_set_launch_shape: ctx is NULL");
+  if (type < 0 || type > 2) return fail(ctx, KF_EINVAL, "unknown filter type %d", type);
+  if (pass < 0 || pass >= KF_NPASS) return fail(ctx, KF_EINVAL, "unknown pass %d", pass);
+  if (grid_mult < 0 || grid_mult > 64) return fail(ctx, KF_EINVAL, "grid_mult must be 0..64");
+  if (ctx->grid_mult[type][pass] != grid_mult) {
+    drop_graphs(ctx);  // grid sizes are part of the captured launches
+    ctx->grid_mult[type][pass] = grid_mult;
+  }
+  return KF_OK;
+}
+
+int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *scales, int nscales, int type,
+                int order, const kf_bank_opts *opts_in, int32_t *chosen, float *ms_out) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_autotune: ctx is NULL");
+  if (type < 0 || type > 2) return fail(ctx, KF_EINVAL, "unknown filter type %d", type);
+  kf_bank_opts o;
+  if (opts_in) o = *opts_in;
+  else kf_bank_opts_default(&o);
+  o.profile = 1;
+  o.graph = 0;
+  constexpr int kCand[4] = {1, 2, 4, 0};
+  float ms[KF_NPASS][4];
+  for (auto &r : ms)
+    for (float &x : r) x = -1.f;
+  const int saved[KF_NPASS] = {ctx->grid_mult[type][0], ctx->grid_mult[type][1], ctx->grid_mult[type][2],
+                               ctx->grid_mult[type][3]};
+  auto pass_of = [](const char *name) {
+    const std::string n = name;
+    if (n == "iir_row" || n == "fir_row") return (int)KF_PASS_ROW;
+    if (n == "iir_colseg") return (int)KF_PASS_SEG;
+    if (n == "iir_colfold") return (int)KF_PASS_FOLD;
+    if (n == "iir_coldet" || n == "fir_coldet") return (int)KF_PASS_DET;
+    return -1;
+  };
+  cudaError_t e;
+  for (int c = 0; c < 4; ++c) {
+    for (int p = 0; p < KF_NPASS; ++p) ctx->grid_mult[type][p] = kCand[c];
+    float acc[KF_NPASS] = {0, 0, 0, 0};
+    bool seen[KF_NPASS] = {false, false, false, false};
+    for (int rep = 0; rep < 3; ++rep) {  // one warm-up, two timed
+      int rc = kf_filter_bank(ctx, frames, nframes, scales, nscales, type, order, &o);
+      if (rc) {
+        for (int p = 0; p < KF_NPASS; ++p) ctx->grid_mult[type][p] = saved[p];
+        return rc;
+      }
+      if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+      if (rep == 0) continue;
+      const kf::Prof &pr = ctx->prof;
+      for (int i = 0; i < pr.n && i < pr.cap; ++i) {
+        const int p = pass_of(pr.names[i]);
+        if (p < 0) continue;
+        float t = 0.f;
+        if ((e = cudaEventElapsedTime(&t, pr.ev[2 * i], pr.ev[2 * i + 1])) != cudaSuccess)
+          return cuda_fail(ctx, e, "cudaEventElapsedTime");
+        acc[p] += t;
+        seen[p] = true;
+      }
+    }
+    for (int p = 0; p < KF_NPASS; ++p) ms[p][c] = seen[p] ? acc[p] / 2.f : -1.f;
+  }
+  for (int p = 0; p < KF_NPASS; ++p) {
+    int best = -1;
+    for (int c = 0; c < 4; ++c)
+      if (ms[p][c] >= 0.f && (best < 0 || ms[p][c] < ms[p][best])) best = c;
+    ctx->grid_mult[type][p] = best < 0 ? saved[p] : kCand[best];
+    if (chosen) chosen[p] = best < 0 ? -1 : kCand[best];
+    if (ms_out)
+      for (int c = 0; c < 4; ++c) ms_out[p * 4 + c] = ms[p][c];
+  }
+  drop_graphs(ctx);
   return KF_OK;
 }
 
@@ -482,6 +783,7 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
   if (st.count > (unsigned long long)ctx->blob_cap) {
     *count = (int64_t)st.count;
     // grow for the next call; this call's list is incomplete
+    drop_graphs(ctx);
     cudaFree(ctx->blobs);
     ctx->blobs = nullptr;
     long ncap = (long)st.count + (long)st.count / 4 + 1024;

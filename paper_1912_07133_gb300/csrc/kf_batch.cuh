@@ -1,0 +1,56 @@
+// kf_batch.cuh -- frame table and work-item lists of a bank call.
+//
+// Every frame of a call keeps its one-sided planes resident in one "plane row
+// space" of pitch PWb (the widest frame's pitch): scale s, row y of frame f is
+// plane row F.prow + s F.H + y.  One 2-D tensor map covers the whole space, so
+// the TMA kernels serve all frames with one map; a box that reaches past a
+// frame's first or last row reads a neighbouring plane (or the fill value),
+// and those rows are replaced by the held boundary values anyway.
+//
+// A launch covers a list of frames; its work items (rows, column tiles, ...)
+// are numbered frame after frame.  Kernels run persistently: block b takes
+// items b, b + gridDim.x, ... and finds the frame of an item by advancing a
+// monotone index over the exclusive prefix sums of the items per frame.
+#pragma once
+#include "kf_common.cuh"
+
+namespace kf {
+
+struct FrameDev {
+  const void *X;   // input frame (IN_* elements)
+  float *resp;     // responses of this frame (S x H x W), or nullptr
+  long xpitch;     // input elements between rows
+  long prow;       // plane row of (scale 0, frame row 0)
+  long eoff;       // floats: edge rows [S][2][PWb]
+  long coff;       // floats: IIR column carries [S][nseg][2][NF][PWb]
+  int dtype;       // IN_F32 / IN_F16 / IN_BF16 / IN_U16
+  float vscale;    // input multiplier
+  int H, W;
+  int nseg;        // IIR column segments
+  int index;       // frame index in the call (blob records)
+};
+
+struct Items {
+  const int *fl;   // frames of this launch: indices into the frame table
+  const int *pre;  // exclusive prefix sums of the items per frame (n + 1 entries)
+  int n;           // frames in the launch
+  int total;       // items in the launch (pre[n])
+};
+
+// position in it.fl of the frame that holds `item`, starting the search at k
+// (the items a block takes only increase, so k only advances)
+__device__ __forceinline__ int advance_frame(const Items &it, int item, int k) {
+  while (item >= __ldg(it.pre + k + 1)) ++k;
+  return k;
+}
+
+// Heavy kernels (near their register limit) keep the current item's frame
+// record in shared memory: the compiler may otherwise re-load its fields from
+// global memory at every use.  Thread 0 copies it; the caller synchronises
+// before and after (the previous item's readers must be done).
+__device__ __forceinline__ void stage_frame(FrameDev *dst, const FrameDev *__restrict__ fr, const Items &it,
+                                            int k) {
+  if (threadIdx.x == 0) *dst = fr[__ldg(it.fl + k)];
+}
+
+}  // namespace kf

@@ -8,16 +8,22 @@
 // the left/right edges and V is held; in y the roles swap (the y-blur input
 // outside the frame is blur_x(U) of the first/last row, held).
 //
-//   k_rowfir    one CTA per (row, 1024-pixel segment): L with a K-pixel halo
-//               in shared memory, 4 outputs per thread with a sliding register
-//               window, all scales.
-//   k_rowfir<EDGE> the same on U alone for rows 0 and H-1.
-//   k_colfir    64 rows x 32 columns x all scales per CTA: per scale the
-//               input block (64 + 2K rows) is staged in shared memory, each
-//               warp slides an 8-row register window down its column; then
-//               the detector.
+// Passes (each persistent over the work items of the frames it covers, see
+// kf_batch.cuh):
+//   k_rowfir      (row, 2048-pixel segment) items: L with a K-pixel halo in
+//                 shared memory, 16 outputs per thread in 8-tap register
+//                 blocks, all scales; two extra rows per frame on U alone.
+//   k_colfir_tma  128 rows x 32 columns x all scales per item, TMA-staged,
+//                 all-scales detector.
+//   k_colfir      64 rows x 32 columns, adjacent-scales detector.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "kf_batch.cuh"
 #include "kf_common.cuh"
 #include "kf_detect.cuh"
 #include "kf_internal.h"
@@ -113,97 +119,133 @@ __device__ __forceinline__ void fir_row_block(const float *sh, int K, const floa
 // halo of the row kernel: >= kmax + TB, a multiple of 16
 __host__ __device__ __forceinline__ int row_halo(int kmax) { return (kmax + TB + 15) / 16 * 16; }
 
-template <bool EDGE>
-__global__ void __launch_bounds__(RNT) k_rowfir(const void *__restrict__ X, long xpitch, int dt, float vs, int H,
-                                                int W, const Coef *__restrict__ coef, int S, int kmax,
-                                                void *__restrict__ P, int st, long PW,
-                                                float *__restrict__ edge, DevStatus *__restrict__ status) {
+// Row pass.  Item: a segment of RSEG outputs of one row of a frame; items
+// beyond the frame's H rows are its U-only first and last rows.
+__global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr, Items it,
+                                                const Coef *__restrict__ coef, int S, int kmax,
+                                                void *__restrict__ P, int st, long PWb, float *__restrict__ edge,
+                                                DevStatus *__restrict__ status) {
   extern __shared__ __align__(16) float sm[];
   const int tid = threadIdx.x;
-  const int y = EDGE ? (blockIdx.y == 0 ? 0 : H - 1) : blockIdx.y;
-  const int xs = blockIdx.x * RSEG;
   // L on [xs - G, xs + RSEG + G): the 8-tap blocks read up to TB elements past
   // the last tap on each side
   const int G = row_halo(kmax);
   const int n = RSEG + 2 * G;
   float *sL = sm;                       // padded: element j at pad20(j)
   float *sh = sm + pad20(n) + 4;
-  with_input_type(X, dt, [&](auto Xt) {
-    const auto *rm = Xt + (long)max(y - 1, 0) * xpitch;
-    const auto *r0 = Xt + (long)y * xpitch;
-    const auto *rp = Xt + (long)min(y + 1, H - 1) * xpitch;
-    auto ld = [&](const decltype(Xt) row, int e) { return vs * in_f32(__ldg(row + e)); };
-    const float vlo = ld(rp, 0) - 2.f * ld(r0, 0) + ld(rm, 0);
-    const float vhi = ld(rp, W - 1) - 2.f * ld(r0, W - 1) + ld(rm, W - 1);
-    for (int j = tid; j < n; j += RNT) {
-      const int e = xs - G + j;
-      float v;
-      if (e < 0) v = EDGE ? 0.f : vlo;
-      else if (e >= W) v = EDGE ? 0.f : vhi;
-      else {
-        const float c0 = ld(r0, e);
-        const float u = ld(r0, min(e + 1, W - 1)) - 2.f * c0 + ld(r0, max(e - 1, 0));
-        v = EDGE ? u : u + (ld(rp, e) - 2.f * c0 + ld(rm, e));
-      }
-      sL[pad20(j)] = v;
-    }
-  });
-  const int base = G + NOUT * tid;  // local index of this thread's first output
-  bool ovf = false;                 // a value beyond the f16 range
-  for (int s = 0; s < S; ++s) {
-    const Coef &c = coef[s];
-    const int K = c.K;
+  __shared__ FrameDev s_fr;
+  bool ovf = false;                     // a value beyond the f16 range
+  int k = 0;
+  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
+    k = advance_frame(it, item, k);
+    __syncthreads();  // the previous item is done with s_fr and sL
+    stage_frame(&s_fr, fr, it, k);
     __syncthreads();
-    stage_taps(sh, c, K, tid, RNT);
-    __syncthreads();
-    float acc[NOUT];
-    fir_row_block(sh, K, sL, base, acc);
-    // planes hold sigma^2 x the one-sided blur (the column pass only negates)
-    const float s2 = c.sigma2;
+    const FrameDev &F = s_fr;
+    const int local = item - __ldg(it.pre + k);
+    const int H = F.H, W = F.W;
+    const int nxs = (W + RSEG - 1) / RSEG;
+    const int xs = (local % nxs) * RSEG, ri = local / nxs;
+    const bool EDGE = ri >= H;            // U alone: first (ri = H) or last (ri = H + 1) row
+    const int which = ri - H;
+    const int y = EDGE ? (which == 0 ? 0 : H - 1) : ri;
+    const float vs = F.vscale;
+    const long xpitch = F.xpitch;
+    with_input_type(F.X, F.dtype, [&](auto Xt) {
+      const auto *rm = Xt + (long)max(y - 1, 0) * xpitch;
+      const auto *r0 = Xt + (long)y * xpitch;
+      const auto *rp = Xt + (long)min(y + 1, H - 1) * xpitch;
+      auto ld = [&](const decltype(Xt) row, int e) { return vs * in_f32(__ldg(row + e)); };
+      const float vlo = ld(rp, 0) - 2.f * ld(r0, 0) + ld(rm, 0);
+      const float vhi = ld(rp, W - 1) - 2.f * ld(r0, W - 1) + ld(rm, W - 1);
+      // 4 elements (20 loads, clamped into the row) per thread in flight
+      for (int j0 = tid; j0 < n; j0 += 4 * RNT) {
+        float cm[4], c0[4], cp[4], um[4], up[4];
 #pragma unroll
-    for (int j = 0; j < NOUT; ++j) acc[j] *= s2;
-    const int x0 = xs + NOUT * tid;
-    const long row = (long)s * H * PW + (long)y * PW;
-    if (EDGE || st == ST_F32) {
-      float *dst = EDGE ? edge + ((long)s * 2 + blockIdx.y) * PW : static_cast<float *>(P) + row;
-      if (x0 + NOUT <= W) {
+        for (int u = 0; u < 4; ++u) {
+          const int e = min(max(xs - G + j0 + u * RNT, 0), W - 1);
+          c0[u] = ld(r0, e);
+          um[u] = ld(r0, max(e - 1, 0));
+          up[u] = ld(r0, min(e + 1, W - 1));
+          cm[u] = ld(rm, e);
+          cp[u] = ld(rp, e);
+        }
 #pragma unroll
-        for (int j = 0; j < NOUT; j += 4)
-          *reinterpret_cast<float4 *>(dst + x0 + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < NOUT; ++j)
-          if (x0 + j < W) dst[x0 + j] = acc[j];
-      }
-    } else {
-      // 16-bit planes: four values per 8-byte store
-      unsigned short *dst = static_cast<unsigned short *>(P) + row;
-      unsigned short h[NOUT];
-#pragma unroll
-      for (int j = 0; j < NOUT; ++j) {
-        if (st == ST_F16) {
-          ovf |= x0 + j < W && fabsf(acc[j]) > F16_MAX;
-          h[j] = __half_as_ushort(__float2half_rn(acc[j]));
-        } else {
-          h[j] = __bfloat16_as_ushort(__float2bfloat16_rn(acc[j]));
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u * RNT, e = xs - G + j;
+          if (j >= n) continue;
+          float v;
+          if (e < 0) v = EDGE ? 0.f : vlo;
+          else if (e >= W) v = EDGE ? 0.f : vhi;
+          else {
+            const float uu = up[u] - 2.f * c0[u] + um[u];
+            v = EDGE ? uu : uu + (cp[u] - 2.f * c0[u] + cm[u]);
+          }
+          sL[pad20(j)] = v;
         }
       }
-      if (x0 + NOUT <= W) {
+    });
+    const int base = G + NOUT * tid;  // local index of this thread's first output
+    for (int s = 0; s < S; ++s) {
+      const Coef &c = coef[s];
+      const int K = c.K;
+      __syncthreads();
+      stage_taps(sh, c, K, tid, RNT);
+      __syncthreads();
+      float acc[NOUT];
+      fir_row_block(sh, K, sL, base, acc);
+      // planes hold sigma^2 x the one-sided blur (the column pass only negates)
+      const float s2 = c.sigma2;
 #pragma unroll
-        for (int j = 0; j < NOUT; j += 4)
-          *reinterpret_cast<uint2 *>(dst + x0 + j) =
-              make_uint2(h[j] | ((unsigned)h[j + 1] << 16), h[j + 2] | ((unsigned)h[j + 3] << 16));
+      for (int j = 0; j < NOUT; ++j) acc[j] *= s2;
+      const int x0 = xs + NOUT * tid;
+      const long row = (F.prow + (long)s * H + y) * PWb;
+      if (EDGE || st == ST_F32) {
+        float *dst = EDGE ? edge + F.eoff + ((long)s * 2 + which) * PWb : static_cast<float *>(P) + row;
+        if (x0 + NOUT <= W) {
+#pragma unroll
+          for (int j = 0; j < NOUT; j += 4)
+            *reinterpret_cast<float4 *>(dst + x0 + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < NOUT; ++j)
+            if (x0 + j < W) dst[x0 + j] = acc[j];
+        }
       } else {
+        // 16-bit planes: four values per 8-byte store
+        unsigned short *dst = static_cast<unsigned short *>(P) + row;
+        unsigned short h[NOUT];
 #pragma unroll
-        for (int j = 0; j < NOUT; ++j)
-          if (x0 + j < W) dst[x0 + j] = h[j];
+        for (int j = 0; j < NOUT; ++j) {
+          if (st == ST_F16) {
+            ovf |= x0 + j < W && fabsf(acc[j]) > F16_MAX;
+            h[j] = __half_as_ushort(__float2half_rn(acc[j]));
+          } else {
+            h[j] = __bfloat16_as_ushort(__float2bfloat16_rn(acc[j]));
+          }
+        }
+        if (x0 + NOUT <= W) {
+#pragma unroll
+          for (int j = 0; j < NOUT; j += 4)
+            *reinterpret_cast<uint2 *>(dst + x0 + j) =
+                make_uint2(h[j] | ((unsigned)h[j + 1] << 16), h[j + 2] | ((unsigned)h[j + 3] << 16));
+        } else {
+#pragma unroll
+          for (int j = 0; j < NOUT; ++j)
+            if (x0 + j < W) dst[x0 + j] = h[j];
+        }
       }
     }
   }
   if (ovf) atomicExch(&status->range, 1);
 }
 
-__global__ void __launch_bounds__(CNT) k_colfir(const void *__restrict__ P, int st, long PW, int H, int W,
+// Column FIR + detector, adjacent-scales neighbourhood.  Item: 64 rows x 32
+// columns of a frame, all scales: per scale the input block (64 + 2(K+8)
+// rows) is staged in shared memory, each warp slides an 8-row register window
+// down its column; then the detector on the R tile of every scale.
+__global__ void __launch_bounds__(CNT) k_colfir(const FrameDev *__restrict__ fr, Items it,
+                                                const void *__restrict__ P, int st, long PWb,
                                                 const float *__restrict__ edge,
                                                 const Coef *__restrict__ coef, int S, int kmax,
                                                 DetectArgs da) {
@@ -215,43 +257,60 @@ __global__ void __launch_bounds__(CNT) k_colfir(const void *__restrict__ P, int 
   float *buf = sm + (long)NIN * 32;             // [S][CROWS][32]
   float *red = buf + (long)S * CROWS * 32;
   float *sh = red + CROWS * 32 * 2 + CROWS * 32 * 2 / 4;
-  const int x = blockIdx.x * TW - 1 + lane;
-  const int xv = min(max(x, 0), W - 1);
-  const int r0 = blockIdx.y * (CROWS - 2) - 1;  // frame row of output row 0
-  for (int s = 0; s < S; ++s) {
-    const Coef &c = coef[s];
-    const int K = c.K;
-    const long pc = (long)s * H * PW + xv;
-    const float top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
+  __shared__ FrameDev s_fr;
+  int k = 0;
+  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
+    k = advance_frame(it, item, k);
+    stage_frame(&s_fr, fr, it, k);  // the previous item ended with __syncthreads
     __syncthreads();
-    stage_taps(sh, c, K, threadIdx.x, CNT);
-    // in[j] = input row r0 - G + j
-    for (int j = warp; j < NIN; j += CNT / 32) {
-      const int r = r0 - G + j;
-      in[j * 32 + lane] = r < 0 ? top : (r >= H ? bot : load_plane(P, pc + (long)r * PW, st));
+    const FrameDev &F = s_fr;
+    const int local = item - __ldg(it.pre + k);
+    const int H = F.H, W = F.W;
+    const int ntx = (W + TW - 1) / TW;
+    const int x = (local % ntx) * TW - 1 + lane;
+    const int xv = min(max(x, 0), W - 1);
+    const int r0 = (local / ntx) * (CROWS - 2) - 1;  // frame row of output row 0
+    for (int s = 0; s < S; ++s) {
+      const Coef &c = coef[s];
+      const int K = c.K;
+      const long pc = (F.prow + (long)s * H) * PWb + xv;
+      const float *ed = edge + F.eoff + (long)s * 2 * PWb + xv;
+      const float top = ed[0], bot = ed[PWb];
+      __syncthreads();
+      stage_taps(sh, c, K, threadIdx.x, CNT);
+      // in[j] = input row r0 - G + j
+      for (int j = warp; j < NIN; j += CNT / 32) {
+        const int r = r0 - G + j;
+        in[j * 32 + lane] = r < 0 ? top : (r >= H ? bot : load_plane(P, pc + (long)r * PWb, st));
+      }
+      __syncthreads();
+      const float *col = in + lane + (G + NOUT * warp) * 32;  // output row NOUT*warp
+      float acc[NOUT];
+      fir_block(sh, K, [&](int t) { return col[t * 32]; }, acc);
+#pragma unroll
+      for (int j = 0; j < NOUT; ++j) buf[((long)s * CROWS + NOUT * warp + j) * 32 + lane] = -acc[j];
     }
     __syncthreads();
-    const float *col = in + lane + (G + NOUT * warp) * 32;  // output row NOUT*warp
-    float acc[NOUT];
-    fir_block(sh, K, [&](int t) { return col[t * 32]; }, acc);
-#pragma unroll
-    for (int j = 0; j < NOUT; ++j) buf[((long)s * CROWS + NOUT * warp + j) * 32 + lane] = -acc[j];
+    DetectArgs a = da;
+    a.S = S;
+    a.NR = CROWS;
+    a.x0 = (local % ntx) * TW - 1;
+    a.r0 = r0;
+    a.H = H;
+    a.W = W;
+    a.frame = F.index;
+    a.resp = F.resp;
+    detect_tile(buf, red, a);
+    __syncthreads();
   }
-  __syncthreads();
-  DetectArgs a = da;
-  a.S = S;
-  a.NR = CROWS;
-  a.x0 = blockIdx.x * TW - 1;
-  a.r0 = r0;
-  detect_tile(buf, red, a);
 }
 
-// Column FIR + detector, all-scales neighbourhood.  A CTA of 8 warps covers
-// 32 columns x 128 rows (row 0 and row 127 are halo); per scale the input
-// block (128 + 2(K+8) rows of the one-sided plane) arrives by TMA while an
-// earlier scale is filtered; rows outside the frame take the held values.
-// Each thread keeps the running maximum / minimum over scales of its 16
-// pixels in registers (their first scale in shared memory); the spatial
+// Column FIR + detector, all-scales neighbourhood.  Item: 32 columns x 128
+// rows of a frame (row 0 and row 127 are halo), a CTA of 8 warps; per scale
+// the input block (128 + 2(K+8) rows of the one-sided plane) arrives by TMA
+// while an earlier scale is filtered; rows outside the frame take the held
+// values.  Each thread keeps the running maximum / minimum over scales of its
+// 16 pixels in registers (their first scale in shared memory); the spatial
 // 3 x 3 test runs once at the end on those extremes.
 //
 // f32 planes: two stages of 36-float rows (x a multiple of 4 floats), the
@@ -271,7 +330,8 @@ __host__ __device__ constexpr int colfir_stage_floats(int stage_rows) {
 
 template <int ST>
 __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ CUtensorMap map,
-                                                        const float *__restrict__ edge, long PW, int H, int W,
+                                                        const FrameDev *__restrict__ fr, Items it,
+                                                        const float *__restrict__ edge, long PWb,
                                                         const Coef *__restrict__ coef, int S, int stage_rows,
                                                         int taps_len, DetectArgs da) {
   using T = typename Store<ST>::T;
@@ -289,121 +349,148 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
   auto taps = [&](int b) { return sm + SF + b * taps_len; };
   unsigned char *amx = reinterpret_cast<unsigned char *>(sm + SF + 2 * taps_len);
   unsigned char *amn = amx + CROWS2 * 32;
-  const int x0 = blockIdx.x * TW - 1;  // frame column of lane 0
-  const int off = ((x0 % XA) + XA) % XA;
-  const int xa = x0 - off;
-  const int r0 = blockIdx.y * (CROWS2 - 2) - 1;  // frame row of output row 0
-  const int x = x0 + lane, xv = min(max(x, 0), W - 1);
-  const bool xin = x >= 0 && x < W;
-  float mxr[NOUT], mnr[NOUT];
-#pragma unroll
-  for (int j = 0; j < NOUT; ++j) {
-    const int p = (NOUT * warp + j) * 32 + lane;
-    mxr[j] = -CUDART_INF_F;
-    mnr[j] = CUDART_INF_F;
-    amx[p] = (unsigned char)S;
-    amn[p] = (unsigned char)S;
-  }
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
     fence_proxy_async();
   }
   __syncthreads();
-  auto issue = [&](int s, int b) {  // thread 0 only
-    const int G = coef[s].K + TB;
-    const int nb = (CROWS2 + 2 * G + BOXH - 1) / BOXH;
-    fence_proxy_async();
-    mbar_arrive_expect_tx(&mbar[b], (uint32_t)(nb * BOXH * BW * sizeof(T)));
-    for (int i = 0; i < nb; ++i)
-      if (!tma_load_3d(land(b) + i * BOXH * BW, &map, xa, r0 - G + i * BOXH, s, &mbar[b], (int)sizeof(T)))
-        atomicExch(&da.status->error, 2);
-  };
-  // scales from the longest filter down (the order of the caller's scales is
-  // kept for ties: the first scale attaining an extreme is the one reported)
-  if (tid == 0) {
-    issue(S - 1, 0);
-    if (!F32 && S > 1) issue(S - 2, 1);
-  }
-  const long plane = (long)H * W;
-  for (int it = 0; it < S; ++it) {
-    const int s = S - 1 - it;
-    const int b = it & 1;
-    if (F32 && tid == 0 && it + 1 < S) issue(s - 1, b ^ 1);
-    const Coef &c = coef[s];
-    const int K = c.K, G = K + TB, nin = CROWS2 + 2 * G;
-    stage_taps(taps(b), c, K, tid, CNT2);
-    const bool ok = mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1), WAIT_LIMIT);
-    if (__syncthreads_or(!ok)) {
-      // a load never completed: report, let the other stage's load finish, stop
-      if (tid == 0) {
-        atomicExch(&da.status->error, 1);
-        if (it + 1 < S) mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), WAIT_LIMIT);
-      }
-      __syncthreads();
-      return;
-    }
-    const bool outside = r0 - G < 0 || r0 + CROWS2 + G > H;
-    float top = 0.f, bot = 0.f;
-    if (outside) top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
-    const float *tile;
-    if constexpr (F32) {
-      float *st = land(b);
-      if (outside) {  // rows outside the frame: held values
-        for (int j = warp; j < nin; j += CNT2 / 32) {
-          const int r = r0 - G + j;
-          if (r < 0) st[j * BOXW + off + lane] = top;
-          else if (r >= H) st[j * BOXW + off + lane] = bot;
-        }
-      }
-      tile = st + off;
-      __syncthreads();
-    } else {
-      const T *src = land(b) + off + lane;
-      for (int j = warp; j < nin; j += CNT2 / 32) {
-        const int r = r0 - G + j;
-        const float v = Store<ST>::ld(src[j * BW]);
-        work[j * 32 + lane] = r < 0 ? top : (r >= H ? bot : v);
-      }
-      tile = work;
-      __syncthreads();  // landing stage b is free again
-      if (tid == 0 && it + 2 < S) issue(s - 2, b);
-    }
-    const float *col = tile + (G + NOUT * warp) * LDW + lane;
-    float acc[NOUT];
-    fir_block(taps(b), K, [&](int t) { return col[t * LDW]; }, acc);
+  __shared__ FrameDev s_fr;
+  uint32_t ph0 = 0u, ph1 = 0u;  // phase to wait for, per barrier
+  int k = 0;
+  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
+    k = advance_frame(it, item, k);
+    stage_frame(&s_fr, fr, it, k);  // the previous item ended with __syncthreads
+    __syncthreads();
+    const FrameDev &F = s_fr;
+    const int local = item - __ldg(it.pre + k);
+    const int H = F.H, W = F.W;
+    const long prow = F.prow;
+    const int ntx = (W + TW - 1) / TW;
+    const int x0 = (local % ntx) * TW - 1;     // frame column of lane 0
+    const int off = ((x0 % XA) + XA) % XA;
+    const int xa = x0 - off;
+    const int r0 = (local / ntx) * (CROWS2 - 2) - 1;  // frame row of output row 0
+    const int x = x0 + lane, xv = min(max(x, 0), W - 1);
+    const bool xin = x >= 0 && x < W;
+    float *resp = F.resp;
+    float mxr[NOUT], mnr[NOUT];
 #pragma unroll
     for (int j = 0; j < NOUT; ++j) {
-      const int i = NOUT * warp + j, y = r0 + i;
-      if (!xin || y < 0 || y >= H) continue;
-      const float v = -acc[j];  // R_L = -sigma^2 (D20 + D02); planes carry sigma^2
-      // scales arrive in decreasing order: >= keeps the smallest scale of a tie
-      if (v >= mxr[j]) mxr[j] = v, amx[i * 32 + lane] = (unsigned char)s;
-      if (v <= mnr[j]) mnr[j] = v, amn[i * 32 + lane] = (unsigned char)s;
-      if (da.resp && i >= 1 && i <= CROWS2 - 2 && lane >= 1 && lane <= TW)
-        da.resp[s * plane + (long)y * W + x] = v;
+      const int p = (NOUT * warp + j) * 32 + lane;
+      mxr[j] = -CUDART_INF_F;
+      mnr[j] = CUDART_INF_F;
+      amx[p] = (unsigned char)S;
+      amn[p] = (unsigned char)S;
+    }
+    auto issue = [&](int s, int b) {  // thread 0 only
+      const int G = coef[s].K + TB;
+      const int nb = (CROWS2 + 2 * G + BOXH - 1) / BOXH;
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&mbar[b], (uint32_t)(nb * BOXH * BW * sizeof(T)));
+      const int y0 = (int)(prow + (long)s * H + r0 - G);
+      for (int i = 0; i < nb; ++i)
+        if (!tma_load_2d(land(b) + i * BOXH * BW, &map, xa, y0 + i * BOXH, &mbar[b], (int)sizeof(T)))
+          atomicExch(&da.status->error, 2);
+    };
+    // scales from the longest filter down (the order of the caller's scales is
+    // kept for ties: the first scale attaining an extreme is the one reported)
+    if (tid == 0) {
+      issue(S - 1, 0);
+      if (!F32 && S > 1) issue(S - 2, 1);
+    }
+    const long plane = (long)H * W;
+    for (int is = 0; is < S; ++is) {
+      const int s = S - 1 - is;
+      const int b = is & 1;
+      if (F32 && tid == 0 && is + 1 < S) issue(s - 1, b ^ 1);
+      const Coef &c = coef[s];
+      const int K = c.K, G = K + TB, nin = CROWS2 + 2 * G;
+      stage_taps(taps(b), c, K, tid, CNT2);
+      const bool ok = mbar_wait_bounded(&mbar[b], b ? ph1 : ph0, WAIT_LIMIT);
+      if (b) ph1 ^= 1u;
+      else ph0 ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        // a load never completed: report, let the other stage's load finish, stop
+        if (tid == 0) {
+          atomicExch(&da.status->error, 1);
+          if (is + 1 < S) mbar_wait_bounded(&mbar[b ^ 1], b ? ph0 : ph1, WAIT_LIMIT);
+        }
+        __syncthreads();
+        return;
+      }
+      const bool outside = r0 - G < 0 || r0 + CROWS2 + G > H;
+      float top = 0.f, bot = 0.f;
+      if (outside) {
+        const float *ed = edge + F.eoff + (long)s * 2 * PWb + xv;
+        top = ed[0];
+        bot = ed[PWb];
+      }
+      const float *tile;
+      if constexpr (F32) {
+        float *stg = land(b);
+        if (outside) {  // rows outside the frame: held values
+          for (int j = warp; j < nin; j += CNT2 / 32) {
+            const int r = r0 - G + j;
+            if (r < 0) stg[j * BOXW + off + lane] = top;
+            else if (r >= H) stg[j * BOXW + off + lane] = bot;
+          }
+        }
+        tile = stg + off;
+        __syncthreads();
+      } else {
+        const T *src = land(b) + off + lane;
+        for (int j = warp; j < nin; j += CNT2 / 32) {
+          const int r = r0 - G + j;
+          const float v = Store<ST>::ld(src[j * BW]);
+          work[j * 32 + lane] = r < 0 ? top : (r >= H ? bot : v);
+        }
+        tile = work;
+        __syncthreads();  // landing stage b is free again
+        if (tid == 0 && is + 2 < S) issue(s - 2, b);
+      }
+      const float *col = tile + (G + NOUT * warp) * LDW + lane;
+      float acc[NOUT];
+      fir_block(taps(b), K, [&](int t) { return col[t * LDW]; }, acc);
+#pragma unroll
+      for (int j = 0; j < NOUT; ++j) {
+        const int i = NOUT * warp + j, y = r0 + i;
+        if (!xin || y < 0 || y >= H) continue;
+        const float v = -acc[j];  // R_L = -sigma^2 (D20 + D02); planes carry sigma^2
+        // scales arrive in decreasing order: >= keeps the smallest scale of a tie
+        if (v >= mxr[j]) mxr[j] = v, amx[i * 32 + lane] = (unsigned char)s;
+        if (v <= mnr[j]) mnr[j] = v, amn[i * 32 + lane] = (unsigned char)s;
+        if (resp && i >= 1 && i <= CROWS2 - 2 && lane >= 1 && lane <= TW) resp[s * plane + (long)y * W + x] = v;
+      }
+      fence_proxy_async();  // held rows written into a stage before its next async copy
+      __syncthreads();
+    }
+    // the stages are free now: the extremes go to shared memory for the 3 x 3 test
+    float *mx = sm, *mn = sm + CROWS2 * 32;
+#pragma unroll
+    for (int j = 0; j < NOUT; ++j) {
+      const int p = (NOUT * warp + j) * 32 + lane;
+      mx[p] = mxr[j];
+      mn[p] = mnr[j];
     }
     __syncthreads();
+    DetectArgs a = da;
+    a.S = S;
+    a.NR = CROWS2;
+    a.x0 = x0;
+    a.r0 = r0;
+    a.H = H;
+    a.W = W;
+    a.frame = F.index;
+    a.resp = resp;
+    spatial_detect(mx, mn, amx, amn, a);
+    fence_proxy_async();  // extremes written over the stages before the next item's copies
+    __syncthreads();
   }
-  // the stages are free now: the extremes go to shared memory for the 3 x 3 test
-  float *mx = sm, *mn = sm + CROWS2 * 32;
-#pragma unroll
-  for (int j = 0; j < NOUT; ++j) {
-    const int p = (NOUT * warp + j) * 32 + lane;
-    mx[p] = mxr[j];
-    mn[p] = mnr[j];
-  }
-  __syncthreads();
-  DetectArgs a = da;
-  a.S = S;
-  a.NR = CROWS2;
-  a.x0 = x0;
-  a.r0 = r0;
-  spatial_detect(mx, mn, amx, amn, a);
 }
 
 template <int ST>
-int launch_colfir_tma(const FrameGeom &g, const BankArgs &a, const DetectArgs &da, int G, int KP,
+int launch_colfir_tma(const Plan &p, const Launch &l, const BankArgs &a, const DetectArgs &da, int G, int KP,
                       cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
@@ -411,24 +498,24 @@ int launch_colfir_tma(const FrameGeom &g, const BankArgs &a, const DetectArgs &d
     attr = true;
   }
   CUtensorMap map;
-  if (encode_plane_map(&map, a.P, ST, g.PW, g.H, a.S, ST == ST_F32 ? BOXW : BOXW16, BOXH)) return -1;
+  if (encode_plane_map(&map, a.P, ST, p.PWb, p.prows, ST == ST_F32 ? BOXW : BOXW16, BOXH)) return -1;
   const int stage_rows = (CROWS2 + 2 * G + BOXH - 1) / BOXH * BOXH;  // whole boxes
   const int taps_len = (KP + 1 + 3) / 4 * 4;
   const int SF = colfir_stage_floats<ST>(stage_rows);
   // stages (>= 2 x 128 x 32 floats for the final extremes) + taps + first-scale bytes
   const size_t tsm = ((size_t)SF + 2 * taps_len) * sizeof(float) + (size_t)CROWS2 * 32 * 2 + TMA_SMEM_ALIGN;
   if (tsm > 220 * 1024 || SF < 2 * CROWS2 * 32) return -1;
-  dim3 gt((g.W + TW - 1) / TW, (g.H + CROWS2 - 3) / (CROWS2 - 2));
+  const int nb = persistent_blocks((const void *)k_colfir_tma<ST>, CNT2, tsm, l.it.total, p.mult[PASS_DET]);
   a.prof->begin("fir_coldet", st);
-  k_colfir_tma<ST><<<gt, CNT2, tsm, st>>>(map, a.edge, g.PW, g.H, g.W, a.coef, a.S, stage_rows, taps_len, da);
+  k_colfir_tma<ST><<<nb, CNT2, tsm, st>>>(map, p.fr, l.it, a.edge, p.PWb, a.coef, a.S, stage_rows, taps_len, da);
   a.prof->end(st);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace
 
-// 3-D tensor map over the S one-sided planes (x, y, scale), box boxw x boxh x 1
-int encode_plane_map(CUtensorMap *m, void *P, int storage, long PW, int H, int S, int boxw, int boxh) {
+// 2-D tensor map over the plane row space (x, plane row), box boxw x boxh
+int encode_plane_map(CUtensorMap *m, void *P, int storage, long PWb, long prows, int boxw, int boxh) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -438,25 +525,74 @@ int encode_plane_map(CUtensorMap *m, void *P, int storage, long PW, int H, int S
       return -1;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t dims[3] = {(cuuint64_t)PW, (cuuint64_t)H, (cuuint64_t)S};
   const cuuint64_t eb = (cuuint64_t)store_bytes(storage);
-  const cuuint64_t strides[2] = {(cuuint64_t)PW * eb, (cuuint64_t)H * PW * eb};
-  const cuuint32_t box[3] = {(cuuint32_t)boxw, (cuuint32_t)boxh, 1};
-  const cuuint32_t es[3] = {1, 1, 1};
+  const cuuint64_t dims[2] = {(cuuint64_t)PWb, (cuuint64_t)prows};
+  const cuuint64_t strides[1] = {(cuuint64_t)PWb * eb};
+  const cuuint32_t box[2] = {(cuuint32_t)boxw, (cuuint32_t)boxh};
+  const cuuint32_t es[2] = {1, 1};
   const CUtensorMapDataType ty = storage == ST_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                  : storage == ST_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  const CUresult r = encode(m, ty, 3, P, dims, strides, box, es,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUresult r = encode(m, ty, 2, P, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -1;
 }
 
-int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
+int persistent_blocks(const void *kernel, int threads, size_t smem, int items, int mult) {
+  if (mult <= 0) return std::max(1, items);
+  constexpr int kMaxDev = 64;
+  static int nsm[kMaxDev];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kMaxDev) dev = 0;
+  if (!nsm[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    nsm[dev] = n > 0 ? n : 1;
+  }
+  // resident blocks per SM, cached per (device, kernel, block size, shared memory)
+  struct Key {
+    int dev;
+    const void *kernel;
+    int threads;
+    size_t smem;
+    bool operator<(const Key &o) const {
+      return std::tie(dev, kernel, threads, smem) < std::tie(o.dev, o.kernel, o.threads, o.smem);
+    }
+  };
+  static std::map<Key, int> cache;
+  static std::mutex mu;
+  int occ = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    const Key key{dev, kernel, threads, smem};
+    auto f = cache.find(key);
+    if (f != cache.end()) {
+      occ = f->second;
+    } else {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1)
+        occ = 1;
+      cache[key] = occ;
+    }
+  }
+  const long cap = (long)nsm[dev] * occ * mult;
+  return (int)std::max(1L, std::min((long)items, cap));
+}
+
+int fir_items(int pass, int H, int W, int S, int neigh) {
+  const int ntx = (W + TW - 1) / TW;
+  switch (pass) {
+    case PASS_ROW: return ((W + RSEG - 1) / RSEG) * (H + 2);
+    case PASS_DET: return neigh == 0 ? ntx * ((H + CROWS2 - 3) / (CROWS2 - 2)) : ntx * ((H + CROWS - 3) / (CROWS - 2));
+    default: return 0;
+  }
+}
+
+int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_rowfir<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_rowfir<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_rowfir, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_colfir, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr = true;
   }
@@ -465,43 +601,48 @@ int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
   const int KP = ((kmax + TB - 1) / TB) * TB;
   const int RG = row_halo(kmax);
   const size_t rsm = (size_t)(pad20(RSEG + 2 * RG) + 4 + KP + 1) * sizeof(float);
-  dim3 gr((g.W + RSEG - 1) / RSEG, g.H);
-  a.prof->begin("fir_row", st);
-  k_rowfir<false><<<gr, RNT, rsm, st>>>(g.X, g.xpitch, g.dtype, g.vscale, g.H, g.W, a.coef, a.S, kmax, a.P,
-                                        a.storage, g.PW, a.edge, a.status);
-  a.prof->end(st);
-  dim3 ge((g.W + RSEG - 1) / RSEG, 2);
-  a.prof->begin("fir_row_edge", st);
-  k_rowfir<true><<<ge, RNT, rsm, st>>>(g.X, g.xpitch, g.dtype, g.vscale, g.H, g.W, a.coef, a.S, kmax, a.P,
-                                       a.storage, g.PW, a.edge, a.status);
-  a.prof->end(st);
   DetectArgs da;
-  da.H = g.H;
-  da.W = g.W;
   da.thr = a.threshold;
   da.neigh = a.neigh;
   da.dark = 1;
-  da.frame = g.frame;
   da.out = a.blobs;
   da.cap = a.cap;
   da.status = a.status;
-  da.resp = a.responses ? a.responses + g.resp_off : nullptr;
-  if (a.neigh == 0) {
-    switch (a.storage) {
-      case ST_F32: return launch_colfir_tma<ST_F32>(g, a, da, G, KP, st);
-      case ST_F16: return launch_colfir_tma<ST_F16>(g, a, da, G, KP, st);
-      case ST_BF16: return launch_colfir_tma<ST_BF16>(g, a, da, G, KP, st);
-      default: return -2;
-    }
-  }
-  // in + buf + detector scratch (2 float planes + 2 byte planes) + taps
+  da.resp = nullptr;
+  // in + buf + detector scratch (2 float planes + 2 byte planes) + taps (adjacent neighbourhood)
   const size_t csm = ((size_t)(CROWS + 2 * G) * 32 + (size_t)a.S * CROWS * 32 + (size_t)CROWS * 32 * 2 +
                       (size_t)CROWS * 32 * 2 / 4 + KP + 1) * sizeof(float);
-  if (csm > 220 * 1024) return -1;
-  dim3 gc((g.W + TW - 1) / TW, (g.H + CROWS - 3) / (CROWS - 2));
-  a.prof->begin("fir_coldet", st);
-  k_colfir<<<gc, CNT, csm, st>>>(a.P, a.storage, g.PW, g.H, g.W, a.edge, a.coef, a.S, kmax, da);
-  a.prof->end(st);
+  if (a.neigh != 0 && csm > 220 * 1024) return -1;
+  auto row = [&](const Launch &l) {
+    const int nb = persistent_blocks((const void *)k_rowfir, RNT, rsm, l.it.total, p.mult[PASS_ROW]);
+    a.prof->begin("fir_row", st);
+    k_rowfir<<<nb, RNT, rsm, st>>>(p.fr, l.it, a.coef, a.S, kmax, a.P, a.storage, p.PWb, a.edge, a.status);
+    a.prof->end(st);
+  };
+  auto det = [&](const Launch &l) -> int {
+    if (a.neigh == 0) {
+      switch (a.storage) {
+        case ST_F32: return launch_colfir_tma<ST_F32>(p, l, a, da, G, KP, st);
+        case ST_F16: return launch_colfir_tma<ST_F16>(p, l, a, da, G, KP, st);
+        case ST_BF16: return launch_colfir_tma<ST_BF16>(p, l, a, da, G, KP, st);
+        default: return -2;
+      }
+    }
+    const int nb = persistent_blocks((const void *)k_colfir, CNT, csm, l.it.total, p.mult[PASS_DET]);
+    a.prof->begin("fir_coldet", st);
+    k_colfir<<<nb, CNT, csm, st>>>(p.fr, l.it, a.P, a.storage, p.PWb, a.edge, a.coef, a.S, kmax, da);
+    a.prof->end(st);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  };
+  if (p.per_frame) {
+    for (int f = 0; f < p.nframes; ++f) {
+      row(p.pass[PASS_ROW][f]);
+      if (int rc = det(p.pass[PASS_DET][f])) return rc;
+    }
+  } else {
+    row(p.pass[PASS_ROW][0]);
+    if (int rc = det(p.pass[PASS_DET][0])) return rc;
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -14,15 +14,18 @@
 // first-order sections (Filter D) or complex one-pole modes (Filter E) whose
 // states keep unit-dc-gain accuracy; the three-term sum (eq A6) adds them.
 //
-// Passes per frame:
+// Passes (each persistent over the work items of the frames it covers, see
+// kf_batch.cuh):
 //   k_row      one CTA per row: chunk of CH pixels per thread, zero-state end
-//              states, Kogge-Stone scan of the carries across the CTA, then
-//              both directions with exact starting states; all scales.
-//   k_row<EDGE> the same on U alone for rows 0 and H-1 (column boundary).
+//              states, warp scan + fold of the carries across the CTA, then
+//              both directions with exact starting states; all scales.  The
+//              two extra items of a frame are its first and last rows on U
+//              alone (column boundary).
 //   k_colseg   zero-state end states of every LC-row column segment.
 //   k_colfold  carries: sequential fold of the segment states per column.
 //   k_coldet   LC+2 rows x 32 columns x all scales per CTA: both column
 //              directions from the carries, response, extremum detector.
+#include "kf_batch.cuh"
 #include "kf_common.cuh"
 #include "kf_detect.cuh"
 #include "kf_internal.h"
@@ -238,25 +241,44 @@ __host__ __device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
 // ---------------------------------------------------------------------------
 // row pass
 // ---------------------------------------------------------------------------
-template <class Rec, bool EDGE>
-__global__ void __launch_bounds__(256) k_row(const void *__restrict__ X, long xpitch, int dt, float vs, int H,
-                                             int W, const Coef *__restrict__ coef, int S, void *__restrict__ P,
-                                             int st, long PW, float *__restrict__ edge,
-                                             DevStatus *__restrict__ status) {
-  extern __shared__ float sm[];
+// One row of one frame: row yw, or (EDGE) the U-only first (yw = 0) or last
+// (yw = 1) row for the column boundary.  One body for both cases keeps the
+// kernel's code small.  All threads of the block; ends with __syncthreads.
+template <class Rec>
+__device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, const Coef *__restrict__ coef,
+                                         int S, void *__restrict__ P, int st, long PWb,
+                                         float *__restrict__ edge, bool &ovf, float *sm) {
   const int NT = blockDim.x, tid = threadIdx.x;
+  const int H = F.H, W = F.W;
   const int RP = pad32(NT * CH) + 1;
   float *s_m = sm, *s_0 = sm + RP, *s_p = sm + 2 * RP, *s_scan = sm + 3 * RP;
-  const int y = EDGE ? (blockIdx.x == 0 ? 0 : H - 1) : blockIdx.x;
-  with_input_type(X, dt, [&](auto Xt) {
+  const int y = EDGE ? (yw == 0 ? 0 : H - 1) : yw;
+  const float vs = F.vscale;
+  const long xpitch = F.xpitch;
+  with_input_type(F.X, F.dtype, [&](auto Xt) {
     const auto *rm = Xt + (long)max(y - 1, 0) * xpitch;
     const auto *r0 = Xt + (long)y * xpitch;
     const auto *rp = Xt + (long)min(y + 1, H - 1) * xpitch;
-    for (int e = tid; e < W; e += NT) {
-      const int a = pad32(e);
-      s_m[a] = vs * in_f32(__ldg(rm + e));
-      s_0[a] = vs * in_f32(__ldg(r0 + e));
-      s_p[a] = vs * in_f32(__ldg(rp + e));
+    // 8 elements (24 loads) per thread in flight before they are stored
+    for (int e0 = tid; e0 < W; e0 += 8 * NT) {
+      float a[8], b[8], c[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = min(e0 + u * NT, W - 1);
+        a[u] = in_f32(__ldg(rm + e));
+        b[u] = in_f32(__ldg(r0 + e));
+        c[u] = in_f32(__ldg(rp + e));
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * NT;
+        if (e < W) {
+          const int q = pad32(e);
+          s_m[q] = vs * a[u];
+          s_0[q] = vs * b[u];
+          s_p[q] = vs * c[u];
+        }
+      }
     }
   });
   __syncthreads();
@@ -280,7 +302,6 @@ __global__ void __launch_bounds__(256) k_row(const void *__restrict__ X, long xp
   const float in_lo = EDGE ? 0.f : v_lo, in_hi = EDGE ? 0.f : v_hi;
   __syncthreads();
   float *s_out = sm;
-  bool ovf = false;  // a value beyond the f16 range
   for (int s = 0; s < S; ++s) {
     const Coef &c = coef[s];
     typename Rec::View v;
@@ -317,9 +338,9 @@ __global__ void __launch_bounds__(256) k_row(const void *__restrict__ X, long xp
 #pragma unroll
     for (int i = 0; i < CH; ++i) s_out[pad32(x0 + i)] = s2 * yv[i];
     __syncthreads();
-    const long row = EDGE ? 0 : (long)s * H * PW + (long)y * PW;
+    const long row = (F.prow + (long)s * H + y) * PWb;
     if (EDGE) {
-      float *dst = edge + ((long)s * 2 + blockIdx.x) * PW;
+      float *dst = edge + F.eoff + ((long)s * 2 + yw) * PWb;
       for (int e = tid; e < W; e += NT) dst[e] = s_out[pad32(e)];
     } else if (st == ST_F32) {
       float *dst = static_cast<float *>(P) + row;
@@ -337,6 +358,29 @@ __global__ void __launch_bounds__(256) k_row(const void *__restrict__ X, long xp
     }
     __syncthreads();
   }
+}
+
+// Row pass: one block per row, persistent over the rows of the launch's
+// frames; items H and H + 1 of a frame are its two U-only edge rows.  All
+// frames of a launch share the block width (chunks of CH pixels per thread).
+template <class Rec>
+__global__ void __launch_bounds__(256) k_row(const FrameDev *__restrict__ fr, Items it,
+                                             const Coef *__restrict__ coef, int S, void *__restrict__ P,
+                                             int st, long PWb, float *__restrict__ edge,
+                                             DevStatus *__restrict__ status) {
+  extern __shared__ float sm[];
+  __shared__ FrameDev s_fr;
+  bool ovf = false;  // a value beyond the f16 range
+  int k = 0;
+  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
+    k = advance_frame(it, item, k);
+    stage_frame(&s_fr, fr, it, k);  // the previous item ended with __syncthreads
+    __syncthreads();
+    const FrameDev &F = s_fr;
+    const int local = item - __ldg(it.pre + k);
+    const bool e = local >= F.H;
+    row_body<Rec>(F, e, e ? local - F.H : local, coef, S, P, st, PWb, edge, ovf, sm);
+  }
   if (ovf) atomicExch(&status->range, 1);
 }
 
@@ -346,78 +390,122 @@ __global__ void __launch_bounds__(256) k_row(const void *__restrict__ X, long xp
 // input of the column recursion at row r (phantom rows use the held one-sided
 // rows of U at the frame's first/last row)
 template <int ST>
-__device__ __forceinline__ float col_in(const typename Store<ST>::T *Pc, long PW, int r, int H, float top,
+__device__ __forceinline__ float col_in(const typename Store<ST>::T *Pc, long PWb, int r, int H, float top,
                                         float bot) {
-  return r < 0 ? top : (r >= H ? bot : Store<ST>::ld(Pc[(long)r * PW]));
+  return r < 0 ? top : (r >= H ? bot : Store<ST>::ld(Pc[(long)r * PWb]));
 }
 
+// Zero-state end states of every LC-row column segment, both directions.
+// Item: (128-column block, segment, scale) of a frame.
 template <class Rec, int ST>
-__global__ void __launch_bounds__(128) k_colseg(const typename Store<ST>::T *__restrict__ P, long PW, int H,
-                                                int W, const float *__restrict__ edge,
-                                                const Coef *__restrict__ coef, float *__restrict__ E,
-                                                int nseg) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= W) return;
-  const int c = blockIdx.y, s = blockIdx.z;
-  typename Rec::View v;
-  v.load(coef[s]);
-  const typename Store<ST>::T *Pc = P + (long)s * H * PW + x;
-  const float top = edge[((long)s * 2 + 0) * PW + x], bot = edge[((long)s * 2 + 1) * PW + x];
-  Rec r;
-  r.zero();
-  // causal segment: rows [c LC - 1, (c+1) LC - 1)
-  const int rf = c * LC - 1;
+__global__ void __launch_bounds__(128) k_colseg(const FrameDev *__restrict__ fr, Items it,
+                                                const typename Store<ST>::T *__restrict__ P, long PWb,
+                                                const float *__restrict__ edge,
+                                                const Coef *__restrict__ coef, float *__restrict__ E) {
+  int k = 0;
+  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
+    k = advance_frame(it, item, k);
+    const FrameDev F = fr[__ldg(it.fl + k)];  // by value: fields stay in registers
+    const int local = item - __ldg(it.pre + k);
+    const int H = F.H, W = F.W, nseg = F.nseg;
+    const int nxb = (W + 127) / 128;
+    const int xb = local % nxb, rest = local / nxb;
+    const int c = rest % nseg, s = rest / nseg;
+    const int x = xb * 128 + threadIdx.x;
+    if (x >= W) continue;
+    typename Rec::View v;
+    v.load(coef[s]);
+    const typename Store<ST>::T *Pc = P + (F.prow + (long)s * H) * PWb + x;
+    const float *ed = edge + F.eoff + (long)s * 2 * PWb + x;
+    const float top = ed[0], bot = ed[PWb];
+    Rec r;
+    const long fs = (long)Rec::NF * PWb;
+    float *Ef = E + F.coff + (((long)s * nseg + c) * 2 + 0) * fs + x;
+    // causal segment: rows [c LC - 1, (c+1) LC - 1); anticausal: rows (c+1) LC
+    // down to c LC + 1.  Inside the frame the loads are unconditional and
+    // issued 8 at a time ahead of their recursion steps.
+    const int rf = c * LC - 1, rb = (c + 1) * LC;
+    if (rf >= 0 && rb < H) {
+      const typename Store<ST>::T *pf = Pc + (long)rf * PWb, *pb = Pc + (long)rb * PWb;
+      r.zero();
+      for (int i0 = 0; i0 < LC; i0 += 8) {
+        float in[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) in[u] = Store<ST>::ld(pf[(long)(i0 + u) * PWb]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) r.push(v, in[u]);
+      }
+      r.store(Ef, PWb);
+      r.zero();
+      for (int i0 = 0; i0 < LC; i0 += 8) {
+        float in[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) in[u] = Store<ST>::ld(pb[-(long)(i0 + u) * PWb]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) r.push(v, in[u]);
+      }
+      r.store(Ef + fs, PWb);
+    } else {
+      r.zero();
 #pragma unroll 8
-  for (int i = 0; i < LC; ++i) r.push(v, col_in<ST>(Pc, PW, rf + i, H, top, bot));
-  const long fs = (long)Rec::NF * PW;
-  float *Ef = E + (((long)s * nseg + c) * 2 + 0) * fs + x;
-  r.store(Ef, PW);
-  // anticausal segment: rows (c+1) LC down to c LC + 1
-  r.zero();
-  const int rb = (c + 1) * LC;
+      for (int i = 0; i < LC; ++i) r.push(v, col_in<ST>(Pc, PWb, rf + i, H, top, bot));
+      r.store(Ef, PWb);
+      r.zero();
 #pragma unroll 8
-  for (int i = 0; i < LC; ++i) r.push(v, col_in<ST>(Pc, PW, rb - i, H, top, bot));
-  r.store(Ef + fs, PW);
+      for (int i = 0; i < LC; ++i) r.push(v, col_in<ST>(Pc, PWb, rb - i, H, top, bot));
+      r.store(Ef + fs, PWb);
+    }
+  }
 }
 
 // Carries of the column segments, one thread per (column, scale, direction):
 // C_0 = steady state of the held row, C_{k+1} = Phi^LC C_k + e_k in the
 // direction's segment order; the segment states e_k are replaced by the C_k.
 // Segment states are read 8 at a time ahead of the sequential fold.
+// Item: (128-column block, scale, direction) of a frame.
 template <class Rec>
-__global__ void __launch_bounds__(128) k_colfold(int W, long PW, const float *__restrict__ edge,
-                                                 const Coef *__restrict__ coef, float *__restrict__ E,
-                                                 int nseg) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= W) return;
-  const int s = blockIdx.y, dir = blockIdx.z;  // 0: top-down, 1: bottom-up
-  const Coef &c = coef[s];
-  const long fs = (long)Rec::NF * PW;
-  float *base = E + ((long)s * nseg * 2 + dir) * fs + x;  // segment k at base + 2 k fs
-  Rec st;
-  st.hold(c, edge[((long)s * 2 + dir) * PW + x]);
-  constexpr int BATCH = 8;
-  for (int k0 = 0; k0 < nseg; k0 += BATCH) {
-    Rec e[BATCH];
+__global__ void __launch_bounds__(128) k_colfold(const FrameDev *__restrict__ fr, Items it, long PWb,
+                                                 const float *__restrict__ edge,
+                                                 const Coef *__restrict__ coef, float *__restrict__ E, int S) {
+  int k = 0;
+  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
+    k = advance_frame(it, item, k);
+    const FrameDev F = fr[__ldg(it.fl + k)];  // by value: fields stay in registers
+    const int local = item - __ldg(it.pre + k);
+    const int W = F.W, nseg = F.nseg;
+    const int nxb = (W + 127) / 128;
+    const int xb = local % nxb, rest = local / nxb;
+    const int s = rest % S, dir = rest / S;  // dir 0: top-down, 1: bottom-up
+    const int x = xb * 128 + threadIdx.x;
+    if (x >= W) continue;
+    const Coef &c = coef[s];
+    const long fs = (long)Rec::NF * PWb;
+    float *base = E + F.coff + ((long)s * nseg * 2 + dir) * fs + x;  // segment k at base + 2 k fs
+    Rec st;
+    st.hold(c, edge[F.eoff + ((long)s * 2 + dir) * PWb + x]);
+    constexpr int BATCH = 8;
+    for (int k0 = 0; k0 < nseg; k0 += BATCH) {
+      Rec e[BATCH];
 #pragma unroll
-    for (int u = 0; u < BATCH; ++u) {
-      const int k = k0 + u;
-      if (k < nseg) e[u].load(base + 2L * (dir ? nseg - 1 - k : k) * fs, PW);
-    }
+      for (int u = 0; u < BATCH; ++u) {
+        const int kk = k0 + u;
+        if (kk < nseg) e[u].load(base + 2L * (dir ? nseg - 1 - kk : kk) * fs, PWb);
+      }
 #pragma unroll
-    for (int u = 0; u < BATCH; ++u) {
-      const int k = k0 + u;
-      if (k >= nseg) break;
-      st.store(base + 2L * (dir ? nseg - 1 - k : k) * fs, PW);
-      Rec n = e[u];
-      n.combine_L(c, st);  // Phi^LC st + e
-      st = n;
+      for (int u = 0; u < BATCH; ++u) {
+        const int kk = k0 + u;
+        if (kk >= nseg) break;
+        st.store(base + 2L * (dir ? nseg - 1 - kk : kk) * fs, PWb);
+        Rec n = e[u];
+        n.combine_L(c, st);  // Phi^LC st + e
+        st = n;
+      }
     }
   }
 }
 
-// Column pass + detector.  One CTA per (32-column, LC+2-row) tile, one warp
-// per scale, one thread per (column, scale).  The tile of every scale's
+// Column pass + detector.  Item: a (32-column, LC+2-row) tile of a frame; one
+// warp per scale, one thread per (column, scale).  The tile of every scale's
 // one-sided plane arrives by TMA into shared memory; rows outside the frame
 // take the held values.  Both recursions run from shared memory, the causal
 // outputs stay in registers, and R overwrites the input in place for the
@@ -443,10 +531,11 @@ __host__ __device__ constexpr int coldet_region_floats() {
 }
 
 template <class Rec, int ST>
-__global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUtensorMap map, long PW, int H,
-                                                int W, const float *__restrict__ edge,
+__global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUtensorMap map,
+                                                const FrameDev *__restrict__ fr, Items it, long PWb,
+                                                const float *__restrict__ edge,
                                                 const Coef *__restrict__ coef, int S,
-                                                const float *__restrict__ E, int nseg, DetectArgs da) {
+                                                const float *__restrict__ E, DetectArgs da) {
   using T = typename Store<ST>::T;
   constexpr bool F32 = ST == ST_F32;
   constexpr int NR = LC + 2;
@@ -459,166 +548,219 @@ __global__ void __launch_bounds__(512, 1) k_coldet(const __grid_constant__ CUten
   static_assert(128 * 64 <= C16B + 80 * 56 && 128 * NR <= C16B + 80 * 64, "widening order");
   extern __shared__ __align__(128) float sm_raw[];
   __shared__ __align__(8) uint64_t mbar;
+  __shared__ FrameDev s_fr;
   float *buf = align_smem(sm_raw);  // [S][REG]
   float *red = buf + (long)S * REG;  // detector scratch
   const int tid = threadIdx.x, lane = tid & 31, s = tid >> 5;
-  const int c = blockIdx.y;
-  const int x0 = blockIdx.x * TW - 1;
   constexpr int XA = F32 ? 4 : 8;  // TMA x alignment in elements
-  const int off = ((x0 % XA) + XA) % XA;
-  const int xv = min(max(x0 + lane, 0), W - 1);
-  const int r0 = c * LC - 1;
+  constexpr int BW = F32 ? CLD : CBOX16;
   if (tid == 0) {
     mbar_init(&mbar, 1);
     fence_proxy_async();
   }
   __syncthreads();  // no thread polls the barrier before it is initialised
-  if (tid == 0) {
-    constexpr int BW = F32 ? CLD : CBOX16;
-    mbar_arrive_expect_tx(&mbar, (uint32_t)(S * NR * BW * sizeof(T)));
-    for (int t = 0; t < S; ++t) {
-      void *dst = F32 ? (void *)(buf + (long)t * REG) : (void *)((char *)(buf + (long)t * REG) + C16B);
-      if (!tma_load_3d(dst, &map, x0 - off, r0, t, &mbar, (int)sizeof(T))) atomicExch(&da.status->error, 2);
-    }
-  }
   const Coef &cf = coef[s];
   typename Rec::View v;
   v.load(cf);
-  const long fs = (long)Rec::NF * PW;
-  const float *Ef = E + (((long)s * nseg + c) * 2) * fs + xv;
-  Rec r;
-  r.load(Ef, PW);
-  const bool ok = mbar_wait_bounded(&mbar, 0, CWAIT_LIMIT);
-  if (__syncthreads_or(!ok)) {
-    if (tid == 0) atomicExch(&da.status->error, 1);
-    return;
-  }
-  float *b = buf + (long)s * REG + (F32 ? off : 0) + lane;
-  const bool outside = r0 < 0 || r0 + NR > H;
-  float top = 0.f, bot = 0.f;
-  if (outside) top = edge[((long)s * 2 + 0) * PW + xv], bot = edge[((long)s * 2 + 1) * PW + xv];
-  // causal pass; rows outside the frame take the held one-sided rows of U
-  // (written back for the anticausal pass), 16-bit input is widened in place
-  const T *b16 = reinterpret_cast<const T *>(reinterpret_cast<const char *>(buf + (long)s * REG) + C16B) + off +
-                 lane;
-  float yp[NR];
+  const long fs = (long)Rec::NF * PWb;
+  uint32_t phase = 0;
+  int k = 0;
+  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
+    k = advance_frame(it, item, k);
+    stage_frame(&s_fr, fr, it, k);  // the previous item ended with __syncthreads
+    __syncthreads();
+    const FrameDev &F = s_fr;
+    const int local = item - __ldg(it.pre + k);
+    const int H = F.H, W = F.W, nseg = F.nseg;
+    const int ntx = (W + TW - 1) / TW;
+    const int c = local / ntx;
+    const int x0 = (local % ntx) * TW - 1;
+    const int off = ((x0 % XA) + XA) % XA;
+    const int xv = min(max(x0 + lane, 0), W - 1);
+    const int r0 = c * LC - 1;
+    const long prow = F.prow;
+    if (tid == 0) {
+      fence_proxy_async();  // earlier generic accesses of the buffer before the async writes
+      mbar_arrive_expect_tx(&mbar, (uint32_t)(S * NR * BW * sizeof(T)));
+      for (int t = 0; t < S; ++t) {
+        void *dst = F32 ? (void *)(buf + (long)t * REG) : (void *)((char *)(buf + (long)t * REG) + C16B);
+        if (!tma_load_2d(dst, &map, x0 - off, (int)(prow + (long)t * H + r0), &mbar, (int)sizeof(T)))
+          atomicExch(&da.status->error, 2);
+      }
+    }
+    const float *Ef = E + F.coff + (((long)s * nseg + c) * 2) * fs + xv;
+    Rec r;
+    r.load(Ef, PWb);
+    const bool ok = mbar_wait_bounded(&mbar, phase, CWAIT_LIMIT);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(&da.status->error, 1);
+      return;
+    }
+    float *b = buf + (long)s * REG + (F32 ? off : 0) + lane;
+    const bool outside = r0 < 0 || r0 + NR > H;
+    float top = 0.f, bot = 0.f;
+    if (outside) {
+      const float *ed = edge + F.eoff + (long)s * 2 * PWb + xv;
+      top = ed[0];
+      bot = ed[PWb];
+    }
+    // causal pass; rows outside the frame take the held one-sided rows of U
+    // (written back for the anticausal pass), 16-bit input is widened in place
+    const T *b16 = reinterpret_cast<const T *>(reinterpret_cast<const char *>(buf + (long)s * REG) + C16B) +
+                   off + lane;
+    float yp[NR];
 #pragma unroll
-  for (int i = 0; i < NR; ++i) {
-    const int y = r0 + i;
-    float in = F32 ? b[i * LD] : Store<ST>::ld(b16[i * CBOX16]);
-    if (outside) in = y < 0 ? top : (y >= H ? bot : in);
-    if (!F32 || outside) b[i * LD] = in;
-    yp[i] = r.out(v);
-    r.push(v, in);
-    if ((i & 7) == 7) __syncwarp();
-  }
-  __syncwarp();
-  r.load(Ef + fs, PW);
+    for (int i = 0; i < NR; ++i) {
+      const int y = r0 + i;
+      float in = F32 ? b[i * LD] : Store<ST>::ld(b16[i * CBOX16]);
+      if (outside) in = y < 0 ? top : (y >= H ? bot : in);
+      if (!F32 || outside) b[i * LD] = in;
+      yp[i] = r.out(v);
+      r.push(v, in);
+      if ((i & 7) == 7) __syncwarp();
+    }
+    __syncwarp();
+    r.load(Ef + fs, PWb);
 #pragma unroll
-  for (int i = NR - 1; i >= 0; --i) {
-    const float in = b[i * LD];
-    b[i * LD] = -(yp[i] + fmaf(v.b0, in, r.out(v)));  // R_L = -sigma^2 (D20 + D02); planes carry sigma^2
-    r.push(v, in);
+    for (int i = NR - 1; i >= 0; --i) {
+      const float in = b[i * LD];
+      b[i * LD] = -(yp[i] + fmaf(v.b0, in, r.out(v)));  // R_L = -sigma^2 (D20 + D02); planes carry sigma^2
+      r.push(v, in);
+    }
+    __syncthreads();
+    DetectArgs a = da;
+    a.S = S;
+    a.NR = NR;
+    a.x0 = x0;
+    a.r0 = r0;
+    a.H = H;
+    a.W = W;
+    a.frame = F.index;
+    a.resp = F.resp;
+    a.ld = LD;
+    a.coff = F32 ? off : 0;
+    a.srows = REG / LD;
+    detect_tile(buf, red, a);
+    fence_proxy_async();  // this thread's writes of the tile before the next item's async copies
+    __syncthreads();      // the tile is read before the next item's copies overwrite it
   }
-  __syncthreads();
-  DetectArgs a = da;
-  a.S = S;
-  a.NR = NR;
-  a.x0 = x0;
-  a.r0 = r0;
-  a.ld = LD;
-  a.coff = F32 ? off : 0;
-  a.srows = REG / LD;
-  detect_tile(buf, red, a);
 }
 
 template <class Rec, int ST>
-int run_iir_st(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
-  const int NT = ((g.W + CH - 1) / CH + 31) / 32 * 32;
-  if (NT > 1024) return -1;
-  const size_t row_smem = (size_t)(3 * (pad32(NT * CH) + 1) + 64 * Rec::NF) * sizeof(float);
+int run_iir_st(const Plan &p, const BankArgs &a, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_row<Rec, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_row<Rec, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_row<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_coldet<Rec, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr = true;
   }
-  if (row_smem > 200 * 1024) return -1;
-  a.prof->begin("iir_row", st);
-  k_row<Rec, false><<<g.H, NT, row_smem, st>>>(g.X, g.xpitch, g.dtype, g.vscale, g.H, g.W, a.coef, a.S, a.P,
-                                                a.storage, g.PW, a.edge, a.status);
-  a.prof->end(st);
-  a.prof->begin("iir_row_edge", st);
-  k_row<Rec, true><<<2, NT, row_smem, st>>>(g.X, g.xpitch, g.dtype, g.vscale, g.H, g.W, a.coef, a.S, a.P,
-                                            a.storage, g.PW, a.edge, a.status);
-  a.prof->end(st);
-  const int nseg = (g.H + LC - 1) / LC;
-  dim3 gs((g.W + 127) / 128, nseg, a.S);
-  a.prof->begin("iir_colseg", st);
-  k_colseg<Rec, ST><<<gs, 128, 0, st>>>(static_cast<const typename Store<ST>::T *>(a.P), g.PW, g.H, g.W, a.edge,
-                                        a.coef, a.carry, nseg);
-  a.prof->end(st);
-  dim3 gf((g.W + 127) / 128, a.S, 2);
-  a.prof->begin("iir_colfold", st);
-  k_colfold<Rec><<<gf, 128, 0, st>>>(g.W, g.PW, a.edge, a.coef, a.carry, nseg);
-  a.prof->end(st);
-  DetectArgs da;
-  da.H = g.H;
-  da.W = g.W;
-  da.thr = a.threshold;
-  da.neigh = a.neigh;
-  da.dark = 1;
-  da.frame = g.frame;
-  da.out = a.blobs;
-  da.cap = a.cap;
-  da.status = a.status;
-  da.resp = a.responses ? a.responses + g.resp_off : nullptr;
   constexpr int NR = LC + 2;
   const size_t det_smem = ((size_t)a.S * coldet_region_floats<ST>() + (size_t)NR * 32 * 2) * sizeof(float) +
                           (size_t)NR * 32 * 2 + TMA_SMEM_ALIGN;
   CUtensorMap map;
-  if (encode_plane_map(&map, a.P, ST, g.PW, g.H, a.S, ST == ST_F32 ? CLD : CBOX16, NR)) return -1;
-  dim3 gd((g.W + TW - 1) / TW, nseg);
-  a.prof->begin("iir_coldet", st);
-  k_coldet<Rec, ST><<<gd, 32 * a.S, det_smem, st>>>(map, g.PW, g.H, g.W, a.edge, a.coef, a.S, a.carry, nseg, da);
-  a.prof->end(st);
+  if (encode_plane_map(&map, a.P, ST, p.PWb, p.prows, ST == ST_F32 ? CLD : CBOX16, NR)) return -1;
+  DetectArgs da;
+  da.thr = a.threshold;
+  da.neigh = a.neigh;
+  da.dark = 1;
+  da.out = a.blobs;
+  da.cap = a.cap;
+  da.status = a.status;
+  da.resp = nullptr;
+  using TS = typename Store<ST>::T;
+  auto row = [&](const Launch &l) {
+    const size_t smem = (size_t)(3 * (pad32(l.nt * CH) + 1) + 64 * Rec::NF) * sizeof(float);
+    if (smem > 200 * 1024) return false;
+    const int nb = persistent_blocks((const void *)k_row<Rec>, l.nt, smem, l.it.total, p.mult[PASS_ROW]);
+    a.prof->begin("iir_row", st);
+    k_row<Rec><<<nb, l.nt, smem, st>>>(p.fr, l.it, a.coef, a.S, a.P, a.storage, p.PWb, a.edge, a.status);
+    a.prof->end(st);
+    return true;
+  };
+  auto seg = [&](const Launch &l) {
+    const int nb = persistent_blocks((const void *)k_colseg<Rec, ST>, 128, 0, l.it.total, p.mult[PASS_SEG]);
+    a.prof->begin("iir_colseg", st);
+    k_colseg<Rec, ST><<<nb, 128, 0, st>>>(p.fr, l.it, static_cast<const TS *>(a.P), p.PWb, a.edge, a.coef,
+                                          a.carry);
+    a.prof->end(st);
+  };
+  auto fold = [&](const Launch &l) {
+    const int nb = persistent_blocks((const void *)k_colfold<Rec>, 128, 0, l.it.total, p.mult[PASS_FOLD]);
+    a.prof->begin("iir_colfold", st);
+    k_colfold<Rec><<<nb, 128, 0, st>>>(p.fr, l.it, p.PWb, a.edge, a.coef, a.carry, a.S);
+    a.prof->end(st);
+  };
+  auto det = [&](const Launch &l) {
+    const int nb =
+        persistent_blocks((const void *)k_coldet<Rec, ST>, 32 * a.S, det_smem, l.it.total, p.mult[PASS_DET]);
+    a.prof->begin("iir_coldet", st);
+    k_coldet<Rec, ST><<<nb, 32 * a.S, det_smem, st>>>(map, p.fr, l.it, p.PWb, a.edge, a.coef, a.S, a.carry, da);
+    a.prof->end(st);
+  };
+  if (p.per_frame) {
+    for (int f = 0; f < p.nframes; ++f) {
+      if (!row(p.pass[PASS_ROW][f])) return -1;
+      seg(p.pass[PASS_SEG][f]);
+      fold(p.pass[PASS_FOLD][f]);
+      det(p.pass[PASS_DET][f]);
+    }
+  } else {
+    for (const Launch &l : p.pass[PASS_ROW])
+      if (!row(l)) return -1;
+    seg(p.pass[PASS_SEG][0]);
+    fold(p.pass[PASS_FOLD][0]);
+    det(p.pass[PASS_DET][0]);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <class Rec>
-int run_iir(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
+int run_iir(const Plan &p, const BankArgs &a, cudaStream_t st) {
   switch (a.storage) {
-    case ST_F32: return run_iir_st<Rec, ST_F32>(g, a, st);
-    case ST_F16: return run_iir_st<Rec, ST_F16>(g, a, st);
-    case ST_BF16: return run_iir_st<Rec, ST_BF16>(g, a, st);
+    case ST_F32: return run_iir_st<Rec, ST_F32>(p, a, st);
+    case ST_F16: return run_iir_st<Rec, ST_F16>(p, a, st);
+    case ST_BF16: return run_iir_st<Rec, ST_BF16>(p, a, st);
     default: return -2;
   }
 }
 
 }  // namespace
 
-size_t iir_carry_floats(int H, long PW, int S, int nf) {
-  const int nseg = (H + LC - 1) / LC;
-  return (size_t)S * nseg * 2 * nf * PW;
+int iir_segments(int H) { return (H + LC - 1) / LC; }
+
+int iir_row_threads(int W) {
+  const int nt = ((W + CH - 1) / CH + 31) / 32 * 32;
+  return nt <= 256 ? nt : 0;
 }
 
-int launch_iir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st) {
+int iir_items(int pass, int H, int W, int S) {
+  const int nxb = (W + 127) / 128, nseg = iir_segments(H);
+  switch (pass) {
+    case PASS_ROW: return H + 2;
+    case PASS_SEG: return nxb * nseg * S;
+    case PASS_FOLD: return nxb * S * 2;
+    case PASS_DET: return ((W + TW - 1) / TW) * nseg;
+    default: return 0;
+  }
+}
+
+int launch_iir(const Plan &p, const BankArgs &a, cudaStream_t st) {
   if (a.type == T_D) {
     switch (a.nstate) {
-      case 2: return run_iir<Chain<2>>(g, a, st);
-      case 3: return run_iir<Chain<3>>(g, a, st);
-      case 4: return run_iir<Chain<4>>(g, a, st);
-      case 5: return run_iir<Chain<5>>(g, a, st);
-      case 6: return run_iir<Chain<6>>(g, a, st);
+      case 2: return run_iir<Chain<2>>(p, a, st);
+      case 3: return run_iir<Chain<3>>(p, a, st);
+      case 4: return run_iir<Chain<4>>(p, a, st);
+      case 5: return run_iir<Chain<5>>(p, a, st);
+      case 6: return run_iir<Chain<6>>(p, a, st);
       default: return -2;
     }
   }
   if (a.type == T_E) {
     switch (a.nstate) {
-      case 1: return run_iir<Modes<1>>(g, a, st);
-      case 2: return run_iir<Modes<2>>(g, a, st);
-      case 3: return run_iir<Modes<3>>(g, a, st);
+      case 1: return run_iir<Modes<1>>(p, a, st);
+      case 2: return run_iir<Modes<2>>(p, a, st);
+      case 3: return run_iir<Modes<3>>(p, a, st);
       default: return -2;
     }
   }

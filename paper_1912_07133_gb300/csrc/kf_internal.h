@@ -4,6 +4,9 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <vector>
+
+#include "kf_batch.cuh"
 #include "kf_common.cuh"
 
 namespace kf {
@@ -13,18 +16,6 @@ namespace kf {
 // of the colored-SG design).
 int launch_design(int type, int order, const double *d_lambdas, int S, int fir_kmax, Coef *d_out,
                   double *d_work, int Nmax, cudaStream_t st);
-
-// Geometry of one frame in the bank.
-struct FrameGeom {
-  const void *X;    // input frame (IN_* element type)
-  int dtype;        // IN_F32 / IN_F16 / IN_BF16 / IN_U16
-  float vscale;     // input multiplier
-  long xpitch;      // elements between input rows
-  int H, W;
-  long PW;          // pitch of the intermediate planes (elements)
-  int frame;        // frame index (for blob records)
-  long resp_off;    // offset of this frame in the responses output
-};
 
 // Optional per-launch event recording (profiling) and launch counting.
 struct Prof {
@@ -49,26 +40,56 @@ struct BankArgs {
   int kmax;              // FIR: largest half-length over the scales
   float threshold;
   int neigh;
-  void *P;               // S planes of H x PW, element type `storage`
+  void *P;               // the plane row space: prows x PWb, element type `storage`
   int storage;           // ST_F32 / ST_F16 / ST_BF16
-  float *edge;           // S x 2 x PW: one-sided rows for the column boundary
-  float *carry;          // S x nseg x 2 x NF x PW (IIR column carries)
+  float *edge;           // per frame S x 2 x PWb: one-sided rows for the column boundary
+  float *carry;          // per frame S x nseg x 2 x NF x PWb (IIR column carries)
   Blob *blobs;
   long cap;
   DevStatus *status;
-  float *responses;      // optional
   Prof *prof;            // launch bookkeeping (never null)
 };
 
-int launch_iir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st);
-int launch_fir_frame(const FrameGeom &g, const BankArgs &a, cudaStream_t st);
+// Passes of the banks.  IIR: row (with the two edge rows per frame), column
+// segment states, carry fold, column pass + detector.  FIR: row, column +
+// detector.
+enum Pass { PASS_ROW = 0, PASS_SEG = 1, PASS_FOLD = 2, PASS_DET = 3, NPASS = 4 };
 
-// 3-D tensor map over S one-sided planes (x, y, scale) of pitch PW and
-// element type `storage`, box boxw x boxh x 1 (kf_fir.cu)
-int encode_plane_map(CUtensorMap *m, void *P, int storage, long PW, int H, int S, int boxw, int boxh);
+// one launch of a pass: its frames and items (device pointers into the call's
+// table) and, for the IIR row pass, the threads per block of its width class
+struct Launch {
+  Items it;
+  int nt = 0;
+};
 
-// workspace needs (bytes) of one frame
-size_t iir_carry_floats(int H, long PW, int S, int nf);
+struct Plan {
+  const FrameDev *fr = nullptr;  // device frame table
+  int nframes = 0;
+  long PWb = 0;                  // plane pitch (elements)
+  long prows = 0;                // rows of the plane row space
+  int maxW = 0, maxH = 0;
+  bool per_frame = false;        // launch every pass frame by frame
+  int mult[NPASS] = {0, 0, 0, 0}; // launch shape per pass (see persistent_blocks)
+  std::vector<Launch> pass[NPASS];
+};
+
+// work items of one frame in a pass (the kernels' decomposition)
+int iir_items(int pass, int H, int W, int S);
+int iir_row_threads(int W);    // threads per block of the IIR row pass (0: too wide)
+int fir_items(int pass, int H, int W, int S, int neigh);
+int iir_segments(int H);       // IIR column segments of a frame
+
+int launch_iir(const Plan &p, const BankArgs &a, cudaStream_t st);
+int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st);
+
+// 2-D tensor map over the plane row space (x, plane row), element type
+// `storage`, box boxw x boxh (kf_fir.cu)
+int encode_plane_map(CUtensorMap *m, void *P, int storage, long PWb, long prows, int boxw, int boxh);
+
+// blocks of a launch over `items` work items: mult = 0, one block per item;
+// mult = k >= 1, at most k x the blocks of this kernel and block shape that are
+// resident on the whole GPU at once (each block loops over items)
+int persistent_blocks(const void *kernel, int threads, size_t smem, int items, int mult);
 
 // candidate ordering (kf_sort.cu)
 size_t sort_workspace_bytes(long n);

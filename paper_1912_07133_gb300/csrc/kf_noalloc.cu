@@ -72,21 +72,29 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
     return nofail(KF_EINVAL, "frame data is not aligned to its element size");
   const int W = frame->width, H = frame->height, S = nscales;
   const long PW = ((long)W + 31) / 32 * 32;
-  // layout of the scratch: coefficients | scales | status | planes | edges | carries
+  // layout of the scratch: coefficients | scales | status | frame table | planes | edges | carries
   const int nstate_max = 6;  // chain length (repeated pole) or 2 x modes (Butterworth)
+  const int nseg = kf::iir_segments(H);
+  // frame table: one frame, each of the four passes one launch over it
+  struct Table {
+    kf::FrameDev fd;
+    int pool[4][3];  // per pass: frame list {0}, item prefix {0, items}
+  } tab;
   const size_t b_coef = align256(sizeof(kf::Coef) * KF_MAX_SCALES);
   const size_t b_lam = align256(sizeof(double) * KF_MAX_SCALES);
   const size_t b_stat = align256(sizeof(kf::DevStatus));
+  const size_t b_tab = align256(sizeof(Table));
   const size_t b_P = align256(sizeof(float) * (size_t)S * H * PW);
   const size_t b_edge = align256(sizeof(float) * (size_t)S * 2 * PW);
-  const size_t b_carry = align256(sizeof(float) * kf::iir_carry_floats(H, PW, S, nstate_max));
-  const size_t need = b_coef + b_lam + b_stat + b_P + b_edge + b_carry;
+  const size_t b_carry = align256(sizeof(float) * (size_t)S * nseg * 2 * nstate_max * PW);
+  const size_t need = b_coef + b_lam + b_stat + b_tab + b_P + b_edge + b_carry;
   if (need > kScratchBytes) {
     char m[200];
     std::snprintf(m, sizeof m, "%d scales of %dx%d need %zu bytes of scratch; the limit is %zu", S, W, H,
                   need, kScratchBytes);
     return nofail(KF_EINVAL, m);
   }
+  if (kf::iir_row_threads(W) == 0) return nofail(KF_EINVAL, "frame too wide for the row pass");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return nofail(KF_ENODEV, "no usable CUDA device");
@@ -101,9 +109,10 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
   auto *coef = reinterpret_cast<kf::Coef *>(base);
   auto *lam = reinterpret_cast<double *>(base + b_coef);
   auto *status = reinterpret_cast<kf::DevStatus *>(base + b_coef + b_lam);
-  auto *P = reinterpret_cast<float *>(base + b_coef + b_lam + b_stat);
-  auto *edge = reinterpret_cast<float *>(base + b_coef + b_lam + b_stat + b_P);
-  auto *carry = reinterpret_cast<float *>(base + b_coef + b_lam + b_stat + b_P + b_edge);
+  auto *d_tab = reinterpret_cast<Table *>(base + b_coef + b_lam + b_stat);
+  auto *P = reinterpret_cast<float *>(base + b_coef + b_lam + b_stat + b_tab);
+  auto *edge = reinterpret_cast<float *>(base + b_coef + b_lam + b_stat + b_tab + b_P);
+  auto *carry = reinterpret_cast<float *>(base + b_coef + b_lam + b_stat + b_tab + b_P + b_edge);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e;
   // FP64 designs into the scratch; the host checks them (stack copy, no allocation)
@@ -111,6 +120,28 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
     return nofail(KF_ECUDA, cudaGetErrorString(e));
   if (kf::launch_design(type, order, lam, S, 96, coef, nullptr, 1, st))
     return nofail(KF_ECUDA, "design kernel launch failed");
+  // the frame table (copied before the synchronisation below, so the stack
+  // copy may go away afterwards)
+  std::memset(&tab, 0, sizeof tab);
+  tab.fd.X = frame->data;
+  tab.fd.resp = responses;
+  tab.fd.xpitch = frame->pitch;
+  tab.fd.prow = 0;
+  tab.fd.eoff = 0;
+  tab.fd.coff = 0;
+  tab.fd.dtype = frame->dtype;
+  tab.fd.vscale = frame->value_scale == 0.0f ? 1.0f : frame->value_scale;
+  tab.fd.H = H;
+  tab.fd.W = W;
+  tab.fd.nseg = nseg;
+  tab.fd.index = 0;
+  for (int p = 0; p < 4; ++p) {
+    tab.pool[p][0] = 0;
+    tab.pool[p][1] = 0;
+    tab.pool[p][2] = kf::iir_items(p, H, W, S);
+  }
+  if ((e = cudaMemcpyAsync(d_tab, &tab, sizeof tab, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return nofail(KF_ECUDA, cudaGetErrorString(e));
   struct Check {
     int status, K;
     double dc;
@@ -149,19 +180,23 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
   a.blobs = nullptr;
   a.cap = 0;
   a.status = status;
-  a.responses = responses;
   a.prof = &prof;
-  kf::FrameGeom g;
-  g.X = frame->data;
-  g.dtype = frame->dtype;
-  g.vscale = frame->value_scale == 0.0f ? 1.0f : frame->value_scale;
-  g.xpitch = frame->pitch;
-  g.H = H;
-  g.W = W;
-  g.PW = PW;
-  g.frame = 0;
-  g.resp_off = 0;
-  const int rc = kf::launch_iir_frame(g, a, st);
+  kf::Plan plan;
+  plan.fr = &d_tab->fd;
+  plan.nframes = 1;
+  plan.PWb = PW;
+  plan.prows = (long)S * H;
+  plan.per_frame = false;
+  for (int p = 0; p < 4; ++p) {
+    kf::Launch l;
+    l.it.fl = &d_tab->pool[p][0];
+    l.it.pre = &d_tab->pool[p][1];
+    l.it.n = 1;
+    l.it.total = tab.pool[p][2];
+    l.nt = p == kf::PASS_ROW ? kf::iir_row_threads(W) : 0;
+    plan.pass[p].push_back(l);
+  }
+  const int rc = kf::launch_iir(plan, a, st);
   if (rc == -2) return nofail(KF_EINVAL, "no kernel instance for this order");
   if (rc) return nofail(KF_ECUDA, cudaGetErrorString(cudaGetLastError()));
   return KF_OK;

@@ -72,4 +72,16 @@ __device__ __forceinline__ bool tma_load_3d(void *dst, const CUtensorMap *map, i
   return true;
 }
 
+// 2-D tiled TMA load of one box at coordinates (x, y); the same rules.
+__device__ __forceinline__ bool tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
+                                            int elem_bytes = 4) {
+  if ((smem_u32(dst) & (TMA_SMEM_ALIGN - 1)) != 0 || ((x * elem_bytes) & 15) != 0) return false;
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+  return true;
+}
+
 }  // namespace kf

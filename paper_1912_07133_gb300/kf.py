@@ -41,12 +41,17 @@ KF_RESP_HESSIAN = 1
 KF_BOUNDARY_HOLD = 0
 KF_NEIGH_ALL_SCALES = 0
 KF_NEIGH_ADJACENT = 1
+KF_SCHED_BATCHED = 0
+KF_SCHED_PER_FRAME = 1
 KF_MAX_SCALES = 16
 KF_MAX_ORDER = 8
 KF_MAX_FIR_K = 160
 
 ENTRY_POINTS = ("kf_bank_opts_default", "kf_create", "kf_destroy", "kf_last_error", "kf_design",
-                "kf_filter_bank", "kf_detect_blobs", "kf_kernel_times", "kf_responses_noalloc")
+                "kf_filter_bank", "kf_detect_blobs", "kf_kernel_times", "kf_responses_noalloc",
+                "kf_set_launch_shape", "kf_autotune")
+KF_PASS_ROW, KF_PASS_SEG, KF_PASS_FOLD, KF_PASS_DET, KF_NPASS = 0, 1, 2, 3, 4
+GRID_CANDIDATES = (1, 2, 4, 0)
 KF_NOALLOC_SCRATCH_MB = 32
 
 
@@ -70,7 +75,8 @@ class kf_bank_opts(ctypes.Structure):
                 ("neighbourhood", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("threshold", ctypes.c_double), ("fir_kmax", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("responses", ctypes.c_void_p),
-                ("reserved", ctypes.c_int64 * 4)]
+                ("schedule", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 3)]
 
 
 class kf_blob(ctypes.Structure):
@@ -122,6 +128,11 @@ def load(path: str = LIB_PATH):
     L.kf_kernel_times.argtypes = [vp, ctypes.POINTER(kf_kernel_time), i32, ctypes.POINTER(i32)]
     L.kf_responses_noalloc.restype = i32
     L.kf_responses_noalloc.argtypes = [ctypes.POINTER(kf_frame), ctypes.POINTER(dbl), i32, i32, i32, vp, vp]
+    L.kf_set_launch_shape.restype = i32
+    L.kf_set_launch_shape.argtypes = [vp, i32, i32, i32]
+    L.kf_autotune.restype = i32
+    L.kf_autotune.argtypes = [vp, ctypes.POINTER(kf_frame), i32, ctypes.POINTER(dbl), i32, i32, i32,
+                              ctypes.POINTER(kf_bank_opts), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
     _lib = L
     return L
 
@@ -253,6 +264,29 @@ def kf_responses_noalloc(frame, scales, ftype: int, order: int, responses, strea
                                        ctypes.c_void_p(stream)))
 
 
+def kf_set_launch_shape(ctx: int, ftype: int, pass_: int, grid_mult: int) -> None:
+    """Launch shape of one pass (0: one block per work item; k: k x the
+    resident blocks of the GPU, looping over items)."""
+    _check(load().kf_set_launch_shape(ctx, ftype, pass_, grid_mult), ctx)
+
+
+def kf_autotune(ctx: int, frames, scales, ftype: int, order: int, opts: kf_bank_opts = None,
+                value_scales=None):
+    """Time every pass at each candidate launch shape on these frames and keep
+    the fastest per pass; returns (chosen shapes, {pass: [ms per candidate]})."""
+    vs = value_scales if value_scales is not None else [0.0] * len(frames)
+    descs = (kf_frame * len(frames))(*[_frame_desc(f, v) for f, v in zip(frames, vs)])
+    sc = (ctypes.c_double * len(scales))(*[float(s) for s in scales])
+    if opts is None:
+        opts = kf_bank_opts_default()
+    chosen = (ctypes.c_int32 * KF_NPASS)()
+    ms = (ctypes.c_float * (KF_NPASS * 4))()
+    _check(load().kf_autotune(ctx, descs, len(frames), sc, len(scales), ftype, order, ctypes.byref(opts),
+                              chosen, ms), ctx)
+    times = {p: list(ms[4 * p: 4 * p + 4]) for p in range(KF_NPASS) if chosen[p] >= 0}
+    return list(chosen), times
+
+
 class Bank:
     """Convenience wrapper: one context, repeated bank calls."""
 
@@ -261,13 +295,15 @@ class Bank:
 
     def run(self, frames, scales, ftype=KF_IIR_REPEATED_POLE, order=4, threshold=0.05,
             neighbourhood=KF_NEIGH_ALL_SCALES, responses=None, fir_kmax=96, profile=False,
-            storage=KF_DTYPE_F32, value_scales=None):
+            storage=KF_DTYPE_F32, value_scales=None, schedule=KF_SCHED_BATCHED, graph=False):
         o = kf_bank_opts_default()
         o.threshold = float(threshold)
         o.profile = 1 if profile else 0
         o.neighbourhood = neighbourhood
         o.fir_kmax = fir_kmax
         o.storage = storage
+        o.schedule = schedule
+        o.graph = 1 if graph else 0
         if responses is not None:
             import torch
 

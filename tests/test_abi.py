@@ -68,3 +68,28 @@ def test_no_device_is_a_loud_error(lib):
         pytest.skip("a GPU is present")
     with pytest.raises(kf.KfError):
         kf.kf_create(0)
+
+
+def test_field_offsets_match_the_c_compiler(tmp_path):
+    """Every field of the ctypes mirrors sits at the offset gcc gives it in
+    include/kf.h."""
+    import ctypes
+    from paper_1912_07133_gb300 import kf
+    structs = {"kf_frame": kf.kf_frame, "kf_bank_opts": kf.kf_bank_opts, "kf_blob": kf.kf_blob,
+               "kf_kernel_time": kf.kf_kernel_time, "kf_coeffs": kf.kf_coeffs}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kf.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)

@@ -1,0 +1,186 @@
+"""Batched persistent launches and graph replays.
+
+* A call of many frames of uneven sizes (and mixed element types) gives the
+  same responses, bit for bit, and the same ordered blob list whether every
+  pass runs once over all frames (batched, width classes for the IIR row
+  pass) or frame by frame; each frame matches the FP64 oracle at the FP32 bar.
+* Graph mode: the first call of a geometry runs eagerly, the second captures,
+  later calls replay with new frame data and response pointers; every call
+  equals an eager call on the same data.  A new geometry, or a workspace that
+  grows, is handled like a first call.
+"""
+import numpy as np
+import pytest
+
+from paper_1912_07133_gb300 import synthetic as SY
+from tests.parity import TOL, compare_blobs, oracle_bank, scale_errors, to_device
+
+pytestmark = pytest.mark.gpu
+
+D, E, C = 0, 1, 2
+SCALES = [2.0, 3.28, 5.38, 8.83]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def uneven_frames(seed=21):
+    """Frames of several widths (three IIR row-width classes) and heights, the
+    first few in other element types."""
+    rng = np.random.default_rng(seed)
+    sizes = [(97, 130), (64, 1100), (300, 33), (257, 640), (31, 2100), (190, 190), (5, 700)]
+    out = []
+    for i, (H, W) in enumerate(sizes):
+        img = SY.tiny_frame(int(rng.integers(1 << 30)), H, W, max(1, H * W // 4000))
+        out.append(img)
+    return out
+
+
+def run(frames, scales, ftype, order, **kw):
+    import torch
+
+    from paper_1912_07133_gb300 import kf
+    ts = [to_device(f) for f in frames]
+    n = sum(len(scales) * t.numel() for t in ts)
+    R = torch.full((n,), float("nan"), device="cuda", dtype=torch.float32)
+    bank = kf.Bank(0)
+    bank.run(ts, scales, ftype, order, threshold=0.02, responses=R, **kw)
+    b = bank.blobs()
+    bank.close()
+    return R.cpu().numpy(), b
+
+
+def split(R, frames, S):
+    out, off = [], 0
+    for f in frames:
+        k = S * f.size
+        out.append(R[off:off + k].reshape(S, *f.shape).astype(np.float64))
+        off += k
+    return out
+
+
+@pytest.mark.parametrize("ftype,order", [(D, 4), (E, 2), (C, 1)])
+def test_batched_and_per_frame_schedules_agree_bitwise(ftype, order):
+    from paper_1912_07133_gb300 import kf
+    frames = uneven_frames()
+    Rb, bb = run(frames, SCALES, ftype, order, schedule=kf.KF_SCHED_BATCHED)
+    Rp, bp = run(frames, SCALES, ftype, order, schedule=kf.KF_SCHED_PER_FRAME)
+    assert np.all(np.isfinite(Rb))
+    assert np.array_equal(Rb, Rp)
+    assert np.array_equal(bb, bp)
+    for i, (f, Rg) in enumerate(zip(frames, split(Rb, frames, len(SCALES)))):
+        Ro = oracle_bank(f, SCALES, ftype, order)
+        assert max(scale_errors(Rg, Ro)) <= TOL, i
+        compare_blobs(bb, Ro, 0.02, frame=i)
+
+
+def test_mixed_element_types_in_one_batch():
+    import torch
+    frames = uneven_frames(seed=22)[:4]
+    counts = SY.counts_frame(seed=23, H=120, W=170, nblobs=4)
+    f16 = frames[1].astype(np.float16)
+    bf16 = torch.from_numpy(frames[2]).to(torch.bfloat16)
+    batch = [frames[0], counts, f16, bf16]
+    vs = [1.0, 1.0 / 4095.0, 1.0, 1.0]
+    exact = [frames[0].astype(np.float64), counts.astype(np.float64) * np.float64(np.float32(vs[1])),
+             f16.astype(np.float64), bf16.to(torch.float64).numpy()]
+    R, b = run(batch, SCALES, D, 4, value_scales=vs)
+    for i, (x, Rg) in enumerate(zip(exact, split(R, exact, len(SCALES)))):
+        Ro = oracle_bank(x, SCALES, D, 4)
+        assert max(scale_errors(Rg, Ro)) <= TOL, i
+        compare_blobs(b, Ro, 0.02, frame=i)
+
+
+@pytest.mark.parametrize("ftype,order", [(D, 3), (C, 1)])
+def test_graph_replays_equal_eager_calls(ftype, order):
+    import torch
+
+    from paper_1912_07133_gb300 import kf
+    frames = uneven_frames(seed=24)[:5]
+    other = [SY.tiny_frame(100 + i, f.shape[0], f.shape[1], 3) for i, f in enumerate(frames)]
+    S = len(SCALES)
+    n = sum(S * f.size for f in frames)
+    bank = kf.Bank(0)
+    eager = {}
+    for name, fs in (("a", frames), ("b", other)):
+        R, b = run(fs, SCALES, ftype, order)
+        eager[name] = (R, b)
+    # the same geometry four times, alternating data and output buffers
+    outs = [torch.full((n,), float("nan"), device="cuda") for _ in range(2)]
+    dev = {name: [to_device(f) for f in fs] for name, fs in (("a", frames), ("b", other))}
+    for call, name in enumerate(["a", "b", "a", "b", "b"]):
+        R = outs[call % 2]
+        R.fill_(float("nan"))
+        bank.run(dev[name], SCALES, ftype, order, threshold=0.02, responses=R, graph=True)
+        b = bank.blobs()
+        assert np.array_equal(R.cpu().numpy(), eager[name][0]), (call, name)
+        assert np.array_equal(b, eager[name][1]), (call, name)
+    # a new geometry (one frame fewer) and back
+    R1 = torch.empty(n - S * frames[-1].size, device="cuda")
+    bank.run(dev["a"][:-1], SCALES, ftype, order, threshold=0.02, responses=R1, graph=True)
+    bank.blobs()
+    assert np.array_equal(R1.cpu().numpy(), eager["a"][0][: R1.numel()])
+    bank.run(dev["a"], SCALES, ftype, order, threshold=0.02, responses=outs[0], graph=True)
+    assert np.array_equal(bank.blobs(), eager["a"][1])
+    assert np.array_equal(outs[0].cpu().numpy(), eager["a"][0])
+    bank.close()
+
+
+def test_graph_mode_survives_workspace_growth():
+    import torch
+
+    from paper_1912_07133_gb300 import kf
+    small = [SY.tiny_frame(31, 64, 96, 2)]
+    big = [SY.tiny_frame(32, 400, 900, 20)]
+    bank = kf.Bank(0)
+    for frames in (small, small, small, big, big, big, small):
+        ts = [to_device(f) for f in frames]
+        R = torch.empty(len(SCALES) * frames[0].size, device="cuda")
+        bank.run(ts, SCALES, D, 4, threshold=0.02, responses=R, graph=True)
+        b = bank.blobs()
+        Re, be = run(frames, SCALES, D, 4)
+        assert np.array_equal(R.cpu().numpy(), Re)
+        assert np.array_equal(b, be)
+    bank.close()
+
+
+@pytest.mark.parametrize("ftype,order", [(D, 4), (E, 2), (C, 1)])
+def test_launch_shapes_do_not_change_results(ftype, order):
+    import torch
+
+    from paper_1912_07133_gb300 import kf
+    frames = uneven_frames(seed=25)[:4]
+    ts = [to_device(f) for f in frames]
+    n = sum(len(SCALES) * t.numel() for t in ts)
+    ref = None
+    bank = kf.Bank(0)
+    for mult in kf.GRID_CANDIDATES:
+        for p in range(kf.KF_NPASS):
+            kf.kf_set_launch_shape(bank.ctx, ftype, p, mult)
+        R = torch.full((n,), float("nan"), device="cuda")
+        bank.run(ts, SCALES, ftype, order, threshold=0.02, responses=R)
+        got = (R.cpu().numpy(), bank.blobs())
+        if ref is None:
+            ref = got
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), mult
+    with pytest.raises(kf.KfError):
+        kf.kf_set_launch_shape(bank.ctx, ftype, 7, 1)
+    bank.close()
+
+
+def test_autotune_picks_a_measured_shape_per_pass():
+    from paper_1912_07133_gb300 import kf
+    frames = uneven_frames(seed=26)
+    ts = [to_device(f) for f in frames]
+    bank = kf.Bank(0)
+    chosen, times = kf.kf_autotune(bank.ctx, ts, SCALES, D, 4)
+    assert set(times) == {0, 1, 2, 3}
+    for p, ms in times.items():
+        assert all(t > 0 for t in ms)
+        assert chosen[p] == kf.GRID_CANDIDATES[int(np.argmin(ms))]
+    chosen_c, times_c = kf.kf_autotune(bank.ctx, ts, SCALES, C, 1)
+    assert set(times_c) == {0, 3} and chosen_c[1] == -1 and chosen_c[2] == -1
+    bank.close()
