@@ -21,7 +21,7 @@ Metric: Mpixel-scales/s = banks x frames x pixels x scales / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload iir_fir|counts|batch] [--storage f32|f16|bf16]
-                  [--no-graph]
+                  [--no-graph] [--no-tune]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.  Under torchrun (N > 1) every rank runs an
@@ -226,6 +226,19 @@ def run_ours(args):
             kf.kf_design(ft, order, s)
     design_ms = (time.perf_counter() - t0) * 1e3
 
+    # launch shapes and segment lengths tuned once per bank on this workload
+    tuned = {}
+    if not args.no_tune:
+        for name, ft, order in BANKS:
+            o = kf.kf_bank_opts_default()
+            o.threshold = THRESHOLD
+            o.fir_kmax = wl["fir_kmax"]
+            o.storage = STORAGE[storage]
+            shapes, lc, _ = kf.kf_autotune(bank.ctx, Xs, SCALES, ft, order, o, vscales)
+            tuned[name] = {"grid_mult": {p: m for p, m in zip(("row", "seg", "fold", "det"), shapes) if m >= 0}}
+            if lc > 0:
+                tuned[name]["segment_rows"] = lc
+
     def run_bank(frames, ft, order, profile=False, schedule=kf.KF_SCHED_BATCHED, use_graph=graph):
         bank.run(frames, SCALES, ft, order, threshold=THRESHOLD, profile=profile, fir_kmax=wl["fir_kmax"],
                  storage=STORAGE[storage], value_scales=vscales, schedule=schedule, graph=use_graph)
@@ -370,6 +383,7 @@ def run_ours(args):
                    "storage": storage, "scales_px": [round(x, 3) for x in SCALES],
                    "banks": [b[0] for b in BANKS], "threshold": THRESHOLD, "fir_kmax": wl["fir_kmax"],
                    "launch": ("batched schedule, replayed from a CUDA graph" if graph else "batched schedule, eager"),
+                   "tuned": tuned or "library defaults (one block per work item, 64-row segments)",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}", "designs": "FP64 design kernel run once "
                    "per bank configuration, timed separately (design_ms)"},
@@ -468,6 +482,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="iir_fir")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default launch shapes)")
     ap.add_argument("--storage", choices=tuple(STORAGE), default=None,
                     help="element type of the one-sided planes (default: the workload's)")
     args = ap.parse_args()

@@ -250,12 +250,22 @@ int kf_kernel_times(kf_ctx *ctx, kf_kernel_time *out, int cap, int *n);
  * Results do not depend on the shape.  Errors: KF_EINVAL. */
 int kf_set_launch_shape(kf_ctx *ctx, int type, int pass, int grid_mult);
 
+/* Column segment length (scan block length of the column recursions) of a
+ * recursive bank on this context: 32 or 64 rows (default 64).  Shorter
+ * segments halve the column pass's shared-memory tile and registers (more
+ * resident blocks) at the cost of twice as many carries.  Results agree to
+ * FP32 rounding.  Errors: KF_EINVAL. */
+int kf_set_segment_length(kf_ctx *ctx, int type, int rows);
+
 /* Autotuner: run the bank on these frames (as kf_filter_bank would, opts as
- * there) once per candidate shape (grid_mult 1, 2, 4, 0), time every pass
- * with CUDA events on the context stream, and keep for each pass of `type`
- * the fastest shape on this context.  chosen (host, KF_NPASS entries, may be
- * NULL) receives the choices (passes the type lacks: -1); ms_out (host,
- * KF_NPASS x 4, may be NULL) the per-pass times of the candidates (ms).
+ * there) once per candidate shape (grid_mult 1, 2, 4, 0) and, for the
+ * recursive banks, per segment length (64, 32); time every pass with CUDA
+ * events on the context stream; keep for `type` the segment length with the
+ * smallest sum of per-pass best times and for each pass its fastest shape.
+ * chosen (host, KF_NPASS + 1 entries, may be NULL) receives the shapes
+ * (passes the type lacks: -1) and, last, the segment length (-1 for the FIR
+ * bank); ms_out (host, KF_NPASS x 4, may be NULL) the per-pass times of the
+ * shape candidates at the chosen segment length (ms).
  * Leaves the last candidate's result as the context's bank result.
  * Synchronises the context stream.  Errors: those of kf_filter_bank. */
 int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes,

@@ -84,6 +84,7 @@ struct kf_ctx {
   // of the persistent shapes for every pass on GB300 (4096^2 and uneven
   // batches); the persistent shapes remain candidates of the autotuner.
   int grid_mult[3][KF_NPASS] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+  int seg_len[3] = {64, 64, 64};  // recursive banks: column segment length (kf_set_segment_length)
 };
 
 namespace {
@@ -261,6 +262,7 @@ std::vector<long long> call_key(const kf_ctx *ctx, const kf_frame *frames, int n
   std::vector<long long> k = {type, order, kmax, S, o.storage, o.neighbourhood, o.schedule, nframes,
                               (long long)(intptr_t)ctx->cur};
   for (int p = 0; p < KF_NPASS; ++p) k.push_back(ctx->grid_mult[type][p]);
+  k.push_back(ctx->seg_len[type]);
   long long t;
   std::memcpy(&t, &o.threshold, sizeof t);
   k.push_back(t);
@@ -466,7 +468,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     d.vscale = fr.value_scale == 0.0f ? 1.0f : fr.value_scale;
     d.H = fr.height;
     d.W = fr.width;
-    d.nseg = iir ? kf::iir_segments(fr.height) : 0;
+    d.nseg = iir ? kf::iir_segments(fr.height, ctx->seg_len[type]) : 0;
     d.index = f;
     prows += (long)nscales * fr.height;
     roff += (long)nscales * fr.height * fr.width;
@@ -484,7 +486,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   std::vector<int> pool;
   std::vector<L> ls;
   auto items = [&](int pass, int f) {
-    return iir ? kf::iir_items(pass, fd[f].H, fd[f].W, nscales)
+    return iir ? kf::iir_items(pass, fd[f].H, fd[f].W, nscales, ctx->seg_len[type])
                : kf::fir_items(pass, fd[f].H, fd[f].W, nscales, opts.neighbourhood);
   };
   auto add = [&](int pass, const std::vector<int> &fl, int nt) {
@@ -546,6 +548,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   plan.prows = prows;
   plan.per_frame = opts.schedule == KF_SCHED_PER_FRAME;
   for (int p = 0; p < KF_NPASS; ++p) plan.mult[p] = ctx->grid_mult[type][p];
+  plan.lc = ctx->seg_len[type];
   const int *dpool = reinterpret_cast<const int *>(ctx->d_table + pool_off);
   for (const L &l : ls) {
     kf::Launch x;
@@ -664,6 +667,18 @@ int kf_set_launch_shape(kf_ctx *ctx, int type, int pass, int grid_mult) {
   return KF_OK;
 }
 
+int kf_set_segment_length(kf_ctx *ctx, int type, int rows) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_set_segment_length: ctx is NULL");
+  if (type != KF_IIR_REPEATED_POLE && type != KF_IIR_BUTTERWORTH)
+    return fail(ctx, KF_EINVAL, "segment length applies to the recursive banks only");
+  if (rows != 32 && rows != 64) return fail(ctx, KF_EINVAL, "segment length must be 32 or 64 rows");
+  if (ctx->seg_len[type] != rows) {
+    drop_graphs(ctx);
+    ctx->seg_len[type] = rows;
+  }
+  return KF_OK;
+}
+
 int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *scales, int nscales, int type,
                 int order, const kf_bank_opts *opts_in, int32_t *chosen, float *ms_out) {
   if (!ctx) return fail(nullptr, KF_EINVAL, "kf_autotune: ctx is NULL");
@@ -674,9 +689,6 @@ int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *
   o.profile = 1;
   o.graph = 0;
   constexpr int kCand[4] = {1, 2, 4, 0};
-  float ms[KF_NPASS][4];
-  for (auto &r : ms)
-    for (float &x : r) x = -1.f;
   const int saved[KF_NPASS] = {ctx->grid_mult[type][0], ctx->grid_mult[type][1], ctx->grid_mult[type][2],
                                ctx->grid_mult[type][3]};
   auto pass_of = [](const char *name) {
@@ -688,40 +700,66 @@ int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *
     return -1;
   };
   cudaError_t e;
-  for (int c = 0; c < 4; ++c) {
-    for (int p = 0; p < KF_NPASS; ++p) ctx->grid_mult[type][p] = kCand[c];
-    float acc[KF_NPASS] = {0, 0, 0, 0};
-    bool seen[KF_NPASS] = {false, false, false, false};
-    for (int rep = 0; rep < 3; ++rep) {  // one warm-up, two timed
-      int rc = kf_filter_bank(ctx, frames, nframes, scales, nscales, type, order, &o);
-      if (rc) {
-        for (int p = 0; p < KF_NPASS; ++p) ctx->grid_mult[type][p] = saved[p];
-        return rc;
+  const bool iir = type != KF_FIR_COLORED_SG;
+  const int saved_lc = ctx->seg_len[type];
+  // per candidate (segment length, shape): per-pass time
+  const int nlc = iir ? 2 : 1;
+  const int lcs[2] = {64, 32};
+  float t[2][4][KF_NPASS];
+  for (int l = 0; l < nlc; ++l) {
+    if (iir) ctx->seg_len[type] = lcs[l];
+    for (int c = 0; c < 4; ++c) {
+      for (int p = 0; p < KF_NPASS; ++p) ctx->grid_mult[type][p] = kCand[c];
+      float acc[KF_NPASS] = {0, 0, 0, 0};
+      bool seen[KF_NPASS] = {false, false, false, false};
+      for (int rep = 0; rep < 3; ++rep) {  // one warm-up, two timed
+        int rc = kf_filter_bank(ctx, frames, nframes, scales, nscales, type, order, &o);
+        if (rc) {
+          for (int p = 0; p < KF_NPASS; ++p) ctx->grid_mult[type][p] = saved[p];
+          ctx->seg_len[type] = saved_lc;
+          return rc;
+        }
+        if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+        if (rep == 0) continue;
+        const kf::Prof &pr = ctx->prof;
+        for (int i = 0; i < pr.n && i < pr.cap; ++i) {
+          const int p = pass_of(pr.names[i]);
+          if (p < 0) continue;
+          float dt = 0.f;
+          if ((e = cudaEventElapsedTime(&dt, pr.ev[2 * i], pr.ev[2 * i + 1])) != cudaSuccess)
+            return cuda_fail(ctx, e, "cudaEventElapsedTime");
+          acc[p] += dt;
+          seen[p] = true;
+        }
       }
-      if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "autotune");
-      if (rep == 0) continue;
-      const kf::Prof &pr = ctx->prof;
-      for (int i = 0; i < pr.n && i < pr.cap; ++i) {
-        const int p = pass_of(pr.names[i]);
-        if (p < 0) continue;
-        float t = 0.f;
-        if ((e = cudaEventElapsedTime(&t, pr.ev[2 * i], pr.ev[2 * i + 1])) != cudaSuccess)
-          return cuda_fail(ctx, e, "cudaEventElapsedTime");
-        acc[p] += t;
-        seen[p] = true;
-      }
+      for (int p = 0; p < KF_NPASS; ++p) t[l][c][p] = seen[p] ? acc[p] / 2.f : -1.f;
     }
-    for (int p = 0; p < KF_NPASS; ++p) ms[p][c] = seen[p] ? acc[p] / 2.f : -1.f;
   }
+  // per segment length: the best shape of every pass and their summed time;
+  // the segment length with the smaller sum wins (the row pass does not depend on it)
+  int best_l = 0;
+  float best_sum = -1.f;
+  int best_c[2][KF_NPASS];
+  for (int l = 0; l < nlc; ++l) {
+    float sum = 0.f;
+    for (int p = 0; p < KF_NPASS; ++p) {
+      int b = -1;
+      for (int c = 0; c < 4; ++c)
+        if (t[l][c][p] >= 0.f && (b < 0 || t[l][c][p] < t[l][b][p])) b = c;
+      best_c[l][p] = b;
+      if (b >= 0) sum += t[l][b][p];
+    }
+    if (best_sum < 0.f || sum < best_sum) best_sum = sum, best_l = l;
+  }
+  if (iir) ctx->seg_len[type] = lcs[best_l];
   for (int p = 0; p < KF_NPASS; ++p) {
-    int best = -1;
-    for (int c = 0; c < 4; ++c)
-      if (ms[p][c] >= 0.f && (best < 0 || ms[p][c] < ms[p][best])) best = c;
-    ctx->grid_mult[type][p] = best < 0 ? saved[p] : kCand[best];
-    if (chosen) chosen[p] = best < 0 ? -1 : kCand[best];
+    const int b = best_c[best_l][p];
+    ctx->grid_mult[type][p] = b < 0 ? saved[p] : kCand[b];
+    if (chosen) chosen[p] = b < 0 ? -1 : kCand[b];
     if (ms_out)
-      for (int c = 0; c < 4; ++c) ms_out[p * 4 + c] = ms[p][c];
+      for (int c = 0; c < 4; ++c) ms_out[p * 4 + c] = t[best_l][c][p];
   }
+  if (chosen) chosen[KF_NPASS] = iir ? lcs[best_l] : -1;
   drop_graphs(ctx);
   return KF_OK;
 }

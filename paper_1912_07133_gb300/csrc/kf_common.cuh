@@ -11,7 +11,6 @@ namespace kf {
 constexpr int MAXK = 8;          // largest recursive order / number of modes
 constexpr int MAXS = 16;         // scales per bank call
 constexpr int CH = 32;           // row-kernel pixels per thread (chunk)
-constexpr int LC = 64;           // column segment length (rows)
 constexpr int TW = 30;           // column-kernel tile interior width (32 with halo)
 constexpr int WARPM = 32;        // powers Phi^(CH m), m = 1..32, for the row scan
 constexpr int MAX_FIR_K = 160;   // largest colored-SG half-length
@@ -102,14 +101,12 @@ struct Coef {
   float p;
   float w[MAXK];
   float hold[MAXK];              // steady state per unit constant input: 1/q^j
-  float phiL[MAXK];              // first column of Phi^LC (Toeplitz)
   float phiM[WARPM][MAXK];       // first column of Phi^(CH m), m = 1..32
   // Filter E: complex (or real) one-pole modes t(n) = z t(n-1) + x(n);
   // one-sided output Re(sum_i g_i t_i(n-1)).
   float zr[MAXK], zi[MAXK];
   float gr[MAXK], gi[MAXK];
   float hr[MAXK], hi[MAXK];      // steady state per unit input: 1/(1-z)
-  float zLr[MAXK], zLi[MAXK];    // z^LC
   float zMr[WARPM][MAXK], zMi[WARPM][MAXK];  // z^(CH m), m = 1..32
   // Filter C taps h[0..K]
   float h[MAX_FIR_K + 1];

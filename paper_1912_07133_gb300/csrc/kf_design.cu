@@ -166,7 +166,6 @@ __device__ void design_D(Coef &c, int order, double lambda) {
     gplus += w[j] * pow(q, -(double)j);
   }
   for (int i = 0; i < K; ++i) {
-    c.phiL[i] = (float)binom_pow(LC, i, p);
     for (int m = 1; m <= WARPM; ++m) c.phiM[m - 1][i] = (float)binom_pow((long)CH * m, i, p);
   }
   c.p = pf;
@@ -265,9 +264,6 @@ __device__ void design_E(Coef &c, int order, double lambda) {
     cd hh = cdiv(cd{1.0, 0.0}, csub(cd{1.0, 0.0}, zm[i]));
     c.hr[i] = (float)hh.r;
     c.hi[i] = (float)hh.i;
-    cd zl = cpow(zm[i], LC);
-    c.zLr[i] = (float)zl.r;
-    c.zLi[i] = (float)zl.i;
     for (int m = 1; m <= WARPM; ++m) {
       cd zs = cpow(zm[i], (long)CH * m);
       c.zMr[m - 1][i] = (float)zs.r;

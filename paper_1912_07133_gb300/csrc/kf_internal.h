@@ -70,14 +70,15 @@ struct Plan {
   int maxW = 0, maxH = 0;
   bool per_frame = false;        // launch every pass frame by frame
   int mult[NPASS] = {0, 0, 0, 0}; // launch shape per pass (see persistent_blocks)
+  int lc = 64;                    // IIR column segment length (32 or 64 rows)
   std::vector<Launch> pass[NPASS];
 };
 
 // work items of one frame in a pass (the kernels' decomposition)
-int iir_items(int pass, int H, int W, int S);
+int iir_items(int pass, int H, int W, int S, int lc);
 int iir_row_threads(int W);    // threads per block of the IIR row pass (0: too wide)
 int fir_items(int pass, int H, int W, int S, int neigh);
-int iir_segments(int H);       // IIR column segments of a frame
+int iir_segments(int H, int lc);  // IIR column segments of a frame (segment length lc)
 
 int launch_iir(const Plan &p, const BankArgs &a, cudaStream_t st);
 int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st);

@@ -74,7 +74,7 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
   const long PW = ((long)W + 31) / 32 * 32;
   // layout of the scratch: coefficients | scales | status | frame table | planes | edges | carries
   const int nstate_max = 6;  // chain length (repeated pole) or 2 x modes (Butterworth)
-  const int nseg = kf::iir_segments(H);
+  const int nseg = kf::iir_segments(H, 64);
   // frame table: one frame, each of the four passes one launch over it
   struct Table {
     kf::FrameDev fd;
@@ -138,7 +138,7 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
   for (int p = 0; p < 4; ++p) {
     tab.pool[p][0] = 0;
     tab.pool[p][1] = 0;
-    tab.pool[p][2] = kf::iir_items(p, H, W, S);
+    tab.pool[p][2] = kf::iir_items(p, H, W, S, 64);
   }
   if ((e = cudaMemcpyAsync(d_tab, &tab, sizeof tab, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return nofail(KF_ECUDA, cudaGetErrorString(e));
@@ -187,6 +187,7 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
   plan.PWb = PW;
   plan.prows = (long)S * H;
   plan.per_frame = false;
+  plan.lc = 64;
   for (int p = 0; p < 4; ++p) {
     kf::Launch l;
     l.it.fl = &d_tab->pool[p][0];

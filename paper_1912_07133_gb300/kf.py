@@ -49,7 +49,7 @@ KF_MAX_FIR_K = 160
 
 ENTRY_POINTS = ("kf_bank_opts_default", "kf_create", "kf_destroy", "kf_last_error", "kf_design",
                 "kf_filter_bank", "kf_detect_blobs", "kf_kernel_times", "kf_responses_noalloc",
-                "kf_set_launch_shape", "kf_autotune")
+                "kf_set_launch_shape", "kf_set_segment_length", "kf_autotune")
 KF_PASS_ROW, KF_PASS_SEG, KF_PASS_FOLD, KF_PASS_DET, KF_NPASS = 0, 1, 2, 3, 4
 GRID_CANDIDATES = (1, 2, 4, 0)
 KF_NOALLOC_SCRATCH_MB = 32
@@ -130,6 +130,8 @@ def load(path: str = LIB_PATH):
     L.kf_responses_noalloc.argtypes = [ctypes.POINTER(kf_frame), ctypes.POINTER(dbl), i32, i32, i32, vp, vp]
     L.kf_set_launch_shape.restype = i32
     L.kf_set_launch_shape.argtypes = [vp, i32, i32, i32]
+    L.kf_set_segment_length.restype = i32
+    L.kf_set_segment_length.argtypes = [vp, i32, i32]
     L.kf_autotune.restype = i32
     L.kf_autotune.argtypes = [vp, ctypes.POINTER(kf_frame), i32, ctypes.POINTER(dbl), i32, i32, i32,
                               ctypes.POINTER(kf_bank_opts), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
@@ -270,21 +272,27 @@ def kf_set_launch_shape(ctx: int, ftype: int, pass_: int, grid_mult: int) -> Non
     _check(load().kf_set_launch_shape(ctx, ftype, pass_, grid_mult), ctx)
 
 
+def kf_set_segment_length(ctx: int, ftype: int, rows: int) -> None:
+    """Column segment length (32 or 64 rows) of a recursive bank."""
+    _check(load().kf_set_segment_length(ctx, ftype, rows), ctx)
+
+
 def kf_autotune(ctx: int, frames, scales, ftype: int, order: int, opts: kf_bank_opts = None,
                 value_scales=None):
-    """Time every pass at each candidate launch shape on these frames and keep
-    the fastest per pass; returns (chosen shapes, {pass: [ms per candidate]})."""
+    """Time every pass at each candidate launch shape (and, for the recursive
+    banks, segment length) on these frames and keep the fastest; returns
+    (chosen shapes per pass, segment length, {pass: [ms per shape candidate]})."""
     vs = value_scales if value_scales is not None else [0.0] * len(frames)
     descs = (kf_frame * len(frames))(*[_frame_desc(f, v) for f, v in zip(frames, vs)])
     sc = (ctypes.c_double * len(scales))(*[float(s) for s in scales])
     if opts is None:
         opts = kf_bank_opts_default()
-    chosen = (ctypes.c_int32 * KF_NPASS)()
+    chosen = (ctypes.c_int32 * (KF_NPASS + 1))()
     ms = (ctypes.c_float * (KF_NPASS * 4))()
     _check(load().kf_autotune(ctx, descs, len(frames), sc, len(scales), ftype, order, ctypes.byref(opts),
                               chosen, ms), ctx)
     times = {p: list(ms[4 * p: 4 * p + 4]) for p in range(KF_NPASS) if chosen[p] >= 0}
-    return list(chosen), times
+    return list(chosen[:KF_NPASS]), chosen[KF_NPASS], times
 
 
 class Bank:

@@ -176,11 +176,85 @@ def test_autotune_picks_a_measured_shape_per_pass():
     frames = uneven_frames(seed=26)
     ts = [to_device(f) for f in frames]
     bank = kf.Bank(0)
-    chosen, times = kf.kf_autotune(bank.ctx, ts, SCALES, D, 4)
-    assert set(times) == {0, 1, 2, 3}
+    chosen, lc, times = kf.kf_autotune(bank.ctx, ts, SCALES, D, 4)
+    assert set(times) == {0, 1, 2, 3} and lc in (32, 64)
     for p, ms in times.items():
         assert all(t > 0 for t in ms)
         assert chosen[p] == kf.GRID_CANDIDATES[int(np.argmin(ms))]
-    chosen_c, times_c = kf.kf_autotune(bank.ctx, ts, SCALES, C, 1)
-    assert set(times_c) == {0, 3} and chosen_c[1] == -1 and chosen_c[2] == -1
+    chosen_c, lc_c, times_c = kf.kf_autotune(bank.ctx, ts, SCALES, C, 1)
+    assert set(times_c) == {0, 3} and chosen_c[1] == -1 and chosen_c[2] == -1 and lc_c == -1
+    # the tuned context still computes the same responses
+    R, b = run(frames, SCALES, D, 4)
+    import torch
+    Rt = torch.full((R.size,), float("nan"), device="cuda")
+    bank.run(ts, SCALES, D, 4, threshold=0.02, responses=Rt)
+    assert np.allclose(Rt.cpu().numpy(), R, rtol=0, atol=TOL * np.nanmax(np.abs(R)))
     bank.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("ftype,order", [(D, 4), (E, 2), (E, 3)])
+def test_segment_length_32_meets_the_bar(ftype, order, storage):
+    """32-row column segments: the FP32 bar against the oracle (f32 planes);
+    with f16 planes the same responses as 64-row segments up to FP32 rounding
+    (the planes are identical, only the column carries are split differently)."""
+    import torch
+
+    from paper_1912_07133_gb300 import kf
+    frames = uneven_frames(seed=27)
+    ts = [to_device(f) for f in frames]
+    n = sum(len(SCALES) * t.numel() for t in ts)
+    out = {}
+    for lc in (64, 32):
+        bank = kf.Bank(0)
+        kf.kf_set_segment_length(bank.ctx, ftype, lc)
+        R = torch.full((n,), float("nan"), device="cuda")
+        bank.run(ts, SCALES, ftype, order, threshold=0.02, responses=R, storage=storage)
+        out[lc] = (R.cpu().numpy(), bank.blobs())
+        bank.close()
+    R32, b32 = out[32]
+    assert np.all(np.isfinite(R32))
+    for i, (f, Rg, Rr) in enumerate(zip(frames, split(R32, frames, len(SCALES)), split(out[64][0], frames, len(SCALES)))):
+        if storage == 0:
+            Ro = oracle_bank(f, SCALES, ftype, order)
+            assert max(scale_errors(Rg, Ro)) <= TOL, i
+            compare_blobs(b32, Ro, 0.02, frame=i)
+        else:
+            assert max(scale_errors(Rg, Rr)) <= TOL, i
+
+
+def test_segment_length_argument_is_checked():
+    from paper_1912_07133_gb300 import kf
+    bank = kf.Bank(0)
+    for args in [(D, 48), (C, 32), (7, 32)]:
+        with pytest.raises(kf.KfError):
+            kf.kf_set_segment_length(bank.ctx, *args)
+    bank.close()
+
+
+@pytest.mark.parametrize("lc", [32, 64])
+@pytest.mark.parametrize("ftype,order", [(D, 3), (E, 2)])
+def test_degenerate_shapes_in_one_batch(ftype, order, lc):
+    """Frames of 1 to 130 rows, 1 to 4099 columns, in one call: every frame
+    matches the oracle (segments shorter than a frame, frames shorter than a
+    segment, ragged tiles)."""
+    import torch
+
+    from paper_1912_07133_gb300 import kf
+    shapes = [(1, 1), (1, 37), (37, 1), (2, 3), (31, 33), (33, 65), (65, 130), (129, 31), (70, 4099)]
+    rng = np.random.default_rng(lc + ftype)
+    frames = [rng.uniform(0, 1, s).astype(np.float32) for s in shapes]
+    scales = [4.0, 7.0]
+    ts = [to_device(f) for f in frames]
+    R = torch.full((sum(len(scales) * f.size for f in frames),), float("nan"), device="cuda")
+    bank = kf.Bank(0)
+    kf.kf_set_segment_length(bank.ctx, ftype, lc)
+    bank.run(ts, scales, ftype, order, threshold=0.05, responses=R)
+    blobs = bank.blobs()
+    bank.close()
+    for i, (f, Rg) in enumerate(zip(frames, split(R.cpu().numpy(), frames, len(scales)))):
+        Ro = oracle_bank(f, scales, ftype, order)
+        for s in range(len(scales)):
+            assert np.abs(Rg[s] - Ro[s]).max() <= TOL * max(np.ptp(Ro[s]), 1e-3), (i, s)
+        if f.size > 1:
+            compare_blobs(blobs, Ro, 0.05, frame=i)
