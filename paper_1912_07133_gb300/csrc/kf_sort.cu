@@ -13,7 +13,7 @@ namespace kf {
 namespace {
 
 constexpr int SORT_NT = 256;               // threads per block
-constexpr int SORT_ITEMS = 8;              // items per thread
+constexpr int SORT_ITEMS = 4;              // items per thread (1024-item tiles: enough blocks for 152 SMs)
 constexpr int TILE = SORT_NT * SORT_ITEMS; // items per block
 constexpr int NWARP = SORT_NT / 32;
 constexpr int ITEMS_PER_WARP = TILE / NWARP;
@@ -52,18 +52,36 @@ __global__ void __launch_bounds__(SORT_NT) k_hist(const unsigned long long *__re
   hist[(long)tid * gridDim.x + blockIdx.x] = h[tid];
 }
 
-// exclusive scan of m entries, one block of 1024 threads: rounds of 1024
-// consecutive (coalesced) entries, warp-shuffle scans, a carried prefix
-__global__ void __launch_bounds__(1024) k_scan(unsigned *__restrict__ a, long m) {
+// Exclusive scan of m entries, one block of 1024 threads, in chunks of
+// SCAN_CHUNK entries: a coalesced load into shared memory (padded by one word
+// per 32 so that a thread's 32 consecutive entries sit in 32 banks), a serial
+// scan of each thread's 32 entries, a block scan of the thread totals with a
+// carried prefix, a coalesced write back.
+constexpr int SCAN_NT = 1024;
+constexpr int SCAN_CHUNK = 32 * SCAN_NT;
+constexpr size_t SCAN_SMEM = (size_t)(SCAN_CHUNK + SCAN_CHUNK / 32) * sizeof(unsigned);
+
+__device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }
+
+__global__ void __launch_bounds__(SCAN_NT) k_scan(unsigned *__restrict__ a, long m) {
+  extern __shared__ unsigned sa[];
   __shared__ unsigned wsum[32];
   __shared__ unsigned carry;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (tid == 0) carry = 0;
-  __syncthreads();
-  for (long r = 0; r < m; r += 1024) {
-    const long i = r + tid;
-    const unsigned v = i < m ? a[i] : 0u;
-    unsigned x = v;  // inclusive warp scan
+  for (long r = 0; r < m; r += SCAN_CHUNK) {
+    const int n = (int)min((long)SCAN_CHUNK, m - r);
+    for (int i = tid; i < SCAN_CHUNK; i += SCAN_NT) sa[scan_pad(i)] = i < n ? a[r + i] : 0u;
+    __syncthreads();
+    unsigned tot = 0;  // this thread's 32 entries, scanned in place
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {
+      const int q = scan_pad(32 * tid + j);
+      const unsigned v = sa[q];
+      sa[q] = tot;
+      tot += v;
+    }
+    unsigned x = tot;  // inclusive scan of the thread totals
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
@@ -81,9 +99,11 @@ __global__ void __launch_bounds__(1024) k_scan(unsigned *__restrict__ a, long m)
       wsum[lane] = t;  // inclusive over warps
     }
     __syncthreads();
-    const unsigned before = carry + (w > 0 ? wsum[w - 1] : 0u) + x - v;
-    if (i < m) a[i] = before;
+    const unsigned before = carry + (w > 0 ? wsum[w - 1] : 0u) + x - tot;
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) sa[scan_pad(32 * tid + j)] += before;
     __syncthreads();
+    for (int i = tid; i < n; i += SCAN_NT) a[r + i] = sa[scan_pad(i)];
     if (tid == 0) carry += wsum[31];
     __syncthreads();
   }
@@ -166,6 +186,11 @@ int launch_sort(const Blob *blobs, long n, float thr, int nscales, long hmax, lo
   auto *i0 = reinterpret_cast<unsigned *>(k1 + n);
   auto *i1 = i0 + n;
   auto *hist = i1 + n;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCAN_SMEM);
+    attr = true;
+  }
   cudaMemsetAsync(d_npass, 0, sizeof(unsigned), st);
   prof->begin("sort_keys", st);
   k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(blobs, n, thr, nscales, hmax, wmax, k0, i0, d_npass);
@@ -173,7 +198,7 @@ int launch_sort(const Blob *blobs, long n, float thr, int nscales, long hmax, lo
   for (int shift = 0; shift < keybits; shift += 8) {
     prof->begin("sort_pass", st);
     k_hist<<<(unsigned)nb, SORT_NT, 0, st>>>(k0, n, shift, hist);
-    k_scan<<<1, 1024, 0, st>>>(hist, 256 * nb);
+    k_scan<<<1, SCAN_NT, SCAN_SMEM, st>>>(hist, 256 * nb);
     k_scatter<<<(unsigned)nb, SORT_NT, 0, st>>>(k0, i0, n, shift, hist, k1, i1);
     prof->end(st);
     std::swap(k0, k1);
