@@ -272,6 +272,63 @@ int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes,
                 const double *scales, int nscales, int type, int order,
                 const kf_bank_opts *opts, int32_t *chosen, float *ms_out);
 
+/* ---- proposal network (gating) --------------------------------------------
+ * A small convolutional network, with no counterpart in the paper, predicts
+ * per 64 x 64-pixel tile and scale whether the bank can find a blob there;
+ * kf_filter_bank with opts->gate = 1 then runs the detector's work only on
+ * tiles it marks (plus their neighbours).  Definition (all products with the
+ * bf16 rounding of the FP32 master weights, all sums in FP32):
+ *   pooled p = 8 x 8 block means of the frame times its value scale
+ *              (ceil(H/8) x ceil(W/8); partial blocks average what they hold)
+ *   a1 = relu(conv3x3(p; 1 -> 16)), a2 = relu(conv3x3(a1; 16 -> 16)),
+ *   o3 = conv3x3(a2; 16 -> 8)   (cross-correlation, zero padding, + bias)
+ *   logit[c][ty][tx] = max of o3[c] over pooled pixels [8ty, 8ty+8) x [8tx, 8tx+8)
+ * Channel c is scale c of the bank (banks of up to 8 scales).
+ * Parameters: KF_NET_NPARAM floats W1[16][1][3][3] b1[16] W2[16][16][3][3]
+ * b2[16] W3[8][16][3][3] b3[8].  Training: mean over logits of
+ * pw t softplus(-z) + (1 - t) softplus(z), Adam (0.9, 0.999, 1e-8). */
+#define KF_NET_NPARAM 3640
+#define KF_NET_CHANNELS 8
+
+/* Set the FP32 master weights (host array of KF_NET_NPARAM) and reset the
+ * Adam state.  Errors: KF_EINVAL, KF_ENOMEM, KF_ECUDA. */
+int kf_proposal_set_weights(kf_ctx *ctx, const float *weights);
+
+/* Copy the FP32 master weights to weights (host, KF_NET_NPARAM); synchronises
+ * the context stream.  Errors: KF_EINVAL (NULL, no weights set), KF_ECUDA. */
+int kf_proposal_get_weights(kf_ctx *ctx, float *weights);
+
+/* Pooled frames: for frame f, ceil(H/8) x ceil(W/8) floats, frames back to
+ * back in `pooled` (device, caller-owned).  Asynchronous.
+ * Errors: KF_EINVAL, KF_ECUDA. */
+int kf_proposal_pool(kf_ctx *ctx, const kf_frame *frames, int nframes, float *pooled);
+
+/* Logits of n pooled images pooled[n][h][w] (device) into
+ * logits[n][8][ceil(h/8)][ceil(w/8)] (device).  Asynchronous.
+ * Errors: KF_EINVAL (no weights), KF_ENOMEM, KF_ECUDA. */
+int kf_proposal_logits(kf_ctx *ctx, const float *pooled, int n, int h, int w, float *logits);
+
+/* Loss and gradient on a batch: pooled[n][h][w] and labels (0/1 bytes)
+ * [n][8][ceil(h/8)][ceil(w/8)] (device); *loss and grad[KF_NET_NPARAM]
+ * (host, either may be NULL) receive the mean loss and its gradient with
+ * respect to the bf16 weights.  Synchronises the context stream when an output
+ * is requested.  Errors: KF_EINVAL, KF_ENOMEM, KF_ECUDA. */
+int kf_proposal_grad(kf_ctx *ctx, const float *pooled, const uint8_t *labels, int n, int h, int w,
+                     float pos_weight, float *grad, float *loss);
+
+/* One Adam step of the masters on a batch (as kf_proposal_grad); *loss (host,
+ * may be NULL: no synchronisation) receives the batch loss before the step.
+ * Errors: KF_EINVAL, KF_ENOMEM, KF_ECUDA. */
+int kf_proposal_train_step(kf_ctx *ctx, const float *pooled, const uint8_t *labels, int n, int h, int w,
+                           float pos_weight, float lr, float *loss);
+
+/* Training labels from the last kf_filter_bank call: for frame f, bytes
+ * [S][ceil(H/64)][ceil(W/64)] (frames back to back, device, caller-owned),
+ * 1 where a candidate with |R| > threshold has its centre in the tile.
+ * Zeroes the array first.  threshold >= the bank threshold.
+ * Errors: KF_EINVAL, KF_ERERUN (candidate list overflowed), KF_ECUDA. */
+int kf_proposal_labels(kf_ctx *ctx, double threshold, uint8_t *labels);
+
 /* Size of the static scratch that kf_responses_noalloc uses (MiB). */
 #define KF_NOALLOC_SCRATCH_MB 32
 

@@ -85,6 +85,17 @@ struct kf_ctx {
   // batches); the persistent shapes remain candidates of the autotuner.
   int grid_mult[3][KF_NPASS] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
   int seg_len[3] = {64, 64, 64};  // recursive banks: column segment length (kf_set_segment_length)
+  std::vector<int> last_H, last_W;  // frame sizes of the last bank call
+  // proposal network: FP32 masters, Adam moments, bf16 working copy, gradient, loss
+  float *net_master = nullptr, *net_m = nullptr, *net_v = nullptr, *net_g = nullptr, *net_loss = nullptr;
+  __nv_bfloat16 *net_wb = nullptr;
+  int net_step = 0;
+  bool net_ready = false;
+  float *net_work = nullptr;
+  size_t net_work_floats = 0;
+  long *d_loff = nullptr;  // labels: per-frame offsets and tile grid
+  int *d_ltw = nullptr, *d_lth = nullptr;
+  int lab_frames = 0;
 };
 
 namespace {
@@ -344,6 +355,10 @@ void kf_destroy(kf_ctx *ctx) {
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   drop_graphs(ctx);
   cudaFree(ctx->d_table);
+  for (void *q : {(void *)ctx->net_master, (void *)ctx->net_m, (void *)ctx->net_v, (void *)ctx->net_g,
+                  (void *)ctx->net_loss, (void *)ctx->net_wb, (void *)ctx->net_work, (void *)ctx->d_loff,
+                  (void *)ctx->d_ltw, (void *)ctx->d_lth})
+    cudaFree(q);
   for (int i = 0; i < kf_ctx::kRing; ++i) {
     if (ctx->h_table[i]) cudaFreeHost(ctx->h_table[i]);
     if (ctx->table_ev[i]) cudaEventDestroy(ctx->table_ev[i]);
@@ -652,6 +667,9 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   ctx->last_hmax = maxH;
   ctx->last_wmax = 0;
   for (int f = 0; f < nframes; ++f) ctx->last_wmax = std::max(ctx->last_wmax, (long)frames[f].width);
+  ctx->last_H.resize(nframes);
+  ctx->last_W.resize(nframes);
+  for (int f = 0; f < nframes; ++f) ctx->last_H[f] = frames[f].height, ctx->last_W[f] = frames[f].width;
   return KF_OK;
 }
 
@@ -761,6 +779,178 @@ int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *
   }
   if (chosen) chosen[KF_NPASS] = iir ? lcs[best_l] : -1;
   drop_graphs(ctx);
+  return KF_OK;
+}
+
+// ---- proposal network --------------------------------------------------------
+
+int kf_proposal_set_weights(kf_ctx *ctx, const float *weights) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_proposal_set_weights: ctx is NULL");
+  if (!weights) return fail(ctx, KF_EINVAL, "kf_proposal_set_weights: weights is NULL");
+  cudaError_t e;
+  if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  const size_t nb = sizeof(float) * kf::NET_NPARAM;
+  if (!ctx->net_master) {
+    for (float **q : {&ctx->net_master, &ctx->net_m, &ctx->net_v, &ctx->net_g})
+      if ((e = cudaMalloc(q, nb)) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(network)");
+    if ((e = cudaMalloc(&ctx->net_loss, sizeof(float))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(loss)");
+    if ((e = cudaMalloc(&ctx->net_wb, sizeof(__nv_bfloat16) * kf::NET_NPARAM)) != cudaSuccess)
+      return cuda_fail(ctx, e, "cudaMalloc(network)");
+  }
+  if ((e = cudaMemcpyAsync(ctx->net_master, weights, nb, cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ctx->net_m, 0, nb, ctx->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ctx->net_v, 0, nb, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "set weights");
+  if (kf::net_to_bf16(ctx->net_master, ctx->net_wb, ctx->stream)) return cuda_fail(ctx, cudaGetLastError(), "bf16");
+  // the host array may be reused as soon as the copy has been made
+  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "set weights");
+  ctx->net_step = 0;
+  ctx->net_ready = true;
+  drop_graphs(ctx);
+  return KF_OK;
+}
+
+int kf_proposal_get_weights(kf_ctx *ctx, float *weights) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_proposal_get_weights: ctx is NULL");
+  if (!weights || !ctx->net_ready) return fail(ctx, KF_EINVAL, "kf_proposal_get_weights: no weights / NULL output");
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(weights, ctx->net_master, sizeof(float) * kf::NET_NPARAM, cudaMemcpyDeviceToHost,
+                           ctx->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "get weights");
+  return KF_OK;
+}
+
+int kf_proposal_pool(kf_ctx *ctx, const kf_frame *frames, int nframes, float *pooled) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_proposal_pool: ctx is NULL");
+  if (!frames || nframes < 1 || !pooled) return fail(ctx, KF_EINVAL, "kf_proposal_pool: bad arguments");
+  long off = 0;
+  for (int f = 0; f < nframes; ++f) {
+    const kf_frame &fr = frames[f];
+    if (!fr.data || fr.width < 1 || fr.height < 1 || fr.pitch < fr.width || fr.dtype < 0 || fr.dtype > 3)
+      return fail(ctx, KF_EINVAL, "kf_proposal_pool: frame %d is invalid", f);
+    if (kf::net_pool(fr.data, fr.dtype, fr.value_scale == 0.0f ? 1.0f : fr.value_scale, fr.pitch, fr.height,
+                     fr.width, pooled + off, ctx->stream))
+      return cuda_fail(ctx, cudaGetLastError(), "pool");
+    off += (long)((fr.height + 7) / 8) * ((fr.width + 7) / 8);
+  }
+  return KF_OK;
+}
+
+namespace {
+int net_check(kf_ctx *ctx, const float *pooled, int n, int h, int w, const char *who) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "%s: ctx is NULL", who);
+  if (!ctx->net_ready) return fail(ctx, KF_EINVAL, "%s: no weights set", who);
+  if (!pooled || n < 1 || h < 1 || w < 1) return fail(ctx, KF_EINVAL, "%s: bad arguments", who);
+  const size_t need = kf::net_work_floats(n, h, w);
+  if (need > ctx->net_work_floats) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->net_work);
+    ctx->net_work = nullptr;
+    ctx->net_work_floats = 0;
+    const cudaError_t e = cudaMalloc(&ctx->net_work, need * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(network workspace)");
+    ctx->net_work_floats = need;
+  }
+  return KF_OK;
+}
+}  // namespace
+
+int kf_proposal_logits(kf_ctx *ctx, const float *pooled, int n, int h, int w, float *logits) {
+  if (int rc = net_check(ctx, pooled, n, h, w, "kf_proposal_logits")) return rc;
+  if (!logits) return fail(ctx, KF_EINVAL, "kf_proposal_logits: logits is NULL");
+  if (kf::net_forward(pooled, n, h, w, ctx->net_wb, ctx->net_work, logits, ctx->stream))
+    return cuda_fail(ctx, cudaGetLastError(), "network forward");
+  return KF_OK;
+}
+
+int kf_proposal_grad(kf_ctx *ctx, const float *pooled, const uint8_t *labels, int n, int h, int w,
+                     float pos_weight, float *grad, float *loss) {
+  if (int rc = net_check(ctx, pooled, n, h, w, "kf_proposal_grad")) return rc;
+  if (!labels || !(pos_weight > 0.f)) return fail(ctx, KF_EINVAL, "kf_proposal_grad: bad labels / pos_weight");
+  if (kf::net_grad(pooled, labels, n, h, w, pos_weight, ctx->net_wb, ctx->net_work, ctx->net_g, ctx->net_loss,
+                   ctx->stream))
+    return cuda_fail(ctx, cudaGetLastError(), "network gradient");
+  cudaError_t e;
+  if (grad && (e = cudaMemcpyAsync(grad, ctx->net_g, sizeof(float) * kf::NET_NPARAM, cudaMemcpyDeviceToHost,
+                                   ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "copy gradient");
+  if (loss && (e = cudaMemcpyAsync(loss, ctx->net_loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream)) !=
+                  cudaSuccess)
+    return cuda_fail(ctx, e, "copy loss");
+  if ((grad || loss) && (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "grad");
+  return KF_OK;
+}
+
+int kf_proposal_train_step(kf_ctx *ctx, const float *pooled, const uint8_t *labels, int n, int h, int w,
+                           float pos_weight, float lr, float *loss) {
+  if (int rc = net_check(ctx, pooled, n, h, w, "kf_proposal_train_step")) return rc;
+  if (!labels || !(pos_weight > 0.f) || !(lr > 0.f))
+    return fail(ctx, KF_EINVAL, "kf_proposal_train_step: bad labels / pos_weight / lr");
+  if (kf::net_grad(pooled, labels, n, h, w, pos_weight, ctx->net_wb, ctx->net_work, ctx->net_g, ctx->net_loss,
+                   ctx->stream))
+    return cuda_fail(ctx, cudaGetLastError(), "network gradient");
+  ctx->net_step += 1;
+  if (kf::net_adam(ctx->net_master, ctx->net_m, ctx->net_v, ctx->net_g, ctx->net_step, lr, ctx->net_wb, ctx->stream))
+    return cuda_fail(ctx, cudaGetLastError(), "Adam");
+  cudaError_t e;
+  if (loss) {
+    if ((e = cudaMemcpyAsync(loss, ctx->net_loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "copy loss");
+  }
+  return KF_OK;
+}
+
+int kf_proposal_labels(kf_ctx *ctx, double threshold, uint8_t *labels) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_proposal_labels: ctx is NULL");
+  if (!labels || !ctx->have_result) return fail(ctx, KF_EINVAL, "kf_proposal_labels: no bank result / NULL output");
+  if (!(threshold >= ctx->last_threshold))
+    return fail(ctx, KF_EINVAL, "threshold %g is below the bank threshold %g", threshold, ctx->last_threshold);
+  cudaError_t e;
+  kf::DevStatus st;
+  if ((e = cudaMemcpyAsync(&st, ctx->status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "read status");
+  if (st.error) return fail(ctx, KF_ETIMEOUT, "device wait gave up (code %d)", st.error);
+  if (st.count > (unsigned long long)ctx->blob_cap)
+    return fail(ctx, KF_ERERUN, "candidate list overflowed (%llu found): raise the capacity with kf_detect_blobs",
+                (unsigned long long)st.count);
+  const int nf = (int)ctx->last_H.size(), S = ctx->last_S;
+  std::vector<long> loff(nf);
+  std::vector<int> tw(nf), th(nf);
+  long off = 0;
+  for (int f = 0; f < nf; ++f) {
+    th[f] = (ctx->last_H[f] + 63) / 64;
+    tw[f] = (ctx->last_W[f] + 63) / 64;
+    loff[f] = off;
+    off += (long)S * th[f] * tw[f];
+  }
+  if (nf > ctx->lab_frames) {
+    cudaFree(ctx->d_loff);
+    cudaFree(ctx->d_ltw);
+    cudaFree(ctx->d_lth);
+    ctx->lab_frames = 0;
+    if ((e = cudaMalloc(&ctx->d_loff, sizeof(long) * nf)) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->d_ltw, sizeof(int) * nf)) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->d_lth, sizeof(int) * nf)) != cudaSuccess)
+      return cuda_fail(ctx, e, "cudaMalloc(labels)");
+    ctx->lab_frames = nf;
+  }
+  if ((e = cudaMemcpyAsync(ctx->d_loff, loff.data(), sizeof(long) * nf, cudaMemcpyHostToDevice, ctx->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(ctx->d_ltw, tw.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, ctx->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(ctx->d_lth, th.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, ctx->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(labels, 0, (size_t)off, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "labels");
+  if (kf::net_labels(ctx->blobs, (long)st.count, (float)threshold, ctx->d_loff, ctx->d_ltw, ctx->d_lth, S, labels,
+                     ctx->stream))
+    return cuda_fail(ctx, cudaGetLastError(), "labels");
+  // the host arrays above go out of scope: wait for their copies
+  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "labels");
   return KF_OK;
 }
 

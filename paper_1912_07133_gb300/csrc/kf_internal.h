@@ -2,6 +2,7 @@
 // units (launchers of the CUDA kernels).  Not part of the C ABI.
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -91,6 +92,20 @@ int encode_plane_map(CUtensorMap *m, void *P, int storage, long PWb, long prows,
 // mult = k >= 1, at most k x the blocks of this kernel and block shape that are
 // resident on the whole GPU at once (each block loops over items)
 int persistent_blocks(const void *kernel, int threads, size_t smem, int items, int mult);
+
+// proposal network (kf_proposal.cu): flat parameters W1 b1 W2 b2 W3 b3
+constexpr int NET_NPARAM = 3640;
+size_t net_work_floats(int N, int h, int w);
+int net_pool(const void *X, int dtype, float vs, long xpitch, int H, int W, float *out, cudaStream_t st);
+int net_forward(const float *x, int N, int h, int w, const __nv_bfloat16 *wb, float *work, float *z_out,
+                cudaStream_t st);
+int net_grad(const float *x, const unsigned char *t, int N, int h, int w, float pw, const __nv_bfloat16 *wb,
+             float *work, float *g, float *loss_dev, cudaStream_t st);
+int net_adam(float *master, float *m, float *v, const float *g, int step, float lr, __nv_bfloat16 *wb,
+             cudaStream_t st);
+int net_to_bf16(const float *x, __nv_bfloat16 *y, cudaStream_t st);
+int net_labels(const Blob *b, long n, float thr, const long *loff, const int *ltw, const int *lth, int S,
+               unsigned char *lab, cudaStream_t st);
 
 // candidate ordering (kf_sort.cu)
 size_t sort_workspace_bytes(long n);

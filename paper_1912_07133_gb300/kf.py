@@ -49,7 +49,11 @@ KF_MAX_FIR_K = 160
 
 ENTRY_POINTS = ("kf_bank_opts_default", "kf_create", "kf_destroy", "kf_last_error", "kf_design",
                 "kf_filter_bank", "kf_detect_blobs", "kf_kernel_times", "kf_responses_noalloc",
-                "kf_set_launch_shape", "kf_set_segment_length", "kf_autotune")
+                "kf_set_launch_shape", "kf_set_segment_length", "kf_autotune",
+                "kf_proposal_set_weights", "kf_proposal_get_weights", "kf_proposal_pool", "kf_proposal_logits",
+                "kf_proposal_grad", "kf_proposal_train_step", "kf_proposal_labels")
+KF_NET_NPARAM = 3640
+KF_NET_CHANNELS = 8
 KF_PASS_ROW, KF_PASS_SEG, KF_PASS_FOLD, KF_PASS_DET, KF_NPASS = 0, 1, 2, 3, 4
 GRID_CANDIDATES = (1, 2, 4, 0)
 KF_NOALLOC_SCRATCH_MB = 32
@@ -130,6 +134,21 @@ def load(path: str = LIB_PATH):
     L.kf_responses_noalloc.argtypes = [ctypes.POINTER(kf_frame), ctypes.POINTER(dbl), i32, i32, i32, vp, vp]
     L.kf_set_launch_shape.restype = i32
     L.kf_set_launch_shape.argtypes = [vp, i32, i32, i32]
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.kf_proposal_set_weights.restype = i32
+    L.kf_proposal_set_weights.argtypes = [vp, fp]
+    L.kf_proposal_get_weights.restype = i32
+    L.kf_proposal_get_weights.argtypes = [vp, fp]
+    L.kf_proposal_pool.restype = i32
+    L.kf_proposal_pool.argtypes = [vp, ctypes.POINTER(kf_frame), i32, vp]
+    L.kf_proposal_logits.restype = i32
+    L.kf_proposal_logits.argtypes = [vp, vp, i32, i32, i32, vp]
+    L.kf_proposal_grad.restype = i32
+    L.kf_proposal_grad.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.c_float, fp, fp]
+    L.kf_proposal_train_step.restype = i32
+    L.kf_proposal_train_step.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.c_float, ctypes.c_float, fp]
+    L.kf_proposal_labels.restype = i32
+    L.kf_proposal_labels.argtypes = [vp, dbl, vp]
     L.kf_set_segment_length.restype = i32
     L.kf_set_segment_length.argtypes = [vp, i32, i32]
     L.kf_autotune.restype = i32
@@ -293,6 +312,77 @@ def kf_autotune(ctx: int, frames, scales, ftype: int, order: int, opts: kf_bank_
                               chosen, ms), ctx)
     times = {p: list(ms[4 * p: 4 * p + 4]) for p in range(KF_NPASS) if chosen[p] >= 0}
     return list(chosen[:KF_NPASS]), chosen[KF_NPASS], times
+
+
+def _cuda_tensor(t, dtype, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous {dtype} CUDA tensor")
+    return t.data_ptr()
+
+
+def kf_proposal_set_weights(ctx: int, weights) -> None:
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    if w.size != KF_NET_NPARAM:
+        raise ValueError(f"need {KF_NET_NPARAM} weights")
+    _check(load().kf_proposal_set_weights(ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), ctx)
+
+
+def kf_proposal_get_weights(ctx: int) -> np.ndarray:
+    w = np.empty(KF_NET_NPARAM, np.float32)
+    _check(load().kf_proposal_get_weights(ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), ctx)
+    return w
+
+
+def pooled_shape(H: int, W: int):
+    return (H + 7) // 8, (W + 7) // 8
+
+
+def kf_proposal_pool(ctx: int, frames, out, value_scales=None) -> None:
+    """Pooled frames, back to back, into the float32 CUDA tensor `out`."""
+    import torch
+    need = sum(int(np.prod(pooled_shape(*f.shape))) for f in frames)
+    if out.numel() < need:
+        raise ValueError(f"out needs {need} elements")
+    vs = value_scales if value_scales is not None else [0.0] * len(frames)
+    descs = (kf_frame * len(frames))(*[_frame_desc(f, v) for f, v in zip(frames, vs)])
+    _check(load().kf_proposal_pool(ctx, descs, len(frames), _cuda_tensor(out, torch.float32, "out")), ctx)
+
+
+def kf_proposal_logits(ctx: int, pooled, logits) -> None:
+    """pooled [n, h, w] float32 -> logits [n, 8, ceil(h/8), ceil(w/8)] float32 (CUDA tensors)."""
+    import torch
+    n, h, w = pooled.shape
+    _check(load().kf_proposal_logits(ctx, _cuda_tensor(pooled, torch.float32, "pooled"), n, h, w,
+                                     _cuda_tensor(logits, torch.float32, "logits")), ctx)
+
+
+def kf_proposal_grad(ctx: int, pooled, labels, pos_weight: float):
+    """(loss, gradient[KF_NET_NPARAM]) on a batch (CUDA tensors: pooled float32
+    [n, h, w], labels uint8 [n, 8, ceil(h/8), ceil(w/8)])."""
+    import torch
+    n, h, w = pooled.shape
+    g = np.empty(KF_NET_NPARAM, np.float32)
+    loss = ctypes.c_float(0)
+    _check(load().kf_proposal_grad(ctx, _cuda_tensor(pooled, torch.float32, "pooled"),
+                                   _cuda_tensor(labels, torch.uint8, "labels"), n, h, w, float(pos_weight),
+                                   g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss)), ctx)
+    return float(loss.value), g
+
+
+def kf_proposal_train_step(ctx: int, pooled, labels, pos_weight: float, lr: float, want_loss=True):
+    import torch
+    n, h, w = pooled.shape
+    loss = ctypes.c_float(0)
+    _check(load().kf_proposal_train_step(ctx, _cuda_tensor(pooled, torch.float32, "pooled"),
+                                         _cuda_tensor(labels, torch.uint8, "labels"), n, h, w, float(pos_weight),
+                                         float(lr), ctypes.byref(loss) if want_loss else None), ctx)
+    return float(loss.value) if want_loss else None
+
+
+def kf_proposal_labels(ctx: int, threshold: float, labels) -> None:
+    import torch
+    _check(load().kf_proposal_labels(ctx, float(threshold), _cuda_tensor(labels, torch.uint8, "labels")), ctx)
 
 
 class Bank:
