@@ -142,7 +142,19 @@ typedef struct {
                             storage, threshold, neighbourhood, schedule,
                             frame count and each frame's width and height.
                             Ignored when profile = 1.                        */
-  int64_t reserved[3];
+  int32_t gate;          /* 1: proposal gating (needs kf_proposal_set_weights,
+                            <= 8 scales, the batched schedule).  Per frame the
+                            proposal network marks 64 x 64 tiles whose logit
+                            of some scale exceeds logit(gate_threshold) in the
+                            tile or its 8 neighbours; only column-pass tiles
+                            overlapping marked tiles run (all scales: the
+                            extremum over scales stays exact), and for the FIR
+                            bank only the row-pass rows they read.  Every blob
+                            reported is the full bank's blob; blobs in unmarked
+                            tiles are not found, and responses there are not
+                            written.                                          */
+  float gate_threshold;  /* probability threshold of the gate, in (0, 1)     */
+  int64_t reserved[2];
 } kf_bank_opts;
 
 /* One detection (Threshold #1 extremum). */

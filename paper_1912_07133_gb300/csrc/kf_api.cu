@@ -96,6 +96,15 @@ struct kf_ctx {
   long *d_loff = nullptr;  // labels: per-frame offsets and tile grid
   int *d_ltw = nullptr, *d_lth = nullptr;
   int lab_frames = 0;
+  // gating buffers: pooled frames, logits, active-tile maps, selected items, counts
+  float *g_pooled = nullptr, *g_logits = nullptr;
+  size_t g_pooled_n = 0, g_logits_n = 0;
+  unsigned char *g_act = nullptr;
+  size_t g_act_n = 0;
+  int2 *g_sel[2] = {nullptr, nullptr};
+  size_t g_sel_n[2] = {0, 0};
+  int *g_count = nullptr;
+  size_t g_count_n = 0;
 };
 
 namespace {
@@ -271,7 +280,13 @@ int upload_table(kf_ctx *ctx, const void *bytes, size_t n) {
 std::vector<long long> call_key(const kf_ctx *ctx, const kf_frame *frames, int nframes, const double *scales, int S,
                                 int type, int order, int kmax, const kf_bank_opts &o) {
   std::vector<long long> k = {type, order, kmax, S, o.storage, o.neighbourhood, o.schedule, nframes,
-                              (long long)(intptr_t)ctx->cur};
+                              (long long)(intptr_t)ctx->cur, o.gate};
+  if (o.gate) {
+    long long gt;
+    double g = o.gate_threshold;
+    std::memcpy(&gt, &g, sizeof gt);
+    k.push_back(gt);
+  }
   for (int p = 0; p < KF_NPASS; ++p) k.push_back(ctx->grid_mult[type][p]);
   k.push_back(ctx->seg_len[type]);
   long long t;
@@ -289,6 +304,7 @@ std::vector<long long> call_key(const kf_ctx *ctx, const kf_frame *frames, int n
 }
 
 constexpr size_t kGraphSlots = 4;
+constexpr int TW_COL = kf::TW;  // interior columns of a column-pass tile
 
 }  // namespace
 
@@ -309,6 +325,7 @@ int kf_bank_opts_default(kf_bank_opts *o) {
   o->threshold = 0.05;
   o->fir_kmax = 96;
   o->responses = nullptr;
+  o->gate_threshold = 0.25f;
   return KF_OK;
 }
 
@@ -355,6 +372,9 @@ void kf_destroy(kf_ctx *ctx) {
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   drop_graphs(ctx);
   cudaFree(ctx->d_table);
+  for (void *q : {(void *)ctx->g_pooled, (void *)ctx->g_logits, (void *)ctx->g_act, (void *)ctx->g_sel[0],
+                  (void *)ctx->g_sel[1], (void *)ctx->g_count})
+    cudaFree(q);
   for (void *q : {(void *)ctx->net_master, (void *)ctx->net_m, (void *)ctx->net_v, (void *)ctx->net_g,
                   (void *)ctx->net_loss, (void *)ctx->net_wb, (void *)ctx->net_work, (void *)ctx->d_loff,
                   (void *)ctx->d_ltw, (void *)ctx->d_lth})
@@ -436,6 +456,14 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   if (kmax_opt > KF_MAX_FIR_K) return fail(ctx, KF_EINVAL, "fir_kmax must be <= %d", KF_MAX_FIR_K);
   if (opts.schedule != KF_SCHED_BATCHED && opts.schedule != KF_SCHED_PER_FRAME)
     return fail(ctx, KF_EINVAL, "unknown schedule %d", opts.schedule);
+  const bool gate = opts.gate != 0;
+  if (gate) {
+    if (!ctx->net_ready) return fail(ctx, KF_EINVAL, "gating needs proposal weights (kf_proposal_set_weights)");
+    if (nscales > KF_NET_CHANNELS) return fail(ctx, KF_EINVAL, "gating covers at most %d scales", KF_NET_CHANNELS);
+    if (opts.schedule != KF_SCHED_BATCHED) return fail(ctx, KF_EINVAL, "gating runs with the batched schedule");
+    if (!(opts.gate_threshold > 0.f && opts.gate_threshold < 1.f))
+      return fail(ctx, KF_EINVAL, "gate_threshold must be in (0, 1)");
+  }
   long maxH = 0, maxPW = 0;
   for (int f = 0; f < nframes; ++f) {
     const kf_frame &fr = frames[f];
@@ -468,11 +496,18 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   // ---- layout: every frame resident in one plane row space of pitch PWb ----
   const long PWb = maxPW;
   std::vector<kf::FrameDev> fd(nframes);
-  long prows = 0, roff = 0;
+  long prows = 0, roff = 0, aoff = 0, poff = 0, zoff = 0;
   size_t coff = 0;
+  std::vector<long> g_poff(nframes), g_zoff(nframes);
   for (int f = 0; f < nframes; ++f) {
     const kf_frame &fr = frames[f];
     kf::FrameDev &d = fd[f];
+    d.aoff = aoff;
+    g_poff[f] = poff;
+    g_zoff[f] = zoff;
+    aoff += (long)((fr.height + 63) / 64) * ((fr.width + 63) / 64);
+    poff += (long)((fr.height + 7) / 8) * ((fr.width + 7) / 8);
+    zoff += (long)KF_NET_CHANNELS * ((fr.height + 63) / 64) * ((fr.width + 63) / 64);
     d.X = fr.data;
     d.resp = opts.responses ? opts.responses + roff : nullptr;
     d.xpitch = fr.pitch;
@@ -574,6 +609,58 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     x.nt = l.nt;
     plan.pass[l.pass].push_back(x);
   }
+  // ---- gating: buffers and the gated launches --------------------------------
+  kf::Items full_det{}, full_row{};
+  if (gate) {
+    int ph = 1, pw = 1;
+    for (int f = 0; f < nframes; ++f) {
+      ph = std::max(ph, (frames[f].height + 7) / 8);
+      pw = std::max(pw, (frames[f].width + 7) / 8);
+    }
+    if ((rc = grow(ctx, &ctx->g_pooled, &ctx->g_pooled_n, (size_t)std::max(poff, 1L), "gate pooled")) ||
+        (rc = grow(ctx, &ctx->g_logits, &ctx->g_logits_n, (size_t)std::max(zoff, 1L), "gate logits")) ||
+        (rc = grow(ctx, &ctx->g_act, &ctx->g_act_n, (size_t)std::max(aoff, 1L), "gate tiles")) ||
+        (rc = grow(ctx, &ctx->g_count, &ctx->g_count_n, (size_t)2, "gate counts")) ||
+        (rc = grow(ctx, &ctx->net_work, &ctx->net_work_floats, kf::net_work_floats(1, ph, pw), "network workspace")))
+      return rc;
+    full_det = plan.pass[kf::PASS_DET][0].it;
+    if ((rc = grow(ctx, &ctx->g_sel[0], &ctx->g_sel_n[0], (size_t)std::max(full_det.total, 1), "gate items")))
+      return rc;
+    plan.pass[kf::PASS_DET][0].it.sel = ctx->g_sel[0];
+    plan.pass[kf::PASS_DET][0].it.dcount = ctx->g_count;
+    if (!iir) {
+      full_row = plan.pass[kf::PASS_ROW][0].it;
+      if ((rc = grow(ctx, &ctx->g_sel[1], &ctx->g_sel_n[1], (size_t)std::max(full_row.total, 1), "gate items")))
+        return rc;
+      plan.pass[kf::PASS_ROW][0].it.sel = ctx->g_sel[1];
+      plan.pass[kf::PASS_ROW][0].it.dcount = ctx->g_count + 1;
+    }
+  }
+  // pooling, logits and tile maps of every frame, then the selected items
+  auto issue_gate = [&](cudaStream_t st, kf::Prof *prof) -> int {
+    const float p = opts.gate_threshold, zthr = std::log(p / (1.f - p));
+    prof->begin("gate", st);
+    for (int f = 0; f < nframes; ++f) {
+      const int H = frames[f].height, W = frames[f].width;
+      const int ph = (H + 7) / 8, pw = (W + 7) / 8, th = (H + 63) / 64, tw = (W + 63) / 64;
+      if (kf::net_pool_table(plan.fr, f, H, W, ctx->g_pooled + g_poff[f], st) ||
+          kf::net_forward(ctx->g_pooled + g_poff[f], 1, ph, pw, ctx->net_wb, ctx->net_work, ctx->g_logits + g_zoff[f],
+                          st) ||
+          kf::gate_tiles(ctx->g_logits + g_zoff[f], nscales, th, tw, zthr, ctx->g_act + fd[f].aoff, st))
+        return cuda_fail(ctx, cudaGetLastError(), "gate");
+    }
+    cudaError_t ee;
+    if ((ee = cudaMemsetAsync(ctx->g_count, 0, 2 * sizeof(int), st)) != cudaSuccess)
+      return cuda_fail(ctx, ee, "gate counts");
+    const int rows = iir ? ctx->seg_len[type] : kf::fir_tile_rows(opts.neighbourhood);
+    if (kf::gate_select_tiles(plan.fr, full_det, ctx->g_act, TW_COL, rows, ctx->g_sel[0], ctx->g_count, st))
+      return cuda_fail(ctx, cudaGetLastError(), "gate selection");
+    if (!iir && kf::gate_select_rows(plan.fr, full_row, ctx->g_act, kf::fir_row_segment(), kf::fir_halo(kmax) + 130,
+                                     ctx->g_sel[1], ctx->g_count + 1, st))
+      return cuda_fail(ctx, cudaGetLastError(), "gate selection");
+    prof->end(st);
+    return KF_OK;
+  };
   kf::BankArgs a;
   a.coef = ctx->cur->d_coef;
   a.S = nscales;
@@ -595,6 +682,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     if ((ee = cudaMemsetAsync(ctx->status, 0, sizeof(kf::DevStatus), st)) != cudaSuccess)
       return cuda_fail(ctx, ee, "reset status");
     a.prof = prof;
+    if (gate)
+      if (int grc = issue_gate(st, prof)) return grc;
     const int lr = iir ? kf::launch_iir(plan, a, st) : kf::launch_fir(plan, a, st);
     if (lr == -2) return fail(ctx, KF_EINVAL, "no kernel instance for order %d", order);
     if (lr) return cuda_fail(ctx, cudaGetLastError(), "filter-bank kernel launch");
@@ -844,6 +933,7 @@ int net_check(kf_ctx *ctx, const float *pooled, int n, int h, int w, const char 
   if (!pooled || n < 1 || h < 1 || w < 1) return fail(ctx, KF_EINVAL, "%s: bad arguments", who);
   const size_t need = kf::net_work_floats(n, h, w);
   if (need > ctx->net_work_floats) {
+    drop_graphs(ctx);  // gated graphs hold the workspace pointer
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->net_work);
     ctx->net_work = nullptr;

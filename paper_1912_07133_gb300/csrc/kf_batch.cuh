@@ -25,6 +25,7 @@ struct FrameDev {
   long coff;       // floats: IIR column carries [S][nseg][2][NF][PWb]
   int dtype;       // IN_F32 / IN_F16 / IN_BF16 / IN_U16
   float vscale;    // input multiplier
+  long aoff;       // gated calls: byte offset of the frame's active-tile map (64 x 64 tiles)
   int H, W;
   int nseg;        // IIR column segments
   int index;       // frame index in the call (blob records)
@@ -34,13 +35,31 @@ struct Items {
   const int *fl;   // frames of this launch: indices into the frame table
   const int *pre;  // exclusive prefix sums of the items per frame (n + 1 entries)
   int n;           // frames in the launch
-  int total;       // items in the launch (pre[n])
+  int total;       // items in the launch (pre[n]); with sel: the capacity of the list
+  const int2 *sel = nullptr;    // gated launches: selected (position in fl, item of that frame) pairs
+  const int *dcount = nullptr;  // gated launches: number of selected pairs (device)
 };
 
 // position in it.fl of the frame that holds `item`, starting the search at k
 // (the items a block takes only increase, so k only advances)
 __device__ __forceinline__ int advance_frame(const Items &it, int item, int k) {
   while (item >= __ldg(it.pre + k + 1)) ++k;
+  return k;
+}
+
+// items of the launch (a gated launch reads its count from the device)
+__device__ __forceinline__ int items_total(const Items &it) { return it.dcount ? __ldg(it.dcount) : it.total; }
+
+// position in it.fl and item of that frame for launch item `item` (k: the
+// previous position, for the monotone search of ungated launches)
+__device__ __forceinline__ int item_frame(const Items &it, int item, int k, int &local) {
+  if (it.sel) {
+    const int2 e = __ldg(it.sel + item);
+    local = e.y;
+    return e.x;
+  }
+  k = advance_frame(it, item, k);
+  local = item - __ldg(it.pre + k);
   return k;
 }
 

@@ -136,13 +136,14 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr,
   __shared__ FrameDev s_fr;
   bool ovf = false;                     // a value beyond the f16 range
   int k = 0;
-  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
-    k = advance_frame(it, item, k);
+  const int nitems = items_total(it);
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    int local;
+    k = item_frame(it, item, k, local);
     __syncthreads();  // the previous item is done with s_fr and sL
     stage_frame(&s_fr, fr, it, k);
     __syncthreads();
     const FrameDev &F = s_fr;
-    const int local = item - __ldg(it.pre + k);
     const int H = F.H, W = F.W;
     const int nxs = (W + RSEG - 1) / RSEG;
     const int xs = (local % nxs) * RSEG, ri = local / nxs;
@@ -259,12 +260,13 @@ __global__ void __launch_bounds__(CNT) k_colfir(const FrameDev *__restrict__ fr,
   float *sh = red + CROWS * 32 * 2 + CROWS * 32 * 2 / 4;
   __shared__ FrameDev s_fr;
   int k = 0;
-  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
-    k = advance_frame(it, item, k);
+  const int nitems = items_total(it);
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    int local;
+    k = item_frame(it, item, k, local);
     stage_frame(&s_fr, fr, it, k);  // the previous item ended with __syncthreads
     __syncthreads();
     const FrameDev &F = s_fr;
-    const int local = item - __ldg(it.pre + k);
     const int H = F.H, W = F.W;
     const int ntx = (W + TW - 1) / TW;
     const int x = (local % ntx) * TW - 1 + lane;
@@ -358,12 +360,13 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
   __shared__ FrameDev s_fr;
   uint32_t ph0 = 0u, ph1 = 0u;  // phase to wait for, per barrier
   int k = 0;
-  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
-    k = advance_frame(it, item, k);
+  const int nitems = items_total(it);
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    int local;
+    k = item_frame(it, item, k, local);
     stage_frame(&s_fr, fr, it, k);  // the previous item ended with __syncthreads
     __syncthreads();
     const FrameDev &F = s_fr;
-    const int local = item - __ldg(it.pre + k);
     const int H = F.H, W = F.W;
     const long prow = F.prow;
     const int ntx = (W + TW - 1) / TW;
@@ -579,6 +582,10 @@ int persistent_blocks(const void *kernel, int threads, size_t smem, int items, i
   const long cap = (long)nsm[dev] * occ * mult;
   return (int)std::max(1L, std::min((long)items, cap));
 }
+
+int fir_row_segment() { return RSEG; }
+int fir_tile_rows(int neigh) { return neigh == 0 ? CROWS2 - 2 : CROWS - 2; }
+int fir_halo(int kmax) { return kmax + TB + 1; }
 
 int fir_items(int pass, int H, int W, int S, int neigh) {
   const int ntx = (W + TW - 1) / TW;

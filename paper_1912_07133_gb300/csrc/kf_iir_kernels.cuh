@@ -367,12 +367,13 @@ __global__ void __launch_bounds__(256) k_row(const FrameDev *__restrict__ fr, It
   __shared__ FrameDev s_fr;
   bool ovf = false;  // a value beyond the f16 range
   int k = 0;
-  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
-    k = advance_frame(it, item, k);
+  const int nitems = items_total(it);
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    int local;
+    k = item_frame(it, item, k, local);
     stage_frame(&s_fr, fr, it, k);  // the previous item ended with __syncthreads
     __syncthreads();
     const FrameDev &F = s_fr;
-    const int local = item - __ldg(it.pre + k);
     const bool e = local >= F.H;
     row_body<Rec>(F, e, e ? local - F.H : local, coef, S, P, st, PWb, edge, ovf, sm);
   }
@@ -398,10 +399,11 @@ __global__ void __launch_bounds__(128) k_colseg(const FrameDev *__restrict__ fr,
                                                 const float *__restrict__ edge,
                                                 const Coef *__restrict__ coef, float *__restrict__ E) {
   int k = 0;
-  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
-    k = advance_frame(it, item, k);
+  const int nitems = items_total(it);
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    int local;
+    k = item_frame(it, item, k, local);
     const FrameDev F = fr[__ldg(it.fl + k)];  // by value: fields stay in registers
-    const int local = item - __ldg(it.pre + k);
     const int H = F.H, W = F.W, nseg = F.nseg;
     const int nxb = (W + 127) / 128;
     const int xb = local % nxb, rest = local / nxb;
@@ -463,10 +465,11 @@ __global__ void __launch_bounds__(128) k_colfold(const FrameDev *__restrict__ fr
                                                  const float *__restrict__ edge,
                                                  const Coef *__restrict__ coef, float *__restrict__ E, int S) {
   int k = 0;
-  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
-    k = advance_frame(it, item, k);
+  const int nitems = items_total(it);
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    int local;
+    k = item_frame(it, item, k, local);
     const FrameDev F = fr[__ldg(it.fl + k)];  // by value: fields stay in registers
-    const int local = item - __ldg(it.pre + k);
     const int W = F.W, nseg = F.nseg;
     const int nxb = (W + 127) / 128;
     const int xb = local % nxb, rest = local / nxb;
@@ -574,12 +577,13 @@ __global__ void __launch_bounds__(512, LC == 32 ? Rec::kColdetMinBlocks32 : 1) k
   const long fs = (long)Rec::NF * PWb;
   uint32_t phase = 0;
   int k = 0;
-  for (int item = blockIdx.x; item < it.total; item += gridDim.x) {
-    k = advance_frame(it, item, k);
+  const int nitems = items_total(it);
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    int local;
+    k = item_frame(it, item, k, local);
     stage_frame(&s_fr, fr, it, k);  // the previous item ended with __syncthreads
     __syncthreads();
     const FrameDev &F = s_fr;
-    const int local = item - __ldg(it.pre + k);
     const int H = F.H, W = F.W, nseg = F.nseg;
     const int ntx = (W + TW - 1) / TW;
     const int c = local / ntx;

@@ -106,6 +106,18 @@ int net_adam(float *master, float *m, float *v, const float *g, int step, float 
 int net_to_bf16(const float *x, __nv_bfloat16 *y, cudaStream_t st);
 int net_labels(const Blob *b, long n, float thr, const long *loff, const int *ltw, const int *lth, int S,
                unsigned char *lab, cudaStream_t st);
+// gating: active-tile map of one frame from its logits; selection of the
+// items of a column pass (interior tiles tw x th) or of the FIR row pass
+int net_pool_table(const FrameDev *fr, int f, int H, int W, float *out, cudaStream_t st);
+int gate_tiles(const float *z, int S, int th, int tw, float zthr, unsigned char *act, cudaStream_t st);
+int gate_select_tiles(const FrameDev *fr, const Items &full, const unsigned char *act, int tw, int th, int2 *sel,
+                      int *count, cudaStream_t st);
+int gate_select_rows(const FrameDev *fr, const Items &full, const unsigned char *act, int rseg, int reach,
+                     int2 *sel, int *count, cudaStream_t st);
+// geometry of the gated passes
+int fir_row_segment();         // pixels per FIR row item
+int fir_tile_rows(int neigh);  // interior rows of a FIR column tile
+int fir_halo(int kmax);        // rows a FIR column tile reads beyond its 128 (or 64) rows
 
 // candidate ordering (kf_sort.cu)
 size_t sort_workspace_bytes(long n);

@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 #include <math_constants.h>
 
+#include "kf_batch.cuh"
 #include "kf_common.cuh"
 #include "kf_internal.h"
 
@@ -35,6 +36,24 @@ __global__ void __launch_bounds__(256) k_pool8(const T *__restrict__ X, long xpi
   for (int r = r0; r < r1; ++r)
     for (int c = c0; c < c1; ++c) s += in_f32(__ldg(X + (long)r * xpitch + c));
   out[(long)y * w + x] = vs * s / (float)((r1 - r0) * (c1 - c0));
+}
+
+// the same for frame f of a call's frame table (the frame pointer is read on
+// the device, so a captured launch serves later calls with other frames)
+__global__ void __launch_bounds__(256) k_pool8_tab(const FrameDev *__restrict__ fr, int f,
+                                                   float *__restrict__ out) {
+  const FrameDev &F = fr[f];
+  const int H = F.H, W = F.W, h = (H + 7) / 8, w = (W + 7) / 8;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= w || y >= h) return;
+  const int r0 = 8 * y, c0 = 8 * x, r1 = min(r0 + 8, H), c1 = min(c0 + 8, W);
+  const long xpitch = F.xpitch;
+  float s = 0.f;
+  with_input_type(F.X, F.dtype, [&](auto Xt) {
+    for (int r = r0; r < r1; ++r)
+      for (int c = c0; c < c1; ++c) s += in_f32(__ldg(Xt + (long)r * xpitch + c));
+  });
+  out[(long)y * w + x] = F.vscale * s / (float)((r1 - r0) * (c1 - c0));
 }
 
 // ---------------------------------------------------------------------------
@@ -268,6 +287,80 @@ __global__ void k_labels(const Blob *__restrict__ b, long n, float thr, const lo
   lab[loff[r.frame] + ((long)r.scale * th + r.y / 64) * tw + r.x / 64] = 1;
 }
 
+// ---------------------------------------------------------------------------
+// gating
+// ---------------------------------------------------------------------------
+// act[ty][tx] = 1 if a logit of scale s < S of the 3 x 3 tile neighbourhood exceeds zthr
+__global__ void k_gate_tiles(const float *__restrict__ z, int S, int th, int tw, float zthr,
+                             unsigned char *__restrict__ act) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= th * tw) return;
+  const int ty = i / tw, tx = i % tw;
+  unsigned char a = 0;
+  for (int s = 0; s < S && !a; ++s)
+    for (int yy = max(ty - 1, 0); yy <= min(ty + 1, th - 1) && !a; ++yy)
+      for (int xx = max(tx - 1, 0); xx <= min(tx + 1, tw - 1); ++xx)
+        if (z[((long)s * th + yy) * tw + xx] > zthr) {
+          a = 1;
+          break;
+        }
+  act[i] = a;
+}
+
+// position in it.fl of the frame holding item `item` (binary search; one thread)
+__device__ __forceinline__ int find_frame(const Items &it, int item) {
+  int lo = 0, hi = it.n;  // pre[lo] <= item < pre[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(it.pre + mid) <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// any active 64 x 64 tile in the pixel rectangle [x0, x1) x [y0, y1) of frame F
+__device__ __forceinline__ bool any_active(const FrameDev &F, const unsigned char *act, int x0, int x1, int y0,
+                                           int y1) {
+  const int tw = (F.W + 63) / 64, th = (F.H + 63) / 64;
+  x0 = max(x0, 0), y0 = max(y0, 0), x1 = min(x1, F.W), y1 = min(y1, F.H);
+  if (x0 >= x1 || y0 >= y1) return false;
+  const unsigned char *a = act + F.aoff;
+  for (int ty = y0 / 64; ty <= (y1 - 1) / 64 && ty < th; ++ty)
+    for (int tx = x0 / 64; tx <= (x1 - 1) / 64 && tx < tw; ++tx)
+      if (a[ty * tw + tx]) return true;
+  return false;
+}
+
+// Items of a column pass (tiles of tw x th interior pixels, tile (tx, ty) =
+// item ty ntx + tx) whose interior overlaps an active tile
+__global__ void k_sel_tiles(const FrameDev *__restrict__ fr, Items full, const unsigned char *__restrict__ act,
+                            int tw, int th, int2 *__restrict__ sel, int *__restrict__ count) {
+  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= full.total) return;
+  const int k = find_frame(full, item);
+  const FrameDev &F = fr[__ldg(full.fl + k)];
+  const int local = item - __ldg(full.pre + k);
+  const int ntx = (F.W + tw - 1) / tw;
+  const int x0 = (local % ntx) * tw, y0 = (local / ntx) * th;
+  if (any_active(F, act, x0, x0 + tw, y0, y0 + th)) sel[atomicAdd(count, 1)] = make_int2(k, local);
+}
+
+// Items of the FIR row pass ((row, segment of rseg pixels) = item row nxs + seg;
+// rows H and H+1: the U-only edge rows, always kept): a row is needed if an
+// active tile lies within `reach` rows of it in the segment's columns +- 64
+__global__ void k_sel_rows(const FrameDev *__restrict__ fr, Items full, const unsigned char *__restrict__ act,
+                           int rseg, int reach, int2 *__restrict__ sel, int *__restrict__ count) {
+  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= full.total) return;
+  const int k = find_frame(full, item);
+  const FrameDev &F = fr[__ldg(full.fl + k)];
+  const int local = item - __ldg(full.pre + k);
+  const int nxs = (F.W + rseg - 1) / rseg;
+  const int xs = (local % nxs) * rseg, y = local / nxs;
+  if (y >= F.H || any_active(F, act, xs - 64, xs + rseg + 64, y - reach, y + reach + 1))
+    sel[atomicAdd(count, 1)] = make_int2(k, local);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -381,6 +474,31 @@ int net_adam(float *master, float *m, float *v, const float *g, int step, float 
 
 int net_to_bf16(const float *x, __nv_bfloat16 *y, cudaStream_t st) {
   k_to_bf16<<<(NET_NPARAM + 255) / 256, 256, 0, st>>>(x, NET_NPARAM, y);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int net_pool_table(const FrameDev *fr, int f, int H, int W, float *out, cudaStream_t st) {
+  const int h = (H + 7) / 8, w = (W + 7) / 8;
+  k_pool8_tab<<<dim3((w + 255) / 256, h), 256, 0, st>>>(fr, f, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int gate_tiles(const float *z, int S, int th, int tw, float zthr, unsigned char *act, cudaStream_t st) {
+  k_gate_tiles<<<(th * tw + 255) / 256, 256, 0, st>>>(z, S, th, tw, zthr, act);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int gate_select_tiles(const FrameDev *fr, const Items &full, const unsigned char *act, int tw, int th, int2 *sel,
+                      int *count, cudaStream_t st) {
+  if (full.total > 0)
+    k_sel_tiles<<<(full.total + 255) / 256, 256, 0, st>>>(fr, full, act, tw, th, sel, count);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int gate_select_rows(const FrameDev *fr, const Items &full, const unsigned char *act, int rseg, int reach,
+                     int2 *sel, int *count, cudaStream_t st) {
+  if (full.total > 0)
+    k_sel_rows<<<(full.total + 255) / 256, 256, 0, st>>>(fr, full, act, rseg, reach, sel, count);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

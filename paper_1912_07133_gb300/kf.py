@@ -80,7 +80,8 @@ class kf_bank_opts(ctypes.Structure):
                 ("threshold", ctypes.c_double), ("fir_kmax", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("responses", ctypes.c_void_p),
                 ("schedule", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int64 * 3)]
+                ("gate", ctypes.c_int32), ("gate_threshold", ctypes.c_float),
+                ("reserved", ctypes.c_int64 * 2)]
 
 
 class kf_blob(ctypes.Structure):
@@ -393,7 +394,8 @@ class Bank:
 
     def run(self, frames, scales, ftype=KF_IIR_REPEATED_POLE, order=4, threshold=0.05,
             neighbourhood=KF_NEIGH_ALL_SCALES, responses=None, fir_kmax=96, profile=False,
-            storage=KF_DTYPE_F32, value_scales=None, schedule=KF_SCHED_BATCHED, graph=False):
+            storage=KF_DTYPE_F32, value_scales=None, schedule=KF_SCHED_BATCHED, graph=False, gate=False,
+            gate_threshold=None):
         o = kf_bank_opts_default()
         o.threshold = float(threshold)
         o.profile = 1 if profile else 0
@@ -402,6 +404,9 @@ class Bank:
         o.storage = storage
         o.schedule = schedule
         o.graph = 1 if graph else 0
+        o.gate = 1 if gate else 0
+        if gate_threshold is not None:
+            o.gate_threshold = float(gate_threshold)
         if responses is not None:
             import torch
 
