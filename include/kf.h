@@ -65,6 +65,10 @@ extern "C" {
 
 #define KF_BOUNDARY_HOLD 0 /* frame edges held to +-infinity (Appendix, A32)     */
 
+#define KF_GATE_OFF 0        /* no proposal gating                               */
+#define KF_GATE_DILATED 1    /* marked tiles and their 8 neighbours              */
+#define KF_GATE_TILES 2      /* marked tiles only                                */
+
 #define KF_SCHED_BATCHED 0   /* one persistent launch per pass for all frames   */
 #define KF_SCHED_PER_FRAME 1 /* every pass launched once per frame              */
 
@@ -142,11 +146,13 @@ typedef struct {
                             storage, threshold, neighbourhood, schedule,
                             frame count and each frame's width and height.
                             Ignored when profile = 1.                        */
-  int32_t gate;          /* 1: proposal gating (needs kf_proposal_set_weights,
-                            <= 8 scales, the batched schedule).  Per frame the
-                            proposal network marks 64 x 64 tiles whose logit
-                            of some scale exceeds logit(gate_threshold) in the
-                            tile or its 8 neighbours; only column-pass tiles
+  int32_t gate;          /* KF_GATE_*: proposal gating (needs
+                            kf_proposal_set_weights, <= 8 scales, the batched
+                            schedule).  Per frame the proposal network marks
+                            64 x 64 tiles whose logit of some scale exceeds
+                            logit(gate_threshold) in the tile
+                            (KF_GATE_TILES) or in the tile or one of its 8
+                            neighbours (KF_GATE_DILATED); only column-pass tiles
                             overlapping marked tiles run (all scales: the
                             extremum over scales stays exact), and for the FIR
                             bank only the row-pass rows they read.  Every blob

@@ -456,7 +456,9 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   if (kmax_opt > KF_MAX_FIR_K) return fail(ctx, KF_EINVAL, "fir_kmax must be <= %d", KF_MAX_FIR_K);
   if (opts.schedule != KF_SCHED_BATCHED && opts.schedule != KF_SCHED_PER_FRAME)
     return fail(ctx, KF_EINVAL, "unknown schedule %d", opts.schedule);
-  const bool gate = opts.gate != 0;
+  const bool gate = opts.gate != KF_GATE_OFF;
+  if (opts.gate != KF_GATE_OFF && opts.gate != KF_GATE_DILATED && opts.gate != KF_GATE_TILES)
+    return fail(ctx, KF_EINVAL, "unknown gate mode %d", opts.gate);
   if (gate) {
     if (!ctx->net_ready) return fail(ctx, KF_EINVAL, "gating needs proposal weights (kf_proposal_set_weights)");
     if (nscales > KF_NET_CHANNELS) return fail(ctx, KF_EINVAL, "gating covers at most %d scales", KF_NET_CHANNELS);
@@ -646,7 +648,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
       if (kf::net_pool_table(plan.fr, f, H, W, ctx->g_pooled + g_poff[f], st) ||
           kf::net_forward(ctx->g_pooled + g_poff[f], 1, ph, pw, ctx->net_wb, ctx->net_work, ctx->g_logits + g_zoff[f],
                           st) ||
-          kf::gate_tiles(ctx->g_logits + g_zoff[f], nscales, th, tw, zthr, ctx->g_act + fd[f].aoff, st))
+          kf::gate_tiles(ctx->g_logits + g_zoff[f], nscales, th, tw, zthr, opts.gate == KF_GATE_DILATED ? 1 : 0,
+                         ctx->g_act + fd[f].aoff, st))
         return cuda_fail(ctx, cudaGetLastError(), "gate");
     }
     cudaError_t ee;

@@ -63,6 +63,20 @@ __device__ __forceinline__ int item_frame(const Items &it, int item, int k, int 
   return k;
 }
 
+// Gated calls: any active 64 x 64 tile in the pixel rectangle [x0, x1) x
+// [y0, y1) of frame F (act: the call's active-tile maps)
+__device__ __forceinline__ bool any_active(const FrameDev &F, const unsigned char *act, int x0, int x1, int y0,
+                                           int y1) {
+  const int tw = (F.W + 63) / 64, th = (F.H + 63) / 64;
+  x0 = max(x0, 0), y0 = max(y0, 0), x1 = min(x1, F.W), y1 = min(y1, F.H);
+  if (x0 >= x1 || y0 >= y1) return false;
+  const unsigned char *a = act + F.aoff;
+  for (int ty = y0 / 64; ty <= (y1 - 1) / 64 && ty < th; ++ty)
+    for (int tx = x0 / 64; tx <= (x1 - 1) / 64 && tx < tw; ++tx)
+      if (a[ty * tw + tx]) return true;
+  return false;
+}
+
 // Heavy kernels (near their register limit) keep the current item's frame
 // record in shared memory: the compiler may otherwise re-load its fields from
 // global memory at every use.  Thread 0 copies it; the caller synchronises

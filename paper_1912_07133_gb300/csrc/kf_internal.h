@@ -109,7 +109,8 @@ int net_labels(const Blob *b, long n, float thr, const long *loff, const int *lt
 // gating: active-tile map of one frame from its logits; selection of the
 // items of a column pass (interior tiles tw x th) or of the FIR row pass
 int net_pool_table(const FrameDev *fr, int f, int H, int W, float *out, cudaStream_t st);
-int gate_tiles(const float *z, int S, int th, int tw, float zthr, unsigned char *act, cudaStream_t st);
+int gate_tiles(const float *z, int S, int th, int tw, float zthr, int dilate, unsigned char *act,
+               cudaStream_t st);
 int gate_select_tiles(const FrameDev *fr, const Items &full, const unsigned char *act, int tw, int th, int2 *sel,
                       int *count, cudaStream_t st);
 int gate_select_rows(const FrameDev *fr, const Items &full, const unsigned char *act, int rseg, int reach,

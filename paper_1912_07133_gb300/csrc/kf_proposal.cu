@@ -290,16 +290,17 @@ __global__ void k_labels(const Blob *__restrict__ b, long n, float thr, const lo
 // ---------------------------------------------------------------------------
 // gating
 // ---------------------------------------------------------------------------
-// act[ty][tx] = 1 if a logit of scale s < S of the 3 x 3 tile neighbourhood exceeds zthr
-__global__ void k_gate_tiles(const float *__restrict__ z, int S, int th, int tw, float zthr,
+// act[ty][tx] = 1 if a logit of scale s < S exceeds zthr in the tile (dil = 0)
+// or in its 3 x 3 tile neighbourhood (dil = 1)
+__global__ void k_gate_tiles(const float *__restrict__ z, int S, int th, int tw, float zthr, int dil,
                              unsigned char *__restrict__ act) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= th * tw) return;
   const int ty = i / tw, tx = i % tw;
   unsigned char a = 0;
   for (int s = 0; s < S && !a; ++s)
-    for (int yy = max(ty - 1, 0); yy <= min(ty + 1, th - 1) && !a; ++yy)
-      for (int xx = max(tx - 1, 0); xx <= min(tx + 1, tw - 1); ++xx)
+    for (int yy = max(ty - dil, 0); yy <= min(ty + dil, th - 1) && !a; ++yy)
+      for (int xx = max(tx - dil, 0); xx <= min(tx + dil, tw - 1); ++xx)
         if (z[((long)s * th + yy) * tw + xx] > zthr) {
           a = 1;
           break;
@@ -316,19 +317,6 @@ __device__ __forceinline__ int find_frame(const Items &it, int item) {
     else hi = mid;
   }
   return lo;
-}
-
-// any active 64 x 64 tile in the pixel rectangle [x0, x1) x [y0, y1) of frame F
-__device__ __forceinline__ bool any_active(const FrameDev &F, const unsigned char *act, int x0, int x1, int y0,
-                                           int y1) {
-  const int tw = (F.W + 63) / 64, th = (F.H + 63) / 64;
-  x0 = max(x0, 0), y0 = max(y0, 0), x1 = min(x1, F.W), y1 = min(y1, F.H);
-  if (x0 >= x1 || y0 >= y1) return false;
-  const unsigned char *a = act + F.aoff;
-  for (int ty = y0 / 64; ty <= (y1 - 1) / 64 && ty < th; ++ty)
-    for (int tx = x0 / 64; tx <= (x1 - 1) / 64 && tx < tw; ++tx)
-      if (a[ty * tw + tx]) return true;
-  return false;
 }
 
 // Items of a column pass (tiles of tw x th interior pixels, tile (tx, ty) =
@@ -483,8 +471,9 @@ int net_pool_table(const FrameDev *fr, int f, int H, int W, float *out, cudaStre
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int gate_tiles(const float *z, int S, int th, int tw, float zthr, unsigned char *act, cudaStream_t st) {
-  k_gate_tiles<<<(th * tw + 255) / 256, 256, 0, st>>>(z, S, th, tw, zthr, act);
+int gate_tiles(const float *z, int S, int th, int tw, float zthr, int dilate, unsigned char *act,
+               cudaStream_t st) {
+  k_gate_tiles<<<(th * tw + 255) / 256, 256, 0, st>>>(z, S, th, tw, zthr, dilate, act);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -41,6 +41,7 @@ KF_RESP_HESSIAN = 1
 KF_BOUNDARY_HOLD = 0
 KF_NEIGH_ALL_SCALES = 0
 KF_NEIGH_ADJACENT = 1
+KF_GATE_OFF, KF_GATE_DILATED, KF_GATE_TILES = 0, 1, 2
 KF_SCHED_BATCHED = 0
 KF_SCHED_PER_FRAME = 1
 KF_MAX_SCALES = 16
@@ -404,7 +405,7 @@ class Bank:
         o.storage = storage
         o.schedule = schedule
         o.graph = 1 if graph else 0
-        o.gate = 1 if gate else 0
+        o.gate = int(gate) if not isinstance(gate, bool) else (KF_GATE_DILATED if gate else KF_GATE_OFF)
         if gate_threshold is not None:
             o.gate_threshold = float(gate_threshold)
         if responses is not None:

@@ -132,6 +132,62 @@ def clustered_frame(seed: int = 4, H: int = 6144, W: int = 6144, tile: int = 64,
     return img.astype(np.float16)
 
 
+def clustered_frame_device(seed: int = 4, H: int = 6144, W: int = 6144, tile: int = 64,
+                           active_fraction: float = 0.05, blobs_per_tile: float = 2.0, device: str = "cuda"):
+    """The clustered-frame recipe generated on the GPU (torch), for the many
+    large frames of proposal training and of the gated benchmark: 1/f
+    background (std 0.1, DC removed) from device Gaussian noise, blob clusters
+    covering about ``active_fraction`` of the 64 x 64 tiles (the same cluster
+    walk as :func:`clustered_frame`), Poisson(``blobs_per_tile``) bright or
+    dark elliptical blobs per active tile, radii 2 to tile/2, rendered within
+    their tile.  Returns an (H, W) float16 CUDA tensor.  Same recipe as
+    :func:`clustered_frame`, other random streams: the frames differ."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    white = torch.randn((H, W), generator=g, device=device, dtype=torch.float32)
+    F = torch.fft.rfft2(white)
+    fy = torch.fft.fftfreq(H, device=device)[:, None]
+    fx = torch.fft.rfftfreq(W, device=device)[None, :]
+    f = torch.sqrt(fx * fx + fy * fy)
+    f[0, 0] = 1.0
+    F = F / f
+    F[0, 0] = 0.0
+    img = torch.fft.irfft2(F, s=(H, W))
+    img *= 0.1 / img.std()
+    th, tw = H // tile, W // tile
+    n_active = max(1, int(round(active_fraction * th * tw)))
+    active = np.zeros((th, tw), bool)
+    while active.sum() < n_active:
+        cy, cx = rng.integers(th), rng.integers(tw)
+        for _ in range(int(rng.integers(1, 7))):
+            active[np.clip(cy, 0, th - 1), np.clip(cx, 0, tw - 1)] = True
+            cy += int(rng.integers(-1, 2))
+            cx += int(rng.integers(-1, 2))
+    par = []
+    for ty, tx in zip(*np.nonzero(active)):
+        for _ in range(rng.poisson(blobs_per_tile)):
+            ra = rng.uniform(2.0, tile / 2)
+            amp = rng.uniform(0.5, 1.0) * (-1.0 if rng.uniform() < 0.5 else 1.0)
+            par.append((tx * tile, ty * tile, rng.uniform(0, tile), rng.uniform(0, tile), ra,
+                        ra * rng.uniform(0.5, 1.0), rng.uniform(0, math.pi), amp))
+    if par:
+        P = torch.tensor(par, device=device, dtype=torch.float32)
+        x0, y0, cx, cy, ra, rb, ang, amp = [P[:, i, None, None] for i in range(8)]
+        yy, xx = torch.meshgrid(torch.arange(tile, device=device, dtype=torch.float32),
+                                torch.arange(tile, device=device, dtype=torch.float32), indexing="ij")
+        dx, dy = xx[None] - cx, yy[None] - cy
+        u = dx * torch.cos(ang) + dy * torch.sin(ang)
+        v = -dx * torch.sin(ang) + dy * torch.cos(ang)
+        val = amp * torch.exp(-2.0 * (u * u / (ra * ra) + v * v / (rb * rb)))
+        rows = (y0.long() + yy.long()[None]).reshape(-1)
+        cols = (x0.long() + xx.long()[None]).reshape(-1)
+        img.index_put_((rows, cols), val.reshape(-1), accumulate=True)
+    return img.to(torch.float16)
+
+
 @dataclass
 class Workload:
     name: str

@@ -47,8 +47,8 @@ def frames_for_gating(seed=40):
     return out
 
 
-def expected_active(frame, c):
-    """Dilated active-tile map from the hand-set network (host arithmetic)."""
+def expected_active(frame, c, dilate=True):
+    """Active-tile map from the hand-set network (host arithmetic)."""
     H, W = frame.shape
     p = np.zeros(((H + 7) // 8, (W + 7) // 8))
     for y in range(p.shape[0]):
@@ -58,6 +58,8 @@ def expected_active(frame, c):
     z = np.array([[np.maximum(p[8 * ty:8 * ty + 8, 8 * tx:8 * tx + 8], 0).max() - c for tx in range(tw)]
                   for ty in range(th)])
     a = z > 0.0  # gate_threshold 0.5
+    if not dilate:
+        return a
     d = np.zeros_like(a)
     for ty in range(th):
         for tx in range(tw):
@@ -78,6 +80,7 @@ def selected(frame, act, rows):
 
 
 def run(frames, ftype, order, gate, c=0.5, graph=False, calls=1):
+    """gate: False, True (marked tiles and neighbours) or a KF_GATE_* mode."""
     import torch
 
     from paper_1912_07133_gb300 import kf
@@ -93,15 +96,17 @@ def run(frames, ftype, order, gate, c=0.5, graph=False, calls=1):
     return R.cpu().numpy(), b
 
 
+@pytest.mark.parametrize("dilated", [True, False])
 @pytest.mark.parametrize("ftype,order,rows", [(D, 4, 64), (E, 2, 64), (C, 1, 126)])
-def test_gated_blobs_are_the_full_blobs_of_the_selected_tiles(ftype, order, rows):
+def test_gated_blobs_are_the_full_blobs_of_the_selected_tiles(ftype, order, rows, dilated):
+    from paper_1912_07133_gb300 import kf
     frames = frames_for_gating()
     Rf, bf = run(frames, ftype, order, gate=False)
-    Rg, bg = run(frames, ftype, order, gate=True)
+    Rg, bg = run(frames, ftype, order, gate=kf.KF_GATE_DILATED if dilated else kf.KF_GATE_TILES)
     off = 0
     n_sel = n_all = 0
     for i, f in enumerate(frames):
-        act = expected_active(f, 0.5)
+        act = expected_active(f, 0.5, dilated)
         assert 0 < act.sum() < act.size
         sel = selected(f, act, rows)
         k = len(SCALES) * f.size
