@@ -95,6 +95,73 @@ __global__ void __launch_bounds__(CT * CT) k_conv_fwd(const float *__restrict__ 
   }
 }
 
+// The same convolution, two pixels per thread (rows y and y + 16 of a 16 x 32
+// tile) with the weights in shared memory as [ci][k][co]: per input tap a
+// thread reads its two inputs and the CO weights as float4 (broadcast across
+// the warp) for 2 CO fused multiply-adds.  Dynamic shared memory: the input
+// tile (CI x 34 x 19) and the weights.
+constexpr int CT2 = 2 * CT;  // tile rows
+template <int CI, int CO>
+constexpr size_t conv2_smem() {
+  return sizeof(float) * ((size_t)CI * (CT2 + 2) * (CT + 3) + (size_t)CI * 9 * CO);
+}
+
+template <int CI, int CO, bool RELU>
+__global__ void __launch_bounds__(CT * CT) k_conv_fwd2(const float *__restrict__ in,
+                                                       const __nv_bfloat16 *__restrict__ Wb,
+                                                       const __nv_bfloat16 *__restrict__ bb, float *__restrict__ out,
+                                                       int h, int w) {
+  static_assert(CO % 4 == 0, "float4 weight loads");
+  extern __shared__ __align__(16) float sm2[];
+  float *s_w = sm2;                                   // [CI * 9][CO]
+  float(*s_in)[CT2 + 2][CT + 3] = reinterpret_cast<float(*)[CT2 + 2][CT + 3]>(sm2 + CI * 9 * CO);
+  const int n = blockIdx.z, x0 = blockIdx.x * CT, y0 = blockIdx.y * CT2, tid = threadIdx.x;
+  const long plane = (long)h * w;
+  const float *inn = in + (long)n * CI * plane;
+  for (int i = tid; i < CO * CI * 9; i += CT * CT) {
+    const int co = i / (CI * 9), r = i % (CI * 9);  // global layout W[co][ci][k]
+    s_w[r * CO + co] = __bfloat162float(Wb[i]);
+  }
+  for (int i = tid; i < CI * (CT2 + 2) * (CT + 2); i += CT * CT) {
+    const int ci = i / ((CT2 + 2) * (CT + 2)), r = (i / (CT + 2)) % (CT2 + 2), c = i % (CT + 2);
+    const int y = y0 + r - 1, x = x0 + c - 1;
+    s_in[ci][r][c] = (y >= 0 && y < h && x >= 0 && x < w) ? __ldg(inn + ci * plane + (long)y * w + x) : 0.f;
+  }
+  __syncthreads();
+  const int tx = tid % CT, ty = tid / CT, x = x0 + tx;
+  float a0[CO], a1[CO];
+#pragma unroll
+  for (int co = 0; co < CO; ++co) a0[co] = a1[co] = __bfloat162float(bb[co]);
+#pragma unroll 1
+  for (int ci = 0; ci < CI; ++ci)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float v0 = s_in[ci][ty + k / 3][tx + k % 3];
+      const float v1 = s_in[ci][ty + CT + k / 3][tx + k % 3];
+      const float4 *wv = reinterpret_cast<const float4 *>(s_w + (ci * 9 + k) * CO);
+#pragma unroll
+      for (int q = 0; q < CO / 4; ++q) {
+        const float4 wq = wv[q];
+        a0[4 * q + 0] = fmaf(wq.x, v0, a0[4 * q + 0]);
+        a0[4 * q + 1] = fmaf(wq.y, v0, a0[4 * q + 1]);
+        a0[4 * q + 2] = fmaf(wq.z, v0, a0[4 * q + 2]);
+        a0[4 * q + 3] = fmaf(wq.w, v0, a0[4 * q + 3]);
+        a1[4 * q + 0] = fmaf(wq.x, v1, a1[4 * q + 0]);
+        a1[4 * q + 1] = fmaf(wq.y, v1, a1[4 * q + 1]);
+        a1[4 * q + 2] = fmaf(wq.z, v1, a1[4 * q + 2]);
+        a1[4 * q + 3] = fmaf(wq.w, v1, a1[4 * q + 3]);
+      }
+    }
+  if (x >= w) return;
+  float *o = out + (long)n * CO * plane + x;
+  const int ya = y0 + ty, yb = y0 + ty + CT;
+#pragma unroll
+  for (int co = 0; co < CO; ++co) {
+    if (ya < h) o[co * plane + (long)ya * w] = RELU ? fmaxf(a0[co], 0.f) : a0[co];
+    if (yb < h) o[co * plane + (long)yb * w] = RELU ? fmaxf(a1[co], 0.f) : a1[co];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // tile max: z[n][c][ty][tx] = max over the 8 x 8 block (first maximum in
 // row-major order; its flat index y w + x is kept for the backward pass)
@@ -413,10 +480,18 @@ int net_pool(const void *X, int dtype, float vs, long xpitch, int H, int W, floa
 int net_forward(const float *x, int N, int h, int w, const __nv_bfloat16 *wb, float *work, float *z_out,
                 cudaStream_t st) {
   Carve c = carve(work, N, h, w);
-  const dim3 g = conv_grid(N, h, w);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv_fwd2<16, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)conv2_smem<16, 16>());
+    cudaFuncSetAttribute(k_conv_fwd2<16, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)conv2_smem<16, 8>());
+    attr = true;
+  }
+  const dim3 g = conv_grid(N, h, w), g2((w + CT - 1) / CT, (h + CT2 - 1) / CT2, N);
   k_conv_fwd<1, 16, true><<<g, CT * CT, 0, st>>>(x, wb + W1, wb + B1, c.x1, h, w);
-  k_conv_fwd<16, 16, true><<<g, CT * CT, 0, st>>>(c.x1, wb + W2, wb + B2, c.a2, h, w);
-  k_conv_fwd<16, 8, false><<<g, CT * CT, 0, st>>>(c.a2, wb + W3, wb + B3, c.o3, h, w);
+  k_conv_fwd2<16, 16, true><<<g2, CT * CT, conv2_smem<16, 16>(), st>>>(c.x1, wb + W2, wb + B2, c.a2, h, w);
+  k_conv_fwd2<16, 8, false><<<g2, CT * CT, conv2_smem<16, 8>(), st>>>(c.a2, wb + W3, wb + B3, c.o3, h, w);
   const int th = (h + 7) / 8, tw = (w + 7) / 8;
   const long T = (long)N * 8 * th * tw;
   k_tilemax<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(c.o3, 8, h, w, th, tw, T, z_out ? z_out : c.z, c.arg);
