@@ -61,7 +61,13 @@ extern "C" {
 #define KF_DTYPE_U16 3  /* unsigned 16-bit counts (input only)                 */
 
 #define KF_RESP_LAPLACIAN 0 /* R_L = -sigma^2 (D20 + D02)                        */
-#define KF_RESP_HESSIAN 1   /* R_H = sigma^4 (D20 D02 - D11^2), eq (26)          */
+#define KF_RESP_HESSIAN 1   /* R_H = sigma^4 (D20 D02 - D11^2), eq (26); bright
+                               maxima only.  R_H and Threshold #2 run the
+                               derivative bank: each needed derivative (D20,
+                               D02, D11; D10, D01 for eq 27) is blurred as its
+                               own channel (Table I taps first), then one
+                               kernel forms R and detects.  Not with gating
+                               or graph replay (calls run eagerly).          */
 
 #define KF_BOUNDARY_HOLD 0 /* frame edges held to +-infinity (Appendix, A32)     */
 
@@ -160,7 +166,11 @@ typedef struct {
                             tiles are not found, and responses there are not
                             written.                                          */
   float gate_threshold;  /* probability threshold of the gate, in (0, 1)     */
-  int64_t reserved[2];
+  float offset_limit;    /* Threshold #2 (Sec. 5): > 0 keeps only candidates
+                            whose eq (27) offset sqrt(dx^2 + dy^2) is at most
+                            this many pixels; 0: off                          */
+  int32_t reserved0;
+  int64_t reserved[1];
 } kf_bank_opts;
 
 /* One detection (Threshold #1 extremum). */
@@ -168,6 +178,8 @@ typedef struct {
   int32_t frame, x, y, scale;
   int32_t polarity;  /* +1 bright (maximum of R), -1 dark (minimum of R_L) */
   float response;    /* R at (x, y, scale) */
+  float dx, dy;      /* sub-pixel offset of the extremum by eq (27) (the
+                        derivative bank: R_H or offset_limit > 0; else 0) */
 } kf_blob;
 
 /* Per-kernel device time of the last profiled kf_filter_bank call. */

@@ -105,6 +105,8 @@ struct kf_ctx {
   size_t g_sel_n[2] = {0, 0};
   int *g_count = nullptr;
   size_t g_count_n = 0;
+  float *ch_buf = nullptr;  // derivative bank: channel planes sigma^2 D (3 or 5 x responses layout)
+  size_t ch_floats = 0;
 };
 
 namespace {
@@ -372,6 +374,7 @@ void kf_destroy(kf_ctx *ctx) {
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   drop_graphs(ctx);
   cudaFree(ctx->d_table);
+  cudaFree(ctx->ch_buf);
   for (void *q : {(void *)ctx->g_pooled, (void *)ctx->g_logits, (void *)ctx->g_act, (void *)ctx->g_sel[0],
                   (void *)ctx->g_sel[1], (void *)ctx->g_count})
     cudaFree(q);
@@ -444,8 +447,14 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
       return fail(ctx, KF_EINVAL, "scale %d must be > 0", s);
   int rc = check_type_order(ctx, type, order);
   if (rc) return rc;
-  if (opts.response != KF_RESP_LAPLACIAN)
-    return fail(ctx, KF_EINVAL, "only the Laplacian response is implemented");
+  if (opts.response != KF_RESP_LAPLACIAN && opts.response != KF_RESP_HESSIAN)
+    return fail(ctx, KF_EINVAL, "unknown response %d", opts.response);
+  if (!(opts.offset_limit >= 0.f) || !std::isfinite(opts.offset_limit))
+    return fail(ctx, KF_EINVAL, "offset_limit must be >= 0");
+  // the derivative bank: R_H, or Threshold #2 with its eq (27) offsets
+  const bool dbank = opts.response == KF_RESP_HESSIAN || opts.offset_limit > 0.f;
+  if (dbank && opts.gate != KF_GATE_OFF)
+    return fail(ctx, KF_EINVAL, "gating runs with the Laplacian response and no offset limit");
   if (opts.boundary != KF_BOUNDARY_HOLD) return fail(ctx, KF_EINVAL, "only the hold boundary is implemented");
   if (opts.neighbourhood != KF_NEIGH_ALL_SCALES && opts.neighbourhood != KF_NEIGH_ADJACENT)
     return fail(ctx, KF_EINVAL, "unknown neighbourhood %d", opts.neighbourhood);
@@ -505,6 +514,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     const kf_frame &fr = frames[f];
     kf::FrameDev &d = fd[f];
     d.aoff = aoff;
+    d.roff = roff;
     g_poff[f] = poff;
     g_zoff[f] = zoff;
     aoff += (long)((fr.height + 63) / 64) * ((fr.width + 63) / 64);
@@ -537,7 +547,9 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   };
   std::vector<int> pool;
   std::vector<L> ls;
+  constexpr int PASS_COMB = 99;  // the derivative bank's combine + detect launch
   auto items = [&](int pass, int f) {
+    if (pass == PASS_COMB) return kf::deriv_items(fd[f].H, fd[f].W);
     return iir ? kf::iir_items(pass, fd[f].H, fd[f].W, nscales, ctx->seg_len[type])
                : kf::fir_items(pass, fd[f].H, fd[f].W, nscales, opts.neighbourhood);
   };
@@ -583,6 +595,11 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
       }
     }
   }
+  if (dbank) {
+    std::vector<int> fl(nframes);
+    for (int f = 0; f < nframes; ++f) fl[f] = f;
+    fits &= add(PASS_COMB, fl, 0);
+  }
   if (!fits) return fail(ctx, KF_EINVAL, "too many work items in one call: split the batch");
   for (const L &l : ls)
     if (iir && l.pass == kf::PASS_ROW && l.nt == 0) return fail(ctx, KF_EINVAL, "frame too wide for the row pass");
@@ -609,7 +626,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     x.it.n = l.n;
     x.it.total = l.total;
     x.nt = l.nt;
-    plan.pass[l.pass].push_back(x);
+    if (l.pass == PASS_COMB) plan.comb = x;
+    else plan.pass[l.pass].push_back(x);
   }
   // ---- gating: buffers and the gated launches --------------------------------
   kf::Items full_det{}, full_row{};
@@ -695,7 +713,51 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   ctx->prof = kf::Prof{};
   ctx->prof.ev = nullptr;
   ctx->have_prof = true;
-  if (opts.graph && !opts.profile) {
+  if (opts.profile) {
+    const int need = 2 * 256;
+    while ((int)ctx->events.size() < need) {
+      cudaEvent_t ev;
+      if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventCreate");
+      ctx->events.push_back(ev);
+    }
+  }
+  if (dbank) {
+    // every needed derivative as its own channel (raw planes sigma^2 D), then
+    // R and the detector; the frame table's response pointers select the
+    // channel planes of each run (runs eagerly: one table per run)
+    const int chans_h[5] = {kf::CH_U, kf::CH_V, kf::CH_W, kf::CH_DX, kf::CH_DY};
+    const int nch = opts.offset_limit > 0.f ? 5 : 3;
+    const size_t per = (size_t)std::max(roff, 1L);
+    if ((rc = grow(ctx, &ctx->ch_buf, &ctx->ch_floats, per * nch, "derivative planes"))) return rc;
+    if (opts.profile) {
+      ctx->prof.ev = ctx->events.data();
+      ctx->prof.cap = 256;
+    }
+    a.prof = &ctx->prof;
+    if ((e = cudaMemsetAsync(ctx->status, 0, sizeof(kf::DevStatus), ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "reset status");
+    auto with_resp = [&](float *base) -> int {
+      for (int f = 0; f < nframes; ++f) fd[f].resp = base ? base + fd[f].roff : nullptr;
+      std::memcpy(table.data(), fd.data(), fd_bytes);
+      return upload_table(ctx, table.data(), table.size());
+    };
+    for (int c = 0; c < nch; ++c) {
+      if ((rc = with_resp(ctx->ch_buf + (size_t)c * per))) return rc;
+      a.chan = chans_h[c];
+      a.raw = 1;
+      const int lr = iir ? kf::launch_iir(plan, a, ctx->stream) : kf::launch_fir(plan, a, ctx->stream);
+      if (lr == -2) return fail(ctx, KF_EINVAL, "no kernel instance for order %d", order);
+      if (lr) return cuda_fail(ctx, cudaGetLastError(), "derivative channel launch");
+    }
+    if ((rc = with_resp(opts.responses))) return rc;
+    a.chan = kf::CH_LAP;
+    a.raw = 0;
+    const float *c20 = ctx->ch_buf, *c02 = ctx->ch_buf + per, *c11 = ctx->ch_buf + 2 * per;
+    const float *c10 = nch == 5 ? ctx->ch_buf + 3 * per : nullptr, *c01 = nch == 5 ? ctx->ch_buf + 4 * per : nullptr;
+    if (kf::launch_combine_detect(plan, plan.comb, a, opts.response == KF_RESP_HESSIAN, c20, c02, c11, c10, c01,
+                                  opts.offset_limit, ctx->stream))
+      return cuda_fail(ctx, cudaGetLastError(), "derivative bank detector");
+  } else if (opts.graph && !opts.profile) {
     const std::vector<long long> key = call_key(ctx, frames, nframes, scales, nscales, type, order, kmax_opt, opts);
     kf_ctx::Graph *g = nullptr;
     for (auto &x : ctx->graphs)
@@ -740,12 +802,6 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     }
   } else {
     if (opts.profile) {
-      const int need = 2 * 256;
-      while ((int)ctx->events.size() < need) {
-        cudaEvent_t ev;
-        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventCreate");
-        ctx->events.push_back(ev);
-      }
       ctx->prof.ev = ctx->events.data();
       ctx->prof.cap = 256;
     }

@@ -26,6 +26,7 @@ struct FrameDev {
   int dtype;       // IN_F32 / IN_F16 / IN_BF16 / IN_U16
   float vscale;    // input multiplier
   long aoff;       // gated calls: byte offset of the frame's active-tile map (64 x 64 tiles)
+  long roff;       // float offset of the frame's planes in response-layout buffers (S x H x W)
   int H, W;
   int nseg;        // IIR column segments
   int index;       // frame index in the call (blob records)

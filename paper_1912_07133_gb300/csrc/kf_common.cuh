@@ -17,6 +17,49 @@ constexpr int MAX_FIR_K = 160;   // largest colored-SG half-length
 
 enum { T_D = 0, T_E = 1, T_C = 2 };
 
+// Derivative channels of the row passes (Table I taps applied to the
+// edge-held frame before the blur): the Laplacian L = U + V of the fused path,
+// or one derivative of the derivative bank (R_H of eq 26, the eq 27 offsets).
+//   U = X[x+1] - 2X + X[x-1]   V = X[y+1] - 2X + X[y-1]
+//   W = (X[x+1,y+1] - X[x-1,y+1] - X[x+1,y-1] + X[x-1,y-1]) / 4
+//   DX = (X[x+1] - X[x-1]) / 2  DY = (X[y+1] - X[y-1]) / 2
+// Beyond the left/right edges the x-differences (U, W, DX) vanish and V, DY
+// keep their row-end value; beyond the top/bottom the y-differences (V, W, DY)
+// vanish and U, DX keep the value of the first/last row.  CH_ZERO: the edge
+// rows of the y-vanishing channels.
+enum { CH_LAP = 0, CH_U = 1, CH_V = 2, CH_W = 3, CH_DX = 4, CH_DY = 5, CH_ZERO = 6 };
+
+// the channel the U-only edge rows carry (the y-held part of the channel)
+__host__ __device__ __forceinline__ int edge_chan(int c) {
+  return (c == CH_LAP || c == CH_U) ? CH_U : (c == CH_DX ? CH_DX : CH_ZERO);
+}
+
+// channel c at column e (0 <= e < W) from rows y-1 (m), y (o), y+1 (p);
+// at(row, e) returns the element with e clamped into the row
+template <class AM, class AO, class AP>
+__device__ __forceinline__ float chan_at(int c, AM m, AO o, AP p, int e) {
+  switch (c) {
+    case CH_LAP: return (o(e + 1) - 2.f * o(e) + o(e - 1)) + (p(e) - 2.f * o(e) + m(e));
+    case CH_U: return o(e + 1) - 2.f * o(e) + o(e - 1);
+    case CH_V: return p(e) - 2.f * o(e) + m(e);
+    case CH_W: return 0.25f * ((p(e + 1) - p(e - 1)) - (m(e + 1) - m(e - 1)));
+    case CH_DX: return 0.5f * (o(e + 1) - o(e - 1));
+    case CH_DY: return 0.5f * (p(e) - m(e));
+    default: return 0.f;
+  }
+}
+
+// channel c beyond the row end at column e (e = 0: left, e = W - 1: right)
+template <class AM, class AO, class AP>
+__device__ __forceinline__ float chan_beyond(int c, AM m, AO o, AP p, int e) {
+  switch (c) {
+    case CH_LAP:
+    case CH_V: return p(e) - 2.f * o(e) + m(e);
+    case CH_DY: return 0.5f * (p(e) - m(e));
+    default: return 0.f;
+  }
+}
+
 // element types of input frames (same values as KF_DTYPE_*) and of the
 // one-sided planes between the row and column passes
 enum { IN_F32 = 0, IN_F16 = 1, IN_BF16 = 2, IN_U16 = 3 };
@@ -121,6 +164,7 @@ struct Coef {
 struct Blob {
   int32_t frame, x, y, scale, polarity;
   float response;
+  float dx, dy;  // eq (27) offset (derivative bank; 0 otherwise)
 };
 
 // Bounded device-side status word shared by the kernels of one call.

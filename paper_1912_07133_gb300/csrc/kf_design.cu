@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(256) k_design(int type, int order, const doubl
 int launch_design(int type, int order, const double *d_lambdas, int S, int fir_kmax, Coef *d_out,
                   double *d_work, int Nmax, cudaStream_t st) {
   k_design<<<S, 256, 0, st>>>(type, order, d_lambdas, fir_kmax, d_out, d_work, Nmax);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace kf

@@ -30,6 +30,11 @@ struct DetectArgs {
   int ld = 32;         // row stride of the response buffer (floats)
   int coff = 0;        // column of lane 0 inside a buffer row
   int srows = 0;       // rows per scale in the buffer (0: NR)
+  int raw = 0;         // 1: the buffer holds a derivative channel: write it, no detection
+  // derivative bank: sigma^2 D planes of the frame (S x H x W) for the eq (27)
+  // offsets of the candidates (d10/d01 null: no offsets), Threshold #2 limit
+  const float *d10 = nullptr, *d01 = nullptr, *d20 = nullptr, *d02 = nullptr, *d11 = nullptr;
+  float limit2 = 0.f;
 };
 
 constexpr int TILE_CANDS = 256;  // candidates staged per tile before one global reservation
@@ -53,6 +58,15 @@ static __device__ __forceinline__ void emit_blob(const DetectArgs &a, TileList &
   b.scale = s;
   b.polarity = pol;
   b.response = v;
+  b.dx = b.dy = 0.f;
+  if (a.d10) {  // eq (27): offset of the extremum of the local quadratic (sigma^2 factors cancel)
+    const long i = ((long)s * a.H + y) * a.W + x;
+    const float d10 = a.d10[i], d01 = a.d01[i], d20 = a.d20[i], d02 = a.d02[i], d11 = a.d11[i];
+    const float det = d20 * d02 - d11 * d11;
+    b.dx = (d01 * d11 - d02 * d10) / det;
+    b.dy = (d10 * d11 - d20 * d01) / det;
+    if (a.limit2 > 0.f && !(sqrtf(b.dx * b.dx + b.dy * b.dy) <= a.limit2)) return;  // Threshold #2
+  }
   const int slot = atomicAdd(&tl.n, 1);
   if (slot < TILE_CANDS) {
     tl.rec[slot] = b;
@@ -127,6 +141,7 @@ static __device__ void detect_tile(const float *buf, float *red, const DetectArg
         a.resp[s * plane + (long)y * a.W + x] = buf[(s * SR + i) * a.ld + a.coff + lane];
     }
   }
+  if (a.raw) return;  // a derivative channel: written, not detected (uniform over the block)
   float *mx = red, *mn = red + NP;
   unsigned char *amx = reinterpret_cast<unsigned char *>(red + 2 * NP);
   unsigned char *amn = amx + NP;

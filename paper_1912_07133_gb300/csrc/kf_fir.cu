@@ -124,7 +124,7 @@ __host__ __device__ __forceinline__ int row_halo(int kmax) { return (kmax + TB +
 __global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr, Items it,
                                                 const Coef *__restrict__ coef, int S, int kmax,
                                                 void *__restrict__ P, int st, long PWb, float *__restrict__ edge,
-                                                DevStatus *__restrict__ status) {
+                                                DevStatus *__restrict__ status, int chan) {
   extern __shared__ __align__(16) float sm[];
   const int tid = threadIdx.x;
   // L on [xs - G, xs + RSEG + G): the 8-tap blocks read up to TB elements past
@@ -159,6 +159,18 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr,
       auto ld = [&](const decltype(Xt) row, int e) { return vs * in_f32(__ldg(row + e)); };
       const float vlo = ld(rp, 0) - 2.f * ld(r0, 0) + ld(rm, 0);
       const float vhi = ld(rp, W - 1) - 2.f * ld(r0, W - 1) + ld(rm, W - 1);
+      if (chan != CH_LAP) {  // one derivative channel of the derivative bank
+        const int cin = EDGE ? edge_chan(chan) : chan;
+        auto am = [&](int e) { return ld(rm, min(max(e, 0), W - 1)); };
+        auto ao = [&](int e) { return ld(r0, min(max(e, 0), W - 1)); };
+        auto ap = [&](int e) { return ld(rp, min(max(e, 0), W - 1)); };
+        for (int j = tid; j < n; j += RNT) {
+          const int e = xs - G + j;
+          sL[pad20(j)] = e < 0 ? chan_beyond(cin, am, ao, ap, 0)
+                               : (e >= W ? chan_beyond(cin, am, ao, ap, W - 1) : chan_at(cin, am, ao, ap, e));
+        }
+        return;
+      }
       // 4 elements (20 loads, clamped into the row) per thread in flight
       for (int j0 = tid; j0 < n; j0 += 4 * RNT) {
         float cm[4], c0[4], cp[4], um[4], up[4];
@@ -258,6 +270,7 @@ __global__ void __launch_bounds__(CNT) k_colfir(const FrameDev *__restrict__ fr,
   float *buf = sm + (long)NIN * 32;             // [S][CROWS][32]
   float *red = buf + (long)S * CROWS * 32;
   float *sh = red + CROWS * 32 * 2 + CROWS * 32 * 2 / 4;
+  const float sgn = da.raw ? 1.f : -1.f;  // R_L = -(column blur); raw channel: +
   __shared__ FrameDev s_fr;
   int k = 0;
   const int nitems = items_total(it);
@@ -290,7 +303,7 @@ __global__ void __launch_bounds__(CNT) k_colfir(const FrameDev *__restrict__ fr,
       float acc[NOUT];
       fir_block(sh, K, [&](int t) { return col[t * 32]; }, acc);
 #pragma unroll
-      for (int j = 0; j < NOUT; ++j) buf[((long)s * CROWS + NOUT * warp + j) * 32 + lane] = -acc[j];
+      for (int j = 0; j < NOUT; ++j) buf[((long)s * CROWS + NOUT * warp + j) * 32 + lane] = sgn * acc[j];
     }
     __syncthreads();
     DetectArgs a = da;
@@ -358,6 +371,7 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
   }
   __syncthreads();
   __shared__ FrameDev s_fr;
+  const float sgn = da.raw ? 1.f : -1.f;
   uint32_t ph0 = 0u, ph1 = 0u;  // phase to wait for, per barrier
   int k = 0;
   const int nitems = items_total(it);
@@ -459,7 +473,7 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
       for (int j = 0; j < NOUT; ++j) {
         const int i = NOUT * warp + j, y = r0 + i;
         if (!xin || y < 0 || y >= H) continue;
-        const float v = -acc[j];  // R_L = -sigma^2 (D20 + D02); planes carry sigma^2
+        const float v = sgn * acc[j];  // R_L = -sigma^2 (D20 + D02), planes carry sigma^2; raw: +
         // scales arrive in decreasing order: >= keeps the smallest scale of a tie
         if (v >= mxr[j]) mxr[j] = v, amx[i * 32 + lane] = (unsigned char)s;
         if (v <= mnr[j]) mnr[j] = v, amn[i * 32 + lane] = (unsigned char)s;
@@ -467,6 +481,11 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
       }
       fence_proxy_async();  // held rows written into a stage before its next async copy
       __syncthreads();
+    }
+    if (da.raw) {  // a derivative channel: written above, no detection (uniform over the block)
+      fence_proxy_async();
+      __syncthreads();
+      continue;
     }
     // the stages are free now: the extremes go to shared memory for the 3 x 3 test
     float *mx = sm, *mn = sm + CROWS2 * 32;
@@ -497,7 +516,7 @@ int launch_colfir_tma(const Plan &p, const Launch &l, const BankArgs &a, const D
                       cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_colfir_tma<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_colfir_tma<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   CUtensorMap map;
@@ -507,12 +526,12 @@ int launch_colfir_tma(const Plan &p, const Launch &l, const BankArgs &a, const D
   const int SF = colfir_stage_floats<ST>(stage_rows);
   // stages (>= 2 x 128 x 32 floats for the final extremes) + taps + first-scale bytes
   const size_t tsm = ((size_t)SF + 2 * taps_len) * sizeof(float) + (size_t)CROWS2 * 32 * 2 + TMA_SMEM_ALIGN;
-  if (tsm > 220 * 1024 || SF < 2 * CROWS2 * 32) return -1;
+  if (tsm > 200 * 1024 || SF < 2 * CROWS2 * 32) return -1;
   const int nb = persistent_blocks((const void *)k_colfir_tma<ST>, CNT2, tsm, l.it.total, p.mult[PASS_DET]);
   a.prof->begin("fir_coldet", st);
   k_colfir_tma<ST><<<nb, CNT2, tsm, st>>>(map, p.fr, l.it, a.edge, p.PWb, a.coef, a.S, stage_rows, taps_len, da);
   a.prof->end(st);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace
@@ -600,7 +619,7 @@ int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_rowfir, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_colfir, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_colfir, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   const int kmax = a.kmax;
@@ -616,14 +635,16 @@ int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st) {
   da.cap = a.cap;
   da.status = a.status;
   da.resp = nullptr;
+  da.raw = a.raw;
   // in + buf + detector scratch (2 float planes + 2 byte planes) + taps (adjacent neighbourhood)
   const size_t csm = ((size_t)(CROWS + 2 * G) * 32 + (size_t)a.S * CROWS * 32 + (size_t)CROWS * 32 * 2 +
                       (size_t)CROWS * 32 * 2 / 4 + KP + 1) * sizeof(float);
-  if (a.neigh != 0 && csm > 220 * 1024) return -1;
+  if (a.neigh != 0 && csm > 200 * 1024) return -1;
   auto row = [&](const Launch &l) {
     const int nb = persistent_blocks((const void *)k_rowfir, RNT, rsm, l.it.total, p.mult[PASS_ROW]);
     a.prof->begin("fir_row", st);
-    k_rowfir<<<nb, RNT, rsm, st>>>(p.fr, l.it, a.coef, a.S, kmax, a.P, a.storage, p.PWb, a.edge, a.status);
+    k_rowfir<<<nb, RNT, rsm, st>>>(p.fr, l.it, a.coef, a.S, kmax, a.P, a.storage, p.PWb, a.edge, a.status,
+                                   a.chan);
     a.prof->end(st);
   };
   auto det = [&](const Launch &l) -> int {
@@ -639,7 +660,7 @@ int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st) {
     a.prof->begin("fir_coldet", st);
     k_colfir<<<nb, CNT, csm, st>>>(p.fr, l.it, a.P, a.storage, p.PWb, a.edge, a.coef, a.S, kmax, da);
     a.prof->end(st);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
   };
   if (p.per_frame) {
     for (int f = 0; f < p.nframes; ++f) {
@@ -650,7 +671,7 @@ int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st) {
     row(p.pass[PASS_ROW][0]);
     if (int rc = det(p.pass[PASS_DET][0])) return rc;
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace kf

@@ -240,9 +240,9 @@ __host__ __device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
 // (yw = 1) row for the column boundary.  One body for both cases keeps the
 // kernel's code small.  All threads of the block; ends with __syncthreads.
 template <class Rec>
-__device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, const Coef *__restrict__ coef,
-                                         int S, void *__restrict__ P, int st, long PWb,
-                                         float *__restrict__ edge, bool &ovf, float *sm) {
+__device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, int chan,
+                                         const Coef *__restrict__ coef, int S, void *__restrict__ P, int st,
+                                         long PWb, float *__restrict__ edge, bool &ovf, float *sm) {
   const int NT = blockDim.x, tid = threadIdx.x;
   const int H = F.H, W = F.W;
   const int RP = pad32(NT * CH) + 1;
@@ -277,24 +277,40 @@ __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, c
     }
   });
   __syncthreads();
-  const float v_lo = s_p[0] - 2.f * s_0[0] + s_m[0];
-  const int eW = pad32(W - 1);
-  const float v_hi = s_p[eW] - 2.f * s_0[eW] + s_m[eW];
   float L[CH];
   const int x0 = tid * CH;
+  float in_lo, in_hi;
+  if (chan == CH_LAP) {
+    const float v_lo = s_p[0] - 2.f * s_0[0] + s_m[0];
+    const int eW = pad32(W - 1);
+    const float v_hi = s_p[eW] - 2.f * s_0[eW] + s_m[eW];
 #pragma unroll
-  for (int i = 0; i < CH; ++i) {
-    const int e = x0 + i;
-    if (e < W) {
-      const float c0 = s_0[pad32(e)];
-      const float u = s_0[pad32(min(e + 1, W - 1))] - 2.f * c0 + s_0[pad32(max(e - 1, 0))];
-      const float v = s_p[pad32(e)] - 2.f * c0 + s_m[pad32(e)];
-      L[i] = EDGE ? u : u + v;
-    } else {
-      L[i] = EDGE ? 0.f : v_hi;  // beyond the right edge only the held V part
+    for (int i = 0; i < CH; ++i) {
+      const int e = x0 + i;
+      if (e < W) {
+        const float c0 = s_0[pad32(e)];
+        const float u = s_0[pad32(min(e + 1, W - 1))] - 2.f * c0 + s_0[pad32(max(e - 1, 0))];
+        const float v = s_p[pad32(e)] - 2.f * c0 + s_m[pad32(e)];
+        L[i] = EDGE ? u : u + v;
+      } else {
+        L[i] = EDGE ? 0.f : v_hi;  // beyond the right edge only the held V part
+      }
     }
+    in_lo = EDGE ? 0.f : v_lo;
+    in_hi = EDGE ? 0.f : v_hi;
+  } else {  // one derivative channel of the derivative bank
+    const int cin = EDGE ? edge_chan(chan) : chan;
+    auto am = [&](int e) { return s_m[pad32(min(max(e, 0), W - 1))]; };
+    auto ao = [&](int e) { return s_0[pad32(min(max(e, 0), W - 1))]; };
+    auto ap = [&](int e) { return s_p[pad32(min(max(e, 0), W - 1))]; };
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      const int e = x0 + i;
+      L[i] = e < W ? chan_at(cin, am, ao, ap, e) : chan_beyond(cin, am, ao, ap, W - 1);
+    }
+    in_lo = chan_beyond(cin, am, ao, ap, 0);
+    in_hi = chan_beyond(cin, am, ao, ap, W - 1);
   }
-  const float in_lo = EDGE ? 0.f : v_lo, in_hi = EDGE ? 0.f : v_hi;
   __syncthreads();
   float *s_out = sm;
   for (int s = 0; s < S; ++s) {
@@ -362,7 +378,7 @@ template <class Rec>
 __global__ void __launch_bounds__(256) k_row(const FrameDev *__restrict__ fr, Items it,
                                              const Coef *__restrict__ coef, int S, void *__restrict__ P,
                                              int st, long PWb, float *__restrict__ edge,
-                                             DevStatus *__restrict__ status) {
+                                             DevStatus *__restrict__ status, int chan) {
   extern __shared__ float sm[];
   __shared__ FrameDev s_fr;
   bool ovf = false;  // a value beyond the f16 range
@@ -375,7 +391,7 @@ __global__ void __launch_bounds__(256) k_row(const FrameDev *__restrict__ fr, It
     __syncthreads();
     const FrameDev &F = s_fr;
     const bool e = local >= F.H;
-    row_body<Rec>(F, e, e ? local - F.H : local, coef, S, P, st, PWb, edge, ovf, sm);
+    row_body<Rec>(F, e, e ? local - F.H : local, chan, coef, S, P, st, PWb, edge, ovf, sm);
   }
   if (ovf) atomicExch(&status->range, 1);
 }
@@ -575,6 +591,7 @@ __global__ void __launch_bounds__(512, LC == 32 ? Rec::kColdetMinBlocks32 : 1) k
   typename Rec::View v;
   v.load(cf);
   const long fs = (long)Rec::NF * PWb;
+  const float sgn = da.raw ? 1.f : -1.f;
   uint32_t phase = 0;
   int k = 0;
   const int nitems = items_total(it);
@@ -638,7 +655,8 @@ __global__ void __launch_bounds__(512, LC == 32 ? Rec::kColdetMinBlocks32 : 1) k
 #pragma unroll
     for (int i = NR - 1; i >= 0; --i) {
       const float in = b[i * LD];
-      b[i * LD] = -(yp[i] + fmaf(v.b0, in, r.out(v)));  // R_L = -sigma^2 (D20 + D02); planes carry sigma^2
+      // R_L = -sigma^2 (D20 + D02) (planes carry sigma^2); raw channel: +sigma^2 D
+      b[i * LD] = sgn * (yp[i] + fmaf(v.b0, in, r.out(v)));
       r.push(v, in);
     }
     __syncthreads();
@@ -665,7 +683,7 @@ int run_iir_st(const Plan &p, const BankArgs &a, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_row<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_coldet<Rec, ST, LC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_coldet<Rec, ST, LC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   constexpr int NR = LC + 2;
@@ -681,13 +699,14 @@ int run_iir_st(const Plan &p, const BankArgs &a, cudaStream_t st) {
   da.cap = a.cap;
   da.status = a.status;
   da.resp = nullptr;
+  da.raw = a.raw;
   using TS = typename Store<ST>::T;
   auto row = [&](const Launch &l) {
     const size_t smem = (size_t)(3 * (pad32(l.nt * CH) + 1) + 64 * Rec::NF) * sizeof(float);
     if (smem > 200 * 1024) return false;
     const int nb = persistent_blocks((const void *)k_row<Rec>, l.nt, smem, l.it.total, p.mult[PASS_ROW]);
     a.prof->begin("iir_row", st);
-    k_row<Rec><<<nb, l.nt, smem, st>>>(p.fr, l.it, a.coef, a.S, a.P, a.storage, p.PWb, a.edge, a.status);
+    k_row<Rec><<<nb, l.nt, smem, st>>>(p.fr, l.it, a.coef, a.S, a.P, a.storage, p.PWb, a.edge, a.status, a.chan);
     a.prof->end(st);
     return true;
   };
@@ -725,7 +744,7 @@ int run_iir_st(const Plan &p, const BankArgs &a, cudaStream_t st) {
     fold(p.pass[PASS_FOLD][0]);
     det(p.pass[PASS_DET][0]);
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <class Rec, int ST>

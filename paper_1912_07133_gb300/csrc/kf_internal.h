@@ -49,6 +49,9 @@ struct BankArgs {
   long cap;
   DevStatus *status;
   Prof *prof;            // launch bookkeeping (never null)
+  int chan = CH_LAP;     // derivative channel of the row pass (CH_*)
+  int raw = 0;           // 1: column passes write +sigma^2 D of the channel, no detection
+  float *raw_out = nullptr;  // raw channel planes (per frame S x H x W at the frame's response offset)
 };
 
 // Passes of the banks.  IIR: row (with the two edge rows per frame), column
@@ -71,6 +74,7 @@ struct Plan {
   int maxW = 0, maxH = 0;
   bool per_frame = false;        // launch every pass frame by frame
   int mult[NPASS] = {0, 0, 0, 0}; // launch shape per pass (see persistent_blocks)
+  Launch comb;                    // derivative bank: the combine + detect launch
   int lc = 64;                    // IIR column segment length (32 or 64 rows)
   std::vector<Launch> pass[NPASS];
 };
@@ -82,6 +86,12 @@ int fir_items(int pass, int H, int W, int S, int neigh);
 int iir_segments(int H, int lc);  // IIR column segments of a frame (segment length lc)
 
 int launch_iir(const Plan &p, const BankArgs &a, cudaStream_t st);
+// derivative bank: tiles of 30 x 30 per frame; R (R_H or R_L) from the
+// channel planes and the detector (kf_deriv.cu)
+int deriv_items(int H, int W);
+int launch_combine_detect(const Plan &p, const Launch &l, const BankArgs &a, int hessian, const float *c20,
+                          const float *c02, const float *c11, const float *c10, const float *c01, float limit2,
+                          cudaStream_t st);
 int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st);
 
 // 2-D tensor map over the plane row space (x, plane row), element type

@@ -472,7 +472,7 @@ int net_pool(const void *X, int dtype, float vs, long xpitch, int H, int W, floa
     case IN_U16: k_pool8<<<g, 256, 0, st>>>(static_cast<const unsigned short *>(X), xpitch, H, W, vs, out, h, w); break;
     default: k_pool8<<<g, 256, 0, st>>>(static_cast<const float *>(X), xpitch, H, W, vs, out, h, w);
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 // logits of N pooled images x [N][h][w] into z_out [N][8][th][tw] (z_out may
@@ -495,7 +495,7 @@ int net_forward(const float *x, int N, int h, int w, const __nv_bfloat16 *wb, fl
   const int th = (h + 7) / 8, tw = (w + 7) / 8;
   const long T = (long)N * 8 * th * tw;
   k_tilemax<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(c.o3, 8, h, w, th, tw, T, z_out ? z_out : c.z, c.arg);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 // forward, weighted BCE against labels t [N][8][th][tw], backward: the mean
@@ -525,52 +525,52 @@ int net_grad(const float *x, const unsigned char *t, int N, int h, int w, float 
   // layer 1 (1 -> 16)
   k_conv_bwd_w<1, 16><<<gr, CT * CT, 0, st>>>(x, c.d1, h, w, c.part);
   k_reduce_tiles<<<(16 * 9 + 16 + 255) / 256, 256, 0, st>>>(c.part, tiles, 16 * 9 + 16, g + W1);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int net_adam(float *master, float *m, float *v, const float *g, int step, float lr, __nv_bfloat16 *wb,
              cudaStream_t st) {
   const float c1 = 1.f - powf(0.9f, (float)step), c2 = 1.f - powf(0.999f, (float)step);
   k_adam<<<(NET_NPARAM + 255) / 256, 256, 0, st>>>(master, m, v, g, NET_NPARAM, lr, c1, c2, wb);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int net_to_bf16(const float *x, __nv_bfloat16 *y, cudaStream_t st) {
   k_to_bf16<<<(NET_NPARAM + 255) / 256, 256, 0, st>>>(x, NET_NPARAM, y);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int net_pool_table(const FrameDev *fr, int f, int H, int W, float *out, cudaStream_t st) {
   const int h = (H + 7) / 8, w = (W + 7) / 8;
   k_pool8_tab<<<dim3((w + 255) / 256, h), 256, 0, st>>>(fr, f, out);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int gate_tiles(const float *z, int S, int th, int tw, float zthr, int dilate, unsigned char *act,
                cudaStream_t st) {
   k_gate_tiles<<<(th * tw + 255) / 256, 256, 0, st>>>(z, S, th, tw, zthr, dilate, act);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int gate_select_tiles(const FrameDev *fr, const Items &full, const unsigned char *act, int tw, int th, int2 *sel,
                       int *count, cudaStream_t st) {
   if (full.total > 0)
     k_sel_tiles<<<(full.total + 255) / 256, 256, 0, st>>>(fr, full, act, tw, th, sel, count);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int gate_select_rows(const FrameDev *fr, const Items &full, const unsigned char *act, int rseg, int reach,
                      int2 *sel, int *count, cudaStream_t st) {
   if (full.total > 0)
     k_sel_rows<<<(full.total + 255) / 256, 256, 0, st>>>(fr, full, act, rseg, reach, sel, count);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int net_labels(const Blob *b, long n, float thr, const long *loff, const int *ltw, const int *lth, int S,
                unsigned char *lab, cudaStream_t st) {
   if (n <= 0) return 0;
   k_labels<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b, n, thr, loff, ltw, S, lab, lth);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace kf

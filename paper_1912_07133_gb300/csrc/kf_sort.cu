@@ -207,7 +207,7 @@ int launch_sort(const Blob *blobs, long n, float thr, int nscales, long hmax, lo
   prof->begin("sort_gather", st);
   k_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(blobs, i0, n, out);
   prof->end(st);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace kf

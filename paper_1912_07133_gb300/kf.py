@@ -82,12 +82,14 @@ class kf_bank_opts(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("responses", ctypes.c_void_p),
                 ("schedule", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("gate", ctypes.c_int32), ("gate_threshold", ctypes.c_float),
-                ("reserved", ctypes.c_int64 * 2)]
+                ("offset_limit", ctypes.c_float), ("reserved0", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 1)]
 
 
 class kf_blob(ctypes.Structure):
     _fields_ = [("frame", ctypes.c_int32), ("x", ctypes.c_int32), ("y", ctypes.c_int32),
-                ("scale", ctypes.c_int32), ("polarity", ctypes.c_int32), ("response", ctypes.c_float)]
+                ("scale", ctypes.c_int32), ("polarity", ctypes.c_int32), ("response", ctypes.c_float),
+                ("dx", ctypes.c_float), ("dy", ctypes.c_float)]
 
 
 class kf_kernel_time(ctypes.Structure):
@@ -95,7 +97,7 @@ class kf_kernel_time(ctypes.Structure):
 
 
 BLOB_DTYPE = np.dtype([("frame", "<i4"), ("x", "<i4"), ("y", "<i4"), ("scale", "<i4"),
-                       ("polarity", "<i4"), ("response", "<f4")])
+                       ("polarity", "<i4"), ("response", "<f4"), ("dx", "<f4"), ("dy", "<f4")])
 
 _lib = None
 
@@ -396,7 +398,7 @@ class Bank:
     def run(self, frames, scales, ftype=KF_IIR_REPEATED_POLE, order=4, threshold=0.05,
             neighbourhood=KF_NEIGH_ALL_SCALES, responses=None, fir_kmax=96, profile=False,
             storage=KF_DTYPE_F32, value_scales=None, schedule=KF_SCHED_BATCHED, graph=False, gate=False,
-            gate_threshold=None):
+            gate_threshold=None, response=KF_RESP_LAPLACIAN, offset_limit=0.0):
         o = kf_bank_opts_default()
         o.threshold = float(threshold)
         o.profile = 1 if profile else 0
@@ -406,6 +408,8 @@ class Bank:
         o.schedule = schedule
         o.graph = 1 if graph else 0
         o.gate = int(gate) if not isinstance(gate, bool) else (KF_GATE_DILATED if gate else KF_GATE_OFF)
+        o.response = response
+        o.offset_limit = float(offset_limit)
         if gate_threshold is not None:
             o.gate_threshold = float(gate_threshold)
         if responses is not None:

@@ -53,7 +53,7 @@ def test_struct_layouts_match_header(lib):
     import ctypes
     from paper_1912_07133_gb300 import kf
     assert ctypes.sizeof(kf.kf_frame) == 32
-    assert ctypes.sizeof(kf.kf_blob) == 24
+    assert ctypes.sizeof(kf.kf_blob) == 32
     assert ctypes.sizeof(kf.kf_bank_opts) == 4 * 4 + 8 + 8 + 8 + 32
     assert ctypes.sizeof(kf.kf_kernel_time) == 40
     o = kf.kf_bank_opts_default()
