@@ -246,8 +246,11 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes,
 
 /* Copy the candidates of the last kf_filter_bank call with |R| > threshold
  * into out[0..capacity) (host, caller-owned), sorted by (frame, scale, y, x);
- * *count (host) receives the number of such blobs.  threshold must be >= the
- * bank's opts->threshold.  Synchronises the context stream.
+ * *count (host) receives the number of such blobs; entries of out past
+ * *count may be overwritten.  threshold must be >= the bank's
+ * opts->threshold.  Synchronises the context stream (once per call: the
+ * ordering, the count and the copy share one synchronisation; pinned `out`
+ * memory copies fastest).
  * Errors: KF_EINVAL, KF_EOVERFLOW (capacity < *count; the first `capacity`
  * blobs are written), KF_ERERUN (the device-side candidate list of the last
  * call overflowed; capacity raised, run the bank again), KF_ERANGE (f16

@@ -49,7 +49,11 @@ struct kf_ctx {
   void *sort_work = nullptr;
   size_t sort_work_bytes = 0;
   unsigned *d_npass = nullptr;
+  unsigned *h_npass = nullptr;  // pinned: read back with the records, one synchronisation
   bool sorted_valid = false;
+  // the device status of the last bank call, read once
+  kf::DevStatus last_status{};
+  bool status_read = false;
   double sorted_thr = 0.0;
   long sorted_n = 0;
   int last_nframes = 0;
@@ -367,6 +371,7 @@ void kf_destroy(kf_ctx *ctx) {
   cudaFree(ctx->sorted);
   cudaFree(ctx->sort_work);
   cudaFree(ctx->d_npass);
+  if (ctx->h_npass) cudaFreeHost(ctx->h_npass);
   cudaFree(ctx->lambdas);
   cudaFree(ctx->dwork);
   cudaFree(ctx->status);
@@ -809,6 +814,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   }
   ctx->have_result = true;
   ctx->sorted_valid = false;
+  ctx->status_read = false;
   ctx->last_threshold = opts.threshold;
   ctx->last_S = nscales;
   ctx->last_nframes = nframes;
@@ -1149,10 +1155,13 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
                 ctx->last_threshold);
   cudaError_t e;
   if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
-  kf::DevStatus st;
-  if ((e = cudaMemcpyAsync(&st, ctx->status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
-    return cuda_fail(ctx, e, "read status");
-  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "filter bank");
+  kf::DevStatus &st = ctx->last_status;
+  if (!ctx->status_read) {
+    if ((e = cudaMemcpyAsync(&st, ctx->status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "read status");
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "filter bank");
+    ctx->status_read = true;
+  }
   if (st.error) return fail(ctx, KF_ETIMEOUT, "device wait gave up (code %d)", st.error);
   if (st.range)
     return fail(ctx, KF_ERANGE,
@@ -1175,7 +1184,12 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
                 (unsigned long long)st.count);
   }
   const long n = (long)st.count;
-  if (!ctx->sorted_valid || ctx->sorted_thr != threshold) {
+  // A new ordering (first call after a bank call, or a new threshold) is
+  // sorted, counted and copied under one synchronisation: the copy takes up to
+  // n records (the passing ones come first), the count arrives with it.
+  const bool fresh = !ctx->sorted_valid || ctx->sorted_thr != threshold;
+  if (fresh) {
+    ctx->sorted_valid = false;
     ctx->sorted_n = 0;
     if (n > 0) {
       const size_t wb = kf::sort_workspace_bytes(ctx->blob_cap);
@@ -1192,6 +1206,8 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
       }
       if (!ctx->d_npass && (e = cudaMalloc(&ctx->d_npass, sizeof(unsigned))) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMalloc(npass)");
+      if (!ctx->h_npass && (e = cudaMallocHost(&ctx->h_npass, sizeof(unsigned))) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMallocHost(npass)");
       const unsigned long long span = (unsigned long long)ctx->last_nframes * ctx->last_S *
                                       (unsigned long long)ctx->last_hmax * ctx->last_wmax;
       int keybits = 0;
@@ -1200,25 +1216,24 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
       if (kf::launch_sort(ctx->blobs, n, (float)threshold, ctx->last_S, ctx->last_hmax, ctx->last_wmax,
                           keybits, ctx->sort_work, ctx->sorted, ctx->d_npass, &none, ctx->stream))
         return cuda_fail(ctx, cudaGetLastError(), "sort launch");
-      unsigned np = 0;
-      if ((e = cudaMemcpyAsync(&np, ctx->d_npass, sizeof np, cudaMemcpyDeviceToHost, ctx->stream)) !=
-          cudaSuccess)
+      if ((e = cudaMemcpyAsync(ctx->h_npass, ctx->d_npass, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                               ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "read count");
-      if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sort");
-      ctx->sorted_n = np;
     }
+  }
+  const int64_t ncopy = std::min<int64_t>(capacity, fresh ? (int64_t)n : (int64_t)ctx->sorted_n);
+  static_assert(sizeof(kf_blob) == sizeof(kf::Blob), "record layout");
+  if (ncopy > 0 && (e = cudaMemcpyAsync(out, ctx->sorted, sizeof(kf::Blob) * ncopy, cudaMemcpyDeviceToHost,
+                                        ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "copy blobs");
+  if ((ncopy > 0 || (fresh && n > 0)) && (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "sort / copy blobs");
+  if (fresh) {
+    ctx->sorted_n = n > 0 ? (long)*ctx->h_npass : 0;
     ctx->sorted_valid = true;
     ctx->sorted_thr = threshold;
   }
   *count = (int64_t)ctx->sorted_n;
-  const int64_t ncopy = std::min<int64_t>(capacity, ctx->sorted_n);
-  if (ncopy > 0) {
-    static_assert(sizeof(kf_blob) == sizeof(kf::Blob), "record layout");
-    if ((e = cudaMemcpyAsync(out, ctx->sorted, sizeof(kf::Blob) * ncopy, cudaMemcpyDeviceToHost,
-                             ctx->stream)) != cudaSuccess)
-      return cuda_fail(ctx, e, "copy blobs");
-    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "copy blobs");
-  }
   if (ctx->sorted_n > capacity)
     return fail(ctx, KF_EOVERFLOW, "capacity %lld < %lld blobs", (long long)capacity,
                 (long long)ctx->sorted_n);

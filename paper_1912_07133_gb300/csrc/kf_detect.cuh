@@ -76,42 +76,69 @@ static __device__ __forceinline__ void emit_blob(const DetectArgs &a, TileList &
   }
 }
 
+// The tie rule of one candidate against its 8 neighbours' extremes m / am:
+// strictly above a neighbour earlier in (y, x) order or with an earlier first
+// scale, at least equal to a later one (pol = -1 mirrors the values).
+static __device__ __forceinline__ bool beats_neighbours(const float *m, const unsigned char *am, int p, int pol,
+                                                        float v, int s) {
+  bool ok = true;
+  for (int di = -1; di <= 1 && ok; ++di)
+    for (int dl = -1; dl <= 1 && ok; ++dl) {
+      if (di == 0 && dl == 0) continue;
+      const int pn = p + di * 32 + dl;
+      const float vn = m[pn];
+      const int sn = am[pn];
+      const bool after = di > 0 || (di == 0 && dl > 0);
+      const float a1 = pol * v, b1 = pol * vn;
+      ok = (a1 > b1) || (a1 == b1 && (sn > s || (sn == s && after)));
+    }
+  return ok;
+}
+
 // Spatial part of the all-scales test.  mx/mn: per-pixel maximum/minimum of R
 // over the scales of an NR x 32 tile (+-inf outside the frame), amx/amn: the
 // first scale attaining them.  A pixel's candidate is its first argmax
 // (argmin); it must beat the 8 neighbours' extremes with the tie rule.
-// Candidates are staged in shared memory and reserved globally once per tile.
-// Must be called by all threads of the block (contains __syncthreads).
+// Each warp walks a band of interior rows, one column per lane, holding the
+// horizontal 3-maxima (3-minima, by shuffles) of three consecutive rows in
+// registers: a pixel below its 3 x 3 maximum cannot pass, and the rest take
+// the exact tie test.  Candidates are staged in shared memory and reserved
+// globally once per tile.  Must be called by all threads of the block
+// (blockDim a multiple of 32; contains __syncthreads).
 static __device__ void spatial_detect(const float *mx, const float *mn, const unsigned char *amx,
                                       const unsigned char *amn, const DetectArgs &a) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   TileList &tl = g_tl;
   unsigned long long &s_base = g_tl_base;
   if (tid == 0) tl.n = 0;
   __syncthreads();
-  const int NI = (a.NR - 2) * 30;  // interior pixels
-  for (int q = tid; q < NI; q += nt) {
-    const int i = 1 + q / 30, lane = 1 + q % 30;
-    const int y = a.r0 + i, x = a.x0 + lane;
-    if (y < 0 || y >= a.H || x < 0 || x >= a.W) continue;
-    const int p = i * 32 + lane;
-    for (int pol = 1; pol >= -1; pol -= 2) {
-      if (pol == -1 && !a.dark) break;
-      const float v = (pol == 1) ? mx[p] : mn[p];
-      const int s = (pol == 1) ? amx[p] : amn[p];
-      if (!(pol * v > a.thr)) continue;
-      bool ok = true;
-      for (int di = -1; di <= 1 && ok; ++di)
-        for (int dl = -1; dl <= 1 && ok; ++dl) {
-          if (di == 0 && dl == 0) continue;
-          const int pn = p + di * 32 + dl;
-          const float vn = (pol == 1) ? mx[pn] : mn[pn];
-          const int sn = (pol == 1) ? amx[pn] : amn[pn];
-          const bool after = di > 0 || (di == 0 && dl > 0);
-          const float a1 = pol * v, b1 = pol * vn;
-          ok = (a1 > b1) || (a1 == b1 && (sn > s || (sn == s && after)));
+  const int chunk = (a.NR - 2 + (nt >> 5) - 1) / (nt >> 5);
+  const int ib = 1 + warp * chunk, ie = min(a.NR - 1, ib + chunk);  // rows [ib, ie), warp-uniform
+  const int x = a.x0 + lane;
+  const bool col = lane >= 1 && lane <= 30 && x >= 0 && x < a.W;
+  constexpr unsigned FULL = 0xffffffffu;
+  auto hmax = [&](float v) { return fmaxf(v, fmaxf(__shfl_up_sync(FULL, v, 1), __shfl_down_sync(FULL, v, 1))); };
+  auto hmin = [&](float v) { return fminf(v, fminf(__shfl_up_sync(FULL, v, 1), __shfl_down_sync(FULL, v, 1))); };
+  if (ib < ie) {
+    float xa = hmax(mx[(ib - 1) * 32 + lane]), na = hmin(mn[(ib - 1) * 32 + lane]);
+    float vc = mx[ib * 32 + lane], wc = mn[ib * 32 + lane];
+    float xb = hmax(vc), nb = hmin(wc);
+    for (int i = ib; i < ie; ++i) {
+      const float vn = mx[(i + 1) * 32 + lane], wn = mn[(i + 1) * 32 + lane];
+      const float xc = hmax(vn), nc = hmin(wn);
+      const int y = a.r0 + i;
+      if (col && y >= 0 && y < a.H) {
+        const int p = i * 32 + lane;
+        if (vc > a.thr && vc >= fmaxf(xa, fmaxf(xb, xc))) {
+          const int s = amx[p];
+          if (beats_neighbours(mx, amx, p, 1, vc, s)) emit_blob(a, tl, s, y, x, 1, vc);
         }
-      if (ok) emit_blob(a, tl, s, y, x, pol, v);
+        if (a.dark && -wc > a.thr && wc <= fminf(na, fminf(nb, nc))) {
+          const int s = amn[p];
+          if (beats_neighbours(mn, amn, p, -1, wc, s)) emit_blob(a, tl, s, y, x, -1, wc);
+        }
+      }
+      xa = xb, xb = xc, na = nb, nb = nc, vc = vn, wc = wn;
     }
   }
   __syncthreads();

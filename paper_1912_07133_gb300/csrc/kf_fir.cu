@@ -22,6 +22,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "kf_batch.cuh"
 #include "kf_common.cuh"
@@ -47,6 +48,41 @@ constexpr uint32_t WAIT_LIMIT = 1u << 20;
 __device__ __forceinline__ void stage_taps(float *sh, const Coef &c, int K, int tid, int nt) {
   const int KP = ((K + TB - 1) / TB) * TB;
   for (int k = tid; k <= KP; k += nt) sh[k] = (k <= K) ? c.h[k] : 0.f;
+}
+
+// Taps for the tensor-core column pass as a zero-padded band,
+// band[u] = h(|u - BAND0 - K|) for |u - BAND0 - K| <= K and 0 elsewhere, so
+// that the Toeplitz entry A[r][q] = h(|q - r - K|) is band[BAND0 + q - r]
+// without an absolute value or a range test.  Each tap is split into TF32
+// parts, hi = tf32(h) and lo = tf32(h - hi), after multiplying by sgn (+-1,
+// exact).
+constexpr int BAND0 = 16;  // band[0..BAND0) pads the smallest index a fragment reads (q - r >= -15)
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return u;
+}
+
+__device__ __forceinline__ void stage_taps_band(float *th, float *tl, const Coef &c, int K, int len, float sgn,
+                                                int tid, int nt) {
+  for (int u = tid; u < len; u += nt) {
+    const int m = abs(u - BAND0 - K);
+    const float v = m <= K ? sgn * c.h[m] : 0.f;
+    const uint32_t hi = to_tf32(v);
+    th[u] = __uint_as_float(hi);
+    tl[u] = __uint_as_float(to_tf32(v - __uint_as_float(hi)));
+  }
+}
+
+// D += A B, one m16n8k8 TF32 tensor-core product (A 16 x 8 row-major, B 8 x 8)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 // Symmetric FIR on a register block of NOUT consecutive outputs.
@@ -343,6 +379,20 @@ __host__ __device__ constexpr int colfir_stage_floats(int stage_rows) {
   return ST == ST_F32 ? 2 * stage_rows * BOXW : stage_rows * BOXW16 + stage_rows * 32;
 }
 
+// pixel of output j (0..15) of a thread in the tensor-core accumulator layout:
+// tile nb = j / 4 holds rows g, g + 8 and columns n = 2 tig, 2 tig + 1 of the
+// warp's 16 x 8 block nb (g = lane / 4, tig = lane % 4).  Column n of block nb
+// is tile column bcol<PERM>(n, nb): with PERM (the 36-float rows of the f32
+// stages) (n & 3) + 4 nb + 16 (n >> 2), so that the eight columns of a block
+// and the four rows tig of a fragment load fall in 32 different banks;
+// without it (the 32-float work tile, whose rows are XOR-swizzled instead)
+// n + 8 nb.
+template <bool PERM>
+__device__ __forceinline__ int bcol(int n, int nb) { return PERM ? (n & 3) + 4 * nb + 16 * (n >> 2) : n + 8 * nb; }
+__device__ __forceinline__ int mma_row(int warp, int lane, int j) { return 16 * warp + (lane >> 2) + 8 * ((j & 3) >> 1); }
+template <bool PERM>
+__device__ __forceinline__ int mma_col(int lane, int j) { return bcol<PERM>(2 * (lane & 3) + (j & 1), j >> 2); }
+
 template <int ST>
 __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ CUtensorMap map,
                                                         const FrameDev *__restrict__ fr, Items it,
@@ -361,7 +411,9 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
   auto land = [&](int b) { return reinterpret_cast<T *>(sm) + (long)b * stage_rows * BW; };
   float *work = sm + stage_rows * BOXW16;  // 16-bit planes only
   const int SF = colfir_stage_floats<ST>(stage_rows);
-  auto taps = [&](int b) { return sm + SF + b * taps_len; };
+  // one band of taps (hi parts, then lo parts): written at the start of a scale,
+  // after the previous scale's closing barrier
+  float *taps = sm + SF;
   unsigned char *amx = reinterpret_cast<unsigned char *>(sm + SF + 2 * taps_len);
   unsigned char *amn = amx + CROWS2 * 32;
   if (tid == 0) {
@@ -389,12 +441,12 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
     const int xa = x0 - off;
     const int r0 = (local / ntx) * (CROWS2 - 2) - 1;  // frame row of output row 0
     const int x = x0 + lane, xv = min(max(x, 0), W - 1);
-    const bool xin = x >= 0 && x < W;
+    const bool inside = x0 >= 0 && x0 + 32 <= W && r0 >= 0 && r0 + CROWS2 <= H;  // the whole 128 x 32 tile
     float *resp = F.resp;
     float mxr[NOUT], mnr[NOUT];
 #pragma unroll
     for (int j = 0; j < NOUT; ++j) {
-      const int p = (NOUT * warp + j) * 32 + lane;
+      const int p = mma_row(warp, lane, j) * 32 + mma_col<F32>(lane, j);
       mxr[j] = -CUDART_INF_F;
       mnr[j] = CUDART_INF_F;
       amx[p] = (unsigned char)S;
@@ -423,7 +475,9 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
       if (F32 && tid == 0 && is + 1 < S) issue(s - 1, b ^ 1);
       const Coef &c = coef[s];
       const int K = c.K, G = K + TB, nin = CROWS2 + 2 * G;
-      stage_taps(taps(b), c, K, tid, CNT2);
+      // R_L = -sigma^2 (D20 + D02) with the planes carrying sigma^2: the taps
+      // carry the sign (a raw derivative channel keeps +)
+      stage_taps_band(taps, taps + taps_len, c, K, taps_len, sgn, tid, CNT2);
       const bool ok = mbar_wait_bounded(&mbar[b], b ? ph1 : ph0, WAIT_LIMIT);
       if (b) ph1 ^= 1u;
       else ph0 ^= 1u;
@@ -460,24 +514,84 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
         for (int j = warp; j < nin; j += CNT2 / 32) {
           const int r = r0 - G + j;
           const float v = Store<ST>::ld(src[j * BW]);
-          work[j * 32 + lane] = r < 0 ? top : (r >= H ? bot : v);
+          work[j * 32 + (lane ^ (8 * (j & 3)))] = r < 0 ? top : (r >= H ? bot : v);  // XOR-swizzled rows
         }
         tile = work;
         __syncthreads();  // landing stage b is free again
         if (tid == 0 && is + 2 < S) issue(s - 2, b);
       }
-      const float *col = tile + (G + NOUT * warp) * LDW + lane;
-      float acc[NOUT];
-      fir_block(taps(b), K, [&](int t) { return col[t * LDW]; }, acc);
+      // Banded Toeplitz product on the tensor cores: warp w computes output rows
+      // o = 16w + r (r < 16) x 32 columns as four m16n8k8 tiles,
+      // out[o] = sum_q A[r][q] stage[16w + 8 + q] over q in [0, 16 + 2K) with
+      // A[r][q] = h(|q - r - K|) (zero beyond K): the same A for every row
+      // block.  Three TF32 products per tap: lo x hi, hi x lo, hi x hi.
+      const int g = lane >> 2, tig = lane & 3;
+      const int J = (16 + 2 * K + 7) / 8;  // k-steps of 8 input rows
+      // A(g, tig) at k-step j is band[BAND0 + 8j + tig - g]; the fragment's other
+      // entries, A(g + 8, tig), A(g, tig + 4) and A(g + 8, tig + 4), sit 8 below,
+      // 4 above and 4 below it: the two below are the previous k-step's first
+      // and third
+      const float *ph = taps + BAND0 + tig - g, *pl = ph + taps_len;
+      uint32_t h1 = __float_as_uint(ph[-8]), h3 = __float_as_uint(ph[-4]);
+      uint32_t l1 = __float_as_uint(pl[-8]), l3 = __float_as_uint(pl[-4]);
+      // B(k, g) of block nb is window row 8j + k (k = tig, tig + 4), tile column
+      // bcol(g, nb); the work tile's row R holds column c at c ^ 8 (R & 3), and
+      // R & 3 = tig here
+      const float *tb = tile + (16 * warp + 8 + tig) * LDW;
+      int cb[4];
 #pragma unroll
-      for (int j = 0; j < NOUT; ++j) {
-        const int i = NOUT * warp + j, y = r0 + i;
-        if (!xin || y < 0 || y >= H) continue;
-        const float v = sgn * acc[j];  // R_L = -sigma^2 (D20 + D02), planes carry sigma^2; raw: +
-        // scales arrive in decreasing order: >= keeps the smallest scale of a tie
-        if (v >= mxr[j]) mxr[j] = v, amx[i * 32 + lane] = (unsigned char)s;
-        if (v <= mnr[j]) mnr[j] = v, amn[i * 32 + lane] = (unsigned char)s;
-        if (resp && i >= 1 && i <= CROWS2 - 2 && lane >= 1 && lane <= TW) resp[s * plane + (long)y * W + x] = v;
+      for (int nb = 0; nb < 4; ++nb) cb[nb] = F32 ? bcol<true>(g, nb) : g + 8 * (nb ^ tig);
+      float d[4][4];
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) d[nb][e] = 0.f;
+#pragma unroll 2
+      for (int j = 0; j < J; ++j) {
+        const uint32_t h0 = __float_as_uint(ph[8 * j]), h2 = __float_as_uint(ph[8 * j + 4]);
+        const uint32_t l0 = __float_as_uint(pl[8 * j]), l2 = __float_as_uint(pl[8 * j + 4]);
+        const float *rp = tb + 8 * j * LDW;
+#pragma unroll
+        for (int nb = 0; nb < 4; ++nb) {
+          const float x0v = rp[cb[nb]], x1v = rp[4 * LDW + cb[nb]];
+          // hi: x with the 13 bits below the TF32 mantissa cleared; lo = x - hi
+          // (exact), of which the tensor core reads the top 19 bits
+          const uint32_t bh0 = __float_as_uint(x0v) & 0xffffe000u, bh1 = __float_as_uint(x1v) & 0xffffe000u;
+          const uint32_t bl0 = __float_as_uint(x0v - __uint_as_float(bh0));
+          const uint32_t bl1 = __float_as_uint(x1v - __uint_as_float(bh1));
+          mma_tf32(d[nb], l0, l1, l2, l3, bh0, bh1);
+          mma_tf32(d[nb], h0, h1, h2, h3, bl0, bl1);
+          mma_tf32(d[nb], h0, h1, h2, h3, bh0, bh1);
+        }
+        h1 = h0;
+        h3 = h2;
+        l1 = l0;
+        l3 = l2;
+      }
+      // scales arrive in decreasing order: >= keeps the smallest scale of a tie;
+      // items wholly inside the frame skip the per-pixel frame test
+      auto extremes = [&](auto check) {
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) {
+          const int i = mma_row(warp, lane, j), cc = mma_col<F32>(lane, j);
+          if (decltype(check)::value) {
+            const int y = r0 + i, xj = x0 + cc;
+            if (xj < 0 || xj >= W || y < 0 || y >= H) continue;
+          }
+          const float v = d[j >> 2][j & 3];
+          if (v >= mxr[j]) mxr[j] = v, amx[i * 32 + cc] = (unsigned char)s;
+          if (v <= mnr[j]) mnr[j] = v, amn[i * 32 + cc] = (unsigned char)s;
+        }
+      };
+      if (inside) extremes(std::false_type());
+      else extremes(std::true_type());
+      if (resp) {
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) {
+          const int i = mma_row(warp, lane, j), cc = mma_col<F32>(lane, j), y = r0 + i, xj = x0 + cc;
+          if (xj >= 0 && xj < W && y >= 0 && y < H && i >= 1 && i <= CROWS2 - 2 && cc >= 1 && cc <= TW)
+            resp[s * plane + (long)y * W + xj] = d[j >> 2][j & 3];
+        }
       }
       fence_proxy_async();  // held rows written into a stage before its next async copy
       __syncthreads();
@@ -491,7 +605,7 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
     float *mx = sm, *mn = sm + CROWS2 * 32;
 #pragma unroll
     for (int j = 0; j < NOUT; ++j) {
-      const int p = (NOUT * warp + j) * 32 + lane;
+      const int p = mma_row(warp, lane, j) * 32 + mma_col<F32>(lane, j);
       mx[p] = mxr[j];
       mn[p] = mnr[j];
     }
@@ -522,7 +636,8 @@ int launch_colfir_tma(const Plan &p, const Launch &l, const BankArgs &a, const D
   CUtensorMap map;
   if (encode_plane_map(&map, a.P, ST, p.PWb, p.prows, ST == ST_F32 ? BOXW : BOXW16, BOXH)) return -1;
   const int stage_rows = (CROWS2 + 2 * G + BOXH - 1) / BOXH * BOXH;  // whole boxes
-  const int taps_len = (KP + 1 + 3) / 4 * 4;
+  // band length >= BAND0 + 2K + 23: one past the largest index a fragment reads
+  const int taps_len = (BAND0 + 2 * KP + 23 + 3) / 4 * 4;
   const int SF = colfir_stage_floats<ST>(stage_rows);
   // stages (>= 2 x 128 x 32 floats for the final extremes) + taps + first-scale bytes
   const size_t tsm = ((size_t)SF + 2 * taps_len) * sizeof(float) + (size_t)CROWS2 * 32 * 2 + TMA_SMEM_ALIGN;

@@ -1,9 +1,12 @@
 // kf_sort.cu -- ordering of the detector's candidate list on the GPU: the
 // candidates arrive in arbitrary (atomic) order; the blob list is returned in
 // (frame, scale, y, x) order.  Least-significant-digit radix sort of 64-bit
-// keys with 8-bit digits (stable per pass), then a gather of the records.
+// keys with digits of up to 9 bits (stable per pass), then a gather of the records.
 // Candidates at or below the re-threshold get the all-ones key and sort last.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <utility>
 
 #include "kf_common.cuh"
 #include "kf_internal.h"
@@ -17,6 +20,8 @@ constexpr int SORT_ITEMS = 4;              // items per thread (1024-item tiles:
 constexpr int TILE = SORT_NT * SORT_ITEMS; // items per block
 constexpr int NWARP = SORT_NT / 32;
 constexpr int ITEMS_PER_WARP = TILE / NWARP;
+constexpr int MAXBITS = 9;                 // digit width per pass (<= 9 bits: 512 digits)
+constexpr int MAXD = 1 << MAXBITS;
 
 __global__ void k_keys(const Blob *__restrict__ b, long n, float thr, int nscales, long hmax, long wmax,
                        unsigned long long *__restrict__ key, unsigned *__restrict__ idx,
@@ -34,106 +39,94 @@ __global__ void k_keys(const Blob *__restrict__ b, long n, float thr, int nscale
   idx[i] = (unsigned)i;
 }
 
-__device__ __forceinline__ int digit(unsigned long long k, int shift) { return (int)((k >> shift) & 0xff); }
+__device__ __forceinline__ int digit(unsigned long long k, int shift, int bits) {
+  return (int)((k >> shift) & ((1ull << bits) - 1ull));
+}
 
 // per-block digit histogram: hist[d * nblocks + block]
 __global__ void __launch_bounds__(SORT_NT) k_hist(const unsigned long long *__restrict__ key, long n, int shift,
-                                                  unsigned *__restrict__ hist) {
-  __shared__ unsigned h[256];
-  const int tid = threadIdx.x;
-  h[tid] = 0;
+                                                  int bits, unsigned *__restrict__ hist) {
+  __shared__ unsigned h[MAXD];
+  const int tid = threadIdx.x, nd = 1 << bits;
+  for (int d = tid; d < nd; d += SORT_NT) h[d] = 0;
   __syncthreads();
   const long base = (long)blockIdx.x * TILE;
   for (int j = 0; j < SORT_ITEMS; ++j) {
     const long i = base + (long)j * SORT_NT + tid;
-    if (i < n) atomicAdd(&h[digit(key[i], shift)], 1u);
+    if (i < n) atomicAdd(&h[digit(key[i], shift, bits)], 1u);
   }
   __syncthreads();
-  hist[(long)tid * gridDim.x + blockIdx.x] = h[tid];
+  for (int d = tid; d < nd; d += SORT_NT) hist[(long)d * gridDim.x + blockIdx.x] = h[d];
 }
 
-// Exclusive scan of m entries, one block of 1024 threads, in chunks of
-// SCAN_CHUNK entries: a coalesced load into shared memory (padded by one word
-// per 32 so that a thread's 32 consecutive entries sit in 32 banks), a serial
-// scan of each thread's 32 entries, a block scan of the thread totals with a
-// carried prefix, a coalesced write back.
-constexpr int SCAN_NT = 1024;
-constexpr int SCAN_CHUNK = 32 * SCAN_NT;
-constexpr size_t SCAN_SMEM = (size_t)(SCAN_CHUNK + SCAN_CHUNK / 32) * sizeof(unsigned);
-
-__device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }
-
-__global__ void __launch_bounds__(SCAN_NT) k_scan(unsigned *__restrict__ a, long m) {
-  extern __shared__ unsigned sa[];
-  __shared__ unsigned wsum[32];
-  __shared__ unsigned carry;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (tid == 0) carry = 0;
-  for (long r = 0; r < m; r += SCAN_CHUNK) {
-    const int n = (int)min((long)SCAN_CHUNK, m - r);
-    for (int i = tid; i < SCAN_CHUNK; i += SCAN_NT) sa[scan_pad(i)] = i < n ? a[r + i] : 0u;
-    __syncthreads();
-    unsigned tot = 0;  // this thread's 32 entries, scanned in place
-#pragma unroll 8
-    for (int j = 0; j < 32; ++j) {
-      const int q = scan_pad(32 * tid + j);
-      const unsigned v = sa[q];
-      sa[q] = tot;
-      tot += v;
-    }
-    unsigned x = tot;  // inclusive scan of the thread totals
+// One warp per digit d: exclusive scan of hist[d * nb + (0..nb)] over the
+// blocks, in place, and the digit's total in tot[d].
+__global__ void __launch_bounds__(SORT_NT) k_scan_digits(unsigned *__restrict__ hist, int nb, int nd,
+                                                         unsigned *__restrict__ tot) {
+  const int lane = threadIdx.x & 31, d = blockIdx.x * NWARP + (threadIdx.x >> 5);
+  if (d >= nd) return;
+  unsigned *h = hist + (long)d * nb;
+  unsigned carry = 0;
+  for (int b0 = 0; b0 < nb; b0 += 32) {
+    const int b = b0 + lane;
+    const unsigned v = b < nb ? h[b] : 0u;
+    unsigned x = v;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
-      if (lane >= d) x += y;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (b < nb) h[b] = carry + x - v;
+    carry += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (lane == 0) tot[d] = carry;
+}
+
+// stable scatter: items keep their order inside a digit; a digit's first
+// position is the sum of the totals of the smaller digits (a block scan of
+// tot) plus the earlier blocks' counts of it (hist, scanned)
+__global__ void __launch_bounds__(SORT_NT) k_scatter(const unsigned long long *__restrict__ kin,
+                                                     const unsigned *__restrict__ iin, long n, int shift,
+                                                     int bits, const unsigned *__restrict__ off,
+                                                     const unsigned *__restrict__ tot,
+                                                     unsigned long long *__restrict__ kout,
+                                                     unsigned *__restrict__ iout) {
+  __shared__ unsigned cnt[NWARP][MAXD];
+  __shared__ unsigned dbase[MAXD];
+  __shared__ unsigned wsum[NWARP];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nd = 1 << bits;
+  {  // digit bases: exclusive scan of tot[0..nd), two digits per thread
+    const unsigned t0 = 2 * tid < nd ? tot[2 * tid] : 0u, t1 = 2 * tid + 1 < nd ? tot[2 * tid + 1] : 0u;
+    unsigned x = t0 + t1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
     if (lane == 31) wsum[w] = x;
     __syncthreads();
-    if (w == 0) {
-      unsigned t = wsum[lane];
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, t, d);
-        if (lane >= d) t += y;
-      }
-      wsum[lane] = t;  // inclusive over warps
-    }
-    __syncthreads();
-    const unsigned before = carry + (w > 0 ? wsum[w - 1] : 0u) + x - tot;
-#pragma unroll 8
-    for (int j = 0; j < 32; ++j) sa[scan_pad(32 * tid + j)] += before;
-    __syncthreads();
-    for (int i = tid; i < n; i += SCAN_NT) a[r + i] = sa[scan_pad(i)];
-    if (tid == 0) carry += wsum[31];
-    __syncthreads();
+    unsigned before = x - t0 - t1;
+    for (int ww = 0; ww < w; ++ww) before += wsum[ww];
+    if (2 * tid < nd) dbase[2 * tid] = before;
+    if (2 * tid + 1 < nd) dbase[2 * tid + 1] = before + t0;
   }
-}
-
-// stable scatter: items keep their order inside a digit
-__global__ void __launch_bounds__(SORT_NT) k_scatter(const unsigned long long *__restrict__ kin,
-                                                     const unsigned *__restrict__ iin, long n, int shift,
-                                                     const unsigned *__restrict__ off,
-                                                     unsigned long long *__restrict__ kout,
-                                                     unsigned *__restrict__ iout) {
-  __shared__ unsigned cnt[NWARP][256];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
-  __syncwarp();
+  for (int d = lane; d < nd; d += 32) cnt[w][d] = 0;
+  __syncthreads();
   const long wbase = (long)blockIdx.x * TILE + (long)w * ITEMS_PER_WARP;
   const unsigned lt = (1u << lane) - 1u;
   // pass 1: per-warp digit counts
   for (int r = 0; r < ITEMS_PER_WARP / 32; ++r) {
     const long i = wbase + r * 32 + lane;
     const bool valid = i < n;
-    const int d = valid ? digit(kin[i], shift) : 256 + lane;  // invalid lanes never match
+    const int d = valid ? digit(kin[i], shift, bits) : MAXD + lane;  // invalid lanes never match
     const unsigned m = __match_any_sync(0xffffffffu, d);
     if (valid && (m & lt) == 0) cnt[w][d] += __popc(m);
     __syncwarp();
   }
   __syncthreads();
   // exclusive prefix over warps, plus the block's global offset for the digit
-  for (int d = tid; d < 256; d += SORT_NT) {
-    unsigned run = off[(long)d * gridDim.x + blockIdx.x];
+  for (int d = tid; d < nd; d += SORT_NT) {
+    unsigned run = dbase[d] + off[(long)d * gridDim.x + blockIdx.x];
     for (int ww = 0; ww < NWARP; ++ww) {
       const unsigned c = cnt[ww][d];
       cnt[ww][d] = run;
@@ -146,7 +139,7 @@ __global__ void __launch_bounds__(SORT_NT) k_scatter(const unsigned long long *_
     const long i = wbase + r * 32 + lane;
     const bool valid = i < n;
     unsigned long long k = valid ? kin[i] : 0ull;
-    const int d = valid ? digit(k, shift) : 256 + lane;
+    const int d = valid ? digit(k, shift, bits) : MAXD + lane;
     const unsigned m = __match_any_sync(0xffffffffu, d);
     if (valid) {
       const unsigned pos = cnt[w][d] + __popc(m & lt);
@@ -169,13 +162,14 @@ __global__ void k_gather(const Blob *__restrict__ b, const unsigned *__restrict_
 
 size_t sort_workspace_bytes(long n) {
   const long nb = (n + TILE - 1) / TILE;
-  return (size_t)n * 2 * (sizeof(unsigned long long) + sizeof(unsigned)) + (size_t)256 * nb * sizeof(unsigned) +
-         256;
+  return (size_t)n * 2 * (sizeof(unsigned long long) + sizeof(unsigned)) +
+         ((size_t)MAXD * nb + MAXD) * sizeof(unsigned) + 256;
 }
 
 // Sort the n candidates of `blobs` into `out` (device) and write the number of
 // records with |response| > thr to *d_npass (device).  `keybits` bounds the
 // real keys: frame, scale, y, x packed as ((frame S + scale) hmax + y) wmax + x.
+// The passes split keybits into equal digits of at most MAXBITS bits.
 int launch_sort(const Blob *blobs, long n, float thr, int nscales, long hmax, long wmax, int keybits,
                 void *work, Blob *out, unsigned *d_npass, Prof *prof, cudaStream_t st) {
   if (n <= 0) return 0;
@@ -186,20 +180,19 @@ int launch_sort(const Blob *blobs, long n, float thr, int nscales, long hmax, lo
   auto *i0 = reinterpret_cast<unsigned *>(k1 + n);
   auto *i1 = i0 + n;
   auto *hist = i1 + n;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCAN_SMEM);
-    attr = true;
-  }
+  auto *tot = hist + (size_t)MAXD * nb;
+  const int npass = std::max(1, (keybits + MAXBITS - 1) / MAXBITS);
+  const int bits = (keybits + npass - 1) / npass;
   cudaMemsetAsync(d_npass, 0, sizeof(unsigned), st);
   prof->begin("sort_keys", st);
   k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(blobs, n, thr, nscales, hmax, wmax, k0, i0, d_npass);
   prof->end(st);
-  for (int shift = 0; shift < keybits; shift += 8) {
+  for (int ps = 0; ps < npass; ++ps) {
+    const int shift = ps * bits, nd = 1 << bits;
     prof->begin("sort_pass", st);
-    k_hist<<<(unsigned)nb, SORT_NT, 0, st>>>(k0, n, shift, hist);
-    k_scan<<<1, SCAN_NT, SCAN_SMEM, st>>>(hist, 256 * nb);
-    k_scatter<<<(unsigned)nb, SORT_NT, 0, st>>>(k0, i0, n, shift, hist, k1, i1);
+    k_hist<<<(unsigned)nb, SORT_NT, 0, st>>>(k0, n, shift, bits, hist);
+    k_scan_digits<<<(unsigned)((nd + NWARP - 1) / NWARP), SORT_NT, 0, st>>>(hist, (int)nb, nd, tot);
+    k_scatter<<<(unsigned)nb, SORT_NT, 0, st>>>(k0, i0, n, shift, bits, hist, tot, k1, i1);
     prof->end(st);
     std::swap(k0, k1);
     std::swap(i0, i1);

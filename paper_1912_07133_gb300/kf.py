@@ -189,6 +189,7 @@ def kf_create(device: int = 0, stream=None) -> int:
 
 def kf_destroy(ctx: int) -> None:
     load().kf_destroy(ctx)
+    _count_guess.pop(ctx, None)
 
 
 def kf_last_error(ctx=None) -> str:
@@ -239,23 +240,39 @@ def kf_filter_bank(ctx: int, frames, scales, ftype: int, order: int, opts: kf_ba
                                  ctypes.byref(opts)), ctx)
 
 
+_count_guess: dict = {}  # ctx -> capacity to offer the next kf_detect_blobs call
+
+
+def _host_records(n: int) -> np.ndarray:
+    """n blob records in page-locked host memory (the device copy runs at full
+    speed into it); plain memory where no CUDA device is present."""
+    if n > 0:
+        import torch
+
+        if torch.cuda.is_available():
+            t = torch.empty(n * BLOB_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+            return t.numpy().view(BLOB_DTYPE)  # the array keeps the pinned block alive
+    return np.empty(n, dtype=BLOB_DTYPE)
+
+
 def kf_detect_blobs(ctx: int, threshold: float, capacity: int = None) -> np.ndarray:
     """Blob list of the last bank call, sorted by (frame, scale, y, x).
 
-    The library orders the list on the GPU and keeps it; the first call (with
-    no output space) returns the count, the second copies exactly that many."""
+    The library orders the list on the GPU and keeps it.  Without a capacity
+    the list is copied into pinned memory sized from the previous call's
+    count: one library call (ordering, count and copy under one stream
+    synchronisation) unless the list outgrew it, when a second call copies
+    the rest of the kept list."""
     L = load()
     n = ctypes.c_int64(0)
-    if capacity is None:
-        rc = L.kf_detect_blobs(ctx, float(threshold), None, 0, ctypes.byref(n))
-        if rc not in (KF_OK, KF_EOVERFLOW):
-            _check(rc, ctx)
-        capacity = int(n.value)
-    out = np.empty(capacity, dtype=BLOB_DTYPE)
-    if capacity == 0:
-        return out
-    rc = L.kf_detect_blobs(ctx, float(threshold), out.ctypes.data_as(ctypes.POINTER(kf_blob)), capacity,
-                           ctypes.byref(n))
+    guessed = capacity is None
+    if guessed:
+        capacity = _count_guess.get(ctx, 1 << 16)
+    out = _host_records(capacity)
+    rc = L.kf_detect_blobs(ctx, float(threshold), out.ctypes.data_as(ctypes.POINTER(kf_blob)) if capacity else None,
+                           capacity, ctypes.byref(n))
+    if guessed and rc in (KF_OK, KF_EOVERFLOW):
+        _count_guess[ctx] = int(n.value) + int(n.value) // 4 + 1024
     if rc == KF_EOVERFLOW and n.value > capacity:
         return kf_detect_blobs(ctx, threshold, int(n.value))
     _check(rc, ctx)
