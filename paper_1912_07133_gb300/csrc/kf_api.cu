@@ -46,11 +46,20 @@ struct kf_ctx {
   Design *cur = nullptr;
   // candidate ordering
   kf::Blob *sorted = nullptr;
+  long sorted_cap = 0;
   void *sort_work = nullptr;
   size_t sort_work_bytes = 0;
   unsigned *d_npass = nullptr;
-  unsigned *h_npass = nullptr;  // pinned: read back with the records, one synchronisation
-  bool sorted_valid = false;
+  // pinned landing place of the status and the count: read with the records
+  // under one synchronisation
+  struct HostRead {
+    kf::DevStatus st;
+    unsigned npass;
+  };
+  HostRead *h_read = nullptr;
+  bool sorted_valid = false;  // an ordering at sorted_thr is enqueued (or done)
+  bool npass_read = false;    // sorted_n holds its count
+  long count_hint = 1 << 16;  // records copied with the first read (the previous count + margin)
   // the device status of the last bank call, read once
   kf::DevStatus last_status{};
   bool status_read = false;
@@ -156,6 +165,41 @@ int grow(kf_ctx *ctx, T **p, size_t *have, size_t need, const char *what) {
   }
   *have = need;
   return KF_OK;
+}
+
+// Ordering buffers for the context's candidate capacity (keys, indices, digit
+// histograms, the ordered list, the count, the pinned read-back); a
+// reallocation drops the captured graphs.
+int ensure_sort(kf_ctx *ctx) {
+  cudaError_t e;
+  const size_t wb = kf::sort_workspace_bytes(ctx->blob_cap);
+  if (!ctx->sort_work || ctx->sort_work_bytes < wb || !ctx->sorted || ctx->sorted_cap < ctx->blob_cap) {
+    drop_graphs(ctx);
+    cudaFree(ctx->sort_work);
+    cudaFree(ctx->sorted);
+    ctx->sort_work = nullptr;
+    ctx->sorted = nullptr;
+    ctx->sort_work_bytes = 0;
+    ctx->sorted_cap = 0;
+    if ((e = cudaMalloc(&ctx->sort_work, wb)) != cudaSuccess) return cuda_fail(ctx, e, "sort workspace");
+    ctx->sort_work_bytes = wb;
+    if ((e = cudaMalloc(&ctx->sorted, sizeof(kf::Blob) * ctx->blob_cap)) != cudaSuccess)
+      return cuda_fail(ctx, e, "sorted blobs");
+    ctx->sorted_cap = ctx->blob_cap;
+  }
+  if (!ctx->d_npass && (e = cudaMalloc(&ctx->d_npass, sizeof(unsigned))) != cudaSuccess)
+    return cuda_fail(ctx, e, "cudaMalloc(npass)");
+  if (!ctx->h_read && (e = cudaMallocHost(&ctx->h_read, sizeof(kf_ctx::HostRead))) != cudaSuccess)
+    return cuda_fail(ctx, e, "cudaMallocHost(status)");
+  return KF_OK;
+}
+
+// Bits of the largest ordering key ((frame S + scale) H + y) W + x.
+int sort_keybits(long nframes, long S, long hmax, long wmax) {
+  const unsigned long long span = (unsigned long long)nframes * S * (unsigned long long)hmax * wmax;
+  int keybits = 0;
+  while (keybits < 64 && (span >> keybits) != 0) ++keybits;
+  return keybits;
 }
 
 int nmax_for(int type, int order, int kmax) {
@@ -371,7 +415,7 @@ void kf_destroy(kf_ctx *ctx) {
   cudaFree(ctx->sorted);
   cudaFree(ctx->sort_work);
   cudaFree(ctx->d_npass);
-  if (ctx->h_npass) cudaFreeHost(ctx->h_npass);
+  if (ctx->h_read) cudaFreeHost(ctx->h_read);
   cudaFree(ctx->lambdas);
   cudaFree(ctx->dwork);
   cudaFree(ctx->status);
@@ -681,7 +725,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     const int rows = iir ? ctx->seg_len[type] : kf::fir_tile_rows(opts.neighbourhood);
     if (kf::gate_select_tiles(plan.fr, full_det, ctx->g_act, TW_COL, rows, ctx->g_sel[0], ctx->g_count, st))
       return cuda_fail(ctx, cudaGetLastError(), "gate selection");
-    if (!iir && kf::gate_select_rows(plan.fr, full_row, ctx->g_act, kf::fir_row_segment(), kf::fir_halo(kmax) + 130,
+    if (!iir && kf::gate_select_rows(plan.fr, full_row, ctx->g_act, kf::fir_row_segment(), kf::fir_row_rows(),
+                                     kf::fir_halo(kmax) + 130,
                                      ctx->g_sel[1], ctx->g_count + 1, st))
       return cuda_fail(ctx, cudaGetLastError(), "gate selection");
     prof->end(st);
@@ -702,7 +747,18 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   a.blobs = ctx->blobs;
   a.cap = ctx->blob_cap;
   a.status = ctx->status;
-  // status reset + all passes, on stream st
+  // the candidate ordering at the bank threshold runs at the end of the call
+  if ((rc = ensure_sort(ctx))) return rc;
+  long wmax = 0;
+  for (int f = 0; f < nframes; ++f) wmax = std::max(wmax, (long)frames[f].width);
+  const int keybits = sort_keybits(nframes, nscales, maxH, wmax);
+  auto issue_sort = [&](cudaStream_t st, kf::Prof *prof) -> int {
+    if (kf::launch_sort(ctx->blobs, ctx->blob_cap, &ctx->status->count, (float)opts.threshold, nscales, maxH, wmax,
+                        keybits, ctx->sort_work, ctx->sorted, ctx->d_npass, prof, st))
+      return cuda_fail(ctx, cudaGetLastError(), "candidate ordering launch");
+    return KF_OK;
+  };
+  // status reset + all passes + ordering, on stream st
   auto issue = [&](cudaStream_t st, kf::Prof *prof) -> int {
     cudaError_t ee;
     if ((ee = cudaMemsetAsync(ctx->status, 0, sizeof(kf::DevStatus), st)) != cudaSuccess)
@@ -713,7 +769,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     const int lr = iir ? kf::launch_iir(plan, a, st) : kf::launch_fir(plan, a, st);
     if (lr == -2) return fail(ctx, KF_EINVAL, "no kernel instance for order %d", order);
     if (lr) return cuda_fail(ctx, cudaGetLastError(), "filter-bank kernel launch");
-    return KF_OK;
+    return issue_sort(st, prof);
   };
   ctx->prof = kf::Prof{};
   ctx->prof.ev = nullptr;
@@ -762,6 +818,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     if (kf::launch_combine_detect(plan, plan.comb, a, opts.response == KF_RESP_HESSIAN, c20, c02, c11, c10, c01,
                                   opts.offset_limit, ctx->stream))
       return cuda_fail(ctx, cudaGetLastError(), "derivative bank detector");
+    if ((rc = issue_sort(ctx->stream, &ctx->prof))) return rc;
   } else if (opts.graph && !opts.profile) {
     const std::vector<long long> key = call_key(ctx, frames, nframes, scales, nscales, type, order, kmax_opt, opts);
     kf_ctx::Graph *g = nullptr;
@@ -813,14 +870,15 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     if ((rc = issue(ctx->stream, &ctx->prof))) return rc;
   }
   ctx->have_result = true;
-  ctx->sorted_valid = false;
+  ctx->sorted_valid = true;  // enqueued with the call
+  ctx->sorted_thr = opts.threshold;
+  ctx->npass_read = false;
   ctx->status_read = false;
   ctx->last_threshold = opts.threshold;
   ctx->last_S = nscales;
   ctx->last_nframes = nframes;
   ctx->last_hmax = maxH;
-  ctx->last_wmax = 0;
-  for (int f = 0; f < nframes; ++f) ctx->last_wmax = std::max(ctx->last_wmax, (long)frames[f].width);
+  ctx->last_wmax = wmax;
   ctx->last_H.resize(nframes);
   ctx->last_W.resize(nframes);
   for (int f = 0; f < nframes; ++f) ctx->last_H[f] = frames[f].height, ctx->last_W[f] = frames[f].width;
@@ -1155,13 +1213,42 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
                 ctx->last_threshold);
   cudaError_t e;
   if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
-  kf::DevStatus &st = ctx->last_status;
+  // A new threshold: order again (device-sized, enqueued without the count).
+  if (!ctx->sorted_valid || ctx->sorted_thr != threshold) {
+    int rc;
+    if ((rc = ensure_sort(ctx))) return rc;
+    const int keybits = sort_keybits(ctx->last_nframes, ctx->last_S, ctx->last_hmax, ctx->last_wmax);
+    kf::Prof none{};
+    if (kf::launch_sort(ctx->blobs, ctx->blob_cap, &ctx->status->count, (float)threshold, ctx->last_S,
+                        ctx->last_hmax, ctx->last_wmax, keybits, ctx->sort_work, ctx->sorted, ctx->d_npass, &none,
+                        ctx->stream))
+      return cuda_fail(ctx, cudaGetLastError(), "sort launch");
+    ctx->sorted_valid = true;
+    ctx->sorted_thr = threshold;
+    ctx->npass_read = false;
+  }
+  // One synchronisation for the status, the count and the records: until the
+  // count is known, the first min(capacity, count_hint) records are copied
+  // with them; a longer list is completed by a second copy.
+  kf_ctx::HostRead *hr = ctx->h_read;
+  if (!ctx->status_read &&
+      (e = cudaMemcpyAsync(&hr->st, ctx->status, sizeof hr->st, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "read status");
+  if (!ctx->npass_read && (e = cudaMemcpyAsync(&hr->npass, ctx->d_npass, sizeof hr->npass, cudaMemcpyDeviceToHost,
+                                               ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "read count");
+  const int64_t first = std::min<int64_t>({capacity, ctx->npass_read ? (int64_t)ctx->sorted_n : ctx->count_hint,
+                                           (int64_t)ctx->sorted_cap});
+  static_assert(sizeof(kf_blob) == sizeof(kf::Blob), "record layout");
+  if (first > 0 && (e = cudaMemcpyAsync(out, ctx->sorted, sizeof(kf::Blob) * first, cudaMemcpyDeviceToHost,
+                                        ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "copy blobs");
+  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "filter bank / ordering");
   if (!ctx->status_read) {
-    if ((e = cudaMemcpyAsync(&st, ctx->status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
-      return cuda_fail(ctx, e, "read status");
-    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "filter bank");
+    ctx->last_status = hr->st;
     ctx->status_read = true;
   }
+  const kf::DevStatus &st = ctx->last_status;
   if (st.error) return fail(ctx, KF_ETIMEOUT, "device wait gave up (code %d)", st.error);
   if (st.range)
     return fail(ctx, KF_ERANGE,
@@ -1179,61 +1266,24 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
     }
     ctx->blob_cap = ncap;
     ctx->have_result = false;
+    ctx->sorted_valid = false;
     return fail(ctx, KF_ERERUN,
                 "candidate list overflowed (%llu found); capacity raised, run the bank again",
                 (unsigned long long)st.count);
   }
-  const long n = (long)st.count;
-  // A new ordering (first call after a bank call, or a new threshold) is
-  // sorted, counted and copied under one synchronisation: the copy takes up to
-  // n records (the passing ones come first), the count arrives with it.
-  const bool fresh = !ctx->sorted_valid || ctx->sorted_thr != threshold;
-  if (fresh) {
-    ctx->sorted_valid = false;
-    ctx->sorted_n = 0;
-    if (n > 0) {
-      const size_t wb = kf::sort_workspace_bytes(ctx->blob_cap);
-      if (!ctx->sort_work || ctx->sort_work_bytes < wb) {
-        cudaFree(ctx->sort_work);
-        cudaFree(ctx->sorted);
-        ctx->sort_work = nullptr;
-        ctx->sorted = nullptr;
-        ctx->sort_work_bytes = 0;
-        if ((e = cudaMalloc(&ctx->sort_work, wb)) != cudaSuccess) return cuda_fail(ctx, e, "sort workspace");
-        if ((e = cudaMalloc(&ctx->sorted, sizeof(kf::Blob) * ctx->blob_cap)) != cudaSuccess)
-          return cuda_fail(ctx, e, "sorted blobs");
-        ctx->sort_work_bytes = wb;
-      }
-      if (!ctx->d_npass && (e = cudaMalloc(&ctx->d_npass, sizeof(unsigned))) != cudaSuccess)
-        return cuda_fail(ctx, e, "cudaMalloc(npass)");
-      if (!ctx->h_npass && (e = cudaMallocHost(&ctx->h_npass, sizeof(unsigned))) != cudaSuccess)
-        return cuda_fail(ctx, e, "cudaMallocHost(npass)");
-      const unsigned long long span = (unsigned long long)ctx->last_nframes * ctx->last_S *
-                                      (unsigned long long)ctx->last_hmax * ctx->last_wmax;
-      int keybits = 0;
-      while (keybits < 64 && (span >> keybits) != 0) ++keybits;
-      kf::Prof none{};
-      if (kf::launch_sort(ctx->blobs, n, (float)threshold, ctx->last_S, ctx->last_hmax, ctx->last_wmax,
-                          keybits, ctx->sort_work, ctx->sorted, ctx->d_npass, &none, ctx->stream))
-        return cuda_fail(ctx, cudaGetLastError(), "sort launch");
-      if ((e = cudaMemcpyAsync(ctx->h_npass, ctx->d_npass, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                               ctx->stream)) != cudaSuccess)
-        return cuda_fail(ctx, e, "read count");
-    }
-  }
-  const int64_t ncopy = std::min<int64_t>(capacity, fresh ? (int64_t)n : (int64_t)ctx->sorted_n);
-  static_assert(sizeof(kf_blob) == sizeof(kf::Blob), "record layout");
-  if (ncopy > 0 && (e = cudaMemcpyAsync(out, ctx->sorted, sizeof(kf::Blob) * ncopy, cudaMemcpyDeviceToHost,
-                                        ctx->stream)) != cudaSuccess)
-    return cuda_fail(ctx, e, "copy blobs");
-  if ((ncopy > 0 || (fresh && n > 0)) && (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
-    return cuda_fail(ctx, e, "sort / copy blobs");
-  if (fresh) {
-    ctx->sorted_n = n > 0 ? (long)*ctx->h_npass : 0;
-    ctx->sorted_valid = true;
-    ctx->sorted_thr = threshold;
+  if (!ctx->npass_read) {
+    ctx->sorted_n = (long)hr->npass;
+    ctx->npass_read = true;
+    ctx->count_hint = ctx->sorted_n + ctx->sorted_n / 8 + 1024;
   }
   *count = (int64_t)ctx->sorted_n;
+  const int64_t all = std::min<int64_t>(capacity, ctx->sorted_n);
+  if (all > first) {
+    if ((e = cudaMemcpyAsync(out + first, ctx->sorted + first, sizeof(kf::Blob) * (all - first),
+                             cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "copy blobs");
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "copy blobs");
+  }
   if (ctx->sorted_n > capacity)
     return fail(ctx, KF_EOVERFLOW, "capacity %lld < %lld blobs", (long long)capacity,
                 (long long)ctx->sorted_n);

@@ -718,6 +718,7 @@ int persistent_blocks(const void *kernel, int threads, size_t smem, int items, i
 }
 
 int fir_row_segment() { return RSEG; }
+int fir_row_rows() { return 1; }
 int fir_tile_rows(int neigh) { return neigh == 0 ? CROWS2 - 2 : CROWS - 2; }
 int fir_halo(int kmax) { return kmax + TB + 1; }
 

@@ -123,16 +123,17 @@ int gate_tiles(const float *z, int S, int th, int tw, float zthr, int dilate, un
                cudaStream_t st);
 int gate_select_tiles(const FrameDev *fr, const Items &full, const unsigned char *act, int tw, int th, int2 *sel,
                       int *count, cudaStream_t st);
-int gate_select_rows(const FrameDev *fr, const Items &full, const unsigned char *act, int rseg, int reach,
-                     int2 *sel, int *count, cudaStream_t st);
+int gate_select_rows(const FrameDev *fr, const Items &full, const unsigned char *act, int rseg, int rrows,
+                     int reach, int2 *sel, int *count, cudaStream_t st);
 // geometry of the gated passes
-int fir_row_segment();         // pixels per FIR row item
+int fir_row_segment();         // outputs per row of a FIR row item
+int fir_row_rows();            // rows of a FIR row item (items past the frame rows: its two U-only edge rows)
 int fir_tile_rows(int neigh);  // interior rows of a FIR column tile
 int fir_halo(int kmax);        // rows a FIR column tile reads beyond its 128 (or 64) rows
 
 // candidate ordering (kf_sort.cu)
-size_t sort_workspace_bytes(long n);
-int launch_sort(const Blob *blobs, long n, float thr, int nscales, long hmax, long wmax, int keybits,
-                void *work, Blob *out, unsigned *d_npass, Prof *prof, cudaStream_t st);
+size_t sort_workspace_bytes(long cap);
+int launch_sort(const Blob *blobs, long cap, const unsigned long long *count, float thr, int nscales, long hmax,
+                long wmax, int keybits, void *work, Blob *out, unsigned *d_npass, Prof *prof, cudaStream_t st);
 
 }  // namespace kf

@@ -400,19 +400,20 @@ __global__ void k_sel_tiles(const FrameDev *__restrict__ fr, Items full, const u
   if (any_active(F, act, x0, x0 + tw, y0, y0 + th)) sel[atomicAdd(count, 1)] = make_int2(k, local);
 }
 
-// Items of the FIR row pass ((row, segment of rseg pixels) = item row nxs + seg;
-// rows H and H+1: the U-only edge rows, always kept): a row is needed if an
-// active tile lies within `reach` rows of it in the segment's columns +- 64
+// Items of the FIR row pass (rrows virtual rows x rseg outputs, item =
+// row block nxs + segment; a block holding the U-only edge rows H and H+1 is
+// always kept): a block is needed if an active tile lies within `reach` rows
+// of it in the segment's columns +- 64
 __global__ void k_sel_rows(const FrameDev *__restrict__ fr, Items full, const unsigned char *__restrict__ act,
-                           int rseg, int reach, int2 *__restrict__ sel, int *__restrict__ count) {
+                           int rseg, int rrows, int reach, int2 *__restrict__ sel, int *__restrict__ count) {
   const int item = blockIdx.x * blockDim.x + threadIdx.x;
   if (item >= full.total) return;
   const int k = find_frame(full, item);
   const FrameDev &F = fr[__ldg(full.fl + k)];
   const int local = item - __ldg(full.pre + k);
   const int nxs = (F.W + rseg - 1) / rseg;
-  const int xs = (local % nxs) * rseg, y = local / nxs;
-  if (y >= F.H || any_active(F, act, xs - 64, xs + rseg + 64, y - reach, y + reach + 1))
+  const int xs = (local % nxs) * rseg, y0 = (local / nxs) * rrows;
+  if (y0 + rrows > F.H || any_active(F, act, xs - 64, xs + rseg + 64, y0 - reach, y0 + rrows + reach))
     sel[atomicAdd(count, 1)] = make_int2(k, local);
 }
 
@@ -559,10 +560,10 @@ int gate_select_tiles(const FrameDev *fr, const Items &full, const unsigned char
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-int gate_select_rows(const FrameDev *fr, const Items &full, const unsigned char *act, int rseg, int reach,
-                     int2 *sel, int *count, cudaStream_t st) {
+int gate_select_rows(const FrameDev *fr, const Items &full, const unsigned char *act, int rseg, int rrows,
+                     int reach, int2 *sel, int *count, cudaStream_t st) {
   if (full.total > 0)
-    k_sel_rows<<<(full.total + 255) / 256, 256, 0, st>>>(fr, full, act, rseg, reach, sel, count);
+    k_sel_rows<<<(full.total + 255) / 256, 256, 0, st>>>(fr, full, act, rseg, rrows, reach, sel, count);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -3,6 +3,10 @@
 // (frame, scale, y, x) order.  Least-significant-digit radix sort of 64-bit
 // keys with digits of up to 9 bits (stable per pass), then a gather of the records.
 // Candidates at or below the re-threshold get the all-ones key and sort last.
+// Every launch reads the candidate count from the device status and loops
+// over the list's 1024-item tiles (grids of at most a few blocks per SM), so
+// the ordering can be enqueued (and captured in a graph) before the count is
+// known on the host.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,49 +27,60 @@ constexpr int ITEMS_PER_WARP = TILE / NWARP;
 constexpr int MAXBITS = 9;                 // digit width per pass (<= 9 bits: 512 digits)
 constexpr int MAXD = 1 << MAXBITS;
 
-__global__ void k_keys(const Blob *__restrict__ b, long n, float thr, int nscales, long hmax, long wmax,
-                       unsigned long long *__restrict__ key, unsigned *__restrict__ idx,
-                       unsigned *__restrict__ npass) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const Blob r = b[i];
-  const bool pass = fabsf(r.response) > thr;
-  unsigned long long k = ~0ull;
-  if (pass) {
-    k = (((unsigned long long)r.frame * nscales + r.scale) * hmax + r.y) * wmax + r.x;
-    atomicAdd(npass, 1u);
+// candidates to order: the device count, clamped to the list's capacity
+__device__ __forceinline__ long list_n(const unsigned long long *count, long cap) {
+  return (long)min(*count, (unsigned long long)cap);
+}
+
+__global__ void k_keys(const Blob *__restrict__ b, long cap, const unsigned long long *__restrict__ count, float thr,
+                       int nscales, long hmax, long wmax, unsigned long long *__restrict__ key,
+                       unsigned *__restrict__ idx, unsigned *__restrict__ npass) {
+  const long n = list_n(count, cap);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const Blob r = b[i];
+    const bool pass = fabsf(r.response) > thr;
+    unsigned long long k = ~0ull;
+    if (pass) {
+      k = (((unsigned long long)r.frame * nscales + r.scale) * hmax + r.y) * wmax + r.x;
+      atomicAdd(npass, 1u);
+    }
+    key[i] = k;
+    idx[i] = (unsigned)i;
   }
-  key[i] = k;
-  idx[i] = (unsigned)i;
 }
 
 __device__ __forceinline__ int digit(unsigned long long k, int shift, int bits) {
   return (int)((k >> shift) & ((1ull << bits) - 1ull));
 }
 
-// per-block digit histogram: hist[d * nblocks + block]
-__global__ void __launch_bounds__(SORT_NT) k_hist(const unsigned long long *__restrict__ key, long n, int shift,
-                                                  int bits, unsigned *__restrict__ hist) {
+// per-tile digit histogram: hist[d * stride + tile]
+__global__ void __launch_bounds__(SORT_NT) k_hist(const unsigned long long *__restrict__ key, long cap,
+                                                  const unsigned long long *__restrict__ count, int shift, int bits,
+                                                  unsigned *__restrict__ hist, int stride) {
   __shared__ unsigned h[MAXD];
+  const long n = list_n(count, cap);
   const int tid = threadIdx.x, nd = 1 << bits;
-  for (int d = tid; d < nd; d += SORT_NT) h[d] = 0;
-  __syncthreads();
-  const long base = (long)blockIdx.x * TILE;
-  for (int j = 0; j < SORT_ITEMS; ++j) {
-    const long i = base + (long)j * SORT_NT + tid;
-    if (i < n) atomicAdd(&h[digit(key[i], shift, bits)], 1u);
+  for (long t = blockIdx.x; t * TILE < n; t += gridDim.x) {  // uniform over the block
+    for (int d = tid; d < nd; d += SORT_NT) h[d] = 0;
+    __syncthreads();
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+      const long i = t * TILE + (long)j * SORT_NT + tid;
+      if (i < n) atomicAdd(&h[digit(key[i], shift, bits)], 1u);
+    }
+    __syncthreads();
+    for (int d = tid; d < nd; d += SORT_NT) hist[(long)d * stride + t] = h[d];
   }
-  __syncthreads();
-  for (int d = tid; d < nd; d += SORT_NT) hist[(long)d * gridDim.x + blockIdx.x] = h[d];
 }
 
-// One warp per digit d: exclusive scan of hist[d * nb + (0..nb)] over the
-// blocks, in place, and the digit's total in tot[d].
-__global__ void __launch_bounds__(SORT_NT) k_scan_digits(unsigned *__restrict__ hist, int nb, int nd,
+// One warp per digit d: exclusive scan of hist[d * stride + (0..nb)] over
+// the nb blocks that hold items, in place, and the digit's total in tot[d].
+__global__ void __launch_bounds__(SORT_NT) k_scan_digits(unsigned *__restrict__ hist, int stride, int nd, long cap,
+                                                         const unsigned long long *__restrict__ count,
                                                          unsigned *__restrict__ tot) {
   const int lane = threadIdx.x & 31, d = blockIdx.x * NWARP + (threadIdx.x >> 5);
   if (d >= nd) return;
-  unsigned *h = hist + (long)d * nb;
+  const int nb = (int)((list_n(count, cap) + TILE - 1) / TILE);
+  unsigned *h = hist + (long)d * stride;
   unsigned carry = 0;
   for (int b0 = 0; b0 < nb; b0 += 32) {
     const int b = b0 + lane;
@@ -86,14 +101,17 @@ __global__ void __launch_bounds__(SORT_NT) k_scan_digits(unsigned *__restrict__ 
 // position is the sum of the totals of the smaller digits (a block scan of
 // tot) plus the earlier blocks' counts of it (hist, scanned)
 __global__ void __launch_bounds__(SORT_NT) k_scatter(const unsigned long long *__restrict__ kin,
-                                                     const unsigned *__restrict__ iin, long n, int shift,
-                                                     int bits, const unsigned *__restrict__ off,
+                                                     const unsigned *__restrict__ iin, long cap,
+                                                     const unsigned long long *__restrict__ count, int shift,
+                                                     int bits, const unsigned *__restrict__ off, int stride,
                                                      const unsigned *__restrict__ tot,
                                                      unsigned long long *__restrict__ kout,
                                                      unsigned *__restrict__ iout) {
   __shared__ unsigned cnt[NWARP][MAXD];
   __shared__ unsigned dbase[MAXD];
   __shared__ unsigned wsum[NWARP];
+  const long n = list_n(count, cap);
+  if ((long)blockIdx.x * TILE >= n) return;  // uniform over the block
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nd = 1 << bits;
   {  // digit bases: exclusive scan of tot[0..nd), two digits per thread
     const unsigned t0 = 2 * tid < nd ? tot[2 * tid] : 0u, t1 = 2 * tid + 1 < nd ? tot[2 * tid + 1] : 0u;
@@ -110,52 +128,56 @@ __global__ void __launch_bounds__(SORT_NT) k_scatter(const unsigned long long *_
     if (2 * tid < nd) dbase[2 * tid] = before;
     if (2 * tid + 1 < nd) dbase[2 * tid + 1] = before + t0;
   }
-  for (int d = lane; d < nd; d += 32) cnt[w][d] = 0;
-  __syncthreads();
-  const long wbase = (long)blockIdx.x * TILE + (long)w * ITEMS_PER_WARP;
   const unsigned lt = (1u << lane) - 1u;
-  // pass 1: per-warp digit counts
-  for (int r = 0; r < ITEMS_PER_WARP / 32; ++r) {
-    const long i = wbase + r * 32 + lane;
-    const bool valid = i < n;
-    const int d = valid ? digit(kin[i], shift, bits) : MAXD + lane;  // invalid lanes never match
-    const unsigned m = __match_any_sync(0xffffffffu, d);
-    if (valid && (m & lt) == 0) cnt[w][d] += __popc(m);
-    __syncwarp();
-  }
-  __syncthreads();
-  // exclusive prefix over warps, plus the block's global offset for the digit
-  for (int d = tid; d < nd; d += SORT_NT) {
-    unsigned run = dbase[d] + off[(long)d * gridDim.x + blockIdx.x];
-    for (int ww = 0; ww < NWARP; ++ww) {
-      const unsigned c = cnt[ww][d];
-      cnt[ww][d] = run;
-      run += c;
+  for (long t = blockIdx.x; t * TILE < n; t += gridDim.x) {  // uniform over the block
+    for (int d = lane; d < nd; d += 32) cnt[w][d] = 0;
+    __syncthreads();
+    const long wbase = t * TILE + (long)w * ITEMS_PER_WARP;
+    // pass 1: per-warp digit counts
+    for (int r = 0; r < ITEMS_PER_WARP / 32; ++r) {
+      const long i = wbase + r * 32 + lane;
+      const bool valid = i < n;
+      const int d = valid ? digit(kin[i], shift, bits) : MAXD + lane;  // invalid lanes never match
+      const unsigned m = __match_any_sync(0xffffffffu, d);
+      if (valid && (m & lt) == 0) cnt[w][d] += __popc(m);
+      __syncwarp();
     }
-  }
-  __syncthreads();
-  // pass 2: positions
-  for (int r = 0; r < ITEMS_PER_WARP / 32; ++r) {
-    const long i = wbase + r * 32 + lane;
-    const bool valid = i < n;
-    unsigned long long k = valid ? kin[i] : 0ull;
-    const int d = valid ? digit(k, shift, bits) : MAXD + lane;
-    const unsigned m = __match_any_sync(0xffffffffu, d);
-    if (valid) {
-      const unsigned pos = cnt[w][d] + __popc(m & lt);
-      kout[pos] = k;
-      iout[pos] = iin[i];
+    __syncthreads();
+    // exclusive prefix over warps, plus the tile's global offset for the digit
+    for (int d = tid; d < nd; d += SORT_NT) {
+      unsigned run = dbase[d] + off[(long)d * stride + t];
+      for (int ww = 0; ww < NWARP; ++ww) {
+        const unsigned c = cnt[ww][d];
+        cnt[ww][d] = run;
+        run += c;
+      }
     }
-    __syncwarp();
-    if (valid && (m & lt) == 0) cnt[w][d] += __popc(m);
-    __syncwarp();
+    __syncthreads();
+    // pass 2: positions
+    for (int r = 0; r < ITEMS_PER_WARP / 32; ++r) {
+      const long i = wbase + r * 32 + lane;
+      const bool valid = i < n;
+      unsigned long long k = valid ? kin[i] : 0ull;
+      const int d = valid ? digit(k, shift, bits) : MAXD + lane;
+      const unsigned m = __match_any_sync(0xffffffffu, d);
+      if (valid) {
+        const unsigned pos = cnt[w][d] + __popc(m & lt);
+        kout[pos] = k;
+        iout[pos] = iin[i];
+      }
+      __syncwarp();
+      if (valid && (m & lt) == 0) cnt[w][d] += __popc(m);
+      __syncwarp();
+    }
+    __syncthreads();  // cnt is reset for the next tile
   }
 }
 
-__global__ void k_gather(const Blob *__restrict__ b, const unsigned *__restrict__ idx, long n,
-                         Blob *__restrict__ out) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = b[idx[i]];
+__global__ void k_gather(const Blob *__restrict__ b, const unsigned *__restrict__ idx, long cap,
+                         const unsigned long long *__restrict__ count, Blob *__restrict__ out) {
+  const long n = list_n(count, cap);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = b[idx[i]];
 }
 
 }  // namespace
@@ -166,39 +188,49 @@ size_t sort_workspace_bytes(long n) {
          ((size_t)MAXD * nb + MAXD) * sizeof(unsigned) + 256;
 }
 
-// Sort the n candidates of `blobs` into `out` (device) and write the number of
-// records with |response| > thr to *d_npass (device).  `keybits` bounds the
-// real keys: frame, scale, y, x packed as ((frame S + scale) hmax + y) wmax + x.
-// The passes split keybits into equal digits of at most MAXBITS bits.
-int launch_sort(const Blob *blobs, long n, float thr, int nscales, long hmax, long wmax, int keybits,
-                void *work, Blob *out, unsigned *d_npass, Prof *prof, cudaStream_t st) {
-  if (n <= 0) return 0;
-  const long nb = (n + TILE - 1) / TILE;
+// Sort the first min(*count, cap) candidates of `blobs` (count: device) into
+// `out` (device) and write the number of records with |response| > thr to
+// *d_npass (device).  `keybits` bounds the real keys: frame, scale, y, x
+// packed as ((frame S + scale) hmax + y) wmax + x.  The passes split keybits
+// into equal digits of at most MAXBITS bits.  Work: sort_workspace_bytes(cap).
+int launch_sort(const Blob *blobs, long cap, const unsigned long long *count, float thr, int nscales, long hmax,
+                long wmax, int keybits, void *work, Blob *out, unsigned *d_npass, Prof *prof, cudaStream_t st) {
+  if (cap <= 0) return 0;
+  const long nb = (cap + TILE - 1) / TILE;
   char *p = static_cast<char *>(work);
   auto *k0 = reinterpret_cast<unsigned long long *>(p);
-  auto *k1 = k0 + n;
-  auto *i0 = reinterpret_cast<unsigned *>(k1 + n);
-  auto *i1 = i0 + n;
-  auto *hist = i1 + n;
+  auto *k1 = k0 + cap;
+  auto *i0 = reinterpret_cast<unsigned *>(k1 + cap);
+  auto *i1 = i0 + cap;
+  auto *hist = i1 + cap;
   auto *tot = hist + (size_t)MAXD * nb;
   const int npass = std::max(1, (keybits + MAXBITS - 1) / MAXBITS);
   const int bits = (keybits + npass - 1) / npass;
-  cudaMemsetAsync(d_npass, 0, sizeof(unsigned), st);
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return -1;
+  const unsigned ng = (unsigned)std::min<long>((cap + 255) / 256, 4L * nsm);  // element loops
+  const unsigned nt = (unsigned)std::min<long>(nb, 2L * nsm);                 // tile loops
+  if (cudaMemsetAsync(d_npass, 0, sizeof(unsigned), st) != cudaSuccess) return -1;
   prof->begin("sort_keys", st);
-  k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(blobs, n, thr, nscales, hmax, wmax, k0, i0, d_npass);
+  k_keys<<<ng, 256, 0, st>>>(blobs, cap, count, thr, nscales, hmax, wmax, k0, i0, d_npass);
   prof->end(st);
   for (int ps = 0; ps < npass; ++ps) {
     const int shift = ps * bits, nd = 1 << bits;
-    prof->begin("sort_pass", st);
-    k_hist<<<(unsigned)nb, SORT_NT, 0, st>>>(k0, n, shift, bits, hist);
-    k_scan_digits<<<(unsigned)((nd + NWARP - 1) / NWARP), SORT_NT, 0, st>>>(hist, (int)nb, nd, tot);
-    k_scatter<<<(unsigned)nb, SORT_NT, 0, st>>>(k0, i0, n, shift, bits, hist, tot, k1, i1);
+    prof->begin("sort_hist", st);
+    k_hist<<<nt, SORT_NT, 0, st>>>(k0, cap, count, shift, bits, hist, (int)nb);
+    prof->end(st);
+    prof->begin("sort_scan", st);
+    k_scan_digits<<<(unsigned)((nd + NWARP - 1) / NWARP), SORT_NT, 0, st>>>(hist, (int)nb, nd, cap, count, tot);
+    prof->end(st);
+    prof->begin("sort_scatter", st);
+    k_scatter<<<nt, SORT_NT, 0, st>>>(k0, i0, cap, count, shift, bits, hist, (int)nb, tot, k1, i1);
     prof->end(st);
     std::swap(k0, k1);
     std::swap(i0, i1);
   }
   prof->begin("sort_gather", st);
-  k_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(blobs, i0, n, out);
+  k_gather<<<ng, 256, 0, st>>>(blobs, i0, cap, count, out);
   prof->end(st);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
