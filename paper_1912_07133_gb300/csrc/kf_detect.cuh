@@ -101,8 +101,8 @@ static __device__ __forceinline__ bool beats_neighbours(const float *m, const un
 // (argmin); it must beat the 8 neighbours' extremes with the tie rule.
 // Each warp walks a band of interior rows, one column per lane, holding the
 // horizontal 3-maxima (3-minima, by shuffles) of three consecutive rows in
-// registers: a pixel below its 3 x 3 maximum cannot pass, and the rest take
-// the exact tie test.  Candidates are staged in shared memory and reserved
+// registers: a pixel below its 3 x 3 maximum cannot pass, one strictly above
+// its 8 neighbours passes, and the rest (ties) take the exact tie test.  Candidates are staged in shared memory and reserved
 // globally once per tile.  Must be called by all threads of the block
 // (blockDim a multiple of 32; contains __syncthreads).
 static __device__ void spatial_detect(const float *mx, const float *mn, const unsigned char *amx,
@@ -117,28 +117,34 @@ static __device__ void spatial_detect(const float *mx, const float *mn, const un
   const int x = a.x0 + lane;
   const bool col = lane >= 1 && lane <= 30 && x >= 0 && x < a.W;
   constexpr unsigned FULL = 0xffffffffu;
-  auto hmax = [&](float v) { return fmaxf(v, fmaxf(__shfl_up_sync(FULL, v, 1), __shfl_down_sync(FULL, v, 1))); };
-  auto hmin = [&](float v) { return fminf(v, fminf(__shfl_up_sync(FULL, v, 1), __shfl_down_sync(FULL, v, 1))); };
+  // maximum (minimum) of the left and right neighbours
+  auto lrmax = [&](float v) { return fmaxf(__shfl_up_sync(FULL, v, 1), __shfl_down_sync(FULL, v, 1)); };
+  auto lrmin = [&](float v) { return fminf(__shfl_up_sync(FULL, v, 1), __shfl_down_sync(FULL, v, 1)); };
   if (ib < ie) {
-    float xa = hmax(mx[(ib - 1) * 32 + lane]), na = hmin(mn[(ib - 1) * 32 + lane]);
+    float vp = mx[(ib - 1) * 32 + lane], wp = mn[(ib - 1) * 32 + lane];
+    float xa = fmaxf(vp, lrmax(vp)), na = fminf(wp, lrmin(wp));  // row i - 1: 3-maximum (minimum)
     float vc = mx[ib * 32 + lane], wc = mn[ib * 32 + lane];
-    float xb = hmax(vc), nb = hmin(wc);
+    float lx = lrmax(vc), ln = lrmin(wc);  // row i: the two side neighbours
     for (int i = ib; i < ie; ++i) {
       const float vn = mx[(i + 1) * 32 + lane], wn = mn[(i + 1) * 32 + lane];
-      const float xc = hmax(vn), nc = hmin(wn);
+      const float lxn = lrmax(vn), lnn = lrmin(wn);
+      const float xc = fmaxf(vn, lxn), nc = fminf(wn, lnn);  // row i + 1
       const int y = a.r0 + i;
       if (col && y >= 0 && y < a.H) {
         const int p = i * 32 + lane;
-        if (vc > a.thr && vc >= fmaxf(xa, fmaxf(xb, xc))) {
+        const float m8 = fmaxf(xa, fmaxf(lx, xc));  // maximum of the 8 neighbours
+        if (vc > a.thr && vc >= m8) {
           const int s = amx[p];
-          if (beats_neighbours(mx, amx, p, 1, vc, s)) emit_blob(a, tl, s, y, x, 1, vc);
+          if (vc > m8 || beats_neighbours(mx, amx, p, 1, vc, s)) emit_blob(a, tl, s, y, x, 1, vc);
         }
-        if (a.dark && -wc > a.thr && wc <= fminf(na, fminf(nb, nc))) {
+        const float n8 = fminf(na, fminf(ln, nc));
+        if (a.dark && -wc > a.thr && wc <= n8) {
           const int s = amn[p];
-          if (beats_neighbours(mn, amn, p, -1, wc, s)) emit_blob(a, tl, s, y, x, -1, wc);
+          if (wc < n8 || beats_neighbours(mn, amn, p, -1, wc, s)) emit_blob(a, tl, s, y, x, -1, wc);
         }
       }
-      xa = xb, xb = xc, na = nb, nb = nc, vc = vn, wc = wn;
+      xa = fmaxf(vc, lx), na = fminf(wc, ln);
+      vc = vn, wc = wn, lx = lxn, ln = lnn;
     }
   }
   __syncthreads();

@@ -427,6 +427,12 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
   uint32_t ph0 = 0u, ph1 = 0u;  // phase to wait for, per barrier
   int k = 0;
   const int nitems = items_total(it);
+  // The stages alternate over the block's whole sequence of (item, scale)
+  // loads: `base` counts the scales of the earlier items.  f32 planes: the
+  // next item's first scale is loaded during this item's last scale
+  // (`pre`), and this item's extremes go to the stage of its last scale.
+  int base = 0;
+  bool pre = false;
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     int local;
     k = item_frame(it, item, k, local);
@@ -452,27 +458,41 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
       amx[p] = (unsigned char)S;
       amn[p] = (unsigned char)S;
     }
-    auto issue = [&](int s, int b) {  // thread 0 only
+    // scale s of a tile (plane rows of frame row r0_, box column xa_) into stage b
+    auto issue_at = [&](int s, int b, long prow_, int H_, int r0_, int xa_) {  // thread 0 only
       const int G = coef[s].K + TB;
       const int nb = (CROWS2 + 2 * G + BOXH - 1) / BOXH;
       fence_proxy_async();
       mbar_arrive_expect_tx(&mbar[b], (uint32_t)(nb * BOXH * BW * sizeof(T)));
-      const int y0 = (int)(prow + (long)s * H + r0 - G);
+      const int y0 = (int)(prow_ + (long)s * H_ + r0_ - G);
       for (int i = 0; i < nb; ++i)
-        if (!tma_load_2d(land(b) + i * BOXH * BW, &map, xa, y0 + i * BOXH, &mbar[b], (int)sizeof(T)))
+        if (!tma_load_2d(land(b) + i * BOXH * BW, &map, xa_, y0 + i * BOXH, &mbar[b], (int)sizeof(T)))
           atomicExch(&da.status->error, 2);
     };
+    auto issue = [&](int s, int b) { issue_at(s, b, prow, H, r0, xa); };
+    const int next = item + gridDim.x;
     // scales from the longest filter down (the order of the caller's scales is
     // kept for ties: the first scale attaining an extreme is the one reported)
     if (tid == 0) {
-      issue(S - 1, 0);
-      if (!F32 && S > 1) issue(S - 2, 1);
+      if (!pre) issue(S - 1, base & 1);
+      if (!F32 && S > 1) issue(S - 2, (base + 1) & 1);
     }
     const long plane = (long)H * W;
     for (int is = 0; is < S; ++is) {
       const int s = S - 1 - is;
-      const int b = is & 1;
-      if (F32 && tid == 0 && is + 1 < S) issue(s - 1, b ^ 1);
+      const int b = (base + is) & 1;
+      if (F32 && tid == 0) {
+        if (is + 1 < S) {
+          issue(s - 1, b ^ 1);
+        } else if (next < nitems) {  // the next item's first scale
+          int ln;
+          const int kq = item_frame(it, next, k, ln);
+          const FrameDev &Fn = fr[__ldg(it.fl + kq)];
+          const int Hn = Fn.H, ntxn = (Fn.W + TW - 1) / TW;
+          const int x0n = (ln % ntxn) * TW - 1, r0n = (ln / ntxn) * (CROWS2 - 2) - 1;
+          issue_at(S - 1, b ^ 1, Fn.prow, Hn, r0n, x0n - ((x0n % XA) + XA) % XA);
+        }
+      }
       const Coef &c = coef[s];
       const int K = c.K, G = K + TB, nin = CROWS2 + 2 * G;
       // R_L = -sigma^2 (D20 + D02) with the planes carrying sigma^2: the taps
@@ -485,7 +505,7 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
         // a load never completed: report, let the other stage's load finish, stop
         if (tid == 0) {
           atomicExch(&da.status->error, 1);
-          if (is + 1 < S) mbar_wait_bounded(&mbar[b ^ 1], b ? ph0 : ph1, WAIT_LIMIT);
+          if (is + 1 < S || (F32 && next < nitems)) mbar_wait_bounded(&mbar[b ^ 1], b ? ph0 : ph1, WAIT_LIMIT);
         }
         __syncthreads();
         return;
@@ -596,13 +616,18 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
       fence_proxy_async();  // held rows written into a stage before its next async copy
       __syncthreads();
     }
+    const int blast = (base + S - 1) & 1;  // stage of the last scale
+    pre = F32 && next < nitems;
+    base += S;
     if (da.raw) {  // a derivative channel: written above, no detection (uniform over the block)
       fence_proxy_async();
       __syncthreads();
       continue;
     }
-    // the stages are free now: the extremes go to shared memory for the 3 x 3 test
-    float *mx = sm, *mn = sm + CROWS2 * 32;
+    // the extremes go to shared memory for the 3 x 3 test: f32, the last
+    // scale's stage (the other one holds the next item's first load); 16-bit,
+    // the landing stages
+    float *mx = F32 ? reinterpret_cast<float *>(land(blast)) : sm, *mn = mx + CROWS2 * 32;
 #pragma unroll
     for (int j = 0; j < NOUT; ++j) {
       const int p = mma_row(warp, lane, j) * 32 + mma_col<F32>(lane, j);
@@ -635,7 +660,8 @@ int launch_colfir_tma(const Plan &p, const Launch &l, const BankArgs &a, const D
   }
   CUtensorMap map;
   if (encode_plane_map(&map, a.P, ST, p.PWb, p.prows, ST == ST_F32 ? BOXW : BOXW16, BOXH)) return -1;
-  const int stage_rows = (CROWS2 + 2 * G + BOXH - 1) / BOXH * BOXH;  // whole boxes
+  // whole boxes; f32: a stage holds the 2 x 128 x 32 extremes of an item
+  const int stage_rows = std::max((CROWS2 + 2 * G + BOXH - 1) / BOXH * BOXH, ST == ST_F32 ? 240 : 0);
   // band length >= BAND0 + 2K + 23: one past the largest index a fragment reads
   const int taps_len = (BAND0 + 2 * KP + 23 + 3) / 4 * 4;
   const int SF = colfir_stage_floats<ST>(stage_rows);
