@@ -244,7 +244,11 @@ def run_ours(args):
     vscales = [wl["value_scale"]] * NF
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
-    bank = kf.Bank(local, stream.cuda_stream)
+    # one library context per bank, each on its own stream: the banks of a
+    # step are independent passes over the same frames and run at once
+    bstreams = {name: torch.cuda.Stream(dev) for name, _, _ in BANKS}
+    banks = {name: kf.Bank(local, bstreams[name].cuda_stream) for name, _, _ in BANKS}
+    concurrent = len(BANKS) > 1 and not args.serial
 
     # one-time designs (FP64 kernel), timed separately: the bank reuses them
     t0 = time.perf_counter()
@@ -261,25 +265,42 @@ def run_ours(args):
             o.threshold = THRESHOLD
             o.fir_kmax = wl["fir_kmax"]
             o.storage = STORAGE[storage]
-            shapes, lc, _ = kf.kf_autotune(bank.ctx, Xs, SCALES, ft, order, o, vscales)
+            shapes, lc, _ = kf.kf_autotune(banks[name].ctx, Xs, SCALES, ft, order, o, vscales)
             tuned[name] = {"grid_mult": {p: m for p, m in zip(("row", "seg", "fold", "det"), shapes) if m >= 0}}
             if lc > 0:
                 tuned[name]["segment_rows"] = lc
 
-    def run_bank(frames, ft, order, profile=False, schedule=kf.KF_SCHED_BATCHED, use_graph=graph):
-        bank.run(frames, SCALES, ft, order, threshold=THRESHOLD, profile=profile, fir_kmax=wl["fir_kmax"],
-                 storage=STORAGE[storage], value_scales=vscales, schedule=schedule, graph=use_graph)
+    def run_bank(name, frames, ft, order, profile=False, schedule=kf.KF_SCHED_BATCHED, use_graph=graph):
+        banks[name].run(frames, SCALES, ft, order, threshold=THRESHOLD, profile=profile, fir_kmax=wl["fir_kmax"],
+                        storage=STORAGE[storage], value_scales=vscales, schedule=schedule, graph=use_graph)
 
-    def step(profile, schedule=kf.KF_SCHED_BATCHED, frames=None):
+    def step(profile, schedule=kf.KF_SCHED_BATCHED, frames=None, serial=None):
+        """One pass of every bank over the frames, blob lists read back.  The
+        banks' streams start after the work already on `stream` and `stream`
+        waits for them at the end.  Concurrent: all banks launched, then the
+        lists read; serial (profiling, frame-by-frame launches): one bank after
+        the other."""
         n, times = 0, {}
-        for _, ft, order in BANKS:
-            run_bank(Xs if frames is None else frames, ft, order, profile, schedule,
-                     graph and not profile and schedule == kf.KF_SCHED_BATCHED)
-            n += len(bank.blobs())
-            if profile:
-                for k, (nl, ms) in bank.kernel_times().items():
-                    a, b = times.get(k, (0, 0.0))
-                    times[k] = (a + nl, b + ms)
+        frames = Xs if frames is None else frames
+        use_graph = graph and not profile and schedule == kf.KF_SCHED_BATCHED
+        serial = (profile or not concurrent or schedule != kf.KF_SCHED_BATCHED) if serial is None else serial
+        for name, _, _ in BANKS:
+            bstreams[name].wait_stream(stream)
+        if serial:
+            for name, ft, order in BANKS:
+                run_bank(name, frames, ft, order, profile, schedule, use_graph)
+                n += len(banks[name].blobs())
+                if profile:
+                    for k, (nl, ms) in banks[name].kernel_times().items():
+                        a, b = times.get(k, (0, 0.0))
+                        times[k] = (a + nl, b + ms)
+        else:
+            for name, ft, order in BANKS:
+                run_bank(name, frames, ft, order, profile, schedule, use_graph)
+            for name, _, _ in BANKS:
+                n += len(banks[name].blobs())
+        for name, _, _ in BANKS:
+            stream.wait_stream(bstreams[name])
         return n, times
 
     def barrier():
@@ -290,7 +311,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step(False)
 
-    def timed(profile, schedule=kf.KF_SCHED_BATCHED):
+    def timed(profile, schedule=kf.KF_SCHED_BATCHED, serial=None):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         kt, nb = {}, 0
@@ -299,7 +320,7 @@ def run_ours(args):
             for i in range(args.steps):
                 flush.zero_()
                 ev[i][0].record(stream)
-                nb, times = step(profile, schedule)
+                nb, times = step(profile, schedule, serial=serial)
                 ev[i][1].record(stream)
                 for k, (nl, ms) in times.items():
                     a, b = kt.get(k, (0, 0.0))
@@ -319,6 +340,13 @@ def run_ours(args):
     ms_per_step = max_over_ranks(total_ms) / args.steps
     pix_scales = len(BANKS) * pixels * len(SCALES)
     value = world * pix_scales / (ms_per_step * 1e-3) / 1e6
+    # --- the same steps with the banks one after the other ------------------
+    serial_run = None
+    if concurrent:
+        s_ms, _, _, _ = timed(False, serial=True)
+        s_step = max_over_ranks(s_ms) / args.steps
+        serial_run = {"value": round(world * pix_scales / (s_step * 1e-3) / 1e6, 1), "ms_per_step": round(s_step, 4),
+                      "launches": "the banks one after the other on their streams"}
     # --- the same steps again with CUDA events around every kernel ------------
     _, ktimes, _, _ = timed(True)
     # --- the same steps launched frame by frame (batch workloads) ------------
@@ -403,7 +431,8 @@ def run_ours(args):
                 "peak_source": hbm_src}
     # filter-bank kernels launched in the timed region (the profiled pass runs the same steps)
     launches = sum(v[0] for v in ktimes.values())
-    bank.close()
+    for b in banks.values():
+        b.close()
 
     cpu = cpu_baseline(host[0], wl, rows=None if args.workload == "iir_fir" else wl["ref_rows"]) \
         if (rank == 0 and not args.no_cpu) else None
@@ -420,7 +449,9 @@ def run_ours(args):
         "config": {"workload": wl["text"], "frames": NF, "frame_sizes": shapes, "input": wl["dtype"],
                    "storage": storage, "scales_px": [round(x, 3) for x in SCALES],
                    "banks": [b[0] for b in BANKS], "threshold": THRESHOLD, "fir_kmax": wl["fir_kmax"],
-                   "launch": ("batched schedule, replayed from a CUDA graph" if graph else "batched schedule, eager"),
+                   "launch": ("batched schedule, replayed from a CUDA graph" if graph else "batched schedule, eager")
+                   + ("; one context and stream per bank, the banks of a step launched at once" if concurrent
+                      else "; the banks one after the other"),
                    "tuned": tuned or "library defaults (one block per work item, 64-row segments)",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}", "designs": "FP64 design kernel run once "
@@ -429,6 +460,8 @@ def run_ours(args):
         "clocks": clocks, "kernels": kern, "blobs_per_step": nblobs,
         "design_ms": round(design_ms, 2),
     }
+    if serial_run:
+        line["serial"] = serial_run
     if per_frame:
         line["per_frame_schedule"] = per_frame
     print(json.dumps(line), flush=True)
@@ -676,6 +709,7 @@ def main():
                     help="gated workload: marked tiles with their neighbours, or marked tiles only")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default launch shapes)")
+    ap.add_argument("--serial", action="store_true", help="run the banks of a step one after the other")
     ap.add_argument("--storage", choices=tuple(STORAGE), default=None,
                     help="element type of the one-sided planes (default: the workload's)")
     args = ap.parse_args()
