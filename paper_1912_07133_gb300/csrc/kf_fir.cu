@@ -115,41 +115,63 @@ __device__ __forceinline__ void fir_block(const float *sh, int K, At at, float (
 // so 128-bit loads of quads that start at multiples of 4 never straddle a gap
 // and a quarter-warp whose threads start 16 elements apart hits 8 distinct
 // 4-bank groups.
-__host__ __device__ __forceinline__ int pad20(int e) { return e + ((e >> 4) << 2); }
+__host__ __device__ __forceinline__ constexpr int pad20(int e) { return e + ((e >> 4) << 2); }
+
+// One block of 8 taps for NOUT consecutive outputs.  pa / pb point at the
+// padded positions of the 16-element groups holding the left / right windows;
+// OA / OB (0 or 8) are the windows' offsets inside them, so every load address
+// is a compile-time offset from the two pointers.  hk: the 8 taps (16-byte
+// aligned).
+template <int OA, int OB>
+__device__ __forceinline__ void fir_row_taps8(const float *hk_s, const float *pa, const float *pb,
+                                              float (&acc)[NOUT]) {
+  float A[NOUT + TB], B[NOUT + TB], hk[TB];
+  const float4 h03 = *reinterpret_cast<const float4 *>(hk_s), h47 = *reinterpret_cast<const float4 *>(hk_s + 4);
+  hk[0] = h03.x, hk[1] = h03.y, hk[2] = h03.z, hk[3] = h03.w;
+  hk[4] = h47.x, hk[5] = h47.y, hk[6] = h47.z, hk[7] = h47.w;
+#pragma unroll
+  for (int q = 0; q < (NOUT + TB) / 4; ++q) {
+    const float4 a = *reinterpret_cast<const float4 *>(pa + pad20(OA + 4 * q));  // A[m] = x(base + m - k0 - 7)
+    const float4 b = *reinterpret_cast<const float4 *>(pb + pad20(OB + 4 * q));  // B[m] = x(base + m + k0 - 1)
+    A[4 * q + 0] = a.x, A[4 * q + 1] = a.y, A[4 * q + 2] = a.z, A[4 * q + 3] = a.w;
+    B[4 * q + 0] = b.x, B[4 * q + 1] = b.y, B[4 * q + 2] = b.z, B[4 * q + 3] = b.w;
+  }
+  // output j, tap k0 + u: x(j - k0 - u) = A[j - u + 7], x(j + k0 + u) = B[j + u + 1]
+#pragma unroll
+  for (int u = 0; u < TB; ++u)
+#pragma unroll
+    for (int j = 0; j < NOUT; ++j) acc[j] = fmaf(hk[u], A[j - u + TB - 1] + B[j + u + 1], acc[j]);
+}
 
 // Symmetric FIR of NOUT consecutive outputs from a padded row: `row` points at
-// element 0, `base` (a multiple of 16) is the first output.  Taps are used 8
-// at a time: the left window x(base-8(i+1) .. +23) and the right window
-// x(base+8i .. +23) are six 128-bit loads each.
+// element 0, `base` (a multiple of 16) is the first output, sh[k] = h_k with
+// sh + 1 16-byte aligned.  Taps are used 8 at a time: block i reads the left
+// window x(base-8(i+1) .. +23) and the right window x(base+8i .. +23), six
+// 128-bit loads each.  Blocks go in pairs, so that the windows move by one
+// 16-element group per pair.
 __device__ __forceinline__ void fir_row_block(const float *sh, int K, const float *row, int base,
                                               float (&acc)[NOUT]) {
-  auto quad = [&](int e) { return *reinterpret_cast<const float4 *>(row + pad20(e)); };
   const float h0 = sh[0];
+  const float *p0 = row + pad20(base);
 #pragma unroll
   for (int q = 0; q < NOUT / 4; ++q) {
-    const float4 v = quad(base + 4 * q);
+    const float4 v = *reinterpret_cast<const float4 *>(p0 + pad20(4 * q));
     acc[4 * q + 0] = h0 * v.x;
     acc[4 * q + 1] = h0 * v.y;
     acc[4 * q + 2] = h0 * v.z;
     acc[4 * q + 3] = h0 * v.w;
   }
-  for (int k0 = 1, i = 0; k0 <= K; k0 += TB, ++i) {
-    float A[NOUT + TB], B[NOUT + TB], hk[TB];
-#pragma unroll
-    for (int u = 0; u < TB; ++u) hk[u] = sh[k0 + u];
-#pragma unroll
-    for (int q = 0; q < (NOUT + TB) / 4; ++q) {
-      const float4 a = quad(base - TB * (i + 1) + 4 * q);  // A[m] = x(base + m - k0 - 7)
-      const float4 b = quad(base + TB * i + 4 * q);        // B[m] = x(base + m + k0 - 1)
-      A[4 * q + 0] = a.x, A[4 * q + 1] = a.y, A[4 * q + 2] = a.z, A[4 * q + 3] = a.w;
-      B[4 * q + 0] = b.x, B[4 * q + 1] = b.y, B[4 * q + 2] = b.z, B[4 * q + 3] = b.w;
-    }
-    // output j, tap k0 + u: x(j - k0 - u) = A[j - u + 7], x(j + k0 + u) = B[j + u + 1]
-#pragma unroll
-    for (int u = 0; u < TB; ++u)
-#pragma unroll
-      for (int j = 0; j < NOUT; ++j) acc[j] = fmaf(hk[u], A[j - u + TB - 1] + B[j + u + 1], acc[j]);
+  // pair n (blocks i = 2n, 2n + 1): the left windows start at 16(m - n - 1) + 8
+  // and 16(m - n - 1), the right ones at 16(m + n) and 16(m + n) + 8 (m = base / 16)
+  const float *pa = row + 20 * ((base >> 4) - 1), *pb = row + 20 * (base >> 4);
+  int k0 = 1;
+  for (; k0 + TB <= K; k0 += 2 * TB) {
+    fir_row_taps8<8, 0>(sh + k0, pa, pb, acc);
+    fir_row_taps8<0, 8>(sh + k0 + TB, pa, pb, acc);
+    pa -= 20;
+    pb += 20;
   }
+  if (k0 <= K) fir_row_taps8<8, 0>(sh + k0, pa, pb, acc);
 }
 
 // halo of the row kernel: >= kmax + TB, a multiple of 16
@@ -168,7 +190,7 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr,
   const int G = row_halo(kmax);
   const int n = RSEG + 2 * G;
   float *sL = sm;                       // padded: element j at pad20(j)
-  float *sh = sm + pad20(n) + 4;
+  float *sh = sm + pad20(n) + 4 + 3;      // taps h_k at sh[k]; sh + 1 is 16-byte aligned
   __shared__ FrameDev s_fr;
   bool ovf = false;                     // a value beyond the f16 range
   int k = 0;
@@ -768,7 +790,7 @@ int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st) {
   const int G = kmax + TB;
   const int KP = ((kmax + TB - 1) / TB) * TB;
   const int RG = row_halo(kmax);
-  const size_t rsm = (size_t)(pad20(RSEG + 2 * RG) + 4 + KP + 1) * sizeof(float);
+  const size_t rsm = (size_t)(pad20(RSEG + 2 * RG) + 4 + 3 + KP + 1) * sizeof(float);
   DetectArgs da;
   da.thr = a.threshold;
   da.neigh = a.neigh;
