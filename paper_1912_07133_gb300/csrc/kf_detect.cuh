@@ -37,7 +37,7 @@ struct DetectArgs {
   float limit2 = 0.f;
 };
 
-constexpr int TILE_CANDS = 256;  // candidates staged per tile before one global reservation
+constexpr int TILE_CANDS = 128;  // candidates staged per tile before one global reservation
 
 struct TileList {
   int n;

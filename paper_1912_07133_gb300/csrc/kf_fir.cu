@@ -433,10 +433,10 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
   auto land = [&](int b) { return reinterpret_cast<T *>(sm) + (long)b * stage_rows * BW; };
   float *work = sm + stage_rows * BOXW16;  // 16-bit planes only
   const int SF = colfir_stage_floats<ST>(stage_rows);
-  // one band of taps (hi parts, then lo parts): written at the start of a scale,
-  // after the previous scale's closing barrier
-  float *taps = sm + SF;
-  unsigned char *amx = reinterpret_cast<unsigned char *>(sm + SF + 2 * taps_len);
+  // two bands of taps (hi parts, then lo parts), alternating with the stages:
+  // a scale writes its band while the previous scale may still read the other
+  float *taps0 = sm + SF;
+  unsigned char *amx = reinterpret_cast<unsigned char *>(sm + SF + 4 * taps_len);
   unsigned char *amn = amx + CROWS2 * 32;
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
@@ -500,21 +500,14 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
       if (!F32 && S > 1) issue(S - 2, (base + 1) & 1);
     }
     const long plane = (long)H * W;
+    // f32: one barrier per scale (after the scale's load and taps); the next
+    // load into a stage is issued after the following scale's barrier, when
+    // every warp is done with that stage.  16-bit: the scales share one work
+    // tile, and each scale also ends with a barrier.
     for (int is = 0; is < S; ++is) {
       const int s = S - 1 - is;
       const int b = (base + is) & 1;
-      if (F32 && tid == 0) {
-        if (is + 1 < S) {
-          issue(s - 1, b ^ 1);
-        } else if (next < nitems) {  // the next item's first scale
-          int ln;
-          const int kq = item_frame(it, next, k, ln);
-          const FrameDev &Fn = fr[__ldg(it.fl + kq)];
-          const int Hn = Fn.H, ntxn = (Fn.W + TW - 1) / TW;
-          const int x0n = (ln % ntxn) * TW - 1, r0n = (ln / ntxn) * (CROWS2 - 2) - 1;
-          issue_at(S - 1, b ^ 1, Fn.prow, Hn, r0n, x0n - ((x0n % XA) + XA) % XA);
-        }
-      }
+      float *taps = taps0 + 2 * b * taps_len;
       const Coef &c = coef[s];
       const int K = c.K, G = K + TB, nin = CROWS2 + 2 * G;
       // R_L = -sigma^2 (D20 + D02) with the planes carrying sigma^2: the taps
@@ -527,10 +520,22 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
         // a load never completed: report, let the other stage's load finish, stop
         if (tid == 0) {
           atomicExch(&da.status->error, 1);
-          if (is + 1 < S || (F32 && next < nitems)) mbar_wait_bounded(&mbar[b ^ 1], b ? ph0 : ph1, WAIT_LIMIT);
+          if (!F32 && is + 1 < S) mbar_wait_bounded(&mbar[b ^ 1], b ? ph0 : ph1, WAIT_LIMIT);
         }
         __syncthreads();
         return;
+      }
+      if (F32 && tid == 0) {
+        if (is + 1 < S) {
+          issue(s - 1, b ^ 1);
+        } else if (next < nitems) {  // the next item's first scale
+          int ln;
+          const int kq = item_frame(it, next, k, ln);
+          const FrameDev &Fn = fr[__ldg(it.fl + kq)];
+          const int Hn = Fn.H, ntxn = (Fn.W + TW - 1) / TW;
+          const int x0n = (ln % ntxn) * TW - 1, r0n = (ln / ntxn) * (CROWS2 - 2) - 1;
+          issue_at(S - 1, b ^ 1, Fn.prow, Hn, r0n, x0n - ((x0n % XA) + XA) % XA);
+        }
       }
       const bool outside = r0 - G < 0 || r0 + CROWS2 + G > H;
       float top = 0.f, bot = 0.f;
@@ -542,15 +547,16 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
       const float *tile;
       if constexpr (F32) {
         float *stg = land(b);
-        if (outside) {  // rows outside the frame: held values
+        if (outside) {  // rows outside the frame: held values (uniform over the block)
           for (int j = warp; j < nin; j += CNT2 / 32) {
             const int r = r0 - G + j;
             if (r < 0) stg[j * BOXW + off + lane] = top;
             else if (r >= H) stg[j * BOXW + off + lane] = bot;
           }
+          fence_proxy_async();  // before the stage's next async copy
+          __syncthreads();
         }
         tile = stg + off;
-        __syncthreads();
       } else {
         const T *src = land(b) + off + lane;
         for (int j = warp; j < nin; j += CNT2 / 32) {
@@ -635,9 +641,12 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
             resp[s * plane + (long)y * W + xj] = d[j >> 2][j & 3];
         }
       }
-      fence_proxy_async();  // held rows written into a stage before its next async copy
-      __syncthreads();
+      if (!F32) {
+        fence_proxy_async();
+        __syncthreads();  // the work tile and the landing stage are free again
+      }
     }
+    if (F32) __syncthreads();  // every warp is done with the last scale's stage
     const int blast = (base + S - 1) & 1;  // stage of the last scale
     pre = F32 && next < nitems;
     base += S;
@@ -688,7 +697,7 @@ int launch_colfir_tma(const Plan &p, const Launch &l, const BankArgs &a, const D
   const int taps_len = (BAND0 + 2 * KP + 23 + 3) / 4 * 4;
   const int SF = colfir_stage_floats<ST>(stage_rows);
   // stages (>= 2 x 128 x 32 floats for the final extremes) + taps + first-scale bytes
-  const size_t tsm = ((size_t)SF + 2 * taps_len) * sizeof(float) + (size_t)CROWS2 * 32 * 2 + TMA_SMEM_ALIGN;
+  const size_t tsm = ((size_t)SF + 4 * taps_len) * sizeof(float) + (size_t)CROWS2 * 32 * 2 + TMA_SMEM_ALIGN;
   if (tsm > 200 * 1024 || SF < 2 * CROWS2 * 32) return -1;
   const int nb = persistent_blocks((const void *)k_colfir_tma<ST>, CNT2, tsm, l.it.total, p.mult[PASS_DET]);
   a.prof->begin("fir_coldet", st);
