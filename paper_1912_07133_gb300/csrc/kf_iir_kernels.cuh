@@ -435,29 +435,31 @@ __global__ void __launch_bounds__(128) k_colseg(const FrameDev *__restrict__ fr,
     const long fs = (long)Rec::NF * PWb;
     float *Ef = E + F.coff + (((long)s * nseg + c) * 2 + 0) * fs + x;
     // causal segment: rows [c LC - 1, (c+1) LC - 1); anticausal: rows (c+1) LC
-    // down to c LC + 1.  Inside the frame the loads are unconditional and
-    // issued 8 at a time ahead of their recursion steps.
+    // down to c LC + 1.  Inside the frame the two directions run side by
+    // side (two independent recursions), their loads unconditional and issued
+    // 8 rows of each at a time ahead of the steps.
     const int rf = c * LC - 1, rb = (c + 1) * LC;
     if (rf >= 0 && rb < H) {
       const typename Store<ST>::T *pf = Pc + (long)rf * PWb, *pb = Pc + (long)rb * PWb;
+      Rec q;
       r.zero();
+      q.zero();
+#pragma unroll
       for (int i0 = 0; i0 < LC; i0 += 8) {
-        float in[8];
+        float inf[8], inb[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) in[u] = Store<ST>::ld(pf[(long)(i0 + u) * PWb]);
+        for (int u = 0; u < 8; ++u) {
+          inf[u] = Store<ST>::ld(pf[(long)(i0 + u) * PWb]);
+          inb[u] = Store<ST>::ld(pb[-(long)(i0 + u) * PWb]);
+        }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) r.push(v, in[u]);
+        for (int u = 0; u < 8; ++u) {
+          r.push(v, inf[u]);
+          q.push(v, inb[u]);
+        }
       }
       r.store(Ef, PWb);
-      r.zero();
-      for (int i0 = 0; i0 < LC; i0 += 8) {
-        float in[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) in[u] = Store<ST>::ld(pb[-(long)(i0 + u) * PWb]);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) r.push(v, in[u]);
-      }
-      r.store(Ef + fs, PWb);
+      q.store(Ef + fs, PWb);
     } else {
       r.zero();
 #pragma unroll 8
@@ -497,23 +499,34 @@ __global__ void __launch_bounds__(128) k_colfold(const FrameDev *__restrict__ fr
     float *base = E + F.coff + ((long)s * nseg * 2 + dir) * fs + x;  // segment k at base + 2 k fs
     Rec st;
     st.hold(c, edge[F.eoff + ((long)s * 2 + dir) * PWb + x]);
+    // segment k's end state is read, then its slot receives the carry into
+    // segment k; batches of 8 alternate, the next batch's loads in flight
+    // while the current one is folded
     constexpr int BATCH = 8;
-    for (int k0 = 0; k0 < nseg; k0 += BATCH) {
-      Rec e[BATCH];
+    auto slot = [&](int kk) { return base + 2L * (dir ? nseg - 1 - kk : kk) * fs; };
+    auto fetch = [&](Rec (&e)[BATCH], int k0) {
 #pragma unroll
-      for (int u = 0; u < BATCH; ++u) {
-        const int kk = k0 + u;
-        if (kk < nseg) e[u].load(base + 2L * (dir ? nseg - 1 - kk : kk) * fs, PWb);
-      }
+      for (int u = 0; u < BATCH; ++u)
+        if (k0 + u < nseg) e[u].load(slot(k0 + u), PWb);
+    };
+    auto fold = [&](const Rec (&e)[BATCH], int k0) {
 #pragma unroll
       for (int u = 0; u < BATCH; ++u) {
         const int kk = k0 + u;
         if (kk >= nseg) break;
-        st.store(base + 2L * (dir ? nseg - 1 - kk : kk) * fs, PWb);
+        st.store(slot(kk), PWb);
         Rec n = e[u];
         n.combine_m(c, LC / CH, st);  // Phi^LC st + e (LC a multiple of CH)
         st = n;
       }
+    };
+    Rec ea[BATCH], eb[BATCH];
+    fetch(ea, 0);
+    for (int k0 = 0; k0 < nseg; k0 += 2 * BATCH) {
+      fetch(eb, k0 + BATCH);
+      fold(ea, k0);
+      fetch(ea, k0 + 2 * BATCH);
+      fold(eb, k0 + BATCH);
     }
   }
 }
