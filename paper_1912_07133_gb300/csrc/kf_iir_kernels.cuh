@@ -46,7 +46,7 @@ namespace {
 template <int KK>
 struct Chain {
   static constexpr int NF = KK;
-  static constexpr int kColdetMinBlocks32 = 2;  // k_coldet with 32-row segments fits 64 registers
+  static constexpr int kColdetRegs32 = 80;  // k_coldet with 32-row segments: registers per thread
   struct View {
     float p, b0, w[KK];
     __device__ void load(const Coef &c) {
@@ -118,7 +118,7 @@ struct Chain {
 template <int NM>
 struct Modes {
   static constexpr int NF = 2 * NM;
-  static constexpr int kColdetMinBlocks32 = NM < 3 ? 2 : 1;  // three modes need more than 64 registers
+  static constexpr int kColdetRegs32 = NM < 3 ? 80 : 128;  // three modes need more
   struct View {
     float zr[NM], zi[NM], gr[NM], gi[NM], b0;
     __device__ void load(const Coef &c) {
@@ -573,7 +573,7 @@ __host__ __device__ constexpr int coldet_region_floats() {
 }
 
 template <class Rec, int ST, int LC>
-__global__ void __launch_bounds__(512, LC == 32 ? Rec::kColdetMinBlocks32 : 1) k_coldet(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(512) __maxnreg__(LC == 32 ? Rec::kColdetRegs32 : 128) k_coldet(const __grid_constant__ CUtensorMap map,
                                                 const FrameDev *__restrict__ fr, Items it, long PWb,
                                                 const float *__restrict__ edge,
                                                 const Coef *__restrict__ coef, int S,
