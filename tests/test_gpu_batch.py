@@ -258,3 +258,38 @@ def test_degenerate_shapes_in_one_batch(ftype, order, lc):
             assert np.abs(Rg[s] - Ro[s]).max() <= TOL * max(np.ptp(Ro[s]), 1e-3), (i, s)
         if f.size > 1:
             compare_blobs(blobs, Ro, 0.05, frame=i)
+
+
+def test_contexts_on_two_streams_run_at_once():
+    """Two contexts, each on its own stream, launched together (graph replays
+    included) give exactly the responses and blob lists of one call after the
+    other."""
+    import torch
+
+    from paper_1912_07133_gb300 import kf
+    img = SY.iir_fir_frame(seed=31, H=1024, W=1536, nblobs=80)
+    x = to_device(img)
+    six = [2.0, 4.0, 8.0, 16.0, 32.0, 48.0]
+    banks = ((D, 4), (C, 1))
+    ref = {}
+    for ft, order in banks:  # one after the other, default stream
+        b = kf.Bank(0)
+        R = torch.empty((len(six), 1024, 1536), device="cuda")
+        b.run([x], six, ft, order, threshold=0.05, responses=R)
+        ref[ft] = (R.cpu().numpy(), b.blobs())
+        b.close()
+    streams = [torch.cuda.Stream() for _ in banks]
+    ctxs = [kf.Bank(0, s.cuda_stream) for s in streams]
+    outs = [torch.empty((len(six), 1024, 1536), device="cuda") for _ in banks]
+    for rep in range(3):  # eager, capture, replay
+        for s in streams:
+            s.wait_stream(torch.cuda.current_stream())
+        for b, (ft, order), R in zip(ctxs, banks, outs):
+            b.run([x], six, ft, order, threshold=0.05, responses=R, graph=True)
+        got = [b.blobs() for b in ctxs]
+        torch.cuda.synchronize()
+        for (ft, _), R, bl in zip(banks, outs, got):
+            assert np.array_equal(R.cpu().numpy(), ref[ft][0]), (rep, ft)
+            assert np.array_equal(bl, ref[ft][1]), (rep, ft)
+    for b in ctxs:
+        b.close()
