@@ -527,6 +527,22 @@ void ko_fir1d(const double *x, long n, long sx, double *y, long sy, int K,
   }
 }
 
+/* Filter A: eq 9 (d = 0) sampled at T_s = 1, renormalised by eq 11. */
+int ko_design_gaussian(double sigma, int fir_kmax, double *h) {
+  if (!(sigma > 0.0)) return -1;
+  int K = (int)ceil(5.0 * sigma);
+  if (fir_kmax > 0 && K > fir_kmax) K = fir_kmax;
+  const double norm = 1.0 / (sigma * sqrt(2.0 * M_PI));
+  double dc = 0.0; /* H0 at dc of the sampled prototype: sum over m = -K..K */
+  for (int m = 0; m <= K; ++m) {
+    h[m] = norm * exp(-(double)m * (double)m / (2.0 * sigma * sigma));
+    dc += m == 0 ? h[m] : 2.0 * h[m];
+  }
+  const double cg = 1.0 / dc; /* eq 11 */
+  for (int m = 0; m <= K; ++m) h[m] *= cg;
+  return K;
+}
+
 /* ======================================================================= */
 /* Filter bank (Sec. 5)                                                      */
 /* ======================================================================= */
@@ -560,6 +576,11 @@ static int make_design(int type, int order, double sigma, int fir_kmax,
     if (fir_kmax > 0 && cap > fir_kmax) cap = fir_kmax;
     d->h = malloc(sizeof(double) * (cap + 1));
     d->K = ko_design_colored_sg(order, sigma, fir_kmax, d->h);
+  } else if (type == KO_FIR_GAUSSIAN) {
+    int cap = (int)ceil(5.0 * sigma);
+    if (fir_kmax > 0 && cap > fir_kmax) cap = fir_kmax;
+    d->h = malloc(sizeof(double) * (cap + 1));
+    d->K = ko_design_gaussian(sigma, fir_kmax, d->h);
   } else
     d->K = -1;
   return d->K < 0 ? -1 : 0;
@@ -567,7 +588,7 @@ static int make_design(int type, int order, double sigma, int fir_kmax,
 
 static void filt1d(const design_t *d, const double *x, long n, long sx,
                    double *y, long sy, int boundary) {
-  if (d->type == KO_FIR_COLORED_SG) ko_fir1d(x, n, sx, y, sy, d->K, d->h, boundary);
+  if (d->type == KO_FIR_COLORED_SG || d->type == KO_FIR_GAUSSIAN) ko_fir1d(x, n, sx, y, sy, d->K, d->h, boundary);
   else ko_iir1d(x, n, sx, y, sy, d->K, d->b0, d->bplus, d->aplus, 1.0, boundary);
 }
 

@@ -74,6 +74,14 @@ int ko_design_butterworth(int L_D, double sigma, double *b0, double *bplus,
  * Returns K, or -1 (omega_c >= pi, or singular). */
 int ko_design_colored_sg(int L_D, double sigma, int Kmax, double *h);
 
+/* Filter A (Sec. 3.1, eqs 9 and 11 with d = 0): the Gaussian g0(x) =
+ * exp(-x^2 / 2 sigma^2) / (sigma sqrt(2 pi)) sampled at the integers |m| <= K
+ * and renormalised to unit gain at dc (eq 11: c_g = 1 / sum_m g0(m)), so
+ * h(m) = c_g g0(m).  K = ceil(5 sigma) (the half-length of the paper's
+ * timing comparison), capped at fir_kmax when fir_kmax > 0.  Writes h[0..K]
+ * (the symmetric half); returns K, or -1 for sigma <= 0. */
+int ko_design_gaussian(double sigma, int fir_kmax, double *h);
+
 /* The same KKT design with an explicit half-length K and cut-off omega_c;
  * omega_c = 0 gives the classic (white-noise) Savitzky-Golay smoother. */
 int ko_design_colored_sg_raw(int L_D, int K, double omega_c, double *h);
@@ -98,6 +106,7 @@ void ko_fir1d(const double *x, long n, long sx, double *y, long sy, int K,
 #define KO_IIR_REPEATED_POLE 0 /* Filter D */
 #define KO_IIR_BUTTERWORTH 1   /* Filter E */
 #define KO_FIR_COLORED_SG 2    /* Filter C */
+#define KO_FIR_GAUSSIAN 3      /* Filter A */
 
 #define KO_RESP_LAPLACIAN 0 /* R_L = -sigma^2 (D20 + D02) */
 #define KO_RESP_HESSIAN 1   /* R_H = sigma^4 (D20 D02 - D11^2), eq (26) */

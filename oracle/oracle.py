@@ -27,6 +27,7 @@ _lib = None
 IIR_REPEATED_POLE = 0  # Filter D
 IIR_BUTTERWORTH = 1  # Filter E
 FIR_COLORED_SG = 2  # Filter C
+FIR_GAUSSIAN = 3  # Filter A
 RESP_LAPLACIAN = 0
 RESP_HESSIAN = 1
 BOUNDARY_HOLD = 0
@@ -91,6 +92,8 @@ def lib():
             L.ko_design_colored_sg.argtypes = [i, d, i, P]
             L.ko_design_colored_sg_raw.restype = i
             L.ko_design_colored_sg_raw.argtypes = [i, i, d, P]
+            L.ko_design_gaussian.restype = i
+            L.ko_design_gaussian.argtypes = [d, i, P]
             L.ko_iir1d.restype = None
             L.ko_iir1d.argtypes = [P, l, l, P, l, i, d, P, P, d, i]
             L.ko_fir1d.restype = None
@@ -240,6 +243,16 @@ def design_colored_sg_mp(L_D: int, K: int, omega_c: float, dps: int = 40) -> np.
     h = np.array([float(x[k]) for k in range(NK)])
     _MP_CACHE[key] = h
     return h.copy()
+
+
+def design_gaussian(sigma: float, kmax: int = 96) -> np.ndarray:
+    """Filter A taps h[0..K] (Sec. 3.1, eqs 9 and 11, d = 0; K = ceil(5 sigma)
+    capped at kmax)."""
+    h = np.zeros(int(np.ceil(5.0 * sigma)) + 1)
+    K = lib().ko_design_gaussian(float(sigma), int(kmax), _p(h))
+    if K < 0:
+        raise ValueError("design failed")
+    return h[:K + 1].copy()
 
 
 def sg_half_length(L_D: int, sigma: float, kmax: int = 96) -> int:

@@ -369,6 +369,10 @@ def test_fir_boundaries_against_padding():
 # 2-D bank against brute-force direct 2-D convolution (Sec. 2, Fig. 5)
 # ----------------------------------------------------------------------------
 def one_d_ir(ftype, order, sigma):
+    if ftype == O.FIR_GAUSSIAN:
+        h = O.design_gaussian(sigma, 96)
+        K = len(h) - 1
+        return h[np.abs(np.arange(-K, K + 1))]
     if ftype == O.FIR_COLORED_SG:
         h = O.design_colored_sg_mp(order, O.sg_half_length(order, sigma, 96), 3.0 / sigma)
         K = len(h) - 1
@@ -405,7 +409,8 @@ def brute_response(img, ftype, order, lam, resp, boundary):
 
 @pytest.mark.parametrize("ftype,order,lam", [
     (O.IIR_REPEATED_POLE, 3, 4.0), (O.IIR_REPEATED_POLE, 4, 7.0),
-    (O.IIR_BUTTERWORTH, 2, 4.0), (O.FIR_COLORED_SG, 1, 4.0), (O.FIR_COLORED_SG, 1, 6.0)])
+    (O.IIR_BUTTERWORTH, 2, 4.0), (O.FIR_COLORED_SG, 1, 4.0), (O.FIR_COLORED_SG, 1, 6.0),
+    (O.FIR_GAUSSIAN, 1, 4.0), (O.FIR_GAUSSIAN, 1, 5.0)])
 @pytest.mark.parametrize("resp", [O.RESP_LAPLACIAN, O.RESP_HESSIAN])
 def test_bank_equals_brute_force_2d_convolution(ftype, order, lam, resp):
     rng = np.random.default_rng(int(lam * 10) + ftype)
@@ -641,3 +646,65 @@ def test_colored_sg_high_precision_is_the_cng_minimum_at_sigma_1():
         v *= 1e-2 / np.abs(v).max()
         for sg in (1, -1):
             assert cng([c[k] + sg * ctx.mpf(float(v[k])) for k in range(K + 1)]) > base
+
+
+# ----------------------------------------------------------------------------
+# Filter A: the Gaussian FIR blur (Sec. 3.1, eqs 9-11, Table III)
+# ----------------------------------------------------------------------------
+def rho_dc(h_full, lmax=4):
+    """rho_l = d^l/d omega^l of H(omega) = sum_m h(m) e^{-i omega m} at dc
+    (the convention of Table III), l = 0..lmax; h_full on m = -K..K."""
+    K = (len(h_full) - 1) // 2
+    m = np.arange(-K, K + 1, dtype=float)
+    return np.array([np.sum(h_full * (-1j * m) ** l) for l in range(lmax + 1)])
+
+
+def full(h):
+    K = len(h) - 1
+    return h[np.abs(np.arange(-K, K + 1))]
+
+
+def test_filter_a_one_stage_moments_match_table_iii():
+    """sigma = 1, K = 5: rho_{0,l} printed to 4 decimals."""
+    g = GOLD["table_III_gaussian_sigma1"]
+    h = O.design_gaussian(g["sigma"], 96)
+    assert len(h) - 1 == g["K"]
+    rho = rho_dc(full(h))
+    want = np.array(g["one_stage_d0"]["re"]) + 1j * np.array(g["one_stage_d0"]["im"])
+    np.testing.assert_allclose(rho, want, rtol=0, atol=0.5e-4)
+
+
+def test_filter_a_two_stage_moments_match_table_iii():
+    """The Gaussian blur cascaded with the Table I taps (d = 1, 2): the italic
+    rows of Table III."""
+    g = GOLD["table_III_gaussian_sigma1"]
+    t = GOLD["table_I_hpf"]
+    h = full(O.design_gaussian(g["sigma"], 96))
+    for d, key in ((1, "two_stage_d1"), (2, "two_stage_d2")):
+        hpf = np.array(t["d%d" % d], dtype=float)  # m = -2..2
+        bpf = np.convolve(h, hpf)  # m = -(K+2)..(K+2)
+        rho = rho_dc(bpf)
+        want = np.array(g[key]["re"]) + 1j * np.array(g[key]["im"])
+        np.testing.assert_allclose(rho, want, rtol=0, atol=0.5e-4, err_msg="d = %d" % d)
+
+
+@pytest.mark.parametrize("sigma,kmax", [(0.7, 96), (1.0, 96), (3.3, 96), (8.0, 96), (24.0, 96), (24.0, 40)])
+def test_filter_a_taps_are_the_normalised_sampled_gaussian(sigma, kmax):
+    """h(m) / h(0) = exp(-m^2 / 2 sigma^2) (eq 9c), unit dc gain (eq 11),
+    K = ceil(5 sigma) capped at kmax."""
+    h = O.design_gaussian(sigma, kmax)
+    K = len(h) - 1
+    assert K == min(math.ceil(5 * sigma), kmax)
+    m = np.arange(K + 1, dtype=float)
+    np.testing.assert_allclose(h / h[0], np.exp(-m * m / (2 * sigma * sigma)), rtol=1e-14, atol=0)
+    assert h[0] + 2 * h[1:].sum() == pytest.approx(1.0, abs=1e-15)
+
+
+def test_filter_a_moments_approach_the_continuous_gaussian():
+    """Table III, analog column: rho_{0,2} = -sigma^2, rho_{0,4} = 3 sigma^4;
+    sampling a wide Gaussian at 5 sigma leaves only the truncated tails."""
+    for sigma in (4.0, 8.0):
+        rho = rho_dc(full(O.design_gaussian(sigma, 200)))
+        assert rho[2].real == pytest.approx(-sigma ** 2, rel=2e-5)
+        assert rho[4].real == pytest.approx(3 * sigma ** 4, rel=2e-4)
+        assert abs(rho[1]) < 1e-15 and abs(rho[3]) < 1e-12
