@@ -50,6 +50,9 @@ extern "C" {
 #define KF_IIR_REPEATED_POLE 0 /* Filter D, Sec. 4.3 / Table IV                  */
 #define KF_IIR_BUTTERWORTH 1   /* Filter E, Sec. 4.4                             */
 #define KF_FIR_COLORED_SG 2    /* Filter C, Sec. 4.2                             */
+#define KF_FIR_GAUSSIAN 3      /* Filter A, Sec. 3.1 (the paper's Gaussian FIR
+                                  comparison blur)                              */
+#define KF_NTYPES 4
 
 /* Element types.  Input frames: any of the four; each element is converted
  * to f32 and multiplied by the frame's value_scale.  Intermediate planes
@@ -222,6 +225,9 @@ const char *kf_last_error(const kf_ctx *ctx);
  *         KF_FIR_COLORED_SG: order = L_D (1 or 2); K = ceil(5 sigma)
  *         (ceil(7 sigma) for L_D = 2) capped at 96, omega_c = 3 / sigma
  *         (Sec. 4.2).
+ *         KF_FIR_GAUSSIAN: order = 1; the Gaussian of eq 9 (d = 0) sampled
+ *         at |m| <= K = ceil(5 sigma) (capped at 96) and renormalised to
+ *         unit dc gain (eq 11) (Sec. 3.1).
  *   scale lambda in pixels, sigma = lambda / 2 (Sec. 5).
  * Errors: KF_EINVAL (bad type/order, sigma <= 0, colored SG with
  * 3/sigma >= pi), KF_ECOND (design solve failed), KF_ENODEV, KF_ECUDA. */

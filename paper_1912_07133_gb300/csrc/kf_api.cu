@@ -96,8 +96,8 @@ struct kf_ctx {
   // Default: one block per work item, which measured fastest or within noise
   // of the persistent shapes for every pass on GB300 (4096^2 and uneven
   // batches); the persistent shapes remain candidates of the autotuner.
-  int grid_mult[3][KF_NPASS] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
-  int seg_len[3] = {64, 64, 64};  // recursive banks: column segment length (kf_set_segment_length)
+  int grid_mult[KF_NTYPES][KF_NPASS] = {};
+  int seg_len[KF_NTYPES] = {64, 64, 64, 64};  // recursive banks: column segment length (kf_set_segment_length)
   std::vector<int> last_H, last_W;  // frame sizes of the last bank call
   // proposal network: FP32 masters, Adam moments, bf16 working copy, gradient, loss
   float *net_master = nullptr, *net_m = nullptr, *net_v = nullptr, *net_g = nullptr, *net_loss = nullptr;
@@ -203,7 +203,7 @@ int sort_keybits(long nframes, long S, long hmax, long wmax) {
 }
 
 int nmax_for(int type, int order, int kmax) {
-  if (type != KF_FIR_COLORED_SG) return 1;
+  if (type != KF_FIR_COLORED_SG) return 1;  // the Gaussian needs no solve
   return kmax + 1 + order + 1;
 }
 
@@ -281,6 +281,8 @@ int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S,
   return KF_OK;
 }
 
+bool is_fir(int type) { return type == KF_FIR_COLORED_SG || type == KF_FIR_GAUSSIAN; }
+
 int check_type_order(kf_ctx *ctx, int type, int order) {
   if (type == KF_IIR_REPEATED_POLE && (order < 2 || order > 6))
     return fail(ctx, KF_EINVAL, "repeated-pole order must be 2..6 (got %d)", order);
@@ -288,7 +290,9 @@ int check_type_order(kf_ctx *ctx, int type, int order) {
     return fail(ctx, KF_EINVAL, "Butterworth order (L_B/2) must be 1..6 (got %d)", order);
   if (type == KF_FIR_COLORED_SG && order != 1 && order != 2)
     return fail(ctx, KF_EINVAL, "colored SG order (L_D) must be 1 or 2 (got %d)", order);
-  if (type < 0 || type > 2) return fail(ctx, KF_EINVAL, "unknown filter type %d", type);
+  if (type == KF_FIR_GAUSSIAN && order != 1)
+    return fail(ctx, KF_EINVAL, "Gaussian FIR order must be 1 (got %d)", order);
+  if (type < 0 || type >= KF_NTYPES) return fail(ctx, KF_EINVAL, "unknown filter type %d", type);
   return KF_OK;
 }
 
@@ -467,7 +471,7 @@ int kf_design(int type, int order, double scale, kf_coeffs *out) {
   out->b0 = c.db0;
   out->dc_gain = c.dc_gain;
   out->moment2 = c.moment2;
-  if (type == KF_FIR_COLORED_SG) {
+  if (is_fir(type)) {
     out->K = c.K;
     for (int k = 0; k <= c.K; ++k) out->h[k] = c.dh[k];
   } else {
@@ -551,7 +555,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     nstate = std::max(nstate, ctx->cur->h_coef[s].K);
     kmax = std::max(kmax, ctx->cur->h_coef[s].K);
   }
-  const bool iir = type != KF_FIR_COLORED_SG;
+  const bool iir = !is_fir(type);
   const int nfs = (type == KF_IIR_BUTTERWORTH) ? 2 * nstate : nstate;  // states per recursion
   // ---- layout: every frame resident in one plane row space of pitch PWb ----
   const long PWb = maxPW;
@@ -887,7 +891,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
 
 int kf_set_launch_shape(kf_ctx *ctx, int type, int pass, int grid_mult) {
   if (!ctx) return fail(nullptr, KF_EINVAL, "kf_set_launch_shape: ctx is NULL");
-  if (type < 0 || type > 2) return fail(ctx, KF_EINVAL, "unknown filter type %d", type);
+  if (type < 0 || type >= KF_NTYPES) return fail(ctx, KF_EINVAL, "unknown filter type %d", type);
   if (pass < 0 || pass >= KF_NPASS) return fail(ctx, KF_EINVAL, "unknown pass %d", pass);
   if (grid_mult < 0 || grid_mult > 64) return fail(ctx, KF_EINVAL, "grid_mult must be 0..64");
   if (ctx->grid_mult[type][pass] != grid_mult) {
@@ -912,7 +916,7 @@ int kf_set_segment_length(kf_ctx *ctx, int type, int rows) {
 int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *scales, int nscales, int type,
                 int order, const kf_bank_opts *opts_in, int32_t *chosen, float *ms_out) {
   if (!ctx) return fail(nullptr, KF_EINVAL, "kf_autotune: ctx is NULL");
-  if (type < 0 || type > 2) return fail(ctx, KF_EINVAL, "unknown filter type %d", type);
+  if (type < 0 || type >= KF_NTYPES) return fail(ctx, KF_EINVAL, "unknown filter type %d", type);
   kf_bank_opts o;
   if (opts_in) o = *opts_in;
   else kf_bank_opts_default(&o);
@@ -930,7 +934,7 @@ int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *
     return -1;
   };
   cudaError_t e;
-  const bool iir = type != KF_FIR_COLORED_SG;
+  const bool iir = !is_fir(type);
   const int saved_lc = ctx->seg_len[type];
   // per candidate (segment length, shape): per-pass time
   const int nlc = iir ? 2 : 1;

@@ -15,7 +15,7 @@ constexpr int TW = 30;           // column-kernel tile interior width (32 with h
 constexpr int WARPM = 32;        // powers Phi^(CH m), m = 1..32, for the row scan
 constexpr int MAX_FIR_K = 160;   // largest colored-SG half-length
 
-enum { T_D = 0, T_E = 1, T_C = 2 };
+enum { T_D = 0, T_E = 1, T_C = 2, T_A = 3 };
 
 // Derivative channels of the row passes (Table I taps applied to the
 // edge-held frame before the blur): the Laplacian L = U + V of the fused path,
@@ -132,7 +132,7 @@ __device__ __forceinline__ void store_plane(void *P, long i, int st, float v) {
 // the input left-to-right (top-to-bottom) and y- right-to-left, both on the
 // INPUT (eq A10a-b), so the two directions are independent.
 struct Coef {
-  int type;      // T_D / T_E / T_C
+  int type;      // T_D / T_E / T_C / T_A
   int K;         // D: chain length = K^lpf; E: number of modes; C: FIR half-length
   int status;    // 0 ok, else design failure code
   int pad0;
@@ -151,7 +151,7 @@ struct Coef {
   float gr[MAXK], gi[MAXK];
   float hr[MAXK], hi[MAXK];      // steady state per unit input: 1/(1-z)
   float zMr[WARPM][MAXK], zMi[WARPM][MAXK];  // z^(CH m), m = 1..32
-  // Filter C taps h[0..K]
+  // FIR taps h[0..K] (Filter C or A)
   float h[MAX_FIR_K + 1];
   // FP64 design, copied to the host by kf_design
   double lambda, sigma, param, db0;

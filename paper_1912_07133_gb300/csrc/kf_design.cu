@@ -547,6 +547,39 @@ __device__ void design_C(Coef &c, int order, double lambda, int kmax, dd *A, dd 
   }
 }
 
+// Filter A (Sec. 3.1): eq 9 with d = 0, the Gaussian of standard deviation
+// sigma sampled at the integers |m| <= K, K = ceil(5 sigma) capped at kmax, and
+// renormalised to unit gain at dc by eq 11 (c_g = 1 / sum_m g0(m)).  One thread.
+__device__ void design_A(Coef &c, double lambda, int kmax) {
+  const double sigma = lambda / 2.0;
+  int K = (int)ceil(5.0 * sigma);
+  if (kmax > 0 && K > kmax) K = kmax;
+  if (!(sigma > 0.0) || K < 1 || K > MAX_FIR_K) {
+    c.status = 1;
+    return;
+  }
+  const double norm = 1.0 / (sigma * sqrt(2.0 * M_PI));
+  double dc = 0.0;
+  for (int m = 0; m <= K; ++m) {
+    c.dh[m] = norm * exp(-(double)m * (double)m / (2.0 * sigma * sigma));
+    dc += m == 0 ? c.dh[m] : 2.0 * c.dh[m];
+  }
+  const double cg = 1.0 / dc;
+  double dcg = 0.0, m2 = 0.0;
+  for (int m = 0; m <= K; ++m) {
+    c.dh[m] *= cg;
+    c.h[m] = (float)c.dh[m];
+    dcg += m == 0 ? c.dh[m] : 2.0 * c.dh[m];
+    m2 += 2.0 * (double)m * (double)m * c.dh[m];
+  }
+  c.K = K;
+  c.b0 = c.h[0];
+  c.db0 = c.dh[0];
+  c.dc_gain = dcg;
+  c.moment2 = m2;
+  c.param = sigma;
+}
+
 __global__ void __launch_bounds__(256) k_design(int type, int order, const double *lambdas,
                                                 int fir_kmax, Coef *out, double *work,
                                                 int Nmax) {
@@ -568,6 +601,7 @@ __global__ void __launch_bounds__(256) k_design(int type, int order, const doubl
   } else if (threadIdx.x == 0) {
     if (type == T_D) design_D(c, order, lambda);
     else if (type == T_E) design_E(c, order, lambda);
+    else if (type == T_A) design_A(c, lambda, fir_kmax);
     else c.status = 1;
   }
 }

@@ -30,6 +30,8 @@ KF_ERANGE = -9
 KF_IIR_REPEATED_POLE = 0
 KF_IIR_BUTTERWORTH = 1
 KF_FIR_COLORED_SG = 2
+KF_FIR_GAUSSIAN = 3
+FIR_TYPES = (KF_FIR_COLORED_SG, KF_FIR_GAUSSIAN)
 
 KF_DTYPE_F32 = 0
 KF_DTYPE_F16 = 1
@@ -202,7 +204,7 @@ def kf_design(ftype: int, order: int, scale: float) -> dict:
     K = c.K
     d = dict(type=c.type, order=c.order, K=K, scale=c.scale, sigma=c.sigma, param=c.param, b0=c.b0,
              dc_gain=c.dc_gain, moment2=c.moment2)
-    if ftype == KF_FIR_COLORED_SG:
+    if ftype in FIR_TYPES:
         d["h"] = np.array(c.h[: K + 1])
     else:
         d["bplus"] = np.array(c.bplus[: K + 1])

@@ -5,7 +5,7 @@ import numpy as np
 from oracle import oracle as O
 
 # filter type ids are the same small integers on both sides of the comparison
-OT = {0: O.IIR_REPEATED_POLE, 1: O.IIR_BUTTERWORTH, 2: O.FIR_COLORED_SG}
+OT = {0: O.IIR_REPEATED_POLE, 1: O.IIR_BUTTERWORTH, 2: O.FIR_COLORED_SG, 3: O.FIR_GAUSSIAN}
 TOL = 1e-5  # max |err| / per-scale response range (FP32 path)
 
 

@@ -13,7 +13,7 @@ from tests.parity import TOL, compare_blobs, gpu_bank, oracle_bank, scale_errors
 
 pytestmark = pytest.mark.gpu
 
-D, E, C = 0, 1, 2
+D, E, C, A = 0, 1, 2, 3
 SIX = [2.0, 4.0, 8.0, 16.0, 32.0, 48.0]
 
 
@@ -60,11 +60,22 @@ def test_design_colored_sg_matches_oracle(lam):
     np.testing.assert_allclose(g["h"], o, rtol=0, atol=1e-12 * np.abs(o).max())
 
 
+@pytest.mark.parametrize("lam", [1.0, 2.0, 4.0, 8.0, 16.0, 32.0, 48.0, 64.0])
+def test_design_gaussian_matches_oracle(lam):
+    """Filter A taps (eqs 9, 11) designed on the GPU in FP64 equal the oracle's."""
+    from paper_1912_07133_gb300 import kf
+    g = kf.kf_design(kf.KF_FIR_GAUSSIAN, 1, lam)
+    o = O.design_gaussian(lam / 2, 96)
+    assert len(g["h"]) == len(o) == min(int(np.ceil(2.5 * lam)), 96) + 1
+    np.testing.assert_allclose(g["h"], o, rtol=1e-14, atol=0)
+    assert g["dc_gain"] == pytest.approx(1.0, abs=1e-14)
+
+
 def test_design_rejects_invalid_parameters():
     from paper_1912_07133_gb300 import kf
     for args in [(kf.KF_IIR_REPEATED_POLE, 1, 4.0), (kf.KF_IIR_REPEATED_POLE, 3, 0.0),
                  (kf.KF_IIR_REPEATED_POLE, 3, -2.0), (kf.KF_FIR_COLORED_SG, 1, 1.8),
-                 (kf.KF_FIR_COLORED_SG, 3, 8.0), (7, 3, 4.0)]:
+                 (kf.KF_FIR_COLORED_SG, 3, 8.0), (kf.KF_FIR_GAUSSIAN, 2, 8.0), (7, 3, 4.0)]:
         with pytest.raises(kf.KfError) as e:
             kf.kf_design(*args)
         assert e.value.code == kf.KF_EINVAL
@@ -88,13 +99,13 @@ def test_tiny_single_scale_frame():
     assert nref >= 15 and ngot >= 15
 
 
-@pytest.mark.parametrize("ftype,order", [(D, 4), (D, 3), (E, 2), (C, 1)])
+@pytest.mark.parametrize("ftype,order", [(D, 4), (D, 3), (E, 2), (C, 1), (A, 1)])
 def test_six_scales_ragged_frame(ftype, order):
     img = S.iir_fir_frame(seed=5, H=777, W=1000, nblobs=30)
     _check(img, SIX, ftype, order)
 
 
-@pytest.mark.parametrize("ftype,order", [(D, 4), (C, 1)])
+@pytest.mark.parametrize("ftype,order", [(D, 4), (C, 1), (A, 1)])
 def test_adjacent_scale_neighbourhood(ftype, order):
     img = S.iir_fir_frame(seed=6, H=300, W=333, nblobs=10)
     _check(img, SIX, ftype, order, neigh=1)
@@ -102,7 +113,7 @@ def test_adjacent_scale_neighbourhood(ftype, order):
 
 @pytest.mark.parametrize("H,W", [(1, 1), (1, 37), (37, 1), (2, 3), (31, 33), (65, 130), (129, 31),
                                  (70, 4099)])
-@pytest.mark.parametrize("ftype,order", [(D, 3), (E, 2), (C, 1)])
+@pytest.mark.parametrize("ftype,order", [(D, 3), (E, 2), (C, 1), (A, 1)])
 def test_small_and_degenerate_shapes(H, W, ftype, order):
     rng = np.random.default_rng(H * 1000 + W)
     img = rng.uniform(0, 1, (H, W)).astype(np.float32)
@@ -157,7 +168,7 @@ def test_runs_are_bitwise_repeatable():
 # ---------------------------------------------------------------------------
 # full size: one 4096 x 4096 frame, six scales (the benchmarked workload)
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("ftype,order", [(D, 4), (C, 1)])
+@pytest.mark.parametrize("ftype,order", [(D, 4), (C, 1), (A, 1)])
 def test_full_size_4096_six_scales(ftype, order):
     img = S.iir_fir_frame()
     (nref, ngot, ndiff), errs = _check(img, SIX, ftype, order)
