@@ -618,7 +618,8 @@ def oracle_step(x, wl):
     """Both banks and the detector through the FP64 oracle on the array x."""
     from oracle import oracle as O
     for _, ft, order in wl["banks"]:
-        R = O.bank(x, wl["scales"], {0: O.IIR_REPEATED_POLE, 1: O.IIR_BUTTERWORTH, 2: O.FIR_COLORED_SG}[ft],
+        R = O.bank(x, wl["scales"], {0: O.IIR_REPEATED_POLE, 1: O.IIR_BUTTERWORTH, 2: O.FIR_COLORED_SG,
+                                     3: O.FIR_GAUSSIAN}[ft],
                    order, fir_kmax=wl["fir_kmax"])
         O.detect(R, THRESHOLD)
 
@@ -654,6 +655,81 @@ def cpu_baseline(img, wl, rows=None):
 # ---------------------------------------------------------------------------
 # reference arm: the oracle timed as a program
 # ---------------------------------------------------------------------------
+# Table V (Sec. 5): one 4096 x 4096 frame, one scale per bank call, the
+# Gaussian FIR (Filter A, K = 5 sigma) against the repeated-pole IIR (Filter D,
+# K^lpf = 3), sigma = 3, 6, 12, 24.  The paper's GPU times (s) for context
+# (another machine; its stage 1 alone).
+TABLE5_SIGMAS = (3.0, 6.0, 12.0, 24.0)
+TABLE5_PAPER_GPU_S = {"A": (0.30, 0.33, 0.42, 0.56), "D": (0.14, 0.14, 0.14, 0.13)}
+
+
+def run_table5(args):
+    """Single-scale banks, Filter A vs Filter D, on the 4096^2 six-scale frame
+    generator; every call with the 3x3 extremum and the ordered read-back."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_1912_07133_gb300 import kf, synthetic
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    kf.load()
+    dev = torch.device("cuda", local)
+    x = torch.from_numpy(synthetic.iir_fir_frame(seed=1, H=4096, W=4096)).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    bank = kf.Bank(local, stream.cuda_stream)
+    runs = [("A", kf.KF_FIR_GAUSSIAN, 1), ("D", kf.KF_IIR_REPEATED_POLE, 3)]
+    table, total_ms = {}, 0.0
+    with ClockSampler(local) as clk:
+        for name, ft, order in runs:
+            table[name] = {}
+            for sig in TABLE5_SIGMAS:
+                lam = [2.0 * sig]
+
+                def call():
+                    bank.run([x], lam, ft, order, threshold=THRESHOLD, fir_kmax=160, graph=True,
+                             neighbourhood=kf.KF_NEIGH_ALL_SCALES)
+                    return len(bank.blobs())
+
+                for _ in range(args.warmup):
+                    call()
+                ms = []
+                for _ in range(args.steps):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    nb = call()
+                    b.record(stream)
+                    b.synchronize()
+                    ms.append(a.elapsed_time(b))
+                med = float(np.median(ms))
+                total_ms += med
+                table[name][str(sig)] = {"ms": round(med, 4), "blobs": nb,
+                                         "K": (min(int(np.ceil(5 * sig)), 160) if ft == kf.KF_FIR_GAUSSIAN else order)}
+        clocks = clk.summary()
+    bank.close()
+    pix_scales = 4096 * 4096 * len(runs) * len(TABLE5_SIGMAS)
+    line = {
+        "metric": "Mpixel-scales/s, Table V single-scale banks (Filter A FIR vs Filter D IIR) on 1 GB300",
+        "value": round(pix_scales / (total_ms * 1e-3) / 1e6, 1), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "4096x4096 FP32 frame (six-scale generator), one scale per call: sigma = 3, 6, "
+                               "12, 24 px; Filter A (Gaussian FIR, K = 5 sigma) and Filter D (repeated pole, "
+                               "K^lpf = 3); Laplacian response, 3x3 extremum, blob list read back",
+                   "statistic": "median of the steps per (filter, sigma); value: their sum",
+                   "l2": "flushed between calls (256 MiB write outside the timed events)",
+                   "launch": "graph replays"},
+        "table_ms": table, "paper_gpu_seconds": {k: dict(zip(map(str, TABLE5_SIGMAS), v))
+                                                 for k, v in TABLE5_PAPER_GPU_S.items()},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -668,6 +744,13 @@ def run_reference(args):
         wl = dict(banks=IIR_FIR, scales=EIGHT, fir_kmax=96, value_scale=1.0, ref_rows=64,
                   text="clustered 6144-wide FP16 frames, 8 scales, both banks (oracle: plain bank, no gating)")
         img = synthetic.clustered_frame(seed=4000, H=256, W=6144).astype(np.float32)
+    elif args.workload == "table5":
+        from paper_1912_07133_gb300 import synthetic
+        wl = dict(banks=(("gaussian_fir", 3, 1), ("iir_repeated_pole_order3", 0, 3)),
+                  scales=[2.0 * s for s in TABLE5_SIGMAS], fir_kmax=160, value_scale=1.0, ref_rows=64,
+                  text="4096x4096 FP32 frame, sigma = 3, 6, 12, 24 px, Filter A (K = 5 sigma) and Filter D "
+                       "(K^lpf = 3), Laplacian response, 3x3 extremum")
+        img = synthetic.iir_fir_frame(seed=1, H=256, W=4096)
     else:
         wl = WORKLOADS[args.workload]
         img = make_frames(wl)[0]
@@ -704,7 +787,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("gated",), default="iir_fir")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("gated", "table5"), default="iir_fir")
     ap.add_argument("--gate-mode", choices=("dilated", "tiles"), default="dilated",
                     help="gated workload: marked tiles with their neighbours, or marked tiles only")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
@@ -719,6 +802,8 @@ def main():
         run_reference(args)
     elif args.workload == "gated":
         run_gated(args)
+    elif args.workload == "table5":
+        run_table5(args)
     else:
         run_ours(args)
 
