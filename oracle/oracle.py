@@ -15,6 +15,8 @@ import os
 import subprocess
 import threading
 
+import math
+
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -312,6 +314,31 @@ def bank(img, lambdas, ftype=IIR_REPEATED_POLE, order=3, resp=RESP_LAPLACIAN,
     if rc:
         raise ValueError("oracle bank: design failed")
     return (R, D) if want_d else R
+
+
+def blob_shape(d20, d02, d11, pol=1):
+    """Shape of a detection (Sec. 5, the Hessian passage after eq 26): with
+    H = [[D20, D11], [D11, D02]], P = (-pol H)^-1 is the covariance of the blob
+    read as a pdf (pol = +1 bright, -1 dark).  Returns (p1, p2, theta, det):
+    the eigenvalues of P, p1 >= p2 (pixels^2), the orientation of the p1
+    eigenvector (radians from +x towards +y, in (-pi/2, pi/2]) and |H|;
+    (nan, nan, nan, det) where -pol H is not positive definite.  A library
+    symmetric eigen-solver is the step."""
+    Hm = np.array([[d20, d11], [d11, d02]], dtype=np.float64)
+    det = float(d20 * d02 - d11 * d11)
+    M = -pol * Hm
+    w = np.linalg.eigvalsh(M)
+    if not (w[0] > 0.0):
+        return float("nan"), float("nan"), float("nan"), det
+    Pm = np.linalg.inv(M)
+    vals, vecs = np.linalg.eigh(Pm)  # ascending
+    v = vecs[:, 1]
+    theta = math.atan2(v[1], v[0])
+    if theta <= -math.pi / 2:
+        theta += math.pi
+    elif theta > math.pi / 2:
+        theta -= math.pi
+    return float(vals[1]), float(vals[0]), theta, det
 
 
 def threads() -> int:
