@@ -185,6 +185,18 @@ typedef struct {
                         derivative bank: R_H or offset_limit > 0; else 0) */
 } kf_blob;
 
+/* Shape of one blob (Sec. 5: the blurred image's Hessian H = [[D20, D11],
+ * [D11, D02]] at the detection read as minus the Fisher information of the
+ * blob taken as a pdf, P = (-pol H)^-1 its covariance, pol = +1 for a bright
+ * blob (D20 + D02 < 0), -1 for a dark one).  16 bytes. */
+typedef struct {
+  float p1, p2;  /* eigenvalues of P, p1 >= p2 (pixels^2); NaN where -pol H is
+                    not positive definite (a saddle)                           */
+  float theta;   /* orientation of the p1 axis: radians from +x towards +y, in
+                    (-pi/2, pi/2] (undefined when p1 = p2)                     */
+  float det;     /* |H| = D20 D02 - D11^2 (1 / pixels^4)                       */
+} kf_blob_shape;
+
 /* Per-kernel device time of the last profiled kf_filter_bank call. */
 typedef struct {
   char name[32];     /* kernel name                                   */
@@ -263,6 +275,17 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes,
  * storage overflowed in the last call), KF_ETIMEOUT, KF_ECUDA. */
 int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out,
                     int64_t capacity, int64_t *count);
+
+/* Shapes of the blobs kf_detect_blobs(ctx, threshold, ...) returns, in the
+ * same order: out[0..capacity) (host, caller-owned), *count (host) the number
+ * of blobs.  Needs a last kf_filter_bank call that ran the derivative bank
+ * (opts.response = KF_RESP_HESSIAN or opts.offset_limit > 0): the derivatives
+ * are read from its planes at each blob's scale and pixel.  Synchronises the
+ * context stream.
+ * Errors: KF_EINVAL (no derivative-bank result, bad arguments, threshold
+ * below the bank's), KF_EOVERFLOW (capacity < *count; the first `capacity`
+ * shapes are written), and those of kf_detect_blobs. */
+int kf_blob_shapes(kf_ctx *ctx, double threshold, kf_blob_shape *out, int64_t capacity, int64_t *count);
 
 /* Kernel launches and, when the call ran with opts->profile = 1, per-kernel
  * CUDA-event times of the last kf_filter_bank call: fills out[0..cap) (host,

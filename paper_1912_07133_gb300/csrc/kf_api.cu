@@ -120,6 +120,15 @@ struct kf_ctx {
   size_t g_count_n = 0;
   float *ch_buf = nullptr;  // derivative bank: channel planes sigma^2 D (3 or 5 x responses layout)
   size_t ch_floats = 0;
+  // the last call's derivative planes (kf_blob_shapes): channel stride, per
+  // frame (plane offset, H, W) on the host and its device copy, the shapes
+  bool have_dplanes = false;
+  size_t dplane_per = 0;
+  std::vector<long> dlay;
+  long *d_dlay = nullptr;
+  size_t d_dlay_n = 0;
+  float *shape_buf = nullptr;
+  size_t shape_floats = 0;
 };
 
 namespace {
@@ -428,6 +437,8 @@ void kf_destroy(kf_ctx *ctx) {
   drop_graphs(ctx);
   cudaFree(ctx->d_table);
   cudaFree(ctx->ch_buf);
+  cudaFree(ctx->d_dlay);
+  cudaFree(ctx->shape_buf);
   for (void *q : {(void *)ctx->g_pooled, (void *)ctx->g_logits, (void *)ctx->g_act, (void *)ctx->g_sel[0],
                   (void *)ctx->g_sel[1], (void *)ctx->g_count})
     cudaFree(q);
@@ -823,6 +834,13 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
                                   opts.offset_limit, ctx->stream))
       return cuda_fail(ctx, cudaGetLastError(), "derivative bank detector");
     if ((rc = issue_sort(ctx->stream, &ctx->prof))) return rc;
+    ctx->dplane_per = per;
+    ctx->dlay.assign(3 * (size_t)nframes, 0);
+    for (int f = 0; f < nframes; ++f) {
+      ctx->dlay[3 * f] = fd[f].roff;
+      ctx->dlay[3 * f + 1] = frames[f].height;
+      ctx->dlay[3 * f + 2] = frames[f].width;
+    }
   } else if (opts.graph && !opts.profile) {
     const std::vector<long long> key = call_key(ctx, frames, nframes, scales, nscales, type, order, kmax_opt, opts);
     kf_ctx::Graph *g = nullptr;
@@ -874,6 +892,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     if ((rc = issue(ctx->stream, &ctx->prof))) return rc;
   }
   ctx->have_result = true;
+  ctx->have_dplanes = dbank;
   ctx->sorted_valid = true;  // enqueued with the call
   ctx->sorted_thr = opts.threshold;
   ctx->npass_read = false;
@@ -1291,6 +1310,46 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
   if (ctx->sorted_n > capacity)
     return fail(ctx, KF_EOVERFLOW, "capacity %lld < %lld blobs", (long long)capacity,
                 (long long)ctx->sorted_n);
+  return KF_OK;
+}
+
+int kf_blob_shapes(kf_ctx *ctx, double threshold, kf_blob_shape *out, int64_t capacity, int64_t *count) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_blob_shapes: ctx is NULL");
+  if (!count || capacity < 0 || (capacity > 0 && !out))
+    return fail(ctx, KF_EINVAL, "kf_blob_shapes: bad output arguments");
+  if (!ctx->have_result || !ctx->have_dplanes)
+    return fail(ctx, KF_EINVAL,
+                "kf_blob_shapes: the last bank call did not run the derivative bank (KF_RESP_HESSIAN or offset_limit)");
+  // the ordered list at this threshold and its count (no records copied)
+  int64_t n = 0;
+  int rc = kf_detect_blobs(ctx, threshold, nullptr, 0, &n);
+  if (rc != KF_OK && rc != KF_EOVERFLOW) return rc;
+  *count = n;
+  if (n == 0) return KF_OK;
+  cudaError_t e;
+  if (ctx->d_dlay_n < ctx->dlay.size()) {
+    cudaFree(ctx->d_dlay);
+    ctx->d_dlay = nullptr;
+    ctx->d_dlay_n = 0;
+    if ((e = cudaMalloc(&ctx->d_dlay, sizeof(long) * ctx->dlay.size())) != cudaSuccess)
+      return cuda_fail(ctx, e, "cudaMalloc(shape layout)");
+    ctx->d_dlay_n = ctx->dlay.size();
+  }
+  if ((rc = grow(ctx, &ctx->shape_buf, &ctx->shape_floats, (size_t)4 * ctx->blob_cap, "shapes"))) return rc;
+  if ((e = cudaMemcpyAsync(ctx->d_dlay, ctx->dlay.data(), sizeof(long) * ctx->dlay.size(), cudaMemcpyHostToDevice,
+                           ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "shape layout");
+  const float *c20 = ctx->ch_buf, *c02 = ctx->ch_buf + ctx->dplane_per, *c11 = ctx->ch_buf + 2 * ctx->dplane_per;
+  if (kf::launch_shapes(ctx->sorted, (long)n, c20, c02, c11, ctx->d_dlay, ctx->cur->d_coef, ctx->shape_buf,
+                        ctx->stream))
+    return cuda_fail(ctx, cudaGetLastError(), "shape launch");
+  static_assert(sizeof(kf_blob_shape) == 4 * sizeof(float), "shape record layout");
+  const int64_t ncopy = std::min<int64_t>(capacity, n);
+  if (ncopy > 0 && (e = cudaMemcpyAsync(out, ctx->shape_buf, sizeof(kf_blob_shape) * ncopy, cudaMemcpyDeviceToHost,
+                                        ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "copy shapes");
+  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "shapes");
+  if (n > capacity) return fail(ctx, KF_EOVERFLOW, "capacity %lld < %lld shapes", (long long)capacity, (long long)n);
   return KF_OK;
 }
 

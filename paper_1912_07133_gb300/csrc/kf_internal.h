@@ -131,6 +131,12 @@ int fir_row_rows();            // rows of a FIR row item (items past the frame r
 int fir_tile_rows(int neigh);  // interior rows of a FIR column tile
 int fir_halo(int kmax);        // rows a FIR column tile reads beyond its 128 (or 64) rows
 
+// shape descriptors of an ordered blob list from the derivative-bank planes
+// (kf_deriv.cu); lay: per frame (plane offset, H, W); out: n float4 records
+// (p1, p2, theta, |H|)
+int launch_shapes(const Blob *b, long n, const float *c20, const float *c02, const float *c11, const long *lay,
+                  const Coef *coef, void *out, cudaStream_t st);
+
 // candidate ordering (kf_sort.cu)
 size_t sort_workspace_bytes(long cap);
 int launch_sort(const Blob *blobs, long cap, const unsigned long long *count, float thr, int nscales, long hmax,

@@ -54,7 +54,7 @@ ENTRY_POINTS = ("kf_bank_opts_default", "kf_create", "kf_destroy", "kf_last_erro
                 "kf_filter_bank", "kf_detect_blobs", "kf_kernel_times", "kf_responses_noalloc",
                 "kf_set_launch_shape", "kf_set_segment_length", "kf_autotune",
                 "kf_proposal_set_weights", "kf_proposal_get_weights", "kf_proposal_pool", "kf_proposal_logits",
-                "kf_proposal_grad", "kf_proposal_train_step", "kf_proposal_labels")
+                "kf_proposal_grad", "kf_proposal_train_step", "kf_proposal_labels", "kf_blob_shapes")
 KF_NET_NPARAM = 3640
 KF_NET_CHANNELS = 8
 KF_PASS_ROW, KF_PASS_SEG, KF_PASS_FOLD, KF_PASS_DET, KF_NPASS = 0, 1, 2, 3, 4
@@ -134,6 +134,8 @@ def load(path: str = LIB_PATH):
                                  ctypes.POINTER(kf_bank_opts)]
     L.kf_detect_blobs.restype = i32
     L.kf_detect_blobs.argtypes = [vp, dbl, ctypes.POINTER(kf_blob), i64, ctypes.POINTER(i64)]
+    L.kf_blob_shapes.restype = i32
+    L.kf_blob_shapes.argtypes = [vp, dbl, ctypes.POINTER(kf_blob_shape), i64, ctypes.POINTER(i64)]
     L.kf_kernel_times.restype = i32
     L.kf_kernel_times.argtypes = [vp, ctypes.POINTER(kf_kernel_time), i32, ctypes.POINTER(i32)]
     L.kf_responses_noalloc.restype = i32
@@ -279,6 +281,30 @@ def kf_detect_blobs(ctx: int, threshold: float, capacity: int = None) -> np.ndar
         return kf_detect_blobs(ctx, threshold, int(n.value))
     _check(rc, ctx)
     return out[: n.value]
+
+
+class kf_blob_shape(ctypes.Structure):
+    _fields_ = [("p1", ctypes.c_float), ("p2", ctypes.c_float), ("theta", ctypes.c_float), ("det", ctypes.c_float)]
+
+
+SHAPE_DTYPE = np.dtype([("p1", "<f4"), ("p2", "<f4"), ("theta", "<f4"), ("det", "<f4")])
+
+
+def kf_blob_shapes(ctx: int, threshold: float) -> np.ndarray:
+    """Shapes (p1, p2, theta, |H|) of the blobs kf_detect_blobs returns at
+    this threshold, in the same order (the last call must have run the
+    derivative bank)."""
+    L = load()
+    n = ctypes.c_int64(0)
+    rc = L.kf_blob_shapes(ctx, float(threshold), None, 0, ctypes.byref(n))
+    if rc not in (KF_OK, KF_EOVERFLOW):
+        _check(rc, ctx)
+    out = np.empty(int(n.value), dtype=SHAPE_DTYPE)
+    if n.value == 0:
+        return out
+    _check(L.kf_blob_shapes(ctx, float(threshold), out.ctypes.data_as(ctypes.POINTER(kf_blob_shape)), len(out),
+                            ctypes.byref(n)), ctx)
+    return out
 
 
 def kf_kernel_times(ctx: int) -> dict:
@@ -446,6 +472,10 @@ class Bank:
 
     def kernel_times(self) -> dict:
         return kf_kernel_times(self.ctx)
+
+    def shapes(self, threshold=None) -> np.ndarray:
+        """Shapes of the blobs `blobs(threshold)` returns (derivative bank)."""
+        return kf_blob_shapes(self.ctx, self.threshold if threshold is None else threshold)
 
     def blobs(self, threshold=None, capacity=None) -> np.ndarray:
         """Blob list of the last run.  If the context's device candidate list

@@ -54,6 +54,7 @@ def test_struct_layouts_match_header(lib):
     from paper_1912_07133_gb300 import kf
     assert ctypes.sizeof(kf.kf_frame) == 32
     assert ctypes.sizeof(kf.kf_blob) == 32
+    assert ctypes.sizeof(kf.kf_blob_shape) == 16
     assert ctypes.sizeof(kf.kf_bank_opts) == 4 * 4 + 8 + 8 + 8 + 32
     assert ctypes.sizeof(kf.kf_kernel_time) == 40
     o = kf.kf_bank_opts_default()
@@ -76,6 +77,7 @@ def test_field_offsets_match_the_c_compiler(tmp_path):
     import ctypes
     from paper_1912_07133_gb300 import kf
     structs = {"kf_frame": kf.kf_frame, "kf_bank_opts": kf.kf_bank_opts, "kf_blob": kf.kf_blob,
+               "kf_blob_shape": kf.kf_blob_shape,
                "kf_kernel_time": kf.kf_kernel_time, "kf_coeffs": kf.kf_coeffs}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kf.h"', "int main(void) {"]
     for name, cls in structs.items():
