@@ -201,3 +201,24 @@ WORKLOADS = {
     "iir_fir_4096": Workload("4096x4096 FP32, 6 scales (lambda 2..48), Filter D 4th order "
                              "and colored SG FIR", SCALES_IIR_FIR, "iir_fir_frame(seed=1)"),
 }
+
+
+def ellipse_pattern(ecc: float = 2.0, axes=(4, 8, 16, 32, 64), rotations=(0, 15, 30, 45), cell: int = 160):
+    """The test pattern of Figs. 6 and 7 (Sec. 5): solid black ellipses on a
+    white background, semi-major axes `axes` (px) from left to right, axis
+    ratio `ecc`, rotated by `rotations` (degrees) from top to bottom, one per
+    cell x cell square.  Returns (FP32 image, [(cy, cx, a, rotation), ...])."""
+    import math
+    H, W = cell * len(rotations), cell * len(axes)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    img = np.ones((H, W))
+    centres = []
+    for i, r in enumerate(rotations):
+        for j, a in enumerate(axes):
+            cy, cx = cell * i + cell / 2, cell * j + cell / 2
+            b, t = a / ecc, math.radians(r)
+            u = (x - cx) * math.cos(t) + (y - cy) * math.sin(t)
+            v = -(x - cx) * math.sin(t) + (y - cy) * math.cos(t)
+            img[(u / a) ** 2 + (v / b) ** 2 <= 1.0] = 0.0
+            centres.append((cy, cx, a, r))
+    return img.astype(np.float32), centres

@@ -761,3 +761,41 @@ def test_blob_shape_of_a_blurred_gaussian_blob():
     w, V = np.linalg.eigh(want)
     assert math.remainder(theta - math.atan2(V[1, 1], V[0, 1]), math.pi) == pytest.approx(0.0, abs=1e-2)
     assert p1 / p2 == pytest.approx(w[1] / w[0], rel=2e-2)
+
+
+# ----------------------------------------------------------------------------
+# Figs. 6 and 7 (Sec. 5): scale selectivity of the normalised Hessian with one
+# scale-invariant Threshold #1, and Threshold #2 against detections on the
+# tips of elongated blobs
+# ----------------------------------------------------------------------------
+def nearest(b, centres):
+    return min((math.hypot(b["y"] - cy, b["x"] - cx), a, r) for cy, cx, a, r in centres)
+
+
+def test_fig6_each_scale_detects_the_centres_of_its_matched_ellipses():
+    """Axis ratio 2, axes 4..64 px, rotations 0..45 deg; Filter D (Table IV),
+    lambda = 4..64 one at a time: every detection lies at the centre of an
+    ellipse whose semi-major axis equals lambda, and all four rotations are
+    found, with one threshold for all scales."""
+    from paper_1912_07133_gb300 import synthetic as SYN
+    img, centres = SYN.ellipse_pattern(2.0)
+    for lam in (4, 8, 16, 32, 64):
+        R = O.bank(img.astype(np.float64), [float(lam)], O.IIR_REPEATED_POLE, 3, O.RESP_HESSIAN)
+        b = O.detect(R, 0.035, O.RESP_HESSIAN, O.NEIGH_ALL)
+        near = [nearest(r, centres) for r in b]
+        assert all(a == lam and d <= 0.05 * lam + 1.0 for d, a, _ in near), (lam, near)
+        assert sorted(r for _, _, r in near) == [0, 15, 30, 45], lam
+
+
+def test_fig7_threshold_2_keeps_only_the_centres_of_matched_ellipses():
+    """Axis ratio 4, lambda = 16: Threshold #1 alone also fires on the tips of
+    the longer ellipses; with Threshold #2 (offset limit 2 px) only the
+    centres of the 16-px ellipses remain."""
+    from paper_1912_07133_gb300 import synthetic as SYN
+    img, centres = SYN.ellipse_pattern(4.0)
+    R, D = O.bank(img.astype(np.float64), [16.0], O.IIR_REPEATED_POLE, 3, O.RESP_HESSIAN, want_d=True)
+    t1 = [nearest(r, centres) for r in O.detect(R, 0.02, O.RESP_HESSIAN, O.NEIGH_ALL, D=D)]
+    tips = [x for x in t1 if x[1] > 16 and x[0] > 0.3 * x[1]]
+    assert len(tips) >= 8
+    t12 = [nearest(r, centres) for r in O.detect(R, 0.02, O.RESP_HESSIAN, O.NEIGH_ALL, D=D, limit2=2.0)]
+    assert t12 and all(a == 16 and d <= 1.0 for d, a, _ in t12)
