@@ -741,7 +741,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     if (kf::gate_select_tiles(plan.fr, full_det, ctx->g_act, TW_COL, rows, ctx->g_sel[0], ctx->g_count, st))
       return cuda_fail(ctx, cudaGetLastError(), "gate selection");
     if (!iir && kf::gate_select_rows(plan.fr, full_row, ctx->g_act, kf::fir_row_segment(), kf::fir_row_rows(),
-                                     kf::fir_halo(kmax) + 130,
+                                     kf::fir_halo(kmax) + rows + 4,
                                      ctx->g_sel[1], ctx->g_count + 1, st))
       return cuda_fail(ctx, cudaGetLastError(), "gate selection");
     prof->end(st);
