@@ -287,6 +287,49 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out,
  * shapes are written), and those of kf_detect_blobs. */
 int kf_blob_shapes(kf_ctx *ctx, double threshold, kf_blob_shape *out, int64_t capacity, int64_t *count);
 
+/* ---- the D = 5 derivative bank (L_D = 2) ----------------------------------
+ * Sec. 4 with D = 2 L_D + 1 = 5: every derivative D_{dx,dy} (eq 3) with
+ * dx + dy <= 4 of the quartic model (eq 1) at each scale, estimated by
+ * separable filters whose moments vanish up to order 4: the differentiator
+ * g_d of Sec. 4.1 (eqs 12-17, pure-delay basis, dc constraints; the five-point
+ * central differences) along x and along y, cascaded with a blur flat at dc
+ * to order 4.  Channel c of a set holds (dx, dy) with n = dx + dy, c =
+ * n (n + 1) / 2 + dy: (0,0); (1,0) (0,1); (2,0) (1,1) (0,2); (3,0) (2,1)
+ * (1,2) (0,3); (4,0) (3,1) (2,2) (1,3) (0,4).  x is the column index, y the
+ * row index; the frame is held beyond its edges (the hold boundary). */
+#define KF_QUARTIC_CHANNELS 15
+
+/* D_{dx,dy} of one frame at nscales scales.
+ *   frame   one device frame (any KF_DTYPE_*, value_scale applied), width
+ *           <= 8188
+ *   scales  host, nscales values lambda > 0 (sigma = lambda / 2), 1..16
+ *   type, order  the blur: KF_IIR_REPEATED_POLE with order = K^lpf = L_D +
+ *           Lbar_pi in 3..6 (L_D = 2 design of Sec. 4.3; at least one Nyquist
+ *           constraint, without which the design is the unit impulse),
+ *           KF_IIR_BUTTERWORTH with order = L_B / 2 in 3..6 (flat to order
+ *           L_B - 1 >= 5), or
+ *           KF_FIR_COLORED_SG with order = L_D = 2 (K = ceil(7 sigma) <= 96,
+ *           omega_c = 3 / sigma, Sec. 4.2)
+ *   out     device, f32, caller-owned: nscales x 15 planes of H x W,
+ *           out[((s * 15 + c) * H + y) * W + x]
+ * Runs on the context stream (asynchronous; out is complete when the stream
+ * is).  Uses the context's bank: afterwards kf_detect_blobs has no result
+ * until the next kf_filter_bank call.
+ * Errors: KF_EINVAL (bad arguments, a type or order without vanishing
+ * moments to order 4), KF_ECOND (design), KF_ECUDA. */
+int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, int nscales, int type,
+                    int order, float *out);
+
+/* Steered derivatives (Sec. 2, after eq 3): with x~ = x cos(phi) + y sin(phi)
+ * and y~ = -x sin(phi) + y cos(phi), the coefficients beta (eq 2: beta_{dx,dy}
+ * = D_{dx,dy} / (dx! dy!)) of the polynomial in (x~, y~) are re-expressed as
+ * the coefficients of the same polynomial in (x, y); each total order maps
+ * to itself.  in, out: device f32, nsets sets of 15 channel planes of npix
+ * pixels each (the layout of kf_quartic_bank's out: nsets = nscales, npix =
+ * H W); out may equal in.  Asynchronous on the context stream.
+ * Errors: KF_EINVAL (NULL pointers, npix < 1, nsets < 1), KF_ECUDA. */
+int kf_quartic_steer(kf_ctx *ctx, const float *in, int64_t npix, int nsets, double phi, float *out);
+
 /* Kernel launches and, when the call ran with opts->profile = 1, per-kernel
  * CUDA-event times of the last kf_filter_bank call: fills out[0..cap) (host,
  * caller-owned) and sets *n (host) to the number of distinct kernels.

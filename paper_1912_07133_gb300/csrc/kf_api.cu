@@ -33,9 +33,9 @@ struct kf_ctx {
   kf::DevStatus *status = nullptr;
   kf::Blob *blobs = nullptr;
   long blob_cap = 0;
-  // design cache: (type, order, kmax, scales) -> coefficients, LRU
+  // design cache: (type, order, L_D, kmax, scales) -> coefficients, LRU
   struct Design {
-    int type = -1, order = -1, kmax = -1, S = 0;
+    int type = -1, order = -1, ld = 1, kmax = -1, S = 0;
     double lam[KF_MAX_SCALES];
     kf::Coef *d_coef = nullptr;
     std::vector<kf::Coef> h_coef;
@@ -129,6 +129,14 @@ struct kf_ctx {
   size_t d_dlay_n = 0;
   float *shape_buf = nullptr;
   size_t shape_floats = 0;
+  // D = 5 bank (kf_quartic_bank): while it runs its channels through the
+  // bank call, the call blurs channel q_chan of its frame as raw planes with
+  // the L_D = q_ld designs; q_chan < 0 otherwise
+  int q_chan = -1, q_ld = 1;
+  float *q_pad = nullptr;  // one differentiated channel on the frame padded by 2
+  size_t q_pad_floats = 0;
+  float *q_raw = nullptr;  // its raw planes sigma^2 D, per scale
+  size_t q_raw_floats = 0;
 };
 
 namespace {
@@ -220,9 +228,9 @@ int nmax_for(int type, int order, int kmax) {
 // already holds exactly this design (small LRU cache); ctx->cur points at it.
 constexpr size_t kDesignSlots = 8;
 
-int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S, int kmax) {
+int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S, int kmax, int ld = 1) {
   for (auto &d : ctx->designs)
-    if (d.type == type && d.order == order && d.kmax == kmax && d.S == S &&
+    if (d.type == type && d.order == order && d.ld == ld && d.kmax == kmax && d.S == S &&
         std::equal(scales, scales + S, d.lam)) {
       d.used = ++ctx->tick;
       ctx->cur = &d;
@@ -263,7 +271,7 @@ int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S,
                            ctx->stream)) != cudaSuccess)
     return cuda_fail(ctx, e, "copy scales");
   if (kf::launch_design(type, order, ctx->lambdas, S, kmax, slot->d_coef, ctx->dwork, ctx->dwork_nmax,
-                        ctx->stream))
+                        ctx->stream, ld))
     return cuda_fail(ctx, cudaGetLastError(), "design kernel launch");
   slot->h_coef.resize(S);
   if ((e = cudaMemcpyAsync(slot->h_coef.data(), slot->d_coef, sizeof(kf::Coef) * S,
@@ -282,6 +290,7 @@ int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S,
   }
   slot->type = type;
   slot->order = order;
+  slot->ld = ld;
   slot->kmax = kmax;
   slot->S = S;
   std::copy(scales, scales + S, slot->lam);
@@ -439,6 +448,8 @@ void kf_destroy(kf_ctx *ctx) {
   cudaFree(ctx->ch_buf);
   cudaFree(ctx->d_dlay);
   cudaFree(ctx->shape_buf);
+  cudaFree(ctx->q_pad);
+  cudaFree(ctx->q_raw);
   for (void *q : {(void *)ctx->g_pooled, (void *)ctx->g_logits, (void *)ctx->g_act, (void *)ctx->g_sel[0],
                   (void *)ctx->g_sel[1], (void *)ctx->g_count})
     cudaFree(q);
@@ -559,7 +570,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   }
   cudaError_t e;
   if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
-  rc = ensure_design(ctx, type, order, scales, nscales, kmax_opt);
+  rc = ensure_design(ctx, type, order, scales, nscales, kmax_opt, ctx->q_ld);
   if (rc) return rc;
   int nstate = 0, kmax = 0;
   for (int s = 0; s < nscales; ++s) {
@@ -762,6 +773,10 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   a.blobs = ctx->blobs;
   a.cap = ctx->blob_cap;
   a.status = ctx->status;
+  if (ctx->q_chan >= 0) {  // a channel of the D = 5 bank: raw planes, no detection
+    a.chan = ctx->q_chan;
+    a.raw = 1;
+  }
   // the candidate ordering at the bank threshold runs at the end of the call
   if ((rc = ensure_sort(ctx))) return rc;
   long wmax = 0;
@@ -1310,6 +1325,120 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
   if (ctx->sorted_n > capacity)
     return fail(ctx, KF_EOVERFLOW, "capacity %lld < %lld blobs", (long long)capacity,
                 (long long)ctx->sorted_n);
+  return KF_OK;
+}
+
+int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, int nscales, int type,
+                    int order, float *out) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_quartic_bank: ctx is NULL");
+  if (!frame || !out) return fail(ctx, KF_EINVAL, "kf_quartic_bank: frame and out must not be NULL");
+  if (!scales || nscales < 1 || nscales > KF_MAX_SCALES)
+    return fail(ctx, KF_EINVAL, "nscales must be 1..%d", KF_MAX_SCALES);
+  // blurs flat at dc to order 4 (L_D = 2)
+  if (type == KF_IIR_REPEATED_POLE) {
+    if (order < 3 || order > 6)
+      return fail(ctx, KF_EINVAL, "the D = 5 bank's repeated-pole order (L_D + Lbar_pi) must be 3..6 (got %d)", order);
+  } else if (type == KF_IIR_BUTTERWORTH) {
+    if (order < 3 || order > 6)
+      return fail(ctx, KF_EINVAL, "the D = 5 bank's Butterworth order (L_B / 2) must be 3..6 (got %d)", order);
+  } else if (type == KF_FIR_COLORED_SG) {
+    if (order != 2) return fail(ctx, KF_EINVAL, "the D = 5 bank's colored SG blur needs L_D = 2 (got %d)", order);
+  } else {
+    return fail(ctx, KF_EINVAL, "the D = 5 bank needs a blur with vanishing moments (types 0, 1, 2; got %d)", type);
+  }
+  const int W = frame->width, H = frame->height;
+  if (!frame->data || W < 1 || H < 1 || frame->pitch < W)
+    return fail(ctx, KF_EINVAL, "kf_quartic_bank: bad frame %dx%d pitch %lld", W, H, (long long)frame->pitch);
+  if (W > 8188) return fail(ctx, KF_EINVAL, "kf_quartic_bank: width > 8188");
+  if (frame->dtype < KF_DTYPE_F32 || frame->dtype > KF_DTYPE_U16)
+    return fail(ctx, KF_EINVAL, "kf_quartic_bank: unknown dtype %d", frame->dtype);
+  if (!std::isfinite(frame->value_scale)) return fail(ctx, KF_EINVAL, "kf_quartic_bank: value_scale is not finite");
+  if ((reinterpret_cast<uintptr_t>(frame->data) & (uintptr_t)(kf::in_bytes(frame->dtype) - 1)) != 0)
+    return fail(ctx, KF_EINVAL, "kf_quartic_bank: data is not aligned to its element size");
+  cudaError_t e;
+  if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  const int Wp = W + 4, Hp = H + 4;
+  const size_t npad = (size_t)Wp * Hp;
+  int rc;
+  if ((rc = grow(ctx, &ctx->q_pad, &ctx->q_pad_floats, npad, "D = 5 channel plane"))) return rc;
+  if ((rc = grow(ctx, &ctx->q_raw, &ctx->q_raw_floats, npad * nscales, "D = 5 raw planes"))) return rc;
+  struct Restore {
+    kf_ctx *c;
+    ~Restore() {
+      c->q_chan = -1;
+      c->q_ld = 1;
+    }
+  } restore{ctx};
+  ctx->q_ld = type == KF_IIR_REPEATED_POLE ? 2 : 1;
+  const float vs = frame->value_scale == 0.f ? 1.f : frame->value_scale;
+  kf_frame pf{};
+  pf.data = ctx->q_pad;
+  pf.width = Wp;
+  pf.height = Hp;
+  pf.pitch = Wp;
+  pf.dtype = KF_DTYPE_F32;
+  pf.value_scale = 1.f;
+  kf_bank_opts o;
+  kf_bank_opts_default(&o);
+  o.responses = ctx->q_raw;
+  o.storage = KF_DTYPE_F32;
+  o.graph = 0;
+  o.gate = KF_GATE_OFF;
+  // FIR blur: the FP32-FMA column pass (the one of the adjacent-scale
+  // neighbourhood; raw planes are not detected, so the neighbourhood has no
+  // other effect).  The tensor-core pass's three TF32 products carry about
+  // 2^-21 of each tap product, and the fourth differences of a textured frame
+  // are up to a thousand times larger than their blurred output.
+  if (type == KF_FIR_COLORED_SG) o.neighbourhood = KF_NEIGH_ADJACENT;
+  for (int n = 0, c = 0; n <= 4; ++n)
+    for (int dy = 0; dy <= n; ++dy, ++c) {
+      if (kf::launch_hpf5(frame->data, frame->dtype, vs, (long)frame->pitch, W, H, n - dy, dy, ctx->q_pad,
+                          ctx->stream))
+        return cuda_fail(ctx, cudaGetLastError(), "differentiator launch");
+      ctx->q_chan = kf::CH_ID;
+      if ((rc = kf_filter_bank(ctx, &pf, 1, scales, nscales, type, order, &o))) return rc;
+      if (kf::launch_quartic_crop(ctx->q_raw, W, H, nscales, ctx->cur->d_coef, c, out, ctx->stream))
+        return cuda_fail(ctx, cudaGetLastError(), "D = 5 crop launch");
+    }
+  ctx->have_result = false;  // the bank ran raw planes: no blob list
+  return KF_OK;
+}
+
+int kf_quartic_steer(kf_ctx *ctx, const float *in, int64_t npix, int nsets, double phi, float *out) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_quartic_steer: ctx is NULL");
+  if (!in || !out || npix < 1 || nsets < 1 || !std::isfinite(phi))
+    return fail(ctx, KF_EINVAL, "kf_quartic_steer: bad arguments");
+  // Per order n: the coefficient of x^(n-a) y^a in the expansion of
+  // (x cos + y sin)^(n-b) (-x sin + y cos)^b, as polynomials in y with x
+  // implied, scaled from beta to D by (n-a)! a! / ((n-b)! b!).
+  const double cph = std::cos(phi), sph = std::sin(phi);
+  float m55[55];
+  int mb = 0;
+  for (int n = 0; n <= 4; ++n) {
+    for (int b = 0; b <= n; ++b) {
+      double poly[5] = {1.0, 0.0, 0.0, 0.0, 0.0};  // coefficient of y^k
+      int deg = 0;
+      auto times = [&](double cx, double cy) {  // poly *= (cx x + cy y)
+        for (int k = deg + 1; k >= 0; --k) poly[k] = cx * poly[k] + (k > 0 ? cy * poly[k - 1] : 0.0);
+        ++deg;
+      };
+      for (int i = 0; i < n - b; ++i) times(cph, sph);
+      for (int i = 0; i < b; ++i) times(-sph, cph);
+      for (int a = 0; a <= n; ++a) {
+        double fa = 1.0, fb = 1.0;
+        for (int k = 2; k <= n - a; ++k) fa *= k;
+        for (int k = 2; k <= a; ++k) fa *= k;
+        for (int k = 2; k <= n - b; ++k) fb *= k;
+        for (int k = 2; k <= b; ++k) fb *= k;
+        m55[mb + a * (n + 1) + b] = (float)(poly[a] * fa / fb);
+      }
+    }
+    mb += (n + 1) * (n + 1);
+  }
+  cudaError_t e;
+  if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  if (kf::launch_steer(in, (long)npix, nsets, m55, out, ctx->stream))
+    return cuda_fail(ctx, cudaGetLastError(), "steering launch");
   return KF_OK;
 }
 

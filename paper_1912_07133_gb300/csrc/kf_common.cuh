@@ -26,12 +26,16 @@ enum { T_D = 0, T_E = 1, T_C = 2, T_A = 3 };
 // Beyond the left/right edges the x-differences (U, W, DX) vanish and V, DY
 // keep their row-end value; beyond the top/bottom the y-differences (V, W, DY)
 // vanish and U, DX keep the value of the first/last row.  CH_ZERO: the edge
-// rows of the y-vanishing channels.
-enum { CH_LAP = 0, CH_U = 1, CH_V = 2, CH_W = 3, CH_DX = 4, CH_DY = 5, CH_ZERO = 6 };
+// rows of the y-vanishing channels.  CH_ID: the frame itself, held beyond
+// every edge (the blur alone: the D = 5 bank differentiates before the bank).
+enum { CH_LAP = 0, CH_U = 1, CH_V = 2, CH_W = 3, CH_DX = 4, CH_DY = 5, CH_ZERO = 6, CH_ID = 7 };
+
+// channels of the D = 5 bank: every D_{dx,dy} with dx + dy <= 4
+constexpr int QUARTIC_NCH = 15;
 
 // the channel the U-only edge rows carry (the y-held part of the channel)
 __host__ __device__ __forceinline__ int edge_chan(int c) {
-  return (c == CH_LAP || c == CH_U) ? CH_U : (c == CH_DX ? CH_DX : CH_ZERO);
+  return (c == CH_LAP || c == CH_U) ? CH_U : (c == CH_DX ? CH_DX : (c == CH_ID ? CH_ID : CH_ZERO));
 }
 
 // channel c at column e (0 <= e < W) from rows y-1 (m), y (o), y+1 (p);
@@ -45,6 +49,7 @@ __device__ __forceinline__ float chan_at(int c, AM m, AO o, AP p, int e) {
     case CH_W: return 0.25f * ((p(e + 1) - p(e - 1)) - (m(e + 1) - m(e - 1)));
     case CH_DX: return 0.5f * (o(e + 1) - o(e - 1));
     case CH_DY: return 0.5f * (p(e) - m(e));
+    case CH_ID: return o(e);
     default: return 0.f;
   }
 }
@@ -56,6 +61,7 @@ __device__ __forceinline__ float chan_beyond(int c, AM m, AO o, AP p, int e) {
     case CH_LAP:
     case CH_V: return p(e) - 2.f * o(e) + m(e);
     case CH_DY: return 0.5f * (p(e) - m(e));
+    case CH_ID: return o(e);
     default: return 0.f;
   }
 }

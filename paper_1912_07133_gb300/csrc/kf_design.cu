@@ -119,20 +119,21 @@ __device__ int solve_small(int n, double *A, double *b) {
 
 // ---------------------------------------------------------------------------
 // Filter D (Sec. 4.3): basis |m|^k p^|m| (k < N_K - 1) plus the unit impulse,
-// constraints at dc (l = 0, 2) and Nyquist (l = 0, 2, .., 2(Lpi-1)) (eqs
-// 13-15, 23-24), c = F^-1 rho.  The pole used is the FP32-rounded p, so the
-// realised recursion satisfies the constraints exactly.
+// constraints at dc (l = 0, 2, .., 2 L_D) and Nyquist (l = 0, 2, ..,
+// 2(Lpi-1)) (eqs 13-15, 23-24), c = F^-1 rho, with order = K^lpf = L_D + Lpi.
+// The pole used is the FP32-rounded p, so the realised recursion satisfies
+// the constraints exactly.
 // ---------------------------------------------------------------------------
-__device__ void design_D(Coef &c, int order, double lambda) {
+__device__ void design_D(Coef &c, int order, double lambda, int ld) {
   const double sigma = lambda / 2.0;
-  const int K = order, Lpi = order - 1, NK = order + 1;
-  if (!(sigma > 0.0) || order < 1 || order > MAXK) { c.status = 1; return; }
+  const int K = order, Ldc = ld + 1, NK = order + 1;
+  if (!(sigma > 0.0) || ld < 1 || order < ld || order > MAXK) { c.status = 1; return; }
   const float pf = (float)exp(-1.0 / sigma);
   const double p = (double)pf, q = 1.0 - p;
   double F[10 * 10], cc[10];
   for (int r = 0; r < NK; ++r) {
-    const bool at_pi = r >= 2;
-    const int lbar = at_pi ? r - 2 : r, l = 2 * lbar;
+    const bool at_pi = r >= Ldc;
+    const int lbar = at_pi ? r - Ldc : r, l = 2 * lbar;
     const double sgn = (lbar & 1) ? -1.0 : 1.0, z = at_pi ? -p : p;
     for (int k = 0; k < NK; ++k) {
       double v;
@@ -142,7 +143,6 @@ __device__ void design_D(Coef &c, int order, double lambda) {
     }
     cc[r] = (r == 0) ? 1.0 : 0.0;
   }
-  (void)Lpi;
   if (solve_small(NK, F, cc)) { c.status = 2; return; }
   double hm[MAXK + 1];
   for (int m = 0; m <= K; ++m) {
@@ -580,7 +580,7 @@ __device__ void design_A(Coef &c, double lambda, int kmax) {
   c.param = sigma;
 }
 
-__global__ void __launch_bounds__(256) k_design(int type, int order, const double *lambdas,
+__global__ void __launch_bounds__(256) k_design(int type, int order, int ld, const double *lambdas,
                                                 int fir_kmax, Coef *out, double *work,
                                                 int Nmax) {
   const int s = blockIdx.x;
@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(256) k_design(int type, int order, const doubl
     dd *A = reinterpret_cast<dd *>(work) + (size_t)s * ((size_t)Nmax * Nmax + Nmax);
     design_C(c, order, lambda, fir_kmax, A, A + (size_t)Nmax * Nmax, Nmax);
   } else if (threadIdx.x == 0) {
-    if (type == T_D) design_D(c, order, lambda);
+    if (type == T_D) design_D(c, order, lambda, ld);
     else if (type == T_E) design_E(c, order, lambda);
     else if (type == T_A) design_A(c, lambda, fir_kmax);
     else c.status = 1;
@@ -609,8 +609,8 @@ __global__ void __launch_bounds__(256) k_design(int type, int order, const doubl
 }  // namespace
 
 int launch_design(int type, int order, const double *d_lambdas, int S, int fir_kmax, Coef *d_out,
-                  double *d_work, int Nmax, cudaStream_t st) {
-  k_design<<<S, 256, 0, st>>>(type, order, d_lambdas, fir_kmax, d_out, d_work, Nmax);
+                  double *d_work, int Nmax, cudaStream_t st, int ld) {
+  k_design<<<S, 256, 0, st>>>(type, order, ld, d_lambdas, fir_kmax, d_out, d_work, Nmax);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

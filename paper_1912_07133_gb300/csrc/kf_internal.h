@@ -14,9 +14,10 @@ namespace kf {
 
 // FP64 design of S scales into d_out (device array of S Coef).  d_work holds
 // S * 2 (Nmax^2 + Nmax) doubles (double-double KKT matrix and right-hand side
-// of the colored-SG design).
+// of the colored-SG design).  ld: L_D of a Filter D design (1: the D = 3
+// bank; 2: D = 5); the other types take L_D from `order`.
 int launch_design(int type, int order, const double *d_lambdas, int S, int fir_kmax, Coef *d_out,
-                  double *d_work, int Nmax, cudaStream_t st);
+                  double *d_work, int Nmax, cudaStream_t st, int ld = 1);
 
 // Optional per-launch event recording (profiling) and launch counting.
 struct Prof {
@@ -136,6 +137,17 @@ int fir_halo(int kmax);        // rows a FIR column tile reads beyond its 128 (o
 // (p1, p2, theta, |H|)
 int launch_shapes(const Blob *b, long n, const float *c20, const float *c02, const float *c11, const long *lay,
                   const Coef *coef, void *out, cudaStream_t st);
+
+// D = 5 derivative bank (kf_quartic.cu): the differentiated channel (dx, dy)
+// of a frame on the frame padded by 2 (f32, pitch W + 4, H + 4 rows); the
+// bank's raw planes of that channel back to D in out[s][chan][H][W]; the
+// steering of 15-channel sets (m55: per order n = 0..4 an (n+1) x (n+1)
+// row-major block)
+int launch_hpf5(const void *X, int dtype, float vs, long pitch, int W, int H, int dx, int dy, float *out,
+                cudaStream_t st);
+int launch_quartic_crop(const float *raw, int W, int H, int S, const Coef *coef, int chan, float *out,
+                        cudaStream_t st);
+int launch_steer(const float *in, long npix, int nsets, const float *m55, float *out, cudaStream_t st);
 
 // candidate ordering (kf_sort.cu)
 size_t sort_workspace_bytes(long cap);

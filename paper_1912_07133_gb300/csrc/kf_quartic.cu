@@ -1,0 +1,157 @@
+// kf_quartic.cu -- the kernels of the D = 5 derivative bank (L_D = 2).
+//
+// The bank estimates D_{dx,dy} (eq 3) for every dx + dy <= 4 at each scale
+// by separable filtering (Sec. 2): the differentiator g_dx along x and g_dy
+// along y (Sec. 4.1), then the L_D = 2 blur along x and along y (the bank's
+// row and column passes, channel CH_ID).  The differentiators run first, in
+// k_hpf5, over the frame held beyond its edges: their output is formed on a
+// frame padded by two pixels on every side (x = -2 .. W + 1, y = -2 .. H + 1),
+// and beyond that padding it is constant, so holding the padded plane at its
+// edges is exactly the differentiated held frame.  k_crop takes the bank's
+// raw planes (sigma^2 times the blurred channel) back to the frame and to D.
+// k_steer forms the steered derivatives of Sec. 2 (after eq 3).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "kf_common.cuh"
+#include "kf_internal.h"
+
+namespace kf {
+
+namespace {
+
+// The differentiators of a D = 5 bank: eqs (13)-(17) with the pure-delay
+// basis and dc constraints only (moments l < 5 of g_d equal to d! delta_{l,d},
+// Sec. 4.1), in correlation form y(n) = sum_j g(j) x(n + j), j = -2..2:
+// integer weights over a common denominator, so that the FP64 sums below are
+// exact for f32 inputs of moderate dynamic range.
+__constant__ int kG5[5][5] = {
+    {0, 0, 1, 0, 0},        // d = 0: the unit impulse
+    {1, -8, 0, 8, -1},      // d = 1, / 12
+    {-1, 16, -30, 16, -1},  // d = 2, / 12
+    {-1, 2, 0, -2, 1},      // d = 3, / 2
+    {1, -4, 6, -4, 1},      // d = 4
+};
+__constant__ double kDen5[5] = {1.0, 12.0, 12.0, 2.0, 1.0};
+
+constexpr int HTX = 32, HTY = 8;  // outputs per block
+
+// U = g_dx (x) g_dy applied to the held frame, on the padded frame
+// (Wp = W + 4) x (Hp = H + 4): out[py * Wp + px] is U at x = px - 2, y = py - 2.
+// FP64 accumulation, one rounding to f32: the differences cancel most of the
+// frame's magnitude, and rounding only the result keeps U accurate relative
+// to itself.
+__global__ void __launch_bounds__(HTX *HTY) k_hpf5(const void *__restrict__ X, int dtype, float vs, long pitch,
+                                                   int W, int H, int dx, int dy, float *__restrict__ out) {
+  __shared__ double xs[HTY + 4][HTX + 4];
+  __shared__ double ts[HTY + 4][HTX];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * HTX + tx;
+  const int px0 = blockIdx.x * HTX, py0 = blockIdx.y * HTY;
+  const int Wp = W + 4, Hp = H + 4;
+  // frame pixels x = px0 - 4 + c, y = py0 - 4 + r, clamped into the frame
+  with_input_type(X, dtype, [&](auto Xt) {
+    for (int i = tid; i < (HTY + 4) * (HTX + 4); i += HTX * HTY) {
+      const int r = i / (HTX + 4), c = i % (HTX + 4);
+      const int x = min(max(px0 - 4 + c, 0), W - 1), y = min(max(py0 - 4 + r, 0), H - 1);
+      xs[r][c] = (double)(vs * in_f32(__ldg(Xt + (long)y * pitch + x)));
+    }
+  });
+  __syncthreads();
+  for (int i = tid; i < (HTY + 4) * HTX; i += HTX * HTY) {
+    const int r = i / HTX, c = i % HTX;
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) t = fma((double)kG5[dx][j], xs[r][c + j], t);
+    ts[r][c] = t;
+  }
+  __syncthreads();
+  const int px = px0 + tx, py = py0 + ty;
+  if (px < Wp && py < Hp) {
+    double u = 0.0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) u = fma((double)kG5[dy][j], ts[ty + j][tx], u);
+    out[(long)py * Wp + px] = (float)(u / (kDen5[dx] * kDen5[dy]));
+  }
+}
+
+// D of channel `chan` at every scale: raw (S planes of the padded frame,
+// sigma^2 times the blurred channel) -> out[(s * 15 + chan) * H * W + y * W + x]
+__global__ void k_crop(const float *__restrict__ raw, int W, int H, int S, const Coef *__restrict__ coef, int chan,
+                       float *__restrict__ out) {
+  const int Wp = W + 4, Hp = H + 4;
+  const long plane = (long)H * W, n = (long)S * plane;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int s = (int)(i / plane);
+    const long r = i - (long)s * plane;
+    const int y = (int)(r / W), x = (int)(r - (long)y * W);
+    const float v = __ldg(raw + ((long)s * Hp + y + 2) * Wp + x + 2);
+    out[((long)s * QUARTIC_NCH + chan) * plane + r] = v / __ldg(&coef[s].sigma2);
+  }
+}
+
+struct SteerMat {
+  float m[55];  // per order n = 0..4, an (n + 1) x (n + 1) block, row-major
+};
+
+// per set and pixel, each order's n + 1 channels through its block (all 15
+// read before any is written: in == out is allowed)
+__global__ void k_steer(const float *in, long npix, int nsets, SteerMat M, float *out) {
+  const long n = npix * nsets;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const long set = i / npix, p = i - set * npix;
+    const float *src = in + set * QUARTIC_NCH * npix + p;
+    float *dst = out + set * QUARTIC_NCH * npix + p;
+    float v[QUARTIC_NCH];
+#pragma unroll
+    for (int c = 0; c < QUARTIC_NCH; ++c) v[c] = src[c * npix];
+    int base = 0, mb = 0;
+#pragma unroll
+    for (int o = 0; o < 5; ++o) {
+#pragma unroll
+      for (int a = 0; a <= o; ++a) {
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b <= o; ++b) acc = fmaf(M.m[mb + a * (o + 1) + b], v[base + b], acc);
+        dst[(base + a) * npix] = acc;
+      }
+      base += o + 1;
+      mb += (o + 1) * (o + 1);
+    }
+  }
+}
+
+int grid_for(long n, int threads) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long want = (n + threads - 1) / threads, cap = 8L * std::max(nsm, 1);
+  return (int)std::max(1L, std::min(want, cap));
+}
+
+}  // namespace
+
+int launch_hpf5(const void *X, int dtype, float vs, long pitch, int W, int H, int dx, int dy, float *out,
+                cudaStream_t st) {
+  if (dx < 0 || dy < 0 || dx + dy > 4 || W < 1 || H < 1) return -1;
+  const dim3 grid((W + 4 + HTX - 1) / HTX, (H + 4 + HTY - 1) / HTY), block(HTX, HTY);
+  k_hpf5<<<grid, block, 0, st>>>(X, dtype, vs, pitch, W, H, dx, dy, out);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_quartic_crop(const float *raw, int W, int H, int S, const Coef *coef, int chan, float *out,
+                        cudaStream_t st) {
+  const long n = (long)S * H * W;
+  k_crop<<<grid_for(n, 256), 256, 0, st>>>(raw, W, H, S, coef, chan, out);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_steer(const float *in, long npix, int nsets, const float *m55, float *out, cudaStream_t st) {
+  SteerMat M;
+  for (int i = 0; i < 55; ++i) M.m[i] = m55[i];
+  const long n = npix * nsets;
+  k_steer<<<grid_for(n, 256), 256, 0, st>>>(in, npix, nsets, M, out);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace kf

@@ -54,7 +54,11 @@ ENTRY_POINTS = ("kf_bank_opts_default", "kf_create", "kf_destroy", "kf_last_erro
                 "kf_filter_bank", "kf_detect_blobs", "kf_kernel_times", "kf_responses_noalloc",
                 "kf_set_launch_shape", "kf_set_segment_length", "kf_autotune",
                 "kf_proposal_set_weights", "kf_proposal_get_weights", "kf_proposal_pool", "kf_proposal_logits",
-                "kf_proposal_grad", "kf_proposal_train_step", "kf_proposal_labels", "kf_blob_shapes")
+                "kf_proposal_grad", "kf_proposal_train_step", "kf_proposal_labels", "kf_blob_shapes",
+                "kf_quartic_bank", "kf_quartic_steer")
+KF_QUARTIC_CHANNELS = 15
+# (dx, dy) of the D = 5 bank's channels: total order n = 0..4, within it dy = 0..n
+QUARTIC_CHANNELS = tuple((n - dy, dy) for n in range(5) for dy in range(n + 1))
 KF_NET_NPARAM = 3640
 KF_NET_CHANNELS = 8
 KF_PASS_ROW, KF_PASS_SEG, KF_PASS_FOLD, KF_PASS_DET, KF_NPASS = 0, 1, 2, 3, 4
@@ -159,6 +163,10 @@ def load(path: str = LIB_PATH):
     L.kf_proposal_labels.argtypes = [vp, dbl, vp]
     L.kf_set_segment_length.restype = i32
     L.kf_set_segment_length.argtypes = [vp, i32, i32]
+    L.kf_quartic_bank.restype = i32
+    L.kf_quartic_bank.argtypes = [vp, ctypes.POINTER(kf_frame), ctypes.POINTER(dbl), i32, i32, i32, vp]
+    L.kf_quartic_steer.restype = i32
+    L.kf_quartic_steer.argtypes = [vp, vp, i64, i32, dbl, vp]
     L.kf_autotune.restype = i32
     L.kf_autotune.argtypes = [vp, ctypes.POINTER(kf_frame), i32, ctypes.POINTER(dbl), i32, i32, i32,
                               ctypes.POINTER(kf_bank_opts), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
@@ -285,6 +293,42 @@ def kf_detect_blobs(ctx: int, threshold: float, capacity: int = None) -> np.ndar
 
 class kf_blob_shape(ctypes.Structure):
     _fields_ = [("p1", ctypes.c_float), ("p2", ctypes.c_float), ("theta", ctypes.c_float), ("det", ctypes.c_float)]
+
+
+def kf_quartic_bank(ctx: int, frame, scales, ftype: int, order: int, out=None, value_scale: float = 0.0):
+    """D_{dx,dy} for dx + dy <= 4 (the D = 5 bank) of one CUDA frame: a float32
+    CUDA tensor (len(scales), 15, H, W) in the QUARTIC_CHANNELS order, written
+    on the context stream (`out`: an existing tensor of that shape, or None)."""
+    import torch
+
+    desc = _frame_desc(frame, value_scale)
+    H, W = frame.shape
+    if out is None:
+        out = torch.empty((len(scales), KF_QUARTIC_CHANNELS, H, W), dtype=torch.float32, device=frame.device)
+    if out.shape != (len(scales), KF_QUARTIC_CHANNELS, H, W) or out.dtype != torch.float32 or \
+            not out.is_contiguous() or out.device != frame.device:
+        raise ValueError("out must be a contiguous float32 tensor (S, 15, H, W) on the frame's device")
+    sc = (ctypes.c_double * len(scales))(*[float(s) for s in scales])
+    _check(load().kf_quartic_bank(ctx, ctypes.byref(desc), sc, len(scales), ftype, order, out.data_ptr()), ctx)
+    return out
+
+
+def kf_quartic_steer(ctx: int, D, phi: float, out=None):
+    """Steered derivatives of a (..., 15, H, W) float32 CUDA tensor of D = 5
+    bank outputs (Sec. 2): a tensor of the same shape (`out` may be D)."""
+    import torch
+
+    if not D.is_cuda or D.dtype != torch.float32 or not D.is_contiguous() or D.dim() < 3 or \
+            D.shape[-3] != KF_QUARTIC_CHANNELS:
+        raise ValueError("D must be a contiguous float32 CUDA tensor (..., 15, H, W)")
+    if out is None:
+        out = torch.empty_like(D)
+    if out.shape != D.shape or out.dtype != D.dtype or not out.is_contiguous():
+        raise ValueError("out must match D")
+    npix = D.shape[-1] * D.shape[-2]
+    nsets = D.numel() // (KF_QUARTIC_CHANNELS * npix)
+    _check(load().kf_quartic_steer(ctx, D.data_ptr(), npix, nsets, float(phi), out.data_ptr()), ctx)
+    return out
 
 
 SHAPE_DTYPE = np.dtype([("p1", "<f4"), ("p2", "<f4"), ("theta", "<f4"), ("det", "<f4")])
