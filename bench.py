@@ -16,6 +16,9 @@ adds the same steps launched frame by frame (per_frame_schedule).
 the 64x64 tiles), 8 scales, both banks at threshold 0.3, gated by the trained
 proposal network against the plain bank (recall judged in the same run).
 
+--workload quartic: the D = 5 derivative bank (all 15 D_{dx,dy}, dx + dy <= 4)
+of one 2048 x 2048 FP32 frame at 4 scales, Filter D with L_D = 2.
+
 --workload counts: 16 uint16 frames of 8192 x 8192 (12-bit Poisson counts on a
 1/f background, 2000 blobs of radii 2-64 px; one generated frame in 16 device
 buffers), value scale 1/4095, 8 scales (radii 2-64 px), Filter D order 4 and
@@ -730,6 +733,140 @@ def run_table5(args):
     print(json.dumps(line), flush=True)
 
 
+# The D = 5 derivative bank (Sec. 4, L_D = 2): every D_{dx,dy}, dx + dy <= 4
+# (15 channels), of one 2048 x 2048 frame at 4 scales, Filter D with L_D = 2
+# and one Nyquist constraint pair (K^lpf = 4).
+QUARTIC_SCALES = (4.0, 8.0, 16.0, 32.0)
+QUARTIC_HW = 2048
+
+
+def quartic_bytes(name, S, H, W, nch=15):
+    """Algorithmic bytes of one launch of a kernel of the D = 5 bank (all 15
+    channels): the differentiator reads the frame and writes the 15 padded
+    planes; the row pass reads them and writes S planes each; the
+    segment-state pass reads those; the column pass reads them and writes S
+    raw planes each; the crop reads those and writes the 15 S output planes."""
+    P = (H + 4) * (W + 4)
+    return {"quartic_hpf": 4 * H * W + 4 * nch * P, "iir_row": nch * (4 * P + 4 * S * P),
+            "iir_colseg": nch * 4 * S * P, "iir_coldet": nch * 8 * S * P,
+            "quartic_crop": nch * (4 * S * P + 4 * S * H * W)}.get(name)
+
+
+def run_quartic(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_1912_07133_gb300 import kf, synthetic
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    kf.load()
+    dev = torch.device("cuda", local)
+    H = W = QUARTIC_HW
+    S = len(QUARTIC_SCALES)
+    host = synthetic.iir_fir_frame(seed=1, H=H, W=W, nblobs=250)
+    x = torch.from_numpy(host).to(dev)
+    out = torch.empty((S, kf.KF_QUARTIC_CHANNELS, H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = kf.kf_create(local, stream.cuda_stream)
+    ft, order = kf.KF_IIR_REPEATED_POLE, 4
+
+    def call(frame=x, profile=False):
+        kf.kf_quartic_bank(ctx, frame, QUARTIC_SCALES, ft, order, out=out, profile=profile)
+
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            call()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        clocks = clk.summary()
+    step_ms = float(np.mean(ms))
+    # end to end: the frame from pinned host memory, the bank, all planes back
+    # to pinned host memory
+    pin_in = torch.from_numpy(host).pin_memory()
+    pin_out = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+    xe = torch.empty_like(x)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        xe.copy_(pin_in, non_blocking=True)
+        call(xe)
+        pin_out.copy_(out, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    # per-kernel times of one profiled call (the step's own launches)
+    call(profile=True)
+    kt = kf.kf_kernel_times(ctx)
+    kf.kf_destroy(ctx)
+    ps = H * W * S
+    total = sum(v[1] for v in kt.values())
+    kernels = {}
+    for name, (n, t) in sorted(kt.items(), key=lambda kv: -kv[1][1]):
+        k = {"launches": n, "ms_per_launch": round(t / n, 4), "share": round(t / total, 4)}
+        b = quartic_bytes(name, S, H, W)
+        if b is not None and t > 0:
+            k["GB_s"] = round(b / (t / n * 1e-3) / 1e9, 1)
+        kernels[name] = k
+    top = max(kt, key=lambda k: kt[k][1])
+    n_top, t_top = kt[top]
+    peak, src = peaks()
+    b_top = quartic_bytes(top, S, H, W)
+    ach = b_top / (t_top / n_top * 1e-3) / 1e9 if b_top else None
+    roof = {"kernel": top, "bound": "hbm", "achieved": round(ach, 1) if ach else None, "peak": peak,
+            "unit": "GB/s", "frac": round(ach / peak, 4) if ach else None, "traffic": None,
+            "peak_source": src, "bytes_per_launch": b_top}
+    cpu = None
+    if not args.no_cpu:
+        cpu = quartic_cpu_baseline(host)
+    line = {
+        "metric": "Mpixel-scales/s, D = 5 derivative bank (15 channels D_{dx,dy}, dx + dy <= 4) on 1 GB300",
+        "value": round(ps / (step_ms * 1e-3) / 1e6, 1), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{H}x{W} FP32 frame (1/f background, 250 blobs), {S} scales (lambda 4-32 px), "
+                               "Filter D with L_D = 2, K^lpf = 4; all 15 channels written to HBM",
+                   "l2": "flushed between steps (256 MiB write outside the timed events); output 1 GiB",
+                   "launch": "eager: the differentiator, one bank call over the 15 channel planes, the crop"},
+        "e2e": {"value": round(ps / (float(np.mean(e2e_ms)) * 1e-3) / 1e6, 1), "unit": UNIT,
+                "h2d_bytes_per_step": int(pin_in.numel() * 4), "d2h_bytes_per_step": int(pin_out.numel() * 4)},
+        "gpu_launches": int(sum(v[0] for v in kt.values())),
+        "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def quartic_cpu_baseline(host, rows=64):
+    """The D = 5 oracle on `rows` rows of the frame, all scales."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from oracle import quartic as Q
+
+    sub = host[:rows].astype(np.float64)
+    Q.quartic_bank(sub[:8, :64], QUARTIC_SCALES[:1], O.IIR_REPEATED_POLE, 4)  # build, warm
+    t0 = time.perf_counter()
+    Q.quartic_bank(sub, QUARTIC_SCALES, O.IIR_REPEATED_POLE, 4)
+    dt = time.perf_counter() - t0
+    return {"value": round(sub.size * len(QUARTIC_SCALES) / dt / 1e6, 4), "unit": UNIT, "cores": 1,
+            "kind": "oracle", "sample": f"{sub.shape[0]}x{sub.shape[1]} rows of the frame, "
+                                        f"{len(QUARTIC_SCALES)} scales, 15 channels ({dt:.2f} s)"}
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -739,6 +876,26 @@ def run_reference(args):
     from oracle import oracle as O
 
     O.build()
+    if args.workload == "quartic":
+        from paper_1912_07133_gb300 import synthetic
+        host = synthetic.iir_fir_frame(seed=1, H=QUARTIC_HW, W=QUARTIC_HW, nblobs=250)
+        for _ in range(args.warmup):
+            quartic_cpu_baseline(host, rows=8)
+        vals = [quartic_cpu_baseline(host, rows=16) for _ in range(args.steps)]
+        v = float(sum(c["value"] for c in vals) / len(vals))
+        sample = vals[0]["sample"].split(" (")[0] + " per step"
+        print(json.dumps({
+            "metric": "Mpixel-scales/s, D = 5 derivative bank (15 channels D_{dx,dy}, dx + dy <= 4) on 1 GB300",
+            "value": round(v, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(16 * QUARTIC_HW * len(QUARTIC_SCALES) / (v * 1e6) * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{QUARTIC_HW}x{QUARTIC_HW} FP32 frame, 4 scales, Filter D L_D = 2",
+                       "sample": sample, "parallelism": "host core"},
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+            flush=True)
+        return
     if args.workload == "gated":
         from paper_1912_07133_gb300 import synthetic
         wl = dict(banks=IIR_FIR, scales=EIGHT, fir_kmax=96, value_scale=1.0, ref_rows=64,
@@ -787,7 +944,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("gated", "table5"), default="iir_fir")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("gated", "table5", "quartic"), default="iir_fir")
     ap.add_argument("--gate-mode", choices=("dilated", "tiles"), default="dilated",
                     help="gated workload: marked tiles with their neighbours, or marked tiles only")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
@@ -804,6 +961,8 @@ def main():
         run_gated(args)
     elif args.workload == "table5":
         run_table5(args)
+    elif args.workload == "quartic":
+        run_quartic(args)
     else:
         run_ours(args)
 

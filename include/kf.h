@@ -312,13 +312,16 @@ int kf_blob_shapes(kf_ctx *ctx, double threshold, kf_blob_shape *out, int64_t ca
  *           omega_c = 3 / sigma, Sec. 4.2)
  *   out     device, f32, caller-owned: nscales x 15 planes of H x W,
  *           out[((s * 15 + c) * H + y) * W + x]
- * Runs on the context stream (asynchronous; out is complete when the stream
- * is).  Uses the context's bank: afterwards kf_detect_blobs has no result
- * until the next kf_filter_bank call.
+ *   profile 1: time every kernel launch with CUDA events (the stream is
+ *           synchronised after each channel); kf_kernel_times then returns
+ *           the per-kernel totals of this call.  0: no timing.
+ * Runs on the context stream (asynchronous unless profiling; out is complete
+ * when the stream is).  Uses the context's bank: afterwards kf_detect_blobs
+ * has no result until the next kf_filter_bank call.
  * Errors: KF_EINVAL (bad arguments, a type or order without vanishing
  * moments to order 4), KF_ECOND (design), KF_ECUDA. */
 int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, int nscales, int type,
-                    int order, float *out);
+                    int order, float *out, int profile);
 
 /* Steered derivatives (Sec. 2, after eq 3): with x~ = x cos(phi) + y sin(phi)
  * and y~ = -x sin(phi) + y cos(phi), the coefficients beta (eq 2: beta_{dx,dy}
@@ -331,7 +334,8 @@ int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, in
 int kf_quartic_steer(kf_ctx *ctx, const float *in, int64_t npix, int nsets, double phi, float *out);
 
 /* Kernel launches and, when the call ran with opts->profile = 1, per-kernel
- * CUDA-event times of the last kf_filter_bank call: fills out[0..cap) (host,
+ * CUDA-event times of the last kf_filter_bank call (or of the last
+ * kf_quartic_bank call with profile = 1, until the next kf_filter_bank call): fills out[0..cap) (host,
  * caller-owned) and sets *n (host) to the number of distinct kernels.
  * Synchronises the context stream.  Without profiling, ms is 0.
  * Errors: KF_EINVAL (NULL arguments, no bank call yet), KF_ECUDA. */

@@ -137,6 +137,13 @@ struct kf_ctx {
   size_t q_pad_floats = 0;
   float *q_raw = nullptr;  // its raw planes sigma^2 D, per scale
   size_t q_raw_floats = 0;
+  // per-kernel times of the last profiled kf_quartic_bank call (returned by
+  // kf_kernel_times until the next kf_filter_bank call)
+  bool q_times_valid = false;
+  std::vector<std::string> q_names;
+  std::vector<int> q_launches;
+  std::vector<float> q_ms;
+  cudaEvent_t q_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -450,6 +457,8 @@ void kf_destroy(kf_ctx *ctx) {
   cudaFree(ctx->shape_buf);
   cudaFree(ctx->q_pad);
   cudaFree(ctx->q_raw);
+  for (cudaEvent_t ev : ctx->q_ev)
+    if (ev) cudaEventDestroy(ev);
   for (void *q : {(void *)ctx->g_pooled, (void *)ctx->g_logits, (void *)ctx->g_act, (void *)ctx->g_sel[0],
                   (void *)ctx->g_sel[1], (void *)ctx->g_count})
     cudaFree(q);
@@ -511,6 +520,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
                    int type, int order, const kf_bank_opts *opts_in) {
   if (!ctx) return fail(nullptr, KF_EINVAL, "kf_filter_bank: ctx is NULL");
   ctx->have_result = false;
+  if (ctx->q_chan < 0) ctx->q_times_valid = false;
   kf_bank_opts opts;
   if (opts_in) opts = *opts_in;
   else kf_bank_opts_default(&opts);
@@ -799,6 +809,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     const int lr = iir ? kf::launch_iir(plan, a, st) : kf::launch_fir(plan, a, st);
     if (lr == -2) return fail(ctx, KF_EINVAL, "no kernel instance for order %d", order);
     if (lr) return cuda_fail(ctx, cudaGetLastError(), "filter-bank kernel launch");
+    if (ctx->q_chan >= 0) return KF_OK;  // raw planes: no candidates to order
     return issue_sort(st, prof);
   };
   ctx->prof = kf::Prof{};
@@ -1205,16 +1216,11 @@ int kf_proposal_labels(kf_ctx *ctx, double threshold, uint8_t *labels) {
   return KF_OK;
 }
 
-int kf_kernel_times(kf_ctx *ctx, kf_kernel_time *out, int cap, int *n) {
-  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_kernel_times: ctx is NULL");
-  if (!n || cap < 0 || (cap > 0 && !out)) return fail(ctx, KF_EINVAL, "kf_kernel_times: bad outputs");
-  if (!ctx->have_prof) return fail(ctx, KF_EINVAL, "kf_kernel_times: no bank call yet");
+// add the launches (and, with events, the times) of the last bank call to the
+// per-kernel lists; the stream must have been synchronised
+static int collect_prof(kf_ctx *ctx, std::vector<std::string> &names, std::vector<int> &launches, std::vector<float> &ms) {
   cudaError_t e;
-  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sync");
   const kf::Prof &p = ctx->prof;
-  std::vector<std::string> names;
-  std::vector<int> launches;
-  std::vector<float> ms;
   for (int i = 0; i < p.n && i < 256; ++i) {
     const std::string nm = p.names[i];
     size_t k = std::find(names.begin(), names.end(), nm) - names.begin();
@@ -1230,6 +1236,25 @@ int kf_kernel_times(kf_ctx *ctx, kf_kernel_time *out, int cap, int *n) {
         return cuda_fail(ctx, e, "cudaEventElapsedTime");
       ms[k] += t;
     }
+  }
+  return KF_OK;
+}
+
+int kf_kernel_times(kf_ctx *ctx, kf_kernel_time *out, int cap, int *n) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_kernel_times: ctx is NULL");
+  if (!n || cap < 0 || (cap > 0 && !out)) return fail(ctx, KF_EINVAL, "kf_kernel_times: bad outputs");
+  if (!ctx->have_prof) return fail(ctx, KF_EINVAL, "kf_kernel_times: no bank call yet");
+  cudaError_t e;
+  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sync");
+  std::vector<std::string> names;
+  std::vector<int> launches;
+  std::vector<float> ms;
+  if (ctx->q_times_valid) {
+    names = ctx->q_names;
+    launches = ctx->q_launches;
+    ms = ctx->q_ms;
+  } else if (int rc = collect_prof(ctx, names, launches, ms)) {
+    return rc;
   }
   *n = (int)names.size();
   for (int i = 0; i < cap && i < (int)names.size(); ++i) {
@@ -1329,7 +1354,7 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
 }
 
 int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, int nscales, int type,
-                    int order, float *out) {
+                    int order, float *out, int profile) {
   if (!ctx) return fail(nullptr, KF_EINVAL, "kf_quartic_bank: ctx is NULL");
   if (!frame || !out) return fail(ctx, KF_EINVAL, "kf_quartic_bank: frame and out must not be NULL");
   if (!scales || nscales < 1 || nscales > KF_MAX_SCALES)
@@ -1350,6 +1375,7 @@ int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, in
   if (!frame->data || W < 1 || H < 1 || frame->pitch < W)
     return fail(ctx, KF_EINVAL, "kf_quartic_bank: bad frame %dx%d pitch %lld", W, H, (long long)frame->pitch);
   if (W > 8188) return fail(ctx, KF_EINVAL, "kf_quartic_bank: width > 8188");
+  if (H > 65535) return fail(ctx, KF_EINVAL, "kf_quartic_bank: height > 65535");
   if (frame->dtype < KF_DTYPE_F32 || frame->dtype > KF_DTYPE_U16)
     return fail(ctx, KF_EINVAL, "kf_quartic_bank: unknown dtype %d", frame->dtype);
   if (!std::isfinite(frame->value_scale)) return fail(ctx, KF_EINVAL, "kf_quartic_bank: value_scale is not finite");
@@ -1360,8 +1386,10 @@ int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, in
   const int Wp = W + 4, Hp = H + 4;
   const size_t npad = (size_t)Wp * Hp;
   int rc;
-  if ((rc = grow(ctx, &ctx->q_pad, &ctx->q_pad_floats, npad, "D = 5 channel plane"))) return rc;
-  if ((rc = grow(ctx, &ctx->q_raw, &ctx->q_raw_floats, npad * nscales, "D = 5 raw planes"))) return rc;
+  if ((rc = grow(ctx, &ctx->q_pad, &ctx->q_pad_floats, npad * kf::QUARTIC_NCH, "D = 5 channel planes")))
+    return rc;
+  if ((rc = grow(ctx, &ctx->q_raw, &ctx->q_raw_floats, npad * nscales * kf::QUARTIC_NCH, "D = 5 raw planes")))
+    return rc;
   struct Restore {
     kf_ctx *c;
     ~Restore() {
@@ -1371,13 +1399,17 @@ int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, in
   } restore{ctx};
   ctx->q_ld = type == KF_IIR_REPEATED_POLE ? 2 : 1;
   const float vs = frame->value_scale == 0.f ? 1.f : frame->value_scale;
-  kf_frame pf{};
-  pf.data = ctx->q_pad;
-  pf.width = Wp;
-  pf.height = Hp;
-  pf.pitch = Wp;
-  pf.dtype = KF_DTYPE_F32;
-  pf.value_scale = 1.f;
+  // the 15 channel planes are the frames of one bank call (one launch per pass)
+  kf_frame pf[kf::QUARTIC_NCH];
+  for (int c = 0; c < kf::QUARTIC_NCH; ++c) {
+    pf[c] = kf_frame{};
+    pf[c].data = ctx->q_pad + (size_t)c * npad;
+    pf[c].width = Wp;
+    pf[c].height = Hp;
+    pf[c].pitch = Wp;
+    pf[c].dtype = KF_DTYPE_F32;
+    pf[c].value_scale = 1.f;
+  }
   kf_bank_opts o;
   kf_bank_opts_default(&o);
   o.responses = ctx->q_raw;
@@ -1390,17 +1422,51 @@ int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, in
   // 2^-21 of each tap product, and the fourth differences of a textured frame
   // are up to a thousand times larger than their blurred output.
   if (type == KF_FIR_COLORED_SG) o.neighbourhood = KF_NEIGH_ADJACENT;
-  for (int n = 0, c = 0; n <= 4; ++n)
-    for (int dy = 0; dy <= n; ++dy, ++c) {
-      if (kf::launch_hpf5(frame->data, frame->dtype, vs, (long)frame->pitch, W, H, n - dy, dy, ctx->q_pad,
-                          ctx->stream))
-        return cuda_fail(ctx, cudaGetLastError(), "differentiator launch");
-      ctx->q_chan = kf::CH_ID;
-      if ((rc = kf_filter_bank(ctx, &pf, 1, scales, nscales, type, order, &o))) return rc;
-      if (kf::launch_quartic_crop(ctx->q_raw, W, H, nscales, ctx->cur->d_coef, c, out, ctx->stream))
-        return cuda_fail(ctx, cudaGetLastError(), "D = 5 crop launch");
+  // profiling: every launch between a pair of events, the stream synchronised
+  // after each, times summed per kernel over the channels
+  ctx->q_times_valid = false;
+  ctx->q_names.clear();
+  ctx->q_launches.clear();
+  ctx->q_ms.clear();
+  o.profile = profile ? 1 : 0;
+  if (profile)
+    for (cudaEvent_t &ev : ctx->q_ev)
+      if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(ctx, e, "cudaEventCreate");
+  auto timed = [&](const char *name, auto &&launch) -> int {
+    if (profile) cudaEventRecord(ctx->q_ev[0], ctx->stream);
+    if (launch()) return cuda_fail(ctx, cudaGetLastError(), name);
+    if (!profile) return KF_OK;
+    cudaEventRecord(ctx->q_ev[1], ctx->stream);
+    float t = 0.f;
+    if ((e = cudaEventSynchronize(ctx->q_ev[1])) != cudaSuccess ||
+        (e = cudaEventElapsedTime(&t, ctx->q_ev[0], ctx->q_ev[1])) != cudaSuccess)
+      return cuda_fail(ctx, e, "profile events");
+    size_t k = std::find(ctx->q_names.begin(), ctx->q_names.end(), std::string(name)) - ctx->q_names.begin();
+    if (k == ctx->q_names.size()) {
+      ctx->q_names.push_back(name);
+      ctx->q_launches.push_back(0);
+      ctx->q_ms.push_back(0.f);
     }
+    ctx->q_launches[k] += 1;
+    ctx->q_ms[k] += t;
+    return KF_OK;
+  };
+  if ((rc = timed("quartic_hpf", [&] {
+         return kf::launch_hpf5(frame->data, frame->dtype, vs, (long)frame->pitch, W, H, ctx->q_pad, ctx->stream);
+       })))
+    return rc;
+  ctx->q_chan = kf::CH_ID;
+  if ((rc = kf_filter_bank(ctx, pf, kf::QUARTIC_NCH, scales, nscales, type, order, &o))) return rc;
+  if (profile) {
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sync");
+    if ((rc = collect_prof(ctx, ctx->q_names, ctx->q_launches, ctx->q_ms))) return rc;
+  }
+  if ((rc = timed("quartic_crop", [&] {
+         return kf::launch_quartic_crop(ctx->q_raw, W, H, nscales, ctx->cur->d_coef, out, ctx->stream);
+       })))
+    return rc;
   ctx->have_result = false;  // the bank ran raw planes: no blob list
+  ctx->q_times_valid = profile != 0;
   return KF_OK;
 }
 

@@ -138,15 +138,13 @@ int fir_halo(int kmax);        // rows a FIR column tile reads beyond its 128 (o
 int launch_shapes(const Blob *b, long n, const float *c20, const float *c02, const float *c11, const long *lay,
                   const Coef *coef, void *out, cudaStream_t st);
 
-// D = 5 derivative bank (kf_quartic.cu): the differentiated channel (dx, dy)
-// of a frame on the frame padded by 2 (f32, pitch W + 4, H + 4 rows); the
-// bank's raw planes of that channel back to D in out[s][chan][H][W]; the
-// steering of 15-channel sets (m55: per order n = 0..4 an (n+1) x (n+1)
-// row-major block)
-int launch_hpf5(const void *X, int dtype, float vs, long pitch, int W, int H, int dx, int dy, float *out,
-                cudaStream_t st);
-int launch_quartic_crop(const float *raw, int W, int H, int S, const Coef *coef, int chan, float *out,
-                        cudaStream_t st);
+// D = 5 derivative bank (kf_quartic.cu): the 15 differentiated channels of a
+// frame on the frame padded by 2 (f32 planes of pitch W + 4 and H + 4 rows,
+// one after the other); the bank's raw planes (per channel S padded planes)
+// back to D in out[s][chan][H][W]; the steering of 15-channel sets (m55: per order n =
+// 0..4 an (n+1) x (n+1) row-major block)
+int launch_hpf5(const void *X, int dtype, float vs, long pitch, int W, int H, float *out, cudaStream_t st);
+int launch_quartic_crop(const float *raw, int W, int H, int S, const Coef *coef, float *out, cudaStream_t st);
 int launch_steer(const float *in, long npix, int nsets, const float *m55, float *out, cudaStream_t st);
 
 // candidate ordering (kf_sort.cu)

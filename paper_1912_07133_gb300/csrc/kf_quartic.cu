@@ -26,26 +26,30 @@ namespace {
 // Sec. 4.1), in correlation form y(n) = sum_j g(j) x(n + j), j = -2..2:
 // integer weights over a common denominator, so that the FP64 sums below are
 // exact for f32 inputs of moderate dynamic range.
-__constant__ int kG5[5][5] = {
-    {0, 0, 1, 0, 0},        // d = 0: the unit impulse
-    {1, -8, 0, 8, -1},      // d = 1, / 12
-    {-1, 16, -30, 16, -1},  // d = 2, / 12
-    {-1, 2, 0, -2, 1},      // d = 3, / 2
-    {1, -4, 6, -4, 1},      // d = 4
-};
-__constant__ double kDen5[5] = {1.0, 12.0, 12.0, 2.0, 1.0};
+__host__ __device__ constexpr int g5(int d, int j) {
+  constexpr int w[5][5] = {
+      {0, 0, 1, 0, 0},        // d = 0: the unit impulse
+      {1, -8, 0, 8, -1},      // d = 1, / 12
+      {-1, 16, -30, 16, -1},  // d = 2, / 12
+      {-1, 2, 0, -2, 1},      // d = 3, / 2
+      {1, -4, 6, -4, 1},      // d = 4
+  };
+  return w[d][j];
+}
+__host__ __device__ constexpr double den5(int d) { return d == 1 || d == 2 ? 12.0 : (d == 3 ? 2.0 : 1.0); }
 
 constexpr int HTX = 32, HTY = 8;  // outputs per block
 
-// U = g_dx (x) g_dy applied to the held frame, on the padded frame
-// (Wp = W + 4) x (Hp = H + 4): out[py * Wp + px] is U at x = px - 2, y = py - 2.
-// FP64 accumulation, one rounding to f32: the differences cancel most of the
-// frame's magnitude, and rounding only the result keeps U accurate relative
-// to itself.
+// every channel U_{dx,dy} = g_dx (x) g_dy of the held frame, on the padded
+// frame (Wp = W + 4) x (Hp = H + 4): plane c of out (stride Wp Hp) holds at
+// py * Wp + px the value at x = px - 2, y = py - 2.  The five x-differences of
+// the block's rows are formed once and shared by the channels.  FP64 sums,
+// one rounding to f32: the differences cancel most of the frame's magnitude,
+// and rounding only the result keeps U accurate relative to itself.
 __global__ void __launch_bounds__(HTX *HTY) k_hpf5(const void *__restrict__ X, int dtype, float vs, long pitch,
-                                                   int W, int H, int dx, int dy, float *__restrict__ out) {
+                                                   int W, int H, float *__restrict__ out) {
   __shared__ double xs[HTY + 4][HTX + 4];
-  __shared__ double ts[HTY + 4][HTX];
+  __shared__ double ts[4][HTY + 4][HTX];  // dx = 1..4 (dx = 0 reads xs)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * HTX + tx;
   const int px0 = blockIdx.x * HTX, py0 = blockIdx.y * HTY;
   const int Wp = W + 4, Hp = H + 4;
@@ -60,34 +64,47 @@ __global__ void __launch_bounds__(HTX *HTY) k_hpf5(const void *__restrict__ X, i
   __syncthreads();
   for (int i = tid; i < (HTY + 4) * HTX; i += HTX * HTY) {
     const int r = i / HTX, c = i % HTX;
-    double t = 0.0;
+    double v[5];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) t = fma((double)kG5[dx][j], xs[r][c + j], t);
-    ts[r][c] = t;
+    for (int j = 0; j < 5; ++j) v[j] = xs[r][c + j];
+#pragma unroll
+    for (int d = 1; d < 5; ++d) {
+      double t = 0.0;
+#pragma unroll
+      for (int j = 0; j < 5; ++j)
+        if (g5(d, j) != 0) t = fma((double)g5(d, j), v[j], t);
+      ts[d - 1][r][c] = t;
+    }
   }
   __syncthreads();
   const int px = px0 + tx, py = py0 + ty;
-  if (px < Wp && py < Hp) {
-    double u = 0.0;
+  if (px >= Wp || py >= Hp) return;
+  const long plane = (long)Wp * Hp, o = (long)py * Wp + px;
 #pragma unroll
-    for (int j = 0; j < 5; ++j) u = fma((double)kG5[dy][j], ts[ty + j][tx], u);
-    out[(long)py * Wp + px] = (float)(u / (kDen5[dx] * kDen5[dy]));
+  for (int n = 0, c = 0; n <= 4; ++n) {
+#pragma unroll
+    for (int dy = 0; dy <= n; ++dy, ++c) {
+      const int dx = n - dy;
+      double u = 0.0;
+#pragma unroll
+      for (int j = 0; j < 5; ++j)
+        if (g5(dy, j) != 0) u = fma((double)g5(dy, j), dx == 0 ? xs[ty + j][tx + 2] : ts[dx - 1][ty + j][tx], u);
+      out[c * plane + o] = (float)(u * (1.0 / (den5(dx) * den5(dy))));
+    }
   }
 }
 
-// D of channel `chan` at every scale: raw (S planes of the padded frame,
-// sigma^2 times the blurred channel) -> out[(s * 15 + chan) * H * W + y * W + x]
-__global__ void k_crop(const float *__restrict__ raw, int W, int H, int S, const Coef *__restrict__ coef, int chan,
-                       float *__restrict__ out) {
+// D at scale s and channel c (blockIdx.z = s * 15 + c), row blockIdx.y: raw
+// (per channel S planes of the padded frame, sigma^2 times the blurred
+// channel) -> out[(s * 15 + c) * H * W + y * W + x]
+__global__ void __launch_bounds__(256) k_crop(const float *__restrict__ raw, int W, int H, int S,
+                                              const Coef *__restrict__ coef, float *__restrict__ out) {
+  const int s = blockIdx.z / QUARTIC_NCH, c = blockIdx.z - s * QUARTIC_NCH;
+  const int y = blockIdx.y, x = blockIdx.x * 256 + threadIdx.x;
+  if (x >= W) return;
   const int Wp = W + 4, Hp = H + 4;
-  const long plane = (long)H * W, n = (long)S * plane;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const int s = (int)(i / plane);
-    const long r = i - (long)s * plane;
-    const int y = (int)(r / W), x = (int)(r - (long)y * W);
-    const float v = __ldg(raw + ((long)s * Hp + y + 2) * Wp + x + 2);
-    out[((long)s * QUARTIC_NCH + chan) * plane + r] = v / __ldg(&coef[s].sigma2);
-  }
+  const float v = __ldg(raw + (((long)c * S + s) * Hp + y + 2) * Wp + x + 2);
+  out[((long)blockIdx.z * H + y) * W + x] = v / __ldg(&coef[s].sigma2);
 }
 
 struct SteerMat {
@@ -131,18 +148,17 @@ int grid_for(long n, int threads) {
 
 }  // namespace
 
-int launch_hpf5(const void *X, int dtype, float vs, long pitch, int W, int H, int dx, int dy, float *out,
-                cudaStream_t st) {
-  if (dx < 0 || dy < 0 || dx + dy > 4 || W < 1 || H < 1) return -1;
+int launch_hpf5(const void *X, int dtype, float vs, long pitch, int W, int H, float *out, cudaStream_t st) {
+  if (W < 1 || H < 1 || H + 4 > 8 * 65535) return -1;
   const dim3 grid((W + 4 + HTX - 1) / HTX, (H + 4 + HTY - 1) / HTY), block(HTX, HTY);
-  k_hpf5<<<grid, block, 0, st>>>(X, dtype, vs, pitch, W, H, dx, dy, out);
+  k_hpf5<<<grid, block, 0, st>>>(X, dtype, vs, pitch, W, H, out);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_quartic_crop(const float *raw, int W, int H, int S, const Coef *coef, int chan, float *out,
-                        cudaStream_t st) {
-  const long n = (long)S * H * W;
-  k_crop<<<grid_for(n, 256), 256, 0, st>>>(raw, W, H, S, coef, chan, out);
+int launch_quartic_crop(const float *raw, int W, int H, int S, const Coef *coef, float *out, cudaStream_t st) {
+  if (W < 1 || H < 1 || H > 65535 || S < 1 || S * QUARTIC_NCH > 65535) return -1;
+  const dim3 grid((W + 255) / 256, H, S * QUARTIC_NCH);
+  k_crop<<<grid, 256, 0, st>>>(raw, W, H, S, coef, out);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -164,7 +164,7 @@ def load(path: str = LIB_PATH):
     L.kf_set_segment_length.restype = i32
     L.kf_set_segment_length.argtypes = [vp, i32, i32]
     L.kf_quartic_bank.restype = i32
-    L.kf_quartic_bank.argtypes = [vp, ctypes.POINTER(kf_frame), ctypes.POINTER(dbl), i32, i32, i32, vp]
+    L.kf_quartic_bank.argtypes = [vp, ctypes.POINTER(kf_frame), ctypes.POINTER(dbl), i32, i32, i32, vp, i32]
     L.kf_quartic_steer.restype = i32
     L.kf_quartic_steer.argtypes = [vp, vp, i64, i32, dbl, vp]
     L.kf_autotune.restype = i32
@@ -295,10 +295,12 @@ class kf_blob_shape(ctypes.Structure):
     _fields_ = [("p1", ctypes.c_float), ("p2", ctypes.c_float), ("theta", ctypes.c_float), ("det", ctypes.c_float)]
 
 
-def kf_quartic_bank(ctx: int, frame, scales, ftype: int, order: int, out=None, value_scale: float = 0.0):
+def kf_quartic_bank(ctx: int, frame, scales, ftype: int, order: int, out=None, value_scale: float = 0.0,
+                    profile: bool = False):
     """D_{dx,dy} for dx + dy <= 4 (the D = 5 bank) of one CUDA frame: a float32
     CUDA tensor (len(scales), 15, H, W) in the QUARTIC_CHANNELS order, written
-    on the context stream (`out`: an existing tensor of that shape, or None)."""
+    on the context stream (`out`: an existing tensor of that shape, or None).
+    profile: time each kernel (kf_kernel_times returns the totals)."""
     import torch
 
     desc = _frame_desc(frame, value_scale)
@@ -309,7 +311,8 @@ def kf_quartic_bank(ctx: int, frame, scales, ftype: int, order: int, out=None, v
             not out.is_contiguous() or out.device != frame.device:
         raise ValueError("out must be a contiguous float32 tensor (S, 15, H, W) on the frame's device")
     sc = (ctypes.c_double * len(scales))(*[float(s) for s in scales])
-    _check(load().kf_quartic_bank(ctx, ctypes.byref(desc), sc, len(scales), ftype, order, out.data_ptr()), ctx)
+    _check(load().kf_quartic_bank(ctx, ctypes.byref(desc), sc, len(scales), ftype, order, out.data_ptr(),
+                                  1 if profile else 0), ctx)
     return out
 
 
