@@ -744,12 +744,11 @@ def quartic_bytes(name, S, H, W, nch=15):
     """Algorithmic bytes of one launch of a kernel of the D = 5 bank (all 15
     channels): the differentiator reads the frame and writes the 15 padded
     planes; the row pass reads them and writes S planes each; the
-    segment-state pass reads those; the column pass reads them and writes S
-    raw planes each; the crop reads those and writes the 15 S output planes."""
+    segment-state pass reads those; the column pass reads them and writes the
+    15 S output planes (cropped to the frame)."""
     P = (H + 4) * (W + 4)
     return {"quartic_hpf": 4 * H * W + 4 * nch * P, "iir_row": nch * (4 * P + 4 * S * P),
-            "iir_colseg": nch * 4 * S * P, "iir_coldet": nch * 8 * S * P,
-            "quartic_crop": nch * (4 * S * P + 4 * S * H * W)}.get(name)
+            "iir_colseg": nch * 4 * S * P, "iir_coldet": nch * (4 * S * P + 4 * S * H * W)}.get(name)
 
 
 def run_quartic(args):
@@ -841,7 +840,7 @@ def run_quartic(args):
         "config": {"workload": f"{H}x{W} FP32 frame (1/f background, 250 blobs), {S} scales (lambda 4-32 px), "
                                "Filter D with L_D = 2, K^lpf = 4; all 15 channels written to HBM",
                    "l2": "flushed between steps (256 MiB write outside the timed events); output 1 GiB",
-                   "launch": "eager: the differentiator, one bank call over the 15 channel planes, the crop"},
+                   "launch": "eager: the differentiator, then one bank call over the 15 channel planes"},
         "e2e": {"value": round(ps / (float(np.mean(e2e_ms)) * 1e-3) / 1e6, 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(pin_in.numel() * 4), "d2h_bytes_per_step": int(pin_out.numel() * 4)},
         "gpu_launches": int(sum(v[0] for v in kt.values())),

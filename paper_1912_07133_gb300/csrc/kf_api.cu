@@ -133,10 +133,10 @@ struct kf_ctx {
   // bank call, the call blurs channel q_chan of its frame as raw planes with
   // the L_D = q_ld designs; q_chan < 0 otherwise
   int q_chan = -1, q_ld = 1;
+  float *q_out = nullptr;  // the caller's D array: channel frame f, scale s at (s * 15 + f) * H * W
+  int q_H = 0, q_W = 0;
   float *q_pad = nullptr;  // one differentiated channel on the frame padded by 2
   size_t q_pad_floats = 0;
-  float *q_raw = nullptr;  // its raw planes sigma^2 D, per scale
-  size_t q_raw_floats = 0;
   // per-kernel times of the last profiled kf_quartic_bank call (returned by
   // kf_kernel_times until the next kf_filter_bank call)
   bool q_times_valid = false;
@@ -456,7 +456,6 @@ void kf_destroy(kf_ctx *ctx) {
   cudaFree(ctx->d_dlay);
   cudaFree(ctx->shape_buf);
   cudaFree(ctx->q_pad);
-  cudaFree(ctx->q_raw);
   for (cudaEvent_t ev : ctx->q_ev)
     if (ev) cudaEventDestroy(ev);
   for (void *q : {(void *)ctx->g_pooled, (void *)ctx->g_logits, (void *)ctx->g_act, (void *)ctx->g_sel[0],
@@ -607,6 +606,15 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     zoff += (long)KF_NET_CHANNELS * ((fr.height + 63) / 64) * ((fr.width + 63) / 64);
     d.X = fr.data;
     d.resp = opts.responses ? opts.responses + roff : nullptr;
+    d.rplane = 0;
+    d.rpitch = d.rmargin = 0;
+    if (ctx->q_chan >= 0) {  // D = 5 channel frame f: cropped into out[s][f][H][W]
+      const long hw = (long)ctx->q_H * ctx->q_W;
+      d.resp = ctx->q_out + f * hw;
+      d.rplane = kf::QUARTIC_NCH * hw;
+      d.rpitch = ctx->q_W;
+      d.rmargin = 2;
+    }
     d.xpitch = fr.pitch;
     d.prow = prows;
     d.eoff = (long)f * nscales * 2 * PWb;
@@ -1388,13 +1396,12 @@ int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, in
   int rc;
   if ((rc = grow(ctx, &ctx->q_pad, &ctx->q_pad_floats, npad * kf::QUARTIC_NCH, "D = 5 channel planes")))
     return rc;
-  if ((rc = grow(ctx, &ctx->q_raw, &ctx->q_raw_floats, npad * nscales * kf::QUARTIC_NCH, "D = 5 raw planes")))
-    return rc;
   struct Restore {
     kf_ctx *c;
     ~Restore() {
       c->q_chan = -1;
       c->q_ld = 1;
+      c->q_out = nullptr;
     }
   } restore{ctx};
   ctx->q_ld = type == KF_IIR_REPEATED_POLE ? 2 : 1;
@@ -1412,7 +1419,6 @@ int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, in
   }
   kf_bank_opts o;
   kf_bank_opts_default(&o);
-  o.responses = ctx->q_raw;
   o.storage = KF_DTYPE_F32;
   o.graph = 0;
   o.gate = KF_GATE_OFF;
@@ -1455,16 +1461,17 @@ int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, in
          return kf::launch_hpf5(frame->data, frame->dtype, vs, (long)frame->pitch, W, H, ctx->q_pad, ctx->stream);
        })))
     return rc;
+  // the column passes write D (the identity channel carries no sigma^2)
+  // straight into out, cropped by the two padding pixels
   ctx->q_chan = kf::CH_ID;
+  ctx->q_out = out;
+  ctx->q_H = H;
+  ctx->q_W = W;
   if ((rc = kf_filter_bank(ctx, pf, kf::QUARTIC_NCH, scales, nscales, type, order, &o))) return rc;
   if (profile) {
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sync");
     if ((rc = collect_prof(ctx, ctx->q_names, ctx->q_launches, ctx->q_ms))) return rc;
   }
-  if ((rc = timed("quartic_crop", [&] {
-         return kf::launch_quartic_crop(ctx->q_raw, W, H, nscales, ctx->cur->d_coef, out, ctx->stream);
-       })))
-    return rc;
   ctx->have_result = false;  // the bank ran raw planes: no blob list
   ctx->q_times_valid = profile != 0;
   return KF_OK;

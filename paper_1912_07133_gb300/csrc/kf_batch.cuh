@@ -27,6 +27,14 @@ struct FrameDev {
   float vscale;    // input multiplier
   long aoff;       // gated calls: byte offset of the frame's active-tile map (64 x 64 tiles)
   long roff;       // float offset of the frame's planes in response-layout buffers (S x H x W)
+  // response layout when rplane > 0: value (s, y, x) at resp[s * rplane +
+  // (y - rmargin) * rpitch + x - rmargin], only for y, x at least rmargin
+  // inside the frame (the D = 5 bank writes its padded channel frames cropped
+  // into the caller's array); rplane = 0: S x H x W planes.  Honoured by
+  // detect_tile (the IIR column pass and the FP32 FIR column pass, the
+  // passes of the D = 5 bank), not by the tensor-core FIR column pass.
+  long rplane;
+  int rpitch, rmargin;
   int H, W;
   int nseg;        // IIR column segments
   int index;       // frame index in the call (blob records)

@@ -265,8 +265,9 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr,
       __syncthreads();
       float acc[NOUT];
       fir_row_block(sh, K, sL, base, acc);
-      // planes hold sigma^2 x the one-sided blur (the column pass only negates)
-      const float s2 = c.sigma2;
+      // planes hold sigma^2 x the one-sided blur (the column pass only
+      // negates; the blur alone for CH_ID)
+      const float s2 = chan == CH_ID ? 1.f : c.sigma2;
 #pragma unroll
       for (int j = 0; j < NOUT; ++j) acc[j] *= s2;
       const int x0 = xs + NOUT * tid;
@@ -373,6 +374,9 @@ __global__ void __launch_bounds__(CNT) k_colfir(const FrameDev *__restrict__ fr,
     a.W = W;
     a.frame = F.index;
     a.resp = F.resp;
+    a.rplane = F.rplane;
+    a.rpitch = F.rpitch;
+    a.rmargin = F.rmargin;
     detect_tile(buf, red, a);
     __syncthreads();
   }

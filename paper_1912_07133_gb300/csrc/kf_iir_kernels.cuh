@@ -344,8 +344,8 @@ __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, i
     }
     // planes hold sigma^2 x the one-sided blur: the column pass then only
     // negates (R_L = -sigma^2 (D20 + D02)), and 16-bit planes keep the
-    // magnitude of R at every scale
-    const float s2 = c.sigma2;
+    // magnitude of R at every scale (the blur alone for CH_ID)
+    const float s2 = chan == CH_ID ? 1.f : c.sigma2;
 #pragma unroll
     for (int i = 0; i < CH; ++i) s_out[pad32(x0 + i)] = s2 * yv[i];
     __syncthreads();
@@ -682,6 +682,9 @@ __global__ void __launch_bounds__(512) __maxnreg__(LC == 32 ? Rec::kColdetRegs32
     a.W = W;
     a.frame = F.index;
     a.resp = F.resp;
+    a.rplane = F.rplane;
+    a.rpitch = F.rpitch;
+    a.rmargin = F.rmargin;
     a.ld = LD;
     a.coff = F32 ? off : 0;
     a.srows = REG / LD;

@@ -3,13 +3,14 @@
 // The bank estimates D_{dx,dy} (eq 3) for every dx + dy <= 4 at each scale
 // by separable filtering (Sec. 2): the differentiator g_dx along x and g_dy
 // along y (Sec. 4.1), then the L_D = 2 blur along x and along y (the bank's
-// row and column passes, channel CH_ID).  The differentiators run first, in
-// k_hpf5, over the frame held beyond its edges: their output is formed on a
-// frame padded by two pixels on every side (x = -2 .. W + 1, y = -2 .. H + 1),
-// and beyond that padding it is constant, so holding the padded plane at its
-// edges is exactly the differentiated held frame.  k_crop takes the bank's
-// raw planes (sigma^2 times the blurred channel) back to the frame and to D.
-// k_steer forms the steered derivatives of Sec. 2 (after eq 3).
+// row and column passes over the 15 channel planes as the frames of one
+// call, channel CH_ID).  The differentiators run first, in k_hpf5, over the
+// frame held beyond its edges: their output is formed on a frame padded by
+// two pixels on every side (x = -2 .. W + 1, y = -2 .. H + 1), and beyond that
+// padding it is constant, so holding the padded plane at its edges is exactly
+// the differentiated held frame.  The column passes write the blurred
+// channels cropped back to the frame, into the caller's array.  k_steer forms
+// the steered derivatives of Sec. 2 (after eq 3).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -94,19 +95,6 @@ __global__ void __launch_bounds__(HTX *HTY) k_hpf5(const void *__restrict__ X, i
   }
 }
 
-// D at scale s and channel c (blockIdx.z = s * 15 + c), row blockIdx.y: raw
-// (per channel S planes of the padded frame, sigma^2 times the blurred
-// channel) -> out[(s * 15 + c) * H * W + y * W + x]
-__global__ void __launch_bounds__(256) k_crop(const float *__restrict__ raw, int W, int H, int S,
-                                              const Coef *__restrict__ coef, float *__restrict__ out) {
-  const int s = blockIdx.z / QUARTIC_NCH, c = blockIdx.z - s * QUARTIC_NCH;
-  const int y = blockIdx.y, x = blockIdx.x * 256 + threadIdx.x;
-  if (x >= W) return;
-  const int Wp = W + 4, Hp = H + 4;
-  const float v = __ldg(raw + (((long)c * S + s) * Hp + y + 2) * Wp + x + 2);
-  out[((long)blockIdx.z * H + y) * W + x] = v / __ldg(&coef[s].sigma2);
-}
-
 struct SteerMat {
   float m[55];  // per order n = 0..4, an (n + 1) x (n + 1) block, row-major
 };
@@ -152,13 +140,6 @@ int launch_hpf5(const void *X, int dtype, float vs, long pitch, int W, int H, fl
   if (W < 1 || H < 1 || H + 4 > 8 * 65535) return -1;
   const dim3 grid((W + 4 + HTX - 1) / HTX, (H + 4 + HTY - 1) / HTY), block(HTX, HTY);
   k_hpf5<<<grid, block, 0, st>>>(X, dtype, vs, pitch, W, H, out);
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
-}
-
-int launch_quartic_crop(const float *raw, int W, int H, int S, const Coef *coef, float *out, cudaStream_t st) {
-  if (W < 1 || H < 1 || H > 65535 || S < 1 || S * QUARTIC_NCH > 65535) return -1;
-  const dim3 grid((W + 255) / 256, H, S * QUARTIC_NCH);
-  k_crop<<<grid, 256, 0, st>>>(raw, W, H, S, coef, out);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
