@@ -25,8 +25,8 @@ namespace {
 // The differentiators of a D = 5 bank: eqs (13)-(17) with the pure-delay
 // basis and dc constraints only (moments l < 5 of g_d equal to d! delta_{l,d},
 // Sec. 4.1), in correlation form y(n) = sum_j g(j) x(n + j), j = -2..2:
-// integer weights over a common denominator, so that the FP64 sums below are
-// exact for f32 inputs of moderate dynamic range.
+// integer weights over a common denominator (the denominator divides once,
+// at the end).
 __host__ __device__ constexpr int g5(int d, int j) {
   constexpr int w[5][5] = {
       {0, 0, 1, 0, 0},        // d = 0: the unit impulse
@@ -41,16 +41,40 @@ __host__ __device__ constexpr double den5(int d) { return d == 1 || d == 2 ? 12.
 
 constexpr int HTX = 32, HTY = 8;  // outputs per block
 
+// Compensated dot products (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26 (2005), algorithm Dot2): each product is
+// split exactly by an FMA (TwoProduct), each sum by Knuth's TwoSum, and the
+// rounding errors are accumulated beside the sum, so the result is as
+// accurate as if computed in twice the working precision and then rounded.
+// The _rn intrinsics are never contracted into FMAs, which the error-free
+// transformations rely on.
+struct Acc2 {
+  float p = 0.f, s = 0.f;  // running sum and accumulated errors
+  __device__ __forceinline__ void add_prod(float w, float x) {
+    const float h = __fmul_rn(w, x), e = fmaf(w, x, -h);  // w x = h + e exactly
+    const float t = __fadd_rn(p, h), z = __fsub_rn(t, p);
+    s += __fadd_rn(__fsub_rn(p, __fsub_rn(t, z)), __fsub_rn(h, z)) + e;  // p + h = t + that exactly
+    p = t;
+  }
+  __device__ __forceinline__ void add_small(float w, float x) { s = fmaf(w, x, s); }
+  // p + s as an unevaluated pair hi + lo (TwoSum)
+  __device__ __forceinline__ float2 pair() const {
+    const float hi = __fadd_rn(p, s), z = __fsub_rn(hi, p);
+    return make_float2(hi, __fadd_rn(__fsub_rn(p, __fsub_rn(hi, z)), __fsub_rn(s, z)));
+  }
+};
+
 // every channel U_{dx,dy} = g_dx (x) g_dy of the held frame, on the padded
 // frame (Wp = W + 4) x (Hp = H + 4): plane c of out (stride Wp Hp) holds at
-// py * Wp + px the value at x = px - 2, y = py - 2.  The five x-differences of
-// the block's rows are formed once and shared by the channels.  FP64 sums,
-// one rounding to f32: the differences cancel most of the frame's magnitude,
-// and rounding only the result keeps U accurate relative to itself.
+// py * Wp + px the value at x = px - 2, y = py - 2.  The four nontrivial
+// x-differences of the block's rows are formed once, as unevaluated sums
+// hi + lo, and shared by the channels.  The differences cancel most of the
+// frame's magnitude; the compensated sums keep U accurate relative to itself
+// (a few units of its last place) whatever the cancellation.
 __global__ void __launch_bounds__(HTX *HTY) k_hpf5(const void *__restrict__ X, int dtype, float vs, long pitch,
                                                    int W, int H, float *__restrict__ out) {
-  __shared__ double xs[HTY + 4][HTX + 4];
-  __shared__ double ts[4][HTY + 4][HTX];  // dx = 1..4 (dx = 0 reads xs)
+  __shared__ float xs[HTY + 4][HTX + 4];
+  __shared__ float2 ts[4][HTY + 4][HTX];  // dx = 1..4 (dx = 0 reads xs)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * HTX + tx;
   const int px0 = blockIdx.x * HTX, py0 = blockIdx.y * HTY;
   const int Wp = W + 4, Hp = H + 4;
@@ -59,22 +83,22 @@ __global__ void __launch_bounds__(HTX *HTY) k_hpf5(const void *__restrict__ X, i
     for (int i = tid; i < (HTY + 4) * (HTX + 4); i += HTX * HTY) {
       const int r = i / (HTX + 4), c = i % (HTX + 4);
       const int x = min(max(px0 - 4 + c, 0), W - 1), y = min(max(py0 - 4 + r, 0), H - 1);
-      xs[r][c] = (double)(vs * in_f32(__ldg(Xt + (long)y * pitch + x)));
+      xs[r][c] = vs * in_f32(__ldg(Xt + (long)y * pitch + x));
     }
   });
   __syncthreads();
   for (int i = tid; i < (HTY + 4) * HTX; i += HTX * HTY) {
     const int r = i / HTX, c = i % HTX;
-    double v[5];
+    float v[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) v[j] = xs[r][c + j];
 #pragma unroll
     for (int d = 1; d < 5; ++d) {
-      double t = 0.0;
+      Acc2 a;
 #pragma unroll
       for (int j = 0; j < 5; ++j)
-        if (g5(d, j) != 0) t = fma((double)g5(d, j), v[j], t);
-      ts[d - 1][r][c] = t;
+        if (g5(d, j) != 0) a.add_prod((float)g5(d, j), v[j]);
+      ts[d - 1][r][c] = a.pair();
     }
   }
   __syncthreads();
@@ -86,11 +110,20 @@ __global__ void __launch_bounds__(HTX *HTY) k_hpf5(const void *__restrict__ X, i
 #pragma unroll
     for (int dy = 0; dy <= n; ++dy, ++c) {
       const int dx = n - dy;
-      double u = 0.0;
+      Acc2 a;
 #pragma unroll
-      for (int j = 0; j < 5; ++j)
-        if (g5(dy, j) != 0) u = fma((double)g5(dy, j), dx == 0 ? xs[ty + j][tx + 2] : ts[dx - 1][ty + j][tx], u);
-      out[c * plane + o] = (float)(u * (1.0 / (den5(dx) * den5(dy))));
+      for (int j = 0; j < 5; ++j) {
+        if (g5(dy, j) == 0) continue;
+        const float w = (float)g5(dy, j);
+        if (dx == 0) {
+          a.add_prod(w, xs[ty + j][tx + 2]);
+        } else {
+          const float2 t = ts[dx - 1][ty + j][tx];
+          a.add_prod(w, t.x);
+          a.add_small(w, t.y);
+        }
+      }
+      out[c * plane + o] = __fadd_rn(a.p, a.s) / (float)(den5(dx) * den5(dy));
     }
   }
 }
