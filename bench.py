@@ -81,7 +81,7 @@ GATED_THRESHOLD = 0.3  # clustered frames: the 1/f background alone stays below 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel, from one ncu capture of the current kernel (profiles/, summary of
 # the same workload); absent: null
-MEASURED_TRAFFIC = {("iir_fir", "fir_coldet", "f32"): 428.8e6}
+MEASURED_TRAFFIC = {("iir_fir", "fir_coldet", "f32"): 428.8e6, ("quartic", "iir_row", "f32"): 1205.2e6}
 
 
 def make_frames(wl):
@@ -827,7 +827,8 @@ def run_quartic(args):
     b_top = quartic_bytes(top, S, H, W)
     ach = b_top / (t_top / n_top * 1e-3) / 1e9 if b_top else None
     roof = {"kernel": top, "bound": "hbm", "achieved": round(ach, 1) if ach else None, "peak": peak,
-            "unit": "GB/s", "frac": round(ach / peak, 4) if ach else None, "traffic": None,
+            "unit": "GB/s", "frac": round(ach / peak, 4) if ach else None,
+            "traffic": MEASURED_TRAFFIC.get(("quartic", top, "f32")),
             "peak_source": src, "bytes_per_launch": b_top}
     cpu = None
     if not args.no_cpu:
