@@ -301,7 +301,7 @@ int kf_blob_shapes(kf_ctx *ctx, double threshold, kf_blob_shape *out, int64_t ca
 
 /* D_{dx,dy} of one frame at nscales scales.
  *   frame   one device frame (any KF_DTYPE_*, value_scale applied), width
- *           <= 8188
+ *           <= 8192
  *   scales  host, nscales values lambda > 0 (sigma = lambda / 2), 1..16
  *   type, order  the blur: KF_IIR_REPEATED_POLE with order = K^lpf = L_D +
  *           Lbar_pi in 3..6 (L_D = 2 design of Sec. 4.3; at least one Nyquist

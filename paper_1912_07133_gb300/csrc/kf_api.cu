@@ -135,8 +135,10 @@ struct kf_ctx {
   int q_chan = -1, q_ld = 1;
   float *q_out = nullptr;  // the caller's D array: channel frame f, scale s at (s * 15 + f) * H * W
   int q_H = 0, q_W = 0;
-  float *q_pad = nullptr;  // one differentiated channel on the frame padded by 2
+  float *q_pad = nullptr;  // the differentiated channels, W x (H + 4) each
   size_t q_pad_floats = 0;
+  float *q_xpre = nullptr;  // their rows' pre-rolls (x = -2, -1, W, W + 1)
+  size_t q_xpre_floats = 0;
   // per-kernel times of the last profiled kf_quartic_bank call (returned by
   // kf_kernel_times until the next kf_filter_bank call)
   bool q_times_valid = false;
@@ -456,6 +458,7 @@ void kf_destroy(kf_ctx *ctx) {
   cudaFree(ctx->d_dlay);
   cudaFree(ctx->shape_buf);
   cudaFree(ctx->q_pad);
+  cudaFree(ctx->q_xpre);
   for (cudaEvent_t ev : ctx->q_ev)
     if (ev) cudaEventDestroy(ev);
   for (void *q : {(void *)ctx->g_pooled, (void *)ctx->g_logits, (void *)ctx->g_act, (void *)ctx->g_sel[0],
@@ -607,13 +610,15 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     d.X = fr.data;
     d.resp = opts.responses ? opts.responses + roff : nullptr;
     d.rplane = 0;
-    d.rpitch = d.rmargin = 0;
-    if (ctx->q_chan >= 0) {  // D = 5 channel frame f: cropped into out[s][f][H][W]
+    d.rpitch = d.rmx = d.rmy = 0;
+    d.xpre = nullptr;
+    if (ctx->q_chan >= 0) {  // D = 5 channel frame f: rows 2 .. H + 1 into out[s][f][H][W]
       const long hw = (long)ctx->q_H * ctx->q_W;
       d.resp = ctx->q_out + f * hw;
       d.rplane = kf::QUARTIC_NCH * hw;
       d.rpitch = ctx->q_W;
-      d.rmargin = 2;
+      d.rmy = 2;
+      d.xpre = reinterpret_cast<const float4 *>(ctx->q_xpre) + (long)f * (ctx->q_H + 4);
     }
     d.xpitch = fr.pitch;
     d.prow = prows;
@@ -1382,7 +1387,7 @@ int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, in
   const int W = frame->width, H = frame->height;
   if (!frame->data || W < 1 || H < 1 || frame->pitch < W)
     return fail(ctx, KF_EINVAL, "kf_quartic_bank: bad frame %dx%d pitch %lld", W, H, (long long)frame->pitch);
-  if (W > 8188) return fail(ctx, KF_EINVAL, "kf_quartic_bank: width > 8188");
+  if (W > 8192) return fail(ctx, KF_EINVAL, "kf_quartic_bank: width > 8192");
   if (H > 65535) return fail(ctx, KF_EINVAL, "kf_quartic_bank: height > 65535");
   if (frame->dtype < KF_DTYPE_F32 || frame->dtype > KF_DTYPE_U16)
     return fail(ctx, KF_EINVAL, "kf_quartic_bank: unknown dtype %d", frame->dtype);
@@ -1391,10 +1396,12 @@ int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, in
     return fail(ctx, KF_EINVAL, "kf_quartic_bank: data is not aligned to its element size");
   cudaError_t e;
   if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
-  const int Wp = W + 4, Hp = H + 4;
-  const size_t npad = (size_t)Wp * Hp;
+  const int Hp = H + 4;
+  const size_t npad = (size_t)W * Hp;
   int rc;
   if ((rc = grow(ctx, &ctx->q_pad, &ctx->q_pad_floats, npad * kf::QUARTIC_NCH, "D = 5 channel planes")))
+    return rc;
+  if ((rc = grow(ctx, &ctx->q_xpre, &ctx->q_xpre_floats, (size_t)4 * Hp * kf::QUARTIC_NCH, "D = 5 pre-rolls")))
     return rc;
   struct Restore {
     kf_ctx *c;
@@ -1411,9 +1418,9 @@ int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, in
   for (int c = 0; c < kf::QUARTIC_NCH; ++c) {
     pf[c] = kf_frame{};
     pf[c].data = ctx->q_pad + (size_t)c * npad;
-    pf[c].width = Wp;
+    pf[c].width = W;
     pf[c].height = Hp;
-    pf[c].pitch = Wp;
+    pf[c].pitch = W;
     pf[c].dtype = KF_DTYPE_F32;
     pf[c].value_scale = 1.f;
   }
@@ -1458,11 +1465,12 @@ int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, in
     return KF_OK;
   };
   if ((rc = timed("quartic_hpf", [&] {
-         return kf::launch_hpf5(frame->data, frame->dtype, vs, (long)frame->pitch, W, H, ctx->q_pad, ctx->stream);
+         return kf::launch_hpf5(frame->data, frame->dtype, vs, (long)frame->pitch, W, H, ctx->q_pad, ctx->q_xpre,
+                                ctx->stream);
        })))
     return rc;
   // the column passes write D (the identity channel carries no sigma^2)
-  // straight into out, cropped by the two padding pixels
+  // straight into out, without the two padding rows at each end
   ctx->q_chan = kf::CH_ID;
   ctx->q_out = out;
   ctx->q_H = H;

@@ -28,13 +28,17 @@ struct FrameDev {
   long aoff;       // gated calls: byte offset of the frame's active-tile map (64 x 64 tiles)
   long roff;       // float offset of the frame's planes in response-layout buffers (S x H x W)
   // response layout when rplane > 0: value (s, y, x) at resp[s * rplane +
-  // (y - rmargin) * rpitch + x - rmargin], only for y, x at least rmargin
+  // (y - rmy) * rpitch + x - rmx], only for y at least rmy and x at least rmx
   // inside the frame (the D = 5 bank writes its padded channel frames cropped
   // into the caller's array); rplane = 0: S x H x W planes.  Honoured by
   // detect_tile (the IIR column pass and the FP32 FIR column pass, the
   // passes of the D = 5 bank), not by the tensor-core FIR column pass.
   long rplane;
-  int rpitch, rmargin;
+  int rpitch, rmx, rmy;
+  // CH_ID rows with two-sample pre-rolls (the D = 5 bank): per frame row,
+  // the values at x = -2 (held beyond), -1, W and W + 1 (held beyond); null:
+  // the row is held at its ends
+  const float4 *xpre;
   int H, W;
   int nseg;        // IIR column segments
   int index;       // frame index in the call (blob records)

@@ -28,7 +28,7 @@ struct DetectArgs {
   DevStatus *status;
   float *resp;         // optional: R planes of this frame (S x H x W)
   long rplane = 0;     // with rplane > 0: the frame's cropped response layout (FrameDev)
-  int rpitch = 0, rmargin = 0;
+  int rpitch = 0, rmx = 0, rmy = 0;
   int ld = 32;         // row stride of the response buffer (floats)
   int coff = 0;        // column of lane 0 inside a buffer row
   int srows = 0;       // rows per scale in the buffer (0: NR)
@@ -168,13 +168,13 @@ static __device__ void detect_tile(const float *buf, float *red, const DetectArg
   const int SR = a.srows ? a.srows : a.NR;
   if (a.resp) {
     const long plane = a.rplane > 0 ? a.rplane : (long)a.H * a.W;
-    const int pitch = a.rplane > 0 ? a.rpitch : a.W, m = a.rplane > 0 ? a.rmargin : 0;
+    const int pitch = a.rplane > 0 ? a.rpitch : a.W, mx = a.rplane > 0 ? a.rmx : 0, my = a.rplane > 0 ? a.rmy : 0;
     for (int q = tid; q < NI; q += nt) {
       const int i = 1 + q / 30, lane = 1 + q % 30;
       const int y = a.r0 + i, x = a.x0 + lane;
-      if (y < m || y >= a.H - m || x < m || x >= a.W - m) continue;
+      if (y < my || y >= a.H - my || x < mx || x >= a.W - mx) continue;
       for (int s = 0; s < a.S; ++s)
-        a.resp[s * plane + (long)(y - m) * pitch + (x - m)] = buf[(s * SR + i) * a.ld + a.coff + lane];
+        a.resp[s * plane + (long)(y - my) * pitch + (x - mx)] = buf[(s * SR + i) * a.ld + a.coff + lane];
     }
   }
   if (a.raw) return;  // a derivative channel: written, not detected (uniform over the block)

@@ -217,6 +217,14 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr,
       auto ld = [&](const decltype(Xt) row, int e) { return vs * in_f32(__ldg(row + e)); };
       const float vlo = ld(rp, 0) - 2.f * ld(r0, 0) + ld(rm, 0);
       const float vhi = ld(rp, W - 1) - 2.f * ld(r0, W - 1) + ld(rm, W - 1);
+      if (chan == CH_ID && F.xpre) {  // D = 5 channel row with its two-sample pre-rolls
+        const float4 xp = F.xpre[y];
+        for (int j = tid; j < n; j += RNT) {
+          const int e = xs - G + j;
+          sL[pad20(j)] = e < -1 ? xp.x : (e == -1 ? xp.y : (e < W ? ld(r0, e) : (e == W ? xp.z : xp.w)));
+        }
+        return;
+      }
       if (chan != CH_LAP) {  // one derivative channel of the derivative bank
         const int cin = EDGE ? edge_chan(chan) : chan;
         auto am = [&](int e) { return ld(rm, min(max(e, 0), W - 1)); };
@@ -376,7 +384,8 @@ __global__ void __launch_bounds__(CNT) k_colfir(const FrameDev *__restrict__ fr,
     a.resp = F.resp;
     a.rplane = F.rplane;
     a.rpitch = F.rpitch;
-    a.rmargin = F.rmargin;
+    a.rmx = F.rmx;
+    a.rmy = F.rmy;
     detect_tile(buf, red, a);
     __syncthreads();
   }

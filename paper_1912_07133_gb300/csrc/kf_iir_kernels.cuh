@@ -250,19 +250,21 @@ __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, i
   const int y = EDGE ? (yw == 0 ? 0 : H - 1) : yw;
   const float vs = F.vscale;
   const long xpitch = F.xpitch;
+  // the identity channel reads its own row only
+  const bool one = chan == CH_ID;
   with_input_type(F.X, F.dtype, [&](auto Xt) {
-    const auto *rm = Xt + (long)max(y - 1, 0) * xpitch;
     const auto *r0 = Xt + (long)y * xpitch;
-    const auto *rp = Xt + (long)min(y + 1, H - 1) * xpitch;
+    const auto *rm = one ? r0 : Xt + (long)max(y - 1, 0) * xpitch;
+    const auto *rp = one ? r0 : Xt + (long)min(y + 1, H - 1) * xpitch;
     // 8 elements (24 loads) per thread in flight before they are stored
     for (int e0 = tid; e0 < W; e0 += 8 * NT) {
       float a[8], b[8], c[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int e = min(e0 + u * NT, W - 1);
-        a[u] = in_f32(__ldg(rm + e));
         b[u] = in_f32(__ldg(r0 + e));
-        c[u] = in_f32(__ldg(rp + e));
+        a[u] = one ? b[u] : in_f32(__ldg(rm + e));
+        c[u] = one ? b[u] : in_f32(__ldg(rp + e));
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
@@ -280,7 +282,20 @@ __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, i
   float L[CH];
   const int x0 = tid * CH;
   float in_lo, in_hi;
-  if (chan == CH_LAP) {
+  // two-sample pre-rolls (CH_ID with xpre): the left carry is the steady state
+  // of U(-2) advanced by U(-1); the right one that of U(W + 1), advanced by
+  // U(W) when the chunks end at W (otherwise U(W) is a chunk element)
+  const float4 xp = (one && F.xpre) ? F.xpre[y] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const bool pre = one && F.xpre, pre_hi = pre && NT * CH == W;
+  if (pre) {
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      const int e = x0 + i;
+      L[i] = e < W ? s_0[pad32(e)] : (e == W ? xp.z : xp.w);
+    }
+    in_lo = xp.x;
+    in_hi = xp.w;
+  } else if (chan == CH_LAP) {
     const float v_lo = s_p[0] - 2.f * s_0[0] + s_m[0];
     const int eW = pad32(W - 1);
     const float v_hi = s_p[eW] - 2.f * s_0[eW] + s_m[eW];
@@ -327,6 +342,8 @@ __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, i
     Rec hlo, hhi;
     hlo.hold(c, in_lo);
     hhi.hold(c, in_hi);
+    if (pre) hlo.push(v, xp.y);
+    if (pre_hi) hhi.push(v, xp.z);
     const Rec cf = carry_scan<Rec, false>(ef, c, tid, NT, s_scan, hlo);
     const Rec cb = carry_scan<Rec, true>(eb, c, NT - 1 - tid, NT, s_scan, hhi);
     float yv[CH];
@@ -684,7 +701,8 @@ __global__ void __launch_bounds__(512) __maxnreg__(LC == 32 ? Rec::kColdetRegs32
     a.resp = F.resp;
     a.rplane = F.rplane;
     a.rpitch = F.rpitch;
-    a.rmargin = F.rmargin;
+    a.rmx = F.rmx;
+    a.rmy = F.rmy;
     a.ld = LD;
     a.coff = F32 ? off : 0;
     a.srows = REG / LD;

@@ -139,10 +139,12 @@ int launch_shapes(const Blob *b, long n, const float *c20, const float *c02, con
                   const Coef *coef, void *out, cudaStream_t st);
 
 // D = 5 derivative bank (kf_quartic.cu): the 15 differentiated channels of a
-// frame on the frame padded by 2 (f32 planes of pitch W + 4 and H + 4 rows,
-// one after the other); the steering of 15-channel sets (m55: per order n =
+// frame on the frame padded by 2 rows (f32 planes of pitch W and H + 4 rows,
+// one after the other) and, per plane row, the values 2 and 1 pixels before
+// and 1 and 2 after the row (xpre, 4 floats); the steering of 15-channel sets (m55: per order n =
 // 0..4 an (n+1) x (n+1) row-major block)
-int launch_hpf5(const void *X, int dtype, float vs, long pitch, int W, int H, float *out, cudaStream_t st);
+int launch_hpf5(const void *X, int dtype, float vs, long pitch, int W, int H, float *out, float *xpre,
+                cudaStream_t st);
 int launch_steer(const float *in, long npix, int nsets, const float *m55, float *out, cudaStream_t st);
 
 // candidate ordering (kf_sort.cu)

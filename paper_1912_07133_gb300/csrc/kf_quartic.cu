@@ -8,8 +8,11 @@
 // frame held beyond its edges: their output is formed on a frame padded by
 // two pixels on every side (x = -2 .. W + 1, y = -2 .. H + 1), and beyond that
 // padding it is constant, so holding the padded plane at its edges is exactly
-// the differentiated held frame.  The column passes write the blurred
-// channels cropped back to the frame, into the caller's array.  k_steer forms
+// the differentiated held frame.  The planes keep the frame's width: the two
+// values beyond each row end enter the row passes as a pre-roll of their
+// recursion (or window); the two rows beyond each column end are plane rows.
+// The column passes write the blurred channels, without those rows, into the
+// caller's array.  k_steer forms
 // the steered derivatives of Sec. 2 (after eq 3).
 #include <cuda_runtime.h>
 
@@ -64,15 +67,17 @@ struct Acc2 {
   }
 };
 
-// every channel U_{dx,dy} = g_dx (x) g_dy of the held frame, on the padded
-// frame (Wp = W + 4) x (Hp = H + 4): plane c of out (stride Wp Hp) holds at
-// py * Wp + px the value at x = px - 2, y = py - 2.  The four nontrivial
+// every channel U_{dx,dy} = g_dx (x) g_dy of the held frame at x = -2 .. W + 1,
+// y = -2 .. H + 1 (Hp = H + 4 rows): plane c of out (W x Hp, stride W Hp)
+// holds at py * W + x the value at (x, py - 2) for x = 0 .. W - 1, and
+// xpre[c * Hp + py] the values at x = -2, -1, W, W + 1.  The four nontrivial
 // x-differences of the block's rows are formed once, as unevaluated sums
 // hi + lo, and shared by the channels.  The differences cancel most of the
 // frame's magnitude; the compensated sums keep U accurate relative to itself
 // (a few units of its last place) whatever the cancellation.
 __global__ void __launch_bounds__(HTX *HTY) k_hpf5(const void *__restrict__ X, int dtype, float vs, long pitch,
-                                                   int W, int H, float *__restrict__ out) {
+                                                   int W, int H, float *__restrict__ out,
+                                                   float *__restrict__ xpre) {
   __shared__ float xs[HTY + 4][HTX + 4];
   __shared__ float2 ts[4][HTY + 4][HTX];  // dx = 1..4 (dx = 0 reads xs)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * HTX + tx;
@@ -104,7 +109,10 @@ __global__ void __launch_bounds__(HTX *HTY) k_hpf5(const void *__restrict__ X, i
   __syncthreads();
   const int px = px0 + tx, py = py0 + ty;
   if (px >= Wp || py >= Hp) return;
-  const long plane = (long)Wp * Hp, o = (long)py * Wp + px;
+  // x = px - 2: inside the frame into the plane, else into the row's pre-roll
+  const bool in = px >= 2 && px < W + 2;
+  const int k = px < 2 ? px : px - W;  // pre-roll slot 0, 1 (left) or 2, 3 (right)
+  const long plane = (long)W * Hp, o = in ? (long)py * W + px - 2 : 0;
 #pragma unroll
   for (int n = 0, c = 0; n <= 4; ++n) {
 #pragma unroll
@@ -123,7 +131,9 @@ __global__ void __launch_bounds__(HTX *HTY) k_hpf5(const void *__restrict__ X, i
           a.add_small(w, t.y);
         }
       }
-      out[c * plane + o] = __fadd_rn(a.p, a.s) / (float)(den5(dx) * den5(dy));
+      const float u = __fadd_rn(a.p, a.s) / (float)(den5(dx) * den5(dy));
+      if (in) out[c * plane + o] = u;
+      else xpre[((long)c * Hp + py) * 4 + k] = u;
     }
   }
 }
@@ -169,10 +179,11 @@ int grid_for(long n, int threads) {
 
 }  // namespace
 
-int launch_hpf5(const void *X, int dtype, float vs, long pitch, int W, int H, float *out, cudaStream_t st) {
+int launch_hpf5(const void *X, int dtype, float vs, long pitch, int W, int H, float *out, float *xpre,
+                cudaStream_t st) {
   if (W < 1 || H < 1 || H + 4 > 8 * 65535) return -1;
   const dim3 grid((W + 4 + HTX - 1) / HTX, (H + 4 + HTY - 1) / HTY), block(HTX, HTY);
-  k_hpf5<<<grid, block, 0, st>>>(X, dtype, vs, pitch, W, H, out);
+  k_hpf5<<<grid, block, 0, st>>>(X, dtype, vs, pitch, W, H, out, xpre);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

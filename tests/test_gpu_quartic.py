@@ -74,9 +74,12 @@ def fp32_bound(frame, scales, ftype, order):
     return 4 * 2.0 ** -24 * (g1 ** 2)[:, None] * umax[None, :]
 
 
-@pytest.mark.parametrize("ftype,order", [(D, 3), (D, 4), (E, 3), (C, 2)])
-def test_quartic_bank_matches_the_oracle(ftype, order):
-    frame = SY.iir_fir_frame(seed=21, H=150, W=133, nblobs=25)
+@pytest.mark.parametrize("ftype,order,shape", [(D, 3, (150, 133)), (D, 4, (150, 133)), (E, 3, (150, 133)),
+                                               (C, 2, (150, 133)), (D, 4, (90, 128)), (C, 2, (90, 128))])
+def test_quartic_bank_matches_the_oracle(ftype, order, shape):
+    """Widths 133 (the row pass's last chunk runs past the frame) and 128 (the
+    chunks end at the frame's edge)."""
+    frame = SY.iir_fir_frame(seed=21, H=shape[0], W=shape[1], nblobs=25)
     scales = [2.0, 3.5, 6.0]
     G = run_gpu(frame, scales, ftype, order)
     R = Q.quartic_bank(frame.astype(np.float64), scales, OT[ftype], order)
