@@ -81,7 +81,8 @@ GATED_THRESHOLD = 0.3  # clustered frames: the 1/f background alone stays below 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel, from one ncu capture of the current kernel (profiles/, summary of
 # the same workload); absent: null
-MEASURED_TRAFFIC = {("iir_fir", "fir_coldet", "f32"): 428.8e6, ("quartic", "iir_row", "f32"): 1205.2e6}
+MEASURED_TRAFFIC = {("iir_fir", "fir_coldet", "f32"): 428.8e6, ("quartic", "iir_coldet", "f32"): 2126.2e6,
+                    ("quartic", "iir_row", "f32"): 1196.8e6}
 
 
 def make_frames(wl):
@@ -742,11 +743,11 @@ QUARTIC_HW = 2048
 
 def quartic_bytes(name, S, H, W, nch=15):
     """Algorithmic bytes of one launch of a kernel of the D = 5 bank (all 15
-    channels): the differentiator reads the frame and writes the 15 padded
-    planes; the row pass reads them and writes S planes each; the
-    segment-state pass reads those; the column pass reads them and writes the
-    15 S output planes (cropped to the frame)."""
-    P = (H + 4) * (W + 4)
+    channels): the differentiator reads the frame and writes the 15 channel
+    planes (W x (H + 4): two rows beyond each end); the row pass reads them
+    and writes S planes each; the segment-state pass reads those; the column
+    pass reads them and writes the 15 S output planes (H rows)."""
+    P = (H + 4) * W
     return {"quartic_hpf": 4 * H * W + 4 * nch * P, "iir_row": nch * (4 * P + 4 * S * P),
             "iir_colseg": nch * 4 * S * P, "iir_coldet": nch * (4 * S * P + 4 * S * H * W)}.get(name)
 
