@@ -239,7 +239,7 @@ __host__ __device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
 // One row of one frame: row yw, or (EDGE) the U-only first (yw = 0) or last
 // (yw = 1) row for the column boundary.  One body for both cases keeps the
 // kernel's code small.  All threads of the block; ends with __syncthreads.
-template <class Rec>
+template <class Rec, bool ID>
 __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, int chan,
                                          const Coef *__restrict__ coef, int S, void *__restrict__ P, int st,
                                          long PWb, float *__restrict__ edge, bool &ovf, float *sm) {
@@ -250,8 +250,8 @@ __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, i
   const int y = EDGE ? (yw == 0 ? 0 : H - 1) : yw;
   const float vs = F.vscale;
   const long xpitch = F.xpitch;
-  // the identity channel reads its own row only
-  const bool one = chan == CH_ID;
+  // ID: the identity channel (CH_ID), which reads its own row only
+  constexpr bool one = ID;
   with_input_type(F.X, F.dtype, [&](auto Xt) {
     const auto *r0 = Xt + (long)y * xpitch;
     const auto *rm = one ? r0 : Xt + (long)max(y - 1, 0) * xpitch;
@@ -287,7 +287,7 @@ __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, i
   // U(W) when the chunks end at W (otherwise U(W) is a chunk element)
   const float4 xp = (one && F.xpre) ? F.xpre[y] : make_float4(0.f, 0.f, 0.f, 0.f);
   const bool pre = one && F.xpre, pre_hi = pre && NT * CH == W;
-  if (pre) {
+  if (one && pre) {
 #pragma unroll
     for (int i = 0; i < CH; ++i) {
       const int e = x0 + i;
@@ -342,8 +342,8 @@ __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, i
     Rec hlo, hhi;
     hlo.hold(c, in_lo);
     hhi.hold(c, in_hi);
-    if (pre) hlo.push(v, xp.y);
-    if (pre_hi) hhi.push(v, xp.z);
+    if (one && pre) hlo.push(v, xp.y);
+    if (one && pre_hi) hhi.push(v, xp.z);
     const Rec cf = carry_scan<Rec, false>(ef, c, tid, NT, s_scan, hlo);
     const Rec cb = carry_scan<Rec, true>(eb, c, NT - 1 - tid, NT, s_scan, hhi);
     float yv[CH];
@@ -362,7 +362,7 @@ __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, i
     // planes hold sigma^2 x the one-sided blur: the column pass then only
     // negates (R_L = -sigma^2 (D20 + D02)), and 16-bit planes keep the
     // magnitude of R at every scale (the blur alone for CH_ID)
-    const float s2 = chan == CH_ID ? 1.f : c.sigma2;
+    const float s2 = one ? 1.f : c.sigma2;
 #pragma unroll
     for (int i = 0; i < CH; ++i) s_out[pad32(x0 + i)] = s2 * yv[i];
     __syncthreads();
@@ -391,7 +391,9 @@ __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, i
 // Row pass: one block per row, persistent over the rows of the launch's
 // frames; items H and H + 1 of a frame are its two U-only edge rows.  All
 // frames of a launch share the block width (chunks of CH pixels per thread).
-template <class Rec>
+// ID: the identity channel of the D = 5 bank (a separate instance keeps the
+// other channels' code as it is).
+template <class Rec, bool ID>
 __global__ void __launch_bounds__(256) k_row(const FrameDev *__restrict__ fr, Items it,
                                              const Coef *__restrict__ coef, int S, void *__restrict__ P,
                                              int st, long PWb, float *__restrict__ edge,
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(256) k_row(const FrameDev *__restrict__ fr, It
     __syncthreads();
     const FrameDev &F = s_fr;
     const bool e = local >= F.H;
-    row_body<Rec>(F, e, e ? local - F.H : local, chan, coef, S, P, st, PWb, edge, ovf, sm);
+    row_body<Rec, ID>(F, e, e ? local - F.H : local, chan, coef, S, P, st, PWb, edge, ovf, sm);
   }
   if (ovf) atomicExch(&status->range, 1);
 }
@@ -716,7 +718,8 @@ template <class Rec, int ST, int LC>
 int run_iir_st(const Plan &p, const BankArgs &a, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_row<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_row<Rec, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_row<Rec, ST == ST_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_coldet<Rec, ST, LC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
@@ -735,12 +738,15 @@ int run_iir_st(const Plan &p, const BankArgs &a, cudaStream_t st) {
   da.resp = nullptr;
   da.raw = a.raw;
   using TS = typename Store<ST>::T;
+  // the identity channel (the D = 5 bank, f32 planes only) has its own instance
+  if (a.chan == CH_ID && ST != ST_F32) return -1;
   auto row = [&](const Launch &l) {
     const size_t smem = (size_t)(3 * (pad32(l.nt * CH) + 1) + 64 * Rec::NF) * sizeof(float);
     if (smem > 200 * 1024) return false;
-    const int nb = persistent_blocks((const void *)k_row<Rec>, l.nt, smem, l.it.total, p.mult[PASS_ROW]);
+    const auto kfn = a.chan == CH_ID ? k_row<Rec, ST == ST_F32> : k_row<Rec, false>;
+    const int nb = persistent_blocks((const void *)kfn, l.nt, smem, l.it.total, p.mult[PASS_ROW]);
     a.prof->begin("iir_row", st);
-    k_row<Rec><<<nb, l.nt, smem, st>>>(p.fr, l.it, a.coef, a.S, a.P, a.storage, p.PWb, a.edge, a.status, a.chan);
+    kfn<<<nb, l.nt, smem, st>>>(p.fr, l.it, a.coef, a.S, a.P, a.storage, p.PWb, a.edge, a.status, a.chan);
     a.prof->end(st);
     return true;
   };
