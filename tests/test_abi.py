@@ -95,3 +95,14 @@ def test_field_offsets_match_the_c_compiler(tmp_path):
         assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
+def test_quartic_entry_points_reject_bad_arguments_without_a_device(lib):
+    """The D = 5 calls check their arguments before any CUDA call: a NULL
+    context or NULL pointers give KF_EINVAL with a message."""
+    from paper_1912_07133_gb300 import kf
+    assert lib.kf_quartic_bank(None, None, None, 1, kf.KF_IIR_REPEATED_POLE, 4, None, 0) == kf.KF_EINVAL
+    assert b"ctx" in lib.kf_last_error(None)
+    assert lib.kf_quartic_steer(None, None, 10, 1, 0.5, None) == kf.KF_EINVAL
+    assert kf.KF_QUARTIC_CHANNELS == 15 and len(kf.QUARTIC_CHANNELS) == 15
+    assert kf.QUARTIC_CHANNELS[:3] == ((0, 0), (1, 0), (0, 1))
