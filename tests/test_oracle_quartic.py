@@ -12,7 +12,8 @@ mathematics, independent of the oracle's own formulas.
   blur, interior), and equals a brute-force 2-D convolution of the outer
   product of the impulse responses over the held frame (all three blurs).
 * Steering maps coefficients so that both polynomials of eq (1) agree at
-  every point, and reduces to the identity and to the quarter turn.
+  every point, reduces to the identity and to the quarter turn, and maps the
+  Hessian by its congruence transform.
 """
 import json
 import math
@@ -192,3 +193,21 @@ def test_steering_special_angles():
     phi = 0.3
     Ds = Q.steer(D, phi)
     assert np.allclose(Ds[1], math.cos(phi) * D[1] - math.sin(phi) * D[2], atol=1e-14)
+
+
+def test_steering_of_the_hessian_is_its_congruence_transform():
+    """Order 2: with [x~, y~]^T = M [x, y]^T, M = [[cos, sin], [-sin, cos]], the
+    Hessian of the polynomial in (x, y) is M^T H M, H = [[D20, D11], [D11, D02]]
+    the Hessian in (x~, y~)."""
+    rng = np.random.default_rng(12)
+    D = rng.normal(size=(15, 1, 1))
+    for phi in (0.3, 1.1, -2.4):
+        c, s = math.cos(phi), math.sin(phi)
+        M = np.array([[c, s], [-s, c]])
+        Hm = np.array([[D[3, 0, 0], D[4, 0, 0]], [D[4, 0, 0], D[5, 0, 0]]])  # (2,0), (1,1), (0,2)
+        Ht = M.T @ Hm @ M
+        Ds = Q.steer(D, phi)[:, 0, 0]
+        assert np.allclose([Ds[3], Ds[4], Ds[5]], [Ht[0, 0], Ht[0, 1], Ht[1, 1]], atol=1e-13)
+        # the determinant and trace are invariant
+        assert abs(Ds[3] * Ds[5] - Ds[4] ** 2 - np.linalg.det(Hm)) < 1e-12
+        assert abs(Ds[3] + Ds[5] - np.trace(Hm)) < 1e-13
