@@ -317,7 +317,9 @@ int kf_blob_shapes(kf_ctx *ctx, double threshold, kf_blob_shape *out, int64_t ca
  *           the per-kernel totals of this call.  0: no timing.
  * Runs on the context stream (asynchronous unless profiling; out is complete
  * when the stream is).  Uses the context's bank: afterwards kf_detect_blobs
- * has no result until the next kf_filter_bank call.
+ * has no result until the next kf_filter_bank call.  The recursive blurs run
+ * on 32-row column segments unless kf_set_segment_length or kf_autotune
+ * chose a length for the type.
  * Errors: KF_EINVAL (bad arguments, a type or order without vanishing
  * moments to order 4), KF_ECOND (design), KF_ECUDA. */
 int kf_quartic_bank(kf_ctx *ctx, const kf_frame *frame, const double *scales, int nscales, int type,
