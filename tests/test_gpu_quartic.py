@@ -91,6 +91,23 @@ def test_quartic_bank_matches_the_oracle(ftype, order, shape):
     assert channel_errors(G, R)[:, low].max() <= TOL
 
 
+@pytest.mark.parametrize("shape", [(1, 1), (1, 37), (5, 3), (2, 70)])
+def test_quartic_bank_degenerate_frames(shape):
+    """Frames narrower or shorter than the stencils, a tile and a row chunk:
+    one pixel, one row, a few pixels.  Every channel against the oracle (whose
+    own FP64 rounding, about 1e-17 of the frame where a derivative is exactly
+    zero, sets a floor of 1e-12 max|X|)."""
+    rng = np.random.default_rng(sum(shape))
+    frame = rng.uniform(0, 1, shape).astype(np.float32)
+    for ftype, order in ((D, 4), (C, 2)):
+        G = run_gpu(frame, [2.0, 5.0], ftype, order)
+        R = Q.quartic_bank(frame.astype(np.float64), [2.0, 5.0], OT[ftype], order)
+        tol = TOL * np.maximum(np.ptp(R, axis=(2, 3)), np.abs(R).max(axis=(2, 3))) + \
+            fp32_bound(frame, [2.0, 5.0], ftype, order) + 1e-12 * float(np.abs(frame).max())
+        err = np.abs(G - R).max(axis=(2, 3))
+        assert np.all(err <= tol), (ftype, float((err / tol).max()))
+
+
 def test_quartic_bank_input_types_and_value_scale():
     import torch
     rng = np.random.default_rng(4)
