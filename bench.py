@@ -127,6 +127,25 @@ def dist_info():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(x, world, device):
+    """x of the slowest rank (every rank gets it): the step time of a job of
+    independent replicas is the time of the last one to finish."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms_per_step):
+    """Whole-job throughput in millions of units per second: the units all
+    ranks processed (each replica the same workload) over the slowest rank's
+    step time."""
+    return world * units_per_rank / (ms_per_step * 1e-3) / 1e6
+
+
 # ---------------------------------------------------------------------------
 # algorithmic work per kernel launch (one frame, all scales)
 # ---------------------------------------------------------------------------
@@ -331,23 +350,19 @@ def run_ours(args):
             barrier()
         return sum(a.elapsed_time(b) for a, b in ev), kt, nb, clk.summary()
 
-    def max_over_ranks(x):
-        if world > 1:
-            t = torch.tensor([x], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return x
+    def slowest(x):
+        return max_over_ranks(x, world, dev)
 
     # --- device-resident timed region (no profiling events) ------------------
     total_ms, _, nblobs, clocks = timed(False)
-    ms_per_step = max_over_ranks(total_ms) / args.steps
+    ms_per_step = slowest(total_ms) / args.steps
     pix_scales = len(BANKS) * pixels * len(SCALES)
-    value = world * pix_scales / (ms_per_step * 1e-3) / 1e6
+    value = job_value(pix_scales, world, ms_per_step)
     # --- the same steps with the banks one after the other ------------------
     serial_run = None
     if concurrent:
         s_ms, _, _, _ = timed(False, serial=True)
-        s_step = max_over_ranks(s_ms) / args.steps
+        s_step = slowest(s_ms) / args.steps
         serial_run = {"value": round(world * pix_scales / (s_step * 1e-3) / 1e6, 1), "ms_per_step": round(s_step, 4),
                       "launches": "the banks one after the other on their streams"}
     # --- the same steps again with CUDA events around every kernel ------------
@@ -358,7 +373,7 @@ def run_ours(args):
         for _ in range(2):
             step(False, kf.KF_SCHED_PER_FRAME)
         pf_ms, _, _, _ = timed(False, kf.KF_SCHED_PER_FRAME)
-        pf_step = max_over_ranks(pf_ms) / args.steps
+        pf_step = slowest(pf_ms) / args.steps
         per_frame = {"value": round(world * pix_scales / (pf_step * 1e-3) / 1e6, 1), "ms_per_step": round(pf_step, 4),
                      "launches": "every pass once per frame, eager (no graph)"}
 
@@ -379,7 +394,7 @@ def run_ours(args):
         if i >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
             bo = nb * np.dtype(kf.BLOB_DTYPE).itemsize
-    e2e_step = max_over_ranks(sum(e2e_ms) / len(e2e_ms))
+    e2e_step = slowest(sum(e2e_ms) / len(e2e_ms))
     e2e = {"value": world * pix_scales / (e2e_step * 1e-3) / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": int(sum(host[j].nbytes for j in src)), "d2h_bytes_per_step": int(bo),
            "ms_per_step": e2e_step}
@@ -532,11 +547,7 @@ def run_gated(args):
                     a, c = kt.get(k, (0, 0.0))
                     kt[k] = (a + nl, c + ms)
             torch.cuda.synchronize(dev)
-        t = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-        if world > 1:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / args.steps, world, dev)
         return t, kt, clk.summary()
 
     for _ in range(args.warmup):
