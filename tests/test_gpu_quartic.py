@@ -91,6 +91,17 @@ def test_quartic_bank_matches_the_oracle(ftype, order, shape):
     assert channel_errors(G, R)[:, low].max() <= TOL
 
 
+@pytest.mark.parametrize("ftype,order", [(D, 5), (D, 6), (E, 4), (E, 6)])
+def test_quartic_bank_other_orders(ftype, order):
+    """The remaining orders the call accepts (Filter D up to K^lpf = 6, Filter
+    E up to L_B / 2 = 6) on a ragged 70 x 90 frame."""
+    frame = SY.iir_fir_frame(seed=31, H=70, W=90, nblobs=8)
+    scales = [2.5, 6.0]
+    G = run_gpu(frame, scales, ftype, order)
+    R = Q.quartic_bank(frame.astype(np.float64), scales, OT[ftype], order)
+    assert channel_errors(G, R, fp32_bound(frame, scales, ftype, order)).max() <= 1.0
+
+
 @pytest.mark.parametrize("shape", [(1, 1), (1, 37), (5, 3), (2, 70)])
 def test_quartic_bank_degenerate_frames(shape):
     """Frames narrower or shorter than the stencils, a tile and a row chunk:
