@@ -211,3 +211,22 @@ def test_steering_of_the_hessian_is_its_congruence_transform():
         # the determinant and trace are invariant
         assert abs(Ds[3] * Ds[5] - Ds[4] ** 2 - np.linalg.det(Hm)) < 1e-12
         assert abs(Ds[3] + Ds[5] - np.trace(Hm)) < 1e-13
+
+
+@pytest.mark.parametrize("order", [3, 4, 6])
+def test_butterworth_is_flat_to_order_two_n_minus_one(order):
+    """Filter E of order n = L_B / 2 (Sec. 4.4): |H| = (1 + (w/wc)^(2n))^(-1/2)
+    before the bilinear map, flat at dc to order 2n - 1, so the moments 2, 4,
+    .. 2n - 2 vanish and moment 2n does not."""
+    g = Q.Blur(O.IIR_BUTTERWORTH, order, 5.0).impulse_response(600)
+    half = (len(g) - 1) // 2
+    m = np.arange(-half, half + 1, dtype=float)
+    assert abs(np.sum(g) - 1.0) < 1e-9
+    # relative to sum |g| |m|^l (dominated by the tails at high l): the
+    # vanishing moments sit at rounding level, the first non-vanishing one
+    # orders of magnitude above it
+    for l in range(2, 2 * order, 2):
+        scale = np.sum(np.abs(g) * np.abs(m) ** l)
+        assert abs(np.sum(g * m ** l)) <= 1e-10 * scale, l
+    l = 2 * order
+    assert abs(np.sum(g * m ** l)) > 1e-8 * np.sum(np.abs(g) * np.abs(m) ** l)
