@@ -8,7 +8,7 @@ shares no code with the CUDA library.
 * ``hpf_taps``: the FIR differentiators of Sec. 4.1 (eqs 12-17, pure-delay
   basis, dc constraints only: the differentiator is cascaded with a blur
   that is flat at dc, so no Nyquist constraint is imposed).
-* ``lpf``: the blur of a D = 5 bank, flat at dc up to order 4 (L_D = 2):
+* ``Blur``: the blur of a D = 5 bank, flat at dc up to order 4 (L_D = 2):
   Filter D (Sec. 4.3), Filter E (Sec. 4.4, order L_B / 2 = L_D + 1) or
   Filter C (Sec. 4.2, L_D = 2, K = ceil(7 sigma), omega_c = 3 / sigma).
 * ``quartic_bank``: the estimates of D_{dx,dy} (eq 3) for every dx + dy <= 4
