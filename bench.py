@@ -26,9 +26,17 @@ Filter C with K <= 160, one-sided planes stored as --storage (default f16).
 
 Metric: Mpixel-scales/s = banks x frames x pixels x scales / step time.
 
+The default run (--workload iir_fir) prints one line for the 4096^2 workload
+and adds, measured after its own timed region with --sub-steps steps each,
+the sub-objects "gated" (gated vs plain on the clustered workload, recall),
+"batch" and "counts" (the workloads above); --only leaves them out.  Every
+line reports the HBM fraction of the algorithmic bytes per bank and per step
+("hbm") and the roofline of the dominant kernel ("roofline").
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload iir_fir|counts|batch] [--storage f32|f16|bf16]
-                  [--no-graph] [--no-tune]
+                  [--workload iir_fir|counts|batch|gated|table5|quartic]
+                  [--storage f32|f16|bf16] [--no-graph] [--no-tune] [--only]
+                  [--sub-steps K2] [--gate-mode tiles|dilated]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.  Under torchrun (N > 1) every rank runs an
@@ -76,12 +84,36 @@ WORKLOADS = {
               "repeated-pole IIR bank + Butterworth bank (L_B = 4), Laplacian response, 3x3x8 extremum, "
               "blob lists read back; all frames in one call")),
 }
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_LANES = 128  # FP32 lanes per SM (Blackwell)
 GATED_THRESHOLD = 0.3  # clustered frames: the 1/f background alone stays below it
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel, from one ncu capture of the current kernel (profiles/, summary of
-# the same workload); absent: null
-MEASURED_TRAFFIC = {("iir_fir", "fir_coldet", "f32"): 428.8e6, ("quartic", "iir_coldet", "f32"): 2243.1e6}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel, from one
+# ncu capture (summaries in profiles/), keyed by (workload, kernel, storage):
+# (bytes, digest of the kernel sources the capture ran).  A figure is reported
+# only while the sources still have that digest; otherwise traffic is null.
+MEASURED_TRAFFIC = {}
+CSRC = os.path.join(ROOT, "paper_1912_07133_gb300", "csrc")
+
+
+def csrc_digest():
+    """sha256 (first 16 hex digits) over the CUDA sources of the library, in
+    name order: changes whenever any kernel changes."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(CSRC, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(workload, kernel, storage):
+    """Measured DRAM bytes per launch of `kernel`, or None when there is no
+    capture of the current sources."""
+    t = MEASURED_TRAFFIC.get((workload, kernel, storage))
+    if t is None or t[1] != csrc_digest():
+        return None
+    return t[0]
 
 
 def make_frames(wl):
@@ -227,10 +259,69 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# device facts and peaks
+# ---------------------------------------------------------------------------
+def sm_max_mhz(clocks=None):
+    """Maximum SM clock: the measured-peaks file's record, else the sampled
+    clocks.max.sm, else the GB300 nominal 2070 MHz."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        pass
+    if clocks and clocks.get("sm_max_mhz"):
+        return float(clocks["sm_max_mhz"])
+    return 2070.0
+
+
+def alu_peak(nsm, mhz):
+    """FP32 ALU peak (TFLOP/s): SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
+    return nsm * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+def bank_bytes(S, pixels, s_in, s_b):
+    """Algorithmic bytes of one bank over `pixels` frame pixels at S scales:
+    the two-pass design reads the frame once, writes and reads back S planes
+    (2 s_b + s_in / S per pixel-scale)."""
+    return pixels * (s_in + 2.0 * s_b * S)
+
+
+def roofline_of(kernel, ms_total, launches, byts, flops, hbm, hbm_src, nsm, mhz, traffic):
+    """Roofline record of one kernel: its algorithmic work per launch over its
+    average event-timed launch duration against the bound that applies.  A
+    FIR pass's work is the method's 2(2K + 1) flop per output and scale,
+    counted once (the tensor-core pass spends three TF32 products on each to
+    keep FP32 accuracy; that factor is reported, not counted as work)."""
+    per = ms_total / max(launches, 1) * 1e-3  # s per launch
+    rec = {"kernel": kernel, "launches": launches, "ms_per_launch": round(per * 1e3, 4)}
+    if flops:
+        ach = flops / launches / per / 1e12
+        if kernel in TENSOR_3XTF32:
+            tp, tsrc = tf32_peak()
+            rec.update(bound="tensor", achieved=round(ach, 3), peak=round(tp, 1), unit="TFLOP/s",
+                       frac=round(ach / tp, 4), peak_source=tsrc, tf32_products_per_tap=3,
+                       work="2(2K+1) flop per output and scale (method work, counted once)")
+        else:
+            pk = alu_peak(nsm, mhz)
+            rec.update(bound="alu", achieved=round(ach, 3), peak=round(pk, 1), unit="TFLOP/s",
+                       frac=round(ach / pk, 4),
+                       peak_source=f"derived: {nsm} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz",
+                       work="2(2K+1) flop per output and scale")
+        if byts:
+            rec["hbm_frac"] = round(byts / launches / per / 1e9 / hbm, 4)
+    else:
+        ach = byts / launches / per / 1e9
+        rec.update(bound="hbm", achieved=round(ach, 1), peak=hbm, unit="GB/s", frac=round(ach / hbm, 4),
+                   peak_source=hbm_src)
+    rec["traffic"] = traffic
+    rec["algorithmic_bytes_per_launch"] = round(byts / max(launches, 1))
+    return rec
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def run_ours(args):
-    import numpy as np
+def setup_device(args):
     import torch
     import torch.distributed as dist
 
@@ -238,15 +329,29 @@ def run_ours(args):
     from paper_1912_07133_gb300 import kf
 
     rank, world, local = dist_info()
-    if world > 1:
+    if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     __graft_entry__.build() if rank == 0 or world == 1 else None
     if world > 1:
         dist.barrier()
     kf.load()
-    wl = WORKLOADS[args.workload]
-    storage = args.storage or wl["storage"]
+    return rank, world, local
+
+
+def measure_workload(args, name, steps, warmup, full=True):
+    """Steps of one workload of WORKLOADS on this rank's GPU.  full: also the
+    serial and frame-by-frame schedules, end to end and the profiled pass's
+    per-kernel roofline (the sub-workloads of the default run take the device
+    timing, the per-bank HBM fractions and the kernel list only)."""
+    import numpy as np
+    import torch
+
+    from paper_1912_07133_gb300 import kf
+
+    rank, world, local = dist_info()
+    wl = WORKLOADS[name]
+    storage = (args.storage if name == args.workload else None) or wl["storage"]
     NF, SCALES, BANKS = wl["frames"], wl["scales"], wl["banks"]
     graph = not args.no_graph
     dev = torch.device("cuda", local)
@@ -268,8 +373,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     # one library context per bank, each on its own stream: the banks of a
     # step are independent passes over the same frames and run at once
-    bstreams = {name: torch.cuda.Stream(dev) for name, _, _ in BANKS}
-    banks = {name: kf.Bank(local, bstreams[name].cuda_stream) for name, _, _ in BANKS}
+    bstreams = {bn: torch.cuda.Stream(dev) for bn, _, _ in BANKS}
+    banks = {bn: kf.Bank(local, bstreams[bn].cuda_stream) for bn, _, _ in BANKS}
     concurrent = len(BANKS) > 1 and not args.serial
 
     # one-time designs (FP64 kernel), timed separately: the bank reuses them
@@ -282,71 +387,71 @@ def run_ours(args):
     # launch shapes and segment lengths tuned once per bank on this workload
     tuned = {}
     if not args.no_tune:
-        for name, ft, order in BANKS:
+        for bn, ft, order in BANKS:
             o = kf.kf_bank_opts_default()
             o.threshold = THRESHOLD
             o.fir_kmax = wl["fir_kmax"]
             o.storage = STORAGE[storage]
-            shapes, lc, _ = kf.kf_autotune(banks[name].ctx, Xs, SCALES, ft, order, o, vscales)
-            tuned[name] = {"grid_mult": {p: m for p, m in zip(("row", "seg", "fold", "det"), shapes) if m >= 0}}
+            shapes, lc, _ = kf.kf_autotune(banks[bn].ctx, Xs, SCALES, ft, order, o, vscales)
+            tuned[bn] = {"grid_mult": {p: m for p, m in zip(("row", "seg", "fold", "det"), shapes) if m >= 0}}
             if lc > 0:
-                tuned[name]["segment_rows"] = lc
+                tuned[bn]["segment_rows"] = lc
 
-    def run_bank(name, frames, ft, order, profile=False, schedule=kf.KF_SCHED_BATCHED, use_graph=graph):
-        banks[name].run(frames, SCALES, ft, order, threshold=THRESHOLD, profile=profile, fir_kmax=wl["fir_kmax"],
-                        storage=STORAGE[storage], value_scales=vscales, schedule=schedule, graph=use_graph)
+    def run_bank(bn, frames, ft, order, profile=False, schedule=kf.KF_SCHED_BATCHED, use_graph=graph):
+        banks[bn].run(frames, SCALES, ft, order, threshold=THRESHOLD, profile=profile, fir_kmax=wl["fir_kmax"],
+                      storage=STORAGE[storage], value_scales=vscales, schedule=schedule, graph=use_graph)
 
     def step(profile, schedule=kf.KF_SCHED_BATCHED, frames=None, serial=None):
         """One pass of every bank over the frames, blob lists read back.  The
         banks' streams start after the work already on `stream` and `stream`
         waits for them at the end.  Concurrent: all banks launched, then the
         lists read; serial (profiling, frame-by-frame launches): one bank after
-        the other."""
+        the other.  Returns (blobs, {bank: {kernel: (launches, ms)}})."""
         n, times = 0, {}
         frames = Xs if frames is None else frames
         use_graph = graph and not profile and schedule == kf.KF_SCHED_BATCHED
         serial = (profile or not concurrent or schedule != kf.KF_SCHED_BATCHED) if serial is None else serial
-        for name, _, _ in BANKS:
-            bstreams[name].wait_stream(stream)
+        for bn, _, _ in BANKS:
+            bstreams[bn].wait_stream(stream)
         if serial:
-            for name, ft, order in BANKS:
-                run_bank(name, frames, ft, order, profile, schedule, use_graph)
-                n += len(banks[name].blobs())
+            for bn, ft, order in BANKS:
+                run_bank(bn, frames, ft, order, profile, schedule, use_graph)
+                n += len(banks[bn].blobs())
                 if profile:
-                    for k, (nl, ms) in banks[name].kernel_times().items():
-                        a, b = times.get(k, (0, 0.0))
-                        times[k] = (a + nl, b + ms)
+                    times[bn] = banks[bn].kernel_times()
         else:
-            for name, ft, order in BANKS:
-                run_bank(name, frames, ft, order, profile, schedule, use_graph)
-            for name, _, _ in BANKS:
-                n += len(banks[name].blobs())
-        for name, _, _ in BANKS:
-            stream.wait_stream(bstreams[name])
+            for bn, ft, order in BANKS:
+                run_bank(bn, frames, ft, order, profile, schedule, use_graph)
+            for bn, _, _ in BANKS:
+                n += len(banks[bn].blobs())
+        for bn, _, _ in BANKS:
+            stream.wait_stream(bstreams[bn])
         return n, times
 
     def barrier():
         if world > 1:
+            import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(False)
 
-    def timed(profile, schedule=kf.KF_SCHED_BATCHED, serial=None):
+    def timed(profile, schedule=kf.KF_SCHED_BATCHED, serial=None, nsteps=steps):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+              for _ in range(nsteps)]
         kt, nb = {}, 0
         barrier()
         with ClockSampler(local) as clk:
-            for i in range(args.steps):
+            for i in range(nsteps):
                 flush.zero_()
                 ev[i][0].record(stream)
                 nb, times = step(profile, schedule, serial=serial)
                 ev[i][1].record(stream)
-                for k, (nl, ms) in times.items():
-                    a, b = kt.get(k, (0, 0.0))
-                    kt[k] = (a + nl, b + ms)
+                for bn, tk in times.items():
+                    for k, (nl, ms) in tk.items():
+                        a, b = kt.setdefault(bn, {}).get(k, (0, 0.0))
+                        kt[bn][k] = (a + nl, b + ms)
             barrier()
         return sum(a.elapsed_time(b) for a, b in ev), kt, nb, clk.summary()
 
@@ -355,159 +460,139 @@ def run_ours(args):
 
     # --- device-resident timed region (no profiling events) ------------------
     total_ms, _, nblobs, clocks = timed(False)
-    ms_per_step = slowest(total_ms) / args.steps
+    ms_per_step = slowest(total_ms) / steps
     pix_scales = len(BANKS) * pixels * len(SCALES)
     value = job_value(pix_scales, world, ms_per_step)
+    out = {"value": round(value, 1), "unit": UNIT, "ms_per_step": round(ms_per_step, 4), "steps": steps,
+           "warmup": warmup, "clocks": clocks, "blobs_per_step": nblobs, "design_ms": round(design_ms, 2)}
     # --- the same steps with the banks one after the other ------------------
-    serial_run = None
-    if concurrent:
+    if concurrent and full:
         s_ms, _, _, _ = timed(False, serial=True)
-        s_step = slowest(s_ms) / args.steps
-        serial_run = {"value": round(world * pix_scales / (s_step * 1e-3) / 1e6, 1), "ms_per_step": round(s_step, 4),
-                      "launches": "the banks one after the other on their streams"}
+        s_step = slowest(s_ms) / steps
+        out["serial"] = {"value": round(world * pix_scales / (s_step * 1e-3) / 1e6, 1),
+                         "ms_per_step": round(s_step, 4),
+                         "launches": "the banks one after the other on their streams"}
     # --- the same steps again with CUDA events around every kernel ------------
     _, ktimes, _, _ = timed(True)
     # --- the same steps launched frame by frame (batch workloads) ------------
-    per_frame = None
-    if NF > 1:
+    if NF > 1 and full:
         for _ in range(2):
             step(False, kf.KF_SCHED_PER_FRAME)
         pf_ms, _, _, _ = timed(False, kf.KF_SCHED_PER_FRAME)
-        pf_step = slowest(pf_ms) / args.steps
-        per_frame = {"value": round(world * pix_scales / (pf_step * 1e-3) / 1e6, 1), "ms_per_step": round(pf_step, 4),
-                     "launches": "every pass once per frame, eager (no graph)"}
+        pf_step = slowest(pf_ms) / steps
+        out["per_frame_schedule"] = {"value": round(world * pix_scales / (pf_step * 1e-3) / 1e6, 1),
+                                     "ms_per_step": round(pf_step, 4),
+                                     "launches": "every pass once per frame, eager (no graph)"}
 
     # --- end to end: host frames in pinned memory, copies inside the timed region
-    pinned = [as_t(h).pin_memory() for h in host]
-    Xe = [torch.empty_like(x) for x in X]
-    Xev = [dview(x) for x in Xe]
-    e2e_ms, bo = [], 0
-    for i in range(args.warmup + args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for x, j in zip(Xe, src):
-            x.copy_(pinned[j], non_blocking=True)
-        nb, _ = step(False, frames=Xev)
-        b.record(stream)
-        b.synchronize()
-        if i >= args.warmup:
-            e2e_ms.append(a.elapsed_time(b))
-            bo = nb * np.dtype(kf.BLOB_DTYPE).itemsize
-    e2e_step = slowest(sum(e2e_ms) / len(e2e_ms))
-    e2e = {"value": world * pix_scales / (e2e_step * 1e-3) / 1e6, "unit": UNIT,
-           "h2d_bytes_per_step": int(sum(host[j].nbytes for j in src)), "d2h_bytes_per_step": int(bo),
-           "ms_per_step": e2e_step}
+    if full:
+        pinned = [as_t(h).pin_memory() for h in host]
+        Xe = [torch.empty_like(x) for x in X]
+        Xev = [dview(x) for x in Xe]
+        e2e_ms, bo = [], 0
+        for i in range(warmup + steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for x, j in zip(Xe, src):
+                x.copy_(pinned[j], non_blocking=True)
+            nb, _ = step(False, frames=Xev)
+            b.record(stream)
+            b.synchronize()
+            if i >= warmup:
+                e2e_ms.append(a.elapsed_time(b))
+                bo = nb * np.dtype(kf.BLOB_DTYPE).itemsize
+        e2e_step = slowest(sum(e2e_ms) / len(e2e_ms))
+        out["e2e"] = {"value": world * pix_scales / (e2e_step * 1e-3) / 1e6, "unit": UNIT,
+                      "h2d_bytes_per_step": int(sum(host[j].nbytes for j in src)), "d2h_bytes_per_step": int(bo),
+                      "ms_per_step": e2e_step}
+        del pinned, Xe, Xev
 
-    # --- roofline of the dominant kernel -------------------------------------
-    # algorithmic work of a kernel per step, summed over the banks that run it
-    # and all frames; achieved = that work x steps / the kernel's summed time
+    # --- HBM fractions and the roofline of the dominant kernel ---------------
     hbm, hbm_src = peaks()
-    alu_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_max_mhz(clocks)
     taps = fir_taps(SCALES, wl["fir_kmax"])
     sizes = dict(s_in=wl["s_in"], s_b=SB[storage])
+    per_bank_bytes = bank_bytes(len(SCALES), pixels, wl["s_in"], SB[storage])
+    banks_rec, step_bytes = {}, 0.0
+    for bn, ft, _o in BANKS:
+        kms = sum(ms for _, ms in ktimes.get(bn, {}).values()) / steps
+        step_bytes += per_bank_bytes
+        banks_rec[bn] = {"kernel_ms": round(kms, 4), "algorithmic_bytes": round(per_bank_bytes),
+                         "hbm_frac": round(per_bank_bytes / (kms * 1e-3) / 1e9 / hbm, 4) if kms else None}
+    out["hbm"] = {"peak_gbs": hbm, "peak_source": hbm_src,
+                  "bytes_per_pixel_scale": round(2.0 * SB[storage] + wl["s_in"] / len(SCALES), 3),
+                  "step_frac": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm, 4),
+                  "banks": banks_rec,
+                  "note": "algorithmic bytes (2 s_b + s_in / S per pixel-scale) over the device-timed step "
+                          "(step_frac) or over the sum of the bank's kernel event times (banks)",
+                  "target_frac": 0.70}
+    # per-kernel totals over the banks (the kernels of two banks of one kind share names)
+    kall = {}
+    for bn, tk in ktimes.items():
+        for k, (nl, ms) in tk.items():
+            a, b = kall.get(k, (0, 0.0))
+            kall[k] = (a + nl, b + ms)
 
     def work(k):
         byts = flops = 0.0
         for _, ft, _o in BANKS:
-            if k.startswith("fir_") == (ft == 2):
+            if k.startswith("fir_") == (ft in (2, 3)):
                 b_, f_ = algorithmic(k, len(SCALES), pixels, taps, **sizes)
                 byts, flops = byts + b_, flops + f_
-        return byts * args.steps, flops * args.steps
+        return byts * steps, flops * steps
 
     kern = {}
-    total_kms = max(sum(v[1] for v in ktimes.values()), 1e-9)
-    for k, (nl, ms) in ktimes.items():
+    total_kms = max(sum(v[1] for v in kall.values()), 1e-9)
+    for k, (nl, ms) in kall.items():
         byts, flops = work(k)
         kern[k] = {"launches": nl, "ms_per_launch": round(ms / max(nl, 1), 4), "share": round(ms / total_kms, 4)}
         if byts:
             kern[k]["GB_s"] = round(byts / (ms * 1e-3) / 1e9, 1)
+            kern[k]["hbm_frac"] = round(byts / (ms * 1e-3) / 1e9 / hbm, 4)
         if flops:
             kern[k]["TFLOP_s"] = round(flops / (ms * 1e-3) / 1e12, 2)
-    dom = max(ktimes, key=lambda k: ktimes[k][1])
+    dom = max(kall, key=lambda k: kall[k][1])
     byts, flops = work(dom)
-    ms = ktimes[dom][1]
-    if flops and dom in TENSOR_3XTF32:
-        # TF32 products the FP32-accurate taps need (three per tap product,
-        # no band padding) per second, against the TF32 tensor peak
-        ach = 3 * flops / (ms * 1e-3) / 1e12
-        tp, tsrc = tf32_peak()
-        roof = {"kernel": dom, "bound": "tensor", "achieved": round(ach, 3), "peak": round(tp, 1),
-                "unit": "TFLOP/s", "frac": round(ach / tp, 4),
-                "traffic": MEASURED_TRAFFIC.get((args.workload, dom, storage)),
-                "peak_source": tsrc, "work": "3 TF32 products x 2(2K+1) flop per output and scale"}
-    elif flops:
-        ach = flops / (ms * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 1),
-                "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4),
-                "traffic": MEASURED_TRAFFIC.get((args.workload, dom, storage)),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
-    else:
-        ach = byts / (ms * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "traffic": MEASURED_TRAFFIC.get((args.workload, dom, storage)),
-                "peak_source": hbm_src}
+    out["roofline"] = roofline_of(dom, kall[dom][1], kall[dom][0], byts, flops, hbm, hbm_src, nsm, mhz,
+                                  traffic_of(name, dom, storage))
+    out["kernels"] = kern
     # filter-bank kernels launched in the timed region (the profiled pass runs the same steps)
-    launches = sum(v[0] for v in ktimes.values())
+    out["gpu_launches"] = sum(v[0] for v in kall.values())
     for b in banks.values():
         b.close()
-
-    cpu = cpu_baseline(host[0], wl, rows=None if args.workload == "iir_fir" else wl["ref_rows"]) \
-        if (rank == 0 and not args.no_cpu) else None
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
-    if rank != 0:
-        return
     shapes = sorted({f"{host[j].shape[1]}x{host[j].shape[0]}" for j in src})
-    line = {
-        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl["text"], "frames": NF, "frame_sizes": shapes, "input": wl["dtype"],
-                   "storage": storage, "scales_px": [round(x, 3) for x in SCALES],
-                   "banks": [b[0] for b in BANKS], "threshold": THRESHOLD, "fir_kmax": wl["fir_kmax"],
-                   "launch": ("batched schedule, replayed from a CUDA graph" if graph else "batched schedule, eager")
-                   + ("; one context and stream per bank, the banks of a step launched at once" if concurrent
-                      else "; the banks one after the other"),
-                   "tuned": tuned or "library defaults (one block per work item, 64-row segments)",
-                   "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": f"replicas x{world}", "designs": "FP64 design kernel run once "
-                   "per bank configuration, timed separately (design_ms)"},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "kernels": kern, "blobs_per_step": nblobs,
-        "design_ms": round(design_ms, 2),
-    }
-    if serial_run:
-        line["serial"] = serial_run
-    if per_frame:
-        line["per_frame_schedule"] = per_frame
-    print(json.dumps(line), flush=True)
+    out["config"] = {"workload": wl["text"], "frames": NF, "frame_sizes": shapes, "input": wl["dtype"],
+                     "storage": storage, "scales_px": [round(x, 3) for x in SCALES],
+                     "banks": [b[0] for b in BANKS], "threshold": THRESHOLD, "fir_kmax": wl["fir_kmax"],
+                     "launch": ("batched schedule, replayed from a CUDA graph" if graph else "batched schedule, eager")
+                     + ("; one context and stream per bank, the banks of a step launched at once" if concurrent
+                        else "; the banks one after the other"),
+                     "tuned": tuned or "library defaults (one block per work item, 64-row segments)",
+                     "l2": "flushed between steps (256 MiB write outside the timed events)",
+                     "parallelism": f"replicas x{world}"}
+    out["_host0"] = host[0]
+    del X, Xs, flush
+    torch.cuda.empty_cache()
+    return out
 
 
-def run_gated(args):
-    """Gated vs plain on the clustered 6144^2 f16 workload (recall judged
-    against the plain bank in the same run)."""
+def measure_gated(args, steps, warmup, full=True, mode_name="tiles"):
+    """Gated vs plain on the clustered 6144^2 f16 workload: 120 frames in
+    calls of 16, both banks at T = 0.3; recall = share of the plain bank's
+    blobs (both banks) that the gated run reports, judged in the same run."""
     import numpy as np
     import torch
-    import torch.distributed as dist
 
-    import __graft_entry__
     from paper_1912_07133_gb300 import kf, synthetic, train_proposal
 
     rank, world, local = dist_info()
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    __graft_entry__.build() if rank == 0 or world == 1 else None
-    if world > 1:
-        dist.barrier()
-    kf.load()
     NF, CHUNK, SIZE, T = 120, 16, 6144, GATED_THRESHOLD
     BANKS = IIR_FIR
     dev = torch.device("cuda", local)
     weights, p_gate, train_stats = train_proposal.load_weights()
-    mode = {"dilated": kf.KF_GATE_DILATED, "tiles": kf.KF_GATE_TILES}[args.gate_mode]
+    mode = {"dilated": kf.KF_GATE_DILATED, "tiles": kf.KF_GATE_TILES}[mode_name]
     frames = [synthetic.clustered_frame_device(4000 + i, SIZE, SIZE, device=f"cuda:{local}") for i in range(NF)]
     chunks = [frames[i:i + CHUNK] for i in range(0, NF, CHUNK)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -532,13 +617,14 @@ def run_gated(args):
         return n, times
 
     def timed(gate, profile=False):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         kt = {}
         if world > 1:
+            import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize(dev)
         with ClockSampler(local) as clk:
-            for i in range(args.steps):
+            for i in range(steps):
                 flush.zero_()
                 ev[i][0].record(stream)
                 _, times = step(gate, profile=profile)
@@ -547,84 +633,149 @@ def run_gated(args):
                     a, c = kt.get(k, (0, 0.0))
                     kt[k] = (a + nl, c + ms)
             torch.cuda.synchronize(dev)
-        t = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / args.steps, world, dev)
+        t = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, world, dev)
         return t, kt, clk.summary()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(True)
         step(False)
-    full, gated = set(), set()
-    step(False, collect=full)
-    step(True, collect=gated)
-    recall = len(full & gated) / max(len(full), 1)
+    full_set, gated_set = set(), set()
+    step(False, collect=full_set)
+    step(True, collect=gated_set)
+    recall = len(full_set & gated_set) / max(len(full_set), 1)
     ms_g, _, clocks = timed(True)
     ms_p, _, clocks_p = timed(False)
     _, ktimes, _ = timed(True, profile=True)
+    _, ktimes_p, _ = timed(False, profile=True)
     pix_scales = len(BANKS) * NF * SIZE * SIZE * len(EIGHT)
     value = world * pix_scales / (ms_g * 1e-3) / 1e6
     plain = world * pix_scales / (ms_p * 1e-3) / 1e6
-    # end to end: every chunk copied from pinned host memory before its calls
-    host = [f.cpu().pin_memory() for f in frames]
-    dbuf = [torch.empty_like(frames[0]) for _ in range(CHUNK)]
-    e2e_ms, bo = [], 0
-    for i in range(args.warmup + args.steps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        nb = 0
-        for c0 in range(0, NF, CHUNK):
-            for j in range(min(CHUNK, NF - c0)):
-                dbuf[j].copy_(host[c0 + j], non_blocking=True)
-            n, _ = step(True, src=[dbuf[:min(CHUNK, NF - c0)]])
-            nb += n
-        b.record(stream)
-        b.synchronize()
-        if i >= args.warmup:
-            e2e_ms.append(a.elapsed_time(b))
-            bo = nb * np.dtype(kf.BLOB_DTYPE).itemsize
-    e2e_step = sum(e2e_ms) / len(e2e_ms)
-    e2e = {"value": world * pix_scales / (e2e_step * 1e-3) / 1e6, "unit": UNIT,
-           "h2d_bytes_per_step": int(sum(h.numel() * 2 for h in host)), "d2h_bytes_per_step": int(bo),
-           "ms_per_step": e2e_step}
-    kern = {}
-    tot = max(sum(v[1] for v in ktimes.values()), 1e-9)
-    for k, (nl, ms) in ktimes.items():
-        kern[k] = {"launches": nl, "ms_per_launch": round(ms / max(nl, 1), 4), "share": round(ms / tot, 4)}
-    dom = max(ktimes, key=lambda k: ktimes[k][1])
-    alu_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    roof = {"kernel": dom, "bound": "alu" if dom.startswith("fir_") else "hbm", "achieved": None,
-            "peak": round(alu_peak, 1) if dom.startswith("fir_") else peaks()[0],
-            "unit": "TFLOP/s" if dom.startswith("fir_") else "GB/s", "frac": None, "traffic": None,
-            "note": "gated: the kernels run a data-dependent subset of their work items; see the default workload "
-                    "for the per-kernel roofline"}
+
+    def kernel_list(kt):
+        tot = max(sum(v[1] for v in kt.values()), 1e-9)
+        return {k: {"launches": nl, "ms_per_step": round(ms / steps, 4), "share": round(ms / tot, 4)}
+                for k, (nl, ms) in sorted(kt.items(), key=lambda kv: -kv[1][1])}
+
+    out = {"value": round(value, 1), "unit": UNIT, "ms_per_step": round(ms_g, 4), "steps": steps, "warmup": warmup,
+           "plain": {"value": round(plain, 1), "ms_per_step": round(ms_p, 4), "clocks": clocks_p,
+                     "kernels": kernel_list(ktimes_p)},
+           "recall": round(recall, 5), "blobs_plain": len(full_set), "blobs_gated": len(gated_set),
+           "speedup_vs_plain": round(ms_p / ms_g, 3), "clocks": clocks, "kernels": kernel_list(ktimes),
+           "gpu_launches": sum(v[0] for v in ktimes.values())}
+    if full:
+        # end to end: every chunk copied from pinned host memory before its calls
+        host = [f.cpu().pin_memory() for f in frames]
+        dbuf = [torch.empty_like(frames[0]) for _ in range(CHUNK)]
+        e2e_ms, bo = [], 0
+        for i in range(warmup + steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            nb = 0
+            for c0 in range(0, NF, CHUNK):
+                for j in range(min(CHUNK, NF - c0)):
+                    dbuf[j].copy_(host[c0 + j], non_blocking=True)
+                n, _ = step(True, src=[dbuf[:min(CHUNK, NF - c0)]])
+                nb += n
+            b.record(stream)
+            b.synchronize()
+            if i >= warmup:
+                e2e_ms.append(a.elapsed_time(b))
+                bo = nb * np.dtype(kf.BLOB_DTYPE).itemsize
+        e2e_step = sum(e2e_ms) / len(e2e_ms)
+        out["e2e"] = {"value": world * pix_scales / (e2e_step * 1e-3) / 1e6, "unit": UNIT,
+                      "h2d_bytes_per_step": int(sum(h.numel() * 2 for h in host)), "d2h_bytes_per_step": int(bo),
+                      "ms_per_step": e2e_step}
+        del host, dbuf
+    out["config"] = {"workload": ("120 x 6144x6144 FP16 clustered frames (1/f background std 0.1, blob clusters in "
+                                  "~5% of the 64x64 tiles, radii 2-32 px; seeds 4000-4119), 8 scales (lambda 2-64 px), "
+                                  "colored SG (K<=96) and 4th-order repeated-pole banks, threshold 0.3, calls of 16 "
+                                  "frames; gated by the trained proposal network vs the plain bank"),
+                     "gate": mode_name, "gate_threshold": p_gate, "frames": NF, "calls_of": CHUNK,
+                     "training": {k: train_stats[k] for k in ("frames", "epochs", "seeds", "label_prior")},
+                     "l2": "flushed between steps (256 MiB write outside the timed events)",
+                     "value_counts": "all pixel-scales of the workload (gated work done on a subset)",
+                     "parallelism": f"replicas x{world}"}
+    out["_frame0"] = frames[0]
     bank.close()
-    cpu = None
-    if rank == 0 and not args.no_cpu:
-        wl = dict(WORKLOADS["iir_fir"], scales=EIGHT, banks=BANKS, value_scale=1.0)
-        cpu = cpu_baseline(frames[0].float().cpu().numpy(), wl, rows=64)
+    del frames, chunks, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+SUB_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "clocks", "hbm", "roofline", "kernels",
+            "config", "gpu_launches", "per_frame_schedule", "blobs_per_step")
+
+
+def run_ours(args):
+    """The workload's JSON line.  The default workload (the 4096^2 six-scale
+    frame, both banks) also carries, as sub-objects measured after its own
+    timed region, the gated-vs-plain comparison on the clustered workload and
+    the uneven-batch and 12-bit-counts workloads (fewer steps each)."""
+    rank, world, local = setup_device(args)
+    import torch.distributed as dist
+    main = measure_workload(args, args.workload, args.steps, args.warmup, full=True)
+    host0 = main.pop("_host0")
+    subs = {}
+    if args.workload == "iir_fir" and not args.only:
+        ss, sw = args.sub_steps, max(3, args.sub_warmup)
+        g = measure_gated(args, ss, sw, full=False, mode_name=args.gate_mode)
+        g.pop("_frame0")
+        subs["gated"] = g
+        for sub in ("batch", "counts"):
+            r = measure_workload(args, sub, ss, sw, full=False)
+            r.pop("_host0")
+            subs[sub] = {k: r[k] for k in SUB_KEYS if k in r}
+    wl = WORKLOADS[args.workload]
+    cpu = cpu_baseline(host0, wl, rows=None if args.workload == "iir_fir" else wl["ref_rows"]) \
+        if (rank == 0 and not args.no_cpu) else None
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms_g, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": ("120 x 6144x6144 FP16 clustered frames (1/f background std 0.1, blob clusters in "
-                                "~5% of the 64x64 tiles, radii 2-32 px; seeds 4000-4119), 8 scales (lambda 2-64 px), "
-                                "colored SG (K<=96) and 4th-order repeated-pole banks, threshold 0.3, calls of 16 "
-                                "frames; gated by the trained proposal network vs the plain bank"),
-                   "gate": args.gate_mode, "gate_threshold": p_gate, "frames": NF, "calls_of": CHUNK,
-                   "training": {k: train_stats[k] for k in ("frames", "epochs", "seeds", "label_prior")},
-                   "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "value_counts": "all pixel-scales of the workload (gated work done on a subset)",
-                   "parallelism": f"replicas x{world}"},
-        "plain": {"value": round(plain, 1), "ms_per_step": round(ms_p, 4), "clocks": clocks_p},
-        "recall": round(recall, 5), "blobs_plain": len(full), "blobs_gated": len(gated),
-        "speedup_vs_plain": round(ms_p / ms_g, 3),
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": sum(v[0] for v in ktimes.values()),
-        "clocks": clocks, "kernels": kern,
+        "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(main["config"], designs="FP64 design kernel run once per bank configuration, "
+                                               "timed separately (design_ms)"),
+        "roofline": main["roofline"], "hbm": main["hbm"], "cpu_baseline": cpu, "e2e": main["e2e"],
+        "gpu_launches": main["gpu_launches"], "clocks": main["clocks"], "kernels": main["kernels"],
+        "blobs_per_step": main["blobs_per_step"], "design_ms": main["design_ms"],
     }
+    for k in ("serial", "per_frame_schedule"):
+        if k in main:
+            line[k] = main[k]
+    line.update(subs)
+    print(json.dumps(line), flush=True)
+
+
+def run_gated(args):
+    """The gated workload as its own JSON line (value: the gated bank)."""
+    rank, world, local = setup_device(args)
+    import torch.distributed as dist
+    g = measure_gated(args, args.steps, args.warmup, full=True, mode_name=args.gate_mode)
+    f0 = g.pop("_frame0")
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        wl = dict(WORKLOADS["iir_fir"], scales=EIGHT, banks=IIR_FIR, value_scale=1.0)
+        cpu = cpu_baseline(f0.float().cpu().numpy(), wl, rows=64)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": g["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": g["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": g["config"],
+            "plain": g["plain"], "recall": g["recall"], "blobs_plain": g["blobs_plain"],
+            "blobs_gated": g["blobs_gated"], "speedup_vs_plain": g["speedup_vs_plain"],
+            "roofline": {"kernel": next(iter(g["kernels"])), "bound": None, "achieved": None, "peak": None,
+                         "frac": None, "traffic": None,
+                         "note": "gated: the kernels run a data-dependent subset of their work items; the "
+                                 "default workload's line carries the per-kernel roofline"},
+            "cpu_baseline": cpu, "e2e": g["e2e"], "gpu_launches": g["gpu_launches"], "clocks": g["clocks"],
+            "kernels": g["kernels"]}
     print(json.dumps(line), flush=True)
 
 
@@ -839,7 +990,7 @@ def run_quartic(args):
     ach = b_top / (t_top / n_top * 1e-3) / 1e9 if b_top else None
     roof = {"kernel": top, "bound": "hbm", "achieved": round(ach, 1) if ach else None, "peak": peak,
             "unit": "GB/s", "frac": round(ach / peak, 4) if ach else None,
-            "traffic": MEASURED_TRAFFIC.get(("quartic", top, "f32")),
+            "traffic": traffic_of("quartic", top, "f32"),
             "peak_source": src, "bytes_per_launch": b_top}
     cpu = None
     if not args.no_cpu:
@@ -956,11 +1107,15 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("gated", "table5", "quartic"), default="iir_fir")
-    ap.add_argument("--gate-mode", choices=("dilated", "tiles"), default="dilated",
+    ap.add_argument("--gate-mode", choices=("dilated", "tiles"), default="tiles",
                     help="gated workload: marked tiles with their neighbours, or marked tiles only")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default launch shapes)")
     ap.add_argument("--serial", action="store_true", help="run the banks of a step one after the other")
+    ap.add_argument("--only", action="store_true",
+                    help="default workload: skip the gated, batch and counts sub-workloads")
+    ap.add_argument("--sub-steps", type=int, default=3, help="timed steps of each sub-workload")
+    ap.add_argument("--sub-warmup", type=int, default=3, help="warm-up steps of each sub-workload (>= 3)")
     ap.add_argument("--storage", choices=tuple(STORAGE), default=None,
                     help="element type of the one-sided planes (default: the workload's)")
     args = ap.parse_args()

@@ -368,6 +368,17 @@ int kf_set_launch_shape(kf_ctx *ctx, int type, int pass, int grid_mult);
  * FP32 rounding.  Errors: KF_EINVAL. */
 int kf_set_segment_length(kf_ctx *ctx, int type, int rows);
 
+/* Failure-detection test hook.  polls > 0: the column pass of the recursive
+ * banks issues no copy to its shared-memory load barrier, so that its bounded
+ * wait (at most `polls` polls, each parking the warp for about a microsecond)
+ * gives up on every tile: the next kf_filter_bank call then makes
+ * kf_detect_blobs return KF_ETIMEOUT (no asynchronous copy is left in flight,
+ * and the context stays usable).  polls = 0 restores the normal loads and
+ * waits.  ctx NULL sets the hook of kf_responses_noalloc, which then returns
+ * KF_ETIMEOUT.  Paper: none (tests of the failure path).
+ * Errors: KF_EINVAL (polls outside 0..2^20). */
+int kf_set_wait_limit(kf_ctx *ctx, int polls);
+
 /* Autotuner: run the bank on these frames (as kf_filter_bank would, opts as
  * there) once per candidate shape (grid_mult 1, 2, 4, 0) and, for the
  * recursive banks, per segment length (64, 32); time every pass with CUDA
@@ -452,7 +463,9 @@ int kf_proposal_labels(kf_ctx *ctx, double threshold, uint8_t *labels);
  * pressure.  The caller passes the frame and the output; every intermediate
  * lives in one static device array of KF_NOALLOC_SCRATCH_MB MiB that each GPU
  * which loads the library holds until the process exits.
- *   frame      one f32 frame descriptor (device data), width <= 8192
+ *   frame      one frame descriptor (device data) of any KF_DTYPE_* (f32,
+ *              f16, bf16 or u16), each element times value_scale (0 = 1),
+ *              as for kf_filter_bank; width <= 8192
  *   scales     host array of nscales blob radii lambda (px), 1..16
  *   type       KF_IIR_REPEATED_POLE (order 2..6) or KF_IIR_BUTTERWORTH
  *              (order 1..6); the FIR bank is not offered here
@@ -463,14 +476,16 @@ int kf_proposal_labels(kf_ctx *ctx, double threshold, uint8_t *labels);
  * The frame's planes, edge rows and column carries must fit the scratch;
  * larger frames (roughly more than 4M pixel-scales) are rejected with
  * KF_EINVAL and a message naming the sizes (kf_last_error(NULL)).
- * The first call on a device looks up the device address of the scratch
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call shares the one scratch array and
- * finds the previous call's contents there: the library clears what must
- * start at zero, but calls that overlap on the GPU (e.g. on two streams)
- * race -- serialise them.  The designs are checked on the host, so the call
- * synchronises the stream once before the filter kernels are enqueued.
- * Errors: KF_EINVAL, KF_ECOND, KF_ENODEV, KF_ECUDA. */
+ * Every call looks up the device address of the scratch on the current
+ * device (cudaGetSymbolAddress; no allocation).  Every call shares the one
+ * scratch array and finds the previous call's contents there: the library
+ * clears what must start at zero, but calls that overlap on the GPU (e.g. on
+ * two streams) race -- serialise them.  The call is synchronous: it waits on
+ * the stream once after the designs (checked on the host) and once after the
+ * filter kernels (to read their status), so it cannot be called while its
+ * stream is being captured into a CUDA graph.
+ * Errors: KF_EINVAL, KF_ECOND, KF_ENODEV, KF_ECUDA, KF_ETIMEOUT (a bounded
+ * device wait gave up: the responses are incomplete). */
 int kf_responses_noalloc(const kf_frame *frame, const double *scales, int nscales, int type,
                          int order, float *responses, void *cuda_stream);
 

@@ -147,6 +147,8 @@ struct kf_ctx {
   std::vector<int> q_launches;
   std::vector<float> q_ms;
   cudaEvent_t q_ev[2] = {nullptr, nullptr};
+  // failure-detection test hook (kf_set_wait_limit): 0, normal waits
+  unsigned wait_test = 0;
 };
 
 namespace {
@@ -797,6 +799,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   a.blobs = ctx->blobs;
   a.cap = ctx->blob_cap;
   a.status = ctx->status;
+  a.wait_test = ctx->wait_test;
   if (ctx->q_chan >= 0) {  // a channel of the D = 5 bank: raw planes, no detection
     a.chan = ctx->q_chan;
     a.raw = 1;
@@ -956,6 +959,19 @@ int kf_set_launch_shape(kf_ctx *ctx, int type, int pass, int grid_mult) {
   if (ctx->grid_mult[type][pass] != grid_mult) {
     drop_graphs(ctx);  // grid sizes are part of the captured launches
     ctx->grid_mult[type][pass] = grid_mult;
+  }
+  return KF_OK;
+}
+
+int kf_set_wait_limit(kf_ctx *ctx, int polls) {
+  if (polls < 0 || polls > 1 << 20) return fail(ctx, KF_EINVAL, "kf_set_wait_limit: polls must be 0..2^20");
+  if (!ctx) {
+    kf::set_noalloc_wait_test((unsigned)polls);
+    return KF_OK;
+  }
+  if (ctx->wait_test != (unsigned)polls) {
+    drop_graphs(ctx);  // the limit is a launch argument of the captured passes
+    ctx->wait_test = (unsigned)polls;
   }
   return KF_OK;
 }

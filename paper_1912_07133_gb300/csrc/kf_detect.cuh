@@ -37,6 +37,10 @@ struct DetectArgs {
   // offsets of the candidates (d10/d01 null: no offsets), Threshold #2 limit
   const float *d10 = nullptr, *d01 = nullptr, *d20 = nullptr, *d02 = nullptr, *d11 = nullptr;
   float limit2 = 0.f;
+  // failure-detection test hook: > 0, the column pass issues no copy to its
+  // load barrier (nothing is in flight) and its bounded wait gives up after
+  // this many polls, so the call reports a timed-out wait
+  unsigned wait_test = 0;
 };
 
 constexpr int TILE_CANDS = 128;  // candidates staged per tile before one global reservation

@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(512) __maxnreg__(LC == 32 ? Rec::kColdetRegs32
     const int xv = min(max(x0 + lane, 0), W - 1);
     const int r0 = c * LC - 1;
     const long prow = F.prow;
-    if (tid == 0) {
+    if (tid == 0 && !da.wait_test) {
       fence_proxy_async();  // earlier generic accesses of the buffer before the async writes
       mbar_arrive_expect_tx(&mbar, (uint32_t)(S * NR * BW * sizeof(T)));
       for (int t = 0; t < S; ++t) {
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(512) __maxnreg__(LC == 32 ? Rec::kColdetRegs32
     const float *Ef = E + F.coff + (((long)s * nseg + c) * 2) * fs + xv;
     Rec r;
     r.load(Ef, PWb);
-    const bool ok = mbar_wait_bounded(&mbar, phase, CWAIT_LIMIT);
+    const bool ok = mbar_wait_bounded(&mbar, phase, da.wait_test ? da.wait_test : CWAIT_LIMIT);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicExch(&da.status->error, 1);
@@ -737,6 +737,7 @@ int run_iir_st(const Plan &p, const BankArgs &a, cudaStream_t st) {
   da.status = a.status;
   da.resp = nullptr;
   da.raw = a.raw;
+  da.wait_test = a.wait_test;
   using TS = typename Store<ST>::T;
   // the identity channel (the D = 5 bank, f32 planes only) has its own instance
   if (a.chan == CH_ID && ST != ST_F32) return -1;

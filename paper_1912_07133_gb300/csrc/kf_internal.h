@@ -53,6 +53,9 @@ struct BankArgs {
   int chan = CH_LAP;     // derivative channel of the row pass (CH_*)
   int raw = 0;           // 1: column passes write +sigma^2 D of the channel, no detection
   float *raw_out = nullptr;  // raw channel planes (per frame S x H x W at the frame's response offset)
+  // failure-detection test hook (kf_set_wait_limit): > 0, the column pass
+  // issues no copy to its load barrier and gives up after this many polls
+  unsigned wait_test = 0;
 };
 
 // Passes of the banks.  IIR: row (with the two edge rows per frame), column
@@ -146,6 +149,9 @@ int launch_shapes(const Blob *b, long n, const float *c20, const float *c02, con
 int launch_hpf5(const void *X, int dtype, float vs, long pitch, int W, int H, float *out, float *xpre,
                 cudaStream_t st);
 int launch_steer(const float *in, long npix, int nsets, const float *m55, float *out, cudaStream_t st);
+
+// failure-detection test hook of kf_responses_noalloc (kf_noalloc.cu)
+void set_noalloc_wait_test(unsigned polls);
 
 // candidate ordering (kf_sort.cu)
 size_t sort_workspace_bytes(long cap);

@@ -27,14 +27,15 @@ constexpr size_t kScratchBytes = (size_t)KF_NOALLOC_SCRATCH_MB << 20;
 // device address.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-void *g_addr[kMaxDevices];  // device address of g_scratch, per device (set-up)
 thread_local char g_msg[256];
+// failure-detection test hook (kf_set_wait_limit(NULL, polls)); 0: normal waits
+unsigned g_wait_test = 0;
 
 }  // namespace
 
 namespace kf {
 void set_global_error(const char *msg);
+void set_noalloc_wait_test(unsigned polls) { g_wait_test = polls; }
 }
 
 namespace {
@@ -96,16 +97,16 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
   }
   if (kf::iir_row_threads(W) == 0) return nofail(KF_EINVAL, "frame too wide for the row pass");
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return nofail(KF_ENODEV, "no usable CUDA device");
-  // set-up, once per device, with that device current
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p) return nofail(KF_ECUDA, cudaGetErrorString(e));
-    g_addr[dev] = p;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return nofail(KF_ENODEV, "no usable CUDA device");
+  // the device address of the scratch on the current device, looked up on
+  // every call (after a device reset the module, and with it the array, is
+  // loaded anew at another address; the lookup allocates nothing)
+  void *addr = nullptr;
+  {
+    const cudaError_t e = cudaGetSymbolAddress(&addr, g_scratch);
+    if (e != cudaSuccess || !addr) return nofail(KF_ECUDA, cudaGetErrorString(e));
   }
-  unsigned char *base = static_cast<unsigned char *>(g_addr[dev]);
+  unsigned char *base = static_cast<unsigned char *>(addr);
   auto *coef = reinterpret_cast<kf::Coef *>(base);
   auto *lam = reinterpret_cast<double *>(base + b_coef);
   auto *status = reinterpret_cast<kf::DevStatus *>(base + b_coef + b_lam);
@@ -181,6 +182,7 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
   a.cap = 0;
   a.status = status;
   a.prof = &prof;
+  a.wait_test = g_wait_test;
   kf::Plan plan;
   plan.fr = &d_tab->fd;
   plan.nframes = 1;
@@ -200,5 +202,16 @@ extern "C" int kf_responses_noalloc(const kf_frame *frame, const double *scales,
   const int rc = kf::launch_iir(plan, a, st);
   if (rc == -2) return nofail(KF_EINVAL, "no kernel instance for this order");
   if (rc) return nofail(KF_ECUDA, cudaGetErrorString(cudaGetLastError()));
+  // the device status: a bounded wait of the column pass that gave up leaves
+  // its tile's responses unwritten, which the caller must learn of
+  kf::DevStatus hs{};
+  if ((e = cudaMemcpyAsync(&hs, status, sizeof hs, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return nofail(KF_ECUDA, cudaGetErrorString(e));
+  if (hs.error) {
+    char m[96];
+    std::snprintf(m, sizeof m, "a device wait gave up (code %d); the responses are incomplete", hs.error);
+    return nofail(KF_ETIMEOUT, m);
+  }
   return KF_OK;
 }

@@ -55,7 +55,7 @@ ENTRY_POINTS = ("kf_bank_opts_default", "kf_create", "kf_destroy", "kf_last_erro
                 "kf_set_launch_shape", "kf_set_segment_length", "kf_autotune",
                 "kf_proposal_set_weights", "kf_proposal_get_weights", "kf_proposal_pool", "kf_proposal_logits",
                 "kf_proposal_grad", "kf_proposal_train_step", "kf_proposal_labels", "kf_blob_shapes",
-                "kf_quartic_bank", "kf_quartic_steer")
+                "kf_quartic_bank", "kf_quartic_steer", "kf_set_wait_limit")
 KF_QUARTIC_CHANNELS = 15
 # (dx, dy) of the D = 5 bank's channels: total order n = 0..4, within it dy = 0..n
 QUARTIC_CHANNELS = tuple((n - dy, dy) for n in range(5) for dy in range(n + 1))
@@ -161,6 +161,8 @@ def load(path: str = LIB_PATH):
     L.kf_proposal_train_step.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.c_float, ctypes.c_float, fp]
     L.kf_proposal_labels.restype = i32
     L.kf_proposal_labels.argtypes = [vp, dbl, vp]
+    L.kf_set_wait_limit.restype = i32
+    L.kf_set_wait_limit.argtypes = [vp, i32]
     L.kf_set_segment_length.restype = i32
     L.kf_set_segment_length.argtypes = [vp, i32, i32]
     L.kf_quartic_bank.restype = i32
@@ -385,6 +387,13 @@ def kf_set_launch_shape(ctx: int, ftype: int, pass_: int, grid_mult: int) -> Non
     """Launch shape of one pass (0: one block per work item; k: k x the
     resident blocks of the GPU, looping over items)."""
     _check(load().kf_set_launch_shape(ctx, ftype, pass_, grid_mult), ctx)
+
+
+def kf_set_wait_limit(ctx, polls: int) -> None:
+    """Failure-detection test hook: polls > 0 makes the column pass's bounded
+    load wait give up (no copy issued); 0 restores normal waits.  ctx None:
+    the hook of kf_responses_noalloc."""
+    _check(load().kf_set_wait_limit(ctx, int(polls)), ctx)
 
 
 def kf_set_segment_length(ctx: int, ftype: int, rows: int) -> None:

@@ -71,3 +71,57 @@ def test_peaks_follow_the_measured_file():
     else:
         assert (hbm, src) == (6800.0, "fallback")
         assert math.isclose(tf32, 1700.0 * 1.1 / 2.25)
+
+
+def test_method_work_counted_once_on_the_tensor_pass():
+    """The tensor-core FIR column pass is credited with the method's
+    2(2K + 1) flop per output and scale, not the three TF32 products that
+    emulate each FP32 product: 17.05 GFLOP in 0.5488 ms is 31.1 TFLOP/s."""
+    taps = bench.fir_taps(SIX)
+    _, flops = bench.algorithmic("fir_coldet", 6, HW, taps)
+    r = bench.roofline_of("fir_coldet", 0.5488 * 20, 20, 4.0 * 6 * HW * 20, flops * 20, 6792.1, "measured",
+                          152, 2070.0, None)
+    assert r["bound"] == "tensor" and r["tf32_products_per_tap"] == 3
+    assert abs(r["achieved"] - 31.07) < 0.05
+    tp, _ = bench.tf32_peak()
+    assert abs(r["frac"] - r["achieved"] / tp) < 1e-4
+    # the FP32 row pass against the ALU peak of the device's SM count
+    r2 = bench.roofline_of("fir_row", 0.4272, 1, 4.0 * HW * 7, flops, 6792.1, "measured", 152, 2070.0, None)
+    assert r2["bound"] == "alu" and abs(r2["peak"] - 80.6) < 0.1
+    assert abs(r2["achieved"] - flops / 0.4272e-3 / 1e12) < 1e-3
+    assert "hbm_frac" in r2
+
+
+def test_alu_peak_follows_the_sm_count():
+    assert abs(bench.alu_peak(152, 2070.0) - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+    assert abs(bench.alu_peak(148, 1965.0) / bench.alu_peak(152, 1965.0) - 148 / 152) < 1e-12
+
+
+def test_bank_bytes_per_pixel_scale():
+    """2 s_b + s_in / S per pixel-scale: 8.667 B at f32 with S = 6, 4.25 B at
+    f16 planes and u16 input with S = 8."""
+    assert abs(bench.bank_bytes(6, HW, 4.0, 4.0) / (6 * HW) - (8.0 + 4.0 / 6)) < 1e-12
+    assert abs(bench.bank_bytes(8, HW, 2.0, 2.0) / (8 * HW) - 4.25) < 1e-12
+
+
+def test_hbm_roofline_of_a_plane_pass():
+    """A pass with bytes and no flops is HBM-bound: achieved GB/s over the
+    measured copy peak."""
+    r = bench.roofline_of("iir_coldet", 0.3036, 1, 4.0 * 6 * HW, 0.0, 6792.1, "measured", 152, 2070.0, 457.5e6)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 4.0 * 6 * HW / 0.3036e-3 / 1e9) < 0.1
+    assert r["traffic"] == 457.5e6
+
+
+def test_traffic_needs_a_capture_of_the_current_sources(tmp_path, monkeypatch):
+    """A stored ncu traffic figure is reported only while the kernel sources
+    still have the digest of the capture."""
+    (tmp_path / "a.cu").write_text("kernel A")
+    monkeypatch.setattr(bench, "CSRC", str(tmp_path))
+    d = bench.csrc_digest()
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", {("w", "k", "f32"): (123.0, d)})
+    assert bench.traffic_of("w", "k", "f32") == 123.0
+    assert bench.traffic_of("w", "other", "f32") is None
+    (tmp_path / "a.cu").write_text("kernel A, changed")
+    assert bench.csrc_digest() != d
+    assert bench.traffic_of("w", "k", "f32") is None

@@ -772,16 +772,27 @@ def nearest(b, centres):
     return min((math.hypot(b["y"] - cy, b["x"] - cx), a, r) for cy, cx, a, r in centres)
 
 
-def test_fig6_each_scale_detects_the_centres_of_its_matched_ellipses():
+# Threshold #1 per blur: the figures print none.  Each blur's normalised
+# determinant at a matched ellipse's centre has its own level (D 0.037-0.055,
+# C 0.134-0.226, E 0.071-0.102 on this pattern), and one value per blur
+# separates it from every other maximum at all five scales.
+FIG6 = {"D": (O.IIR_REPEATED_POLE, 3, 0.035), "C": (O.FIR_COLORED_SG, 1, 0.132),
+        "E": (O.IIR_BUTTERWORTH, 2, 0.066)}
+
+
+@pytest.mark.parametrize("blur", ["D", "C", "E"])
+def test_fig6_each_scale_detects_the_centres_of_its_matched_ellipses(blur):
     """Axis ratio 2, axes 4..64 px, rotations 0..45 deg; Filter D (Table IV),
-    lambda = 4..64 one at a time: every detection lies at the centre of an
-    ellipse whose semi-major axis equals lambda, and all four rotations are
-    found, with one threshold for all scales."""
+    C (colored SG, L_D = 1, K = ceil(5 sigma) up to 160) or E (Butterworth,
+    L_B = 4), lambda = 4..64 one at a time: every detection lies at the
+    centre of an ellipse whose semi-major axis equals lambda, and all four
+    rotations are found, with one threshold for all scales."""
     from paper_1912_07133_gb300 import synthetic as SYN
+    ft, order, T = FIG6[blur]
     img, centres = SYN.ellipse_pattern(2.0)
     for lam in (4, 8, 16, 32, 64):
-        R = O.bank(img.astype(np.float64), [float(lam)], O.IIR_REPEATED_POLE, 3, O.RESP_HESSIAN)
-        b = O.detect(R, 0.035, O.RESP_HESSIAN, O.NEIGH_ALL)
+        R = O.bank(img.astype(np.float64), [float(lam)], ft, order, O.RESP_HESSIAN, fir_kmax=160)
+        b = O.detect(R, T, O.RESP_HESSIAN, O.NEIGH_ALL)
         near = [nearest(r, centres) for r in b]
         assert all(a == lam and d <= 0.05 * lam + 1.0 for d, a, _ in near), (lam, near)
         assert sorted(r for _, _, r in near) == [0, 15, 30, 45], lam
