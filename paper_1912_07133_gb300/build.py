@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libkf.so")
-SOURCES = ["kf_api.cu", "kf_design.cu", "kf_iir.cu", "kf_iir_d.cu", "kf_iir_e.cu", "kf_fir.cu", "kf_sort.cu",
+SOURCES = ["kf_api.cu", "kf_design.cu", "kf_iir.cu", "kf_iir_d.cu", "kf_iir_e.cu", "kf_fir.cu", "kf_fir_tc.cu",
+           "kf_sort.cu",
            "kf_noalloc.cu", "kf_proposal.cu", "kf_deriv.cu", "kf_quartic.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

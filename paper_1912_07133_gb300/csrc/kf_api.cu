@@ -40,6 +40,11 @@ struct kf_ctx {
     kf::Coef *d_coef = nullptr;
     std::vector<kf::Coef> h_coef;
     unsigned long long used = 0;
+    // FIR designs: the taps as band operands of the tensor-core column pass
+    float *d_bands = nullptr;
+    size_t bands_floats = 0;
+    kf::TcGeom tc;
+    bool tc_ok = false;
   };
   std::vector<Design> designs;
   unsigned long long tick = 0;
@@ -300,6 +305,27 @@ int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S,
     if (!(std::fabs(c.dc_gain - 1.0) < 1e-6))
       return fail(ctx, KF_ECOND, "design for scale %g has dc gain %.9g", scales[s], c.dc_gain);
   }
+  // FIR designs of at most 8 scales: the band operands of the tensor-core
+  // column pass (R_L = -sigma^2 (...): the taps carry the sign)
+  slot->tc_ok = false;
+  if ((type == KF_FIR_COLORED_SG || type == KF_FIR_GAUSSIAN) && S <= kf::TC_MAXS) {
+    int Ks[kf::TC_MAXS];
+    for (int s = 0; s < S; ++s) Ks[s] = slot->h_coef[s].K;
+    const long nf = kf::tc_geometry(Ks, S, &slot->tc);
+    if (nf > 0) {
+      if ((size_t)nf > slot->bands_floats) {
+        if (slot->d_bands) cudaFree(slot->d_bands);
+        slot->d_bands = nullptr;
+        slot->bands_floats = 0;
+        if ((e = cudaMalloc(&slot->d_bands, (size_t)nf * sizeof(float))) != cudaSuccess)
+          return cuda_fail(ctx, e, "cudaMalloc(tap bands)");
+        slot->bands_floats = (size_t)nf;
+      }
+      if (kf::launch_tc_bands(slot->d_coef, slot->tc, -1.f, slot->d_bands, ctx->stream))
+        return cuda_fail(ctx, cudaGetLastError(), "tap band launch");
+      slot->tc_ok = true;
+    }
+  }
   slot->type = type;
   slot->order = order;
   slot->ld = ld;
@@ -445,7 +471,7 @@ void kf_destroy(kf_ctx *ctx) {
   cudaFree(ctx->P);
   cudaFree(ctx->edge);
   cudaFree(ctx->carry);
-  for (auto &d : ctx->designs) cudaFree(d.d_coef);
+  for (auto &d : ctx->designs) cudaFree(d.d_coef), cudaFree(d.d_bands);
   cudaFree(ctx->sorted);
   cudaFree(ctx->sort_work);
   cudaFree(ctx->d_npass);
@@ -494,7 +520,7 @@ int kf_design(int type, int order, double scale, kf_coeffs *out) {
   rc = ensure_design(&tmp, type, order, &scale, 1, 96);
   kf::Coef c{};
   if (!rc) c = tmp.cur->h_coef[0];
-  for (auto &d : tmp.designs) cudaFree(d.d_coef);
+  for (auto &d : tmp.designs) cudaFree(d.d_coef), cudaFree(d.d_bands);
   cudaFree(tmp.lambdas);
   cudaFree(tmp.dwork);
   if (rc) return fail(nullptr, rc, "%s", tmp.err.c_str());
@@ -594,6 +620,14 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   }
   const bool iir = !is_fir(type);
   const int nfs = (type == KF_IIR_BUTTERWORTH) ? 2 * nstate : nstate;  // states per recursion
+  // the FIR column pass on the tensor cores (f32 planes, all-scales
+  // neighbourhood, <= 8 scales, detection); the other calls take the
+  // mma.sync and FP32 passes
+  long rows_all = 0;
+  for (int f = 0; f < nframes; ++f) rows_all += (long)nscales * frames[f].height;
+  const bool tcpass = !iir && ctx->cur->tc_ok &&
+                      kf::fir_tc_applies(nscales, opts.storage, opts.neighbourhood, dbank || ctx->q_chan >= 0,
+                                         maxPW, rows_all);
   // ---- layout: every frame resident in one plane row space of pitch PWb ----
   const long PWb = maxPW;
   std::vector<kf::FrameDev> fd(nframes);
@@ -652,7 +686,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   auto items = [&](int pass, int f) {
     if (pass == PASS_COMB) return kf::deriv_items(fd[f].H, fd[f].W);
     return iir ? kf::iir_items(pass, fd[f].H, fd[f].W, nscales, ctx->seg_len[type])
-               : kf::fir_items(pass, fd[f].H, fd[f].W, nscales, opts.neighbourhood);
+               : kf::fir_items(pass, fd[f].H, fd[f].W, nscales, opts.neighbourhood, tcpass);
   };
   auto add = [&](int pass, const std::vector<int> &fl, int nt) {
     L l{pass, nt, (int)fl.size(), 0, pool.size(), 0};
@@ -775,7 +809,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     if ((ee = cudaMemsetAsync(ctx->g_count, 0, 2 * sizeof(int), st)) != cudaSuccess)
       return cuda_fail(ctx, ee, "gate counts");
     const int rows = iir ? ctx->seg_len[type] : kf::fir_tile_rows(opts.neighbourhood);
-    if (kf::gate_select_tiles(plan.fr, full_det, ctx->g_act, TW_COL, rows, ctx->g_sel[0], ctx->g_count, st))
+    if (kf::gate_select_tiles(plan.fr, full_det, ctx->g_act, tcpass ? kf::fir_tc_tile_cols() : TW_COL, rows,
+                              ctx->g_sel[0], ctx->g_count, st))
       return cuda_fail(ctx, cudaGetLastError(), "gate selection");
     if (!iir && kf::gate_select_rows(plan.fr, full_row, ctx->g_act, kf::fir_row_segment(), kf::fir_row_rows(),
                                      kf::fir_halo(kmax) + rows + 4,
@@ -800,6 +835,10 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   a.cap = ctx->blob_cap;
   a.status = ctx->status;
   a.wait_test = ctx->wait_test;
+  if (tcpass) {
+    a.tc_bands = ctx->cur->d_bands;
+    a.tc = ctx->cur->tc;
+  }
   if (ctx->q_chan >= 0) {  // a channel of the D = 5 bank: raw planes, no detection
     a.chan = ctx->q_chan;
     a.raw = 1;

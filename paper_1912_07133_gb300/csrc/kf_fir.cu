@@ -792,8 +792,9 @@ int fir_row_rows() { return 1; }
 int fir_tile_rows(int neigh) { return neigh == 0 ? CROWS2 - 2 : CROWS - 2; }
 int fir_halo(int kmax) { return kmax + TB + 1; }
 
-int fir_items(int pass, int H, int W, int S, int neigh) {
-  const int ntx = (W + TW - 1) / TW;
+int fir_items(int pass, int H, int W, int S, int neigh, bool tc) {
+  const int tw = tc ? fir_tc_tile_cols() : TW;
+  const int ntx = (W + tw - 1) / tw;
   switch (pass) {
     case PASS_ROW: return ((W + RSEG - 1) / RSEG) * (H + 2);
     case PASS_DET: return neigh == 0 ? ntx * ((H + CROWS2 - 3) / (CROWS2 - 2)) : ntx * ((H + CROWS - 3) / (CROWS - 2));
@@ -834,6 +835,7 @@ int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st) {
     a.prof->end(st);
   };
   auto det = [&](const Launch &l) -> int {
+    if (a.tc_bands) return launch_colfir_tc(p, l, a, da, st);  // the tensor-core (tcgen05) pass
     if (a.neigh == 0) {
       switch (a.storage) {
         case ST_F32: return launch_colfir_tma<ST_F32>(p, l, a, da, G, KP, st);

@@ -35,6 +35,20 @@ struct Prof {
   }
 };
 
+// Tensor-core FIR column pass (kf_fir_tc.cu): per scale (<= 8) the taps as a
+// banded Toeplitz operand for MMAs of 128 output rows; K half-length, Kp = K
+// rounded up to 4, Kd = 128 + 2 Kp input rows, G band chunks of 128 bytes
+// (per hi and lo part), boff the float offset of the scale's hi band in the
+// band buffer (its lo band follows G x 32 floats later).
+constexpr int TC_MAXS = 8;
+struct TcGeom {
+  int S = 0;
+  int K[TC_MAXS] = {}, Kp[TC_MAXS] = {}, Kd[TC_MAXS] = {}, G[TC_MAXS] = {};
+  long boff[TC_MAXS] = {};
+  int gmax = 0;
+  long floats = 0;
+};
+
 struct BankArgs {
   const Coef *coef;      // device, S entries
   int S;
@@ -56,6 +70,10 @@ struct BankArgs {
   // failure-detection test hook (kf_set_wait_limit): > 0, the column pass
   // issues no copy to its load barrier and gives up after this many polls
   unsigned wait_test = 0;
+  // tensor-core FIR column pass: the design's taps as band operands (device)
+  // and their geometry; null: the pass does not apply to this call
+  const float *tc_bands = nullptr;
+  TcGeom tc;
 };
 
 // Passes of the banks.  IIR: row (with the two edge rows per frame), column
@@ -86,7 +104,17 @@ struct Plan {
 // work items of one frame in a pass (the kernels' decomposition)
 int iir_items(int pass, int H, int W, int S, int lc);
 int iir_row_threads(int W);    // threads per block of the IIR row pass (0: too wide)
-int fir_items(int pass, int H, int W, int S, int neigh);
+int fir_items(int pass, int H, int W, int S, int neigh, bool tc = false);
+// tensor-core FIR column pass (kf_fir_tc.cu): whether it serves a call (f32
+// planes, all-scales neighbourhood, <= 8 scales, detection, a plane row
+// space of at least 68 x 32 elements), its tiles' interior width, the band geometry of a design (floats of the band buffer,
+// -1 if it does not apply), the band builder and the launch
+bool fir_tc_applies(int S, int storage, int neigh, int raw, long PWb, long prows);
+int fir_tc_tile_cols();
+long tc_geometry(const int *K, int S, TcGeom *g);
+int launch_tc_bands(const Coef *d_coef, const TcGeom &g, float sgn, float *d_bands, cudaStream_t st);
+int launch_colfir_tc(const Plan &p, const Launch &l, const BankArgs &a, const struct DetectArgs &da,
+                     cudaStream_t st);
 int iir_segments(int H, int lc);  // IIR column segments of a frame (segment length lc)
 
 int launch_iir(const Plan &p, const BankArgs &a, cudaStream_t st);
