@@ -73,6 +73,9 @@ extern "C" {
                                or graph replay (calls run eagerly).          */
 
 #define KF_BOUNDARY_HOLD 0 /* frame edges held to +-infinity (Appendix, A32)     */
+#define KF_BOUNDARY_ZERO 1 /* frame extended by zeros (the FIR initialisation
+                              of Sec. 5); FIR blurs (Filters A, C) with the
+                              Laplacian response and no offset limit only    */
 
 #define KF_GATE_OFF 0        /* no proposal gating                               */
 #define KF_GATE_DILATED 1    /* marked tiles and their 8 neighbours              */
@@ -123,7 +126,8 @@ typedef struct {
 /* Options of one filter-bank call. */
 typedef struct {
   int32_t response;      /* KF_RESP_*                                          */
-  int32_t boundary;      /* KF_BOUNDARY_HOLD (only hold is implemented)        */
+  int32_t boundary;      /* KF_BOUNDARY_HOLD, or KF_BOUNDARY_ZERO for the FIR
+                            blurs with the Laplacian response               */
   int32_t neighbourhood; /* KF_NEIGH_*                                         */
   int32_t storage;       /* element type of the one-sided planes between the
                             row and column passes: KF_DTYPE_F32 / F16 / BF16.

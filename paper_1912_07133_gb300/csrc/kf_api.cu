@@ -390,7 +390,7 @@ int upload_table(kf_ctx *ctx, const void *bytes, size_t n) {
 std::vector<long long> call_key(const kf_ctx *ctx, const kf_frame *frames, int nframes, const double *scales, int S,
                                 int type, int order, int kmax, const kf_bank_opts &o) {
   std::vector<long long> k = {type, order, kmax, S, o.storage, o.neighbourhood, o.schedule, nframes,
-                              (long long)(intptr_t)ctx->cur, o.gate};
+                              (long long)(intptr_t)ctx->cur, o.gate, o.boundary};
   if (o.gate) {
     long long gt;
     double g = o.gate_threshold;
@@ -571,7 +571,12 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   const bool dbank = opts.response == KF_RESP_HESSIAN || opts.offset_limit > 0.f;
   if (dbank && opts.gate != KF_GATE_OFF)
     return fail(ctx, KF_EINVAL, "gating runs with the Laplacian response and no offset limit");
-  if (opts.boundary != KF_BOUNDARY_HOLD) return fail(ctx, KF_EINVAL, "only the hold boundary is implemented");
+  if (opts.boundary != KF_BOUNDARY_HOLD && opts.boundary != KF_BOUNDARY_ZERO)
+    return fail(ctx, KF_EINVAL, "unknown boundary %d", opts.boundary);
+  if (opts.boundary == KF_BOUNDARY_ZERO && (!is_fir(type) || dbank || ctx->q_chan >= 0))
+    return fail(ctx, KF_EINVAL,
+                "the zero boundary applies to the FIR blurs (Filters A and C) with the Laplacian response and "
+                "no offset limit");
   if (opts.neighbourhood != KF_NEIGH_ALL_SCALES && opts.neighbourhood != KF_NEIGH_ADJACENT)
     return fail(ctx, KF_EINVAL, "unknown neighbourhood %d", opts.neighbourhood);
   if (opts.storage != KF_DTYPE_F32 && opts.storage != KF_DTYPE_F16 && opts.storage != KF_DTYPE_BF16)
@@ -835,6 +840,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   a.cap = ctx->blob_cap;
   a.status = ctx->status;
   a.wait_test = ctx->wait_test;
+  a.zero = opts.boundary == KF_BOUNDARY_ZERO;
   if (tcpass) {
     a.tc_bands = ctx->cur->d_bands;
     a.tc = ctx->cur->tc;

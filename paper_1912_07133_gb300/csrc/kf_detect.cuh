@@ -41,7 +41,16 @@ struct DetectArgs {
   // load barrier (nothing is in flight) and its bounded wait gives up after
   // this many polls, so the call reports a timed-out wait
   unsigned wait_test = 0;
+  int zero = 0;  // FIR column passes: the zero boundary (rows -1 and H from the edge rows, zero beyond)
 };
+
+// Input of a column pass at frame row y outside [0, H): the held one-sided
+// edge rows (top, bot) for the hold boundary; for the zero boundary those
+// rows one row beyond the frame and zero further out.
+__device__ __forceinline__ float col_outside(int y, int H, float top, float bot, int zero) {
+  if (y < 0) return (zero && y < -1) ? 0.f : top;
+  return (zero && y > H) ? 0.f : bot;
+}
 
 constexpr int TILE_CANDS = 128;  // candidates staged per tile before one global reservation
 

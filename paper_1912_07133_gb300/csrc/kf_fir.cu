@@ -182,7 +182,7 @@ __host__ __device__ __forceinline__ int row_halo(int kmax) { return (kmax + TB +
 __global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr, Items it,
                                                 const Coef *__restrict__ coef, int S, int kmax,
                                                 void *__restrict__ P, int st, long PWb, float *__restrict__ edge,
-                                                DevStatus *__restrict__ status, int chan) {
+                                                DevStatus *__restrict__ status, int chan, int zero) {
   extern __shared__ __align__(16) float sm[];
   const int tid = threadIdx.x;
   // L on [xs - G, xs + RSEG + G): the 8-tap blocks read up to TB elements past
@@ -222,6 +222,34 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr,
         for (int j = tid; j < n; j += RNT) {
           const int e = xs - G + j;
           sL[pad20(j)] = e < -1 ? xp.x : (e == -1 ? xp.y : (e < W ? ld(r0, e) : (e == W ? xp.z : xp.w)));
+        }
+        return;
+      }
+      if (zero) {
+        // zero boundary (fused Laplacian): the frame extended by zeros, so U
+        // and V take zero neighbours beyond the edges and L is X(0) and
+        // X(W - 1) one pixel beyond the row ends and zero further out; the
+        // edge items carry the first / last input row itself (the Laplacian
+        // one row beyond the frame), zero beyond its ends
+        auto ldz = [&](const decltype(Xt) row, int e, bool rowin) {
+          return (rowin && e >= 0 && e < W) ? ld(row, e) : 0.f;
+        };
+        const bool hm = y - 1 >= 0, hp = y + 1 < H;
+        for (int j = tid; j < n; j += RNT) {
+          const int e = xs - G + j;
+          float v;
+          if (EDGE) {
+            v = ldz(r0, e, true);
+          } else if (e < -1 || e > W) {
+            v = 0.f;
+          } else if (e == -1 || e == W) {
+            v = ld(r0, e < 0 ? 0 : W - 1);
+          } else {
+            const float c0 = ld(r0, e);
+            v = (ldz(r0, e + 1, true) - 2.f * c0 + ldz(r0, e - 1, true)) +
+                (ldz(rp, e, hp) - 2.f * c0 + ldz(rm, e, hm));
+          }
+          sL[pad20(j)] = v;
         }
         return;
       }
@@ -332,6 +360,7 @@ __global__ void __launch_bounds__(CNT) k_colfir(const FrameDev *__restrict__ fr,
   extern __shared__ float sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int G = kmax + TB;
+  const int zero = da.zero;
   const int NIN = CROWS + 2 * G;
   float *in = sm;                               // [NIN][32]
   float *buf = sm + (long)NIN * 32;             // [S][CROWS][32]
@@ -363,7 +392,8 @@ __global__ void __launch_bounds__(CNT) k_colfir(const FrameDev *__restrict__ fr,
       // in[j] = input row r0 - G + j
       for (int j = warp; j < NIN; j += CNT / 32) {
         const int r = r0 - G + j;
-        in[j * 32 + lane] = r < 0 ? top : (r >= H ? bot : load_plane(P, pc + (long)r * PWb, st));
+        in[j * 32 + lane] =
+            (r < 0 || r >= H) ? col_outside(r, H, top, bot, zero) : load_plane(P, pc + (long)r * PWb, st);
       }
       __syncthreads();
       const float *col = in + lane + (G + NOUT * warp) * 32;  // output row NOUT*warp
@@ -563,8 +593,7 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
         if (outside) {  // rows outside the frame: held values (uniform over the block)
           for (int j = warp; j < nin; j += CNT2 / 32) {
             const int r = r0 - G + j;
-            if (r < 0) stg[j * BOXW + off + lane] = top;
-            else if (r >= H) stg[j * BOXW + off + lane] = bot;
+            if (r < 0 || r >= H) stg[j * BOXW + off + lane] = col_outside(r, H, top, bot, da.zero);
           }
           fence_proxy_async();  // before the stage's next async copy
           __syncthreads();
@@ -575,7 +604,8 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
         for (int j = warp; j < nin; j += CNT2 / 32) {
           const int r = r0 - G + j;
           const float v = Store<ST>::ld(src[j * BW]);
-          work[j * 32 + (lane ^ (8 * (j & 3)))] = r < 0 ? top : (r >= H ? bot : v);  // XOR-swizzled rows
+          work[j * 32 + (lane ^ (8 * (j & 3)))] =
+              (r < 0 || r >= H) ? col_outside(r, H, top, bot, da.zero) : v;  // XOR-swizzled rows
         }
         tile = work;
         __syncthreads();  // landing stage b is free again
@@ -823,6 +853,8 @@ int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st) {
   da.status = a.status;
   da.resp = nullptr;
   da.raw = a.raw;
+  da.wait_test = a.wait_test;
+  da.zero = a.zero;
   // in + buf + detector scratch (2 float planes + 2 byte planes) + taps (adjacent neighbourhood)
   const size_t csm = ((size_t)(CROWS + 2 * G) * 32 + (size_t)a.S * CROWS * 32 + (size_t)CROWS * 32 * 2 +
                       (size_t)CROWS * 32 * 2 / 4 + KP + 1) * sizeof(float);
@@ -831,7 +863,7 @@ int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st) {
     const int nb = persistent_blocks((const void *)k_rowfir, RNT, rsm, l.it.total, p.mult[PASS_ROW]);
     a.prof->begin("fir_row", st);
     k_rowfir<<<nb, RNT, rsm, st>>>(p.fr, l.it, a.coef, a.S, kmax, a.P, a.storage, p.PWb, a.edge, a.status,
-                                   a.chan);
+                                   a.chan, a.zero);
     a.prof->end(st);
   };
   auto det = [&](const Launch &l) -> int {

@@ -29,15 +29,17 @@
 // interior 62 x 126), warp-specialised:
 //   warp 0      TMA producer: per scale the band pair (bulk copy, two slots)
 //               and the 32-row chunks of the one-sided plane (2-D tensor
-//               copies of 68 x 32 floats, two landing slots);
+//               copies of 68 x 32 floats into a ring of 8-12 landing slots,
+//               as many as the shared memory holds: the chunks in flight
+//               cover the copy latency);
 //   warp 1      tensor-memory allocation and the MMA issue (one thread): per
 //               chunk 4 k-steps x 3 products of M = 128, N = 64, K = 8;
 //   warps 2-5   split each landed chunk into the B operands (raw and low
 //               parts, transposed into core matrices, held rows substituted
-//               at the frame's top and bottom), then the epilogue: all scales
-//               of the tile out of tensor memory (per-pixel extremes over the
-//               scales, optional responses), the 3 x 3 spatial test and the
-//               candidate list.
+//               at the frame's top and bottom), then the epilogue in two
+//               passes (bright, then dark blobs): the per-pixel extreme over
+//               all scales out of tensor memory (and the optional responses),
+//               the 3 x 3 spatial test, and the tile's candidate list.
 // Every wait is bounded; a wait that gives up sets the call's error status
 // and the CTA stops taking tiles (copies in flight are awaited, with a
 // bound, before the tensor memory is released).
@@ -151,50 +153,43 @@ __device__ __forceinline__ bool tc_beats(const float *m, const unsigned char *am
   return ok;
 }
 
-// The spatial 3 x 3 test over the per-pixel extremes of a 128 x 64 tile (rows
-// 0 and 127, columns 0 and 63 halo) by the 128 epilogue threads: each warp
+// The spatial 3 x 3 test of one polarity over a 128 x 64 tile (rows 0 and
+// 127, columns 0 and 63 halo) by the 128 epilogue threads.  ext holds pol x
+// the per-pixel extreme over the scales (-inf outside the frame), aext the
+// first scale attaining it, so a candidate is a value above the threshold
+// that beats its 8 neighbours with the tie rule (strictly an earlier
+// neighbour in (scale, y, x) order, non-strictly a later one).  Each warp
 // walks a band of rows, each lane two columns (lane, lane + 32), with the
-// horizontal 3-maxima (3-minima) of three rows in registers; candidates are
-// staged in the tile list and reserved globally once per tile.
-__device__ void tc_detect(const float *mx, const float *mn, const unsigned char *amx, const unsigned char *amn,
-                          const DetectArgs &a, int ew, int lane) {
+// horizontal 3-maxima of three rows in registers; candidates are staged in
+// the tile list.
+__device__ void tc_detect(const float *ext, const unsigned char *aext, int pol, const DetectArgs &a, int ew,
+                          int lane) {
   TileList &tl = g_tl;
-  unsigned long long &s_base = g_tl_base;
-  if (ew == 0 && lane == 0) tl.n = 0;
-  epi_sync();
   constexpr unsigned FULL = 0xffffffffu;
   const int ib = 1 + 32 * ew, ie = min(TC_M - 1, ib + 32);
-  // neighbours left and right of the two columns
-  auto sides = [&](float v0, float v1, bool mxm, float &s0, float &s1) {
+  // maximum of the left and right neighbours of the two columns
+  auto sides = [&](float v0, float v1, float &s0, float &s1) {
     const float u0 = __shfl_up_sync(FULL, v0, 1), d0 = __shfl_down_sync(FULL, v0, 1);
     const float u1 = __shfl_up_sync(FULL, v1, 1), d1 = __shfl_down_sync(FULL, v1, 1);
     const float b1 = __shfl_sync(FULL, v1, 0), e0 = __shfl_sync(FULL, v0, 31);
-    const float ninf = mxm ? -CUDART_INF_F : CUDART_INF_F;
-    const float l0 = lane == 0 ? ninf : u0, r0 = lane == 31 ? b1 : d0;
-    const float l1 = lane == 0 ? e0 : u1, r1 = lane == 31 ? ninf : d1;
-    s0 = mxm ? fmaxf(l0, r0) : fminf(l0, r0);
-    s1 = mxm ? fmaxf(l1, r1) : fminf(l1, r1);
+    const float l0 = lane == 0 ? -CUDART_INF_F : u0, r0 = lane == 31 ? b1 : d0;
+    const float l1 = lane == 0 ? e0 : u1, r1 = lane == 31 ? -CUDART_INF_F : d1;
+    s0 = fmaxf(l0, r0);
+    s1 = fmaxf(l1, r1);
   };
-  float xa0, xa1, na0, na1, vc0, vc1, wc0, wc1, lx0, lx1, ln0, ln1;
+  float xa0, xa1, vc0, vc1, lx0, lx1;
   {
-    const float p0 = mx[(ib - 1) * XS + lane], p1 = mx[(ib - 1) * XS + lane + 32];
-    const float q0 = mn[(ib - 1) * XS + lane], q1 = mn[(ib - 1) * XS + lane + 32];
+    const float p0 = ext[(ib - 1) * XS + lane], p1 = ext[(ib - 1) * XS + lane + 32];
     float s0, s1;
-    sides(p0, p1, true, s0, s1);
-    xa0 = fmaxf(p0, s0), xa1 = fmaxf(p1, s1);
-    sides(q0, q1, false, s0, s1);
-    na0 = fminf(q0, s0), na1 = fminf(q1, s1);
-    vc0 = mx[ib * XS + lane], vc1 = mx[ib * XS + lane + 32];
-    wc0 = mn[ib * XS + lane], wc1 = mn[ib * XS + lane + 32];
-    sides(vc0, vc1, true, lx0, lx1);
-    sides(wc0, wc1, false, ln0, ln1);
+    sides(p0, p1, s0, s1);
+    xa0 = fmaxf(p0, s0), xa1 = fmaxf(p1, s1);  // row i - 1: 3-maxima
+    vc0 = ext[ib * XS + lane], vc1 = ext[ib * XS + lane + 32];
+    sides(vc0, vc1, lx0, lx1);                 // row i: the two side neighbours
   }
   for (int i = ib; i < ie; ++i) {
-    const float vn0 = mx[(i + 1) * XS + lane], vn1 = mx[(i + 1) * XS + lane + 32];
-    const float wn0 = mn[(i + 1) * XS + lane], wn1 = mn[(i + 1) * XS + lane + 32];
-    float lxn0, lxn1, lnn0, lnn1;
-    sides(vn0, vn1, true, lxn0, lxn1);
-    sides(wn0, wn1, false, lnn0, lnn1);
+    const float vn0 = ext[(i + 1) * XS + lane], vn1 = ext[(i + 1) * XS + lane + 32];
+    float lxn0, lxn1;
+    sides(vn0, vn1, lxn0, lxn1);
     const int y = a.r0 + i;
     if (y >= 0 && y < a.H) {
 #pragma unroll
@@ -202,27 +197,25 @@ __device__ void tc_detect(const float *mx, const float *mn, const unsigned char 
         const int c = lane + 32 * hh;
         const int x = a.x0 + c;
         if (c < 1 || c > TC_N - 2 || x < 0 || x >= a.W) continue;
-        const float vc = hh ? vc1 : vc0, wc = hh ? wc1 : wc0;
+        const float vc = hh ? vc1 : vc0;
         // maximum of the 8 neighbours: row i - 1 (3 columns), row i (2), row i + 1 (3)
         const float m8 = fmaxf(hh ? xa1 : xa0, fmaxf(hh ? lx1 : lx0, fmaxf(hh ? vn1 : vn0, hh ? lxn1 : lxn0)));
         if (vc > a.thr && vc >= m8) {
-          const int s = amx[i * XB + c];
-          if (vc > m8 || tc_beats(mx, amx, i, c, 1, vc, s)) emit_blob(a, tl, s, y, x, 1, vc);
-        }
-        const float n8 = fminf(hh ? na1 : na0, fminf(hh ? ln1 : ln0, fminf(hh ? wn1 : wn0, hh ? lnn1 : lnn0)));
-        if (a.dark && -wc > a.thr && wc <= n8) {
-          const int s = amn[i * XB + c];
-          if (wc < n8 || tc_beats(mn, amn, i, c, -1, wc, s)) emit_blob(a, tl, s, y, x, -1, wc);
+          const int s = aext[i * XB + c];
+          if (vc > m8 || tc_beats(ext, aext, i, c, 1, vc, s)) emit_blob(a, tl, s, y, x, pol, pol * vc);
         }
       }
     }
     xa0 = fmaxf(vc0, lx0), xa1 = fmaxf(vc1, lx1);
-    na0 = fminf(wc0, ln0), na1 = fminf(wc1, ln1);
-    vc0 = vn0, vc1 = vn1, wc0 = wn0, wc1 = wn1;
-    lx0 = lxn0, lx1 = lxn1, ln0 = lnn0, ln1 = lnn1;
+    vc0 = vn0, vc1 = vn1, lx0 = lxn0, lx1 = lxn1;
   }
+}
+
+// the tile list's candidates to the call's list (one global reservation)
+__device__ void tc_flush(const DetectArgs &a, int t) {
+  TileList &tl = g_tl;
+  unsigned long long &s_base = g_tl_base;
   epi_sync();
-  const int t = 32 * ew + lane;
   const int nloc = min(tl.n, TILE_CANDS);
   if (t == 0 && nloc > 0) s_base = atomicAdd(&a.status->count, (unsigned long long)nloc);
   epi_sync();
@@ -232,15 +225,18 @@ __device__ void tc_detect(const float *mx, const float *mn, const unsigned char 
   }
 }
 
+constexpr int TC_MAXL = 12;  // landing slots at most
+
 struct TcSmem {
-  uint64_t land_full[2], land_empty[2], b_full[2], b_empty[2], tap_full[2], tap_empty[2], d_full, d_empty, fin;
+  uint64_t land_full[TC_MAXL], land_empty[TC_MAXL], b_full[2], b_empty[2], tap_full[2], tap_empty[2], d_full,
+      d_empty, fin;
   uint32_t tmem;
   int abort;
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_colfir_tc(const __grid_constant__ CUtensorMap map, const FrameDev *__restrict__ fr, Items it,
-                const float *__restrict__ edge, long PWb, const float *__restrict__ bands, TcGeom g,
+                const float *__restrict__ edge, long PWb, const float *__restrict__ bands, TcGeom g, int NL,
                 DetectArgs da) {
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   __shared__ TcSmem sh;
@@ -249,17 +245,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const size_t tapb = ((size_t)2 * g.gmax * 128 + 1023) / 1024 * 1024;  // one band pair (hi, lo)
   unsigned char *taps = base;                                               // [2][tapb]
   unsigned char *bop = taps + 2 * tapb;                                     // [2][hi 8 KB | lo 8 KB]
-  float *land = reinterpret_cast<float *>(bop + 4 * BOP_BYTES);             // [2][32][68]
-  float *mx = land + 2 * TC_BOXW * TC_CH;                                   // [128][XS]
-  float *mn = mx + TC_M * XS;
-  unsigned char *amx = reinterpret_cast<unsigned char *>(mn + TC_M * XS);  // [128][XB]
-  unsigned char *amn = amx + TC_M * XB;
+  float *land = reinterpret_cast<float *>(bop + 4 * BOP_BYTES);             // [NL][32][68]
+  float *ext = land + (size_t)NL * TC_BOXW * TC_CH;                         // [128][XS]
+  unsigned char *aext = reinterpret_cast<unsigned char *>(ext + TC_M * XS);  // [128][XB]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int S = g.S;
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NL; ++b) {
       mbar_init(&sh.land_full[b], 1);
       mbar_init(&sh.land_empty[b], 4);
+    }
+    for (int b = 0; b < 2; ++b) {
       mbar_init(&sh.b_full[b], 4);
       mbar_init(&sh.b_empty[b], 1);
       mbar_init(&sh.tap_full[b], 1);
@@ -316,8 +312,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const int nch = (g.Kd[s] + TC_CH - 1) / TC_CH;
           const long y0 = F.prow + (long)s * H + r0 - g.Kp[s];
           for (int c = 0; c < nch; ++c) {
-            const int ls = nl & 1;
-            if (!mbar_wait_bounded(&sh.land_empty[ls], ((nl >> 1) & 1) ^ 1, wlim)) {
+            const int ls = nl % NL;
+            if (!mbar_wait_bounded(&sh.land_empty[ls], ((nl / NL) & 1) ^ 1, wlim)) {
               give_up(3);
               break;
             }
@@ -332,8 +328,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
       // copies still in flight complete before the CTA ends (bounded)
-      for (uint32_t u = nl > 2 ? nl - 2 : 0; u < nl; ++u)
-        if (!da.wait_test) mbar_wait_bounded(&sh.land_full[u & 1], (u >> 1) & 1, wlim);
+      for (uint32_t u = nl > (uint32_t)NL ? nl - NL : 0; u < nl; ++u)
+        if (!da.wait_test) mbar_wait_bounded(&sh.land_full[u % NL], (u / NL) & 1, wlim);
       for (uint32_t u = nt > 2 ? nt - 2 : 0; u < nt; ++u)
         if (!da.wait_test) mbar_wait_bounded(&sh.tap_full[u & 1], (u >> 1) & 1, wlim);
     }
@@ -410,8 +406,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int nch = (g.Kd[s] + TC_CH - 1) / TC_CH;
         const float *ed = edge + F.eoff + (long)s * 2 * PWb;
         for (int c = 0; c < nch; ++c) {
-          const int ls = nl & 1, bs = nb & 1;
-          bool ok = mbar_wait_bounded(&sh.land_full[ls], (nl >> 1) & 1, wlim);
+          const int ls = nl % NL, bs = nb & 1;
+          bool ok = mbar_wait_bounded(&sh.land_full[ls], (nl / NL) & 1, wlim);
           ok = ok && mbar_wait_bounded(&sh.b_empty[bs], ((nb >> 1) & 1) ^ 1, wlim);
           if (epi_sync_or(!ok)) {
             if (ew == 0 && lane == 0) give_up(1);
@@ -431,7 +427,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             float x = L[qq * TC_BOXW + off + cc];
             if (outside) {
               const int y = yq + qq;
-              if (y < 0 || y >= H) x = ed[(y < 0 ? 0 : PWb) + min(max(x0 + cc, 0), W - 1)];
+              if (y < 0 || y >= H) {
+                const float *e = ed + min(max(x0 + cc, 0), W - 1);
+                x = col_outside(y, H, e[0], e[PWb], da.zero);
+              }
             }
             const float hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
             const int o = ccm * 256 + qcm * 32 + lane;  // float offset: 1024 B per column group, 128 B per row quad
@@ -462,43 +461,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const bool yin = y >= 0 && y < H;
       float *resp = F.resp;
       const long plane = (long)H * W;
-#pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        float vmax[32], vmin[32];
-        uint32_t pmax[4] = {0, 0, 0, 0}, pmin[4] = {0, 0, 0, 0};  // first scale, 4 bits per column
-#pragma unroll
-        for (int j = 0; j < 32; ++j) vmax[j] = -CUDART_INF_F, vmin[j] = CUDART_INF_F;
-        for (int s = 0; s < S; ++s) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(TC_N * s + 32 * h), v);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (v[j] > vmax[j]) vmax[j] = v[j], pmax[j >> 3] = (pmax[j >> 3] & ~(15u << (4 * (j & 7)))) | ((uint32_t)s << (4 * (j & 7)));
-            if (v[j] < vmin[j]) vmin[j] = v[j], pmin[j >> 3] = (pmin[j >> 3] & ~(15u << (4 * (j & 7)))) | ((uint32_t)s << (4 * (j & 7)));
-          }
-          if (resp && yin && o >= 1 && o <= TC_M - 2) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int c = 32 * h + j, x = x0 + c;
-              if (c >= 1 && c <= TC_N - 2 && x >= 0 && x < W) resp[s * plane + (long)y * W + x] = v[j];
-            }
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int c = 32 * h + j, x = x0 + c;
-          const bool in = yin && x >= 0 && x < W;
-          mx[o * XS + c] = in ? vmax[j] : -CUDART_INF_F;
-          mn[o * XS + c] = in ? vmin[j] : CUDART_INF_F;
-          amx[o * XB + c] = in ? (unsigned char)((pmax[j >> 3] >> (4 * (j & 7))) & 15u) : (unsigned char)S;
-          amn[o * XB + c] = in ? (unsigned char)((pmin[j >> 3] >> (4 * (j & 7))) & 15u) : (unsigned char)S;
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh.d_empty);  // tensor memory free for the next tile
-      ++ntile;
-      epi_sync();
       DetectArgs a = da;
       a.S = S;
       a.x0 = x0;
@@ -506,7 +468,54 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       a.H = H;
       a.W = W;
       a.frame = F.index;
-      tc_detect(mx, mn, amx, amn, a, ew, lane);
+      if (ew == 0 && lane == 0) g_tl.n = 0;
+      // pass 0: bright blobs (maxima of R over the scales); pass 1: dark ones
+      // (minima, stored negated so that both passes test maxima).  The
+      // second pass's reads of the tensor memory are its last.
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {
+        const float pol = pass ? -1.f : 1.f;
+        if (pass) epi_sync();  // the first pass's detector is done with ext
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          float vx[32];
+          uint32_t px[4] = {0, 0, 0, 0};  // first scale attaining the extreme, 4 bits per column
+#pragma unroll
+          for (int j = 0; j < 32; ++j) vx[j] = -CUDART_INF_F;
+          for (int s = 0; s < S; ++s) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(TC_N * s + 32 * h), v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float w = pol * v[j];
+              if (w > vx[j]) vx[j] = w, px[j >> 3] = (px[j >> 3] & ~(15u << (4 * (j & 7)))) | ((uint32_t)s << (4 * (j & 7)));
+            }
+            if (!pass && resp && yin && o >= 1 && o <= TC_M - 2) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const int c = 32 * h + j, x = x0 + c;
+                if (c >= 1 && c <= TC_N - 2 && x >= 0 && x < W) resp[s * plane + (long)y * W + x] = v[j];
+              }
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int c = 32 * h + j, x = x0 + c;
+            const bool in = yin && x >= 0 && x < W;
+            ext[o * XS + c] = in ? vx[j] : -CUDART_INF_F;
+            aext[o * XB + c] = in ? (unsigned char)((px[j >> 3] >> (4 * (j & 7))) & 15u) : (unsigned char)S;
+          }
+        }
+        if (pass) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.d_empty);  // tensor memory free for the next tile
+        }
+        epi_sync();
+        if (pass == 0 || a.dark) tc_detect(ext, aext, pass ? -1 : 1, a, ew, lane);
+      }
+      ++ntile;
+      tc_flush(a, 32 * ew + lane);
     }
   }
   // ---------------- release the tensor memory ----------------
@@ -565,9 +574,18 @@ long tc_geometry(const int *K, int S, TcGeom *g) {
   return off;
 }
 
-size_t tc_smem_bytes(const TcGeom &g) {
+// dynamic shared memory of the pass with nl landing slots
+size_t tc_smem_bytes(const TcGeom &g, int nl) {
   const size_t tapb = ((size_t)2 * g.gmax * 128 + 1023) / 1024 * 1024;
-  return 1024 + 2 * tapb + 4 * BOP_BYTES + 2 * LAND_BYTES + (size_t)2 * TC_M * XS * 4 + (size_t)2 * TC_M * XB;
+  return 1024 + 2 * tapb + 4 * BOP_BYTES + (size_t)nl * LAND_BYTES + (size_t)TC_M * XS * 4 + (size_t)TC_M * XB;
+}
+
+// landing slots that fit 216 KB of dynamic shared memory (the rest of the
+// 227 KB a block may have is its static part): 10 for K <= 96, 8 for K <= 160
+int tc_landing_slots(const TcGeom &g) {
+  int nl = TC_MAXL;
+  while (nl > 2 && tc_smem_bytes(g, nl) > (size_t)216 * 1024) --nl;
+  return nl;
 }
 
 int launch_tc_bands(const Coef *d_coef, const TcGeom &g, float sgn, float *d_bands, cudaStream_t st) {
@@ -579,7 +597,8 @@ int launch_colfir_tc(const Plan &p, const Launch &l, const BankArgs &a, const De
   // dynamic shared memory (<= 206 KB for K <= 160) plus the static part
   // (barriers, candidate list) within the 227 KB a block may have
   static size_t attr = 0;
-  const size_t smem = tc_smem_bytes(a.tc);
+  const int nl = tc_landing_slots(a.tc);
+  const size_t smem = tc_smem_bytes(a.tc, nl);
   if (smem > 216 * 1024) return -1;
   if (smem > attr) {
     if (cudaFuncSetAttribute(k_colfir_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -598,7 +617,7 @@ int launch_colfir_tc(const Plan &p, const Launch &l, const BankArgs &a, const De
   }
   const int nb = std::max(1, std::min(l.it.total, nsm));
   a.prof->begin("fir_coldet", st);
-  k_colfir_tc<<<nb, TC_THREADS, smem, st>>>(map, p.fr, l.it, a.edge, p.PWb, a.tc_bands, a.tc, da);
+  k_colfir_tc<<<nb, TC_THREADS, smem, st>>>(map, p.fr, l.it, a.edge, p.PWb, a.tc_bands, a.tc, nl, da);
   a.prof->end(st);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }

@@ -667,71 +667,29 @@ __global__ void __launch_bounds__(512) __maxnreg__(LC == 32 ? Rec::kColdetRegs32
       top = ed[0];
       bot = ed[PWb];
     }
-    if constexpr (F32) {
-      // Both directions in one loop: at step i the causal recursion takes row
-      // i and the anticausal one row NR-1-i (two independent chains per
-      // thread).  A row's first visitor keeps its one-sided output in a
-      // register; the second adds its own and writes R over the input, which
-      // neither recursion reads again.  Rows outside the frame take the held
-      // one-sided rows of U.
-      static_assert(NR % 2 == 0, "even tile height");
-      constexpr int HALF = NR / 2;
-      Rec ra;
-      ra.load(Ef + fs, PWb);
-      float pt[HALF], pb[HALF];
+    // causal pass; rows outside the frame take the held one-sided rows of U
+    // (written back for the anticausal pass), 16-bit input is widened in place
+    const T *b16 = reinterpret_cast<const T *>(reinterpret_cast<const char *>(buf + (long)s * REG) + C16B) +
+                   off + lane;
+    float yp[NR];
 #pragma unroll
-      for (int i = 0; i < HALF; ++i) {
-        const int j = NR - 1 - i;
-        float xc = b[i * LD], xa = b[j * LD];
-        if (outside) {
-          xc = r0 + i < 0 ? top : (r0 + i >= H ? bot : xc);
-          xa = r0 + j < 0 ? top : (r0 + j >= H ? bot : xa);
-        }
-        pt[i] = r.out(v);
-        r.push(v, xc);
-        pb[i] = fmaf(v.b0, xa, ra.out(v));
-        ra.push(v, xa);
-      }
+    for (int i = 0; i < NR; ++i) {
+      const int y = r0 + i;
+      float in = F32 ? b[i * LD] : Store<ST>::ld(b16[i * CBOX16]);
+      if (outside) in = y < 0 ? top : (y >= H ? bot : in);
+      if (!F32 || outside) b[i * LD] = in;
+      yp[i] = r.out(v);
+      r.push(v, in);
+      if ((i & 7) == 7) __syncwarp();
+    }
+    __syncwarp();
+    r.load(Ef + fs, PWb);
 #pragma unroll
-      for (int i = HALF; i < NR; ++i) {
-        const int j = NR - 1 - i;
-        float xc = b[i * LD], xa = b[j * LD];
-        if (outside) {
-          xc = r0 + i < 0 ? top : (r0 + i >= H ? bot : xc);
-          xa = r0 + j < 0 ? top : (r0 + j >= H ? bot : xa);
-        }
-        const float yc = r.out(v);
-        r.push(v, xc);
-        const float ya = fmaf(v.b0, xa, ra.out(v));
-        ra.push(v, xa);
-        // R_L = -sigma^2 (D20 + D02) (planes carry sigma^2); raw channel: +sigma^2 D
-        b[i * LD] = sgn * (yc + pb[j]);
-        b[j * LD] = sgn * (pt[j] + ya);
-      }
-    } else {
-      // 16-bit planes: the causal pass widens the box in place (row order),
-      // then the anticausal pass
-      const T *b16 = reinterpret_cast<const T *>(reinterpret_cast<const char *>(buf + (long)s * REG) + C16B) +
-                     off + lane;
-      float yp[NR];
-#pragma unroll
-      for (int i = 0; i < NR; ++i) {
-        const int y = r0 + i;
-        float in = Store<ST>::ld(b16[i * CBOX16]);
-        if (outside) in = y < 0 ? top : (y >= H ? bot : in);
-        b[i * LD] = in;
-        yp[i] = r.out(v);
-        r.push(v, in);
-        if ((i & 7) == 7) __syncwarp();
-      }
-      __syncwarp();
-      r.load(Ef + fs, PWb);
-#pragma unroll
-      for (int i = NR - 1; i >= 0; --i) {
-        const float in = b[i * LD];
-        b[i * LD] = sgn * (yp[i] + fmaf(v.b0, in, r.out(v)));
-        r.push(v, in);
-      }
+    for (int i = NR - 1; i >= 0; --i) {
+      const float in = b[i * LD];
+      // R_L = -sigma^2 (D20 + D02) (planes carry sigma^2); raw channel: +sigma^2 D
+      b[i * LD] = sgn * (yp[i] + fmaf(v.b0, in, r.out(v)));
+      r.push(v, in);
     }
     __syncthreads();
     DetectArgs a = da;

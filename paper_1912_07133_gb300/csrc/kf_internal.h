@@ -70,6 +70,11 @@ struct BankArgs {
   // failure-detection test hook (kf_set_wait_limit): > 0, the column pass
   // issues no copy to its load barrier and gives up after this many polls
   unsigned wait_test = 0;
+  // FIR banks: 1 for the zero boundary (the frame extended by zeros: the
+  // Laplacian is nonzero one pixel beyond the edges, the column passes take
+  // the blurred first / last input row one row beyond and zero further out);
+  // 0 for the hold boundary
+  int zero = 0;
   // tensor-core FIR column pass: the design's taps as band operands (device)
   // and their geometry; null: the pass does not apply to this call
   const float *tc_bands = nullptr;

@@ -41,6 +41,7 @@ KF_DTYPE_U16 = 3
 KF_RESP_LAPLACIAN = 0
 KF_RESP_HESSIAN = 1
 KF_BOUNDARY_HOLD = 0
+KF_BOUNDARY_ZERO = 1
 KF_NEIGH_ALL_SCALES = 0
 KF_NEIGH_ADJACENT = 1
 KF_GATE_OFF, KF_GATE_DILATED, KF_GATE_TILES = 0, 1, 2
@@ -499,7 +500,7 @@ class Bank:
     def run(self, frames, scales, ftype=KF_IIR_REPEATED_POLE, order=4, threshold=0.05,
             neighbourhood=KF_NEIGH_ALL_SCALES, responses=None, fir_kmax=96, profile=False,
             storage=KF_DTYPE_F32, value_scales=None, schedule=KF_SCHED_BATCHED, graph=False, gate=False,
-            gate_threshold=None, response=KF_RESP_LAPLACIAN, offset_limit=0.0):
+            gate_threshold=None, response=KF_RESP_LAPLACIAN, offset_limit=0.0, boundary=KF_BOUNDARY_HOLD):
         o = kf_bank_opts_default()
         o.threshold = float(threshold)
         o.profile = 1 if profile else 0
@@ -511,6 +512,7 @@ class Bank:
         o.gate = int(gate) if not isinstance(gate, bool) else (KF_GATE_DILATED if gate else KF_GATE_OFF)
         o.response = response
         o.offset_limit = float(offset_limit)
+        o.boundary = int(boundary)
         if gate_threshold is not None:
             o.gate_threshold = float(gate_threshold)
         if responses is not None:

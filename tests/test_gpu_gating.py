@@ -67,13 +67,14 @@ def expected_active(frame, c, dilate=True):
     return d
 
 
-def selected(frame, act, rows):
-    """Per pixel: inside the interior of a column tile the gate selects."""
+def selected(frame, act, rows, tw=TW):
+    """Per pixel: inside the interior (tw columns x rows) of a column tile the
+    gate selects."""
     H, W = frame.shape
     sel = np.zeros((H, W), bool)
     for y0 in range(0, H, rows):
-        for x0 in range(0, W, TW):
-            y1, x1 = min(y0 + rows, H), min(x0 + TW, W)
+        for x0 in range(0, W, tw):
+            y1, x1 = min(y0 + rows, H), min(x0 + tw, W)
             if act[y0 // 64:(y1 - 1) // 64 + 1, x0 // 64:(x1 - 1) // 64 + 1].any():
                 sel[y0:y1, x0:x1] = True
     return sel
@@ -97,8 +98,9 @@ def run(frames, ftype, order, gate, c=0.5, graph=False, calls=1):
 
 
 @pytest.mark.parametrize("dilated", [True, False])
-@pytest.mark.parametrize("ftype,order,rows", [(D, 4, 64), (E, 2, 64), (C, 1, 126)])
-def test_gated_blobs_are_the_full_blobs_of_the_selected_tiles(ftype, order, rows, dilated):
+# column tiles: 30 x 64 (recursive banks), 62 x 126 (the FIR bank's tensor-core pass)
+@pytest.mark.parametrize("ftype,order,rows,tw", [(D, 4, 64, 30), (E, 2, 64, 30), (C, 1, 126, 62)])
+def test_gated_blobs_are_the_full_blobs_of_the_selected_tiles(ftype, order, rows, tw, dilated):
     from paper_1912_07133_gb300 import kf
     frames = frames_for_gating()
     Rf, bf = run(frames, ftype, order, gate=False)
@@ -108,7 +110,7 @@ def test_gated_blobs_are_the_full_blobs_of_the_selected_tiles(ftype, order, rows
     for i, f in enumerate(frames):
         act = expected_active(f, 0.5, dilated)
         assert 0 < act.sum() < act.size
-        sel = selected(f, act, rows)
+        sel = selected(f, act, rows, tw)
         k = len(SCALES) * f.size
         Rfi = Rf[off:off + k].reshape(len(SCALES), *f.shape)
         Rgi = Rg[off:off + k].reshape(len(SCALES), *f.shape)
