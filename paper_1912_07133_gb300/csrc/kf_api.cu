@@ -813,7 +813,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     cudaError_t ee;
     if ((ee = cudaMemsetAsync(ctx->g_count, 0, 2 * sizeof(int), st)) != cudaSuccess)
       return cuda_fail(ctx, ee, "gate counts");
-    const int rows = iir ? ctx->seg_len[type] : kf::fir_tile_rows(opts.neighbourhood);
+    const int rows = iir ? ctx->seg_len[type]
+                         : (tcpass ? kf::fir_tc_tile_rows(nscales) : kf::fir_tile_rows(opts.neighbourhood));
     if (kf::gate_select_tiles(plan.fr, full_det, ctx->g_act, tcpass ? kf::fir_tc_tile_cols() : TW_COL, rows,
                               ctx->g_sel[0], ctx->g_count, st))
       return cuda_fail(ctx, cudaGetLastError(), "gate selection");

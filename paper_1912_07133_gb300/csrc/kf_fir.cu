@@ -824,10 +824,11 @@ int fir_halo(int kmax) { return kmax + TB + 1; }
 
 int fir_items(int pass, int H, int W, int S, int neigh, bool tc) {
   const int tw = tc ? fir_tc_tile_cols() : TW;
+  const int th = tc ? fir_tc_tile_rows(S) : (neigh == 0 ? CROWS2 - 2 : CROWS - 2);
   const int ntx = (W + tw - 1) / tw;
   switch (pass) {
     case PASS_ROW: return ((W + RSEG - 1) / RSEG) * (H + 2);
-    case PASS_DET: return neigh == 0 ? ntx * ((H + CROWS2 - 3) / (CROWS2 - 2)) : ntx * ((H + CROWS - 3) / (CROWS - 2));
+    case PASS_DET: return ntx * ((H + th - 1) / th);
     default: return 0;
   }
 }

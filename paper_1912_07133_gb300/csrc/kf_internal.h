@@ -36,13 +36,14 @@ struct Prof {
 };
 
 // Tensor-core FIR column pass (kf_fir_tc.cu): per scale (<= 8) the taps as a
-// banded Toeplitz operand for MMAs of 128 output rows; K half-length, Kp = K
-// rounded up to 4, Kd = 128 + 2 Kp input rows, G band chunks of 128 bytes
+// banded Toeplitz operand for MMAs of NR output rows; K half-length, Kp = K
+// rounded up to 4, Kd = NR + 2 Kp input rows, G band chunks of 128 bytes
 // (per hi and lo part), boff the float offset of the scale's hi band in the
 // band buffer (its lo band follows G x 32 floats later).
 constexpr int TC_MAXS = 8;
 struct TcGeom {
   int S = 0;
+  int NR = 64;  // output rows per tile (64 for <= 6 scales, else 32)
   int K[TC_MAXS] = {}, Kp[TC_MAXS] = {}, Kd[TC_MAXS] = {}, G[TC_MAXS] = {};
   long boff[TC_MAXS] = {};
   int gmax = 0;
@@ -109,13 +110,14 @@ struct Plan {
 // work items of one frame in a pass (the kernels' decomposition)
 int iir_items(int pass, int H, int W, int S, int lc);
 int iir_row_threads(int W);    // threads per block of the IIR row pass (0: too wide)
-int fir_items(int pass, int H, int W, int S, int neigh, bool tc = false);
+int fir_items(int pass, int H, int W, int S, int neigh, bool tc = false);  // tc: the tensor-core column pass
 // tensor-core FIR column pass (kf_fir_tc.cu): whether it serves a call (f32
 // planes, all-scales neighbourhood, <= 8 scales, detection, a plane row
 // space of at least 68 x 32 elements), its tiles' interior width, the band geometry of a design (floats of the band buffer,
 // -1 if it does not apply), the band builder and the launch
 bool fir_tc_applies(int S, int storage, int neigh, int raw, long PWb, long prows);
 int fir_tc_tile_cols();
+int fir_tc_tile_rows(int S);
 long tc_geometry(const int *K, int S, TcGeom *g);
 int launch_tc_bands(const Coef *d_coef, const TcGeom &g, float sgn, float *d_bands, cudaStream_t st);
 int launch_colfir_tc(const Plan &p, const Launch &l, const BankArgs &a, const struct DetectArgs &da,

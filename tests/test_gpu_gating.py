@@ -98,8 +98,8 @@ def run(frames, ftype, order, gate, c=0.5, graph=False, calls=1):
 
 
 @pytest.mark.parametrize("dilated", [True, False])
-# column tiles: 30 x 64 (recursive banks), 62 x 126 (the FIR bank's tensor-core pass)
-@pytest.mark.parametrize("ftype,order,rows,tw", [(D, 4, 64, 30), (E, 2, 64, 30), (C, 1, 126, 62)])
+# column tiles: 30 x 64 (recursive banks), 126 x 62 (the FIR bank's tensor-core pass, <= 6 scales)
+@pytest.mark.parametrize("ftype,order,rows,tw", [(D, 4, 64, 30), (E, 2, 64, 30), (C, 1, 62, 126)])
 def test_gated_blobs_are_the_full_blobs_of_the_selected_tiles(ftype, order, rows, tw, dilated):
     from paper_1912_07133_gb300 import kf
     frames = frames_for_gating()

@@ -45,10 +45,15 @@ def oracle_zero(img, scales, ftype, order):
 
 
 def check(kf, img, scales, ftype, order, neigh=0):
+    """Responses within 1e-5 of each scale's range -- of its largest magnitude
+    where that is larger (a frame of a few pixels amid zeros has a nearly
+    constant response, and FP32 rounding scales with the response, not its
+    range) -- and the blob lists by the margin rule."""
     Rg, b = gpu_zero(kf, img, scales, ftype, order, neigh)
     Ro = oracle_zero(img, scales, ftype, order)
     for s in range(len(scales)):
-        assert np.abs(Rg[s] - Ro[s]).max() <= TOL * max(np.ptp(Ro[s]), 1e-3), (scales[s], s)
+        bar = TOL * max(np.ptp(Ro[s]), np.abs(Ro[s]).max() if min(img.shape) <= 3 else 0.0, 1e-3)
+        assert np.abs(Rg[s] - Ro[s]).max() <= bar, (scales[s], s)
     if img.size > 1:
         compare_blobs(b, Ro, 0.05, neigh=neigh)
     return Rg, Ro, b
