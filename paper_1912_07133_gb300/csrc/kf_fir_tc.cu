@@ -28,7 +28,9 @@
 // x = hi + lo (hi = x with its low 13 bits cleared, lo = x - hi exactly) and
 // the taps split once per design (hi = tf32(h), lo = tf32(h - hi)),
 // out = A_lo B_hi + A_hi B_lo + A_hi B_hi leaves about 2^-21 of each product.
-// A_hi is the raw data (the tensor core truncates it to hi).
+// A_hi is the raw data (the tensor core truncates it to hi).  16-bit planes
+// (f16, bf16) hold values exact in TF32: two products, A_hi (B_lo + B_hi),
+// except in chunks that reach the frame's held f32 edge rows.
 //
 // One CTA per SM, persistent over the call's tiles (interior 126 x (NR - 2)),
 // warp-specialised:
@@ -42,9 +44,9 @@
 //               it and stores it into the chunk's tensor-memory slot;
 //   warps 6-9   epilogue: every scale of the tile out of tensor memory
 //               (per-pixel extremes over the scales, the optional
-//               responses), then -- with the tensor memory released to the
-//               next tile's MMAs -- the 3 x 3 spatial test and the tile's
-//               candidate list.
+//               responses), each scale's columns released to the next
+//               tile's MMAs as soon as they are read; then the 3 x 3 spatial
+//               test and the tile's candidate list.
 // Tensor memory (512 columns): the accumulators of scale s at columns
 // [NR s, NR (s + 1)) (at most 384), two operand slots of 64 columns (hi,
 // lo) at 384 and 448.  Every wait is bounded; a wait that gives up sets the
@@ -66,14 +68,18 @@ namespace {
 
 constexpr int TC_M = 128;               // image columns per tile (MMA M, tensor-memory lanes)
 constexpr int TC_CH = 32;               // input rows per chunk
-constexpr int TC_BOXW = 132;            // landed chunk width (floats): 128 columns + TMA alignment offset <= 3
+constexpr int TC_BOXW = 132;            // landed chunk width (f32): 128 columns + TMA alignment offset <= 3
+constexpr int TC_BOXW16 = 136;          // landed chunk width (16-bit): 128 columns + offset <= 7
 constexpr int TC_THREADS = 320;         // warps 0 (loads), 1 (MMA), 2-5 (split), 6-9 (epilogue)
 constexpr int TC_MAXL = 6;              // landing slots at most
 constexpr int TC_ACOL = 384;            // tensor-memory column of the first operand slot
 constexpr int XS = TC_M + 1;            // row stride (floats) of the per-pixel extremes
 constexpr int XB = TC_M + 4;            // row stride (bytes) of their first-scale maps
 constexpr uint32_t TC_WAIT = 1u << 20;  // polls of a bounded wait (each parks the warp up to ~1 us)
-constexpr size_t LAND_BYTES = (size_t)TC_BOXW * TC_CH * 4;  // 16896
+// landed chunk bytes: 16896 (f32 planes) or 8704 (16-bit planes)
+__host__ __device__ constexpr size_t land_bytes(int st) {
+  return st == ST_F32 ? (size_t)TC_BOXW * TC_CH * 4 : (size_t)TC_BOXW16 * TC_CH * 2;
+}
 
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   // shared-memory matrix descriptor: start >> 4, leading and stride byte
@@ -252,7 +258,7 @@ __device__ void tc_flush(const DetectArgs &a, int t) {
 
 struct TcSmem {
   uint64_t land_full[TC_MAXL], land_empty[TC_MAXL], a_full[2], a_empty[2], tap_full[2], tap_empty[2], d_full,
-      d_empty, fin;
+      d_empty[TC_MAXS], fin;
   uint32_t tmem;
   int abort;
 };
@@ -266,10 +272,18 @@ __device__ __forceinline__ TcTile tc_tile(int local, int W, int NR) {
   return {(local % ntx) * (TC_M - 2) - 1, (local / ntx) * (NR - 2) - 1};
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// 320 threads of one CTA per SM: up to 200 registers each (the epilogue
+// keeps a column's running extremes over the scales for 64 rows)
+template <int ST>
+__global__ void __maxnreg__(200)
     k_colfir_tc(const __grid_constant__ CUtensorMap map, const FrameDev *__restrict__ fr, Items it,
                 const float *__restrict__ edge, long PWb, const float *__restrict__ bands, TcGeom g, int NL,
                 DetectArgs da) {
+  using T = typename Store<ST>::T;
+  constexpr bool F32 = ST == ST_F32;
+  constexpr int BW = F32 ? TC_BOXW : TC_BOXW16;  // landed row (elements)
+  constexpr int XA = F32 ? 4 : 8;                 // TMA x alignment (elements)
+  constexpr size_t LAND = land_bytes(ST);
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   __shared__ TcSmem sh;
   unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) &
@@ -277,8 +291,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int NR = g.NR;
   const size_t tapb = ((size_t)2 * g.gmax * 128 + 1023) / 1024 * 1024;  // one band pair (hi, lo)
   unsigned char *taps = base;                                               // [2][tapb]
-  float *land = reinterpret_cast<float *>(taps + 2 * tapb);                 // [NL][32][132]
-  float *mx = land + (size_t)NL * TC_BOXW * TC_CH;                          // [NR][XS]
+  T *land = reinterpret_cast<T *>(taps + 2 * tapb);                         // [NL][32][BW]
+  float *mx = reinterpret_cast<float *>(taps + 2 * tapb + (size_t)NL * LAND);  // [NR][XS]
   float *mn = mx + (size_t)NR * XS;
   unsigned char *amx = reinterpret_cast<unsigned char *>(mn + (size_t)NR * XS);  // [NR][XB]
   unsigned char *amn = amx + (size_t)NR * XB;
@@ -296,7 +310,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&sh.tap_empty[b], 1);
     }
     mbar_init(&sh.d_full, 1);
-    mbar_init(&sh.d_empty, 4);
+    for (int t = 0; t < TC_MAXS; ++t) mbar_init(&sh.d_empty[t], 4);
     mbar_init(&sh.fin, 1);
     sh.abort = 0;
     fence_proxy_async();
@@ -328,7 +342,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         k = item_frame(it, item, k, local);
         const FrameDev &F = fr[__ldg(it.fl + k)];
         const TcTile t = tc_tile(local, F.W, NR);
-        const int xa = t.x0 - (((t.x0 % 4) + 4) % 4);
+        const int xa = t.x0 - (((t.x0 % XA) + XA) % XA);
         for (int s = 0; s < S && !*abort; ++s) {
           const int ts = nt & 1;
           if (!mbar_wait_bounded(&sh.tap_empty[ts], ((nt >> 1) & 1) ^ 1, wlim)) {
@@ -351,9 +365,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             if (!da.wait_test) {
               fence_proxy_async();
-              mbar_arrive_expect_tx(&sh.land_full[ls], (uint32_t)LAND_BYTES);
-              if (!tma_load_2d(land + (size_t)ls * TC_BOXW * TC_CH, &map, xa, (int)(y0 + (long)c * TC_CH),
-                               &sh.land_full[ls]))
+              mbar_arrive_expect_tx(&sh.land_full[ls], (uint32_t)LAND);
+              if (!tma_load_2d(land + (size_t)ls * BW * TC_CH, &map, xa, (int)(y0 + (long)c * TC_CH),
+                               &sh.land_full[ls], (int)sizeof(T)))
                 give_up(2);
             }
             ++nl;
@@ -373,18 +387,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t na = 0, nt = 0, ntile = 0;
       bool issued = false;
       const uint32_t idesc = tc_idesc(NR);
+      int k = 0;
       for (int item = blockIdx.x; item < nitems && !*abort; item += gridDim.x) {
-        if (!mbar_wait_bounded(&sh.d_empty, (ntile & 1) ^ 1, wlim)) {
-          give_up(4);
-          break;
-        }
-        tc_fence_after();
+        int local;
+        k = item_frame(it, item, k, local);
+        const int H = fr[__ldg(it.fl + k)].H;
+        const int r0 = tc_tile(local, fr[__ldg(it.fl + k)].W, NR).r0;
         for (int s = 0; s < S && !*abort; ++s) {
           const int ts = nt & 1;
-          if (!mbar_wait_bounded(&sh.tap_full[ts], (nt >> 1) & 1, wlim)) {
+          // the epilogue has read the previous tile's accumulators of scale s
+          if (!mbar_wait_bounded(&sh.d_empty[s], (ntile & 1) ^ 1, wlim) ||
+              !mbar_wait_bounded(&sh.tap_full[ts], (nt >> 1) & 1, wlim)) {
             give_up(1);
             break;
           }
+          tc_fence_after();
           const uint32_t b_hi = smem_u32(taps + ts * tapb), b_lo = b_hi + (uint32_t)g.G[s] * 128u;
           const int nch = (g.Kd[s] + TC_CH - 1) / TC_CH;
           const uint32_t d = tmem + (uint32_t)(NR * s);
@@ -397,11 +414,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_after();
             const uint32_t a_hi = tmem + (uint32_t)(TC_ACOL + 64 * as), a_lo = a_hi + 32u;
             const int nk = min(TC_CH / 8, (g.Kd[s] - c * TC_CH) / 8);
+            // a chunk that reaches the held (f32) edge rows needs its low parts
+            const int yq = r0 - g.Kp[s] + c * TC_CH;
+            const bool three = F32 || yq < 0 || yq + TC_CH > H;
             for (int kk = 0; kk < nk; ++kk) {
               const uint32_t ks = (uint32_t)(4 * c + kk);
               const uint64_t bh = sdesc(b_hi + 256u * ks, 128, 256), bl = sdesc(b_lo + 256u * ks, 128, 256);
-              tc_mma(d, a_lo + 8u * kk, bh, idesc, ks > 0);
-              tc_mma(d, a_hi + 8u * kk, bl, idesc, 1);
+              if (three) {
+                tc_mma(d, a_lo + 8u * kk, bh, idesc, ks > 0);
+                tc_mma(d, a_hi + 8u * kk, bl, idesc, 1);
+              } else {  // 16-bit planes are exact in TF32: no low part
+                tc_mma(d, a_hi + 8u * kk, bl, idesc, ks > 0);
+              }
               tc_mma(d, a_hi + 8u * kk, bh, idesc, 1);
             }
             issued = true;
@@ -434,11 +458,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const FrameDev &F = fr[__ldg(it.fl + k)];
       const int H = F.H, W = F.W;
       const TcTile t = tc_tile(local, W, NR);
-      const int off = ((t.x0 % 4) + 4) % 4;
+      const int off = ((t.x0 % XA) + XA) % XA;
       const int xc = min(max(t.x0 + c, 0), W - 1);
       for (int s = 0; s < S && !bad; ++s) {
         const int nch = (g.Kd[s] + TC_CH - 1) / TC_CH;
-        const float *ed = edge + F.eoff + (long)s * 2 * PWb + xc;
+        // the held (or zero-boundary) edge values of this column, read once
+        // per scale where the scale's rows reach beyond the frame
+        float top = 0.f, bot = 0.f;
+        if (t.r0 - g.Kp[s] < 0 || t.r0 - g.Kp[s] + g.Kd[s] > H) {
+          const float *ed = edge + F.eoff + (long)s * 2 * PWb + xc;
+          top = ed[0];
+          bot = ed[PWb];
+        }
         for (int ch = 0; ch < nch; ++ch) {
           const int ls = nl % NL, as = na & 1;
           bool ok = mbar_wait_bounded(&sh.land_full[ls], (nl / NL) & 1, wlim);
@@ -449,29 +480,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             break;
           }
           tc_fence_after();
-          const float *L = land + (size_t)ls * TC_BOXW * TC_CH + off + c;
+          const T *L = land + (size_t)ls * BW * TC_CH + off + c;
           const int yq = t.r0 - g.Kp[s] + ch * TC_CH;  // frame row of chunk row 0
           uint32_t hi[32], lo[32];
           if (yq >= 0 && yq + TC_CH <= H) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              const float x = L[j * TC_BOXW];
+              const float x = Store<ST>::ld(L[j * BW]);
               hi[j] = __float_as_uint(x);
               lo[j] = __float_as_uint(x - __uint_as_float(hi[j] & 0xffffe000u));
             }
           } else {  // rows outside the frame: the boundary rule (held or zero)
-            const float top = ed[0], bot = ed[PWb];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int y = yq + j;
-              const float x = (y < 0 || y >= H) ? col_outside(y, H, top, bot, da.zero) : L[j * TC_BOXW];
+              const float x = (y < 0 || y >= H) ? col_outside(y, H, top, bot, da.zero) : Store<ST>::ld(L[j * BW]);
               hi[j] = __float_as_uint(x);
               lo[j] = __float_as_uint(x - __uint_as_float(hi[j] & 0xffffe000u));
             }
           }
           const uint32_t ta = tmem + lanes + (uint32_t)(TC_ACOL + 64 * as);
           tmem_st32(ta, hi);
-          tmem_st32(ta + 32u, lo);
+          // f32: the low parts; a 16-bit plane value is exact in TF32, but
+          // the held edge rows (f32) need their low parts too
+          if (F32 || yq < 0 || yq + TC_CH > H) tmem_st32(ta + 32u, lo);
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           tc_fence_before();
           __syncwarp();
@@ -510,44 +542,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       float *resp = F.resp;
       const long plane = (long)H * W;
       // per-pixel extremes over the scales (first scale attaining them) and
-      // the responses: accumulator column n is output row NR - 1 - n
-#pragma unroll 1
-      for (int n0 = 0; n0 < NR; n0 += 32) {
-        float vmax[32], vmin[32];
-        uint32_t pmax[4] = {0, 0, 0, 0}, pmin[4] = {0, 0, 0, 0};  // 4 bits per row
+      // the responses: accumulator column n is output row NR - 1 - n.  Scale
+      // by scale: once a scale's accumulators are read, its columns go to
+      // the next tile's MMAs.
+      float vmax[64], vmin[64];
+      uint32_t pmax[8], pmin[8];  // first scale attaining the extreme, 4 bits per row
 #pragma unroll
-        for (int j = 0; j < 32; ++j) vmax[j] = -CUDART_INF_F, vmin[j] = CUDART_INF_F;
-        for (int s = 0; s < S; ++s) {
+      for (int j = 0; j < 64; ++j) vmax[j] = -CUDART_INF_F, vmin[j] = CUDART_INF_F;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) pmax[j] = pmin[j] = 0u;
+      for (int s = 0; s < S; ++s) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (32 * h >= NR) break;
           float v[32];
-          tmem_ld32(tmem + lanes + (uint32_t)(NR * s + n0), v);
+          tmem_ld32(tmem + lanes + (uint32_t)(NR * s + 32 * h), v);
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const uint32_t sh4 = 4u * (j & 7);
-            if (v[j] > vmax[j]) vmax[j] = v[j], pmax[j >> 3] = (pmax[j >> 3] & ~(15u << sh4)) | ((uint32_t)s << sh4);
-            if (v[j] < vmin[j]) vmin[j] = v[j], pmin[j >> 3] = (pmin[j >> 3] & ~(15u << sh4)) | ((uint32_t)s << sh4);
+            const int n = 32 * h + j;
+            const uint32_t sh4 = 4u * (n & 7);
+            if (v[j] > vmax[n]) vmax[n] = v[j], pmax[n >> 3] = (pmax[n >> 3] & ~(15u << sh4)) | ((uint32_t)s << sh4);
+            if (v[j] < vmin[n]) vmin[n] = v[j], pmin[n >> 3] = (pmin[n >> 3] & ~(15u << sh4)) | ((uint32_t)s << sh4);
           }
           if (resp && xin && c >= 1 && c <= TC_M - 2) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              const int o = NR - 1 - (n0 + j), y = t.r0 + o;
+              const int o = NR - 1 - (32 * h + j), y = t.r0 + o;
               if (o >= 1 && o <= NR - 2 && y >= 0 && y < H) resp[s * plane + (long)y * W + x] = v[j];
             }
           }
         }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int o = NR - 1 - (n0 + j), y = t.r0 + o;
-          const bool in = xin && y >= 0 && y < H;
-          const uint32_t sh4 = 4u * (j & 7);
-          mx[o * XS + c] = in ? vmax[j] : -CUDART_INF_F;
-          mn[o * XS + c] = in ? vmin[j] : CUDART_INF_F;
-          amx[o * XB + c] = in ? (unsigned char)((pmax[j >> 3] >> sh4) & 15u) : (unsigned char)S;
-          amn[o * XB + c] = in ? (unsigned char)((pmin[j >> 3] >> sh4) & 15u) : (unsigned char)S;
-        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.d_empty[s]);  // scale s's columns free for the next tile
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh.d_empty);  // tensor memory free for the next tile
+#pragma unroll
+      for (int n = 0; n < 64; ++n) {
+        if (n >= NR) break;
+        const int o = NR - 1 - n, y = t.r0 + o;
+        const bool in = xin && y >= 0 && y < H;
+        const uint32_t sh4 = 4u * (n & 7);
+        mx[o * XS + c] = in ? vmax[n] : -CUDART_INF_F;
+        mn[o * XS + c] = in ? vmin[n] : CUDART_INF_F;
+        amx[o * XB + c] = in ? (unsigned char)((pmax[n >> 3] >> sh4) & 15u) : (unsigned char)S;
+        amn[o * XB + c] = in ? (unsigned char)((pmin[n >> 3] >> sh4) & 15u) : (unsigned char)S;
+      }
       ++ntile;
       if (ew == 0 && lane == 0) g_tl.n = 0;
       epi_sync();
@@ -592,24 +631,25 @@ __global__ void __launch_bounds__(256) k_tc_bands(const Coef *__restrict__ coef,
 }
 
 // dynamic shared memory of the pass with nl landing slots
-size_t tc_smem_bytes(const TcGeom &g, int nl) {
+size_t tc_smem_bytes(const TcGeom &g, int nl, int st) {
   const size_t tapb = ((size_t)2 * g.gmax * 128 + 1023) / 1024 * 1024;
-  return 1024 + 2 * tapb + (size_t)nl * LAND_BYTES + (size_t)2 * g.NR * XS * 4 + (size_t)2 * g.NR * XB;
+  return 1024 + 2 * tapb + (size_t)nl * land_bytes(st) + (size_t)2 * g.NR * XS * 4 + (size_t)2 * g.NR * XB;
 }
 
 // landing slots that fit 216 KB of dynamic shared memory (the rest of the
 // 227 KB a block may have is its static part)
-int tc_landing_slots(const TcGeom &g) {
+int tc_landing_slots(const TcGeom &g, int st) {
   int nl = TC_MAXL;
-  while (nl > 2 && tc_smem_bytes(g, nl) > (size_t)216 * 1024) --nl;
+  while (nl > 2 && tc_smem_bytes(g, nl, st) > (size_t)216 * 1024) --nl;
   return nl;
 }
 
 }  // namespace
 
 bool fir_tc_applies(int S, int storage, int neigh, int raw, long PWb, long prows) {
-  // the tensor map's box (132 x 32) fits the plane row space
-  return S >= 1 && S <= TC_MAXS && storage == ST_F32 && neigh == 0 && !raw && PWb >= TC_BOXW && prows >= TC_CH;
+  // the tensor map's box (132 or 136 elements x 32 rows) fits the plane row space
+  return S >= 1 && S <= TC_MAXS && storage >= ST_F32 && storage <= ST_BF16 && neigh == 0 && !raw &&
+         PWb >= TC_BOXW16 && prows >= TC_CH;
 }
 
 int fir_tc_tile_cols() { return TC_M - 2; }
@@ -639,20 +679,21 @@ int launch_tc_bands(const Coef *d_coef, const TcGeom &g, float sgn, float *d_ban
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_colfir_tc(const Plan &p, const Launch &l, const BankArgs &a, const DetectArgs &da, cudaStream_t st) {
+template <int ST>
+int launch_colfir_tc_st(const Plan &p, const Launch &l, const BankArgs &a, const DetectArgs &da, cudaStream_t st) {
   // dynamic shared memory (<= 216 KB) plus the static part (barriers,
   // candidate list) within the 227 KB a block may have
   static size_t attr = 0;
-  const int nl = tc_landing_slots(a.tc);
-  const size_t smem = tc_smem_bytes(a.tc, nl);
+  const int nl = tc_landing_slots(a.tc, ST);
+  const size_t smem = tc_smem_bytes(a.tc, nl, ST);
   if (smem > 216 * 1024 || nl < 2) return -1;
   if (smem > attr) {
-    if (cudaFuncSetAttribute(k_colfir_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_colfir_tc<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return -1;
     attr = smem;
   }
   CUtensorMap map;
-  if (encode_plane_map(&map, a.P, ST_F32, p.PWb, p.prows, TC_BOXW, TC_CH)) return -1;
+  if (encode_plane_map(&map, a.P, ST, p.PWb, p.prows, ST == ST_F32 ? TC_BOXW : TC_BOXW16, TC_CH)) return -1;
   // one CTA per SM (the tensor memory is allocated whole), persistent over the tiles
   static int nsm = 0;
   if (!nsm) {
@@ -663,9 +704,18 @@ int launch_colfir_tc(const Plan &p, const Launch &l, const BankArgs &a, const De
   }
   const int nb = std::max(1, std::min(l.it.total, nsm));
   a.prof->begin("fir_coldet", st);
-  k_colfir_tc<<<nb, TC_THREADS, smem, st>>>(map, p.fr, l.it, a.edge, p.PWb, a.tc_bands, a.tc, nl, da);
+  k_colfir_tc<ST><<<nb, TC_THREADS, smem, st>>>(map, p.fr, l.it, a.edge, p.PWb, a.tc_bands, a.tc, nl, da);
   a.prof->end(st);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_colfir_tc(const Plan &p, const Launch &l, const BankArgs &a, const DetectArgs &da, cudaStream_t st) {
+  switch (a.storage) {
+    case ST_F32: return launch_colfir_tc_st<ST_F32>(p, l, a, da, st);
+    case ST_F16: return launch_colfir_tc_st<ST_F16>(p, l, a, da, st);
+    case ST_BF16: return launch_colfir_tc_st<ST_BF16>(p, l, a, da, st);
+    default: return -2;
+  }
 }
 
 }  // namespace kf
