@@ -272,10 +272,10 @@ __device__ __forceinline__ TcTile tc_tile(int local, int W, int NR) {
   return {(local % ntx) * (TC_M - 2) - 1, (local / ntx) * (NR - 2) - 1};
 }
 
-// 320 threads of one CTA per SM: up to 200 registers each (the epilogue
+// 320 threads of one CTA per SM: up to 192 registers each (the epilogue
 // keeps a column's running extremes over the scales for 64 rows)
 template <int ST>
-__global__ void __maxnreg__(200)
+__global__ void __maxnreg__(192)
     k_colfir_tc(const __grid_constant__ CUtensorMap map, const FrameDev *__restrict__ fr, Items it,
                 const float *__restrict__ edge, long PWb, const float *__restrict__ bands, TcGeom g, int NL,
                 DetectArgs da) {
