@@ -174,6 +174,33 @@ __device__ __forceinline__ bool split_sync_or(bool p) {
   return r != 0;
 }
 
+// Candidates of one tile, staged in shared memory and reserved in the call's
+// list once per tile (a 128 x 64 tile of a textured frame holds a few hundred).
+constexpr int TC_CANDS = 512;
+struct TcList {
+  int n;
+  int pad[7];
+  Blob rec[TC_CANDS];
+};
+
+__device__ __forceinline__ void tc_emit(const DetectArgs &a, TcList &tl, int s, int y, int x, int pol, float v) {
+  Blob b;
+  b.frame = a.frame;
+  b.x = x;
+  b.y = y;
+  b.scale = s;
+  b.polarity = pol;
+  b.response = v;
+  b.dx = b.dy = 0.f;
+  const int slot = atomicAdd(&tl.n, 1);
+  if (slot < TC_CANDS) {
+    tl.rec[slot] = b;
+  } else {
+    const unsigned long long idx = atomicAdd(&a.status->count, 1ull);
+    if (idx < (unsigned long long)a.cap) a.out[idx] = b;
+  }
+}
+
 // tie rule of one candidate against its 8 neighbours' extremes (pol = -1
 // mirrors the values): strictly above a neighbour earlier in (y, x) order or
 // with an earlier first scale, at least equal to a later one
@@ -199,8 +226,7 @@ __device__ __forceinline__ bool tc_beats(const float *m, const unsigned char *am
 // registers (left and right neighbours by shuffles, from shared memory at
 // the warp's edges); candidates are staged in the tile list.
 __device__ void tc_detect(const float *mx, const float *mn, const unsigned char *amx, const unsigned char *amn,
-                          const DetectArgs &a, int NR, int ew, int lane) {
-  TileList &tl = g_tl;
+                          TcList &tl, const DetectArgs &a, int NR, int ew, int lane) {
   constexpr unsigned FULL = 0xffffffffu;
   const int c = 32 * ew + lane;
   const int x = a.x0 + c;
@@ -229,12 +255,12 @@ __device__ void tc_detect(const float *mx, const float *mn, const unsigned char 
       const float m8 = fmaxf(xa, fmaxf(lx, fmaxf(vn, lxn)));  // maximum of the 8 neighbours
       if (vc > a.thr && vc >= m8) {
         const int s = amx[i * XB + c];
-        if (vc > m8 || tc_beats(mx, amx, i, c, 1, vc, s)) emit_blob(a, tl, s, y, x, 1, vc);
+        if (vc > m8 || tc_beats(mx, amx, i, c, 1, vc, s)) tc_emit(a, tl, s, y, x, 1, vc);
       }
       const float n8 = fminf(na, fminf(ln, fminf(wn, lnn)));
       if (a.dark && -wc > a.thr && wc <= n8) {
         const int s = amn[i * XB + c];
-        if (wc < n8 || tc_beats(mn, amn, i, c, -1, wc, s)) emit_blob(a, tl, s, y, x, -1, wc);
+        if (wc < n8 || tc_beats(mn, amn, i, c, -1, wc, s)) tc_emit(a, tl, s, y, x, -1, wc);
       }
     }
     xa = fmaxf(vc, lx), na = fminf(wc, ln);
@@ -243,11 +269,9 @@ __device__ void tc_detect(const float *mx, const float *mn, const unsigned char 
 }
 
 // the tile list's candidates to the call's list (one global reservation)
-__device__ void tc_flush(const DetectArgs &a, int t) {
-  TileList &tl = g_tl;
-  unsigned long long &s_base = g_tl_base;
+__device__ void tc_flush(const DetectArgs &a, TcList &tl, unsigned long long &s_base, int t) {
   epi_sync();
-  const int nloc = min(tl.n, TILE_CANDS);
+  const int nloc = min(tl.n, TC_CANDS);
   if (t == 0 && nloc > 0) s_base = atomicAdd(&a.status->count, (unsigned long long)nloc);
   epi_sync();
   for (int i = t; i < nloc; i += 128) {
@@ -261,6 +285,7 @@ struct TcSmem {
       d_empty[TC_MAXS], fin;
   uint32_t tmem;
   int abort;
+  unsigned long long base;  // the tile's reservation in the call's candidate list
 };
 
 // geometry of an item (tile) of a frame
@@ -272,10 +297,10 @@ __device__ __forceinline__ TcTile tc_tile(int local, int W, int NR) {
   return {(local % ntx) * (TC_M - 2) - 1, (local / ntx) * (NR - 2) - 1};
 }
 
-// 320 threads of one CTA per SM: up to 192 registers each (the epilogue
-// keeps a column's running extremes over the scales for 64 rows)
+// 320 threads of one CTA per SM (registers are allotted as for 12 warps: at
+// most 168 per thread)
 template <int ST>
-__global__ void __maxnreg__(192)
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_colfir_tc(const __grid_constant__ CUtensorMap map, const FrameDev *__restrict__ fr, Items it,
                 const float *__restrict__ edge, long PWb, const float *__restrict__ bands, TcGeom g, int NL,
                 DetectArgs da) {
@@ -296,6 +321,7 @@ __global__ void __maxnreg__(192)
   float *mn = mx + (size_t)NR * XS;
   unsigned char *amx = reinterpret_cast<unsigned char *>(mn + (size_t)NR * XS);  // [NR][XB]
   unsigned char *amn = amx + (size_t)NR * XB;
+  TcList &tl = *reinterpret_cast<TcList *>(amn + (size_t)NR * XB);  // 16-byte aligned (NR a multiple of 32)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int S = g.S;
   if (tid == 0) {
@@ -542,53 +568,51 @@ __global__ void __maxnreg__(192)
       float *resp = F.resp;
       const long plane = (long)H * W;
       // per-pixel extremes over the scales (first scale attaining them) and
-      // the responses: accumulator column n is output row NR - 1 - n.  Scale
-      // by scale: once a scale's accumulators are read, its columns go to
-      // the next tile's MMAs.
-      float vmax[64], vmin[64];
-      uint32_t pmax[8], pmin[8];  // first scale attaining the extreme, 4 bits per row
+      // the responses: accumulator column n is output row NR - 1 - n, read
+      // in blocks of 32 rows; after a scale's last block its columns go to
+      // the next tile's MMAs
+#pragma unroll 1
+      for (int n0 = 0; n0 < NR; n0 += 32) {
+        const bool last = n0 + 32 >= NR;
+        float vmax[32], vmin[32];
+        uint32_t pmax[4] = {0, 0, 0, 0}, pmin[4] = {0, 0, 0, 0};  // 4 bits per row
 #pragma unroll
-      for (int j = 0; j < 64; ++j) vmax[j] = -CUDART_INF_F, vmin[j] = CUDART_INF_F;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) pmax[j] = pmin[j] = 0u;
-      for (int s = 0; s < S; ++s) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (32 * h >= NR) break;
+        for (int j = 0; j < 32; ++j) vmax[j] = -CUDART_INF_F, vmin[j] = CUDART_INF_F;
+        for (int s = 0; s < S; ++s) {
           float v[32];
-          tmem_ld32(tmem + lanes + (uint32_t)(NR * s + 32 * h), v);
+          tmem_ld32(tmem + lanes + (uint32_t)(NR * s + n0), v);
+          if (last) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.d_empty[s]);  // scale s's columns free for the next tile
+          }
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const int n = 32 * h + j;
-            const uint32_t sh4 = 4u * (n & 7);
-            if (v[j] > vmax[n]) vmax[n] = v[j], pmax[n >> 3] = (pmax[n >> 3] & ~(15u << sh4)) | ((uint32_t)s << sh4);
-            if (v[j] < vmin[n]) vmin[n] = v[j], pmin[n >> 3] = (pmin[n >> 3] & ~(15u << sh4)) | ((uint32_t)s << sh4);
+            const uint32_t sh4 = 4u * (j & 7);
+            if (v[j] > vmax[j]) vmax[j] = v[j], pmax[j >> 3] = (pmax[j >> 3] & ~(15u << sh4)) | ((uint32_t)s << sh4);
+            if (v[j] < vmin[j]) vmin[j] = v[j], pmin[j >> 3] = (pmin[j >> 3] & ~(15u << sh4)) | ((uint32_t)s << sh4);
           }
           if (resp && xin && c >= 1 && c <= TC_M - 2) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              const int o = NR - 1 - (32 * h + j), y = t.r0 + o;
+              const int o = NR - 1 - (n0 + j), y = t.r0 + o;
               if (o >= 1 && o <= NR - 2 && y >= 0 && y < H) resp[s * plane + (long)y * W + x] = v[j];
             }
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sh.d_empty[s]);  // scale s's columns free for the next tile
-      }
 #pragma unroll
-      for (int n = 0; n < 64; ++n) {
-        if (n >= NR) break;
-        const int o = NR - 1 - n, y = t.r0 + o;
-        const bool in = xin && y >= 0 && y < H;
-        const uint32_t sh4 = 4u * (n & 7);
-        mx[o * XS + c] = in ? vmax[n] : -CUDART_INF_F;
-        mn[o * XS + c] = in ? vmin[n] : CUDART_INF_F;
-        amx[o * XB + c] = in ? (unsigned char)((pmax[n >> 3] >> sh4) & 15u) : (unsigned char)S;
-        amn[o * XB + c] = in ? (unsigned char)((pmin[n >> 3] >> sh4) & 15u) : (unsigned char)S;
+        for (int j = 0; j < 32; ++j) {
+          const int o = NR - 1 - (n0 + j), y = t.r0 + o;
+          const bool in = xin && y >= 0 && y < H;
+          const uint32_t sh4 = 4u * (j & 7);
+          mx[o * XS + c] = in ? vmax[j] : -CUDART_INF_F;
+          mn[o * XS + c] = in ? vmin[j] : CUDART_INF_F;
+          amx[o * XB + c] = in ? (unsigned char)((pmax[j >> 3] >> sh4) & 15u) : (unsigned char)S;
+          amn[o * XB + c] = in ? (unsigned char)((pmin[j >> 3] >> sh4) & 15u) : (unsigned char)S;
+        }
       }
       ++ntile;
-      if (ew == 0 && lane == 0) g_tl.n = 0;
+      if (ew == 0 && lane == 0) tl.n = 0;
       epi_sync();
       DetectArgs a = da;
       a.S = S;
@@ -597,8 +621,8 @@ __global__ void __maxnreg__(192)
       a.H = H;
       a.W = W;
       a.frame = F.index;
-      tc_detect(mx, mn, amx, amn, a, NR, ew, lane);
-      tc_flush(a, 32 * ew + lane);
+      tc_detect(mx, mn, amx, amn, tl, a, NR, ew, lane);
+      tc_flush(a, tl, sh.base, 32 * ew + lane);
     }
   }
   // ---------------- release the tensor memory ----------------
@@ -633,7 +657,8 @@ __global__ void __launch_bounds__(256) k_tc_bands(const Coef *__restrict__ coef,
 // dynamic shared memory of the pass with nl landing slots
 size_t tc_smem_bytes(const TcGeom &g, int nl, int st) {
   const size_t tapb = ((size_t)2 * g.gmax * 128 + 1023) / 1024 * 1024;
-  return 1024 + 2 * tapb + (size_t)nl * land_bytes(st) + (size_t)2 * g.NR * XS * 4 + (size_t)2 * g.NR * XB;
+  return 1024 + 2 * tapb + (size_t)nl * land_bytes(st) + (size_t)2 * g.NR * XS * 4 + (size_t)2 * g.NR * XB +
+         sizeof(TcList);
 }
 
 // landing slots that fit 216 KB of dynamic shared memory (the rest of the
