@@ -191,7 +191,7 @@ def algorithmic(name, S, HW, taps, s_in=4.0, s_b=4.0):
     s_in bytes per input pixel, s_b per stored plane element."""
     if name in ("iir_row", "fir_row"):
         byts = s_in * HW + s_b * S * HW              # read frame, write S planes
-    elif name in ("iir_colseg", "iir_coldet", "fir_coldet"):
+    elif name in ("iir_colseg", "iir_coldet", "iir_colscan", "fir_coldet"):
         byts = s_b * S * HW                          # read S planes
     else:
         byts = 0.0
@@ -395,7 +395,9 @@ def measure_workload(args, name, steps, warmup, full=True):
             shapes, lc, _ = kf.kf_autotune(banks[bn].ctx, Xs, SCALES, ft, order, o, vscales)
             tuned[bn] = {"grid_mult": {p: m for p, m in zip(("row", "seg", "fold", "det"), shapes) if m >= 0}}
             if lc > 0:
-                tuned[bn]["segment_rows"] = lc
+                tuned[bn]["column_pass"] = f"segments of {lc} rows"
+            elif lc == 0:
+                tuned[bn]["column_pass"] = "single read"
 
     def run_bank(bn, frames, ft, order, profile=False, schedule=kf.KF_SCHED_BATCHED, use_graph=graph):
         banks[bn].run(frames, SCALES, ft, order, threshold=THRESHOLD, profile=profile, fir_kmax=wl["fir_kmax"],
@@ -907,10 +909,11 @@ def quartic_bytes(name, S, H, W, nch=15):
     channels): the differentiator reads the frame and writes the 15 channel
     planes (W x (H + 4): two rows beyond each end); the row pass reads them
     and writes S planes each; the segment-state pass reads those; the column
-    pass reads them and writes the 15 S output planes (H rows)."""
+    pass (either form) reads them and writes the 15 S output planes (H rows)."""
     P = (H + 4) * W
     return {"quartic_hpf": 4 * H * W + 4 * nch * P, "iir_row": nch * (4 * P + 4 * S * P),
-            "iir_colseg": nch * 4 * S * P, "iir_coldet": nch * (4 * S * P + 4 * S * H * W)}.get(name)
+            "iir_colseg": nch * 4 * S * P, "iir_coldet": nch * (4 * S * P + 4 * S * H * W),
+            "iir_colscan": nch * (4 * S * P + 4 * S * H * W)}.get(name)
 
 
 def run_quartic(args):

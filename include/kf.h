@@ -372,6 +372,27 @@ int kf_set_launch_shape(kf_ctx *ctx, int type, int pass, int grid_mult);
  * FP32 rounding.  Errors: KF_EINVAL. */
 int kf_set_segment_length(kf_ctx *ctx, int type, int rows);
 
+/* Column pass of a recursive bank on this context (Sec. 5: the column blur
+ * of the separable filter, both one-sided recursions of eq A6 along y).
+ *   KF_COLUMN_SINGLE_READ: each plane tile is read from device
+ *     memory once; the carries of the recursions between tiles are exchanged
+ *     while the tiles stay in shared memory (clusters of 8 tiles of 32 rows;
+ *     between clusters through end states published in device memory and
+ *     folded in a fixed order, so results repeat bit for bit).  Used for
+ *     calls whose tallest frame's column strips fit on the GPU at once, with
+ *     the segment passes otherwise.  With gating, every tile is still read
+ *     (the carries need it); the final pass and the detector run on the
+ *     selected tiles.
+ *   KF_COLUMN_SEGMENTS (default): the segment end states, the carry fold
+ *     and the final column pass as three passes (the planes are read twice;
+ *     no pass waits on another block, and on the measured workloads this is
+ *     the faster form).
+ * kf_autotune times both and keeps the faster.  Results agree to FP32
+ * rounding.  Errors: KF_EINVAL. */
+#define KF_COLUMN_SINGLE_READ 0
+#define KF_COLUMN_SEGMENTS 1
+int kf_set_column_pass(kf_ctx *ctx, int type, int mode);
+
 /* Failure-detection test hook.  polls > 0: the column pass of the recursive
  * banks issues no copy to its shared-memory load barrier, so that its bounded
  * wait (at most `polls` polls, each parking the warp for about a microsecond)
@@ -385,13 +406,15 @@ int kf_set_wait_limit(kf_ctx *ctx, int polls);
 
 /* Autotuner: run the bank on these frames (as kf_filter_bank would, opts as
  * there) once per candidate shape (grid_mult 1, 2, 4, 0) and, for the
- * recursive banks, per segment length (64, 32); time every pass with CUDA
- * events on the context stream; keep for `type` the segment length with the
- * smallest sum of per-pass best times and for each pass its fastest shape.
- * chosen (host, KF_NPASS + 1 entries, may be NULL) receives the shapes
- * (passes the type lacks: -1) and, last, the segment length (-1 for the FIR
- * bank); ms_out (host, KF_NPASS x 4, may be NULL) the per-pass times of the
- * shape candidates at the chosen segment length (ms).
+ * recursive banks, per column pass (segments of 64 rows, of 32 rows, the
+ * single-read pass); time every pass with CUDA events on the context
+ * stream; keep for `type` the column pass with the smallest sum of per-pass
+ * best times and for each pass its fastest shape.  chosen (host, KF_NPASS +
+ * 1 entries, may be NULL) receives the shapes (passes the type or the
+ * chosen column pass lacks: -1) and, last, the segment length (0: the
+ * single-read column pass; -1 for the FIR bank); ms_out (host, KF_NPASS x
+ * 4, may be NULL) the per-pass times of the shape candidates at the chosen
+ * column pass (ms).
  * Leaves the last candidate's result as the context's bank result.
  * Synchronises the context stream.  Errors: those of kf_filter_bank. */
 int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes,

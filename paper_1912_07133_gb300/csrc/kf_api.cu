@@ -27,6 +27,8 @@ struct kf_ctx {
   size_t edge_floats = 0;
   float *carry = nullptr;
   size_t carry_floats = 0;
+  float *scan = nullptr;  // single-read column pass: ticket, flags, super-tile states
+  size_t scan_floats = 0;
   double *lambdas = nullptr;
   double *dwork = nullptr;
   int dwork_nmax = 0;
@@ -104,6 +106,8 @@ struct kf_ctx {
   int grid_mult[KF_NTYPES][KF_NPASS] = {};
   int seg_len[KF_NTYPES] = {64, 64, 64, 64};  // recursive banks: column segment length (kf_set_segment_length)
   bool seg_chosen[KF_NTYPES] = {false, false, false, false};  // set by kf_set_segment_length or kf_autotune
+  // recursive banks: column pass (kf_set_column_pass)
+  int column_pass[KF_NTYPES] = {KF_COLUMN_SEGMENTS, KF_COLUMN_SEGMENTS, KF_COLUMN_SEGMENTS, KF_COLUMN_SEGMENTS};
   std::vector<int> last_H, last_W;  // frame sizes of the last bank call
   // proposal network: FP32 masters, Adam moments, bf16 working copy, gradient, loss
   float *net_master = nullptr, *net_m = nullptr, *net_v = nullptr, *net_g = nullptr, *net_loss = nullptr;
@@ -399,6 +403,7 @@ std::vector<long long> call_key(const kf_ctx *ctx, const kf_frame *frames, int n
   }
   for (int p = 0; p < KF_NPASS; ++p) k.push_back(ctx->grid_mult[type][p]);
   k.push_back(ctx->seg_len[type]);
+  k.push_back(ctx->column_pass[type]);
   long long t;
   std::memcpy(&t, &o.threshold, sizeof t);
   k.push_back(t);
@@ -471,6 +476,7 @@ void kf_destroy(kf_ctx *ctx) {
   cudaFree(ctx->P);
   cudaFree(ctx->edge);
   cudaFree(ctx->carry);
+  cudaFree(ctx->scan);
   for (auto &d : ctx->designs) cudaFree(d.d_coef), cudaFree(d.d_bands);
   cudaFree(ctx->sorted);
   cudaFree(ctx->sort_work);
@@ -633,6 +639,10 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   const bool tcpass = !iir && ctx->cur->tc_ok &&
                       kf::fir_tc_applies(nscales, opts.storage, opts.neighbourhood, dbank || ctx->q_chan >= 0,
                                          maxPW, rows_all);
+  // the single-read column pass of the recursive banks (calls whose tallest
+  // frame's column strips fit on the GPU at once); else the segment passes
+  const bool use_scan = iir && ctx->column_pass[type] == KF_COLUMN_SINGLE_READ &&
+                        kf::iir_scan_fits(type, nstate, opts.storage, nscales, (int)maxH);
   // ---- layout: every frame resident in one plane row space of pitch PWb ----
   const long PWb = maxPW;
   std::vector<kf::FrameDev> fd(nframes);
@@ -670,7 +680,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     d.vscale = fr.value_scale == 0.0f ? 1.0f : fr.value_scale;
     d.H = fr.height;
     d.W = fr.width;
-    d.nseg = iir ? kf::iir_segments(fr.height, ctx->seg_len[type]) : 0;
+    d.nseg = (iir && !use_scan) ? kf::iir_segments(fr.height, ctx->seg_len[type]) : 0;
     d.index = f;
     prows += (long)nscales * fr.height;
     roff += (long)nscales * fr.height * fr.width;
@@ -679,7 +689,15 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   const size_t plane_floats = ((size_t)prows * PWb * kf::store_bytes(opts.storage) + 3) / 4;
   if ((rc = grow(ctx, &ctx->P, &ctx->P_floats, plane_floats, "planes"))) return rc;
   if ((rc = grow(ctx, &ctx->edge, &ctx->edge_floats, (size_t)nframes * nscales * 2 * PWb, "edge rows"))) return rc;
-  if (iir && (rc = grow(ctx, &ctx->carry, &ctx->carry_floats, std::max(coff, (size_t)1), "carries"))) return rc;
+  if (iir && !use_scan && (rc = grow(ctx, &ctx->carry, &ctx->carry_floats, std::max(coff, (size_t)1), "carries")))
+    return rc;
+  if (use_scan) {
+    long U = 0;
+    for (int f = 0; f < nframes; ++f) U += kf::iir_scan_items(fd[f].H, fd[f].W);
+    if (U > INT32_MAX / 4) return fail(ctx, KF_EINVAL, "too many column tiles in one call: split the batch");
+    const size_t nb = kf::iir_scan_bytes(U, nscales, nfs);
+    if ((rc = grow(ctx, &ctx->scan, &ctx->scan_floats, (nb + 3) / 4, "column-pass states"))) return rc;
+  }
   // ---- work-item lists of the launches --------------------------------------
   struct L {
     int pass, nt, n, total;
@@ -688,8 +706,10 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   std::vector<int> pool;
   std::vector<L> ls;
   constexpr int PASS_COMB = 99;  // the derivative bank's combine + detect launch
+  constexpr int PASS_SCAN = 98;  // the single-read column pass of the recursive banks
   auto items = [&](int pass, int f) {
     if (pass == PASS_COMB) return kf::deriv_items(fd[f].H, fd[f].W);
+    if (pass == PASS_SCAN) return kf::iir_scan_items(fd[f].H, fd[f].W);
     return iir ? kf::iir_items(pass, fd[f].H, fd[f].W, nscales, ctx->seg_len[type])
                : kf::fir_items(pass, fd[f].H, fd[f].W, nscales, opts.neighbourhood, tcpass);
   };
@@ -740,6 +760,15 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     for (int f = 0; f < nframes; ++f) fl[f] = f;
     fits &= add(PASS_COMB, fl, 0);
   }
+  if (use_scan) {
+    if (opts.schedule == KF_SCHED_PER_FRAME) {
+      for (int f = 0; f < nframes; ++f) fits &= add(PASS_SCAN, {f}, 0);
+    } else {
+      std::vector<int> fl(nframes);
+      for (int f = 0; f < nframes; ++f) fl[f] = f;
+      fits &= add(PASS_SCAN, fl, 0);
+    }
+  }
   if (!fits) return fail(ctx, KF_EINVAL, "too many work items in one call: split the batch");
   for (const L &l : ls)
     if (iir && l.pass == kf::PASS_ROW && l.nt == 0) return fail(ctx, KF_EINVAL, "frame too wide for the row pass");
@@ -767,6 +796,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     x.it.total = l.total;
     x.nt = l.nt;
     if (l.pass == PASS_COMB) plan.comb = x;
+    else if (l.pass == PASS_SCAN) plan.scan.push_back(x);
     else plan.pass[l.pass].push_back(x);
   }
   // ---- gating: buffers and the gated launches --------------------------------
@@ -815,7 +845,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
       return cuda_fail(ctx, ee, "gate counts");
     const int rows = iir ? ctx->seg_len[type]
                          : (tcpass ? kf::fir_tc_tile_rows(nscales) : kf::fir_tile_rows(opts.neighbourhood));
-    if (kf::gate_select_tiles(plan.fr, full_det, ctx->g_act, tcpass ? kf::fir_tc_tile_cols() : TW_COL, rows,
+    if (!use_scan &&
+        kf::gate_select_tiles(plan.fr, full_det, ctx->g_act, tcpass ? kf::fir_tc_tile_cols() : TW_COL, rows,
                               ctx->g_sel[0], ctx->g_count, st))
       return cuda_fail(ctx, cudaGetLastError(), "gate selection");
     if (!iir && kf::gate_select_rows(plan.fr, full_row, ctx->g_act, kf::fir_row_segment(), kf::fir_row_rows(),
@@ -837,6 +868,8 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   a.storage = opts.storage;  // KF_DTYPE_F32 / F16 / BF16 equal ST_F32 / ST_F16 / ST_BF16
   a.edge = ctx->edge;
   a.carry = ctx->carry;
+  a.scan = use_scan ? ctx->scan : nullptr;
+  a.gate_act = gate ? ctx->g_act : nullptr;
   a.blobs = ctx->blobs;
   a.cap = ctx->blob_cap;
   a.status = ctx->status;
@@ -1035,6 +1068,19 @@ int kf_set_segment_length(kf_ctx *ctx, int type, int rows) {
   return KF_OK;
 }
 
+int kf_set_column_pass(kf_ctx *ctx, int type, int mode) {
+  if (!ctx) return fail(nullptr, KF_EINVAL, "kf_set_column_pass: ctx is NULL");
+  if (type != KF_IIR_REPEATED_POLE && type != KF_IIR_BUTTERWORTH)
+    return fail(ctx, KF_EINVAL, "the column pass applies to the recursive banks only");
+  if (mode != KF_COLUMN_SINGLE_READ && mode != KF_COLUMN_SEGMENTS)
+    return fail(ctx, KF_EINVAL, "unknown column pass %d", mode);
+  if (ctx->column_pass[type] != mode) {
+    drop_graphs(ctx);
+    ctx->column_pass[type] = mode;
+  }
+  return KF_OK;
+}
+
 int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *scales, int nscales, int type,
                 int order, const kf_bank_opts *opts_in, int32_t *chosen, float *ms_out) {
   if (!ctx) return fail(nullptr, KF_EINVAL, "kf_autotune: ctx is NULL");
@@ -1052,18 +1098,22 @@ int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *
     if (n == "iir_row" || n == "fir_row") return (int)KF_PASS_ROW;
     if (n == "iir_colseg") return (int)KF_PASS_SEG;
     if (n == "iir_colfold") return (int)KF_PASS_FOLD;
-    if (n == "iir_coldet" || n == "fir_coldet") return (int)KF_PASS_DET;
+    if (n == "iir_coldet" || n == "iir_colscan" || n == "fir_coldet") return (int)KF_PASS_DET;
     return -1;
   };
   cudaError_t e;
   const bool iir = !is_fir(type);
-  const int saved_lc = ctx->seg_len[type];
-  // per candidate (segment length, shape): per-pass time
-  const int nlc = iir ? 2 : 1;
-  const int lcs[2] = {64, 32};
-  float t[2][4][KF_NPASS];
+  const int saved_lc = ctx->seg_len[type], saved_col = ctx->column_pass[type];
+  // per candidate (column pass: segments of 64 or 32 rows, or the
+  // single-read pass (0); shape): per-pass time
+  const int nlc = iir ? 3 : 1;
+  const int lcs[3] = {64, 32, 0};
+  float t[3][4][KF_NPASS];
   for (int l = 0; l < nlc; ++l) {
-    if (iir) ctx->seg_len[type] = lcs[l];
+    if (iir) {
+      ctx->seg_len[type] = lcs[l] ? lcs[l] : saved_lc;
+      ctx->column_pass[type] = lcs[l] ? KF_COLUMN_SEGMENTS : KF_COLUMN_SINGLE_READ;
+    }
     for (int c = 0; c < 4; ++c) {
       for (int p = 0; p < KF_NPASS; ++p) ctx->grid_mult[type][p] = kCand[c];
       float acc[KF_NPASS] = {0, 0, 0, 0};
@@ -1073,6 +1123,7 @@ int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *
         if (rc) {
           for (int p = 0; p < KF_NPASS; ++p) ctx->grid_mult[type][p] = saved[p];
           ctx->seg_len[type] = saved_lc;
+          ctx->column_pass[type] = saved_col;
           return rc;
         }
         if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "autotune");
@@ -1095,7 +1146,7 @@ int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *
   // the segment length with the smaller sum wins (the row pass does not depend on it)
   int best_l = 0;
   float best_sum = -1.f;
-  int best_c[2][KF_NPASS];
+  int best_c[3][KF_NPASS];
   for (int l = 0; l < nlc; ++l) {
     float sum = 0.f;
     for (int p = 0; p < KF_NPASS; ++p) {
@@ -1108,8 +1159,9 @@ int kf_autotune(kf_ctx *ctx, const kf_frame *frames, int nframes, const double *
     if (best_sum < 0.f || sum < best_sum) best_sum = sum, best_l = l;
   }
   if (iir) {
-    ctx->seg_len[type] = lcs[best_l];
-    ctx->seg_chosen[type] = true;
+    ctx->seg_len[type] = lcs[best_l] ? lcs[best_l] : saved_lc;
+    ctx->column_pass[type] = lcs[best_l] ? KF_COLUMN_SEGMENTS : KF_COLUMN_SINGLE_READ;
+    if (lcs[best_l]) ctx->seg_chosen[type] = true;
   }
   for (int p = 0; p < KF_NPASS; ++p) {
     const int b = best_c[best_l][p];

@@ -15,4 +15,15 @@ int run_iir_chain(int K, const Plan &p, const BankArgs &a, cudaStream_t st) {
   }
 }
 
+bool iir_scan_fits_chain(int K, int storage, int S, int maxH) {
+  switch (K) {
+    case 2: return colscan_fits_st<Chain<2>>(storage, S, maxH);
+    case 3: return colscan_fits_st<Chain<3>>(storage, S, maxH);
+    case 4: return colscan_fits_st<Chain<4>>(storage, S, maxH);
+    case 5: return colscan_fits_st<Chain<5>>(storage, S, maxH);
+    case 6: return colscan_fits_st<Chain<6>>(storage, S, maxH);
+    default: return false;
+  }
+}
+
 }  // namespace kf

@@ -13,4 +13,13 @@ int run_iir_modes(int NM, const Plan &p, const BankArgs &a, cudaStream_t st) {
   }
 }
 
+bool iir_scan_fits_modes(int NM, int storage, int S, int maxH) {
+  switch (NM) {
+    case 1: return colscan_fits_st<Modes<1>>(storage, S, maxH);
+    case 2: return colscan_fits_st<Modes<2>>(storage, S, maxH);
+    case 3: return colscan_fits_st<Modes<3>>(storage, S, maxH);
+    default: return false;
+  }
+}
+
 }  // namespace kf

@@ -36,6 +36,8 @@
 #include "kf_internal.h"
 #include "kf_tma.cuh"
 
+#include <cooperative_groups.h>
+
 namespace kf {
 
 namespace {
@@ -100,6 +102,23 @@ struct Chain {
   __device__ __forceinline__ void load(const float *src, long stride) {
 #pragma unroll
     for (int j = 0; j < KK; ++j) t[j] = src[j * stride];
+  }
+  // powers of Phi as records (the first column of the lower-triangular
+  // Toeplitz Phi^n): identity, Phi^(CH m) from the design's table, and
+  // this += pw x v (pw a power, v a state or another power)
+  __device__ __forceinline__ void identity() {
+#pragma unroll
+    for (int j = 0; j < KK; ++j) t[j] = j == 0 ? 1.f : 0.f;
+  }
+  __device__ __forceinline__ void load_pow(const Coef &c, int m) {
+#pragma unroll
+    for (int i = 0; i < KK; ++i) t[i] = c.phiM[m - 1][i];
+  }
+  __device__ __forceinline__ void mac(const Chain &pw, const Chain &v) { combine(pw.t, v); }
+  // state published by another CTA of the grid (read past L1)
+  __device__ __forceinline__ void load_cg(const float *src, long stride) {
+#pragma unroll
+    for (int j = 0; j < KK; ++j) t[j] = __ldcg(src + j * stride);
   }
   __device__ __forceinline__ Chain shfl_up(int d) const {
     Chain r;
@@ -171,6 +190,20 @@ struct Modes {
   __device__ __forceinline__ void load(const float *src, long stride) {
 #pragma unroll
     for (int i = 0; i < NM; ++i) tr[i] = src[(2 * i) * stride], ti[i] = src[(2 * i + 1) * stride];
+  }
+  // powers of Phi (diagonal: z^n per mode), as for Chain
+  __device__ __forceinline__ void identity() {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) tr[i] = 1.f, ti[i] = 0.f;
+  }
+  __device__ __forceinline__ void load_pow(const Coef &c, int m) {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) tr[i] = c.zMr[m - 1][i], ti[i] = c.zMi[m - 1][i];
+  }
+  __device__ __forceinline__ void mac(const Modes &pw, const Modes &v) { combine_z(pw.tr, pw.ti, v); }
+  __device__ __forceinline__ void load_cg(const float *src, long stride) {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) tr[i] = __ldcg(src + (2 * i) * stride), ti[i] = __ldcg(src + (2 * i + 1) * stride);
   }
   __device__ __forceinline__ Modes shfl_up(int d) const {
     Modes r;
@@ -714,6 +747,411 @@ __global__ void __launch_bounds__(512) __maxnreg__(LC == 32 ? Rec::kColdetRegs32
   }
 }
 
+// ---------------------------------------------------------------------------
+// single-read column pass
+// ---------------------------------------------------------------------------
+// k_colscan reads every plane once: the carries of the column recursions are
+// found while the tiles sit in shared memory, instead of by a separate pass
+// over the planes (k_colseg + k_colfold).  A cluster of SCAN_G CTAs takes a
+// super-tile: SCAN_G consecutive 32-row tiles (34 rows with the detector's
+// halo) of one 32-column strip, all scales.  Per super-tile:
+//   1. each CTA loads its tile (TMA) and runs both recursions from the zero
+//      state over its segment (the same segments as k_colseg): e+, e-;
+//   2. through distributed shared memory each CTA folds the end states of the
+//      tiles above it (P = sum_i Phi^(32(r-1-i)) e+_i) and below it (Q); the
+//      bottom and top CTAs form the super-tile's end states A+ and A- and
+//      publish them in global memory (a flag per super-tile and direction);
+//   3. the bottom CTA folds the carry entering the super-tile from above,
+//      C+ = Phi^256 (... (Phi^256 hold(top) + A+_0) ...) + A+_(k-1), from
+//      the published end states of the strip's super-tiles above it, in
+//      that fixed order; the top CTA folds C- from the super-tiles below,
+//      starting at the held bottom.  A fixed order makes the result the same
+//      on every run and for every schedule of the super-tiles;
+//   4. each CTA's carries are Phi^(32 r) C+ + P and Phi^(32 (n-1-r)) C- + Q,
+//      and the final recursions, the response and the detector run on the
+//      tile in shared memory as in k_coldet.
+// Super-tiles are taken in ticket order, strip by strip from the top, so a
+// super-tile waits only on super-tiles that already hold a cluster or that
+// need none of its results; the host launches this pass only when twice the
+// super-tiles of a strip fit on the GPU at once.  Every wait is bounded by
+// wall time; a wait that gives up (or a call that has already failed) turns
+// the rest of the launch into no-ops that still pass every cluster barrier.
+constexpr int SCAN_G = 8;           // tiles (CTAs) per cluster
+constexpr int SCAN_LC = 32;         // rows per tile (one CH chunk: Phi^32 = phiM[0])
+constexpr unsigned long long SCAN_WAIT_NS = 2000000000ull;  // 2 s
+constexpr int SCAN_BATCH = 4;       // end states of other super-tiles loaded at once
+
+struct ScanArgs {
+  int *ticket;     // launch ticket counter (zero before the launch)
+  unsigned *flag;  // [2][U]: 1 once the super-tile's end state of the direction is published
+  float *data;     // [U][2 dir][NF][S][32]: the super-tiles' zero-state end states
+  int U;           // super-tiles of the launch
+  // gated calls: the active-tile maps (64 x 64 tiles, FrameDev.aoff); the
+  // final recursions and the detector run only on tiles whose interior meets
+  // an active tile (the loads and end states run everywhere: the carries need
+  // every tile).  Null: every tile.
+  const unsigned char *act;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait until the n flags flag[0..n) are all >= 1 (the warp polls 32 at a
+// time).  Returns false if a wait gave up (error 4 recorded) or the call has
+// already failed.
+__device__ __forceinline__ bool scan_wait_all(const unsigned *flag, int n, DevStatus *st) {
+  const int lane = threadIdx.x & 31;
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int j = j0 + lane;
+    unsigned long long t0 = 0;
+    for (unsigned i = 0;; ++i) {
+      const bool ok = j >= n || ld_acquire_u32(flag + j) >= 1u;
+      if (__all_sync(0xffffffffu, ok)) break;
+      if (*reinterpret_cast<volatile int *>(&st->error)) return false;
+      const unsigned long long now = global_ns();
+      if (i == 0) {
+        t0 = now;
+      } else if (now - t0 > SCAN_WAIT_NS) {
+        if (lane == 0) atomicCAS(&st->error, 0, 4);
+        return false;
+      }
+      __nanosleep(100);
+    }
+  }
+  return true;
+}
+
+// Step 3 of k_colscan for direction dir (0: causal, by the super-tile's
+// bottom CTA; 1: anticausal, by its top CTA), all threads of the CTA: the
+// super-tile's end state A = Phi^32 P + e of this tile (P: the folded end
+// states of the cluster's other tiles on the far side), published in global
+// memory; then the carry entering the super-tile, folded in a fixed order
+// from the held edge row and the published end states of the strip's
+// super-tiles on the near side, and stored into every CTA of the cluster.
+// Kept out of line: the kernel's main path needs its registers.
+template <class Rec>
+__device__ __noinline__ void colscan_publish(int dir, const Coef &cf, const float *agg, const float *pq,
+                                             float *cin, ScanArgs sa, long DS, int u, int sup, int nsup,
+                                             int ntile, int nreal, float edge_row, DevStatus *status) {
+  namespace cg = cooperative_groups;
+  const int lane = threadIdx.x & 31, s = threadIdx.x >> 5;
+  const long SS = DS / Rec::NF, o = (long)dir * DS + s * 32 + lane;
+  Rec A, P;
+  A.load(agg + o, SS);
+  P.load(pq + o, SS);
+  A.combine_m(cf, 1, P);
+  A.store(sa.data + (long)u * 2 * DS + o, SS);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) st_release_u32(sa.flag + (long)dir * sa.U + u, 1u);
+  Rec C;
+  C.hold(cf, edge_row);
+  // causal: the super-tiles above, from the strip's first; anticausal: those
+  // below, from the strip's last (nlast tiles) up
+  const int n = dir == 0 ? sup : nsup - 1 - sup;
+  const int ufar = dir == 0 ? u - sup : u - sup + nsup - 1, step = dir == 0 ? 1 : -1;
+  const int nlast = ntile - (nsup - 1) * SCAN_G;
+  if (scan_wait_all(sa.flag + (dir == 0 ? (long)ufar : (long)sa.U + u + 1), n, status))
+    for (int j0 = 0; j0 < n; j0 += SCAN_BATCH) {
+      Rec e[SCAN_BATCH];
+#pragma unroll
+      for (int q = 0; q < SCAN_BATCH; ++q)
+        if (j0 + q < n) e[q].load_cg(sa.data + (long)(ufar + step * (j0 + q)) * 2 * DS + o, SS);
+#pragma unroll
+      for (int q = 0; q < SCAN_BATCH; ++q)
+        if (j0 + q < n) {
+          // C enters the super-tile being added: whole (SCAN_G tiles) unless
+          // it is the strip's last
+          e[q].combine_m(cf, (dir == 1 && j0 + q == 0) ? nlast : SCAN_G, C);
+          C = e[q];
+        }
+    }
+  cg::cluster_group cl = cg::this_cluster();
+  for (int i = 0; i < nreal; ++i) C.store(cl.map_shared_rank(cin, i) + o, SS);
+}
+
+template <class Rec, int ST>
+__host__ __device__ constexpr int colscan_scratch_floats(int S) {
+  // detector scratch, or (aliasing it before the detector runs) the tile's
+  // end states, the super-tile carries and the end states of the tiles above
+  // and below: 3 x [2][NF][S][32]
+  return (SCAN_LC + 2) * 32 * 2 + ((SCAN_LC + 2) * 32 * 2 + 3) / 4 > 6 * Rec::NF * S * 32
+             ? (SCAN_LC + 2) * 32 * 2 + ((SCAN_LC + 2) * 32 * 2 + 3) / 4
+             : 6 * Rec::NF * S * 32;
+}
+
+template <class Rec, int ST>
+__global__ void __launch_bounds__(512) __maxnreg__(Rec::kColdetRegs32) k_colscan(const __grid_constant__ CUtensorMap map,
+                                                const FrameDev *__restrict__ fr, Items it, long PWb,
+                                                const float *__restrict__ edge,
+                                                const Coef *__restrict__ coef, int S, ScanArgs sa,
+                                                DetectArgs da) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  using T = typename Store<ST>::T;
+  constexpr bool F32 = ST == ST_F32;
+  constexpr int LC = SCAN_LC, NR = LC + 2, G = SCAN_G, NF = Rec::NF;
+  constexpr int REG = coldet_region_floats<ST, LC>();
+  constexpr int LD = F32 ? CLD : 32;
+  constexpr int C16B = coldet_c16b(NR);
+  extern __shared__ __align__(128) float sm_raw[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ FrameDev s_fr;
+  __shared__ int s_ticket, s_bad;
+  float *buf = align_smem(sm_raw);   // [S][REG]
+  float *red = buf + (long)S * REG;  // detector scratch
+  const long SS = (long)S * 32;      // stride of a state component in agg / cin
+  float *agg = red;                  // [2][NF][S][32] this tile's zero-state end states
+  float *cin = red + 2 * NF * SS;    // [2][NF][S][32] carries entering the super-tile
+  float *pq = red + 4 * NF * SS;     // [2][NF][S][32] end states of the tiles above (P) and below (Q)
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, s = tid >> 5;
+  constexpr int XA = F32 ? 4 : 8;
+  constexpr int BW = F32 ? CLD : CBOX16;
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  const Coef &cf = coef[s];
+  const long DS = (long)NF * SS;  // floats of one (dir, kind) record of a super-tile
+  uint32_t phase = 0;
+  int k = 0;
+  for (;;) {
+    if (rank == 0 && tid == 0) {
+      const int u = atomicAdd(sa.ticket, 1);
+      for (int i = 0; i < G; ++i) *cl.map_shared_rank(&s_ticket, i) = u;
+    }
+    cl.sync();  // B0: the ticket is known; the previous super-tile is done everywhere
+    const int u = s_ticket;
+    if (u >= sa.U) break;
+    int local;
+    k = item_frame(it, u, k, local);
+    stage_frame(&s_fr, fr, it, k);
+    if (tid == 0) s_bad = *reinterpret_cast<volatile int *>(&da.status->error);
+    __syncthreads();
+    const FrameDev &F = s_fr;
+    const bool bad = s_bad != 0;
+    const int H = F.H, W = F.W;
+    const int ntile = (H + LC - 1) / LC, nsup = (ntile + G - 1) / G;
+    const int strip = local / nsup, sup = local % nsup;
+    const int nreal = min(G, ntile - sup * G);
+    const bool real = rank < nreal;
+    const int t = sup * G + rank;
+    const int x0 = strip * TW - 1;
+    const int off = ((x0 % XA) + XA) % XA;
+    const int xv = min(max(x0 + lane, 0), W - 1);
+    const int r0 = t * LC - 1;
+    const float *ed = edge + F.eoff + (long)s * 2 * PWb + xv;
+    float *b = buf + (long)s * REG + (F32 ? off : 0) + lane;
+    // 1. load and zero-state end states
+    if (real && !bad) {
+      typename Rec::View v;  // loaded where used: fewer registers live across the loop
+      v.load(cf);
+      if (tid == 0 && !da.wait_test) {
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&mbar, (uint32_t)(S * NR * BW * sizeof(T)));
+        for (int q = 0; q < S; ++q) {
+          void *dst = F32 ? (void *)(buf + (long)q * REG) : (void *)((char *)(buf + (long)q * REG) + C16B);
+          if (!tma_load_2d(dst, &map, x0 - off, (int)(F.prow + (long)q * H + r0), &mbar, (int)sizeof(T)))
+            atomicExch(&da.status->error, 2);
+        }
+      }
+      const bool ok = mbar_wait_bounded(&mbar, phase, da.wait_test ? da.wait_test : CWAIT_LIMIT);
+      phase ^= 1u;
+      if (!ok && tid == 0) atomicCAS(&da.status->error, 0, 1);
+      const bool outside = r0 < 0 || r0 + NR > H;
+      float top = 0.f, bot = 0.f;
+      if (outside) {
+        top = ed[0];
+        bot = ed[PWb];
+      }
+      // causal segment: tile rows 0 .. LC-1; every row is widened to f32 (and
+      // rows outside the frame take the held edge rows) in place
+      const T *b16 = reinterpret_cast<const T *>(reinterpret_cast<const char *>(buf + (long)s * REG) + C16B) +
+                     off + lane;
+      Rec e;
+      e.zero();
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        const int y = r0 + i;
+        float in = F32 ? b[i * LD] : Store<ST>::ld(b16[i * CBOX16]);
+        if (outside) in = y < 0 ? top : (y >= H ? bot : in);
+        if (!F32 || outside) b[i * LD] = in;
+        if (i < LC) e.push(v, in);
+        if ((i & 7) == 7) __syncwarp();
+      }
+      __syncwarp();
+      e.store(agg + s * 32 + lane, SS);
+      // anticausal segment: tile rows NR-1 down to 2
+      e.zero();
+#pragma unroll
+      for (int i = NR - 1; i >= 2; --i) e.push(v, b[i * LD]);
+      e.store(agg + DS + s * 32 + lane, SS);
+    }
+    cl.sync();  // B1: every tile's end states are visible to the cluster
+    // 2. end states of the tiles above (P) and below (Q) this one, kept in
+    // shared memory until the carries arrive
+    if (real) {
+      Rec P;
+      P.zero();
+      for (int i = 0; i < rank; ++i) {
+        Rec n;
+        n.load(cl.map_shared_rank(agg, i) + s * 32 + lane, SS);
+        n.combine_m(cf, 1, P);  // Phi^32 P + e_i
+        P = n;
+      }
+      P.store(pq + s * 32 + lane, SS);
+      P.zero();
+      for (int i = nreal - 1; i > rank; --i) {
+        Rec n;
+        n.load(cl.map_shared_rank(agg, i) + DS + s * 32 + lane, SS);
+        n.combine_m(cf, 1, P);
+        P = n;
+      }
+      P.store(pq + DS + s * 32 + lane, SS);
+    }
+    // 3. the super-tile's end states and the carries entering it
+    if (rank == nreal - 1)
+      colscan_publish<Rec>(0, cf, agg, pq, cin, sa, DS, u, sup, nsup, ntile, nreal, ed[0], da.status);
+    if (rank == 0)
+      colscan_publish<Rec>(1, cf, agg, pq, cin, sa, DS, u, sup, nsup, ntile, nreal, ed[PWb], da.status);
+    cl.sync();  // B2: the super-tile's carries are in every CTA
+    // 4. this tile's carries, final recursions, response, detector
+    if (real && !bad && (!sa.act || any_active(F, sa.act, strip * TW, strip * TW + TW, t * LC, t * LC + LC))) {
+      Rec cp, cq;
+      cp.load(cin + s * 32 + lane, SS);
+      cq.load(cin + DS + s * 32 + lane, SS);
+      if (rank > 0) {
+        Rec n;
+        n.load(pq + s * 32 + lane, SS);
+        n.combine_m(cf, rank, cp);
+        cp = n;
+      }
+      if (rank < nreal - 1) {
+        Rec n;
+        n.load(pq + DS + s * 32 + lane, SS);
+        n.combine_m(cf, nreal - 1 - rank, cq);
+        cq = n;
+      }
+      typename Rec::View v;
+      v.load(cf);
+      const float sgn = da.raw ? 1.f : -1.f;
+      float yp[NR];
+      Rec r = cp;
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        yp[i] = r.out(v);
+        r.push(v, b[i * LD]);
+      }
+      r = cq;
+#pragma unroll
+      for (int i = NR - 1; i >= 0; --i) {
+        const float in = b[i * LD];
+        b[i * LD] = sgn * (yp[i] + fmaf(v.b0, in, r.out(v)));
+        r.push(v, in);
+      }
+      __syncthreads();
+      DetectArgs a = da;
+      a.S = S;
+      a.NR = NR;
+      a.x0 = x0;
+      a.r0 = r0;
+      a.H = H;
+      a.W = W;
+      a.frame = F.index;
+      a.resp = F.resp;
+      a.rplane = F.rplane;
+      a.rpitch = F.rpitch;
+      a.rmx = F.rmx;
+      a.rmy = F.rmy;
+      a.ld = LD;
+      a.coff = F32 ? off : 0;
+      a.srows = REG / LD;
+      detect_tile(buf, red, a);
+      fence_proxy_async();  // generic accesses of the buffer before the next tile's async copies
+    }
+    __syncthreads();
+  }
+}
+
+template <class Rec, int ST>
+size_t colscan_smem(int S) {
+  return ((size_t)S * coldet_region_floats<ST, SCAN_LC>() + colscan_scratch_floats<Rec, ST>(S)) * sizeof(float) +
+         TMA_SMEM_ALIGN;
+}
+
+template <class Rec, int ST>
+cudaLaunchConfig_t colscan_config(int S, int nclusters, cudaStream_t st, cudaLaunchAttribute *attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nclusters * SCAN_G));
+  cfg.blockDim = dim3((unsigned)(32 * S));
+  cfg.dynamicSmemBytes = colscan_smem<Rec, ST>(S);
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = SCAN_G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// clusters of k_colscan<Rec, ST> resident on the current device at once (0:
+// the kernel cannot run), cached per (device, S)
+template <class Rec, int ST>
+int colscan_clusters(int S) {
+  constexpr int kMaxDev = 64;
+  static int cache[kMaxDev][MAXS + 1];
+  static bool attr_set[kMaxDev];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kMaxDev || S < 1 || S > MAXS) return 0;
+  if (cache[dev][S]) return cache[dev][S] > 0 ? cache[dev][S] : 0;
+  if (!attr_set[dev]) {
+    cudaFuncSetAttribute(k_colscan<Rec, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set[dev] = true;
+  }
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t cfg = colscan_config<Rec, ST>(S, 1, nullptr, at);
+  int n = 0;
+  if (cfg.dynamicSmemBytes > 200 * 1024 ||
+      cudaOccupancyMaxActiveClusters(&n, (void *)k_colscan<Rec, ST>, &cfg) != cudaSuccess)
+    n = 0;
+  cudaGetLastError();  // a failed query leaves no sticky error
+  cache[dev][S] = n > 0 ? n : -1;
+  return n;
+}
+
+// whether every super-tile of a strip of a frame of height maxH (and a
+// second such bank running at the same time) fits on the device at once
+template <class Rec, int ST>
+bool colscan_fits(int S, int maxH) {
+  const int nt = (maxH + SCAN_LC - 1) / SCAN_LC, nsup = (nt + SCAN_G - 1) / SCAN_G;
+  return colscan_clusters<Rec, ST>(S) >= 2 * nsup;
+}
+
+template <class Rec>
+bool colscan_fits_st(int storage, int S, int maxH) {
+  switch (storage) {
+    case ST_F32: return colscan_fits<Rec, ST_F32>(S, maxH);
+    case ST_F16: return colscan_fits<Rec, ST_F16>(S, maxH);
+    case ST_BF16: return colscan_fits<Rec, ST_BF16>(S, maxH);
+    default: return false;
+  }
+}
+
 template <class Rec, int ST, int LC>
 int run_iir_st(const Plan &p, const BankArgs &a, cudaStream_t st) {
   static bool attr = false;
@@ -721,6 +1159,7 @@ int run_iir_st(const Plan &p, const BankArgs &a, cudaStream_t st) {
     cudaFuncSetAttribute(k_row<Rec, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_row<Rec, ST == ST_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_coldet<Rec, ST, LC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_colscan<Rec, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   constexpr int NR = LC + 2;
@@ -771,6 +1210,40 @@ int run_iir_st(const Plan &p, const BankArgs &a, cudaStream_t st) {
     k_coldet<Rec, ST, LC><<<nb, 32 * a.S, det_smem, st>>>(map, p.fr, l.it, p.PWb, a.edge, a.coef, a.S, a.carry, da);
     a.prof->end(st);
   };
+  // single-read column pass: ticket and flags cleared, then one persistent
+  // launch of clusters over every super-tile of the call
+  auto scan = [&](const Launch &l) -> bool {
+    const int U = l.it.total;
+    const int ncl = colscan_clusters<Rec, ST>(a.S);
+    if (ncl < 1) return false;
+    CUtensorMap smap;
+    if (encode_plane_map(&smap, a.P, ST, p.PWb, p.prows, ST == ST_F32 ? CLD : CBOX16, SCAN_LC + 2)) return false;
+    ScanArgs sa;
+    sa.ticket = static_cast<int *>(a.scan);
+    sa.flag = reinterpret_cast<unsigned *>(static_cast<int *>(a.scan) + 32);
+    sa.data = reinterpret_cast<float *>(static_cast<char *>(a.scan) + ((size_t)(32 + 2 * (size_t)U) * 4 + 255) / 256 * 256);
+    sa.U = U;
+    sa.act = a.gate_act;
+    if (cudaMemsetAsync(a.scan, 0, (32 + 2 * (size_t)U) * sizeof(int), st) != cudaSuccess) return false;
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = colscan_config<Rec, ST>(a.S, std::min(ncl, std::max(U, 1)), st, at);
+    a.prof->begin("iir_colscan", st);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_colscan<Rec, ST>, smap, p.fr, l.it, p.PWb,
+                                             (const float *)a.edge, a.coef, a.S, sa, da);
+    a.prof->end(st);
+    return e == cudaSuccess;
+  };
+  if (a.scan) {
+    if (p.per_frame) {
+      for (int f = 0; f < p.nframes; ++f)
+        if (!row(p.pass[PASS_ROW][f]) || !scan(p.scan[f])) return -1;
+    } else {
+      for (const Launch &l : p.pass[PASS_ROW])
+        if (!row(l)) return -1;
+      if (!scan(p.scan[0])) return -1;
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+  }
   if (p.per_frame) {
     for (int f = 0; f < p.nframes; ++f) {
       if (!row(p.pass[PASS_ROW][f])) return -1;

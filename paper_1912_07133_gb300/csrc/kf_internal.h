@@ -80,6 +80,13 @@ struct BankArgs {
   // and their geometry; null: the pass does not apply to this call
   const float *tc_bands = nullptr;
   TcGeom tc;
+  // single-read IIR column pass (k_colscan): scratch of the launch (ticket,
+  // publication flags, the super-tiles' end states and carries); null: the
+  // segment passes (k_colseg, k_colfold, k_coldet) run instead
+  void *scan = nullptr;
+  // gated calls: the active-tile maps of the frames (FrameDev.aoff); null
+  // otherwise
+  const unsigned char *gate_act = nullptr;
 };
 
 // Passes of the banks.  IIR: row (with the two edge rows per frame), column
@@ -105,6 +112,7 @@ struct Plan {
   Launch comb;                    // derivative bank: the combine + detect launch
   int lc = 64;                    // IIR column segment length (32 or 64 rows)
   std::vector<Launch> pass[NPASS];
+  std::vector<Launch> scan;       // IIR single-read column pass: one launch (per frame, if per_frame)
 };
 
 // work items of one frame in a pass (the kernels' decomposition)
@@ -123,6 +131,12 @@ int launch_tc_bands(const Coef *d_coef, const TcGeom &g, float sgn, float *d_ban
 int launch_colfir_tc(const Plan &p, const Launch &l, const BankArgs &a, const struct DetectArgs &da,
                      cudaStream_t st);
 int iir_segments(int H, int lc);  // IIR column segments of a frame (segment length lc)
+// single-read IIR column pass: super-tiles of a frame, bytes of the launch
+// scratch for U super-tiles, and whether the pass can serve a call (every
+// super-tile of the tallest frame's strips resident at once)
+int iir_scan_items(int H, int W);
+size_t iir_scan_bytes(long U, int S, int nf);
+bool iir_scan_fits(int type, int nstate, int storage, int S, int maxH);
 
 int launch_iir(const Plan &p, const BankArgs &a, cudaStream_t st);
 // derivative bank: tiles of 30 x 30 per frame; R (R_H or R_L) from the

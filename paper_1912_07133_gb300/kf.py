@@ -47,13 +47,15 @@ KF_NEIGH_ADJACENT = 1
 KF_GATE_OFF, KF_GATE_DILATED, KF_GATE_TILES = 0, 1, 2
 KF_SCHED_BATCHED = 0
 KF_SCHED_PER_FRAME = 1
+KF_COLUMN_SINGLE_READ = 0
+KF_COLUMN_SEGMENTS = 1
 KF_MAX_SCALES = 16
 KF_MAX_ORDER = 8
 KF_MAX_FIR_K = 160
 
 ENTRY_POINTS = ("kf_bank_opts_default", "kf_create", "kf_destroy", "kf_last_error", "kf_design",
                 "kf_filter_bank", "kf_detect_blobs", "kf_kernel_times", "kf_responses_noalloc",
-                "kf_set_launch_shape", "kf_set_segment_length", "kf_autotune",
+                "kf_set_launch_shape", "kf_set_segment_length", "kf_set_column_pass", "kf_autotune",
                 "kf_proposal_set_weights", "kf_proposal_get_weights", "kf_proposal_pool", "kf_proposal_logits",
                 "kf_proposal_grad", "kf_proposal_train_step", "kf_proposal_labels", "kf_blob_shapes",
                 "kf_quartic_bank", "kf_quartic_steer", "kf_set_wait_limit")
@@ -166,6 +168,8 @@ def load(path: str = LIB_PATH):
     L.kf_set_wait_limit.argtypes = [vp, i32]
     L.kf_set_segment_length.restype = i32
     L.kf_set_segment_length.argtypes = [vp, i32, i32]
+    L.kf_set_column_pass.restype = i32
+    L.kf_set_column_pass.argtypes = [vp, i32, i32]
     L.kf_quartic_bank.restype = i32
     L.kf_quartic_bank.argtypes = [vp, ctypes.POINTER(kf_frame), ctypes.POINTER(dbl), i32, i32, i32, vp, i32]
     L.kf_quartic_steer.restype = i32
@@ -400,6 +404,12 @@ def kf_set_wait_limit(ctx, polls: int) -> None:
 def kf_set_segment_length(ctx: int, ftype: int, rows: int) -> None:
     """Column segment length (32 or 64 rows) of a recursive bank."""
     _check(load().kf_set_segment_length(ctx, ftype, rows), ctx)
+
+
+def kf_set_column_pass(ctx: int, ftype: int, mode: int) -> None:
+    """Column pass of a recursive bank: KF_COLUMN_SEGMENTS (default) or
+    KF_COLUMN_SINGLE_READ."""
+    _check(load().kf_set_column_pass(ctx, ftype, mode), ctx)
 
 
 def kf_autotune(ctx: int, frames, scales, ftype: int, order: int, opts: kf_bank_opts = None,
