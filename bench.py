@@ -606,8 +606,11 @@ def measure_gated(args, steps, warmup, full=True, mode_name="tiles"):
         n, times = 0, {}
         for ci, ch in enumerate(src if src is not None else chunks):
             for bi, (_, ft, order) in enumerate(BANKS):
+                # the second bank of a chunk reuses the first one's tile marks
+                # (the proposal network runs once per frame)
                 bank.run(ch, EIGHT, ft, order, threshold=T, fir_kmax=96, gate=mode if gate else kf.KF_GATE_OFF,
-                         gate_threshold=p_gate, graph=graph and not profile, profile=profile)
+                         gate_threshold=p_gate, graph=graph and not profile, profile=profile,
+                         gate_reuse=gate and bi > 0)
                 b = bank.blobs()
                 n += len(b)
                 if collect is not None:

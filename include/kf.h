@@ -176,7 +176,16 @@ typedef struct {
   float offset_limit;    /* Threshold #2 (Sec. 5): > 0 keeps only candidates
                             whose eq (27) offset sqrt(dx^2 + dy^2) is at most
                             this many pixels; 0: off                          */
-  int32_t reserved0;
+  int32_t gate_reuse;    /* gated calls: 1 reuses the tile marks of the
+                            previous gated call on this context instead of
+                            running the proposal network again (the marks
+                            depend on the frames, the weights, the scale count,
+                            the gate mode and threshold, not on the filter
+                            type): the call must have the same frame count and
+                            sizes, scale count, gate mode and threshold, with
+                            no weight change since, else KF_EINVAL; the caller
+                            guarantees that the frames hold the same values.
+                            0: evaluate the network.                         */
   int64_t reserved[1];
 } kf_bank_opts;
 

@@ -113,6 +113,10 @@ struct kf_ctx {
   float *net_master = nullptr, *net_m = nullptr, *net_v = nullptr, *net_g = nullptr, *net_loss = nullptr;
   __nv_bfloat16 *net_wb = nullptr;
   int net_step = 0;
+  unsigned long long net_version = 0;  // bumped whenever the weights change
+  // the gate of the last gated call that evaluated the network: frame sizes,
+  // scale count, mode, threshold and weight version (for opts.gate_reuse)
+  std::vector<long long> gate_sig;
   bool net_ready = false;
   float *net_work = nullptr;
   size_t net_work_floats = 0;
@@ -394,7 +398,7 @@ int upload_table(kf_ctx *ctx, const void *bytes, size_t n) {
 std::vector<long long> call_key(const kf_ctx *ctx, const kf_frame *frames, int nframes, const double *scales, int S,
                                 int type, int order, int kmax, const kf_bank_opts &o) {
   std::vector<long long> k = {type, order, kmax, S, o.storage, o.neighbourhood, o.schedule, nframes,
-                              (long long)(intptr_t)ctx->cur, o.gate, o.boundary};
+                              (long long)(intptr_t)ctx->cur, o.gate, o.boundary, o.gate_reuse};
   if (o.gate) {
     long long gt;
     double g = o.gate_threshold;
@@ -601,6 +605,22 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     if (opts.schedule != KF_SCHED_BATCHED) return fail(ctx, KF_EINVAL, "gating runs with the batched schedule");
     if (!(opts.gate_threshold > 0.f && opts.gate_threshold < 1.f))
       return fail(ctx, KF_EINVAL, "gate_threshold must be in (0, 1)");
+  }
+  if (opts.gate_reuse != 0 && opts.gate_reuse != 1) return fail(ctx, KF_EINVAL, "gate_reuse must be 0 or 1");
+  // what the tile marks of a gated call depend on
+  std::vector<long long> gate_sig;
+  if (gate) {
+    long long thr;
+    double gt = opts.gate_threshold;
+    std::memcpy(&thr, &gt, sizeof thr);
+    gate_sig = {nframes, nscales, opts.gate, thr, (long long)ctx->net_version};
+    for (int f = 0; f < nframes; ++f) gate_sig.push_back(((long long)frames[f].width << 32) | frames[f].height);
+    if (opts.gate_reuse && gate_sig != ctx->gate_sig)
+      return fail(ctx, KF_EINVAL,
+                  "gate_reuse: no earlier gated call with these frame sizes, scale count, gate mode, threshold "
+                  "and weights");
+  } else if (opts.gate_reuse) {
+    return fail(ctx, KF_EINVAL, "gate_reuse needs gating");
   }
   long maxH = 0, maxPW = 0;
   for (int f = 0; f < nframes; ++f) {
@@ -830,7 +850,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   auto issue_gate = [&](cudaStream_t st, kf::Prof *prof) -> int {
     const float p = opts.gate_threshold, zthr = std::log(p / (1.f - p));
     prof->begin("gate", st);
-    for (int f = 0; f < nframes; ++f) {
+    for (int f = 0; f < (opts.gate_reuse ? 0 : nframes); ++f) {
       const int H = frames[f].height, W = frames[f].width;
       const int ph = (H + 7) / 8, pw = (W + 7) / 8, th = (H + 63) / 64, tw = (W + 63) / 64;
       if (kf::net_pool_table(plan.fr, f, H, W, ctx->g_pooled + g_poff[f], st) ||
@@ -1014,6 +1034,7 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     if ((rc = issue(ctx->stream, &ctx->prof))) return rc;
   }
   ctx->have_result = true;
+  if (gate && !opts.gate_reuse) ctx->gate_sig = gate_sig;  // the marks a later call may reuse
   ctx->have_dplanes = dbank;
   ctx->sorted_valid = true;  // enqueued with the call
   ctx->sorted_thr = opts.threshold;
@@ -1199,6 +1220,7 @@ int kf_proposal_set_weights(kf_ctx *ctx, const float *weights) {
   if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "set weights");
   ctx->net_step = 0;
   ctx->net_ready = true;
+  ++ctx->net_version;
   drop_graphs(ctx);
   return KF_OK;
 }
@@ -1285,6 +1307,7 @@ int kf_proposal_train_step(kf_ctx *ctx, const float *pooled, const uint8_t *labe
                    ctx->stream))
     return cuda_fail(ctx, cudaGetLastError(), "network gradient");
   ctx->net_step += 1;
+  ++ctx->net_version;
   if (kf::net_adam(ctx->net_master, ctx->net_m, ctx->net_v, ctx->net_g, ctx->net_step, lr, ctx->net_wb, ctx->stream))
     return cuda_fail(ctx, cudaGetLastError(), "Adam");
   cudaError_t e;

@@ -91,18 +91,46 @@ static __device__ __forceinline__ void emit_blob(const DetectArgs &a, TileList &
   }
 }
 
-// The tie rule of one candidate against its 8 neighbours' extremes m / am:
-// strictly above a neighbour earlier in (y, x) order or with an earlier first
-// scale, at least equal to a later one (pol = -1 mirrors the values).
-static __device__ __forceinline__ bool beats_neighbours(const float *m, const unsigned char *am, int p, int pol,
-                                                        float v, int s) {
+// First scale attaining a pixel's extreme, from per-pixel byte arrays.
+struct ArgBytes {
+  const unsigned char *amx, *amn;
+  __device__ __forceinline__ int operator()(int p, int pol) const { return pol > 0 ? amx[p] : amn[p]; }
+};
+
+// The same found on demand by scanning the tile's scales (buffer row i =
+// p / 32, column p % 32) for the first value equal to the extreme: the
+// per-pixel pass then keeps only the extremes (two min/max per scale), and
+// the scan runs for candidates and ties only.
+struct ArgScan {
+  const float *buf, *mx, *mn;
+  int S, SR, ld, coff;
+  __device__ __forceinline__ int operator()(int p, int pol) const {
+    const float t = pol > 0 ? mx[p] : mn[p];
+    const float *b = buf + (p >> 5) * ld + coff + (p & 31);
+    for (int s = 0; s < S; ++s)
+      if (b[(long)s * SR * ld] == t) return s;
+    return S;  // outside the frame (+-inf)
+  }
+};
+
+// The tie rule of one candidate against its 8 neighbours' extremes m (first
+// scales from arg): strictly above a neighbour earlier in (y, x) order or with
+// an earlier first scale, at least equal to a later one (pol = -1 mirrors the
+// values).
+template <class ArgF>
+static __device__ __forceinline__ bool beats_neighbours(const float *m, const ArgF &arg, int p, int pol, float v,
+                                                        int s) {
   bool ok = true;
   for (int di = -1; di <= 1 && ok; ++di)
     for (int dl = -1; dl <= 1 && ok; ++dl) {
       if (di == 0 && dl == 0) continue;
       const int pn = p + di * 32 + dl;
       const float vn = m[pn];
-      const int sn = am[pn];
+      if (pol * v != pol * vn) {  // no tie: the first scale does not matter
+        ok = pol * v > pol * vn;
+        continue;
+      }
+      const int sn = arg(pn, pol);
       const bool after = di > 0 || (di == 0 && dl > 0);
       const float a1 = pol * v, b1 = pol * vn;
       ok = (a1 > b1) || (a1 == b1 && (sn > s || (sn == s && after)));
@@ -111,8 +139,8 @@ static __device__ __forceinline__ bool beats_neighbours(const float *m, const un
 }
 
 // Spatial part of the all-scales test.  mx/mn: per-pixel maximum/minimum of R
-// over the scales of an NR x 32 tile (+-inf outside the frame), amx/amn: the
-// first scale attaining them.  A pixel's candidate is its first argmax
+// over the scales of an NR x 32 tile (+-inf outside the frame), arg(p, pol):
+// the first scale attaining them.  A pixel's candidate is its first argmax
 // (argmin); it must beat the 8 neighbours' extremes with the tie rule.
 // Each warp walks a band of interior rows, one column per lane, holding the
 // horizontal 3-maxima (3-minima, by shuffles) of three consecutive rows in
@@ -120,8 +148,8 @@ static __device__ __forceinline__ bool beats_neighbours(const float *m, const un
 // its 8 neighbours passes, and the rest (ties) take the exact tie test.  Candidates are staged in shared memory and reserved
 // globally once per tile.  Must be called by all threads of the block
 // (blockDim a multiple of 32; contains __syncthreads).
-static __device__ void spatial_detect(const float *mx, const float *mn, const unsigned char *amx,
-                                      const unsigned char *amn, const DetectArgs &a) {
+template <class ArgF>
+static __device__ void spatial_detect(const float *mx, const float *mn, const ArgF &arg, const DetectArgs &a) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   TileList &tl = g_tl;
   unsigned long long &s_base = g_tl_base;
@@ -149,13 +177,13 @@ static __device__ void spatial_detect(const float *mx, const float *mn, const un
         const int p = i * 32 + lane;
         const float m8 = fmaxf(xa, fmaxf(lx, xc));  // maximum of the 8 neighbours
         if (vc > a.thr && vc >= m8) {
-          const int s = amx[p];
-          if (vc > m8 || beats_neighbours(mx, amx, p, 1, vc, s)) emit_blob(a, tl, s, y, x, 1, vc);
+          const int s = arg(p, 1);
+          if (vc > m8 || beats_neighbours(mx, arg, p, 1, vc, s)) emit_blob(a, tl, s, y, x, 1, vc);
         }
         const float n8 = fminf(na, fminf(ln, nc));
         if (a.dark && -wc > a.thr && wc <= n8) {
-          const int s = amn[p];
-          if (wc < n8 || beats_neighbours(mn, amn, p, -1, wc, s)) emit_blob(a, tl, s, y, x, -1, wc);
+          const int s = arg(p, -1);
+          if (wc < n8 || beats_neighbours(mn, arg, p, -1, wc, s)) emit_blob(a, tl, s, y, x, -1, wc);
         }
       }
       xa = fmaxf(vc, lx), na = fminf(wc, ln);
@@ -192,29 +220,27 @@ static __device__ void detect_tile(const float *buf, float *red, const DetectArg
   }
   if (a.raw) return;  // a derivative channel: written, not detected (uniform over the block)
   float *mx = red, *mn = red + NP;
-  unsigned char *amx = reinterpret_cast<unsigned char *>(red + 2 * NP);
-  unsigned char *amn = amx + NP;
   if (a.neigh == 0) {
-    // per-pixel extremes over scales (first argmax / argmin), out-of-frame -> +-inf
+    // per-pixel extremes over scales, out-of-frame -> +-inf (the first scale
+    // attaining them is found on demand)
     for (int p = tid; p < NP; p += nt) {
       const int i = p >> 5, lane = p & 31;
       const int y = a.r0 + i, x = a.x0 + lane;
       float vmax = -CUDART_INF_F, vmin = CUDART_INF_F;
-      int smax = a.S, smin = a.S;
       if (y >= 0 && y < a.H && x >= 0 && x < a.W) {
+        const float *b = buf + i * a.ld + a.coff + lane;
         for (int s = 0; s < a.S; ++s) {
-          const float v = buf[(s * SR + i) * a.ld + a.coff + lane];
-          if (v > vmax) vmax = v, smax = s;
-          if (v < vmin) vmin = v, smin = s;
+          const float v = b[(long)s * SR * a.ld];
+          vmax = fmaxf(vmax, v);
+          vmin = fminf(vmin, v);
         }
       }
       mx[p] = vmax;
       mn[p] = vmin;
-      amx[p] = (unsigned char)smax;
-      amn[p] = (unsigned char)smin;
     }
     __syncthreads();
-    spatial_detect(mx, mn, amx, amn, a);
+    ArgScan arg{buf, mx, mn, a.S, SR, a.ld, a.coff};
+    spatial_detect(mx, mn, arg, a);
     return;
   }
   // adjacent scales: every (scale, pixel) against its 3 x 3 x 3 neighbourhood

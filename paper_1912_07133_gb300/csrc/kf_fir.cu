@@ -718,7 +718,7 @@ __global__ void __launch_bounds__(CNT2, 2) k_colfir_tma(const __grid_constant__ 
     a.W = W;
     a.frame = F.index;
     a.resp = resp;
-    spatial_detect(mx, mn, amx, amn, a);
+    spatial_detect(mx, mn, ArgBytes{amx, amn}, a);
     fence_proxy_async();  // extremes written over the stages before the next item's copies
     __syncthreads();
   }

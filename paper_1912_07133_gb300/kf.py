@@ -91,7 +91,7 @@ class kf_bank_opts(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("responses", ctypes.c_void_p),
                 ("schedule", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("gate", ctypes.c_int32), ("gate_threshold", ctypes.c_float),
-                ("offset_limit", ctypes.c_float), ("reserved0", ctypes.c_int32),
+                ("offset_limit", ctypes.c_float), ("gate_reuse", ctypes.c_int32),
                 ("reserved", ctypes.c_int64 * 1)]
 
 
@@ -510,7 +510,8 @@ class Bank:
     def run(self, frames, scales, ftype=KF_IIR_REPEATED_POLE, order=4, threshold=0.05,
             neighbourhood=KF_NEIGH_ALL_SCALES, responses=None, fir_kmax=96, profile=False,
             storage=KF_DTYPE_F32, value_scales=None, schedule=KF_SCHED_BATCHED, graph=False, gate=False,
-            gate_threshold=None, response=KF_RESP_LAPLACIAN, offset_limit=0.0, boundary=KF_BOUNDARY_HOLD):
+            gate_threshold=None, response=KF_RESP_LAPLACIAN, offset_limit=0.0, boundary=KF_BOUNDARY_HOLD,
+            gate_reuse=False):
         o = kf_bank_opts_default()
         o.threshold = float(threshold)
         o.profile = 1 if profile else 0
@@ -523,6 +524,7 @@ class Bank:
         o.response = response
         o.offset_limit = float(offset_limit)
         o.boundary = int(boundary)
+        o.gate_reuse = 1 if gate_reuse else 0
         if gate_threshold is not None:
             o.gate_threshold = float(gate_threshold)
         if responses is not None:

@@ -170,3 +170,39 @@ def test_gate_arguments_are_checked():
     with pytest.raises(kf.KfError):
         bank.run([x], [2.0] * 9, D, 4, gate=True)
     bank.close()
+
+
+def test_gate_reuse_gives_the_marks_of_the_earlier_call():
+    """A second bank on the same frames with gate_reuse: the tile marks of the
+    earlier gated call (one network evaluation per frame), the same blobs as
+    evaluating the gate again; refused without a matching earlier call."""
+    import torch
+
+    from paper_1912_07133_gb300 import kf
+    frames = frames_for_gating(44)
+    ts = [to_device(f) for f in frames]
+    bank = kf.Bank(0)
+    kf.kf_proposal_set_weights(bank.ctx, hand_weights(0.5))
+    with pytest.raises(kf.KfError) as e:  # nothing to reuse yet
+        bank.run(ts, SCALES, C, 1, threshold=0.03, gate=kf.KF_GATE_TILES, gate_threshold=0.5, gate_reuse=True)
+    assert e.value.code == kf.KF_EINVAL
+    bank.run(ts, SCALES, D, 4, threshold=0.03, gate=kf.KF_GATE_TILES, gate_threshold=0.5)
+    bank.run(ts, SCALES, C, 1, threshold=0.03, gate=kf.KF_GATE_TILES, gate_threshold=0.5, gate_reuse=True)
+    reused = bank.blobs()
+    bank.run(ts, SCALES, C, 1, threshold=0.03, gate=kf.KF_GATE_TILES, gate_threshold=0.5)
+    fresh = bank.blobs()
+    assert len(fresh) > 0 and np.array_equal(reused, fresh)
+    for kw in [dict(gate_threshold=0.6), dict(gate=kf.KF_GATE_DILATED)]:  # other marks
+        args = dict(threshold=0.03, gate=kf.KF_GATE_TILES, gate_threshold=0.5, gate_reuse=True)
+        args.update(kw)
+        with pytest.raises(kf.KfError):
+            bank.run(ts, SCALES, C, 1, **args)
+    with pytest.raises(kf.KfError):  # another frame set
+        bank.run(ts[:2], SCALES, C, 1, threshold=0.03, gate=kf.KF_GATE_TILES, gate_threshold=0.5, gate_reuse=True)
+    kf.kf_proposal_set_weights(bank.ctx, hand_weights(0.4))  # new weights: the marks are stale
+    with pytest.raises(kf.KfError):
+        bank.run(ts, SCALES, C, 1, threshold=0.03, gate=kf.KF_GATE_TILES, gate_threshold=0.5, gate_reuse=True)
+    with pytest.raises(kf.KfError):  # reuse without gating
+        bank.run(ts, SCALES, C, 1, threshold=0.03, gate_reuse=True)
+    torch.cuda.synchronize()
+    bank.close()
