@@ -48,6 +48,46 @@ namespace {
 template <int KK>
 struct Chain {
   static constexpr int NF = KK;
+  // two independent chains (e.g. the two directions of a recursion) advanced
+  // together by packed FP32 instructions (fma.rn.f32x2): per component the
+  // same IEEE operations in the same order as push() and out()
+  static constexpr bool kPacked = true;
+  struct Pair {
+    // the coefficients duplicated into both halves of a register pair
+    struct Coefs {
+      float2 p2, w2[KK];
+      template <class V>
+      __device__ __forceinline__ explicit Coefs(const V &v) {
+        p2 = make_float2(v.p, v.p);
+#pragma unroll
+        for (int j = 0; j < KK; ++j) w2[j] = make_float2(v.w[j], v.w[j]);
+      }
+    };
+    float2 t[KK];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+      for (int j = 0; j < KK; ++j) t[j] = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void push(const Coefs &c, float2 x2) {
+#pragma unroll
+      for (int j = KK - 1; j > 0; --j) t[j] = __ffma2_rn(c.p2, t[j], t[j - 1]);
+      t[0] = __ffma2_rn(c.p2, t[0], x2);
+    }
+    __device__ __forceinline__ float2 out(const Coefs &c) const {
+      float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < KK; ++j) y = __ffma2_rn(c.w2[j], t[j], y);
+      return y;
+    }
+    __device__ __forceinline__ void set(const Chain &a, const Chain &b) {
+#pragma unroll
+      for (int j = 0; j < KK; ++j) t[j] = make_float2(a.t[j], b.t[j]);
+    }
+    __device__ __forceinline__ void get(Chain &a, Chain &b) const {
+#pragma unroll
+      for (int j = 0; j < KK; ++j) a.t[j] = t[j].x, b.t[j] = t[j].y;
+    }
+  };
   static constexpr int kColdetRegs32 = 80;  // k_coldet with 32-row segments: registers per thread
   struct View {
     float p, b0, w[KK];
@@ -137,6 +177,53 @@ struct Chain {
 template <int NM>
 struct Modes {
   static constexpr int NF = 2 * NM;
+  // two independent sets of modes advanced by packed FP32 instructions, with
+  // per component the operations of push() and out()
+  static constexpr bool kPacked = true;
+  struct Pair {
+    struct Coefs {
+      float2 zr[NM], zi[NM], mzi[NM], gr[NM], mgi[NM];
+      template <class V>
+      __device__ __forceinline__ explicit Coefs(const V &v) {
+#pragma unroll
+        for (int i = 0; i < NM; ++i) {
+          zr[i] = make_float2(v.zr[i], v.zr[i]);
+          zi[i] = make_float2(v.zi[i], v.zi[i]);
+          mzi[i] = make_float2(-v.zi[i], -v.zi[i]);
+          gr[i] = make_float2(v.gr[i], v.gr[i]);
+          mgi[i] = make_float2(-v.gi[i], -v.gi[i]);
+        }
+      }
+    };
+    float2 tr[NM], ti[NM];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+      for (int i = 0; i < NM; ++i) tr[i] = ti[i] = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void push(const Coefs &c, float2 x2) {
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        const float2 nr = __ffma2_rn(c.zr[i], tr[i], __ffma2_rn(c.mzi[i], ti[i], x2));
+        const float2 ni = __ffma2_rn(c.zr[i], ti[i], __fmul2_rn(c.zi[i], tr[i]));
+        tr[i] = nr;
+        ti[i] = ni;
+      }
+    }
+    __device__ __forceinline__ float2 out(const Coefs &c) const {
+      float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < NM; ++i) y = __ffma2_rn(c.gr[i], tr[i], __ffma2_rn(c.mgi[i], ti[i], y));
+      return y;
+    }
+    __device__ __forceinline__ void set(const Modes &a, const Modes &b) {
+#pragma unroll
+      for (int i = 0; i < NM; ++i) tr[i] = make_float2(a.tr[i], b.tr[i]), ti[i] = make_float2(a.ti[i], b.ti[i]);
+    }
+    __device__ __forceinline__ void get(Modes &a, Modes &b) const {
+#pragma unroll
+      for (int i = 0; i < NM; ++i) a.tr[i] = tr[i].x, a.ti[i] = ti[i].x, b.tr[i] = tr[i].y, b.ti[i] = ti[i].y;
+    }
+  };
   static constexpr int kColdetRegs32 = NM < 3 ? 80 : 128;  // three modes need more
   struct View {
     float zr[NM], zi[NM], gr[NM], gi[NM], b0;
@@ -366,12 +453,21 @@ __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, i
     typename Rec::View v;
     v.load(c);
     Rec ef, eb;
-    ef.zero();
-    eb.zero();
+    if constexpr (Rec::kPacked) {  // both directions in one packed chain
+      typename Rec::Pair e2;
+      const typename Rec::Pair::Coefs pc(v);
+      e2.zero();
 #pragma unroll
-    for (int i = 0; i < CH; ++i) ef.push(v, L[i]);
+      for (int i = 0; i < CH; ++i) e2.push(pc, make_float2(L[i], L[CH - 1 - i]));
+      e2.get(ef, eb);
+    } else {
+      ef.zero();
+      eb.zero();
 #pragma unroll
-    for (int i = CH - 1; i >= 0; --i) eb.push(v, L[i]);
+      for (int i = 0; i < CH; ++i) ef.push(v, L[i]);
+#pragma unroll
+      for (int i = CH - 1; i >= 0; --i) eb.push(v, L[i]);
+    }
     Rec hlo, hhi;
     hlo.hold(c, in_lo);
     hhi.hold(c, in_hi);
@@ -380,17 +476,39 @@ __device__ __forceinline__ void row_body(const FrameDev &F, bool EDGE, int yw, i
     const Rec cf = carry_scan<Rec, false>(ef, c, tid, NT, s_scan, hlo);
     const Rec cb = carry_scan<Rec, true>(eb, c, NT - 1 - tid, NT, s_scan, hhi);
     float yv[CH];
-    Rec r = cf;
+    if constexpr (Rec::kPacked) {
+      // step i advances the causal chain at pixel i and the anticausal one at
+      // pixel CH-1-i; a pixel's two outputs meet when the second arrives:
+      // yv = y+ + (b0 L + y-), the same operations as the scalar passes
+      typename Rec::Pair r2;
+      const typename Rec::Pair::Coefs pc(v);
+      r2.set(cf, cb);
 #pragma unroll
-    for (int i = 0; i < CH; ++i) {
-      yv[i] = r.out(v);
-      r.push(v, L[i]);
-    }
-    r = cb;
+      for (int i = 0; i < CH; ++i) {
+        const int k = CH - 1 - i;
+        const float2 o = r2.out(pc);
+        if (i < k) {
+          yv[i] = o.x;  // y+ first
+          yv[k] = o.y;  // y- first
+        } else {
+          yv[i] = o.x + fmaf(v.b0, L[i], yv[i]);
+          yv[k] = yv[k] + fmaf(v.b0, L[k], o.y);
+        }
+        r2.push(pc, make_float2(L[i], L[k]));
+      }
+    } else {
+      Rec r = cf;
 #pragma unroll
-    for (int i = CH - 1; i >= 0; --i) {
-      yv[i] += fmaf(v.b0, L[i], r.out(v));
-      r.push(v, L[i]);
+      for (int i = 0; i < CH; ++i) {
+        yv[i] = r.out(v);
+        r.push(v, L[i]);
+      }
+      r = cb;
+#pragma unroll
+      for (int i = CH - 1; i >= 0; --i) {
+        yv[i] += fmaf(v.b0, L[i], r.out(v));
+        r.push(v, L[i]);
+      }
     }
     // planes hold sigma^2 x the one-sided blur: the column pass then only
     // negates (R_L = -sigma^2 (D20 + D02)), and 16-bit planes keep the
@@ -494,20 +612,38 @@ __global__ void __launch_bounds__(128) k_colseg(const FrameDev *__restrict__ fr,
     if (rf >= 0 && rb < H) {
       const typename Store<ST>::T *pf = Pc + (long)rf * PWb, *pb = Pc + (long)rb * PWb;
       Rec q;
-      r.zero();
-      q.zero();
+      if constexpr (Rec::kPacked) {
+        typename Rec::Pair r2;
+        const typename Rec::Pair::Coefs pc(v);
+        r2.zero();
 #pragma unroll
-      for (int i0 = 0; i0 < LC; i0 += 8) {
-        float inf[8], inb[8];
+        for (int i0 = 0; i0 < LC; i0 += 8) {
+          float inf[8], inb[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          inf[u] = Store<ST>::ld(pf[(long)(i0 + u) * PWb]);
-          inb[u] = Store<ST>::ld(pb[-(long)(i0 + u) * PWb]);
+          for (int u = 0; u < 8; ++u) {
+            inf[u] = Store<ST>::ld(pf[(long)(i0 + u) * PWb]);
+            inb[u] = Store<ST>::ld(pb[-(long)(i0 + u) * PWb]);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) r2.push(pc, make_float2(inf[u], inb[u]));
         }
+        r2.get(r, q);
+      } else {
+        r.zero();
+        q.zero();
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          r.push(v, inf[u]);
-          q.push(v, inb[u]);
+        for (int i0 = 0; i0 < LC; i0 += 8) {
+          float inf[8], inb[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            inf[u] = Store<ST>::ld(pf[(long)(i0 + u) * PWb]);
+            inb[u] = Store<ST>::ld(pb[-(long)(i0 + u) * PWb]);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            r.push(v, inf[u]);
+            q.push(v, inb[u]);
+          }
         }
       }
       r.store(Ef, PWb);
@@ -705,24 +841,63 @@ __global__ void __launch_bounds__(512) __maxnreg__(LC == 32 ? Rec::kColdetRegs32
     const T *b16 = reinterpret_cast<const T *>(reinterpret_cast<const char *>(buf + (long)s * REG) + C16B) +
                    off + lane;
     float yp[NR];
+    if constexpr (Rec::kPacked) {
+      // rows outside the frame take the held rows, 16-bit input is widened
+      // in place (top-down, the warp in step every 8 rows), then step i
+      // advances the causal chain at row i and the anticausal one at row
+      // NR-1-i; a row's R is formed when its second output arrives, with the
+      // operations of the scalar passes: sgn (y+ + (b0 x + y-))
+      if (!F32 || outside) {
 #pragma unroll
-    for (int i = 0; i < NR; ++i) {
-      const int y = r0 + i;
-      float in = F32 ? b[i * LD] : Store<ST>::ld(b16[i * CBOX16]);
-      if (outside) in = y < 0 ? top : (y >= H ? bot : in);
-      if (!F32 || outside) b[i * LD] = in;
-      yp[i] = r.out(v);
-      r.push(v, in);
-      if ((i & 7) == 7) __syncwarp();
-    }
-    __syncwarp();
-    r.load(Ef + fs, PWb);
+        for (int i = 0; i < NR; ++i) {
+          const int y = r0 + i;
+          float in = F32 ? b[i * LD] : Store<ST>::ld(b16[i * CBOX16]);
+          if (outside) in = y < 0 ? top : (y >= H ? bot : in);
+          b[i * LD] = in;
+          if ((i & 7) == 7) __syncwarp();
+        }
+        __syncwarp();
+      }
+      Rec q;
+      q.load(Ef + fs, PWb);
+      typename Rec::Pair r2;
+      const typename Rec::Pair::Coefs pc(v);
+      r2.set(r, q);
 #pragma unroll
-    for (int i = NR - 1; i >= 0; --i) {
-      const float in = b[i * LD];
-      // R_L = -sigma^2 (D20 + D02) (planes carry sigma^2); raw channel: +sigma^2 D
-      b[i * LD] = sgn * (yp[i] + fmaf(v.b0, in, r.out(v)));
-      r.push(v, in);
+      for (int i = 0; i < NR; ++i) {
+        const int k = NR - 1 - i;
+        const float xi = b[i * LD], xk = b[k * LD];
+        const float2 o = r2.out(pc);
+        if (i < k) {
+          yp[i] = o.x;  // y+ first
+          yp[k] = o.y;  // y- first
+        } else {
+          // R_L = -sigma^2 (D20 + D02) (planes carry sigma^2); raw channel: +sigma^2 D
+          b[i * LD] = sgn * (o.x + fmaf(v.b0, xi, yp[i]));
+          b[k * LD] = sgn * (yp[k] + fmaf(v.b0, xk, o.y));
+        }
+        r2.push(pc, make_float2(xi, xk));
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        const int y = r0 + i;
+        float in = F32 ? b[i * LD] : Store<ST>::ld(b16[i * CBOX16]);
+        if (outside) in = y < 0 ? top : (y >= H ? bot : in);
+        if (!F32 || outside) b[i * LD] = in;
+        yp[i] = r.out(v);
+        r.push(v, in);
+        if ((i & 7) == 7) __syncwarp();
+      }
+      __syncwarp();
+      r.load(Ef + fs, PWb);
+#pragma unroll
+      for (int i = NR - 1; i >= 0; --i) {
+        const float in = b[i * LD];
+        // R_L = -sigma^2 (D20 + D02) (planes carry sigma^2); raw channel: +sigma^2 D
+        b[i * LD] = sgn * (yp[i] + fmaf(v.b0, in, r.out(v)));
+        r.push(v, in);
+      }
     }
     __syncthreads();
     DetectArgs a = da;
