@@ -90,7 +90,11 @@ GATED_THRESHOLD = 0.3  # clustered frames: the 1/f background alone stays below 
 # ncu capture (summaries in profiles/), keyed by (workload, kernel, storage):
 # (bytes, digest of the kernel sources the capture ran).  A figure is reported
 # only while the sources still have that digest; otherwise traffic is null.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("iir_fir", "fir_row", "f32"): (408.0e6, "6b270b19b71585eb"),     # k_rowfir: 67.3 read + 340.7 written
+    ("iir_fir", "fir_coldet", "f32"): (430.8e6, "6b270b19b71585eb"),  # k_colfir_tc: 424.5 + 6.3
+    ("iir_fir", "iir_row", "f32"): (406.1e6, "6b270b19b71585eb"),     # k_row: 67.3 + 338.8
+}
 CSRC = os.path.join(ROOT, "paper_1912_07133_gb300", "csrc")
 
 
@@ -375,6 +379,11 @@ def measure_workload(args, name, steps, warmup, full=True):
     # step are independent passes over the same frames and run at once
     bstreams = {bn: torch.cuda.Stream(dev) for bn, _, _ in BANKS}
     banks = {bn: kf.Bank(local, bstreams[bn].cuda_stream) for bn, _, _ in BANKS}
+    if args.column_pass:  # a fixed column pass for the recursive banks (the autotuner may change it)
+        mode = {"segments": kf.KF_COLUMN_SEGMENTS, "single-read": kf.KF_COLUMN_SINGLE_READ}[args.column_pass]
+        for bn, ft, _ in BANKS:
+            if ft in (kf.KF_IIR_REPEATED_POLE, kf.KF_IIR_BUTTERWORTH):
+                kf.kf_set_column_pass(banks[bn].ctx, ft, mode)
     concurrent = len(BANKS) > 1 and not args.serial
 
     # one-time designs (FP64 kernel), timed separately: the bank reuses them
@@ -1122,6 +1131,8 @@ def main():
                     help="default workload: skip the gated, batch and counts sub-workloads")
     ap.add_argument("--sub-steps", type=int, default=3, help="timed steps of each sub-workload")
     ap.add_argument("--sub-warmup", type=int, default=3, help="warm-up steps of each sub-workload (>= 3)")
+    ap.add_argument("--column-pass", choices=("segments", "single-read"), default=None,
+                    help="column pass of the recursive banks (with --no-tune it stays fixed)")
     ap.add_argument("--storage", choices=tuple(STORAGE), default=None,
                     help="element type of the one-sided planes (default: the workload's)")
     args = ap.parse_args()
