@@ -212,9 +212,9 @@ int grow(kf_ctx *ctx, T **p, size_t *have, size_t need, const char *what) {
 // Ordering buffers for the context's candidate capacity (keys, indices, digit
 // histograms, the ordered list, the count, the pinned read-back); a
 // reallocation drops the captured graphs.
-int ensure_sort(kf_ctx *ctx) {
+int ensure_sort(kf_ctx *ctx, long nrows) {
   cudaError_t e;
-  const size_t wb = kf::sort_workspace_bytes(ctx->blob_cap);
+  const size_t wb = kf::sort_workspace_bytes(ctx->blob_cap, nrows);
   if (!ctx->sort_work || ctx->sort_work_bytes < wb || !ctx->sorted || ctx->sorted_cap < ctx->blob_cap) {
     drop_graphs(ctx);
     cudaFree(ctx->sort_work);
@@ -904,13 +904,14 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
     a.raw = 1;
   }
   // the candidate ordering at the bank threshold runs at the end of the call
-  if ((rc = ensure_sort(ctx))) return rc;
+  const long nrows = (long)nframes * nscales * maxH;  // row buckets of the ordering
+  if ((rc = ensure_sort(ctx, nrows))) return rc;
   long wmax = 0;
   for (int f = 0; f < nframes; ++f) wmax = std::max(wmax, (long)frames[f].width);
   const int keybits = sort_keybits(nframes, nscales, maxH, wmax);
   auto issue_sort = [&](cudaStream_t st, kf::Prof *prof) -> int {
     if (kf::launch_sort(ctx->blobs, ctx->blob_cap, &ctx->status->count, (float)opts.threshold, nscales, maxH, wmax,
-                        keybits, ctx->sort_work, ctx->sorted, ctx->d_npass, prof, st))
+                        keybits, nrows, ctx->sort_work, ctx->sorted, ctx->d_npass, prof, st))
       return cuda_fail(ctx, cudaGetLastError(), "candidate ordering launch");
     return KF_OK;
   };
@@ -1434,11 +1435,13 @@ int kf_detect_blobs(kf_ctx *ctx, double threshold, kf_blob *out, int64_t capacit
   // A new threshold: order again (device-sized, enqueued without the count).
   if (!ctx->sorted_valid || ctx->sorted_thr != threshold) {
     int rc;
-    if ((rc = ensure_sort(ctx))) return rc;
+    const long nrows = (long)ctx->last_nframes * ctx->last_S * ctx->last_hmax;
+    if ((rc = ensure_sort(ctx, nrows))) return rc;
     const int keybits = sort_keybits(ctx->last_nframes, ctx->last_S, ctx->last_hmax, ctx->last_wmax);
     kf::Prof none{};
     if (kf::launch_sort(ctx->blobs, ctx->blob_cap, &ctx->status->count, (float)threshold, ctx->last_S,
-                        ctx->last_hmax, ctx->last_wmax, keybits, ctx->sort_work, ctx->sorted, ctx->d_npass, &none,
+                        ctx->last_hmax, ctx->last_wmax, keybits, nrows, ctx->sort_work, ctx->sorted, ctx->d_npass,
+                        &none,
                         ctx->stream))
       return cuda_fail(ctx, cudaGetLastError(), "sort launch");
     ctx->sorted_valid = true;

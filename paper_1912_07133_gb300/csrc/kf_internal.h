@@ -203,8 +203,9 @@ int launch_steer(const float *in, long npix, int nsets, const float *m55, float 
 void set_noalloc_wait_test(unsigned polls);
 
 // candidate ordering (kf_sort.cu)
-size_t sort_workspace_bytes(long cap);
+size_t sort_workspace_bytes(long cap, long nrows);
 int launch_sort(const Blob *blobs, long cap, const unsigned long long *count, float thr, int nscales, long hmax,
-                long wmax, int keybits, void *work, Blob *out, unsigned *d_npass, Prof *prof, cudaStream_t st);
+                long wmax, int keybits, long nrows, void *work, Blob *out, unsigned *d_npass, Prof *prof,
+                cudaStream_t st);
 
 }  // namespace kf

@@ -180,22 +180,216 @@ __global__ void k_gather(const Blob *__restrict__ b, const unsigned *__restrict_
     out[i] = b[idx[i]];
 }
 
+// ---------------------------------------------------------------------------
+// row-bucket ordering: a counting sort of the passing candidates by (frame,
+// scale, y) -- one bucket per frame row of a scale -- then within a bucket by
+// x (keys are unique: one candidate per pixel and scale).  Six light launches
+// instead of the radix's eleven; used while the buckets fit the workspace.
+// ---------------------------------------------------------------------------
+constexpr long ROW_BUCKETS_MAX = 1L << 22;
+constexpr int SCAN_CHUNK = 4096;  // buckets per block of the scans
+
+__device__ __forceinline__ unsigned row_bucket(const Blob &r, int nscales, long hmax) {
+  return (unsigned)(((long)r.frame * nscales + r.scale) * hmax + r.y);
+}
+
+// bucket and slot of every passing candidate; the passing count
+__global__ void __launch_bounds__(256) k_rows_count(const Blob *__restrict__ b, long cap,
+                                                    const unsigned long long *__restrict__ count, float thr,
+                                                    int nscales, long hmax, unsigned *__restrict__ cnt,
+                                                    unsigned *__restrict__ bid, unsigned *__restrict__ slot,
+                                                    unsigned *__restrict__ npass) {
+  const long n = list_n(count, cap);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < n;
+       i += (long)gridDim.x * blockDim.x) {
+    bool pass = false;
+    if (i < n) {
+      const Blob r = b[i];
+      pass = fabsf(r.response) > thr;
+      unsigned k = ~0u;
+      if (pass) {
+        k = row_bucket(r, nscales, hmax);
+        slot[i] = atomicAdd(cnt + k, 1u);
+      }
+      bid[i] = k;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, pass);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(npass, (unsigned)__popc(m));
+  }
+}
+
+// block sums of SCAN_CHUNK buckets
+__global__ void __launch_bounds__(1024) k_rows_part(const unsigned *__restrict__ cnt, long nb,
+                                                    unsigned *__restrict__ part) {
+  __shared__ unsigned ws[32];
+  const long c0 = (long)blockIdx.x * SCAN_CHUNK;
+  unsigned v = 0;
+  for (int j = threadIdx.x; j < SCAN_CHUNK; j += 1024)
+    if (c0 + j < nb) v += cnt[c0 + j];
+  v = __reduce_add_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const unsigned t = __reduce_add_sync(0xffffffffu, ws[threadIdx.x]);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of the block sums (at most 1024 of them), in place
+__global__ void __launch_bounds__(1024) k_rows_top(unsigned *__restrict__ part, int np) {
+  __shared__ unsigned ws[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned v = t < np ? part[t] : 0u;
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned z = ws[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= o) z += y;
+    }
+    ws[lane] = z - ws[lane];  // exclusive over warps
+  }
+  __syncthreads();
+  if (t < np) part[t] = ws[w] + x - v;
+}
+
+// exclusive scan of the buckets: off[k] = first position of bucket k
+__global__ void __launch_bounds__(1024) k_rows_off(const unsigned *__restrict__ cnt, long nb,
+                                                   const unsigned *__restrict__ part, unsigned *__restrict__ off) {
+  __shared__ unsigned ws[32];
+  __shared__ unsigned carry;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const long c0 = (long)blockIdx.x * SCAN_CHUNK;
+  if (t == 0) carry = part[blockIdx.x];
+  for (int j0 = 0; j0 < SCAN_CHUNK; j0 += 1024) {
+    const long k = c0 + j0 + t;
+    const unsigned v = k < nb ? cnt[k] : 0u;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      unsigned z = ws[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, z, o);
+        if (lane >= o) z += y;
+      }
+      ws[lane] = z - ws[lane];
+    }
+    __syncthreads();
+    if (k < nb) off[k] = carry + ws[w] + x - v;
+    __syncthreads();
+    if (t == 1023) carry += ws[w] + x;
+    __syncthreads();
+  }
+}
+
+// candidate i (passing) to its bucket, with its x
+__global__ void __launch_bounds__(256) k_rows_scatter(const Blob *__restrict__ b, long cap,
+                                                      const unsigned long long *__restrict__ count,
+                                                      const unsigned *__restrict__ bid,
+                                                      const unsigned *__restrict__ slot,
+                                                      const unsigned *__restrict__ off, unsigned *__restrict__ tmp,
+                                                      int *__restrict__ xs) {
+  const long n = list_n(count, cap);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const unsigned k = bid[i];
+    if (k == ~0u) continue;
+    const unsigned pos = off[k] + slot[i];
+    tmp[pos] = (unsigned)i;
+    xs[pos] = b[i].x;
+  }
+}
+
+// each placed candidate's rank by x among its bucket's; the record to the
+// ordered list
+__global__ void __launch_bounds__(256) k_rows_rank(const Blob *__restrict__ b, const unsigned *__restrict__ tmp,
+                                                   const int *__restrict__ xs, const unsigned *__restrict__ bid,
+                                                   const unsigned *__restrict__ cnt,
+                                                   const unsigned *__restrict__ off,
+                                                   const unsigned *__restrict__ npass, Blob *__restrict__ out) {
+  const long n = *npass;
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
+    const unsigned i = tmp[p];
+    const unsigned k = bid[i];
+    const unsigned lo = off[k], m = cnt[k];
+    const int x = xs[p];
+    unsigned r = 0;
+    for (unsigned q = 0; q < m; ++q) r += xs[lo + q] < x;
+    out[lo + r] = b[i];
+  }
+}
+
 }  // namespace
 
-size_t sort_workspace_bytes(long n) {
+size_t sort_workspace_bytes(long n, long nrows) {
   const long nb = (n + TILE - 1) / TILE;
-  return (size_t)n * 2 * (sizeof(unsigned long long) + sizeof(unsigned)) +
-         ((size_t)MAXD * nb + MAXD) * sizeof(unsigned) + 256;
+  const size_t radix = (size_t)n * 2 * (sizeof(unsigned long long) + sizeof(unsigned)) +
+                       ((size_t)MAXD * nb + MAXD) * sizeof(unsigned) + 256;
+  if (nrows > ROW_BUCKETS_MAX) return radix;
+  const size_t rows = ((size_t)2 * nrows + 1024 + (size_t)4 * n) * sizeof(unsigned) + 256;
+  return std::max(radix, rows);
 }
 
 // Sort the first min(*count, cap) candidates of `blobs` (count: device) into
 // `out` (device) and write the number of records with |response| > thr to
-// *d_npass (device).  `keybits` bounds the real keys: frame, scale, y, x
-// packed as ((frame S + scale) hmax + y) wmax + x.  The passes split keybits
-// into equal digits of at most MAXBITS bits.  Work: sort_workspace_bytes(cap).
+// *d_npass (device); only those records are ordered (the ones at or below
+// thr are not used).  nrows = frames x scales x hmax row buckets: up to
+// ROW_BUCKETS_MAX the row-bucket ordering runs, beyond it the radix sort:
+// `keybits` bounds the real keys, frame, scale, y, x packed as ((frame S +
+// scale) hmax + y) wmax + x, split into equal digits of at most MAXBITS bits.
+// Work: sort_workspace_bytes(cap, nrows).
 int launch_sort(const Blob *blobs, long cap, const unsigned long long *count, float thr, int nscales, long hmax,
-                long wmax, int keybits, void *work, Blob *out, unsigned *d_npass, Prof *prof, cudaStream_t st) {
+                long wmax, int keybits, long nrows, void *work, Blob *out, unsigned *d_npass, Prof *prof,
+                cudaStream_t st) {
   if (cap <= 0) return 0;
+  if (nrows >= 1 && nrows <= ROW_BUCKETS_MAX) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return -1;
+    char *p = static_cast<char *>(work);
+    auto *cnt = reinterpret_cast<unsigned *>(p);
+    auto *off = cnt + nrows;
+    auto *part = off + nrows;
+    auto *bid = part + 1024;
+    auto *slot = bid + cap;
+    auto *tmp = slot + cap;
+    auto *xs = reinterpret_cast<int *>(tmp + cap);
+    const int np = (int)((nrows + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    const unsigned ng = (unsigned)std::min<long>((cap + 255) / 256, 8L * nsm);
+    if (cudaMemsetAsync(d_npass, 0, sizeof(unsigned), st) != cudaSuccess ||
+        cudaMemsetAsync(cnt, 0, (size_t)nrows * sizeof(unsigned), st) != cudaSuccess)
+      return -1;
+    prof->begin("sort_count", st);
+    k_rows_count<<<ng, 256, 0, st>>>(blobs, cap, count, thr, nscales, hmax, cnt, bid, slot, d_npass);
+    prof->end(st);
+    prof->begin("sort_scan", st);
+    k_rows_part<<<np, 1024, 0, st>>>(cnt, nrows, part);
+    k_rows_top<<<1, 1024, 0, st>>>(part, np);
+    k_rows_off<<<np, 1024, 0, st>>>(cnt, nrows, part, off);
+    prof->end(st);
+    prof->begin("sort_scatter", st);
+    k_rows_scatter<<<ng, 256, 0, st>>>(blobs, cap, count, bid, slot, off, tmp, xs);
+    prof->end(st);
+    prof->begin("sort_gather", st);
+    k_rows_rank<<<ng, 256, 0, st>>>(blobs, tmp, xs, bid, cnt, off, d_npass, out);
+    prof->end(st);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+  }
   const long nb = (cap + TILE - 1) / TILE;
   char *p = static_cast<char *>(work);
   auto *k0 = reinterpret_cast<unsigned long long *>(p);

@@ -1,9 +1,13 @@
-"""The ordered blob list: the radix ordering enqueued with every bank call and
-the read-back of kf_detect_blobs.
+"""The ordered blob list: the ordering enqueued with every bank call (a
+counting sort by (frame, scale, row) bucket, then by x inside a bucket; the
+radix sort when the row buckets exceed 2^22) and the read-back of
+kf_detect_blobs.
 
-* Keys of many bits (several frames x scales x rows x columns: four radix
-  passes) come back strictly ordered by (frame, scale, y, x), and the batch's
-  list is the concatenation of the frames' own lists.
+* Keys of many bits (several frames x scales x rows x columns) come back
+  strictly ordered by (frame, scale, y, x), and the batch's list is the
+  concatenation of the frames' own lists.
+* A batch beyond 2^22 row buckets (radix ordering) gives the same records in
+  the same order as its frames called one by one (row-bucket ordering).
 * A higher read-back threshold gives the ordered subset of the bank's list.
 * A list longer than the first speculative copy (sized from the previous
   call's count) is completed by the second copy.
@@ -102,4 +106,29 @@ def test_no_candidates():
     bank.run([to_device(flat)], [2.0, 4.0], D, 4, threshold=0.05)
     assert len(bank.blobs()) == 0
     assert len(bank.blobs(threshold=0.5)) == 0
+    bank.close()
+
+
+def test_radix_ordering_beyond_the_row_buckets_equals_the_row_bucket_ordering():
+    """64 frames of 4100 x 24 at 16 scales: 4.2 M row buckets, so the batched
+    call orders by radix; each frame alone (65,600 buckets) by row buckets."""
+    from paper_1912_07133_gb300 import kf
+    rng = np.random.default_rng(7)
+    frames = [rng.uniform(0, 1, (4100, 24)).astype(np.float32) for _ in range(64)]
+    scales = [2.0 + 0.25 * i for i in range(16)]
+    assert 64 * len(scales) * 4100 > (1 << 22)
+    ts = [to_device(f) for f in frames]
+    bank = kf.Bank(0)
+    bank.run(ts, scales, D, 3, threshold=0.02)
+    b = bank.blobs()
+    assert len(b) > 1000
+    k = keys(b, len(scales), 4100, 24)
+    assert np.all(np.diff(k) > 0)
+    for i in (0, 17, 63):
+        bank.run([ts[i]], scales, D, 3, threshold=0.02)
+        one = bank.blobs()
+        mine = b[b["frame"] == i]
+        assert len(one) == len(mine) > 0
+        for f in ("scale", "y", "x", "polarity", "response"):
+            assert np.array_equal(one[f], mine[f]), (i, f)
     bank.close()
