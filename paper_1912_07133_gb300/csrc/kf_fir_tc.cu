@@ -42,11 +42,13 @@
 //   warps 2-5   splitting: each thread takes one column of a landed chunk
 //               (held rows substituted at the frame's top and bottom), splits
 //               it and stores it into the chunk's tensor-memory slot;
-//   warps 6-9   epilogue: every scale of the tile out of tensor memory
-//               (per-pixel extremes over the scales, the optional
-//               responses), each scale's columns released to the next
-//               tile's MMAs as soon as they are read; then the 3 x 3 spatial
-//               test and the tile's candidate list.
+//   warps 6-13  epilogue, two warps per tensor-memory lane quarter (each
+//               reads one 32-row block of the accumulators): every scale of
+//               the tile out of tensor memory (per-pixel extremes over the
+//               scales, the optional responses), each scale's columns
+//               released to the next tile's MMAs once its readers are done;
+//               then the 3 x 3 spatial test (each warp half of the rows) and
+//               the tile's candidate list.
 // Tensor memory (512 columns): the accumulators of scale s at columns
 // [NR s, NR (s + 1)) (at most 384), two operand slots of 64 columns (hi,
 // lo) at 384 and 448.  Every wait is bounded; a wait that gives up sets the
@@ -70,7 +72,8 @@ constexpr int TC_M = 128;               // image columns per tile (MMA M, tensor
 constexpr int TC_CH = 32;               // input rows per chunk
 constexpr int TC_BOXW = 132;            // landed chunk width (f32): 128 columns + TMA alignment offset <= 3
 constexpr int TC_BOXW16 = 136;          // landed chunk width (16-bit): 128 columns + offset <= 7
-constexpr int TC_THREADS = 320;         // warps 0 (loads), 1 (MMA), 2-5 (split), 6-9 (epilogue)
+constexpr int TC_THREADS = 448;         // warps 0 (loads), 1 (MMA), 2-5 (split), 6-13 (epilogue)
+constexpr int TC_EPI = 256;             // epilogue threads: two warps per tensor-memory lane quarter
 constexpr int TC_MAXL = 6;              // landing slots at most
 constexpr int TC_ACOL = 384;            // tensor-memory column of the first operand slot
 constexpr int XS = TC_M + 1;            // row stride (floats) of the per-pixel extremes
@@ -150,18 +153,18 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
       : "memory");
 }
 
-// barrier of the 128 epilogue threads (warps 6-9), optionally with an OR of a predicate
+// barrier of the 256 epilogue threads (warps 6-13), optionally with an OR of a predicate
 __device__ __forceinline__ bool epi_sync_or(bool p) {
   uint32_t r;
   asm volatile(
-      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.or.pred po, 1, 128, pi;\n\t"
+      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.or.pred po, 1, 256, pi;\n\t"
       "selp.u32 %0, 1, 0, po;\n\t}"
       : "=r"(r)
       : "r"((uint32_t)p)
       : "memory");
   return r != 0;
 }
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 // barrier of the 128 splitting threads (warps 2-5), with an OR of a predicate
 __device__ __forceinline__ bool split_sync_or(bool p) {
   uint32_t r;
@@ -220,36 +223,29 @@ __device__ __forceinline__ bool tc_beats(const float *m, const unsigned char *am
 }
 
 // The spatial 3 x 3 test over the per-pixel extremes of an NR x 128 tile
-// (rows 0 and NR - 1, columns 0 and 127 halo) by the 128 epilogue threads:
+// (rows 0 and NR - 1, columns 0 and 127 halo) by the 256 epilogue threads:
 // warp ew takes columns [32 ew, 32 ew + 32), one per lane, and walks the
-// interior rows with the horizontal 3-maxima (3-minima) of three rows in
-// registers (left and right neighbours by shuffles, from shared memory at
-// the warp's edges); candidates are staged in the tile list.
+// interior rows [ib, ie) with the horizontal 3-maxima (3-minima) of three rows in
+// registers (left and right neighbours read from shared memory: shuffles
+// with the warp's edge lanes reading shared memory measured twice as slow);
+// candidates are staged in the tile list.
 __device__ void tc_detect(const float *mx, const float *mn, const unsigned char *amx, const unsigned char *amn,
-                          TcList &tl, const DetectArgs &a, int NR, int ew, int lane) {
-  constexpr unsigned FULL = 0xffffffffu;
+                          TcList &tl, const DetectArgs &a, int ew, int lane, int ib, int ie) {
   const int c = 32 * ew + lane;
   const int x = a.x0 + c;
   const bool col = c >= 1 && c <= TC_M - 2 && x >= 0 && x < a.W;
-  auto sidemax = [&](const float *m, int i, float v) {
-    const float u = __shfl_up_sync(FULL, v, 1), d = __shfl_down_sync(FULL, v, 1);
-    const float l = lane == 0 ? (c > 0 ? m[i * XS + c - 1] : -CUDART_INF_F) : u;
-    const float r = lane == 31 ? (c < TC_M - 1 ? m[i * XS + c + 1] : -CUDART_INF_F) : d;
-    return fmaxf(l, r);
-  };
-  auto sidemin = [&](const float *m, int i, float v) {
-    const float u = __shfl_up_sync(FULL, v, 1), d = __shfl_down_sync(FULL, v, 1);
-    const float l = lane == 0 ? (c > 0 ? m[i * XS + c - 1] : CUDART_INF_F) : u;
-    const float r = lane == 31 ? (c < TC_M - 1 ? m[i * XS + c + 1] : CUDART_INF_F) : d;
-    return fminf(l, r);
-  };
-  float vp = mx[c], wp = mn[c];
-  float xa = fmaxf(vp, sidemax(mx, 0, vp)), na = fminf(wp, sidemin(mn, 0, wp));  // row i - 1
-  float vc = mx[XS + c], wc = mn[XS + c];
-  float lx = sidemax(mx, 1, vc), ln = sidemin(mn, 1, wc);  // row i: the two side neighbours
-  for (int i = 1; i < NR - 1; ++i) {
+  // consecutive columns: conflict-free; the tile's edge columns are halo and
+  // never tested, so they read themselves
+  const int cl = c > 0 ? c - 1 : c, cr = c < TC_M - 1 ? c + 1 : c;
+  auto sidemax = [&](const float *m, int i) { return fmaxf(m[i * XS + cl], m[i * XS + cr]); };
+  auto sidemin = [&](const float *m, int i) { return fminf(m[i * XS + cl], m[i * XS + cr]); };
+  float vp = mx[(ib - 1) * XS + c], wp = mn[(ib - 1) * XS + c];
+  float xa = fmaxf(vp, sidemax(mx, ib - 1)), na = fminf(wp, sidemin(mn, ib - 1));
+  float vc = mx[ib * XS + c], wc = mn[ib * XS + c];
+  float lx = sidemax(mx, ib), ln = sidemin(mn, ib);
+  for (int i = ib; i < ie; ++i) {
     const float vn = mx[(i + 1) * XS + c], wn = mn[(i + 1) * XS + c];
-    const float lxn = sidemax(mx, i + 1, vn), lnn = sidemin(mn, i + 1, wn);
+    const float lxn = sidemax(mx, i + 1), lnn = sidemin(mn, i + 1);
     const int y = a.r0 + i;
     if (col && y >= 0 && y < a.H) {
       const float m8 = fmaxf(xa, fmaxf(lx, fmaxf(vn, lxn)));  // maximum of the 8 neighbours
@@ -274,7 +270,7 @@ __device__ void tc_flush(const DetectArgs &a, TcList &tl, unsigned long long &s_
   const int nloc = min(tl.n, TC_CANDS);
   if (t == 0 && nloc > 0) s_base = atomicAdd(&a.status->count, (unsigned long long)nloc);
   epi_sync();
-  for (int i = t; i < nloc; i += 128) {
+  for (int i = t; i < nloc; i += TC_EPI) {
     const unsigned long long idx = s_base + i;
     if (idx < (unsigned long long)a.cap) a.out[idx] = tl.rec[i];
   }
@@ -297,8 +293,7 @@ __device__ __forceinline__ TcTile tc_tile(int local, int W, int NR) {
   return {(local % ntx) * (TC_M - 2) - 1, (local / ntx) * (NR - 2) - 1};
 }
 
-// 320 threads of one CTA per SM (registers are allotted as for 12 warps: at
-// most 168 per thread)
+// 448 threads of one CTA per SM (at most 144 registers per thread)
 template <int ST>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_colfir_tc(const __grid_constant__ CUtensorMap map, const FrameDev *__restrict__ fr, Items it,
@@ -336,7 +331,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&sh.tap_empty[b], 1);
     }
     mbar_init(&sh.d_full, 1);
-    for (int t = 0; t < TC_MAXS; ++t) mbar_init(&sh.d_empty[t], 4);
+    for (int t = 0; t < TC_MAXS; ++t) mbar_init(&sh.d_empty[t], 4 * (g.NR / 32));  // the warps that read it
     mbar_init(&sh.fin, 1);
     sh.abort = 0;
     fence_proxy_async();
@@ -543,8 +538,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 6-9) ----------------
-    const int ew = warp - 6;            // 0..3: columns 32 ew .. of the spatial test
+    // ---------------- epilogue (warps 6-13) ----------------
+    // warp ew reads accumulator columns [32 half, + 32) of its quarter's
+    // lanes, then takes columns 32 (ew % 4) .. of the spatial test on half
+    // of the tile's interior rows
+    const int ew = warp - 6;            // 0..7
+    const int half = ew >> 2;           // accumulator block and row half
     const int quarter = warp & 3;       // tensor-memory lanes 32 quarter ..
     const int c = 32 * quarter + lane;  // tile column of this lane's accumulators
     const uint32_t lanes = (uint32_t)(32 * quarter) << 16;
@@ -568,12 +567,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       float *resp = F.resp;
       const long plane = (long)H * W;
       // per-pixel extremes over the scales (first scale attaining them) and
-      // the responses: accumulator column n is output row NR - 1 - n, read
-      // in blocks of 32 rows; after a scale's last block its columns go to
-      // the next tile's MMAs
+      // the responses: accumulator column n is output row NR - 1 - n; this
+      // warp reads the block of 32 at n0; once every reading warp has read a
+      // scale its columns go to the next tile's MMAs
 #pragma unroll 1
-      for (int n0 = 0; n0 < NR; n0 += 32) {
-        const bool last = n0 + 32 >= NR;
+      for (int n0 = 32 * half; n0 < NR && n0 < 32 * (half + 1); n0 += 32) {
+        const bool last = true;
         float vmax[32], vmin[32];
         uint32_t pmax[4] = {0, 0, 0, 0}, pmin[4] = {0, 0, 0, 0};  // 4 bits per row
 #pragma unroll
@@ -614,6 +613,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       ++ntile;
       if (ew == 0 && lane == 0) tl.n = 0;
       epi_sync();
+      const int ihalf = 1 + (NR - 2) / 2;  // interior rows [1, ihalf) and [ihalf, NR - 1)
       DetectArgs a = da;
       a.S = S;
       a.x0 = t.x0;
@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       a.H = H;
       a.W = W;
       a.frame = F.index;
-      tc_detect(mx, mn, amx, amn, tl, a, NR, ew, lane);
+      tc_detect(mx, mn, amx, amn, tl, a, ew & 3, lane, half ? ihalf : 1, half ? NR - 1 : ihalf);
       tc_flush(a, tl, sh.base, 32 * ew + lane);
     }
   }

@@ -196,7 +196,8 @@ __device__ __forceinline__ unsigned row_bucket(const Blob &r, int nscales, long 
 // bucket and slot of every passing candidate; the passing count
 __global__ void __launch_bounds__(256) k_rows_count(const Blob *__restrict__ b, long cap,
                                                     const unsigned long long *__restrict__ count, float thr,
-                                                    int nscales, long hmax, unsigned *__restrict__ cnt,
+                                                    int nscales, long hmax, long wmax, long nrows,
+                                                    unsigned *__restrict__ cnt,
                                                     unsigned *__restrict__ bid, unsigned *__restrict__ slot,
                                                     unsigned *__restrict__ npass) {
   const long n = list_n(count, cap);
@@ -205,7 +206,10 @@ __global__ void __launch_bounds__(256) k_rows_count(const Blob *__restrict__ b, 
     bool pass = false;
     if (i < n) {
       const Blob r = b[i];
-      pass = fabsf(r.response) > thr;
+      // a record outside the call's geometry (never written by the detectors)
+      // takes no bucket: the bucket index addresses the count array
+      pass = fabsf(r.response) > thr && r.frame >= 0 && r.scale >= 0 && r.scale < nscales && r.y >= 0 &&
+             r.y < hmax && r.x >= 0 && r.x < wmax && ((long)r.frame * nscales + r.scale) * hmax + r.y < nrows;
       unsigned k = ~0u;
       if (pass) {
         k = row_bucket(r, nscales, hmax);
@@ -375,7 +379,7 @@ int launch_sort(const Blob *blobs, long cap, const unsigned long long *count, fl
         cudaMemsetAsync(cnt, 0, (size_t)nrows * sizeof(unsigned), st) != cudaSuccess)
       return -1;
     prof->begin("sort_count", st);
-    k_rows_count<<<ng, 256, 0, st>>>(blobs, cap, count, thr, nscales, hmax, cnt, bid, slot, d_npass);
+    k_rows_count<<<ng, 256, 0, st>>>(blobs, cap, count, thr, nscales, hmax, wmax, nrows, cnt, bid, slot, d_npass);
     prof->end(st);
     prof->begin("sort_scan", st);
     k_rows_part<<<np, 1024, 0, st>>>(cnt, nrows, part);
