@@ -91,9 +91,9 @@ GATED_THRESHOLD = 0.3  # clustered frames: the 1/f background alone stays below 
 # (bytes, digest of the kernel sources the capture ran).  A figure is reported
 # only while the sources still have that digest; otherwise traffic is null.
 MEASURED_TRAFFIC = {
-    ("iir_fir", "fir_row", "f32"): (408.0e6, "6b270b19b71585eb"),     # k_rowfir: 67.3 read + 340.7 written
-    ("iir_fir", "fir_coldet", "f32"): (430.8e6, "6b270b19b71585eb"),  # k_colfir_tc: 424.5 + 6.3
-    ("iir_fir", "iir_row", "f32"): (406.1e6, "6b270b19b71585eb"),     # k_row: 67.3 + 338.8
+    ("iir_fir", "fir_row", "f32"): (408.0e6, "f124394df0a89444"),     # k_rowfir: 67.3 read + 340.7 written
+    ("iir_fir", "fir_coldet", "f32"): (432.4e6, "f124394df0a89444"),  # k_colfir_tc: 424.8 + 7.6
+    ("iir_fir", "iir_row", "f32"): (406.2e6, "f124394df0a89444"),     # k_row: 67.3 + 338.9
 }
 CSRC = os.path.join(ROOT, "paper_1912_07133_gb300", "csrc")
 
