@@ -343,6 +343,24 @@ def setup_device(args):
     return rank, world, local
 
 
+PASS_NAMES = ("row", "seg", "fold", "det")
+
+
+def shape_overrides(spec, bank_name):
+    """(pass, grid_mult) pairs of `spec` ("iir.row=-2,fir.row=-3": bank name
+    prefix before the first '_', pass name, kf_set_launch_shape value) that
+    apply to the bank `bank_name`."""
+    out = []
+    for part in filter(None, (spec or "").split(",")):
+        key, val = part.split("=")
+        bank, pname = key.strip().split(".")
+        if pname not in PASS_NAMES:
+            raise ValueError(f"--shape: unknown pass {pname!r} (one of {PASS_NAMES})")
+        if bank_name.split("_")[0] == bank:
+            out.append((pname, int(val)))
+    return out
+
+
 def measure_workload(args, name, steps, warmup, full=True):
     """Steps of one workload of WORKLOADS on this rank's GPU.  full: also the
     serial and frame-by-frame schedules, end to end and the profiled pass's
@@ -407,6 +425,12 @@ def measure_workload(args, name, steps, warmup, full=True):
                 tuned[bn]["column_pass"] = f"segments of {lc} rows"
             elif lc == 0:
                 tuned[bn]["column_pass"] = "single read"
+    # fixed launch shapes over the tuned ones (e.g. per-SM shares, so that the
+    # banks' kernels share every SM)
+    for bn, ft, _ in BANKS:
+        for pname, m in shape_overrides(args.shape, bn):
+            kf.kf_set_launch_shape(banks[bn].ctx, ft, PASS_NAMES.index(pname), m)
+            tuned.setdefault(bn, {}).setdefault("grid_mult", {})[pname] = m
 
     def run_bank(bn, frames, ft, order, profile=False, schedule=kf.KF_SCHED_BATCHED, use_graph=graph):
         banks[bn].run(frames, SCALES, ft, order, threshold=THRESHOLD, profile=profile, fir_kmax=wl["fir_kmax"],
@@ -1133,6 +1157,8 @@ def main():
     ap.add_argument("--sub-warmup", type=int, default=3, help="warm-up steps of each sub-workload (>= 3)")
     ap.add_argument("--column-pass", choices=("segments", "single-read"), default=None,
                     help="column pass of the recursive banks (with --no-tune it stays fixed)")
+    ap.add_argument("--shape", default=None,
+                    help="launch shapes over the tuned ones, e.g. iir.row=-2,fir.row=-3 (negative: blocks per SM)")
     ap.add_argument("--storage", choices=tuple(STORAGE), default=None,
                     help="element type of the one-sided planes (default: the workload's)")
     args = ap.parse_args()

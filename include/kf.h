@@ -370,8 +370,14 @@ int kf_kernel_times(kf_ctx *ctx, kf_kernel_time *out, int cap, int *n);
  * in turn:
  *   grid_mult = 0  one block per work item (the default);
  *   grid_mult = k  at most k x (blocks resident per SM for this kernel and
- *                  block size) x (SMs) blocks, each looping over items.
- * Results do not depend on the shape.  Errors: KF_EINVAL. */
+ *                  block size) x (SMs) blocks, each looping over items;
+ *   grid_mult = -b at most b blocks per SM (b = 1..16, capped at the blocks
+ *                  resident per SM) x (SMs): the pass takes a share of every
+ *                  SM and leaves the rest to kernels of other streams (banks
+ *                  of other contexts running at the same time).
+ * The tensor-core FIR column pass is always one block per SM and ignores the
+ * setting.  Results do not depend on the shape.  Errors: KF_EINVAL
+ * (grid_mult outside -16..64). */
 int kf_set_launch_shape(kf_ctx *ctx, int type, int pass, int grid_mult);
 
 /* Column segment length (scan block length of the column recursions) of a

@@ -47,6 +47,11 @@ struct kf_ctx {
     size_t bands_floats = 0;
     kf::TcGeom tc;
     bool tc_ok = false;
+    // FIR designs: the grouped tap table of the row pass
+    float *d_rowtaps = nullptr;
+    size_t rowtaps_floats = 0;
+    std::vector<float> h_rowtaps;
+    kf::RowGroups rg;
   };
   std::vector<Design> designs;
   unsigned long long tick = 0;
@@ -313,6 +318,22 @@ int ensure_design(kf_ctx *ctx, int type, int order, const double *scales, int S,
     if (!(std::fabs(c.dc_gain - 1.0) < 1e-6))
       return fail(ctx, KF_ECOND, "design for scale %g has dc gain %.9g", scales[s], c.dc_gain);
   }
+  // FIR designs: the row pass's grouped tap table
+  if (type == KF_FIR_COLORED_SG || type == KF_FIR_GAUSSIAN) {
+    const long nf = kf::row_groups(slot->h_coef.data(), S, &slot->rg, &slot->h_rowtaps);
+    if (nf <= 0) return fail(ctx, KF_EINVAL, "row tap table: %d scales", S);
+    if ((size_t)nf > slot->rowtaps_floats) {
+      if (slot->d_rowtaps) cudaFree(slot->d_rowtaps);
+      slot->d_rowtaps = nullptr;
+      slot->rowtaps_floats = 0;
+      if ((e = cudaMalloc(&slot->d_rowtaps, (size_t)nf * sizeof(float))) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMalloc(row tap table)");
+      slot->rowtaps_floats = (size_t)nf;
+    }
+    if ((e = cudaMemcpyAsync(slot->d_rowtaps, slot->h_rowtaps.data(), (size_t)nf * sizeof(float),
+                             cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "copy row tap table");
+  }
   // FIR designs of at most 8 scales: the band operands of the tensor-core
   // column pass (R_L = -sigma^2 (...): the taps carry the sign)
   slot->tc_ok = false;
@@ -481,7 +502,7 @@ void kf_destroy(kf_ctx *ctx) {
   cudaFree(ctx->edge);
   cudaFree(ctx->carry);
   cudaFree(ctx->scan);
-  for (auto &d : ctx->designs) cudaFree(d.d_coef), cudaFree(d.d_bands);
+  for (auto &d : ctx->designs) cudaFree(d.d_coef), cudaFree(d.d_bands), cudaFree(d.d_rowtaps);
   cudaFree(ctx->sorted);
   cudaFree(ctx->sort_work);
   cudaFree(ctx->d_npass);
@@ -530,7 +551,7 @@ int kf_design(int type, int order, double scale, kf_coeffs *out) {
   rc = ensure_design(&tmp, type, order, &scale, 1, 96);
   kf::Coef c{};
   if (!rc) c = tmp.cur->h_coef[0];
-  for (auto &d : tmp.designs) cudaFree(d.d_coef), cudaFree(d.d_bands);
+  for (auto &d : tmp.designs) cudaFree(d.d_coef), cudaFree(d.d_bands), cudaFree(d.d_rowtaps);
   cudaFree(tmp.lambdas);
   cudaFree(tmp.dwork);
   if (rc) return fail(nullptr, rc, "%s", tmp.err.c_str());
@@ -895,6 +916,10 @@ int kf_filter_bank(kf_ctx *ctx, const kf_frame *frames, int nframes, const doubl
   a.status = ctx->status;
   a.wait_test = ctx->wait_test;
   a.zero = opts.boundary == KF_BOUNDARY_ZERO;
+  if (!iir) {
+    a.row_taps = ctx->cur->d_rowtaps;
+    a.rg = ctx->cur->rg;
+  }
   if (tcpass) {
     a.tc_bands = ctx->cur->d_bands;
     a.tc = ctx->cur->tc;
@@ -1056,7 +1081,7 @@ int kf_set_launch_shape(kf_ctx *ctx, int type, int pass, int grid_mult) {
   if (!ctx) return fail(nullptr, KF_EINVAL, "kf_set_launch_shape: ctx is NULL");
   if (type < 0 || type >= KF_NTYPES) return fail(ctx, KF_EINVAL, "unknown filter type %d", type);
   if (pass < 0 || pass >= KF_NPASS) return fail(ctx, KF_EINVAL, "unknown pass %d", pass);
-  if (grid_mult < 0 || grid_mult > 64) return fail(ctx, KF_EINVAL, "grid_mult must be 0..64");
+  if (grid_mult < -16 || grid_mult > 64) return fail(ctx, KF_EINVAL, "grid_mult must be -16..64");
   if (ctx->grid_mult[type][pass] != grid_mult) {
     drop_graphs(ctx);  // grid sizes are part of the captured launches
     ctx->grid_mult[type][pass] = grid_mult;

@@ -117,70 +117,101 @@ __device__ __forceinline__ void fir_block(const float *sh, int K, At at, float (
 // 4-bank groups.
 __host__ __device__ __forceinline__ constexpr int pad20(int e) { return e + ((e >> 4) << 2); }
 
-// One block of 8 taps for NOUT consecutive outputs.  pa / pb point at the
-// padded positions of the 16-element groups holding the left / right windows;
-// OA / OB (0 or 8) are the windows' offsets inside them, so every load address
-// is a compile-time offset from the two pointers.  hk: the 8 taps (16-byte
-// aligned).
+// Scales of one group of the row pass: the pair sums x(j - k) + x(j + k) are
+// the same for every scale, so a group forms each sum once and applies the
+// taps of all its scales whose half-length reaches k.  The scales are ordered
+// by K, largest first; groups of three keep the accumulators at 48 registers.
+constexpr int RGS = ROW_GS;
+constexpr int RWIN = NOUT + TB;  // window length of a block of 8 taps
+
+// The two windows of one block of 8 taps: pa / pb point at the padded
+// positions of the 16-element groups holding the left / right windows; OA / OB
+// (0 or 8) are the windows' offsets inside them, so every load address is a
+// compile-time offset from the two pointers.
 template <int OA, int OB>
-__device__ __forceinline__ void fir_row_taps8(const float *hk_s, const float *pa, const float *pb,
-                                              float (&acc)[NOUT]) {
-  float A[NOUT + TB], B[NOUT + TB], hk[TB];
-  const float4 h03 = *reinterpret_cast<const float4 *>(hk_s), h47 = *reinterpret_cast<const float4 *>(hk_s + 4);
-  hk[0] = h03.x, hk[1] = h03.y, hk[2] = h03.z, hk[3] = h03.w;
-  hk[4] = h47.x, hk[5] = h47.y, hk[6] = h47.z, hk[7] = h47.w;
+__device__ __forceinline__ void fir_row_windows(const float *pa, const float *pb, float (&A)[RWIN],
+                                                float (&B)[RWIN]) {
 #pragma unroll
-  for (int q = 0; q < (NOUT + TB) / 4; ++q) {
+  for (int q = 0; q < RWIN / 4; ++q) {
     const float4 a = *reinterpret_cast<const float4 *>(pa + pad20(OA + 4 * q));  // A[m] = x(base + m - k0 - 7)
     const float4 b = *reinterpret_cast<const float4 *>(pb + pad20(OB + 4 * q));  // B[m] = x(base + m + k0 - 1)
     A[4 * q + 0] = a.x, A[4 * q + 1] = a.y, A[4 * q + 2] = a.z, A[4 * q + 3] = a.w;
     B[4 * q + 0] = b.x, B[4 * q + 1] = b.y, B[4 * q + 2] = b.z, B[4 * q + 3] = b.w;
   }
-  // output j, tap k0 + u: x(j - k0 - u) = A[j - u + 7], x(j + k0 + u) = B[j + u + 1]
-#pragma unroll
-  for (int u = 0; u < TB; ++u)
-#pragma unroll
-    for (int j = 0; j < NOUT; ++j) acc[j] = fmaf(hk[u], A[j - u + TB - 1] + B[j + u + 1], acc[j]);
 }
 
-// Symmetric FIR of NOUT consecutive outputs from a padded row: `row` points at
-// element 0, `base` (a multiple of 16) is the first output, sh[k] = h_k with
-// sh + 1 16-byte aligned.  Taps are used 8 at a time: block i reads the left
+// One block of 8 taps for NOUT consecutive outputs of the first NA scales of
+// a group.  T[u]: the taps k0 + u of the group's scales (.x, .y, .z; zero
+// beyond a scale's K).  Per scale the products are accumulated in increasing
+// k, as a one-scale pass would.
+template <int NA>
+__device__ __forceinline__ void fir_row_mac8(const float (&A)[RWIN], const float (&B)[RWIN], const float4 *T,
+                                             float (&acc)[RGS][NOUT]) {
+  // output j, tap k0 + u: x(j - k0 - u) = A[j - u + 7], x(j + k0 + u) = B[j + u + 1]
+#pragma unroll
+  for (int u = 0; u < TB; ++u) {
+    const float4 h = T[u];
+#pragma unroll
+    for (int j = 0; j < NOUT; ++j) {
+      const float v = A[j - u + TB - 1] + B[j + u + 1];
+      acc[0][j] = fmaf(h.x, v, acc[0][j]);
+      if (NA > 1) acc[1][j] = fmaf(h.y, v, acc[1][j]);
+      if (NA > 2) acc[2][j] = fmaf(h.z, v, acc[2][j]);
+    }
+  }
+}
+
+// Symmetric FIR of NOUT consecutive outputs for the scales of one group from
+// a padded row: `row` points at element 0, `base` (a multiple of 16) is the
+// first output, T[k] = the group's taps h_k (half-lengths K0 >= K1 >= K2; -1
+// for a missing scale).  Taps are used 8 at a time: block i reads the left
 // window x(base-8(i+1) .. +23) and the right window x(base+8i .. +23), six
-// 128-bit loads each.  Blocks go in pairs, so that the windows move by one
-// 16-element group per pair.
-__device__ __forceinline__ void fir_row_block(const float *sh, int K, const float *row, int base,
-                                              float (&acc)[NOUT]) {
-  const float h0 = sh[0];
+// 128-bit loads each; the windows move by one 16-element group every second
+// block.  The block's scales are those whose half-length reaches its first
+// tap (the first na of the group).
+__device__ __forceinline__ void fir_row_group(const float4 *T, int K0, int K1, int K2, const float *row, int base,
+                                              float (&acc)[RGS][NOUT]) {
+  const float4 h0 = T[0];
   const float *p0 = row + pad20(base);
 #pragma unroll
   for (int q = 0; q < NOUT / 4; ++q) {
     const float4 v = *reinterpret_cast<const float4 *>(p0 + pad20(4 * q));
-    acc[4 * q + 0] = h0 * v.x;
-    acc[4 * q + 1] = h0 * v.y;
-    acc[4 * q + 2] = h0 * v.z;
-    acc[4 * q + 3] = h0 * v.w;
+    const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      acc[0][4 * q + e] = h0.x * x[e];
+      acc[1][4 * q + e] = h0.y * x[e];
+      acc[2][4 * q + e] = h0.z * x[e];
+    }
   }
-  // pair n (blocks i = 2n, 2n + 1): the left windows start at 16(m - n - 1) + 8
-  // and 16(m - n - 1), the right ones at 16(m + n) and 16(m + n) + 8 (m = base / 16)
+  // block 2n reads its left window at 16(m - n - 1) + 8 and its right one at
+  // 16(m + n); block 2n + 1 at 16(m - n - 1) and 16(m + n) + 8 (m = base / 16)
   const float *pa = row + 20 * ((base >> 4) - 1), *pb = row + 20 * (base >> 4);
-  int k0 = 1;
-  for (; k0 + TB <= K; k0 += 2 * TB) {
-    fir_row_taps8<8, 0>(sh + k0, pa, pb, acc);
-    fir_row_taps8<0, 8>(sh + k0 + TB, pa, pb, acc);
-    pa -= 20;
-    pb += 20;
+  for (int k0 = 1, odd = 0; k0 <= K0; k0 += TB, odd ^= 1) {
+    float A[RWIN], B[RWIN];
+    if (odd) fir_row_windows<0, 8>(pa, pb, A, B);
+    else fir_row_windows<8, 0>(pa, pb, A, B);
+    const int na = 1 + (K1 >= k0) + (K2 >= k0);
+    if (na == 3) fir_row_mac8<3>(A, B, T + k0, acc);
+    else if (na == 2) fir_row_mac8<2>(A, B, T + k0, acc);
+    else fir_row_mac8<1>(A, B, T + k0, acc);
+    if (odd) pa -= 20, pb += 20;
   }
-  if (k0 <= K) fir_row_taps8<8, 0>(sh + k0, pa, pb, acc);
 }
 
 // halo of the row kernel: >= kmax + TB, a multiple of 16
 __host__ __device__ __forceinline__ int row_halo(int kmax) { return (kmax + TB + 15) / 16 * 16; }
+// tap table of the row kernel: entries per group (taps 0 .. K rounded up to
+// whole 8-tap blocks) and its offset (floats, 16-byte aligned) after the
+// padded row of n elements
+__host__ __device__ __forceinline__ int row_taps_len(int kmax) { return (kmax + TB - 1) / TB * TB + 1; }
+__host__ __device__ __forceinline__ int row_taps_offset(int n) { return (pad20(n) + 3) / 4 * 4; }
 
 // Row pass.  Item: a segment of RSEG outputs of one row of a frame; items
 // beyond the frame's H rows are its U-only first and last rows.
-__global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr, Items it,
-                                                const Coef *__restrict__ coef, int S, int kmax,
+__global__ void __launch_bounds__(RNT, 4) k_rowfir(const FrameDev *__restrict__ fr, Items it,
+                                                const Coef *__restrict__ coef, const float4 *__restrict__ taps,
+                                                RowGroups rg, int kmax,
                                                 void *__restrict__ P, int st, long PWb, float *__restrict__ edge,
                                                 DevStatus *__restrict__ status, int chan, int zero) {
   extern __shared__ __align__(16) float sm[];
@@ -190,8 +221,19 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr,
   const int G = row_halo(kmax);
   const int n = RSEG + 2 * G;
   float *sL = sm;                       // padded: element j at pad20(j)
-  float *sh = sm + pad20(n) + 4 + 3;      // taps h_k at sh[k]; sh + 1 is 16-byte aligned
+  // taps of the scale groups: T[g * TK + k] = h_k of the group's scales
+  float4 *T = reinterpret_cast<float4 *>(sm + row_taps_offset(n));
+  const int S = rg.S, NG = rg.NG, TK = rg.TK;
+  __shared__ int s_ord[ROW_MAXS];       // scales by half-length, largest first
+  __shared__ int s_K[ROW_MAXS + 2];     // half-length of group slot i (-1: empty)
   __shared__ FrameDev s_fr;
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < ROW_MAXS; ++i) s_ord[i] = rg.ord[i];
+#pragma unroll
+    for (int i = 0; i < ROW_MAXS + 2; ++i) s_K[i] = rg.K[i];
+  }
+  for (int e = tid; e < NG * TK; e += RNT) T[e] = taps[e];
   bool ovf = false;                     // a value beyond the f16 range
   int k = 0;
   const int nitems = items_total(it);
@@ -292,32 +334,22 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr,
         }
       }
     });
+    __syncthreads();  // L staged
     const int base = G + NOUT * tid;  // local index of this thread's first output
-    for (int s = 0; s < S; ++s) {
-      const Coef &c = coef[s];
-      const int K = c.K;
-      __syncthreads();
-      stage_taps(sh, c, K, tid, RNT);
-      __syncthreads();
-      float acc[NOUT];
-      fir_row_block(sh, K, sL, base, acc);
-      // planes hold sigma^2 x the one-sided blur (the column pass only
-      // negates; the blur alone for CH_ID)
-      const float s2 = chan == CH_ID ? 1.f : c.sigma2;
-#pragma unroll
-      for (int j = 0; j < NOUT; ++j) acc[j] *= s2;
-      const int x0 = xs + NOUT * tid;
+    const int x0 = xs + NOUT * tid;
+    // one plane row of scale s from NOUT outputs (f32 or 16-bit planes)
+    auto store = [&](int s, const float (&v)[NOUT]) {
       const long row = (F.prow + (long)s * H + y) * PWb;
       if (EDGE || st == ST_F32) {
         float *dst = EDGE ? edge + F.eoff + ((long)s * 2 + which) * PWb : static_cast<float *>(P) + row;
         if (x0 + NOUT <= W) {
 #pragma unroll
           for (int j = 0; j < NOUT; j += 4)
-            *reinterpret_cast<float4 *>(dst + x0 + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+            *reinterpret_cast<float4 *>(dst + x0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         } else {
 #pragma unroll
           for (int j = 0; j < NOUT; ++j)
-            if (x0 + j < W) dst[x0 + j] = acc[j];
+            if (x0 + j < W) dst[x0 + j] = v[j];
         }
       } else {
         // 16-bit planes: four values per 8-byte store
@@ -326,10 +358,10 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr,
 #pragma unroll
         for (int j = 0; j < NOUT; ++j) {
           if (st == ST_F16) {
-            ovf |= x0 + j < W && fabsf(acc[j]) > F16_MAX;
-            h[j] = __half_as_ushort(__float2half_rn(acc[j]));
+            ovf |= x0 + j < W && fabsf(v[j]) > F16_MAX;
+            h[j] = __half_as_ushort(__float2half_rn(v[j]));
           } else {
-            h[j] = __bfloat16_as_ushort(__float2bfloat16_rn(acc[j]));
+            h[j] = __bfloat16_as_ushort(__float2bfloat16_rn(v[j]));
           }
         }
         if (x0 + NOUT <= W) {
@@ -342,6 +374,21 @@ __global__ void __launch_bounds__(RNT) k_rowfir(const FrameDev *__restrict__ fr,
           for (int j = 0; j < NOUT; ++j)
             if (x0 + j < W) dst[x0 + j] = h[j];
         }
+      }
+    };
+    for (int g = 0; g < NG; ++g) {
+      float acc[RGS][NOUT];
+      fir_row_group(T + g * TK, s_K[g * RGS], s_K[g * RGS + 1], s_K[g * RGS + 2], sL, base, acc);
+#pragma unroll
+      for (int i = 0; i < RGS; ++i) {
+        if (g * RGS + i >= S) break;
+        const int sc = s_ord[g * RGS + i];
+        // planes hold sigma^2 x the one-sided blur (the column pass only
+        // negates; the blur alone for CH_ID)
+        const float s2 = chan == CH_ID ? 1.f : coef[sc].sigma2;
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) acc[i][j] *= s2;
+        store(sc, acc[i]);
       }
     }
   }
@@ -813,7 +860,8 @@ int persistent_blocks(const void *kernel, int threads, size_t smem, int items, i
       cache[key] = occ;
     }
   }
-  const long cap = (long)nsm[dev] * occ * mult;
+  // mult < 0: a share of -mult blocks on every SM (at most the resident limit)
+  const long cap = mult < 0 ? (long)nsm[dev] * std::min(occ, -mult) : (long)nsm[dev] * occ * mult;
   return (int)std::max(1L, std::min((long)items, cap));
 }
 
@@ -833,6 +881,28 @@ int fir_items(int pass, int H, int W, int S, int neigh, bool tc) {
   }
 }
 
+long row_groups(const Coef *h_coef, int S, RowGroups *g, std::vector<float> *table) {
+  if (S < 1 || S > ROW_MAXS) return -1;
+  RowGroups r;
+  r.S = S;
+  r.NG = (S + RGS - 1) / RGS;
+  int kmax = 0;
+  for (int i = 0; i < S; ++i) r.ord[i] = i, kmax = std::max(kmax, h_coef[i].K);
+  std::stable_sort(r.ord, r.ord + S, [&](int a, int b) { return h_coef[a].K > h_coef[b].K; });
+  for (int i = 0; i < ROW_MAXS + 2; ++i) r.K[i] = i < S ? h_coef[r.ord[i]].K : -1;
+  r.TK = row_taps_len(kmax);
+  table->assign((size_t)4 * r.NG * r.TK, 0.f);
+  for (int gi = 0; gi < r.NG; ++gi)
+    for (int i = 0; i < RGS; ++i) {
+      const int slot = gi * RGS + i;
+      if (slot >= S) continue;
+      const Coef &c = h_coef[r.ord[slot]];
+      for (int k = 0; k <= c.K; ++k) (*table)[((size_t)gi * r.TK + k) * 4 + i] = c.h[k];
+    }
+  *g = r;
+  return (long)table->size();
+}
+
 int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
@@ -844,7 +914,9 @@ int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st) {
   const int G = kmax + TB;
   const int KP = ((kmax + TB - 1) / TB) * TB;
   const int RG = row_halo(kmax);
-  const size_t rsm = (size_t)(pad20(RSEG + 2 * RG) + 4 + 3 + KP + 1) * sizeof(float);
+  if (!a.row_taps || a.rg.S != a.S || a.rg.TK > row_taps_len(kmax)) return -1;
+  const size_t rsm = (size_t)row_taps_offset(RSEG + 2 * RG) * sizeof(float) +
+                     (size_t)a.rg.NG * a.rg.TK * sizeof(float4);
   DetectArgs da;
   da.thr = a.threshold;
   da.neigh = a.neigh;
@@ -863,8 +935,8 @@ int launch_fir(const Plan &p, const BankArgs &a, cudaStream_t st) {
   auto row = [&](const Launch &l) {
     const int nb = persistent_blocks((const void *)k_rowfir, RNT, rsm, l.it.total, p.mult[PASS_ROW]);
     a.prof->begin("fir_row", st);
-    k_rowfir<<<nb, RNT, rsm, st>>>(p.fr, l.it, a.coef, a.S, kmax, a.P, a.storage, p.PWb, a.edge, a.status,
-                                   a.chan, a.zero);
+    k_rowfir<<<nb, RNT, rsm, st>>>(p.fr, l.it, a.coef, reinterpret_cast<const float4 *>(a.row_taps), a.rg, kmax,
+                                   a.P, a.storage, p.PWb, a.edge, a.status, a.chan, a.zero);
     a.prof->end(st);
   };
   auto det = [&](const Launch &l) -> int {

@@ -50,6 +50,21 @@ struct TcGeom {
   long floats = 0;
 };
 
+// FIR row pass: the call's scales ordered by half-length (largest first) in
+// groups of three that share the pair sums x(j - k) + x(j + k), and the
+// grouped tap table: entry g * TK + k holds h_k of the group's three scales
+// (four floats, the fourth zero; zero beyond a scale's K).  Built on the host
+// from the design (kf_fir.cu).
+constexpr int ROW_GS = 3;
+constexpr int ROW_MAXS = 16;
+struct RowGroups {
+  int S = 0, NG = 0, TK = 0;
+  int ord[ROW_MAXS] = {};       // scales by K, largest first (stable)
+  int K[ROW_MAXS + 2] = {};     // half-length of group slot i (-1: empty)
+};
+// fills g and the table (4 x NG x TK floats); returns its length in floats
+long row_groups(const Coef *h_coef, int S, RowGroups *g, std::vector<float> *table);
+
 struct BankArgs {
   const Coef *coef;      // device, S entries
   int S;
@@ -80,6 +95,9 @@ struct BankArgs {
   // and their geometry; null: the pass does not apply to this call
   const float *tc_bands = nullptr;
   TcGeom tc;
+  // FIR row pass: the design's grouped tap table (device) and its groups
+  const float *row_taps = nullptr;
+  RowGroups rg;
   // single-read IIR column pass (k_colscan): scratch of the launch (ticket,
   // publication flags, the super-tiles' end states and carries); null: the
   // segment passes (k_colseg, k_colfold, k_coldet) run instead
@@ -153,7 +171,9 @@ int encode_plane_map(CUtensorMap *m, void *P, int storage, long PWb, long prows,
 
 // blocks of a launch over `items` work items: mult = 0, one block per item;
 // mult = k >= 1, at most k x the blocks of this kernel and block shape that are
-// resident on the whole GPU at once (each block loops over items)
+// resident on the whole GPU at once (each block loops over items); mult = -b,
+// b blocks per SM (at most the resident limit) so that kernels of other
+// streams keep the rest of every SM
 int persistent_blocks(const void *kernel, int threads, size_t smem, int items, int mult);
 
 // proposal network (kf_proposal.cu): flat parameters W1 b1 W2 b2 W3 b3

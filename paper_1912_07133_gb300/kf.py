@@ -390,7 +390,8 @@ def kf_responses_noalloc(frame, scales, ftype: int, order: int, responses, strea
 
 def kf_set_launch_shape(ctx: int, ftype: int, pass_: int, grid_mult: int) -> None:
     """Launch shape of one pass (0: one block per work item; k: k x the
-    resident blocks of the GPU, looping over items)."""
+    resident blocks of the GPU, looping over items; -b: b blocks per SM, a
+    share that leaves the rest of every SM to other streams' kernels)."""
     _check(load().kf_set_launch_shape(ctx, ftype, pass_, grid_mult), ctx)
 
 

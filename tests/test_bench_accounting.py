@@ -6,6 +6,8 @@ import math
 import os
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
@@ -125,3 +127,12 @@ def test_traffic_needs_a_capture_of_the_current_sources(tmp_path, monkeypatch):
     (tmp_path / "a.cu").write_text("kernel A, changed")
     assert bench.csrc_digest() != d
     assert bench.traffic_of("w", "k", "f32") is None
+
+
+def test_shape_overrides_pick_the_bank_and_pass():
+    spec = "iir.row=-2,iir.det=-2,fir.row=-3"
+    assert bench.shape_overrides(spec, "iir_repeated_pole_order4") == [("row", -2), ("det", -2)]
+    assert bench.shape_overrides(spec, "fir_colored_sg") == [("row", -3)]
+    assert bench.shape_overrides(None, "fir_colored_sg") == []
+    with pytest.raises(ValueError):
+        bench.shape_overrides("iir.col=1", "iir_repeated_pole_order4")

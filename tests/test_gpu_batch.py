@@ -157,7 +157,8 @@ def test_launch_shapes_do_not_change_results(ftype, order):
     n = sum(len(SCALES) * t.numel() for t in ts)
     ref = None
     bank = kf.Bank(0)
-    for mult in kf.GRID_CANDIDATES:
+    # the tuner's candidates and per-SM shares (one or three blocks per SM)
+    for mult in list(kf.GRID_CANDIDATES) + [-1, -3]:
         for p in range(kf.KF_NPASS):
             kf.kf_set_launch_shape(bank.ctx, ftype, p, mult)
         R = torch.full((n,), float("nan"), device="cuda")
@@ -166,8 +167,9 @@ def test_launch_shapes_do_not_change_results(ftype, order):
         if ref is None:
             ref = got
         assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), mult
-    with pytest.raises(kf.KfError):
-        kf.kf_set_launch_shape(bank.ctx, ftype, 7, 1)
+    for p, m in [(7, 1), (0, -17), (0, 65)]:
+        with pytest.raises(kf.KfError):
+            kf.kf_set_launch_shape(bank.ctx, ftype, p, m)
     bank.close()
 
 
