@@ -37,6 +37,7 @@ namespace {
 constexpr int NOUT = 16;             // outputs per thread (register block)
 constexpr int TB = 8;                // taps per block of the inner loop
 constexpr int RNT = 128;             // threads per row CTA
+constexpr int RLD = 8;               // row staging: elements per thread in flight (5 loads each)
 constexpr int RSEG = RNT * NOUT;     // outputs per row CTA (2048)
 constexpr int CNT = 128;             // threads per column CTA (4 warps x 32 columns)
 constexpr int CROWS = 4 * NOUT;      // output rows per column CTA (64, incl. 2 halo rows)
@@ -209,7 +210,7 @@ __host__ __device__ __forceinline__ int row_taps_offset(int n) { return (pad20(n
 
 // Row pass.  Item: a segment of RSEG outputs of one row of a frame; items
 // beyond the frame's H rows are its U-only first and last rows.
-__global__ void __launch_bounds__(RNT, 4) k_rowfir(const FrameDev *__restrict__ fr, Items it,
+__global__ void __launch_bounds__(RNT, 512 / RNT) k_rowfir(const FrameDev *__restrict__ fr, Items it,
                                                 const Coef *__restrict__ coef, const float4 *__restrict__ taps,
                                                 RowGroups rg, int kmax,
                                                 void *__restrict__ P, int st, long PWb, float *__restrict__ edge,
@@ -235,14 +236,17 @@ __global__ void __launch_bounds__(RNT, 4) k_rowfir(const FrameDev *__restrict__ 
   }
   for (int e = tid; e < NG * TK; e += RNT) T[e] = taps[e];
   bool ovf = false;                     // a value beyond the f16 range
-  int k = 0;
+  int k = 0, staged = -1;
   const int nitems = items_total(it);
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     int local;
     k = item_frame(it, item, k, local);
     __syncthreads();  // the previous item is done with s_fr and sL
-    stage_frame(&s_fr, fr, it, k);
-    __syncthreads();
+    if (k != staged) {  // the frame record, staged again only for another frame
+      stage_frame(&s_fr, fr, it, k);
+      staged = k;
+      __syncthreads();
+    }
     const FrameDev &F = s_fr;
     const int H = F.H, W = F.W;
     const int nxs = (W + RSEG - 1) / RSEG;
@@ -307,11 +311,11 @@ __global__ void __launch_bounds__(RNT, 4) k_rowfir(const FrameDev *__restrict__ 
         }
         return;
       }
-      // 4 elements (20 loads, clamped into the row) per thread in flight
-      for (int j0 = tid; j0 < n; j0 += 4 * RNT) {
-        float cm[4], c0[4], cp[4], um[4], up[4];
+      // RLD elements (5 RLD loads, clamped into the row) per thread in flight
+      for (int j0 = tid; j0 < n; j0 += RLD * RNT) {
+        float cm[RLD], c0[RLD], cp[RLD], um[RLD], up[RLD];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < RLD; ++u) {
           const int e = min(max(xs - G + j0 + u * RNT, 0), W - 1);
           c0[u] = ld(r0, e);
           um[u] = ld(r0, max(e - 1, 0));
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(RNT, 4) k_rowfir(const FrameDev *__restrict__ 
           cp[u] = ld(rp, e);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < RLD; ++u) {
           const int j = j0 + u * RNT, e = xs - G + j;
           if (j >= n) continue;
           float v;
