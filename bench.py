@@ -91,9 +91,9 @@ GATED_THRESHOLD = 0.3  # clustered frames: the 1/f background alone stays below 
 # (bytes, digest of the kernel sources the capture ran).  A figure is reported
 # only while the sources still have that digest; otherwise traffic is null.
 MEASURED_TRAFFIC = {
-    ("iir_fir", "fir_row", "f32"): (410.2e6, "7c2bfdad3c3d4526"),     # k_rowfir: 67.25 read + 342.94 written
-    ("iir_fir", "fir_coldet", "f32"): (429.4e6, "7c2bfdad3c3d4526"),  # k_colfir_tc: 421.84 + 7.58
-    ("iir_fir", "iir_row", "f32"): (406.1e6, "7c2bfdad3c3d4526"),     # k_row: 67.27 + 338.84
+    ("iir_fir", "fir_row", "f32"): (410.3e6, "9ea06d9fd8c98d98"),     # k_rowfir: 67.29 read + 342.98 written
+    ("iir_fir", "fir_coldet", "f32"): (431.4e6, "9ea06d9fd8c98d98"),  # k_colfir_tc: 423.76 + 7.65
+    ("iir_fir", "iir_row", "f32"): (406.0e6, "9ea06d9fd8c98d98"),     # k_row: 67.28 + 338.72
 }
 CSRC = os.path.join(ROOT, "paper_1912_07133_gb300", "csrc")
 
