@@ -45,6 +45,7 @@ independent replica on its own GPU (weak scaling); rank 0 prints one JSON line.
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -91,23 +92,34 @@ GATED_THRESHOLD = 0.3  # clustered frames: the 1/f background alone stays below 
 # (bytes, digest of the kernel sources the capture ran).  A figure is reported
 # only while the sources still have that digest; otherwise traffic is null.
 MEASURED_TRAFFIC = {
-    ("iir_fir", "fir_row", "f32"): (410.3e6, "9ea06d9fd8c98d98"),     # k_rowfir: 67.29 read + 342.98 written
-    ("iir_fir", "fir_coldet", "f32"): (431.4e6, "9ea06d9fd8c98d98"),  # k_colfir_tc: 423.76 + 7.65
-    ("iir_fir", "iir_row", "f32"): (406.0e6, "9ea06d9fd8c98d98"),     # k_row: 67.28 + 338.72
+    ("iir_fir", "fir_row", "f32"): (410.3e6, "bc30a23c87b096b4"),     # k_rowfir: 67.29 read + 342.98 written
+    ("iir_fir", "fir_coldet", "f32"): (431.4e6, "bc30a23c87b096b4"),  # k_colfir_tc: 423.76 + 7.65
+    ("iir_fir", "iir_row", "f32"): (406.0e6, "bc30a23c87b096b4"),     # k_row: 67.28 + 338.72
 }
 CSRC = os.path.join(ROOT, "paper_1912_07133_gb300", "csrc")
 
 
+_COMMENT_OR_LITERAL = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'', re.S)
+
+
+def code_only(text):
+    """C++/CUDA source without its comments (string and character literals
+    kept), whitespace runs collapsed: what the compiler sees of it."""
+    text = _COMMENT_OR_LITERAL.sub(lambda m: " " if m.group(0).startswith("/") else m.group(0), text)
+    return " ".join(text.split())
+
+
 def csrc_digest():
-    """sha256 (first 16 hex digits) over the CUDA sources of the library, in
-    name order: changes whenever any kernel changes."""
+    """sha256 (first 16 hex digits) over the CUDA sources of the library
+    without their comments, in name order: changes whenever any kernel's code
+    changes, not when only a comment does."""
     import hashlib
     h = hashlib.sha256()
     for name in sorted(os.listdir(CSRC)):
         if name.endswith((".cu", ".cuh", ".h")):
             h.update(name.encode())
-            with open(os.path.join(CSRC, name), "rb") as f:
-                h.update(f.read())
+            with open(os.path.join(CSRC, name), encoding="utf-8") as f:
+                h.update(code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -12,7 +12,8 @@
 // kf_batch.cuh):
 //   k_rowfir      (row, 2048-pixel segment) items: L with a K-pixel halo in
 //                 shared memory, 16 outputs per thread in 8-tap register
-//                 blocks, all scales; two extra rows per frame on U alone.
+//                 blocks, all scales in groups of three that share the
+//                 symmetric pair sums; two extra rows per frame on U alone.
 //   k_colfir_tma  128 rows x 32 columns x all scales per item, TMA-staged,
 //                 all-scales detector.
 //   k_colfir      64 rows x 32 columns, adjacent-scales detector.

@@ -136,3 +136,18 @@ def test_shape_overrides_pick_the_bank_and_pass():
     assert bench.shape_overrides(None, "fir_colored_sg") == []
     with pytest.raises(ValueError):
         bench.shape_overrides("iir.col=1", "iir_repeated_pole_order4")
+
+
+def test_digest_follows_code_not_comments(tmp_path, monkeypatch):
+    """A comment-only edit keeps the source digest (the stored traffic stays
+    valid); an edit of the code, even inside a string literal, changes it."""
+    monkeypatch.setattr(bench, "CSRC", str(tmp_path))
+    src = tmp_path / "k.cu"
+    src.write_text('// a kernel\n__global__ void k(float *p) { p[0] = 1.f; /* one */ }\nconst char *s = "// x";\n')
+    d = bench.csrc_digest()
+    src.write_text('// a kernel, reworded\n__global__ void k(float *p) {\n  p[0] = 1.f;  // one\n}\nconst char *s = "// x";\n')
+    assert bench.csrc_digest() == d
+    src.write_text('// a kernel\n__global__ void k(float *p) { p[0] = 2.f; }\nconst char *s = "// x";\n')
+    assert bench.csrc_digest() != d
+    src.write_text('// a kernel\n__global__ void k(float *p) { p[0] = 1.f; }\nconst char *s = "// y";\n')
+    assert bench.csrc_digest() != d
